@@ -1,0 +1,322 @@
+"""CPU oracle for MAPE's data-parallel hot path (test infrastructure only).
+
+This file is test infrastructure.  Only the tests, the smoke check and the
+CPU-baseline leg of the benchmark may import it; the product path never
+calls it.  It shares no code with the CUDA path: both sides receive the same
+arrays from the seeded input generator and compute on their own.
+
+Everything is plain numpy in float64 (continuous stages) and int64 (integer
+stages), restating the paper's definitions and algorithm steps in the
+paper's order.  A library matmul serves as a step where the paper writes a
+matrix product; nothing is blocked, fused or reordered.
+
+Notation follows the paper: B is the n x d kernel-lattice basis (Theorem 3.2,
+§3.1), z in R^d a coordinate vector, g = B z a direction, l/u the bounds, and
+starts are rows (one start per row of Z).
+
+Readings of points the paper leaves open (each also listed in the design
+notes of the repository):
+  * gradient of the floor/ceil product: floor and ceil are treated as
+    locally constant, so d/dz (z-floor z)(ceil z-z) = ceil z + floor z - 2z;
+  * subgradient of |y| at 0 is 0 (sign(0) = 0);
+  * gradient of max{1/||z||_inf - 1, 0}: zero when ||z||_inf >= 1, else
+    -sign(z_k)/||z||_inf^2 at k = the FIRST index attaining max |z_j|; zero
+    at z = 0 exactly (where Phi is +inf);
+  * Adam: the textbook update with bias correction (Kingma & Ba), constants
+    beta1 = 0.9, beta2 = 0.999, eps = 1e-8; the loss is summed over starts,
+    so every start is an independent problem;
+  * rounding to the nearest integer breaks ties to even;
+  * the collected set excludes g = 0 and stores each direction once up to
+    sign, with the first nonzero entry positive;
+  * Algorithm 1 tries both +g and -g for every stored direction, with
+    lambda >= 1; among optimal moves it takes the lowest direction index (in
+    the sorted direction list), +g before -g, then the smallest lambda.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# §3.1: Theorem 3.2 and the inverse map z = (B^T B)^{-1} B^T g
+
+
+def kernel_basis_check(A, B):
+    """True iff A B = 0 exactly (condition for Theorem 3.2)."""
+    return bool(np.all(np.asarray(A, np.int64) @ np.asarray(B, np.int64) == 0))
+
+
+def project_to_coordinates(B, G0):
+    """z = (B^T B)^{-1} B^T g for every sample row g (§3.2, Algorithm 2).
+
+    Solved as the normal equations with a dense fp64 solve; B^T B is symmetric
+    positive definite because B has full column rank.
+    """
+    Bf = np.asarray(B, np.float64)
+    H = Bf.T @ Bf
+    R = np.asarray(G0, np.float64) @ Bf            # rows: (B^T g)^T
+    return np.linalg.solve(H, R.T).T               # (P, d)
+
+
+# ---------------------------------------------------------------------------
+# §3.2, Eq. (3): the surrogate Phi and its gradient
+
+
+def phi(B, Z, lam1, lam2):
+    """Phi(z) = ||B z||_1 + lam1 sum_i (z_i - floor z_i)(ceil z_i - z_i)
+    + lam2 max{1/||z||_inf - 1, 0}, one value per start row (Eq. (3))."""
+    Z = np.asarray(Z, np.float64)
+    Y = Z @ np.asarray(B, np.float64).T                      # rows: (B z)^T
+    l1 = np.abs(Y).sum(axis=1)
+    frac = ((Z - np.floor(Z)) * (np.ceil(Z) - Z)).sum(axis=1)
+    zinf = np.abs(Z).max(axis=1)
+    with np.errstate(divide="ignore"):
+        inv = np.where(zinf > 0, 1.0 / np.where(zinf > 0, zinf, 1.0), np.inf)
+    return l1 + lam1 * frac + lam2 * np.maximum(inv - 1.0, 0.0)
+
+
+def phi_grad(B, Z, lam1, lam2):
+    """Gradient of Eq. (3) for every start row, under the readings above."""
+    Z = np.asarray(Z, np.float64)
+    Bf = np.asarray(B, np.float64)
+    Y = Z @ Bf.T
+    grad = np.sign(Y) @ Bf                                   # B^T sign(B z)
+    grad += lam1 * (np.ceil(Z) + np.floor(Z) - 2.0 * Z)
+    absZ = np.abs(Z)
+    k = absZ.argmax(axis=1)                                   # first maximiser
+    zinf = absZ[np.arange(Z.shape[0]), k]
+    active = (zinf < 1.0) & (zinf > 0.0)
+    rows = np.nonzero(active)[0]
+    zk = Z[rows, k[rows]]
+    grad[rows, k[rows]] += -lam2 * np.sign(zk) / (zinf[rows] ** 2)
+    return grad
+
+
+def adam_update(z, m, v, grad, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step at step number t >= 1 (Kingma & Ba, Algorithm 1)."""
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    z = z - lr * m_hat / (np.sqrt(v_hat) + eps)
+    return z, m, v
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 2: round, map, bound test; conditions C1-C4 (§3)
+
+
+def round_and_map(B, Z):
+    """zhat = nearest integer to z (ties to even); g = B zhat (int64)."""
+    zhat = np.rint(np.asarray(Z, np.float64)).astype(np.int64)
+    return zhat, zhat @ np.asarray(B, np.int64).T
+
+
+def bound_consistent(G, l, u):
+    """C4: l - u <= g <= u - l, per row."""
+    span = np.asarray(u, np.int64) - np.asarray(l, np.int64)
+    return np.all(np.abs(np.asarray(G, np.int64)) <= span, axis=1)
+
+
+def kernel_condition(A, G):
+    """C1: A g = 0 exactly, per row."""
+    return np.all(np.asarray(G, np.int64) @ np.asarray(A, np.int64).T == 0, axis=1)
+
+
+def canonical_sign(g):
+    """The representative of {g, -g} whose first nonzero entry is positive."""
+    g = np.asarray(g, np.int64)
+    nz = np.nonzero(g)[0]
+    if nz.size and g[nz[0]] < 0:
+        return -g
+    return g
+
+
+def conformal_leq(x, y):
+    """x ⊑ y  iff  x_i y_i >= 0 and |x_i| <= |y_i| for all i (§1)."""
+    x = np.asarray(x, np.int64)
+    y = np.asarray(y, np.int64)
+    return bool(np.all(x * y >= 0) and np.all(np.abs(x) <= np.abs(y)))
+
+
+def minimal_elements(G):
+    """Rows g of G (a set stored once up to sign) with no other row h such that
+    h ⊑ g or -h ⊑ g: the ⊑-minimal elements of the symmetric set (C3).
+
+    Returns a boolean mask.  Plain O(K^2 n) comparison of every pair.
+    """
+    G = np.asarray(G, np.int64)
+    K = G.shape[0]
+    keep = np.ones(K, dtype=bool)
+    absG = np.abs(G)
+    for i in range(K):
+        g = G[i]
+        dominated_pos = np.all((G * g >= 0) & (absG <= absG[i]), axis=1)
+        dominated_neg = np.all((-G * g >= 0) & (absG <= absG[i]), axis=1)
+        hit = dominated_pos | dominated_neg
+        hit[i] = False
+        keep[i] = not hit.any()
+    return keep
+
+
+def sort_directions(G):
+    """Lexicographic row order (ascending, first column most significant)."""
+    G = np.asarray(G, np.int64)
+    if G.shape[0] == 0:
+        return G
+    order = np.lexsort(G.T[::-1])
+    return G[order]
+
+
+def collect(A, B, l, u, Z):
+    """The collection step of Algorithm 2 for one snapshot of all starts:
+    returns the set of canonical directions B round(z) that are nonzero,
+    bound-consistent (C4) and satisfy A g = 0 (C1)."""
+    _, G = round_and_map(B, Z)
+    ok = bound_consistent(G, l, u) & np.any(G != 0, axis=1) & kernel_condition(A, G)
+    return {tuple(canonical_sign(g)) for g in G[ok]}
+
+
+def parallel_extraction(A, B, l, u, Z0, T, lam1=0.85, lam2=1.0, lr=0.003,
+                        beta1=0.9, beta2=0.999, eps=1e-8, period=1,
+                        keep_trace=False):
+    """Algorithm 2 (§3.2) from given starting points Z0 (P x d).
+
+    For t = 1..T every start takes one Adam step on Eq. (3); every ``period``
+    steps the rounded point is mapped and, when it passes the tests, added to
+    the set.  Afterwards the set is reduced to its ⊑-minimal elements and
+    sorted.  Returns a dict with the final directions and counts.
+    """
+    z = np.asarray(Z0, np.float64).copy()
+    m = np.zeros_like(z)
+    v = np.zeros_like(z)
+    found = set()
+    trace = [] if keep_trace else None
+    for t in range(1, T + 1):
+        grad = phi_grad(B, z, lam1, lam2)
+        z, m, v = adam_update(z, m, v, grad, t, lr, beta1, beta2, eps)
+        if keep_trace:
+            trace.append(z.copy())
+        if t % period == 0:
+            found |= collect(A, B, l, u, z)
+    unique = sort_directions(np.array(sorted(found), dtype=np.int64).reshape(-1, len(l)))
+    keep = minimal_elements(unique)
+    return {"unique": unique, "directions": unique[keep], "Z": z, "M": m, "V": v,
+            "trace": trace}
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 (§2): augmentation with a direction set as the test set
+
+
+def f_value(Q, c, w, x):
+    """f(x) = x^T Q x + c^T x + sum_i w_i x_i^4 in exact integers."""
+    x = np.asarray(x, np.int64)
+    val = int(x @ np.asarray(Q, np.int64) @ x) + int(np.asarray(c, np.int64) @ x)
+    if w is not None:
+        val += int(np.asarray(w, np.int64) @ (x ** 4))
+    return val
+
+
+def in_feasible_region(A, b, l, u, x):
+    """x in S: A x = b and l <= x <= u."""
+    x = np.asarray(x, np.int64)
+    return bool(np.all(np.asarray(A, np.int64) @ x == np.asarray(b, np.int64))
+                and np.all(x >= l) and np.all(x <= u))
+
+
+def feasible_step_lengths(l, u, x, g):
+    """All lambda >= 1 with l <= x + lambda g <= u (by direct test)."""
+    g = np.asarray(g, np.int64)
+    x = np.asarray(x, np.int64)
+    if not np.any(g):
+        return []
+    out = []
+    lam = 1
+    while True:
+        y = x + lam * g
+        if np.all(y >= l) and np.all(y <= u):
+            out.append(lam)
+            lam += 1
+        else:
+            return out
+
+
+def augment(A, b, l, u, Q, c, w, directions, x0, max_iters=100000):
+    """Algorithm 1: while some (g, lambda) with g in ±directions, lambda >= 1,
+    x + lambda g in S and f(x + lambda g) < f(x) exists, move to the argmin of
+    f(x + lambda g).  f is evaluated directly at every candidate point.
+
+    Returns (x, f(x), list of moves (direction index, sign, lambda, f)).
+    """
+    x = np.asarray(x0, np.int64).copy()
+    fx = f_value(Q, c, w, x)
+    moves = []
+    D = np.asarray(directions, np.int64)
+    for _ in range(max_iters):
+        best = None
+        for k in range(D.shape[0]):
+            for sgn in (1, -1):
+                g = sgn * D[k]
+                for lam in feasible_step_lengths(l, u, x, g):
+                    y = x + lam * g
+                    if not in_feasible_region(A, b, l, u, y):
+                        continue
+                    fy = f_value(Q, c, w, y)
+                    if fy < fx and (best is None or fy < best[0]):
+                        best = (fy, k, sgn, lam)
+        if best is None:
+            break
+        fy, k, sgn, lam = best
+        x = x + lam * sgn * D[k]
+        fx = fy
+        moves.append((k, sgn, lam, fy))
+    return x, fx, moves
+
+
+# ---------------------------------------------------------------------------
+# Definition of the Graver basis (§1), by enumeration, for tiny instances
+
+
+def kernel_box(A, bound):
+    """All nonzero integer g with A g = 0 and |g_i| <= bound."""
+    A = np.asarray(A, np.int64)
+    n = A.shape[1]
+    pts = np.array(list(itertools.product(range(-bound, bound + 1), repeat=n)),
+                   dtype=np.int64)
+    ok = np.all(pts @ A.T == 0, axis=1) & np.any(pts != 0, axis=1)
+    return pts[ok]
+
+
+def graver_basis_box(A, bound):
+    """⊑-minimal elements of Ker_Z(A) \\ {0} among |g_i| <= bound, one per sign
+    pair (canonical sign), sorted.  Inside a box, minimality among the box's
+    kernel elements is the same as minimality in all of Ker_Z(A), because
+    every h ⊑ g also lies in the box."""
+    K = kernel_box(A, bound)
+    absK = np.abs(K)
+    out = set()
+    for i in range(K.shape[0]):
+        g = K[i]
+        below = np.all((K * g >= 0) & (absK <= absK[i]), axis=1)
+        below[i] = False
+        if not below.any():
+            out.add(tuple(canonical_sign(g)))
+    return sort_directions(np.array(sorted(out), dtype=np.int64).reshape(-1, A.shape[1]))
+
+
+def is_graver_element(A, g):
+    """g is ⊑-minimal in Ker_Z(A) \\ {0}: no nonzero h ⊑ g, h != g, has A h = 0.
+    Enumerates every h conformal to g directly."""
+    g = np.asarray(g, np.int64)
+    A = np.asarray(A, np.int64)
+    if not np.any(g) or np.any(A @ g != 0):
+        return False
+    ranges = [range(0, abs(int(gi)) + 1) for gi in g]
+    sgn = np.sign(g)
+    for mags in itertools.product(*ranges):
+        h = sgn * np.array(mags, np.int64)
+        if np.any(h) and np.any(h != g) and np.all(A @ h == 0):
+            return False
+    return True

@@ -1,0 +1,297 @@
+"""Pins for the CPU oracle: each test checks it against something other than
+itself -- a hand-evaluated example, a textbook Graver basis, a closed form, a
+library routine (torch.optim.Adam), finite differences, an invariant or brute
+force on tiny inputs.  CPU only."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mape_oracle as O
+from paper_2412_13576_gb300 import instances as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            rows.setdefault(key, []).append([float(v) for v in vals])
+    return rows
+
+
+# --- §3.1, Theorem 3.2 ------------------------------------------------------
+
+@pytest.mark.parametrize("make", [I.small_dense, I.medium_sparse, I.tiny_graver_case])
+def test_closed_form_basis_is_kernel(make):
+    inst = make()
+    assert O.kernel_basis_check(inst.A, inst.B)
+    bad = inst.B.copy()
+    bad[-1, 0] += 1
+    assert not O.kernel_basis_check(inst.A, bad)
+    assert np.all(inst.A @ inst.xbar.astype(np.int64) == inst.b)
+    assert np.all(inst.xbar >= inst.l) and np.all(inst.xbar <= inst.u)
+
+
+def test_projection_is_inverse_map():
+    """z = (B^T B)^{-1} B^T g returns w exactly (to fp64 rounding) when g = B w."""
+    inst = I.small_dense()
+    rng = np.random.default_rng(0)
+    W = rng.integers(-4, 5, size=(50, inst.d))
+    G = W @ inst.B.T
+    Z = O.project_to_coordinates(inst.B, G)
+    np.testing.assert_allclose(Z, W, atol=1e-9)
+    # for a generic g the residual is orthogonal to the range of B
+    G0 = I.uniform_samples(inst, 40, seed=3).G0
+    Z = O.project_to_coordinates(inst.B, G0)
+    resid = G0.astype(np.float64) - Z @ inst.B.T
+    np.testing.assert_allclose(resid @ inst.B, 0.0, atol=1e-9)
+
+
+# --- §3.2, Eq. (3) ------------------------------------------------------------
+
+def test_phi_and_grad_hand_example():
+    gold = _read_golden("phi_hand_example.txt")
+    B = np.array(gold["B"])
+    z = np.array(gold["z"])
+    assert O.phi(B, z, 0.85, 1.0)[0] == pytest.approx(gold["phi"][0][0], abs=1e-12)
+    np.testing.assert_allclose(O.phi_grad(B, z, 0.85, 1.0)[0], gold["grad"][0], atol=1e-12)
+
+
+def test_phi_at_integer_points_is_l1_norm():
+    inst = I.small_dense()
+    rng = np.random.default_rng(1)
+    Z = rng.integers(-3, 4, size=(64, inst.d)).astype(np.float64)
+    Z[np.abs(Z).max(axis=1) == 0, 0] = 1.0
+    expect = np.abs(Z @ inst.B.T).sum(axis=1)
+    np.testing.assert_allclose(O.phi(inst.B, Z, 0.85, 1.0), expect, rtol=0, atol=1e-12)
+    # the integrality term has zero gradient at integers; with ||z||_inf >= 1
+    # the gradient is B^T sign(Bz) alone
+    g = O.phi_grad(inst.B, Z, 0.85, 1.0)
+    np.testing.assert_allclose(g, np.sign(Z @ inst.B.T) @ inst.B, atol=1e-12)
+
+
+def test_phi_at_origin_is_infinite():
+    B = np.eye(3)
+    assert np.isinf(O.phi(B, np.zeros((1, 3)), 0.85, 1.0)[0])
+    assert np.all(O.phi_grad(B, np.zeros((1, 3)), 0.85, 1.0) == 0)
+
+
+def _away_from_kinks(B, Z, tol):
+    Y = Z @ np.asarray(B, np.float64).T
+    fr = np.abs(Z - np.rint(Z))
+    a = np.sort(np.abs(Z), axis=1)
+    zinf = a[:, -1]
+    return ((np.abs(Y).min(axis=1) > tol) & (fr.min(axis=1) > tol)
+            & (np.abs(zinf - 1.0) > tol) & (a[:, -1] - a[:, -2] > tol))
+
+
+@pytest.mark.parametrize("scale", [0.4, 3.0])
+def test_grad_matches_central_differences(scale):
+    """Central differences of Phi alone (no gradient formula) at points away
+    from the kinks of |.|, floor/ceil and the max; scale 0.4 puts most points
+    inside ||z||_inf < 1 so the inverse-norm term is active."""
+    inst = I.small_dense()
+    rng = np.random.default_rng(2)
+    Z = rng.uniform(-scale, scale, size=(400, inst.d))
+    Z = Z[_away_from_kinks(inst.B, Z, 1e-3)][:40]
+    assert Z.shape[0] >= 10
+    h = 1e-7
+    fd = np.zeros_like(Z)
+    for j in range(inst.d):
+        e = np.zeros(inst.d)
+        e[j] = h
+        fd[:, j] = (O.phi(inst.B, Z + e, 0.85, 1.0) - O.phi(inst.B, Z - e, 0.85, 1.0)) / (2 * h)
+    np.testing.assert_allclose(O.phi_grad(inst.B, Z, 0.85, 1.0), fd, rtol=1e-6, atol=1e-5)
+    if scale < 1:
+        assert (np.abs(Z).max(axis=1) < 1).any()
+
+
+def test_adam_first_step_moves_by_lr_sign():
+    rng = np.random.default_rng(3)
+    z = rng.standard_normal((5, 7))
+    grad = rng.standard_normal((5, 7))
+    z1, m1, v1 = O.adam_update(z, np.zeros_like(z), np.zeros_like(z), grad, 1, 0.003)
+    np.testing.assert_allclose(z1 - z, -0.003 * np.sign(grad), rtol=1e-6)
+
+
+def test_adam_matches_torch_optimizer():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    z0 = rng.standard_normal((6, 5))
+    p = torch.nn.Parameter(torch.tensor(z0, dtype=torch.float64))
+    opt = torch.optim.Adam([p], lr=0.003, betas=(0.9, 0.999), eps=1e-8)
+    z, m, v = z0.copy(), np.zeros_like(z0), np.zeros_like(z0)
+    for t in range(1, 26):
+        grad = rng.standard_normal(z0.shape)
+        p.grad = torch.tensor(grad)
+        opt.step()
+        z, m, v = O.adam_update(z, m, v, grad, t, 0.003)
+    np.testing.assert_allclose(z, p.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+# --- Algorithm 2: rounding, C1, C4, canonical sign ----------------------------
+
+def test_rounding_breaks_ties_to_even():
+    B = np.eye(4, dtype=np.int64)
+    zhat, g = O.round_and_map(B, np.array([[0.5, 1.5, -2.5, 2.4999]]))
+    assert zhat.tolist() == [[0, 2, -2, 2]]
+    assert g.tolist() == [[0, 2, -2, 2]]
+
+
+def test_bound_and_kernel_conditions():
+    A = np.array([[1, 1, 1]])
+    l = np.array([0, 0, 0])
+    u = np.array([2, 1, 3])
+    G = np.array([[2, -1, -1], [3, 0, -3], [1, 1, 0], [0, 1, -1]])
+    assert O.bound_consistent(G, l, u).tolist() == [True, False, True, True]
+    assert O.kernel_condition(A, G).tolist() == [True, True, False, True]
+
+
+def test_canonical_sign_and_conformal_order():
+    assert O.canonical_sign([0, -2, 1]).tolist() == [0, 2, -1]
+    assert O.canonical_sign([0, 3, -1]).tolist() == [0, 3, -1]
+    assert O.conformal_leq([1, 0, -1], [2, 1, -1])
+    assert not O.conformal_leq([1, 0, -1], [2, 1, 1])     # sign conflict
+    assert not O.conformal_leq([1, 0, -2], [2, 1, -1])    # too long
+    assert O.conformal_leq([0, 0, 0], [1, -1, 0])
+
+
+# --- Graver basis: textbook cases and the definition ---------------------------
+
+def test_graver_basis_textbook_cases():
+    ones3 = O.graver_basis_box(np.array([[1, 1, 1]]), 3)
+    assert sorted(map(tuple, ones3.tolist())) == [(0, 1, -1), (1, -1, 0), (1, 0, -1)]
+    assert O.graver_basis_box(np.array([[1, 2]]), 4).tolist() == [[2, -1]]
+    assert O.graver_basis_box(np.array([[2, -3]]), 4).tolist() == [[3, 2]]
+    gold = _read_golden("twisted_cubic_graver.txt")
+    A = np.array(gold["A"], dtype=np.int64)
+    expect = sorted(tuple(int(v) for v in g) for g in gold["g"])
+    got = sorted(map(tuple, O.graver_basis_box(A, 3).tolist()))
+    assert got == expect
+    for g in expect:
+        assert O.is_graver_element(A, g)
+    assert not O.is_graver_element(A, (2, -4, 2, 0))   # twice an element
+    assert not O.is_graver_element(A, (1, -1, 0, 0))   # not in the kernel
+
+
+def _conformal_decomposition_exists(v, basis):
+    """Graver property: every kernel vector is a sum of basis elements (either
+    sign) each conformal to it."""
+    v = np.asarray(v, np.int64)
+    while np.any(v):
+        for g in basis:
+            for s in (1, -1):
+                if O.conformal_leq(s * g, v):
+                    v = v - s * g
+                    break
+            else:
+                continue
+            break
+        else:
+            return False
+    return True
+
+
+def test_tiny_graver_basis_decomposes_the_kernel_box():
+    inst = I.tiny_graver_case()
+    basis = O.graver_basis_box(inst.A, 3)
+    assert basis.shape[0] > 0
+    kernel = O.kernel_box(inst.A, 3)
+    for v in kernel:
+        assert _conformal_decomposition_exists(v, basis)
+    for g in basis:
+        assert O.is_graver_element(inst.A, g)
+
+
+def test_minimal_elements_agrees_with_enumeration():
+    inst = I.tiny_graver_case()
+    kernel = O.kernel_box(inst.A, 3)
+    canon = np.unique(np.array([O.canonical_sign(g) for g in kernel]), axis=0)
+    mins = canon[O.minimal_elements(canon)]
+    assert sorted(map(tuple, mins.tolist())) == sorted(map(tuple, O.graver_basis_box(inst.A, 3).tolist()))
+
+
+def test_extraction_on_tiny_instance_returns_graver_elements():
+    """Algorithm 2 with many starts: every returned direction is a true Graver
+    element (checked against the enumerated basis), lies in the kernel and in
+    the bound box; most of the basis is found."""
+    inst = I.tiny_graver_case()
+    st = I.normal_starts(inst, 2048, seed=5)
+    res = O.parallel_extraction(inst.A, inst.B, inst.l, inst.u, st.Z0, T=150)
+    D = res["directions"]
+    basis = set(map(tuple, O.graver_basis_box(inst.A, 3).tolist()))
+    assert D.shape[0] > 0
+    assert set(map(tuple, D.tolist())) <= basis
+    assert np.all(O.kernel_condition(inst.A, D))
+    assert np.all(O.bound_consistent(D, inst.l, inst.u))
+    assert D.shape[0] >= 0.5 * len(basis)
+
+
+# --- Algorithm 1 and Proposition 2.1 ------------------------------------------
+
+def test_f_value_hand_example():
+    Q = np.array([[2, -1], [-1, 0]])
+    c = np.array([3, -4])
+    w = np.array([1, 2])
+    x = np.array([2, -1])
+    # x^T Q x = 2*4 + 2*(-1)*2*(-1) + 0 = 8 + 4 = 12; c^T x = 6 + 4 = 10;
+    # sum w x^4 = 16 + 2 = 18
+    assert O.f_value(Q, c, w, x) == 40
+    assert O.f_value(Q, c, None, x) == 22
+
+
+def test_step_lengths_by_bounds():
+    l = np.array([0, 0, -3])
+    u = np.array([10, 4, 3])
+    assert O.feasible_step_lengths(l, u, [1, 1, 0], [2, 1, -1]) == [1, 2, 3]
+    assert O.feasible_step_lengths(l, u, [10, 1, 0], [1, 0, 0]) == []
+
+
+def _box_points(inst):
+    import itertools
+    rng = [range(int(a), int(b) + 1) for a, b in zip(inst.l, inst.u)]
+    pts = np.array(list(itertools.product(*rng)), dtype=np.int64)
+    return pts[np.all(pts @ inst.A.T.astype(np.int64) == inst.b, axis=1)]
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13, 14])
+def test_prop21_graver_augmentation_reaches_optimum(seed):
+    """Proposition 2.1: for separable convex f the Graver basis is a test set,
+    so Algorithm 1 from any feasible point reaches the global minimum (found
+    here by enumerating S)."""
+    inst = I.tiny_graver_case(seed=seed)
+    rng = np.random.default_rng(seed)
+    Q = np.diag(rng.integers(0, 4, size=inst.n))
+    c = rng.integers(-6, 7, size=inst.n)
+    w = rng.integers(0, 2, size=inst.n)
+    basis = O.graver_basis_box(inst.A, 3)
+    S = _box_points(inst)
+    best = min(O.f_value(Q, c, w, x) for x in S)
+    for x0 in S[rng.choice(S.shape[0], size=min(6, S.shape[0]), replace=False)]:
+        x, fx, moves = O.augment(inst.A, inst.b, inst.l, inst.u, Q, c, w, basis, x0)
+        assert fx == best
+        assert O.in_feasible_region(inst.A, inst.b, inst.l, inst.u, x)
+
+
+def test_augment_moves_keep_feasibility_and_strictly_decrease():
+    inst = I.small_dense()
+    st = I.normal_starts(inst, 256, seed=2001)
+    res = O.parallel_extraction(inst.A, inst.B, inst.l, inst.u, st.Z0, T=60)
+    D = res["directions"]
+    x = inst.xbar.astype(np.int64)
+    fx = O.f_value(inst.Q, inst.c, None, x)
+    xf, ff, moves = O.augment(inst.A, inst.b, inst.l, inst.u, inst.Q, inst.c, None, D, x)
+    assert len(moves) > 0
+    prev = fx
+    for k, s, lam, fval in moves:
+        x = x + lam * s * D[k]
+        assert O.in_feasible_region(inst.A, inst.b, inst.l, inst.u, x)
+        assert O.f_value(inst.Q, inst.c, None, x) == fval < prev
+        prev = fval
+    assert np.array_equal(x, xf)
