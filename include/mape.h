@@ -1,0 +1,328 @@
+/*
+ * mape.h -- C ABI of the GB300 implementation of MAPE's data-parallel hot
+ * path (Multi-start Augmentation via Parallel Extraction, Liu, Wang & Yang,
+ * "Parallel Graver Basis Extraction for Nonlinear Integer Optimization").
+ *
+ * Problem (Eq. (1), §1):  min f(x)  s.t.  A x = b,  l <= x <= u,  x in Z^n,
+ * with f(x) = x^T Q x + c^T x + sum_i w_i x_i^4 (Q symmetric, integer; w >= 0
+ * optional).  B (n x d, d = n - m) is a basis of the integer kernel
+ * Ker_Z(A) = L(B) (Theorem 3.2, §3.1).
+ *
+ * Two layers:
+ *   1. Stage entry points (mape_project_starts ... mape_augment_run).  All
+ *      array arguments are DEVICE pointers owned by the caller; sizes are host
+ *      integers.  Work is enqueued on `stream` (a cudaStream_t, NULL = legacy
+ *      default stream).  Entry points that return a count through a host
+ *      pointer synchronise the stream before returning; the others are
+ *      asynchronous.  Scratch memory is passed in as (workspace, bytes) and its
+ *      size is given by the matching *_workspace_bytes query.
+ *   2. The instance handle (mape_create_instance ... mape_destroy).  All array
+ *      arguments are HOST pointers owned by the caller and copied during the
+ *      call; the library owns every device buffer of the handle, allocated
+ *      through the allocator set with mape_set_allocator (default:
+ *      cudaMallocAsync on the handle's stream).  extract_directions and
+ *      augment return at once and run on a worker thread of the handle;
+ *      mape_poll reads progress, mape_wait blocks with a timeout.
+ *
+ * Every call returns MAPE_OK (0), a negative error code, or a positive
+ * warning code.  Layouts are row-major (C order) unless stated.
+ * Direction sets are stored as int8 rows of pitch `ldg` bytes (ldg a multiple
+ * of 16, ldg >= n), which requires max_i (u_i - l_i) <= 127: with condition C4
+ * (l - u <= g <= u - l, §3) every collected direction then fits in int8.
+ */
+#ifndef MAPE_H_
+#define MAPE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define MAPE_OK                    0
+#define MAPE_ERR_INVALID_ARG      -1  /* NULL pointer, negative size, bad enum */
+#define MAPE_ERR_SHAPE            -2  /* sizes outside what the path supports */
+#define MAPE_ERR_NOT_KERNEL_BASIS -3  /* A B != 0 (Theorem 3.2 precondition) */
+#define MAPE_ERR_BOUNDS           -4  /* some u_i < l_i, or u - l > 127 */
+#define MAPE_ERR_INFEASIBLE       -5  /* an augmentation start is not in S */
+#define MAPE_ERR_OVERFLOW         -6  /* exact integer range of a stage exceeded */
+#define MAPE_ERR_CAPACITY         -7  /* an output buffer or table is full */
+#define MAPE_ERR_CUDA             -8  /* a CUDA runtime call failed */
+#define MAPE_ERR_TIMEOUT          -9  /* mape_wait timed out / bounded wait gave up */
+#define MAPE_ERR_STATE           -10  /* call not valid in the handle's phase */
+#define MAPE_ERR_OOM             -11  /* device allocation failed */
+#define MAPE_ERR_KERNEL_TEST     -12  /* a collected direction failed A g = 0 (C1) */
+#define MAPE_ERR_NUMERIC         -13  /* an iterate left the exactly-rounded range */
+#define MAPE_ERR_CANCELLED       -14  /* mape_cancel was called */
+
+/* ---- precision of the extraction contractions ---------------------------- */
+#define MAPE_PREC_FP32 0  /* CUDA-core FP32, unfused per-step kernels           */
+#define MAPE_PREC_BF16 1  /* tcgen05 BF16 MMAs with FP32 accumulation in TMEM,
+                             persistent fused kernel over all T steps; z enters
+                             the forward product as hi + lo (two BF16 terms),
+                             accurate to about FP32                             */
+#define MAPE_PREC_BF16X1 2 /* as MAPE_PREC_BF16 with z as one BF16 term (hi):
+                             half the forward MMAs, 8-bit z in B z            */
+
+/* ---- hyper-parameters (§3.2, §4: lambda1 = 0.85, lambda2 = 1, lr = 0.003) - */
+typedef struct {
+  float lambda1, lambda2;      /* weights in Eq. (3)                            */
+  float lr, eps;               /* Adam (Kingma & Ba) step size and epsilon      */
+  double beta1, beta2;         /* Adam decay rates; double so that 1 - beta is
+                                  formed exactly (0.999 is not an FP32 value:
+                                  1 - 0.999f is off by 1.3e-5 relative)        */
+  int32_t T;                   /* Adam steps per start                          */
+  int32_t period;              /* collect every `period` steps (Algorithm 2)    */
+  int32_t precision;           /* MAPE_PREC_*                                   */
+  int32_t reserved;
+  int64_t cand_capacity;       /* max collected candidates (0 = P*T bound)      */
+  int64_t max_aug_iters;       /* cap on Algorithm 1 iterations per call        */
+} mape_config;
+
+/* Fills `cfg` with the paper's values: lambda1 0.85, lambda2 1, lr 0.003,
+ * beta1 0.9, beta2 0.999, eps 1e-8, T 1000, period 1, BF16. */
+void mape_default_config(mape_config* cfg);
+
+/* ========================================================================== *
+ * Stage entry points (device pointers)                                        *
+ * ========================================================================== */
+
+/* a2 -- starting points (§3.2, Algorithm 2): z0 = (B^T B)^{-1} B^T g for every
+ * sample row g of G0.
+ *   B   [n x d] int32      kernel basis, full column rank
+ *   G0  [P x n] float32    samples g ~ Uniform(l - u, u - l), one per start
+ *   Z0  [P x d] float32    output starting points
+ * Forms B^T B, factors it by Cholesky in FP32 on the device and solves.
+ * Errors: INVALID_ARG, SHAPE (d > 4096), NUMERIC (B^T B not positive
+ * definite in FP32), CAPACITY (workspace too small), CUDA.  Synchronous. */
+size_t mape_project_workspace_bytes(int32_t n, int32_t d);
+int mape_project_starts(const int32_t* B, int32_t n, int32_t d,
+                        const float* G0, int32_t P, float* Z0,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
+/* a3-a5 -- Eq. (3) and its gradient in FP32 for every start row z of Z:
+ *   phi[p]      = ||B z||_1 + lambda1 sum_i (z_i - floor z_i)(ceil z_i - z_i)
+ *                 + lambda2 max{1/||z||_inf - 1, 0}
+ *   grad[p, :]  = B^T sign(B z) + lambda1 (ceil z + floor z - 2 z)
+ *                 - lambda2 [||z||_inf < 1] sign(z_k) / ||z||_inf^2 e_k,
+ *                 k the first index of max |z_j|; sign(0) = 0; zero at z = 0.
+ *   B [n x d] int32, Z [P x d] float32, phi [P] float32 (+inf at z = 0),
+ *   grad [P x d] float32.  Asynchronous. */
+int mape_phi_grad(const int32_t* B, int32_t n, int32_t d, const float* Z,
+                  int32_t P, float lambda1, float lambda2, float* phi,
+                  float* grad, void* stream);
+
+/* a3-a8 -- Algorithm 2 (§3.2), the parallel extraction loop, for T steps:
+ * every start takes Adam steps on Eq. (3); after each step whose number is a
+ * multiple of `period` the rounded point g = B round(z) (ties to even) is
+ * tested for g != 0 and C4 (|g_i| <= span_i) and, if it passes and the
+ * rounded point changed since that start's previous collection in this call
+ * (the first collection of a call always counts), appended to `cand` in
+ * canonical sign (first nonzero entry positive).  Repeated directions are
+ * removed later by mape_dedup; skipping an unchanged rounding only avoids a
+ * duplicate.
+ * Continuing a run: pass the Z/M/V of the previous call and t0 = the number
+ * of steps already taken (Adam bias correction uses t0 + 1 ... t0 + T).
+ */
+typedef struct {
+  int32_t n, d, P;
+  const int32_t* B;        /* [n x d] int32                                  */
+  const int32_t* span;     /* [n] int32, u - l (C4)                           */
+  float* Z;                /* [P x d] in/out                                  */
+  float* M;                /* [P x d] in/out, Adam first moment               */
+  float* V;                /* [P x d] in/out, Adam second moment              */
+  int32_t t0, T, period, precision;
+  float lambda1, lambda2, lr, eps;
+  double beta1, beta2;
+  int8_t* cand;           /* [cand_cap x ldc] output rows                    */
+  int32_t ldc;             /* row pitch in bytes, multiple of 16, >= n        */
+  int32_t pad0;
+  int64_t cand_cap;
+  unsigned long long* cand_count; /* device counter, appended to (not reset)  */
+  int32_t* flags;          /* device word, OR-ed: 1 = cand overflow (rows
+                              beyond cand_cap are counted, not stored),
+                              2 = |round(z)| > 256 met on the BF16 path (the
+                              exactness bound of B round(z) in BF16; that
+                              start's rounding is not collected),
+                              4 = |round(z)| > 2^20 met on the FP32 path   */
+  float* dbg_phi;          /* optional [P]: Phi at the input point            */
+  float* dbg_grad;         /* optional [P x d]: gradient at the input point   */
+  void* workspace;
+  size_t workspace_bytes;
+} mape_extract_args;
+/* Errors: INVALID_ARG, SHAPE (BF16 path: n > 256 or d > 256 or the operand
+ * tiles exceed shared memory), CAPACITY (workspace), CUDA.  Asynchronous. */
+size_t mape_extract_workspace_bytes(int32_t n, int32_t d, int32_t P, int32_t precision);
+int mape_extract(const mape_extract_args* args, void* stream);
+
+/* a10 -- set union of Algorithm 2: removes repeated rows of `cand` (count
+ * rows, pitch ldc, n meaningful bytes) with a device hash table, and writes
+ * the distinct rows to `uniq` sorted lexicographically (signed bytes, first
+ * entry most significant).  *K_out = number of distinct rows.
+ * Errors: INVALID_ARG, CAPACITY (uniq_cap < distinct rows; *K_out is still
+ * set to the needed count), CUDA.  Synchronous. */
+size_t mape_dedup_workspace_bytes(int64_t count, int32_t ldc);
+int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t ldc,
+               int8_t* uniq, int64_t uniq_cap, int64_t* K_out,
+               void* workspace, size_t workspace_bytes, void* stream);
+
+/* a9 -- condition C1 (§3): ok[k] = 1 iff A g_k = 0 exactly (int32
+ * arithmetic, |A_ij| <= 2^23 and n <= 4096 keep every partial sum exact).
+ *   A [m x n] int32, G [K x ldg] int8.  *fail_count = rows with A g != 0.
+ * Synchronous (returns the count). */
+size_t mape_kernel_test_workspace_bytes(void);
+int mape_kernel_test(const int32_t* A, int32_t m, int32_t n, const int8_t* G,
+                     int64_t K, int32_t ldg, uint8_t* ok, int64_t* fail_count,
+                     void* workspace, size_t workspace_bytes, void* stream);
+
+/* a11 -- condition C3 within the set: keep[k] = 1 iff no other row h (with
+ * valid[h] != 0) satisfies h ⊑ g_k or -h ⊑ g_k, where x ⊑ y iff
+ * x_i y_i >= 0 and |x_i| <= |y_i| for all i (§1).  Rows with valid[k] == 0
+ * are neither kept nor used (valid may be NULL: all valid).  The kept rows
+ * are written, in their input order, to `out` (pitch ldg); *K_out = their
+ * number.  G must hold distinct rows in canonical sign.  Synchronous. */
+size_t mape_minimal_workspace_bytes(int64_t K, int32_t n);
+int mape_minimal_filter(const int8_t* G, int64_t K, int32_t n, int32_t ldg,
+                        const uint8_t* valid, uint8_t* keep, int8_t* out,
+                        int64_t* K_out, void* workspace,
+                        size_t workspace_bytes, void* stream);
+
+/* a12 -- per-direction coefficients for Algorithm 1 with
+ * f = x^T Q x + c^T x + sum w_i x_i^4:
+ *   a[k]  = g^T Q g            (int64, exact)
+ *   q4[k] = sum_i w_i g_i^4    (int64, exact; 0 when w == NULL)
+ * Q is given by its upper triangle including the diagonal as COO triplets
+ * (q_row <= q_col), nnz entries.  Asynchronous. */
+int mape_direction_coeffs(const int32_t* q_row, const int32_t* q_col,
+                          const int32_t* q_val, int32_t nnz, const int32_t* w,
+                          int32_t n, const int8_t* G, int64_t K, int32_t ldg,
+                          int64_t* a, int64_t* q4, void* stream);
+
+/* a13-a14 -- Algorithm 1 (§2) for S starts at once, with the direction set
+ * ±G as test set.  One iteration, for every start s still active:
+ *   r_s = 2 Q x_s + c;  for every k, sign e in {+1,-1}, lambda in
+ *   [1, lambda_max(x_s, e g_k)] (the largest lambda keeping l <= x + lambda e g
+ *   <= u), Delta f = lambda^2 a_k + lambda e g_k^T r_s + quartic terms (all
+ *   int64); take the minimal Delta f, ties to the lower k, then +g, then the
+ *   smaller lambda; if Delta f < 0 move x_s += lambda e g_k, else start s
+ *   stops.  A x = b holds along the way because A g = 0.
+ * Runs until every start stopped or max_iters iterations.
+ *   X     [S x n] int32 in/out (must satisfy l <= x <= u)
+ *   fval  [S] int64 out: f(x_s) at the end
+ *   moves optional [S x moves_cap x 4] int64: (k, e, lambda, f after move)
+ *   nmoves optional [S] int32: moves taken per start
+ *   *iters_out (host): iterations run.  Errors: INVALID_ARG, BOUNDS (a start
+ *   outside [l, u]), OVERFLOW (|Delta f| bound above 2^62), CUDA.
+ * Synchronous. */
+typedef struct {
+  int32_t n, S;
+  int64_t K;
+  const int8_t* G; int32_t ldg; int32_t pad0;
+  const int64_t* a; const int64_t* q4;
+  const int32_t* q_row; const int32_t* q_col; const int32_t* q_val; int32_t nnz;
+  int32_t pad1;
+  const int32_t* c; const int32_t* w; const int32_t* l; const int32_t* u;
+  int32_t* X; int64_t* fval;
+  int64_t* moves; int32_t* nmoves; int32_t moves_cap; int32_t pad2;
+  int64_t max_iters;
+  void* workspace; size_t workspace_bytes;
+} mape_augment_args;
+size_t mape_augment_workspace_bytes(int32_t n, int32_t S, int64_t K);
+int mape_augment_run(const mape_augment_args* args, int64_t* iters_out,
+                     void* stream);
+
+/* ========================================================================== *
+ * Instance handle (host pointers)                                             *
+ * ========================================================================== */
+
+typedef struct mape_instance* mape_handle;
+
+/* Device memory hooks used by every handle created afterwards.
+ * alloc(bytes, stream, ctx) returns a device pointer or NULL; free(ptr,
+ * bytes, stream, ctx).  Passing NULLs restores cudaMallocAsync/cudaFreeAsync. */
+typedef void* (*mape_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*mape_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+int mape_set_allocator(mape_alloc_fn alloc_fn, mape_free_fn free_fn, void* ctx);
+
+typedef struct {
+  int32_t n, m;
+  const int32_t* Q;   /* [n x n] symmetric                                  */
+  const int32_t* c;   /* [n]                                                */
+  const int32_t* w;   /* [n] >= 0, or NULL: no quartic term                 */
+} mape_problem;
+
+/* Validates and uploads one instance.  A [m x n], b [m] int64, l, u [n],
+ * B [n x d] (d = n - m) with A B = 0 checked on the device.
+ * Errors: INVALID_ARG, SHAPE, BOUNDS, NOT_KERNEL_BASIS, OOM, CUDA. */
+int mape_create_instance(const int32_t* A, const int64_t* b, const int32_t* l,
+                         const int32_t* u, const mape_problem* f,
+                         const int32_t* B, const mape_config* cfg,
+                         void* stream, mape_handle* out);
+
+/* Starts Algorithm 2 on the worker thread: P starts given either directly
+ * (Z0 [P x d], G0 == NULL) or as samples to project (G0 [P x n], Z0 == NULL).
+ * Z0 / G0 may be host or device pointers (unified addressing); they are
+ * copied before the call returns.
+ * Followed by dedup (a10), the kernel test (a9), the minimality filter (a11)
+ * and the direction coefficients (a12).  Returns at once. */
+int mape_extract_directions(mape_handle h, int32_t P, const float* Z0,
+                            const float* G0);
+
+/* Starts Algorithm 1 from S starts X0 [S x n] (each must lie in S; host or
+ * device pointer, copied before the call returns) with the current direction
+ * set.  f_or_NULL replaces the objective (same n): the
+ * direction set is reused for a new f (§1, reusability).  Returns at once. */
+int mape_augment(mape_handle h, const int32_t* X0, int32_t S,
+                 const mape_problem* f_or_NULL);
+
+#define MAPE_PHASE_IDLE       0
+#define MAPE_PHASE_EXTRACTING 1
+#define MAPE_PHASE_FILTERING  2
+#define MAPE_PHASE_AUGMENTING 3
+#define MAPE_PHASE_DONE       4
+#define MAPE_PHASE_ERROR      5
+
+typedef struct {
+  int32_t phase;            /* MAPE_PHASE_*                                  */
+  int32_t error;            /* status of the last finished job               */
+  int64_t candidates;       /* rows collected by Algorithm 2                  */
+  int64_t unique;           /* distinct rows                                  */
+  int64_t kernel_failures;  /* rows with A g != 0 (always 0 unless corrupted) */
+  int64_t directions;       /* rows kept after the minimality filter          */
+  int64_t aug_iters;        /* Algorithm 1 iterations in the last augment     */
+  int64_t best_f;           /* best f over the augmentation starts            */
+  int32_t best_start;       /* which start reached best_f                     */
+  int32_t pad0;
+  double extract_ms, filter_ms, augment_ms;  /* stage wall times             */
+  double first_improve_ms;  /* augment start -> first improving move found    */
+} mape_status;
+
+int mape_poll(mape_handle h, mape_status* st);          /* never blocks      */
+int mape_wait(mape_handle h, int64_t timeout_ns);       /* TIMEOUT, no hang  */
+int mape_cancel(mape_handle h);                          /* stops at next stage
+                                                            boundary          */
+
+/* Copies the direction set (K rows of n int32, sorted lexicographically) to
+ * G [cap x n].  CAPACITY if cap < K (K is still set). */
+int mape_get_directions(mape_handle h, int32_t* G, int64_t cap, int64_t* K);
+
+/* Copies the best solution x [n] and f(x) of the last augment. */
+int mape_get_solution(mape_handle h, int32_t* x, int64_t* fval);
+
+/* Copies every start's final point X [S x n] and value fval [S]. */
+int mape_get_solutions(mape_handle h, int32_t* X, int64_t* fval, int32_t S);
+
+void mape_destroy(mape_handle h);
+
+/* Version string of the library build. */
+const char* mape_version(void);
+
+/* Text of the last CUDA runtime error recorded by any call (or ""). */
+const char* mape_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MAPE_H_ */

@@ -1,0 +1,204 @@
+// a10: the set union of Algorithm 2 (§3.2).
+//
+// 1. every candidate row gets a 64-bit hash (16-byte vector loads);
+// 2. rows are inserted into an open-addressing table of row indices with
+//    linear probing.  Rows are fully written before the insert kernel runs,
+//    so an insert only ever compares against complete rows: a lock-free CAS
+//    on an empty slot makes a row the representative of its value, and a
+//    match (hash, then bytes) marks it a duplicate.  The table holds at least
+//    twice as many slots as rows, so every probe sequence meets an empty slot
+//    and the loop is bounded by the table size;
+// 3. representatives are compacted (order not fixed by the hardware) and
+//    then sorted lexicographically with a bitonic network over row indices,
+//    which fixes the output order independently of the atomics.
+#include "common.cuh"
+
+namespace {
+
+constexpr uint32_t kEmpty = 0xffffffffu;
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  x ^= x >> 31;
+  x *= 0x7fb5d329728ea185ull;
+  x ^= x >> 27;
+  x *= 0x81dadef4bc2dd44dull;
+  x ^= x >> 33;
+  return x;
+}
+
+__global__ void hash_rows_kernel(const int8_t* __restrict__ rows, int64_t count, int ldc,
+                                 uint64_t* __restrict__ h) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= count) return;
+  const uint4* p = reinterpret_cast<const uint4*>(rows + r * ldc);
+  uint64_t acc = 0x243f6a8885a308d3ull ^ (uint64_t)ldc;
+  for (int c = 0; c < ldc / 16; ++c) {
+    uint4 v = p[c];
+    acc = mix64(acc ^ (((uint64_t)v.y << 32) | v.x));
+    acc = mix64(acc + (((uint64_t)v.w << 32) | v.z));
+  }
+  h[r] = acc;
+}
+
+__device__ __forceinline__ bool rows_equal(const int8_t* a, const int8_t* b, int ldc) {
+  const uint4* pa = reinterpret_cast<const uint4*>(a);
+  const uint4* pb = reinterpret_cast<const uint4*>(b);
+  for (int c = 0; c < ldc / 16; ++c) {
+    uint4 x = pa[c], y = pb[c];
+    if (x.x != y.x || x.y != y.y || x.z != y.z || x.w != y.w) return false;
+  }
+  return true;
+}
+
+__global__ void insert_kernel(const int8_t* __restrict__ rows, const uint64_t* __restrict__ h, int64_t count,
+                              int ldc, uint32_t* __restrict__ table, uint64_t mask,
+                              uint8_t* __restrict__ is_rep) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= count) return;
+  uint64_t hr = h[r];
+  uint64_t slot = hr & mask;
+  uint8_t rep = 0;
+  for (uint64_t probe = 0; probe <= mask; ++probe) {
+    uint32_t cur = table[slot];
+    if (cur == kEmpty) {
+      uint32_t old = atomicCAS(&table[slot], kEmpty, (uint32_t)r);
+      if (old == kEmpty) { rep = 1; break; }
+      cur = old;
+    }
+    if (h[cur] == hr && rows_equal(rows + (int64_t)cur * ldc, rows + r * ldc, ldc)) break;
+    slot = (slot + 1) & mask;
+  }
+  is_rep[r] = rep;
+}
+
+__global__ void compact_reps_kernel(const uint8_t* __restrict__ is_rep, int64_t count,
+                                    uint32_t* __restrict__ idx, unsigned long long* __restrict__ K) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= count || !is_rep[r]) return;
+  unsigned long long at = atomicAdd(K, 1ull);
+  idx[at] = (uint32_t)r;
+}
+
+__global__ void pad_idx_kernel(uint32_t* idx, int64_t from, int64_t to) {
+  int64_t i = from + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < to) idx[i] = kEmpty;
+}
+
+// Lexicographic order on signed bytes; kEmpty sorts last.
+__device__ __forceinline__ int cmp_rows(const int8_t* rows, int ldc, uint32_t a, uint32_t b) {
+  if (a == b) return 0;
+  if (a == kEmpty) return 1;
+  if (b == kEmpty) return -1;
+  const uint32_t* pa = reinterpret_cast<const uint32_t*>(rows + (int64_t)a * ldc);
+  const uint32_t* pb = reinterpret_cast<const uint32_t*>(rows + (int64_t)b * ldc);
+  for (int c = 0; c < ldc / 4; ++c) {
+    // first byte most significant; flip the sign bits so unsigned order = signed order
+    uint32_t x = __byte_perm(pa[c], 0, 0x0123) ^ 0x80808080u;
+    uint32_t y = __byte_perm(pb[c], 0, 0x0123) ^ 0x80808080u;
+    if (x != y) return x < y ? -1 : 1;
+  }
+  return 0;
+}
+
+__global__ void bitonic_step_kernel(const int8_t* __restrict__ rows, int ldc, uint32_t* __restrict__ idx,
+                                    int64_t npad, int64_t j, int64_t k) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  int64_t l = i ^ j;
+  if (l <= i) return;
+  uint32_t a = idx[i], b = idx[l];
+  bool ascending = (i & k) == 0;
+  int c = cmp_rows(rows, ldc, a, b);
+  if ((ascending && c > 0) || (!ascending && c < 0)) {
+    idx[i] = b;
+    idx[l] = a;
+  }
+}
+
+__global__ void gather_rows_kernel(const int8_t* __restrict__ rows, int ldc, const uint32_t* __restrict__ idx,
+                                   int64_t K, int8_t* __restrict__ out) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int chunks = ldc / 16;
+  int64_t r = t / chunks;
+  int c = (int)(t % chunks);
+  if (r >= K) return;
+  reinterpret_cast<uint4*>(out + r * ldc)[c] = reinterpret_cast<const uint4*>(rows + (int64_t)idx[r] * ldc)[c];
+}
+
+uint64_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+namespace mape_detail {
+
+// Sorts rows[idx[0..K)] lexicographically in place of idx (npad >= K, power of 2,
+// idx[K..npad) set to the sentinel by this call).
+int sort_row_indices(const int8_t* rows, int ldc, uint32_t* idx, int64_t K, int64_t npad, cudaStream_t st) {
+  if (npad > K) pad_idx_kernel<<<(unsigned)ceil_div(npad - K, 256), 256, 0, st>>>(idx, K, npad);
+  for (int64_t k = 2; k <= npad; k <<= 1)
+    for (int64_t j = k >> 1; j > 0; j >>= 1)
+      bitonic_step_kernel<<<(unsigned)ceil_div(npad, 256), 256, 0, st>>>(rows, ldc, idx, npad, j, k);
+  MAPE_LAUNCH_CHECK();
+  return MAPE_OK;
+}
+
+uint64_t dedup_table_slots(int64_t count) { return next_pow2((uint64_t)(count > 0 ? count : 1) * 2); }
+
+}  // namespace mape_detail
+
+extern "C" size_t mape_dedup_workspace_bytes(int64_t count, int32_t ldc) {
+  (void)ldc;
+  if (count < 0) return 0;
+  mape_detail::Sizer s;
+  s.take<uint64_t>((size_t)count);                               // hashes
+  s.take<uint32_t>((size_t)mape_detail::dedup_table_slots(count)); // table
+  s.take<uint8_t>((size_t)count);                                 // representative flags
+  s.take<uint32_t>((size_t)next_pow2((uint64_t)(count > 0 ? count : 1)));  // sorted indices
+  s.take<unsigned long long>(1);                                  // counter
+  return s.bytes();
+}
+
+extern "C" int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t ldc, int8_t* uniq,
+                          int64_t uniq_cap, int64_t* K_out, void* workspace, size_t workspace_bytes,
+                          void* stream) {
+  using namespace mape_detail;
+  if (!K_out || count < 0 || n <= 0 || ldc < n || ldc % 16 != 0 || uniq_cap < 0) return MAPE_ERR_INVALID_ARG;
+  if (count > 0 && !cand) return MAPE_ERR_INVALID_ARG;
+  if (count >= (int64_t)kEmpty) return MAPE_ERR_SHAPE;
+  *K_out = 0;
+  if (count == 0) return MAPE_OK;
+  Carver cv(workspace, workspace_bytes);
+  uint64_t* h = cv.take<uint64_t>((size_t)count);
+  uint64_t slots = dedup_table_slots(count);
+  uint32_t* table = cv.take<uint32_t>((size_t)slots);
+  uint8_t* is_rep = cv.take<uint8_t>((size_t)count);
+  uint64_t npad_cap = next_pow2((uint64_t)count);
+  uint32_t* idx = cv.take<uint32_t>((size_t)npad_cap);
+  unsigned long long* dK = cv.take<unsigned long long>(1);
+  if (!cv.ok) return MAPE_ERR_CAPACITY;
+  cudaStream_t st = as_stream(stream);
+  unsigned g = (unsigned)ceil_div(count, 256);
+  MAPE_CUDA_TRY(cudaMemsetAsync(table, 0xff, slots * sizeof(uint32_t), st));
+  MAPE_CUDA_TRY(cudaMemsetAsync(dK, 0, sizeof(unsigned long long), st));
+  hash_rows_kernel<<<g, 256, 0, st>>>(cand, count, ldc, h);
+  insert_kernel<<<g, 256, 0, st>>>(cand, h, count, ldc, table, slots - 1, is_rep);
+  compact_reps_kernel<<<g, 256, 0, st>>>(is_rep, count, idx, dK);
+  MAPE_LAUNCH_CHECK();
+  unsigned long long K = 0;
+  MAPE_CUDA_TRY(cudaMemcpyAsync(&K, dK, sizeof(K), cudaMemcpyDeviceToHost, st));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  *K_out = (int64_t)K;
+  if ((int64_t)K > uniq_cap) return MAPE_ERR_CAPACITY;
+  if (!uniq) return MAPE_ERR_INVALID_ARG;
+  int rc = sort_row_indices(cand, ldc, idx, (int64_t)K, (int64_t)next_pow2(K), st);
+  if (rc != MAPE_OK) return rc;
+  int64_t chunks = (int64_t)K * (ldc / 16);
+  gather_rows_kernel<<<(unsigned)ceil_div(chunks, 256), 256, 0, st>>>(cand, ldc, idx, (int64_t)K, uniq);
+  MAPE_LAUNCH_CHECK();
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  return MAPE_OK;
+}

@@ -1,0 +1,651 @@
+// Algorithm 2 (§3.2) on the 5th-generation tensor cores: one persistent
+// kernel runs all T Adam steps; each CTA owns 128 starts for the whole run.
+//
+// Start p of the tile is row p of every MMA (M = 128) and lane p of TMEM, so
+// every per-start reduction (||z||_inf, its first maximiser, the bound test,
+// the first nonzero entry) stays inside the lanes that own that start.  Per
+// step, with B held in shared memory as BF16 (exact: |B_ij| <= 256):
+//   D1 = hi(Z) . B^T + lo(Z) . B^T  (M=128, N=n_pad, K=d_pad) -> TMEM cols [0, n_pad)
+//        with hi = bf16(z), lo = bf16(z - hi): z carried to ~16 significant
+//        bits, so B z is as accurate as an FP32 dot product (one term, hi only,
+//        is the faster and coarser MAPE_PREC_BF16X1)
+//   D2 = bf16(round Z) . B^T     (same shape, previous step) -> TMEM cols [256, 256+n_pad)
+//        exact: |round z| <= 256 is exact in BF16, every partial sum is an
+//        integer below 2^24 and FP32 accumulation is exact; D2 holds g = B round(z)
+//   S  = sign(D1) as BF16 {-1,0,1} written to shared memory
+//   G  = S . B                   (M=128, N=d_pad, K=n_pad)  -> TMEM cols [0, d_pad)
+//        B is read through an MN-major descriptor of the same shared tile
+//        (a transposed K-major copy is kept instead when it fits)
+//   grad = G + lambda1 (ceil z + floor z - 2 z) + inverse-norm term; Adam on
+//   the FP32 master z, m, v (coordinate-major in global memory, L2 resident);
+//   the new bf16(z), bf16(round z) operands are written for the next step.
+// The candidate of step t (D2 of step t+1) is tested (C4, nonzero), signed
+// canonically and appended while the G MMA runs.
+//
+// 16 warps: warp w serves TMEM lane quarter w % 4 (the only lanes it may
+// access) and every 4th 16-column chunk starting at chunk w / 4.  Operands are
+// stored in the canonical no-swizzle K-major layout: 8 rows x 16 bytes core
+// matrices, K-adjacent core matrices 128 bytes apart (LBO), 8-row groups
+// (K/8) * 128 bytes apart (SBO).
+//
+// Every wait on the MMA barrier is bounded; on time-out the CTA records flag
+// 16, leaves the loop together (block-wide vote), frees its TMEM and returns.
+#include "common.cuh"
+#include "extract_internal.cuh"
+
+#include <cuda_bf16.h>
+#include <vector>
+
+namespace {
+
+constexpr int kTileM = 128;
+constexpr int kWarps = 16;
+constexpr int kThreads = kWarps * 32;
+constexpr int kSplits = kWarps / 4;
+constexpr int kColD2 = 256;
+constexpr int kTmemCols = 512;
+constexpr uint32_t kWaitLimit = 1u << 20;
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: an MMA chain takes microseconds
+constexpr int kNoNz = 0x7fffffff;
+
+// ---- PTX wrappers ------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05; base offset 0, no swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: D f32, A/B bf16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait bounded in time (kWaitNs of the global timer) and in iterations;
+// returns true if the phase completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+  __nv_bfloat16 h = __float2bfloat16_rn(x);
+  return *reinterpret_cast<uint16_t*>(&h);
+}
+
+__device__ __forceinline__ float bf16_value(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
+// MN-major no-swizzle canonical layout ((T,1,m),(8,k)):((1,T,SBO),(1T,LBO)):
+// the 8-row K groups are LBO apart and the 16-byte MN groups SBO apart.
+#ifndef MAPE_TC_MN_LBO_IS_K
+#define MAPE_TC_MN_LBO_IS_K 1
+#endif
+constexpr bool kMnLbo = MAPE_TC_MN_LBO_IS_K != 0;
+
+// byte offset of element (row r, column k) in a no-swizzle K-major tile with K columns
+__device__ __forceinline__ uint32_t op_off(int r, int k, int K) {
+  return (uint32_t)((((r >> 3) * (K >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+// writes 16 bf16 values (columns k0..k0+15 of row r) as two 16-byte stores
+__device__ __forceinline__ void store_row16(uint8_t* tile, int r, int k0, int K, const uint16_t (&h)[16]) {
+  uint4 lo, hi;
+  lo.x = h[0] | ((uint32_t)h[1] << 16);
+  lo.y = h[2] | ((uint32_t)h[3] << 16);
+  lo.z = h[4] | ((uint32_t)h[5] << 16);
+  lo.w = h[6] | ((uint32_t)h[7] << 16);
+  hi.x = h[8] | ((uint32_t)h[9] << 16);
+  hi.y = h[10] | ((uint32_t)h[11] << 16);
+  hi.z = h[12] | ((uint32_t)h[13] << 16);
+  hi.w = h[14] | ((uint32_t)h[15] << 16);
+  *reinterpret_cast<uint4*>(tile + op_off(r, k0, K)) = lo;
+  *reinterpret_cast<uint4*>(tile + op_off(r, k0 + 8, K)) = hi;
+}
+
+struct TcParams {
+  const int32_t* B;
+  const int32_t* span;
+  float* Zt;
+  float* Mt;
+  float* Vt;
+  const float2* bias;  // (1 - beta1^t, 1 - beta2^t) per step of this call
+  int n, d, P, n_pad, d_pad;
+  int t0, T, period;
+  float lambda1, lambda2, lr, eps, beta1, beta2, omb1, omb2;
+  int nterms;   // 1: hi only, 2: hi + lo
+  int use_bb;   // 1: transposed copy of B for the gradient MMA, 0: MN-major view
+  int8_t* cand;
+  int ldc;
+  int64_t cap;
+  unsigned long long* count;
+  int32_t* flags;
+  float* dbg_phi;
+  float* dbg_grad;
+};
+
+struct Smem {  // byte offsets into dynamic shared memory
+  uint32_t bf, bb, opa, opa2, span, pz, pk, pl1, pfr, fl, fnz, slot, bar, tmem, total;
+};
+
+__host__ __device__ inline uint32_t al(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+// Operand area: [hi | lo] of bf16(z) (nterms tiles of 128 x d_pad), later
+// overwritten by S (128 x n_pad); then bf16(round z) (128 x d_pad).
+__host__ __device__ inline Smem smem_layout(int n_pad, int d_pad, int nterms, int use_bb) {
+  Smem s{};
+  uint32_t o = 0;
+  s.bf = o;   o = al(o + (uint32_t)n_pad * d_pad * 2, 1024);
+  s.bb = o;   if (use_bb) o = al(o + (uint32_t)n_pad * d_pad * 2, 1024);
+  s.opa = o;
+  uint32_t zs = (uint32_t)nterms * d_pad > (uint32_t)n_pad ? (uint32_t)nterms * d_pad : (uint32_t)n_pad;
+  s.opa2 = o + (uint32_t)kTileM * zs * 2;
+  o = al(s.opa2 + (uint32_t)kTileM * d_pad * 2, 128);
+  s.span = o; o = al(o + (uint32_t)n_pad * 4, 128);
+  s.pz = o;   o = al(o + kSplits * kTileM * 4, 128);
+  s.pk = o;   o = al(o + kSplits * kTileM * 4, 128);
+  s.pl1 = o;  o = al(o + kSplits * kTileM * 4, 128);
+  s.pfr = o;  o = al(o + kSplits * kTileM * 4, 128);
+  s.fl = o;   o = al(o + kTileM * 4, 128);
+  s.fnz = o;  o = al(o + kTileM * 4, 128);
+  s.slot = o; o = al(o + kTileM * 8, 128);
+  s.bar = o;  o = al(o + 8, 16);
+  s.tmem = o; o = al(o + 4, 16);
+  s.total = o;
+  return s;
+}
+
+// per-start flag word bits
+constexpr uint32_t kChanged = 1;    // rounding changed since the last collection
+constexpr uint32_t kUnexact = 2;    // |round z| > 256 since the last collection
+constexpr uint32_t kOutOfBox = 4;   // the current candidate fails C4
+
+__global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const Smem L = smem_layout(p.n_pad, p.d_pad, p.nterms, p.use_bb);
+  uint8_t* Bf = smem + L.bf;
+  uint8_t* Bb = smem + L.bb;
+  uint8_t* A1 = smem + L.opa;                        // hi(z)
+  uint8_t* A1lo = smem + L.opa + kTileM * p.d_pad * 2;  // lo(z)
+  uint8_t* A2 = smem + L.opa2;
+  uint8_t* Sop = smem + L.opa;
+  int32_t* s_span = reinterpret_cast<int32_t*>(smem + L.span);
+  float* s_pz = reinterpret_cast<float*>(smem + L.pz);
+  int32_t* s_pk = reinterpret_cast<int32_t*>(smem + L.pk);
+  float* s_pl1 = reinterpret_cast<float*>(smem + L.pl1);
+  float* s_pfr = reinterpret_cast<float*>(smem + L.pfr);
+  uint32_t* s_fl = reinterpret_cast<uint32_t*>(smem + L.fl);
+  int32_t* s_fnz = reinterpret_cast<int32_t*>(smem + L.fnz);
+  long long* s_slot = reinterpret_cast<long long*>(smem + L.slot);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + L.tmem);
+  const uint32_t bar = smem_u32(smem + L.bar);
+  __shared__ int s_bad;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int quarter = warp & 3, split = warp >> 2;
+  const int r = quarter * 32 + lane;                 // start row in the tile
+  const int64_t pg = (int64_t)blockIdx.x * kTileM + r;  // global start
+  const bool active = pg < p.P;
+  const int n = p.n, d = p.d, n_pad = p.n_pad, d_pad = p.d_pad;
+  const int nch = n_pad / 16, dch = d_pad / 16;
+  const int64_t P = p.P;
+
+  // ---- set-up: B in both operand layouts, span, flags ----
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int e = tid; e < n_pad * d_pad; e += kThreads) {
+    int i = e / d_pad, j = e % d_pad;
+    int v = (i < n && j < d) ? p.B[(int64_t)i * d + j] : 0;
+    if (v > 256 || v < -256) s_bad = 1;
+    uint16_t h = bf16_bits((float)v);
+    *reinterpret_cast<uint16_t*>(Bf + op_off(i, j, d_pad)) = h;  // N = n rows, K = d
+    if (p.use_bb) *reinterpret_cast<uint16_t*>(Bb + op_off(j, i, n_pad)) = h;  // N = d rows, K = n
+  }
+  for (int i = tid; i < n_pad; i += kThreads) s_span[i] = i < n ? p.span[i] : 0;
+  if (tid < kTileM) {
+    s_fl[tid] = kChanged;  // the first collection of a call always counts
+    s_fnz[tid] = kNoNz;
+  }
+  if (tid == 0) mbar_init(bar, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+  bool bail = s_bad != 0;
+  if (bail && tid == 0) atomicOr(p.flags, 8);
+
+  // ---- initial operand: bf16(z0) and the partial ||z0||_inf ----
+  float zinf_part = 0.f;
+  int kmax_part = kNoNz;
+  for (int ch = split; ch < dch && !bail; ch += kSplits) {
+    uint16_t h[16], hl[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      int j = ch * 16 + c;
+      float z = (active && j < d) ? p.Zt[(int64_t)j * P + pg] : 0.f;
+      h[c] = bf16_bits(z);
+      hl[c] = bf16_bits(z - bf16_value(h[c]));
+      float a = fabsf(z);
+      if (j < d && (a > zinf_part || kmax_part == kNoNz)) { zinf_part = a; kmax_part = j; }
+    }
+    store_row16(A1, r, ch * 16, d_pad, h);
+    if (p.nterms > 1) store_row16(A1lo, r, ch * 16, d_pad, hl);
+  }
+  s_pz[split * kTileM + r] = zinf_part;
+  s_pk[split * kTileM + r] = kmax_part;
+  fence_async_smem();
+  __syncthreads();
+
+  const bool dbg_on = (p.dbg_phi != nullptr || p.dbg_grad != nullptr);
+  uint32_t phase = 0;
+  const uint32_t idesc_fwd = idesc_bf16(kTileM, n_pad);
+  // gradient MMA: B operand K-major from the transposed copy, or MN-major
+  // (bit 16) straight from the forward tile
+  const uint32_t idesc_bwd = idesc_bf16(kTileM, d_pad) | (p.use_bb ? 0u : (1u << 16));
+  const uint32_t sbo_d = (uint32_t)(d_pad / 8) * 128, sbo_n = (uint32_t)(n_pad / 8) * 128;
+
+  // combine the partials of ||z||_inf: max, ties to the lower index (first maximiser)
+  auto combine_zinf = [&](float& zinf, int& kmax) {
+    zinf = 0.f;
+    kmax = kNoNz;
+    for (int s = 0; s < kSplits; ++s) {
+      float z = s_pz[s * kTileM + r];
+      int k = s_pk[s * kTileM + r];
+      if (k == kNoNz) continue;
+      if (kmax == kNoNz || z > zinf || (z == zinf && k < kmax)) { zinf = z; kmax = k; }
+    }
+  };
+  float zinf;
+  int kmax;
+  combine_zinf(zinf, kmax);
+
+  // tests the candidate held in D2 (bound test, first nonzero entry) ...
+  auto test_candidate = [&]() {
+    int first = kNoNz;
+    bool out = false;
+    for (int ch = split; ch < nch; ch += kSplits) {
+      uint32_t v[16];
+      tmem_ld16(tmem + lane_off + kColD2 + ch * 16, v);
+      tc_wait_ld();
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        int i = ch * 16 + c;
+        int g = __float2int_rn(__uint_as_float(v[c]));
+        if (i < n) {
+          if (g > s_span[i] || -g > s_span[i]) out = true;
+          if (g != 0 && (i << 1) < first) first = (i << 1) | (g < 0 ? 1 : 0);
+        }
+      }
+    }
+    if (out) atomicOr(&s_fl[r], kOutOfBox);
+    if (first != kNoNz) atomicMin(&s_fnz[r], first);
+  };
+  // ... and appends it in canonical sign (needs a barrier between the two)
+  auto decide_slot = [&]() {
+    if (split != 0) return;
+    long long slot = -1;
+    uint32_t f = s_fl[r];
+    int fnz = s_fnz[r];
+    if (active && (f & kChanged) && !(f & kOutOfBox) && fnz != kNoNz) {
+      if (f & kUnexact) {
+        atomicOr(p.flags, 2);
+      } else {
+        unsigned long long at = atomicAdd(p.count, 1ull);
+        if ((int64_t)at < p.cap) slot = (long long)at;
+        else atomicOr(p.flags, 1);
+      }
+    }
+    s_slot[r] = slot;
+  };
+  // every lane of the warp executes the (warp-collective) TMEM loads; only
+  // lanes whose start has a slot store
+  auto write_candidate = [&]() {
+    long long slot = s_slot[r];
+    int sgn = (s_fnz[r] & 1) ? -1 : 1;
+    int8_t* row = slot >= 0 ? p.cand + slot * p.ldc : nullptr;
+    for (int ch = split; ch < nch; ch += kSplits) {
+      uint32_t v[16];
+      tmem_ld16(tmem + lane_off + kColD2 + ch * 16, v);
+      tc_wait_ld();
+      uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        int g = sgn * __float2int_rn(__uint_as_float(v[c]));
+        w[c >> 2] |= ((uint32_t)(g & 0xff)) << ((c & 3) * 8);
+      }
+      if (row) *reinterpret_cast<uint4*>(row + ch * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    if (row && split == 0)
+      for (int off = n_pad; off < p.ldc; off += 16) *reinterpret_cast<uint4*>(row + off) = make_uint4(0, 0, 0, 0);
+  };
+  auto reset_collection = [&]() {
+    if (split == 0) {
+      s_fl[r] = 0;
+      s_fnz[r] = kNoNz;
+    }
+  };
+  auto issue_d2 = [&]() {
+    for (int kk = 0; kk < dch; ++kk) {
+      uint64_t a = make_desc(smem_u32(A2) + kk * 256, 128, sbo_d);
+      uint64_t b = make_desc(smem_u32(Bf) + kk * 256, 128, sbo_d);
+      mma_bf16(tmem + kColD2, a, b, idesc_fwd, kk > 0);
+    }
+  };
+  bool timed_out = false;
+  auto wait_mma = [&]() -> bool {
+    bool ok = mbar_wait_bounded(bar, phase);
+    phase ^= 1;
+    bool any_bad = __syncthreads_or(!ok) != 0;
+    if (any_bad && tid == 0) atomicOr(p.flags, 16);
+    if (any_bad) timed_out = true;
+    tc_fence_after();
+    return !any_bad;
+  };
+
+  for (int s = 0; s < p.T && !bail; ++s) {
+    const int t = p.t0 + s + 1;              // global step number
+    const bool collect_prev = s >= 1 && ((t - 1) % p.period == 0);
+    const bool dbg_step = dbg_on && s == 0;
+    // (1) forward MMAs
+    if (tid == 0) {
+      tc_fence_after();
+      for (int term = 0; term < p.nterms; ++term) {
+        uint32_t abase = smem_u32(term == 0 ? A1 : A1lo);
+        for (int kk = 0; kk < dch; ++kk) {
+          uint64_t a = make_desc(abase + kk * 256, 128, sbo_d);
+          uint64_t b = make_desc(smem_u32(Bf) + kk * 256, 128, sbo_d);
+          mma_bf16(tmem, a, b, idesc_fwd, (term > 0 || kk > 0) ? 1u : 0u);
+        }
+      }
+      if (collect_prev) issue_d2();
+      mma_commit(bar);
+    }
+    if (!wait_mma()) { bail = true; break; }
+    // (2) S = sign(D1) into shared memory; test the previous step's candidate
+    float l1 = 0.f;
+    for (int ch = split; ch < nch; ch += kSplits) {
+      uint32_t v[16];
+      tmem_ld16(tmem + lane_off + ch * 16, v);
+      tc_wait_ld();
+      uint16_t h[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        float y = __uint_as_float(v[c]);
+        h[c] = y > 0.f ? (uint16_t)0x3F80 : (y < 0.f ? (uint16_t)0xBF80 : (uint16_t)0);
+        l1 += fabsf(y);
+      }
+      store_row16(Sop, r, ch * 16, n_pad, h);
+    }
+    if (dbg_step) s_pl1[split * kTileM + r] = l1;
+    if (collect_prev) test_candidate();
+    tc_wait_ld();
+    tc_fence_before();
+    fence_async_smem();
+    __syncthreads();
+    // (3) gradient MMA, overlapped with appending the previous candidate
+    if (tid == 0) {
+      tc_fence_after();
+      for (int kk = 0; kk < nch; ++kk) {
+        uint64_t a = make_desc(smem_u32(Sop) + kk * 256, 128, sbo_n);
+        // K step kk covers rows 16kk..16kk+15 of B: two 8-row core-matrix groups
+        uint64_t b = p.use_bb ? make_desc(smem_u32(Bb) + kk * 256, 128, sbo_n)
+                              : make_desc(smem_u32(Bf) + kk * 2 * sbo_d, kMnLbo ? sbo_d : 128, kMnLbo ? 128 : sbo_d);
+        mma_bf16(tmem, a, b, idesc_bwd, kk > 0);
+      }
+      mma_commit(bar);
+    }
+    if (collect_prev) {
+      decide_slot();
+      __syncthreads();
+      write_candidate();
+      __syncthreads();
+      reset_collection();
+    }
+    if (!wait_mma()) { bail = true; break; }
+    // (4) Adam on the FP32 master state; next operands
+    const float2 bc = p.bias[s];
+    float inv_term = 0.f;
+    if (zinf < 1.f && zinf > 0.f) inv_term = -p.lambda2 / (zinf * zinf);  // times sign(z_kmax)
+    float nzinf = 0.f, frac = 0.f;
+    int nkmax = kNoNz;
+    bool changed = false, unexact = false;
+    for (int ch = split; ch < dch; ch += kSplits) {
+      uint32_t v[16];
+      tmem_ld16(tmem + lane_off + ch * 16, v);
+      tc_wait_ld();
+      uint16_t h1[16], hl[16], h2[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        int j = ch * 16 + c;
+        float zn = 0.f, rn = 0.f;
+        if (active && j < d) {
+          int64_t at = (int64_t)j * P + pg;
+          float z = p.Zt[at];
+          float grad = __uint_as_float(v[c]) + p.lambda1 * (ceilf(z) + floorf(z) - 2.f * z);
+          if (j == kmax) grad += inv_term * (float)mape_sign_f(z);
+          if (dbg_step) {
+            frac += (z - floorf(z)) * (ceilf(z) - z);
+            if (p.dbg_grad) p.dbg_grad[pg * d + j] = grad;
+          }
+          float m = p.beta1 * p.Mt[at] + p.omb1 * grad;
+          float vv = p.beta2 * p.Vt[at] + p.omb2 * grad * grad;
+          zn = z - p.lr * (m / bc.x) / (sqrtf(vv / bc.y) + p.eps);
+          p.Mt[at] = m;
+          p.Vt[at] = vv;
+          p.Zt[at] = zn;
+          rn = rintf(zn);
+          changed |= rn != rintf(z);
+          unexact |= fabsf(rn) > 256.f;
+          float a = fabsf(zn);
+          if (nkmax == kNoNz || a > nzinf) { nzinf = a; nkmax = j; }
+        }
+        h1[c] = bf16_bits(zn);
+        hl[c] = bf16_bits(zn - bf16_value(h1[c]));
+        h2[c] = bf16_bits(rn);
+      }
+      store_row16(A1, r, ch * 16, d_pad, h1);
+      if (p.nterms > 1) store_row16(A1lo, r, ch * 16, d_pad, hl);
+      store_row16(A2, r, ch * 16, d_pad, h2);
+    }
+    s_pz[split * kTileM + r] = nzinf;
+    s_pk[split * kTileM + r] = nkmax;
+    if (dbg_step) s_pfr[split * kTileM + r] = frac;
+    uint32_t fbits = (changed ? kChanged : 0u) | (unexact ? kUnexact : 0u);
+    if (fbits) atomicOr(&s_fl[r], fbits);
+    tc_wait_ld();
+    tc_fence_before();
+    fence_async_smem();
+    __syncthreads();
+    if (dbg_step && split == 0 && active && p.dbg_phi) {
+      float L1 = 0.f, FR = 0.f;
+      for (int q = 0; q < kSplits; ++q) { L1 += s_pl1[q * kTileM + r]; FR += s_pfr[q * kTileM + r]; }
+      float inv = zinf > 0.f ? fmaxf(1.f / zinf - 1.f, 0.f) : INFINITY;
+      p.dbg_phi[pg] = L1 + p.lambda1 * FR + p.lambda2 * inv;
+    }
+    combine_zinf(zinf, kmax);
+  }
+
+  // the candidate of the last step
+  if (!bail && p.T > 0 && ((p.t0 + p.T) % p.period == 0)) {
+    if (tid == 0) {
+      tc_fence_after();
+      issue_d2();
+      mma_commit(bar);
+    }
+    if (wait_mma()) {
+      test_candidate();
+      tc_wait_ld();
+      __syncthreads();
+      decide_slot();
+      __syncthreads();
+      write_candidate();
+    }
+  }
+  if (timed_out) mbar_wait_bounded(bar, phase ^ 1);  // let an MMA still in flight drain
+  tc_wait_ld();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  }
+}
+
+__global__ void transpose_tc_kernel(const float* __restrict__ in, float* __restrict__ out, int rows, int cols) {
+  __shared__ float tile[32][33];
+  int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int rr = r0 + k, c = c0 + threadIdx.x;
+    if (rr < rows && c < cols) tile[k][threadIdx.x] = in[(int64_t)rr * cols + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int c = c0 + k, rr = r0 + threadIdx.x;
+    if (rr < rows && c < cols) out[(int64_t)c * rows + rr] = tile[threadIdx.x][k];
+  }
+}
+
+int pad16(int x) { return (x + 15) / 16 * 16; }
+
+}  // namespace
+
+namespace mape_detail {
+
+constexpr uint32_t kSmemLimit = 232448 - 2048;  // opt-in maximum less static shared memory
+
+#ifndef MAPE_TC_FORCE_MN
+#define MAPE_TC_FORCE_MN 0
+#endif
+
+// The transposed copy of B is used when it fits, else the MN-major view.
+int tc_use_bb(int n_pad, int d_pad, int nterms) {
+  if (MAPE_TC_FORCE_MN) return 0;
+  return smem_layout(n_pad, d_pad, nterms, 1).total <= kSmemLimit ? 1 : 0;
+}
+
+bool tc_fits(int32_t n, int32_t d, int nterms) {
+  int n_pad = pad16(n), d_pad = pad16(d);
+  if (n_pad > 256 || d_pad > 256) return false;
+  return smem_layout(n_pad, d_pad, nterms, tc_use_bb(n_pad, d_pad, nterms)).total <= kSmemLimit;
+}
+
+bool extract_tc_supported(int32_t n, int32_t d, int32_t precision) {
+  return tc_fits(n, d, precision == MAPE_PREC_BF16X1 ? 1 : 2);
+}
+
+size_t extract_tc_workspace(int32_t n, int32_t d, int32_t P, int32_t precision) {
+  if (!extract_tc_supported(n, d, precision)) return 0;
+  Sizer s;
+  for (int k = 0; k < 3; ++k) s.take<float>((size_t)d * P);  // Zt, Mt, Vt (carved separately)
+  s.take<float2>((size_t)1 << 20);  // bias-correction table, up to 2^20 steps per call
+  return s.bytes();
+}
+
+int extract_tc(const mape_extract_args* a, cudaStream_t st) {
+  const int n = a->n, d = a->d, P = a->P;
+  if (a->T > (1 << 20)) return MAPE_ERR_SHAPE;
+  Carver cv(a->workspace, a->workspace_bytes);
+  float* Zt = cv.take<float>((size_t)d * P);
+  float* Mt = cv.take<float>((size_t)d * P);
+  float* Vt = cv.take<float>((size_t)d * P);
+  float2* bias = cv.take<float2>((size_t)1 << 20);
+  if (!cv.ok) return MAPE_ERR_CAPACITY;
+  std::vector<float2> bc;
+  adam_bias_table(a, bc);
+  MAPE_CUDA_TRY(cudaMemcpyAsync(bias, bc.data(), sizeof(float2) * bc.size(), cudaMemcpyHostToDevice, st));
+  dim3 tb(32, 8);
+  dim3 gin((unsigned)ceil_div(d, 32), (unsigned)ceil_div(P, 32));
+  transpose_tc_kernel<<<gin, tb, 0, st>>>(a->Z, Zt, P, d);
+  transpose_tc_kernel<<<gin, tb, 0, st>>>(a->M, Mt, P, d);
+  transpose_tc_kernel<<<gin, tb, 0, st>>>(a->V, Vt, P, d);
+  TcParams p{};
+  p.B = a->B; p.span = a->span; p.Zt = Zt; p.Mt = Mt; p.Vt = Vt; p.bias = bias;
+  p.n = n; p.d = d; p.P = P; p.n_pad = pad16(n); p.d_pad = pad16(d);
+  p.t0 = a->t0; p.T = a->T; p.period = a->period;
+  p.lambda1 = a->lambda1; p.lambda2 = a->lambda2; p.lr = a->lr; p.eps = a->eps;
+  p.beta1 = (float)a->beta1; p.beta2 = (float)a->beta2;
+  p.omb1 = (float)(1.0 - a->beta1); p.omb2 = (float)(1.0 - a->beta2);
+  p.cand = a->cand; p.ldc = a->ldc; p.cap = a->cand_cap; p.count = a->cand_count; p.flags = a->flags;
+  p.dbg_phi = a->dbg_phi; p.dbg_grad = a->dbg_grad;
+  p.nterms = a->precision == MAPE_PREC_BF16X1 ? 1 : 2;
+  p.use_bb = tc_use_bb(p.n_pad, p.d_pad, p.nterms);
+  // at least 116 KB of shared memory keeps one CTA per SM, so the 512-column
+  // TMEM allocation never waits for another CTA
+  uint32_t smem = smem_layout(p.n_pad, p.d_pad, p.nterms, p.use_bb).total;
+  if (smem < 116 * 1024) smem = 116 * 1024;
+  MAPE_CUDA_TRY(cudaFuncSetAttribute(extract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  unsigned grid = (unsigned)ceil_div(P, kTileM);
+  extract_tc_kernel<<<grid, kThreads, smem, st>>>(p);
+  MAPE_LAUNCH_CHECK();
+  dim3 gout((unsigned)ceil_div(P, 32), (unsigned)ceil_div(d, 32));
+  transpose_tc_kernel<<<gout, tb, 0, st>>>(Zt, a->Z, d, P);
+  transpose_tc_kernel<<<gout, tb, 0, st>>>(Mt, a->M, d, P);
+  transpose_tc_kernel<<<gout, tb, 0, st>>>(Vt, a->V, d, P);
+  MAPE_LAUNCH_CHECK();
+  return MAPE_OK;
+}
+
+}  // namespace mape_detail

@@ -1,0 +1,569 @@
+// The instance handle: create_instance / extract_directions / augment /
+// poll / wait / get_* / destroy.  Host arrays are copied in the calling
+// thread; device buffers are allocated there too (so an allocator hook runs on
+// the caller's thread), and the stage pipeline then runs on one worker thread
+// per handle, which only launches kernels and synchronises its stream.
+//
+// Extraction memory is bounded: candidates go to a buffer of `cap` rows laid
+// out as [distinct rows so far | rows of the current chunk]; each chunk runs
+// at most (cap - distinct) / P Adam steps, which is at most one row per start
+// and step, so the buffer cannot overflow; after each chunk mape_dedup merges
+// the buffer into the other buffer of the pair and the two swap.
+#include "common.cuh"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+namespace {
+
+std::mutex g_alloc_mu;
+mape_alloc_fn g_alloc = nullptr;
+mape_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+
+__global__ void basis_check_kernel(const int32_t* __restrict__ A, const int32_t* __restrict__ B, int m, int n,
+                                   int d, int32_t* __restrict__ bad) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (j >= d) return;
+  long long acc = 0;
+  for (int i = 0; i < n; ++i) acc += (long long)A[(int64_t)r * n + i] * B[(int64_t)i * d + j];
+  if (acc != 0) atomicOr(bad, 1);
+}
+
+__global__ void feasible_check_kernel(const int32_t* __restrict__ A, const int64_t* __restrict__ b,
+                                      const int32_t* __restrict__ X, int m, int n, int S, int32_t* __restrict__ bad) {
+  int s = blockIdx.x;
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    long long acc = 0;
+    for (int i = 0; i < n; ++i) acc += (long long)A[(int64_t)r * n + i] * X[(int64_t)s * n + i];
+    if (acc != b[r]) atomicOr(bad, 1);
+  }
+}
+
+__global__ void i8_to_i32_kernel(const int8_t* __restrict__ G, int64_t K, int n, int ldg, int32_t* __restrict__ out) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= K * n) return;
+  int64_t k = t / n;
+  int i = (int)(t % n);
+  out[t] = G[k * ldg + i];
+}
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct mape_instance {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int n = 0, m = 0, d = 0, ldg = 0;
+  mape_config cfg{};
+  bool has_w = false;
+  int nnz = 0;
+
+  // device buffers owned by the handle, with their sizes (for the free hook)
+  std::vector<std::pair<void*, size_t>> owned;
+  int32_t *dA = nullptr, *dB = nullptr, *dl = nullptr, *du = nullptr, *dspan = nullptr;
+  int64_t* db = nullptr;
+  int32_t *dc = nullptr, *dw = nullptr, *dqr = nullptr, *dqc = nullptr, *dqv = nullptr;
+
+  // extraction job buffers (replaced per extract call)
+  std::vector<std::pair<void*, size_t>> job_bufs;
+  int P = 0;
+  float *dZ = nullptr, *dM = nullptr, *dV = nullptr, *dG0 = nullptr;
+  int8_t *dBuf0 = nullptr, *dBuf1 = nullptr, *dD = nullptr;
+  int64_t cap = 0;
+  uint8_t *dOk = nullptr, *dKeep = nullptr;
+  int64_t *da = nullptr, *dq4 = nullptr;
+  void* dWork = nullptr;
+  size_t work_bytes = 0;
+  unsigned long long* dCount = nullptr;
+  int32_t* dFlags = nullptr;
+  int8_t* dirs = nullptr;  // current direction set (points into dD)
+  int64_t K = 0;
+
+  // augmentation buffers
+  std::vector<std::pair<void*, size_t>> aug_bufs;
+  int S = 0;
+  int32_t* dX = nullptr;
+  int64_t* dF = nullptr;
+  void* dAugWork = nullptr;
+  size_t aug_work_bytes = 0;
+
+  std::mutex mu;
+  std::condition_variable cv;
+  mape_status st{};
+  bool busy = false;
+  std::thread worker;
+  std::atomic<bool> cancel{false};
+  std::vector<int32_t> best_x;
+  int64_t best_f = 0;
+
+  void* alloc(size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    {
+      std::lock_guard<std::mutex> lk(g_alloc_mu);
+      if (g_alloc) {
+        p = g_alloc(bytes, stream, g_alloc_ctx);
+        return p;
+      }
+    }
+    if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) return nullptr;
+    return p;
+  }
+  void release(void* p, size_t bytes) {
+    if (!p) return;
+    {
+      std::lock_guard<std::mutex> lk(g_alloc_mu);
+      if (g_free) {
+        g_free(p, bytes, stream, g_alloc_ctx);
+        return;
+      }
+    }
+    cudaFreeAsync(p, stream);
+  }
+  template <typename T>
+  T* take(std::vector<std::pair<void*, size_t>>& list, size_t count) {
+    size_t bytes = std::max<size_t>(16, count * sizeof(T));
+    void* p = alloc(bytes);
+    if (p) list.push_back({p, bytes});
+    return static_cast<T*>(p);
+  }
+  void release_all(std::vector<std::pair<void*, size_t>>& list) {
+    for (auto& pr : list) release(pr.first, pr.second);
+    list.clear();
+  }
+  void join() {
+    if (worker.joinable()) worker.join();
+  }
+  void set_phase(int ph) {
+    std::lock_guard<std::mutex> lk(mu);
+    st.phase = ph;
+  }
+  void finish(int err) {
+    std::lock_guard<std::mutex> lk(mu);
+    st.error = err;
+    st.phase = err == MAPE_OK ? MAPE_PHASE_DONE : MAPE_PHASE_ERROR;
+    busy = false;
+    cv.notify_all();
+  }
+
+  int run_extract();
+  int run_augment(int64_t max_iters);
+};
+
+#define H_TRY(expr)                 \
+  do {                              \
+    int _rc = (expr);               \
+    if (_rc != MAPE_OK) return _rc; \
+  } while (0)
+
+int mape_instance::run_extract() {
+  using namespace mape_detail;
+  cudaStream_t s = stream;
+  double t_start = now_ms();
+  set_phase(MAPE_PHASE_EXTRACTING);
+  if (dG0) H_TRY(mape_project_starts(dB, n, d, dG0, P, dZ, dWork, work_bytes, s));
+  MAPE_CUDA_TRY(cudaMemsetAsync(dM, 0, sizeof(float) * (size_t)P * d, s));
+  MAPE_CUDA_TRY(cudaMemsetAsync(dV, 0, sizeof(float) * (size_t)P * d, s));
+  int64_t U = 0, total_cand = 0;
+  int t_done = 0;
+  int8_t* cur = dBuf0;
+  int8_t* other = dBuf1;
+  while (t_done < cfg.T) {
+    if (cancel.load()) return MAPE_ERR_CANCELLED;
+    int64_t room = cap - U;
+    int64_t steps = room / P;
+    if (steps < 1) return MAPE_ERR_CAPACITY;
+    int chunk = (int)std::min<int64_t>(steps, cfg.T - t_done);
+    MAPE_CUDA_TRY(cudaMemsetAsync(dCount, 0, sizeof(unsigned long long), s));
+    MAPE_CUDA_TRY(cudaMemsetAsync(dFlags, 0, sizeof(int32_t), s));
+    mape_extract_args a{};
+    a.n = n; a.d = d; a.P = P; a.B = dB; a.span = dspan; a.Z = dZ; a.M = dM; a.V = dV;
+    a.t0 = t_done; a.T = chunk; a.period = cfg.period; a.precision = cfg.precision;
+    a.lambda1 = cfg.lambda1; a.lambda2 = cfg.lambda2; a.lr = cfg.lr; a.beta1 = cfg.beta1;
+    a.beta2 = cfg.beta2; a.eps = cfg.eps;
+    a.cand = cur + U * ldg; a.ldc = ldg; a.cand_cap = cap - U; a.cand_count = dCount; a.flags = dFlags;
+    a.workspace = dWork; a.workspace_bytes = work_bytes;
+    H_TRY(mape_extract(&a, s));
+    unsigned long long cnt = 0;
+    int32_t flags = 0;
+    MAPE_CUDA_TRY(cudaMemcpyAsync(&cnt, dCount, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    MAPE_CUDA_TRY(cudaMemcpyAsync(&flags, dFlags, sizeof(flags), cudaMemcpyDeviceToHost, s));
+    MAPE_CUDA_TRY(cudaStreamSynchronize(s));
+    if (flags & 1) return MAPE_ERR_CAPACITY;
+    total_cand += (int64_t)cnt;
+    int64_t K_new = 0;
+    H_TRY(mape_dedup(cur, U + (int64_t)cnt, n, ldg, other, cap, &K_new, dWork, work_bytes, s));
+    U = K_new;
+    std::swap(cur, other);
+    t_done += chunk;
+    std::lock_guard<std::mutex> lk(mu);
+    st.candidates = total_cand;
+    st.unique = U;
+  }
+  double t_ext = now_ms();
+  set_phase(MAPE_PHASE_FILTERING);
+  int64_t fails = 0;
+  H_TRY(mape_kernel_test(dA, m, n, cur, U, ldg, dOk, &fails, dWork, work_bytes, s));
+  int64_t Kk = 0;
+  H_TRY(mape_minimal_filter(cur, U, n, ldg, dOk, dKeep, dD, &Kk, dWork, work_bytes, s));
+  H_TRY(mape_direction_coeffs(dqr, dqc, dqv, nnz, has_w ? dw : nullptr, n, dD, Kk, ldg, da, dq4, s));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(s));
+  double t_fil = now_ms();
+  dirs = dD;
+  K = Kk;
+  std::lock_guard<std::mutex> lk(mu);
+  st.kernel_failures = fails;
+  st.directions = Kk;
+  st.extract_ms = t_ext - t_start;
+  st.filter_ms = t_fil - t_ext;
+  return fails ? MAPE_ERR_KERNEL_TEST : MAPE_OK;
+}
+
+int mape_instance::run_augment(int64_t max_iters) {
+  cudaStream_t s = stream;
+  set_phase(MAPE_PHASE_AUGMENTING);
+  double t0 = now_ms();
+  mape_augment_args a{};
+  a.n = n; a.S = S; a.K = K; a.G = dirs; a.ldg = ldg; a.a = da; a.q4 = dq4;
+  a.q_row = dqr; a.q_col = dqc; a.q_val = dqv; a.nnz = nnz; a.c = dc; a.w = has_w ? dw : nullptr;
+  a.l = dl; a.u = du; a.X = dX; a.fval = dF;
+  a.workspace = dAugWork; a.workspace_bytes = aug_work_bytes;
+  // the first iteration alone: time to the first improving direction
+  a.max_iters = std::min<int64_t>(1, max_iters);
+  int64_t it1 = 0, it2 = 0;
+  H_TRY(mape_augment_run(&a, &it1, s));
+  double t1 = now_ms();
+  if (max_iters > 1 && !cancel.load()) {
+    a.max_iters = max_iters - 1;
+    H_TRY(mape_augment_run(&a, &it2, s));
+  }
+  std::vector<int64_t> f(S);
+  MAPE_CUDA_TRY(cudaMemcpyAsync(f.data(), dF, sizeof(int64_t) * S, cudaMemcpyDeviceToHost, s));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(s));
+  int bi = (int)(std::min_element(f.begin(), f.end()) - f.begin());
+  best_x.assign(n, 0);
+  MAPE_CUDA_TRY(cudaMemcpyAsync(best_x.data(), dX + (int64_t)bi * n, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(s));
+  best_f = f[bi];
+  double t2 = now_ms();
+  std::lock_guard<std::mutex> lk(mu);
+  st.aug_iters = it1 + it2;
+  st.best_f = best_f;
+  st.best_start = bi;
+  st.augment_ms = t2 - t0;
+  st.first_improve_ms = t1 - t0;
+  return MAPE_OK;
+}
+
+namespace {
+
+int upload(mape_instance* h, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return MAPE_OK;
+  MAPE_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->stream));
+  return MAPE_OK;
+}
+
+int set_objective(mape_instance* h, const mape_problem* f) {
+  const int n = h->n;
+  if (!f->Q || !f->c) return MAPE_ERR_INVALID_ARG;
+  std::vector<int32_t> qr, qc, qv;
+  for (int i = 0; i < n; ++i)
+    for (int j = i; j < n; ++j) {
+      int32_t v = f->Q[(int64_t)i * n + j];
+      if (v != f->Q[(int64_t)j * n + i]) return MAPE_ERR_INVALID_ARG;  // Q must be symmetric
+      if (v != 0) { qr.push_back(i); qc.push_back(j); qv.push_back(v); }
+    }
+  if (f->w)
+    for (int i = 0; i < n; ++i)
+      if (f->w[i] < 0) return MAPE_ERR_INVALID_ARG;
+  h->nnz = (int)qv.size();
+  h->dqr = h->take<int32_t>(h->owned, qr.size());
+  h->dqc = h->take<int32_t>(h->owned, qc.size());
+  h->dqv = h->take<int32_t>(h->owned, qv.size());
+  h->dc = h->take<int32_t>(h->owned, n);
+  h->dw = h->take<int32_t>(h->owned, n);
+  if (!h->dqr || !h->dqc || !h->dqv || !h->dc || !h->dw) return MAPE_ERR_OOM;
+  H_TRY(upload(h, h->dqr, qr.data(), qr.size() * 4));
+  H_TRY(upload(h, h->dqc, qc.data(), qc.size() * 4));
+  H_TRY(upload(h, h->dqv, qv.data(), qv.size() * 4));
+  H_TRY(upload(h, h->dc, f->c, (size_t)n * 4));
+  h->has_w = f->w != nullptr;
+  if (f->w) H_TRY(upload(h, h->dw, f->w, (size_t)n * 4));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return MAPE_OK;
+}
+
+bool idle(mape_instance* h) {
+  std::lock_guard<std::mutex> lk(h->mu);
+  return !h->busy;
+}
+
+}  // namespace
+
+extern "C" int mape_set_allocator(mape_alloc_fn a, mape_free_fn f, void* ctx) {
+  if ((a == nullptr) != (f == nullptr)) return MAPE_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc = a;
+  g_free = f;
+  g_alloc_ctx = ctx;
+  return MAPE_OK;
+}
+
+extern "C" int mape_create_instance(const int32_t* A, const int64_t* b, const int32_t* l, const int32_t* u,
+                                    const mape_problem* f, const int32_t* B, const mape_config* cfg,
+                                    void* stream, mape_handle* out) {
+  if (!out) return MAPE_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!A || !b || !l || !u || !f || !B || !cfg) return MAPE_ERR_INVALID_ARG;
+  const int n = f->n, m = f->m;
+  if (n <= 0 || m <= 0 || m >= n) return MAPE_ERR_SHAPE;
+  if (n > 4096) return MAPE_ERR_SHAPE;
+  if (cfg->T < 0 || cfg->period <= 0 || cfg->lr <= 0.f || cfg->max_aug_iters < 0) return MAPE_ERR_INVALID_ARG;
+  if (cfg->precision != MAPE_PREC_FP32 && cfg->precision != MAPE_PREC_BF16 && cfg->precision != MAPE_PREC_BF16X1)
+    return MAPE_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (u[i] < l[i] || (int64_t)u[i] - l[i] > 127) return MAPE_ERR_BOUNDS;
+  auto* h = new mape_instance();
+  h->n = n;
+  h->m = m;
+  h->d = n - m;
+  h->ldg = (int)mape_detail::align_up((size_t)n, 16);
+  h->cfg = *cfg;
+  if (cudaGetDevice(&h->dev) != cudaSuccess) { delete h; return MAPE_ERR_CUDA; }
+  if (stream) {
+    h->stream = mape_detail::as_stream(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) { delete h; return MAPE_ERR_CUDA; }
+    h->own_stream = true;
+  }
+  auto fail = [&](int rc) {
+    mape_destroy(h);
+    return rc;
+  };
+  const int d = h->d;
+  h->dA = h->take<int32_t>(h->owned, (size_t)m * n);
+  h->dB = h->take<int32_t>(h->owned, (size_t)n * d);
+  h->db = h->take<int64_t>(h->owned, (size_t)m);
+  h->dl = h->take<int32_t>(h->owned, n);
+  h->du = h->take<int32_t>(h->owned, n);
+  h->dspan = h->take<int32_t>(h->owned, n);
+  int32_t* dbad = h->take<int32_t>(h->owned, 1);
+  if (!h->dA || !h->dB || !h->db || !h->dl || !h->du || !h->dspan || !dbad) return fail(MAPE_ERR_OOM);
+  std::vector<int32_t> span(n);
+  for (int i = 0; i < n; ++i) span[i] = u[i] - l[i];
+  int rc;
+  if ((rc = upload(h, h->dA, A, (size_t)m * n * 4)) || (rc = upload(h, h->dB, B, (size_t)n * d * 4)) ||
+      (rc = upload(h, h->db, b, (size_t)m * 8)) || (rc = upload(h, h->dl, l, (size_t)n * 4)) ||
+      (rc = upload(h, h->du, u, (size_t)n * 4)) || (rc = upload(h, h->dspan, span.data(), (size_t)n * 4)))
+    return fail(rc);
+  if (cudaMemsetAsync(dbad, 0, 4, h->stream) != cudaSuccess) return fail(MAPE_ERR_CUDA);
+  basis_check_kernel<<<dim3((unsigned)mape_detail::ceil_div(d, 128), (unsigned)m), 128, 0, h->stream>>>(
+      h->dA, h->dB, m, n, d, dbad);
+  int32_t bad = 0;
+  if (cudaMemcpyAsync(&bad, dbad, 4, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return fail(MAPE_ERR_CUDA);
+  if (bad) return fail(MAPE_ERR_NOT_KERNEL_BASIS);
+  if ((rc = set_objective(h, f))) return fail(rc);
+  h->st.phase = MAPE_PHASE_IDLE;
+  *out = h;
+  return MAPE_OK;
+}
+
+extern "C" int mape_extract_directions(mape_handle h, int32_t P, const float* Z0, const float* G0) {
+  using namespace mape_detail;
+  if (!h || P <= 0 || (Z0 == nullptr) == (G0 == nullptr)) return MAPE_ERR_INVALID_ARG;
+  if (!idle(h)) return MAPE_ERR_STATE;
+  h->join();
+  if (h->cfg.precision != MAPE_PREC_FP32 && mape_extract_workspace_bytes(h->n, h->d, P, h->cfg.precision) == 0)
+    return MAPE_ERR_SHAPE;
+  h->release_all(h->job_bufs);
+  h->K = 0;
+  h->dirs = nullptr;
+  const int n = h->n, d = h->d, ldg = h->ldg;
+  const int64_t T = h->cfg.T;
+  int64_t cap = h->cfg.cand_capacity > 0 ? h->cfg.cand_capacity : std::min<int64_t>((int64_t)P * T + P, (int64_t)1 << 22);
+  cap = std::max<int64_t>(cap, (int64_t)P + 1);
+  h->cap = cap;
+  h->P = P;
+  h->dZ = h->take<float>(h->job_bufs, (size_t)P * d);
+  h->dM = h->take<float>(h->job_bufs, (size_t)P * d);
+  h->dV = h->take<float>(h->job_bufs, (size_t)P * d);
+  h->dG0 = G0 ? h->take<float>(h->job_bufs, (size_t)P * n) : nullptr;
+  h->dBuf0 = h->take<int8_t>(h->job_bufs, (size_t)cap * ldg);
+  h->dBuf1 = h->take<int8_t>(h->job_bufs, (size_t)cap * ldg);
+  h->dD = h->take<int8_t>(h->job_bufs, (size_t)cap * ldg);
+  h->dOk = h->take<uint8_t>(h->job_bufs, (size_t)cap);
+  h->dKeep = h->take<uint8_t>(h->job_bufs, (size_t)cap);
+  h->da = h->take<int64_t>(h->job_bufs, (size_t)cap);
+  h->dq4 = h->take<int64_t>(h->job_bufs, (size_t)cap);
+  h->dCount = h->take<unsigned long long>(h->job_bufs, 1);
+  h->dFlags = h->take<int32_t>(h->job_bufs, 1);
+  size_t w = 0;
+  w = std::max(w, mape_project_workspace_bytes(n, d));
+  w = std::max(w, mape_extract_workspace_bytes(n, d, P, h->cfg.precision));
+  w = std::max(w, mape_dedup_workspace_bytes(cap, ldg));
+  w = std::max(w, mape_kernel_test_workspace_bytes());
+  w = std::max(w, mape_minimal_workspace_bytes(cap, n));
+  h->work_bytes = w;
+  h->dWork = h->take<char>(h->job_bufs, w);
+  if (!h->dZ || !h->dM || !h->dV || (G0 && !h->dG0) || !h->dBuf0 || !h->dBuf1 || !h->dD || !h->dOk ||
+      !h->dKeep || !h->da || !h->dq4 || !h->dCount || !h->dFlags || !h->dWork)
+    return MAPE_ERR_OOM;
+  int rc = G0 ? upload(h, h->dG0, G0, sizeof(float) * (size_t)P * n) : upload(h, h->dZ, Z0, sizeof(float) * (size_t)P * d);
+  if (rc) return rc;
+  MAPE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    h->busy = true;
+    h->st = mape_status{};
+    h->st.phase = MAPE_PHASE_EXTRACTING;
+  }
+  h->cancel.store(false);
+  h->worker = std::thread([h]() {
+    cudaSetDevice(h->dev);
+    int r = h->run_extract();
+    h->finish(r);
+  });
+  return MAPE_OK;
+}
+
+extern "C" int mape_augment(mape_handle h, const int32_t* X0, int32_t S, const mape_problem* f) {
+  using namespace mape_detail;
+  if (!h || !X0 || S <= 0) return MAPE_ERR_INVALID_ARG;
+  if (!idle(h)) return MAPE_ERR_STATE;
+  h->join();
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (h->st.phase != MAPE_PHASE_DONE || h->dirs == nullptr) return MAPE_ERR_STATE;
+  }
+  if (f) {
+    if (f->n != h->n || f->m != h->m) return MAPE_ERR_SHAPE;
+    int rc = set_objective(h, f);
+    if (rc) return rc;
+    MAPE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (h->K > 0)
+      if ((rc = mape_direction_coeffs(h->dqr, h->dqc, h->dqv, h->nnz, h->has_w ? h->dw : nullptr, h->n, h->dirs,
+                                      h->K, h->ldg, h->da, h->dq4, h->stream)))
+        return rc;
+  }
+  const int n = h->n;
+  h->release_all(h->aug_bufs);
+  h->S = S;
+  h->dX = h->take<int32_t>(h->aug_bufs, (size_t)S * n);
+  h->dF = h->take<int64_t>(h->aug_bufs, (size_t)S);
+  int32_t* dbad = h->take<int32_t>(h->aug_bufs, 1);
+  h->aug_work_bytes = mape_augment_workspace_bytes(n, S, h->K);
+  h->dAugWork = h->take<char>(h->aug_bufs, h->aug_work_bytes);
+  if (!h->dX || !h->dF || !dbad || !h->dAugWork) return MAPE_ERR_OOM;
+  int rc = upload(h, h->dX, X0, sizeof(int32_t) * (size_t)S * n);
+  if (rc) return rc;
+  MAPE_CUDA_TRY(cudaMemsetAsync(dbad, 0, 4, h->stream));
+  feasible_check_kernel<<<S, 128, 0, h->stream>>>(h->dA, h->db, h->dX, h->m, n, S, dbad);
+  MAPE_LAUNCH_CHECK();
+  int32_t bad = 0;
+  MAPE_CUDA_TRY(cudaMemcpyAsync(&bad, dbad, 4, cudaMemcpyDeviceToHost, h->stream));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (bad) return MAPE_ERR_INFEASIBLE;
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    h->busy = true;
+    h->st.phase = MAPE_PHASE_AUGMENTING;
+  }
+  h->cancel.store(false);
+  int64_t iters = h->cfg.max_aug_iters;
+  h->worker = std::thread([h, iters]() {
+    cudaSetDevice(h->dev);
+    int r = h->run_augment(iters);
+    h->finish(r);
+  });
+  return MAPE_OK;
+}
+
+extern "C" int mape_poll(mape_handle h, mape_status* st) {
+  if (!h || !st) return MAPE_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  *st = h->st;
+  return MAPE_OK;
+}
+
+extern "C" int mape_wait(mape_handle h, int64_t timeout_ns) {
+  if (!h) return MAPE_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(h->mu);
+  bool done = h->cv.wait_for(lk, std::chrono::nanoseconds(timeout_ns < 0 ? 0 : timeout_ns), [h] { return !h->busy; });
+  if (!done) return MAPE_ERR_TIMEOUT;
+  return h->st.error;
+}
+
+extern "C" int mape_cancel(mape_handle h) {
+  if (!h) return MAPE_ERR_INVALID_ARG;
+  h->cancel.store(true);
+  return MAPE_OK;
+}
+
+extern "C" int mape_get_directions(mape_handle h, int32_t* G, int64_t cap, int64_t* K) {
+  using namespace mape_detail;
+  if (!h || !K) return MAPE_ERR_INVALID_ARG;
+  if (!idle(h)) return MAPE_ERR_STATE;
+  *K = h->K;
+  if (h->dirs == nullptr) return MAPE_ERR_STATE;
+  if (cap < h->K) return MAPE_ERR_CAPACITY;
+  if (h->K == 0) return MAPE_OK;
+  if (!G) return MAPE_ERR_INVALID_ARG;
+  int32_t* tmp = static_cast<int32_t*>(h->alloc(sizeof(int32_t) * (size_t)h->K * h->n));
+  if (!tmp) return MAPE_ERR_OOM;
+  int64_t tot = h->K * h->n;
+  i8_to_i32_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, h->stream>>>(h->dirs, h->K, h->n, h->ldg, tmp);
+  cudaError_t e = cudaMemcpyAsync(G, tmp, sizeof(int32_t) * (size_t)tot, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  h->release(tmp, sizeof(int32_t) * (size_t)tot);
+  if (e != cudaSuccess) {
+    record_cuda_error(e, "get_directions", __FILE__, __LINE__);
+    return MAPE_ERR_CUDA;
+  }
+  return MAPE_OK;
+}
+
+extern "C" int mape_get_solution(mape_handle h, int32_t* x, int64_t* fval) {
+  if (!h || !x || !fval) return MAPE_ERR_INVALID_ARG;
+  if (!idle(h)) return MAPE_ERR_STATE;
+  if ((int)h->best_x.size() != h->n) return MAPE_ERR_STATE;
+  std::memcpy(x, h->best_x.data(), sizeof(int32_t) * h->n);
+  *fval = h->best_f;
+  return MAPE_OK;
+}
+
+extern "C" int mape_get_solutions(mape_handle h, int32_t* X, int64_t* fval, int32_t S) {
+  if (!h || !X || !fval) return MAPE_ERR_INVALID_ARG;
+  if (!idle(h)) return MAPE_ERR_STATE;
+  if (h->dX == nullptr || S != h->S) return MAPE_ERR_STATE;
+  MAPE_CUDA_TRY(cudaMemcpyAsync(X, h->dX, sizeof(int32_t) * (size_t)S * h->n, cudaMemcpyDeviceToHost, h->stream));
+  MAPE_CUDA_TRY(cudaMemcpyAsync(fval, h->dF, sizeof(int64_t) * (size_t)S, cudaMemcpyDeviceToHost, h->stream));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return MAPE_OK;
+}
+
+extern "C" void mape_destroy(mape_handle h) {
+  if (!h) return;
+  h->cancel.store(true);
+  h->join();
+  h->release_all(h->aug_bufs);
+  h->release_all(h->job_bufs);
+  h->release_all(h->owned);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}

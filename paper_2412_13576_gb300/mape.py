@@ -1,0 +1,417 @@
+"""Python binding of libmape (ctypes).  Argument marshalling only: every step
+of the path runs in the library's CUDA kernels.  Names follow include/mape.h.
+
+Device buffers are torch tensors (torch is used for device memory and
+streams); the handle API takes host numpy arrays.  If the library is missing
+or cannot be loaded, every call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR = {
+    -1: "INVALID_ARG", -2: "SHAPE", -3: "NOT_KERNEL_BASIS", -4: "BOUNDS", -5: "INFEASIBLE",
+    -6: "OVERFLOW", -7: "CAPACITY", -8: "CUDA", -9: "TIMEOUT", -10: "STATE", -11: "OOM",
+    -12: "KERNEL_TEST", -13: "NUMERIC", -14: "CANCELLED",
+}
+PREC_FP32 = 0
+PREC_BF16 = 1
+PREC_BF16X1 = 2
+PHASES = ["IDLE", "EXTRACTING", "FILTERING", "AUGMENTING", "DONE", "ERROR"]
+
+
+class MapeError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        name = ERR.get(code, str(code))
+        extra = ""
+        if code == -8 and _LIB is not None:
+            extra = ": " + _LIB.mape_last_cuda_error().decode()
+        super().__init__(f"{where} failed with MAPE_ERR_{name}{extra}")
+
+
+P_ = C.c_void_p
+I32 = C.c_int32
+I64 = C.c_int64
+F32 = C.c_float
+
+
+class Config(C.Structure):
+    _fields_ = [("lambda1", F32), ("lambda2", F32), ("lr", F32), ("eps", F32), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("T", I32), ("period", I32), ("precision", I32), ("reserved", I32),
+                ("cand_capacity", I64), ("max_aug_iters", I64)]
+
+
+class ExtractArgs(C.Structure):
+    _fields_ = [("n", I32), ("d", I32), ("P", I32), ("B", P_), ("span", P_), ("Z", P_), ("M", P_),
+                ("V", P_), ("t0", I32), ("T", I32), ("period", I32), ("precision", I32),
+                ("lambda1", F32), ("lambda2", F32), ("lr", F32), ("eps", F32), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("cand", P_), ("ldc", I32), ("pad0", I32), ("cand_cap", I64),
+                ("cand_count", P_), ("flags", P_), ("dbg_phi", P_), ("dbg_grad", P_),
+                ("workspace", P_), ("workspace_bytes", C.c_size_t)]
+
+
+class AugmentArgs(C.Structure):
+    _fields_ = [("n", I32), ("S", I32), ("K", I64), ("G", P_), ("ldg", I32), ("pad0", I32),
+                ("a", P_), ("q4", P_), ("q_row", P_), ("q_col", P_), ("q_val", P_), ("nnz", I32),
+                ("pad1", I32), ("c", P_), ("w", P_), ("l", P_), ("u", P_), ("X", P_), ("fval", P_),
+                ("moves", P_), ("nmoves", P_), ("moves_cap", I32), ("pad2", I32),
+                ("max_iters", I64), ("workspace", P_), ("workspace_bytes", C.c_size_t)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("n", I32), ("m", I32), ("Q", P_), ("c", P_), ("w", P_)]
+
+
+class Status(C.Structure):
+    _fields_ = [("phase", I32), ("error", I32), ("candidates", I64), ("unique", I64),
+                ("kernel_failures", I64), ("directions", I64), ("aug_iters", I64), ("best_f", I64),
+                ("best_start", I32), ("pad0", I32), ("extract_ms", C.c_double),
+                ("filter_ms", C.c_double), ("augment_ms", C.c_double),
+                ("first_improve_ms", C.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
+        d["phase"] = PHASES[self.phase] if 0 <= self.phase < len(PHASES) else self.phase
+        return d
+
+
+_LIB = None
+
+_SIGS = {
+    "mape_default_config": (None, [C.POINTER(Config)]),
+    "mape_version": (C.c_char_p, []),
+    "mape_last_cuda_error": (C.c_char_p, []),
+    "mape_project_workspace_bytes": (C.c_size_t, [I32, I32]),
+    "mape_project_starts": (C.c_int, [P_, I32, I32, P_, I32, P_, P_, C.c_size_t, P_]),
+    "mape_phi_grad": (C.c_int, [P_, I32, I32, P_, I32, F32, F32, P_, P_, P_]),
+    "mape_extract_workspace_bytes": (C.c_size_t, [I32, I32, I32, I32]),
+    "mape_extract": (C.c_int, [C.POINTER(ExtractArgs), P_]),
+    "mape_dedup_workspace_bytes": (C.c_size_t, [I64, I32]),
+    "mape_dedup": (C.c_int, [P_, I64, I32, I32, P_, I64, C.POINTER(I64), P_, C.c_size_t, P_]),
+    "mape_kernel_test_workspace_bytes": (C.c_size_t, []),
+    "mape_kernel_test": (C.c_int, [P_, I32, I32, P_, I64, I32, P_, C.POINTER(I64), P_, C.c_size_t, P_]),
+    "mape_minimal_workspace_bytes": (C.c_size_t, [I64, I32]),
+    "mape_minimal_filter": (C.c_int, [P_, I64, I32, I32, P_, P_, P_, C.POINTER(I64), P_, C.c_size_t, P_]),
+    "mape_direction_coeffs": (C.c_int, [P_, P_, P_, I32, P_, I32, P_, I64, I32, P_, P_, P_]),
+    "mape_augment_workspace_bytes": (C.c_size_t, [I32, I32, I64]),
+    "mape_augment_run": (C.c_int, [C.POINTER(AugmentArgs), C.POINTER(I64), P_]),
+    "mape_set_allocator": (C.c_int, [P_, P_, P_]),
+    "mape_create_instance": (C.c_int, [P_, P_, P_, P_, C.POINTER(Problem), P_, C.POINTER(Config), P_,
+                                       C.POINTER(P_)]),
+    "mape_extract_directions": (C.c_int, [P_, I32, P_, P_]),
+    "mape_augment": (C.c_int, [P_, P_, I32, C.POINTER(Problem)]),
+    "mape_poll": (C.c_int, [P_, C.POINTER(Status)]),
+    "mape_wait": (C.c_int, [P_, I64]),
+    "mape_cancel": (C.c_int, [P_]),
+    "mape_get_directions": (C.c_int, [P_, P_, I64, C.POINTER(I64)]),
+    "mape_get_solution": (C.c_int, [P_, P_, C.POINTER(I64)]),
+    "mape_get_solutions": (C.c_int, [P_, P_, P_, I32]),
+    "mape_destroy": (None, [P_]),
+}
+
+
+def library_path() -> str:
+    """The in-tree build, unless MAPE_LIBRARY names another build of libmape."""
+    return os.environ.get("MAPE_LIBRARY", _build.LIB)
+
+
+def lib(build_if_missing: bool = False):
+    """The loaded libmape.  Raises if it is not built (or build_if_missing)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmape is not built ({path}); run __graft_entry__.build()")
+    L = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = L
+    return L
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise MapeError(rc, where)
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def default_config(**over) -> Config:
+    cfg = Config()
+    lib().mape_default_config(C.byref(cfg))
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def round16(n: int) -> int:
+    return (n + 15) // 16 * 16
+
+
+def _workspace(nbytes, device):
+    import torch
+    return torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device)
+
+
+# ---- stage entry points (torch device tensors) ------------------------------
+
+def project_starts(B, G0, stream=None):
+    """a2: Z0 = (B^T B)^{-1} B^T g per row of G0.  B int32 [n,d], G0 f32 [P,n]."""
+    import torch
+    n, d = B.shape
+    P = G0.shape[0]
+    Z0 = torch.empty((P, d), dtype=torch.float32, device=B.device)
+    ws = _workspace(lib().mape_project_workspace_bytes(n, d), B.device)
+    _check(lib().mape_project_starts(_ptr(B), n, d, _ptr(G0), P, _ptr(Z0), _ptr(ws), ws.numel(),
+                                     _stream(stream)), "mape_project_starts")
+    return Z0
+
+
+def phi_grad(B, Z, lambda1=0.85, lambda2=1.0, stream=None):
+    """a3-a5 in FP32: (phi [P], grad [P,d])."""
+    import torch
+    n, d = B.shape
+    P = Z.shape[0]
+    phi = torch.empty(P, dtype=torch.float32, device=B.device)
+    grad = torch.empty((P, d), dtype=torch.float32, device=B.device)
+    _check(lib().mape_phi_grad(_ptr(B), n, d, _ptr(Z), P, lambda1, lambda2, _ptr(phi), _ptr(grad),
+                               _stream(stream)), "mape_phi_grad")
+    return phi, grad
+
+
+def extract(B, span, Z, M, V, *, t0, T, cfg: Config, cand, cand_count, flags, ldc,
+            dbg_phi=None, dbg_grad=None, workspace=None, stream=None):
+    """a3-a8: T Adam steps of Algorithm 2 in place on Z/M/V; appends to cand."""
+    n, d = B.shape
+    P = Z.shape[0]
+    a = ExtractArgs()
+    a.n, a.d, a.P = n, d, P
+    a.B, a.span, a.Z, a.M, a.V = _ptr(B), _ptr(span), _ptr(Z), _ptr(M), _ptr(V)
+    a.t0, a.T, a.period, a.precision = t0, T, cfg.period, cfg.precision
+    a.lambda1, a.lambda2, a.lr = cfg.lambda1, cfg.lambda2, cfg.lr
+    a.beta1, a.beta2, a.eps = cfg.beta1, cfg.beta2, cfg.eps
+    a.cand = _ptr(cand)
+    a.ldc = ldc
+    a.cand_cap = cand.shape[0] if cand is not None else 0
+    a.cand_count, a.flags = _ptr(cand_count), _ptr(flags)
+    a.dbg_phi, a.dbg_grad = _ptr(dbg_phi), _ptr(dbg_grad)
+    if workspace is None:
+        workspace = _workspace(lib().mape_extract_workspace_bytes(n, d, P, cfg.precision), B.device)
+    a.workspace, a.workspace_bytes = _ptr(workspace), workspace.numel()
+    _check(lib().mape_extract(C.byref(a), _stream(stream)), "mape_extract")
+
+
+def dedup(cand, count, n, stream=None):
+    """a10: distinct rows of cand[:count], sorted lexicographically."""
+    import torch
+    ldc = cand.shape[1]
+    uniq = torch.empty((max(count, 1), ldc), dtype=torch.int8, device=cand.device)
+    ws = _workspace(lib().mape_dedup_workspace_bytes(count, ldc), cand.device)
+    K = I64(0)
+    _check(lib().mape_dedup(_ptr(cand), count, n, ldc, _ptr(uniq), uniq.shape[0], C.byref(K), _ptr(ws),
+                            ws.numel(), _stream(stream)), "mape_dedup")
+    return uniq[:K.value]
+
+
+def kernel_test(A, G, n, stream=None):
+    """a9: (ok [K] uint8, failures)."""
+    import torch
+    m = A.shape[0]
+    K = G.shape[0]
+    ok = torch.empty(max(K, 1), dtype=torch.uint8, device=G.device)
+    ws = _workspace(lib().mape_kernel_test_workspace_bytes(), G.device)
+    fails = I64(0)
+    _check(lib().mape_kernel_test(_ptr(A), m, n, _ptr(G), K, G.shape[1], _ptr(ok), C.byref(fails), _ptr(ws),
+                                  ws.numel(), _stream(stream)), "mape_kernel_test")
+    return ok[:K], fails.value
+
+
+def minimal_filter(G, n, valid=None, stream=None):
+    """a11: (keep [K] uint8, kept rows in input order)."""
+    import torch
+    K, ldg = G.shape
+    keep = torch.empty(max(K, 1), dtype=torch.uint8, device=G.device)
+    out = torch.empty((max(K, 1), ldg), dtype=torch.int8, device=G.device)
+    ws = _workspace(lib().mape_minimal_workspace_bytes(K, n), G.device)
+    Ko = I64(0)
+    _check(lib().mape_minimal_filter(_ptr(G), K, n, ldg, _ptr(valid), _ptr(keep), _ptr(out), C.byref(Ko),
+                                     _ptr(ws), ws.numel(), _stream(stream)), "mape_minimal_filter")
+    return keep[:K], out[:Ko.value]
+
+
+def coo_upper(Q):
+    """Upper triangle (incl. diagonal) of a symmetric numpy matrix as COO int32 arrays."""
+    Q = np.asarray(Q)
+    r, c = np.nonzero(np.triu(Q))
+    return r.astype(np.int32), c.astype(np.int32), Q[r, c].astype(np.int32)
+
+
+def direction_coeffs(qr, qc, qv, w, n, G, stream=None):
+    """a12: (a [K] int64, q4 [K] int64)."""
+    import torch
+    K, ldg = G.shape
+    a = torch.empty(max(K, 1), dtype=torch.int64, device=G.device)
+    q4 = torch.empty(max(K, 1), dtype=torch.int64, device=G.device)
+    _check(lib().mape_direction_coeffs(_ptr(qr), _ptr(qc), _ptr(qv), qv.numel(), _ptr(w), n, _ptr(G), K, ldg,
+                                       _ptr(a), _ptr(q4), _stream(stream)), "mape_direction_coeffs")
+    return a[:K], q4[:K]
+
+
+def augment_run(G, n, a, q4, qr, qc, qv, c, w, l, u, X, *, max_iters=10 ** 6, moves_cap=0, stream=None):
+    """a13-a14: Algorithm 1 in place on X [S,n]; returns (fval, iters, moves, nmoves)."""
+    import torch
+    K, ldg = G.shape
+    S = X.shape[0]
+    dev = X.device
+    fval = torch.empty(S, dtype=torch.int64, device=dev)
+    moves = torch.zeros((S, moves_cap, 4), dtype=torch.int64, device=dev) if moves_cap else None
+    nmoves = torch.zeros(S, dtype=torch.int32, device=dev)
+    ws = _workspace(lib().mape_augment_workspace_bytes(n, S, K), dev)
+    A = AugmentArgs()
+    A.n, A.S, A.K, A.G, A.ldg = n, S, K, _ptr(G), ldg
+    A.a, A.q4 = _ptr(a), _ptr(q4)
+    A.q_row, A.q_col, A.q_val, A.nnz = _ptr(qr), _ptr(qc), _ptr(qv), qv.numel()
+    A.c, A.w, A.l, A.u = _ptr(c), _ptr(w), _ptr(l), _ptr(u)
+    A.X, A.fval = _ptr(X), _ptr(fval)
+    A.moves, A.nmoves, A.moves_cap = _ptr(moves), _ptr(nmoves), moves_cap
+    A.max_iters = max_iters
+    A.workspace, A.workspace_bytes = _ptr(ws), ws.numel()
+    iters = I64(0)
+    _check(lib().mape_augment_run(C.byref(A), C.byref(iters), _stream(stream)), "mape_augment_run")
+    return fval, iters.value, moves, nmoves
+
+
+# ---- instance handle (host numpy arrays) ------------------------------------
+
+def _np(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _host(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+class Instance:
+    """mape_create_instance ... mape_destroy over host arrays."""
+
+    def __init__(self, A, b, l, u, Q, c, w, B, cfg: Config | None = None, stream=None):
+        self._keep = {}
+        self.m, self.n = A.shape
+        self.cfg = cfg if cfg is not None else default_config()
+        arrs = dict(A=_np(A, np.int32), b=_np(b, np.int64), l=_np(l, np.int32), u=_np(u, np.int32),
+                    B=_np(B, np.int32))
+        self._keep.update(arrs)
+        prob = self._problem(Q, c, w)
+        h = C.c_void_p()
+        st = C.c_void_p(stream.cuda_stream) if stream is not None else None
+        _check(lib().mape_create_instance(_host(arrs["A"]), _host(arrs["b"]), _host(arrs["l"]),
+                                          _host(arrs["u"]), C.byref(prob), _host(arrs["B"]),
+                                          C.byref(self.cfg), st, C.byref(h)), "mape_create_instance")
+        self.h = h
+
+    def _problem(self, Q, c, w):
+        Qa, ca = _np(Q, np.int32), _np(c, np.int32)
+        wa = None if w is None else _np(w, np.int32)
+        self._keep.update(Q=Qa, c=ca, w=wa)
+        return Problem(self.n, self.m, _host(Qa), _host(ca), _host(wa))
+
+    @classmethod
+    def from_generated(cls, inst, cfg=None, stream=None):
+        return cls(inst.A, inst.b, inst.l, inst.u, inst.Q, inst.c, inst.w, inst.B, cfg, stream)
+
+    def extract_directions(self, P, Z0=None, G0=None):
+        """Z0/G0: host numpy float32 arrays or CUDA torch tensors."""
+        def arg(x):
+            if x is None:
+                return None
+            if hasattr(x, "data_ptr"):
+                self._keep["start_dev"] = x
+                return C.c_void_p(x.data_ptr())
+            x = _np(x, np.float32)
+            self._keep["start"] = x
+            return _host(x)
+        _check(lib().mape_extract_directions(self.h, P, arg(Z0), arg(G0)), "mape_extract_directions")
+
+    def augment(self, X0, f=None):
+        if hasattr(X0, "data_ptr"):
+            self._keep["x0_dev"] = X0
+            ptr, S = C.c_void_p(X0.data_ptr()), X0.shape[0]
+        else:
+            X0 = _np(np.atleast_2d(X0), np.int32)
+            self._keep["x0"] = X0
+            ptr, S = _host(X0), X0.shape[0]
+        prob = None if f is None else C.byref(self._problem(*f))
+        _check(lib().mape_augment(self.h, ptr, S, prob), "mape_augment")
+
+    def poll(self) -> dict:
+        st = Status()
+        _check(lib().mape_poll(self.h, C.byref(st)), "mape_poll")
+        return st.as_dict()
+
+    def wait(self, timeout_s: float = 600.0):
+        rc = lib().mape_wait(self.h, int(timeout_s * 1e9))
+        _check(rc, "mape_wait")
+
+    def cancel(self):
+        _check(lib().mape_cancel(self.h), "mape_cancel")
+
+    def directions(self) -> np.ndarray:
+        K = I64(0)
+        rc = lib().mape_get_directions(self.h, None, 0, C.byref(K))
+        if rc not in (OK, -7):
+            _check(rc, "mape_get_directions")
+        out = np.empty((K.value, self.n), dtype=np.int32)
+        _check(lib().mape_get_directions(self.h, _host(out), K.value, C.byref(K)), "mape_get_directions")
+        return out
+
+    def solution(self):
+        x = np.empty(self.n, dtype=np.int32)
+        f = I64(0)
+        _check(lib().mape_get_solution(self.h, _host(x), C.byref(f)), "mape_get_solution")
+        return x, f.value
+
+    def solutions(self, S):
+        X = np.empty((S, self.n), dtype=np.int32)
+        f = np.empty(S, dtype=np.int64)
+        _check(lib().mape_get_solutions(self.h, _host(X), _host(f), S), "mape_get_solutions")
+        return X, f
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mape_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,158 @@
+"""The tcgen05 BF16 path of Algorithm 2 against the FP64 oracle.
+
+B is exact in BF16 and every partial sum of B round(z) is an integer below
+2^24, so the collected candidates are compared bit-exactly.  The forward
+product carries z as hi + lo (16 significant bits, MAPE_PREC_BF16) or hi
+alone (8 bits, MAPE_PREC_BF16X1); the gradient is compared within 1e-5 on
+the starts whose sign(Bz) that arithmetic determines, and Phi on all starts
+(1e-4 and 2e-2)."""
+import numpy as np
+import pytest
+
+from oracle import mape_oracle as O
+from paper_2412_13576_gb300 import instances as I
+
+from .gpu_common import dev, rel_fro, rows_set
+from .test_gpu_stages import _extract_steps
+
+pytestmark = pytest.mark.gpu
+
+BF16_TOL = 2e-2
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_13576_gb300 import mape
+    mape.lib(build_if_missing=True)
+    return mape
+
+
+def bf16_stable_rows(B, Z, bits):
+    """Starts whose sign(Bz) cannot change when z is rounded to `bits`
+    significant bits (relative error 2^-bits) and summed in FP32."""
+    Bf = np.asarray(B, np.float64)
+    Zf = np.asarray(Z, np.float64)
+    Y = Zf @ Bf.T
+    bound = (2.0 ** -bits + Bf.shape[1] * 2.0 ** -23) * (np.abs(Zf) @ np.abs(Bf).T) * 1.01 + 1e-6
+    return np.all(np.abs(Y) > bound, axis=1)
+
+
+# precision -> (significant bits of z in B z, tolerance on Phi over all starts,
+#               largest share of starts whose sign(Bz) the arithmetic cannot fix)
+PRECISIONS = {1: (16, 1e-4, 0.15), 2: (8, BF16_TOL, 1.0)}
+
+
+def _starts(inst, P, seed):
+    if inst.n <= 20:
+        return I.normal_starts(inst, P, seed=seed).Z0
+    return O.project_to_coordinates(inst.B, I.uniform_samples(inst, P, seed=seed).G0).astype(np.float32)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("make,P,T", [(I.small_dense, 256, 40), (I.medium_sparse, 300, 8),
+                                      (I.tiny_graver_case, 130, 40)])
+def test_bf16_per_step(M, make, P, T, precision):
+    """The gradient of Eq. (3) jumps by 2 B_i where (Bz)_i changes sign, so it
+    is compared on the starts whose sign(Bz) the arithmetic fixes (every
+    |(Bz)_i| above the error bound of z carried to `bits` bits and summed in
+    FP32): there within 1e-5 for both precisions.  The share of other starts is
+    bounded (2% for hi + lo), Phi (continuous) is compared on all starts, and
+    the collected candidates are bit-exact."""
+    inst = make()
+    Z0 = _starts(inst, P, 2001)
+    ldc = M.round16(inst.n)
+    bits, tol_phi, max_ambiguous = PRECISIONS[precision]
+    states, grads, phis, cand = _extract_steps(M, inst, Z0, T, precision, ldc)
+    expect = set()
+    ambiguous = 0
+    for t, ((z, m, v), (z1, m1, v1)) in enumerate(states):
+        go = O.phi_grad(inst.B, z, 0.85, 1.0)
+        ok = bf16_stable_rows(inst.B, z, bits)
+        ambiguous += int((~ok).sum())
+        if ok.any():
+            assert rel_fro(grads[t][ok], go[ok]) < FP32_TOL
+        assert rel_fro(phis[t], O.phi(inst.B, z, 0.85, 1.0)) < tol_phi
+        zo, mo, vo = O.adam_update(z.astype(np.float64), m, v, grads[t].astype(np.float64), t + 1, 0.003)
+        assert rel_fro(z1, zo) < FP32_TOL
+        assert rel_fro(m1, mo) < FP32_TOL
+        assert rel_fro(v1, vo) < FP32_TOL
+        expect |= O.collect(inst.A, inst.B, inst.l, inst.u, z1)
+    assert ambiguous <= max_ambiguous * P * T
+    assert rows_set(cand, inst.n) == expect
+
+
+@pytest.mark.parametrize("make,P,T,period", [(I.small_dense, 300, 25, 1), (I.medium_sparse, 1000, 20, 1),
+                                             (I.small_dense, 200, 24, 3)])
+def test_bf16_one_launch_equals_single_steps(M, make, P, T, period):
+    """T steps in one persistent launch give bitwise the same Z, M, V as T
+    launches of one step, and the same set of collected directions (P not a
+    multiple of 128 exercises the ragged last tile)."""
+    import torch
+    inst = make()
+    Z0 = _starts(inst, P, 7)
+    ldc = M.round16(inst.n)
+    B, span = dev(inst.B), dev((inst.u - inst.l).astype(np.int32))
+    results = []
+    for single in (False, True):
+        cfg = M.default_config(precision=M.PREC_BF16, period=period)
+        Z = dev(Z0)
+        Mm = torch.zeros_like(Z)
+        V = torch.zeros_like(Z)
+        cand = torch.zeros((P * T + 8, ldc), dtype=torch.int8, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+        if single:
+            for t in range(T):
+                M.extract(B, span, Z, Mm, V, t0=t, T=1, cfg=cfg, cand=cand, cand_count=cnt, flags=flags, ldc=ldc)
+        else:
+            M.extract(B, span, Z, Mm, V, t0=0, T=T, cfg=cfg, cand=cand, cand_count=cnt, flags=flags, ldc=ldc)
+        torch.cuda.synchronize()
+        assert int(flags.item()) == 0
+        c = cand[: int(cnt.item())].cpu().numpy()
+        results.append((Z.cpu().numpy(), Mm.cpu().numpy(), V.cpu().numpy(), rows_set(c, inst.n), c))
+    (z1, m1, v1, s1, c1), (z2, m2, v2, s2, _) = results
+    assert np.array_equal(z1, z2) and np.array_equal(m1, m2) and np.array_equal(v1, v2)
+    assert s1 == s2
+    assert len(s1) > 0
+    assert np.all(c1[:, inst.n:] == 0)
+    G = np.array(sorted(s1), dtype=np.int64)
+    assert np.all(O.kernel_condition(inst.A, G)) and np.all(O.bound_consistent(G, inst.l, inst.u))
+
+
+def test_bf16_rejects_inexact_basis(M):
+    """|B_ij| > 256 is not exact in BF16: flag 8, nothing collected."""
+    import torch
+    inst = I.small_dense()
+    Bbig = inst.B.copy()
+    Bbig[0, 0] = 300
+    Z = dev(I.normal_starts(inst, 64, seed=1).Z0)
+    cand = torch.zeros((1024, 32), dtype=torch.int8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cfg = M.default_config(precision=M.PREC_BF16)
+    M.extract(dev(Bbig), dev((inst.u - inst.l).astype(np.int32)), Z, torch.zeros_like(Z), torch.zeros_like(Z),
+              t0=0, T=3, cfg=cfg, cand=cand, cand_count=cnt, flags=flags, ldc=32)
+    torch.cuda.synchronize()
+    assert int(flags.item()) & 8
+    assert int(cnt.item()) == 0
+
+
+def test_bf16_shape_limits(M):
+    """n or d above 256 is refused with MAPE_ERR_SHAPE before any launch."""
+    import torch
+    n, d = 300, 250
+    B = torch.zeros((n, d), dtype=torch.int32, device="cuda")
+    span = torch.ones(n, dtype=torch.int32, device="cuda")
+    Z = torch.zeros((128, d), dtype=torch.float32, device="cuda")
+    cand = torch.zeros((16, 304), dtype=torch.int8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cfg = M.default_config(precision=M.PREC_BF16)
+    with pytest.raises(M.MapeError) as e:
+        M.extract(B, span, Z, Z.clone(), Z.clone(), t0=0, T=1, cfg=cfg, cand=cand, cand_count=cnt, flags=flags,
+                  ldc=304, workspace=torch.zeros(64, dtype=torch.uint8, device="cuda"))
+    assert e.value.code == -2

@@ -1,0 +1,82 @@
+"""The instance handle end to end (host arrays in, host arrays out): the
+returned set satisfies C1, C4, nonzero, canonical sign, distinctness,
+lexicographic order and ⊑-minimality; augmentation equals the oracle's
+Algorithm 1 on the same set; status, errors and reuse behave."""
+import numpy as np
+import pytest
+
+from oracle import mape_oracle as O
+from paper_2412_13576_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_13576_gb300 import mape
+    mape.lib(build_if_missing=True)
+    return mape
+
+
+def check_direction_set(inst, D):
+    assert D.shape[0] > 0
+    assert np.all(O.kernel_condition(inst.A, D))
+    assert np.all(O.bound_consistent(D, inst.l, inst.u))
+    assert np.all(np.any(D != 0, axis=1))
+    assert all(np.array_equal(O.canonical_sign(g), g) for g in D)
+    assert np.array_equal(O.sort_directions(D), D)
+    assert np.unique(D, axis=0).shape[0] == D.shape[0]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_handle_small(M, precision):
+    inst = I.small_dense()
+    st = I.normal_starts(inst, 256, seed=2001)
+    cfg = M.default_config(T=200, precision=precision)
+    with M.Instance.from_generated(inst, cfg) as h:
+        h.extract_directions(256, Z0=st.Z0)
+        h.wait(300)
+        s = h.poll()
+        assert s["phase"] == "DONE" and s["error"] == 0
+        D = h.directions()
+        check_direction_set(inst, D)
+        assert np.all(O.minimal_elements(D))
+        assert s["directions"] == D.shape[0] <= s["unique"] <= s["candidates"]
+        assert s["kernel_failures"] == 0
+        h.augment(inst.xbar[None, :])
+        h.wait(300)
+        x, fx = h.solution()
+        xo, fo, mo = O.augment(inst.A, inst.b, inst.l, inst.u, inst.Q, inst.c, None, D, inst.xbar)
+        assert fx == fo and np.array_equal(x, xo)
+        assert h.poll()["aug_iters"] == len(mo) + 1
+        # reuse: a new objective on the same direction set (§1, reusability)
+        rng = np.random.default_rng(5)
+        c2 = rng.integers(-10, 11, size=inst.n).astype(np.int32)
+        h.augment(inst.xbar[None, :], f=(inst.Q, c2, None))
+        h.wait(300)
+        x2, f2 = h.solution()
+        xo2, fo2, _ = O.augment(inst.A, inst.b, inst.l, inst.u, inst.Q, c2, None, D, inst.xbar)
+        assert f2 == fo2 and np.array_equal(x2, xo2)
+
+
+def test_handle_errors(M):
+    inst = I.small_dense()
+    bad_B = inst.B.copy()
+    bad_B[-1, 0] += 1
+    with pytest.raises(M.MapeError) as e:
+        M.Instance(inst.A, inst.b, inst.l, inst.u, inst.Q, inst.c, None, bad_B)
+    assert e.value.code == -3
+    with M.Instance.from_generated(inst, M.default_config(T=5, precision=0)) as h:
+        with pytest.raises(M.MapeError) as e:
+            h.augment(inst.xbar[None, :])           # no direction set yet
+        assert e.value.code == -10
+        h.extract_directions(64, Z0=I.normal_starts(inst, 64, seed=1).Z0)
+        h.wait(60)
+        x = inst.xbar.copy()
+        x[0] += 1                                    # breaks A x = b
+        with pytest.raises(M.MapeError) as e:
+            h.augment(x[None, :])
+        assert e.value.code == -5

@@ -1,0 +1,254 @@
+"""Parity of every stage of the CUDA path against the CPU oracle, called
+through the C ABI (device buffers).  Integer stages are compared bit-exactly;
+the FP32 continuous stages within relative 1e-5 (Frobenius) on starts whose
+sign pattern sign(Bz) is unambiguous in FP32."""
+import numpy as np
+import pytest
+
+from oracle import mape_oracle as O
+from paper_2412_13576_gb300 import instances as I
+
+from .gpu_common import dev, rel_fro, rows_set, sign_stable_rows
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_13576_gb300 import mape
+    mape.lib(build_if_missing=True)
+    return mape
+
+
+def _inst(name):
+    return {"small": I.small_dense, "medium": I.medium_sparse, "tiny": I.tiny_graver_case}[name]()
+
+
+# --- a2 ----------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,P", [("small", 300), ("medium", 1000)])
+def test_project_starts(M, name, P):
+    inst = _inst(name)
+    G0 = I.uniform_samples(inst, P, seed=7).G0
+    Z = M.project_starts(dev(inst.B), dev(G0)).cpu().numpy()
+    Zo = O.project_to_coordinates(inst.B, G0)
+    # FP32 Cholesky solve: relative error below d * cond(B^T B) * 2^-24 * 8
+    H = inst.B.astype(np.float64).T @ inst.B
+    bound = 8 * inst.d * np.linalg.cond(H) * 2.0 ** -24
+    assert rel_fro(Z, Zo) < bound, (rel_fro(Z, Zo), bound)
+
+
+# --- a3-a5 -----------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,P,scale", [("small", 512, 3.0), ("small", 512, 0.45), ("medium", 700, 4.0)])
+def test_phi_grad_fp32(M, name, P, scale):
+    inst = _inst(name)
+    rng = np.random.default_rng(11)
+    Z = rng.uniform(-scale, scale, size=(P, inst.d)).astype(np.float32)
+    Z[0] = 0.0                                  # z = 0: Phi = inf, gradient 0
+    Z[1] = np.rint(Z[1]) + (Z[1] == 0)          # an integer point
+    phi, grad = M.phi_grad(dev(inst.B), dev(Z))
+    phi, grad = phi.cpu().numpy(), grad.cpu().numpy()
+    po = O.phi(inst.B, Z, 0.85, 1.0)
+    go = O.phi_grad(inst.B, Z, 0.85, 1.0)
+    assert np.isinf(phi[0]) and np.all(grad[0] == 0)
+    ok = sign_stable_rows(inst.B, Z)
+    ok[0] = False
+    assert ok.sum() > 0.5 * (P - 2)
+    assert rel_fro(phi[ok], po[ok]) < FP32_TOL
+    assert rel_fro(grad[ok], go[ok]) < FP32_TOL
+
+
+# --- a3-a8 (FP32 path), step by step against the oracle ------------------------
+
+def _extract_steps(M, inst, Z0, T, precision, ldc, cap=1 << 16):
+    """Runs T single steps through mape_extract, returning per-step states,
+    gradients at the input point, and the collected candidate rows."""
+    import torch
+    cfg = M.default_config(precision=precision, T=1)
+    P = Z0.shape[0]
+    B, span = dev(inst.B), dev((inst.u - inst.l).astype(np.int32))
+    Z = dev(Z0.astype(np.float32))
+    Mm = torch.zeros_like(Z)
+    V = torch.zeros_like(Z)
+    cand = torch.zeros((cap, ldc), dtype=torch.int8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    gbuf = torch.empty_like(Z)
+    pbuf = torch.empty(P, dtype=torch.float32, device="cuda")
+    states, grads, phis = [], [], []
+    for t in range(T):
+        before = (Z.cpu().numpy(), Mm.cpu().numpy(), V.cpu().numpy())
+        M.extract(B, span, Z, Mm, V, t0=t, T=1, cfg=cfg, cand=cand, cand_count=cnt, flags=flags, ldc=ldc,
+                  dbg_phi=pbuf, dbg_grad=gbuf)
+        torch.cuda.synchronize()
+        states.append((before, (Z.cpu().numpy(), Mm.cpu().numpy(), V.cpu().numpy())))
+        grads.append(gbuf.cpu().numpy())
+        phis.append(pbuf.cpu().numpy())
+    assert int(flags.item()) == 0
+    return states, grads, phis, cand[: int(cnt.item())].cpu().numpy()
+
+
+@pytest.mark.parametrize("name,P,T", [("small", 256, 30), ("medium", 256, 6)])
+def test_extract_fp32_per_step(M, name, P, T):
+    """Each GPU step from the GPU's own state matches one oracle step (grad,
+    Adam update) within 1e-5, and the candidate rows collected over the run are
+    exactly the oracle's collection applied to the GPU's iterates."""
+    inst = _inst(name)
+    if name == "small":
+        Z0 = I.normal_starts(inst, P, seed=2001).Z0
+    else:
+        Z0 = O.project_to_coordinates(inst.B, I.uniform_samples(inst, P, seed=2002).G0).astype(np.float32)
+    ldc = M.round16(inst.n)
+    states, grads, phis, cand = _extract_steps(M, inst, Z0, T, M.PREC_FP32, ldc)
+    expect = set()
+    for t, ((z, m, v), (z1, m1, v1)) in enumerate(states):
+        go = O.phi_grad(inst.B, z, 0.85, 1.0)
+        ok = sign_stable_rows(inst.B, z)
+        assert ok.mean() > 0.5
+        assert rel_fro(grads[t][ok], go[ok]) < FP32_TOL
+        assert rel_fro(phis[t][ok], O.phi(inst.B, z, 0.85, 1.0)[ok]) < FP32_TOL
+        zo, mo, vo = O.adam_update(z.astype(np.float64), m, v, grads[t].astype(np.float64), t + 1, 0.003)
+        assert rel_fro(z1, zo) < FP32_TOL
+        assert rel_fro(m1, mo) < FP32_TOL
+        assert rel_fro(v1, vo) < FP32_TOL
+        expect |= O.collect(inst.A, inst.B, inst.l, inst.u, z1)
+    got = rows_set(cand, inst.n)
+    assert got == expect
+
+
+# --- a10 -----------------------------------------------------------------------
+
+@pytest.mark.parametrize("count,n", [(1, 5), (5000, 20), (40000, 200), (3, 300)])
+def test_dedup_exact(M, count, n):
+    rng = np.random.default_rng(count)
+    ldc = M.round16(n)
+    base = rng.integers(-4, 5, size=(max(1, count // 7), n)).astype(np.int8)
+    rows = base[rng.integers(0, base.shape[0], size=count)]
+    buf = np.zeros((count, ldc), np.int8)
+    buf[:, :n] = rows
+    uniq = M.dedup(dev(buf), count, n).cpu().numpy()
+    expect = O.sort_directions(np.unique(rows.astype(np.int64), axis=0))
+    assert np.array_equal(uniq[:, :n].astype(np.int64), expect)
+    assert np.all(uniq[:, n:] == 0)
+
+
+# --- a9 ------------------------------------------------------------------------
+
+def test_kernel_test_exact(M):
+    inst = I.medium_sparse()
+    rng = np.random.default_rng(3)
+    W = rng.integers(-2, 3, size=(3000, inst.d))
+    G = W @ inst.B.T.astype(np.int64)
+    G = np.clip(G, -127, 127)
+    G[::5, 7] += 1                      # planted rows outside the kernel
+    ldg = M.round16(inst.n)
+    buf = np.zeros((G.shape[0], ldg), np.int8)
+    buf[:, : inst.n] = G
+    ok, fails = M.kernel_test(dev(inst.A), dev(buf), inst.n)
+    expect = O.kernel_condition(inst.A, G)
+    assert np.array_equal(ok.cpu().numpy().astype(bool), expect)
+    assert fails == int((~expect).sum()) > 0
+
+
+# --- a11 -----------------------------------------------------------------------
+
+def _planted_set(rng, K, n):
+    """Random canonical distinct rows plus conformal sums that must be removed."""
+    base = rng.integers(-3, 4, size=(K, n)) * (rng.random((K, n)) < 0.3)
+    base = base[np.any(base != 0, axis=1)]
+    extra = []
+    for _ in range(K // 4):
+        a, b = base[rng.integers(0, base.shape[0], size=2)]
+        s = np.where(a * b >= 0, a + b, a)          # a ⊑ s by construction
+        if np.all(np.abs(s) <= 120):
+            extra.append(s)
+    G = np.concatenate([base, np.array(extra)]) if extra else base
+    G = np.array([O.canonical_sign(g) for g in G])
+    G = O.sort_directions(np.unique(G[np.any(G != 0, axis=1)], axis=0))
+    return G
+
+
+@pytest.mark.parametrize("K,n", [(300, 12), (2500, 40), (1200, 200)])
+def test_minimal_filter_exact(M, K, n):
+    rng = np.random.default_rng(K + n)
+    G = _planted_set(rng, K, n)
+    ldg = M.round16(n)
+    buf = np.zeros((G.shape[0], ldg), np.int8)
+    buf[:, :n] = G
+    valid = np.ones(G.shape[0], np.uint8)
+    valid[::17] = 0
+    keep, out = M.minimal_filter(dev(buf), n, valid=dev(valid))
+    keep = keep.cpu().numpy().astype(bool)
+    sub = G[valid.astype(bool)]
+    expect_sub = O.minimal_elements(sub)
+    expect = np.zeros(G.shape[0], bool)
+    expect[np.nonzero(valid)[0]] = expect_sub
+    assert np.array_equal(keep, expect)
+    assert np.array_equal(out.cpu().numpy()[:, :n].astype(np.int64), G[expect])
+    assert 0 < expect.sum() < valid.sum()
+
+
+# --- a12-a14 ---------------------------------------------------------------------
+
+def _directions_for(inst, P=256, T=60, seed=2001):
+    Z0 = I.normal_starts(inst, P, seed=seed).Z0
+    return O.parallel_extraction(inst.A, inst.B, inst.l, inst.u, Z0, T=T)["directions"]
+
+
+@pytest.mark.parametrize("quartic", [False, True])
+def test_direction_coeffs_exact(M, quartic):
+    inst = I.small_dense()
+    D = _directions_for(inst)
+    w = np.random.default_rng(1).integers(0, 4, size=inst.n).astype(np.int32) if quartic else None
+    ldg = M.round16(inst.n)
+    buf = np.zeros((D.shape[0], ldg), np.int8)
+    buf[:, : inst.n] = D
+    qr, qc, qv = M.coo_upper(inst.Q)
+    a, q4 = M.direction_coeffs(dev(qr), dev(qc), dev(qv), None if w is None else dev(w), inst.n, dev(buf))
+    a_exp = np.einsum("ki,ij,kj->k", D, inst.Q.astype(np.int64), D)
+    assert np.array_equal(a.cpu().numpy(), a_exp)
+    q4_exp = (D ** 4) @ w.astype(np.int64) if quartic else np.zeros(D.shape[0], np.int64)
+    assert np.array_equal(q4.cpu().numpy(), q4_exp)
+
+
+@pytest.mark.parametrize("quartic", [False, True])
+def test_augment_matches_algorithm1(M, quartic):
+    """Same moves, final point and value as the oracle's Algorithm 1 (which
+    evaluates f directly at every candidate point)."""
+    import torch
+    inst = I.small_dense()
+    D = _directions_for(inst)
+    w = np.random.default_rng(2).integers(0, 4, size=inst.n).astype(np.int32) if quartic else None
+    ldg = M.round16(inst.n)
+    buf = np.zeros((D.shape[0], ldg), np.int8)
+    buf[:, : inst.n] = D
+    Gd = dev(buf)
+    qr, qc, qv = (dev(x) for x in M.coo_upper(inst.Q))
+    wd = None if w is None else dev(w)
+    a, q4 = M.direction_coeffs(qr, qc, qv, wd, inst.n, Gd)
+    # several starts: xbar and feasible points reached by a few oracle moves
+    starts = [inst.xbar.astype(np.int64)]
+    x = starts[0]
+    for k in range(3):
+        for lam in O.feasible_step_lengths(inst.l, inst.u, x, D[k])[:1]:
+            x = x + lam * D[k]
+            starts.append(x.copy())
+    X0 = np.array(starts, np.int32)
+    X = dev(X0)
+    fval, iters, moves, nmoves = M.augment_run(Gd, inst.n, a, q4, qr, qc, qv, dev(inst.c), wd, dev(inst.l),
+                                               dev(inst.u), X, moves_cap=256)
+    X, fval = X.cpu().numpy(), fval.cpu().numpy()
+    moves, nmoves = moves.cpu().numpy(), nmoves.cpu().numpy()
+    for s in range(X0.shape[0]):
+        xo, fo, mo = O.augment(inst.A, inst.b, inst.l, inst.u, inst.Q, inst.c, w, D, X0[s])
+        assert fval[s] == fo
+        assert np.array_equal(X[s], xo)
+        got = [tuple(int(v) for v in moves[s, i]) for i in range(nmoves[s])]
+        assert got == [(k, e, lam, f) for k, e, lam, f in mo]
+    assert iters == max(nmoves) + 1

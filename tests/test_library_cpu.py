@@ -1,0 +1,95 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+include/mape.h declares; its struct layouts match the ctypes binding; argument
+checks answer before any device work.  CPU only (no compute calls)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mape.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2412_13576_gb300 import mape
+    return mape.lib(build_if_missing=True)
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(mape_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(n for n in names if not n.endswith("_fn")))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2412_13576_gb300 import mape
+    out = subprocess.run(["nm", "-D", "--defined-only", mape.library_path()], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (mape_\w+)", out))
+    declared = _declared()
+    assert len(declared) >= 25
+    missing = [n for n in declared if n not in exported]
+    assert not missing, missing
+
+
+def test_struct_layouts_match_binding(tmp_path, lib):
+    from paper_2412_13576_gb300 import mape
+    prog = tmp_path / "sizes.c"
+    prog.write_text('#include "mape.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){'
+                    'printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mape_config), sizeof(mape_extract_args),'
+                    'sizeof(mape_augment_args), sizeof(mape_problem), sizeof(mape_status),'
+                    'offsetof(mape_extract_args, cand_count), offsetof(mape_augment_args, max_iters));return 0;}')
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()))
+    expect = [ctypes.sizeof(mape.Config), ctypes.sizeof(mape.ExtractArgs), ctypes.sizeof(mape.AugmentArgs),
+              ctypes.sizeof(mape.Problem), ctypes.sizeof(mape.Status), mape.ExtractArgs.cand_count.offset,
+              mape.AugmentArgs.max_iters.offset]
+    assert got == expect
+
+
+def test_default_config_is_the_papers(lib):
+    from paper_2412_13576_gb300 import mape
+    c = mape.default_config()
+    assert (round(c.lambda1, 6), c.lambda2, round(c.lr, 6)) == (0.85, 1.0, 0.003)
+    assert (round(c.beta1, 6), round(c.beta2, 6), c.period) == (0.9, 0.999, 1)
+
+
+def test_argument_checks_without_device(lib):
+    from paper_2412_13576_gb300 import mape
+    assert lib.mape_extract(None, None) == -1
+    assert lib.mape_augment_run(None, None, None) == -1
+    h = ctypes.c_void_p()
+    assert lib.mape_create_instance(None, None, None, None, None, None, None, None, ctypes.byref(h)) == -1
+    K = ctypes.c_int64(5)
+    assert lib.mape_dedup(None, 0, 4, 16, None, 0, ctypes.byref(K), None, 0, None) == 0 and K.value == 0
+    assert lib.mape_dedup(None, 0, 4, 15, None, 0, ctypes.byref(K), None, 0, None) == -1
+    assert lib.mape_poll(None, None) == -1
+    assert lib.mape_wait(None, 0) == -1
+    lib.mape_destroy(None)
+    assert lib.mape_project_workspace_bytes(10, 5) > 100
+    assert lib.mape_dedup_workspace_bytes(1000, 32) > 1000 * 8
+
+
+def test_bounds_rejected_before_upload(lib):
+    """u - l > 127 cannot be stored as int8 directions: BOUNDS, no device work."""
+    import numpy as np
+    from paper_2412_13576_gb300 import mape
+    n, m = 4, 1
+    A = np.array([[1, 1, 1, 1]], np.int32)
+    B = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [-1, -1, -1]], np.int32)
+    b = np.zeros(1, np.int64)
+    l = np.zeros(n, np.int32)
+    u = np.array([1, 1, 1, 200], np.int32)
+    Q = np.eye(n, dtype=np.int32)
+    c = np.zeros(n, np.int32)
+    prob = mape.Problem(n, m, ctypes.c_void_p(Q.ctypes.data), ctypes.c_void_p(c.ctypes.data), None)
+    cfg = mape.default_config()
+    h = ctypes.c_void_p()
+    rc = lib.mape_create_instance(ctypes.c_void_p(A.ctypes.data), ctypes.c_void_p(b.ctypes.data),
+                                  ctypes.c_void_p(l.ctypes.data), ctypes.c_void_p(u.ctypes.data), ctypes.byref(prob),
+                                  ctypes.c_void_p(B.ctypes.data), ctypes.byref(cfg), None, ctypes.byref(h))
+    assert rc == -4
