@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark of the MAPE hot path: verified Graver directions per second.
+
+One step = one pass of the whole path on the medium workload (n = 200, m = 40,
+A = [C | I] with C 40x160 in [-3,3] at density 0.1, box [0,10], nonconvex
+quadratic f; P = 8192 starts from projected uniform samples, T = 1000 Adam
+steps): starting points, Algorithm 2 with collection every step, dedup, the
+kernel test, the minimality filter, the direction coefficients and
+Algorithm 1 from xbar.  value = directions that pass C1, C4, nonzero and
+set-minimality, summed over the timed steps and ranks, over the max-over-ranks
+device time of those steps.  Inputs are resident in device memory; L2 is
+flushed (256 MiB write) before every timed step, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own replica (its own start seed): the
+starts are independent problems, so there is no data-path collective and the
+scaling is weak.  --impl reference times the CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "verified Graver directions/s"
+UNIT = "directions/s"
+N_FULL, M_FULL, P_FULL, T_FULL = 200, 40, 8192, 1000
+WORKLOAD = ("medium_sparse: n=200 m=40 d=160, A=[C|I_40], C 40x160 in [-3,3] at density 0.1, box [0,10], "
+            "Q sym in [-5,5] at 0.05, c in [-20,20]; P=8192 projected Uniform(l-u,u-l) starts, T=1000 Adam "
+            "steps (lr 0.003, lambda1 0.85, lambda2 1), collection every step; Algorithm 1 from xbar")
+CPU_SAMPLE_P = 48        # starts of the bounded CPU sample (T = 1000 as in the workload)
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["bf16", "bf16x1", "fp32"], default="bf16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
+    ap.add_argument("--cpu-sample", type=int, nargs=2, metavar=("P", "T"), help=argparse.SUPPRESS)
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_over_ranks(units, ms, world):
+    """Sum of units over ranks and max of device time over ranks (the
+    whole-job throughput of weakly scaled replicas)."""
+    if world == 1:
+        return float(units), float(ms)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.th.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- peaks
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def cpu_sample(P, T):
+    """Oracle extraction + minimality filter on P starts of the workload, in
+    this (single-threaded) process; prints a JSON line."""
+    import numpy as np
+    from oracle import mape_oracle as O
+    from paper_2412_13576_gb300 import instances as I
+    inst = I.medium_sparse()
+    G0 = I.uniform_samples(inst, P, seed=2002).G0
+    t0 = time.perf_counter()
+    Z0 = O.project_to_coordinates(inst.B, G0)
+    res = O.parallel_extraction(inst.A, inst.B, inst.l, inst.u, Z0, T=T)
+    dt = time.perf_counter() - t0
+    K = int(res["directions"].shape[0])
+    print(json.dumps({"directions": K, "unique": int(res["unique"].shape[0]), "seconds": dt,
+                      "value": K / dt, "P": P, "T": T, "threads": 1}))
+
+
+def run_cpu_sample(P, T, timeout=600):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(P), str(T)],
+                         capture_output=True, text=True, env=env, timeout=timeout)
+    if out.returncode != 0:
+        raise RuntimeError("CPU sample failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_obj(r):
+    return {"value": r["value"], "unit": UNIT, "cores": r["threads"], "kind": "oracle",
+            "sample": (f"oracle (numpy fp64/int64, 1 thread) on {r['P']} of the {P_FULL} starts, all {r['T']} "
+                       f"steps of Algorithm 2 + dedup + minimality filter: {r['directions']} directions in "
+                       f"{r['seconds']:.1f} s (augmentation excluded: it adds no directions)")}
+
+
+# ---------------------------------------------------------------- our arm
+
+PREC = {"bf16": 1, "bf16x1": 2, "fp32": 0}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2412_13576_gb300 import instances as I
+    from paper_2412_13576_gb300 import mape
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    L = mape.lib(build_if_missing=True)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    inst = I.medium_sparse()
+    starts = I.uniform_samples(inst, P_FULL, seed=2002 + rank)
+    G0 = torch.from_numpy(starts.G0).to(dev)
+    x0 = torch.from_numpy(inst.xbar[None, :].astype(np.int32)).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    cfg = mape.default_config(T=T_FULL, precision=PREC[args.precision])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def one_step(h):
+        h.extract_directions(P_FULL, G0=G0)
+        h.wait(600)
+        h.augment(x0)
+        h.wait(600)
+        return h.poll()
+
+    h = mape.Instance.from_generated(inst, cfg, stream=stream)
+    for _ in range(args.warmup):
+        one_step(h)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    total_ms, directions, statuses = 0.0, 0, []
+    launches0 = L.mape_launch_count()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = one_step(h)
+            e1.record(stream)
+            stream.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            directions += st["directions"]
+            statuses.append(st)
+    launches = L.mape_launch_count() - launches0
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    h.close()
+    units_all, ms_max = reduce_over_ranks(directions, total_ms, world)
+    value = units_all / (ms_max / 1e3)
+
+    # e2e: the public handle API with host buffers, every copy inside the region
+    G0_host = starts.G0
+    x0_host = inst.xbar[None, :].astype(np.int32)
+    e2e_times, e2e_units = [], 0
+    h2d = (inst.A.nbytes + inst.b.nbytes + inst.l.nbytes + inst.u.nbytes + inst.B.nbytes + inst.Q.nbytes
+           + inst.c.nbytes + G0_host.nbytes + x0_host.nbytes)
+    d2h = 0
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with mape.Instance.from_generated(inst, cfg, stream=stream) as he:
+            he.extract_directions(P_FULL, G0=G0_host)
+            he.wait(600)
+            he.augment(x0_host)
+            he.wait(600)
+            D = he.directions()
+            x, fx = he.solution()
+        e2e_times.append(time.perf_counter() - t0)
+        e2e_units += D.shape[0]
+        d2h = D.nbytes + x.nbytes + 8
+    e2e_value = e2e_units / sum(e2e_times)
+
+    result = None
+    if rank == 0:
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"bf16": "bf16", "bf16x1": "bf16", "fp32": "f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "P": P_FULL, "T": T_FULL, "n": N_FULL, "m": M_FULL,
+                       "precision": args.precision, "l2": "flushed (256 MiB write) before each timed step",
+                       "replicas_per_rank": 1},
+            "directions_per_step": directions / args.steps,
+            "stages_ms": {k: statistics.median(s[k] for s in statuses)
+                          for k in ("extract_ms", "filter_ms", "augment_ms", "first_improve_ms")},
+            "best_f": statuses[-1]["best_f"],
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "steps": len(e2e_times)},
+        }
+        result["roofline"] = roofline(mape, inst, starts, stream, args)
+        if not args.no_plain and args.precision != "fp32":
+            result["vs_plain_fp32"] = plain_fp32(mape, inst, G0, x0, stream)
+        if not args.no_cpu_baseline and world == 1:
+            result["cpu_baseline"] = cpu_baseline_obj(run_cpu_sample(CPU_SAMPLE_P, T_FULL))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return result
+
+
+def roofline(mape, inst, starts, stream, args, reps=3):
+    """Times the dominant kernel (the fused extraction launch, T = 1000 steps)
+    alone with CUDA events on its stream; algorithmic work = the dense MMA
+    flops per launch."""
+    import numpy as np
+    import torch
+    peaks, src = measured_peaks()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    B = torch.from_numpy(inst.B).to(dev)
+    span = torch.from_numpy((inst.u - inst.l).astype(np.int32)).to(dev)
+    prec = PREC[args.precision]
+    cfg = mape.default_config(T=T_FULL, precision=prec)
+    with torch.cuda.stream(stream):
+        Z0 = mape.project_starts(B, torch.from_numpy(starts.G0).to(dev), stream=stream)
+    ldc = mape.round16(inst.n)
+    cand = torch.empty((P_FULL * 64, ldc), dtype=torch.int8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    flags = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(mape.lib().mape_extract_workspace_bytes(inst.n, inst.d, P_FULL, prec), dtype=torch.uint8,
+                     device=dev)
+    times = []
+    for i in range(reps + 1):
+        Z = Z0.clone()
+        Mm = torch.zeros_like(Z)
+        V = torch.zeros_like(Z)
+        cnt.zero_()
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mape.extract(B, span, Z, Mm, V, t0=0, T=T_FULL, cfg=cfg, cand=cand, cand_count=cnt, flags=flags, ldc=ldc,
+                     workspace=ws, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        if i > 0:
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    n, d = inst.n, inst.d
+    if prec == 0:
+        return {"kernel": "extract_fp32 (3 kernels per step)", "bound": "alu", "ms": ms}
+    nterms = 2 if prec == 1 else 1
+    flops = 2.0 * n * d * P_FULL * T_FULL * (nterms + 2)   # forward terms, B round(z), gradient
+    achieved = flops / (ms / 1e3) / 1e12
+    peak = peaks["bf16_tflops"]
+    return {"bound": "tensor", "kernel": "extract_tc_kernel", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "ms_per_launch": ms,
+            "flops_per_launch": flops, "peak_source": f"{src} bf16 burst (MEASURED_PEAKS.json)",
+            "note": "dense MMA flops of one launch (T=1000 steps, P=8192): 2*n*d*P*T*(2 forward terms + "
+                    "B round(z) + gradient); the launch includes its 6 layout transposes (<0.1%)"}
+
+
+def plain_fp32(mape, inst, G0, x0, stream):
+    """One step of the plain FP32 single-instance path (unfused CUDA-core
+    kernels, one launch per stage and Adam step) for comparison."""
+    import torch
+    cfg = mape.default_config(T=T_FULL, precision=0)
+    with mape.Instance.from_generated(inst, cfg, stream=stream) as h:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.extract_directions(P_FULL, G0=G0)
+        h.wait(900)
+        h.augment(x0)
+        h.wait(900)
+        e1.record(stream)
+        stream.synchronize()
+        st = h.poll()
+    ms = e0.elapsed_time(e1)
+    return {"value": st["directions"] / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "best_f": st["best_f"],
+            "directions": st["directions"]}
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    total_s, total_units = 0.0, 0
+    r = None
+    for _ in range(args.warmup):
+        run_cpu_sample(CPU_SAMPLE_P, T_FULL)
+    for _ in range(args.steps):
+        r = run_cpu_sample(CPU_SAMPLE_P, T_FULL)
+        total_s += r["seconds"]
+        total_units += r["directions"]
+    value = total_units / total_s
+    cb = cpu_baseline_obj(r)
+    cb["value"] = value
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+int64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "P": P_FULL, "T": T_FULL, "n": N_FULL, "m": M_FULL,
+                       "sample_starts": CPU_SAMPLE_P},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.cpu_sample:
+        cpu_sample(*args.cpu_sample)
+        return 0
+    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -322,6 +322,10 @@ const char* mape_version(void);
 /* Text of the last CUDA runtime error recorded by any call (or ""). */
 const char* mape_last_cuda_error(void);
 
+/* Number of CUDA kernels this library has launched in this process (all
+ * threads, all handles); the difference across a region counts its launches. */
+unsigned long long mape_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -285,7 +285,7 @@ extern "C" int mape_direction_coeffs(const int32_t* q_row, const int32_t* q_col,
       (K > 0 && (!G || !a || !q4)))
     return MAPE_ERR_INVALID_ARG;
   if (K == 0) return MAPE_OK;
-  coeffs_kernel<<<(unsigned)ceil_div(K, 128), 128, 0, as_stream(stream)>>>(q_row, q_col, q_val, nnz, w, n, G, K,
+  mape_detail::launch(coeffs_kernel, (unsigned)ceil_div(K, 128), 128, 0, as_stream(stream), q_row, q_col, q_val, nnz, w, n, G, K,
                                                                          ldg, a, q4);
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
@@ -340,7 +340,7 @@ extern "C" int mape_augment_run(const mape_augment_args* A, int64_t* iters_out, 
   MAPE_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
   unsigned int h_active = (unsigned)S;
   MAPE_CUDA_TRY(cudaMemcpyAsync(n_active, &h_active, sizeof(unsigned int), cudaMemcpyHostToDevice, st));
-  init_kernel<<<S, 256, 0, st>>>(A->q_row, A->q_col, A->q_val, A->nnz, A->c, A->w, A->l, A->u, A->X, n, R,
+  mape_detail::launch(init_kernel, S, 256, 0, st, A->q_row, A->q_col, A->q_val, A->nnz, A->c, A->w, A->l, A->u, A->X, n, R,
                                  A->fval, active, bad);
   MAPE_LAUNCH_CHECK();
   int32_t h_bad = 0;
@@ -360,9 +360,9 @@ extern "C" int mape_augment_run(const mape_augment_args* A, int64_t* iters_out, 
   while (done_iters < A->max_iters) {
     int64_t c = std::min<int64_t>(chunk, A->max_iters - done_iters);
     for (int64_t q = 0; q < c; ++q) {
-      score_kernel<<<dim3((unsigned)nb, (unsigned)S), kScoreThreads, smem, st>>>(
+      mape_detail::launch(score_kernel, dim3((unsigned)nb, (unsigned)S), kScoreThreads, smem, st, 
           A->G, K, A->ldg, n, A->a, A->q4, A->w, A->l, A->u, A->X, R, active, partial, nb);
-      apply_kernel<<<S, 256, 0, st>>>(A->G, A->ldg, n, A->q_row, A->q_col, A->q_val, A->nnz, A->X, R, A->fval,
+      mape_detail::launch(apply_kernel, S, 256, 0, st, A->G, A->ldg, n, A->q_row, A->q_col, A->q_val, A->nnz, A->X, R, A->fval,
                                       active, partial, nb, A->moves, nmoves, A->moves_cap, iters, n_active);
     }
     MAPE_LAUNCH_CHECK();

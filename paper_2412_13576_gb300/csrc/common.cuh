@@ -60,3 +60,14 @@ struct Sizer {
 // Device-side integer helpers ------------------------------------------------
 
 __device__ __forceinline__ int mape_sign_f(float y) { return (y > 0.f) - (y < 0.f); }
+
+namespace mape_detail {
+// Every kernel of the library is launched through launch(), which counts the
+// launches (mape_launch_count).
+void note_launch();
+template <typename... KArgs, typename... Args>
+inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  kernel<<<grid, block, smem, st>>>(args...);
+  note_launch();
+}
+}  // namespace mape_detail

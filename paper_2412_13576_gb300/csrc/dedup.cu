@@ -138,10 +138,10 @@ namespace mape_detail {
 // Sorts rows[idx[0..K)] lexicographically in place of idx (npad >= K, power of 2,
 // idx[K..npad) set to the sentinel by this call).
 int sort_row_indices(const int8_t* rows, int ldc, uint32_t* idx, int64_t K, int64_t npad, cudaStream_t st) {
-  if (npad > K) pad_idx_kernel<<<(unsigned)ceil_div(npad - K, 256), 256, 0, st>>>(idx, K, npad);
+  if (npad > K) mape_detail::launch(pad_idx_kernel, (unsigned)ceil_div(npad - K, 256), 256, 0, st, idx, K, npad);
   for (int64_t k = 2; k <= npad; k <<= 1)
     for (int64_t j = k >> 1; j > 0; j >>= 1)
-      bitonic_step_kernel<<<(unsigned)ceil_div(npad, 256), 256, 0, st>>>(rows, ldc, idx, npad, j, k);
+      mape_detail::launch(bitonic_step_kernel, (unsigned)ceil_div(npad, 256), 256, 0, st, rows, ldc, idx, npad, j, k);
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
 }
@@ -184,9 +184,9 @@ extern "C" int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t 
   unsigned g = (unsigned)ceil_div(count, 256);
   MAPE_CUDA_TRY(cudaMemsetAsync(table, 0xff, slots * sizeof(uint32_t), st));
   MAPE_CUDA_TRY(cudaMemsetAsync(dK, 0, sizeof(unsigned long long), st));
-  hash_rows_kernel<<<g, 256, 0, st>>>(cand, count, ldc, h);
-  insert_kernel<<<g, 256, 0, st>>>(cand, h, count, ldc, table, slots - 1, is_rep);
-  compact_reps_kernel<<<g, 256, 0, st>>>(is_rep, count, idx, dK);
+  mape_detail::launch(hash_rows_kernel, g, 256, 0, st, cand, count, ldc, h);
+  mape_detail::launch(insert_kernel, g, 256, 0, st, cand, h, count, ldc, table, slots - 1, is_rep);
+  mape_detail::launch(compact_reps_kernel, g, 256, 0, st, is_rep, count, idx, dK);
   MAPE_LAUNCH_CHECK();
   unsigned long long K = 0;
   MAPE_CUDA_TRY(cudaMemcpyAsync(&K, dK, sizeof(K), cudaMemcpyDeviceToHost, st));
@@ -197,7 +197,7 @@ extern "C" int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t 
   int rc = sort_row_indices(cand, ldc, idx, (int64_t)K, (int64_t)next_pow2(K), st);
   if (rc != MAPE_OK) return rc;
   int64_t chunks = (int64_t)K * (ldc / 16);
-  gather_rows_kernel<<<(unsigned)ceil_div(chunks, 256), 256, 0, st>>>(cand, ldc, idx, (int64_t)K, uniq);
+  mape_detail::launch(gather_rows_kernel, (unsigned)ceil_div(chunks, 256), 256, 0, st, cand, ldc, idx, (int64_t)K, uniq);
   MAPE_LAUNCH_CHECK();
   MAPE_CUDA_TRY(cudaStreamSynchronize(st));
   return MAPE_OK;

@@ -5,12 +5,16 @@
 
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 namespace mape_detail {
 
 static std::mutex g_err_mu;
 static char g_last_err[512] = "";
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void record_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
   std::lock_guard<std::mutex> lk(g_err_mu);
@@ -21,6 +25,8 @@ void record_cuda_error(cudaError_t e, const char* what, const char* file, int li
 }  // namespace mape_detail
 
 extern "C" const char* mape_last_cuda_error(void) { return mape_detail::g_last_err; }
+
+extern "C" unsigned long long mape_launch_count(void) { return mape_detail::g_launches.load(); }
 
 extern "C" const char* mape_version(void) { return "mape-gb300 0.1 (sm_103a)"; }
 

@@ -306,12 +306,12 @@ int extract_fp32(const mape_extract_args* a, cudaStream_t st) {
   std::vector<float2> bc;
   adam_bias_table(a, bc);
 
-  to_float_kernel<<<(unsigned)ceil_div((int64_t)n * d, 256), 256, 0, st>>>(a->B, Bf, (int64_t)n * d);
+  mape_detail::launch(to_float_kernel, (unsigned)ceil_div((int64_t)n * d, 256), 256, 0, st, a->B, Bf, (int64_t)n * d);
   dim3 tb(32, 8);
-  transpose_kernel<<<dim3((unsigned)ceil_div(d, 32), (unsigned)ceil_div(P, 32)), tb, 0, st>>>(a->Z, Zt, P, d);
-  transpose_kernel<<<dim3((unsigned)ceil_div(d, 32), (unsigned)ceil_div(P, 32)), tb, 0, st>>>(a->M, Mt, P, d);
-  transpose_kernel<<<dim3((unsigned)ceil_div(d, 32), (unsigned)ceil_div(P, 32)), tb, 0, st>>>(a->V, Vt, P, d);
-  fill_u8_kernel<<<(unsigned)ceil_div(P, 256), 256, 0, st>>>(changed, 1, P);
+  mape_detail::launch(transpose_kernel, dim3((unsigned)ceil_div(d, 32), (unsigned)ceil_div(P, 32)), tb, 0, st, a->Z, Zt, P, d);
+  mape_detail::launch(transpose_kernel, dim3((unsigned)ceil_div(d, 32), (unsigned)ceil_div(P, 32)), tb, 0, st, a->M, Mt, P, d);
+  mape_detail::launch(transpose_kernel, dim3((unsigned)ceil_div(d, 32), (unsigned)ceil_div(P, 32)), tb, 0, st, a->V, Vt, P, d);
+  mape_detail::launch(fill_u8_kernel, (unsigned)ceil_div(P, 256), 256, 0, st, changed, 1, P);
   MAPE_LAUNCH_CHECK();
 
   dim3 fgrid((unsigned)ceil_div(P, kThreads), (unsigned)nblk);
@@ -321,19 +321,19 @@ int extract_fp32(const mape_extract_args* a, cudaStream_t st) {
     const bool first = (s == 0);
     StepParams sp{a->lambda1, a->lambda2, a->lr, (float)a->beta1, (float)a->beta2, (float)(1.0 - a->beta1),
                   (float)(1.0 - a->beta2), a->eps, bc[s].x, bc[s].y};
-    forward_sign_kernel<<<fgrid, kThreads, 0, st>>>(Bf, Zt, S, first && a->dbg_phi ? l1p : nullptr, n, d, P);
-    backward_adam_kernel<<<bgrid, kThreads, 0, st>>>(Bf, S, Zt, Mt, Vt, changed, sp, n, d, P, l1p, nblk,
+    mape_detail::launch(forward_sign_kernel, fgrid, kThreads, 0, st, Bf, Zt, S, first && a->dbg_phi ? l1p : nullptr, n, d, P);
+    mape_detail::launch(backward_adam_kernel, bgrid, kThreads, 0, st, Bf, S, Zt, Mt, Vt, changed, sp, n, d, P, l1p, nblk,
                                                      first ? a->dbg_phi : nullptr,
                                                      first ? a->dbg_grad : nullptr);
     int t = a->t0 + s + 1;
     if (t % a->period == 0)
-      collect_kernel<<<cgrid, 256, 0, st>>>(a->B, Zt, a->span, changed, n, d, P, a->cand, a->ldc,
+      mape_detail::launch(collect_kernel, cgrid, 256, 0, st, a->B, Zt, a->span, changed, n, d, P, a->cand, a->ldc,
                                             a->cand_cap, a->cand_count, a->flags);
     MAPE_LAUNCH_CHECK();
   }
-  transpose_kernel<<<dim3((unsigned)ceil_div(P, 32), (unsigned)ceil_div(d, 32)), tb, 0, st>>>(Zt, a->Z, d, P);
-  transpose_kernel<<<dim3((unsigned)ceil_div(P, 32), (unsigned)ceil_div(d, 32)), tb, 0, st>>>(Mt, a->M, d, P);
-  transpose_kernel<<<dim3((unsigned)ceil_div(P, 32), (unsigned)ceil_div(d, 32)), tb, 0, st>>>(Vt, a->V, d, P);
+  mape_detail::launch(transpose_kernel, dim3((unsigned)ceil_div(P, 32), (unsigned)ceil_div(d, 32)), tb, 0, st, Zt, a->Z, d, P);
+  mape_detail::launch(transpose_kernel, dim3((unsigned)ceil_div(P, 32), (unsigned)ceil_div(d, 32)), tb, 0, st, Mt, a->M, d, P);
+  mape_detail::launch(transpose_kernel, dim3((unsigned)ceil_div(P, 32), (unsigned)ceil_div(d, 32)), tb, 0, st, Vt, a->V, d, P);
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
 }
@@ -345,7 +345,7 @@ extern "C" int mape_phi_grad(const int32_t* B, int32_t n, int32_t d, const float
   if (n <= 0 || d <= 0 || P < 0 || !B || (P > 0 && (!Z || !phi || !grad))) return MAPE_ERR_INVALID_ARG;
   if (n > 48 * 1024) return MAPE_ERR_SHAPE;
   if (P == 0) return MAPE_OK;
-  phi_grad_kernel<<<P, 128, (size_t)n, mape_detail::as_stream(stream)>>>(B, Z, n, d, lambda1, lambda2, phi, grad);
+  mape_detail::launch(phi_grad_kernel, P, 128, (size_t)n, mape_detail::as_stream(stream), B, Z, n, d, lambda1, lambda2, phi, grad);
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
 }

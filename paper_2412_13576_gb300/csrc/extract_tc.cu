@@ -618,9 +618,9 @@ int extract_tc(const mape_extract_args* a, cudaStream_t st) {
   MAPE_CUDA_TRY(cudaMemcpyAsync(bias, bc.data(), sizeof(float2) * bc.size(), cudaMemcpyHostToDevice, st));
   dim3 tb(32, 8);
   dim3 gin((unsigned)ceil_div(d, 32), (unsigned)ceil_div(P, 32));
-  transpose_tc_kernel<<<gin, tb, 0, st>>>(a->Z, Zt, P, d);
-  transpose_tc_kernel<<<gin, tb, 0, st>>>(a->M, Mt, P, d);
-  transpose_tc_kernel<<<gin, tb, 0, st>>>(a->V, Vt, P, d);
+  mape_detail::launch(transpose_tc_kernel, gin, tb, 0, st, a->Z, Zt, P, d);
+  mape_detail::launch(transpose_tc_kernel, gin, tb, 0, st, a->M, Mt, P, d);
+  mape_detail::launch(transpose_tc_kernel, gin, tb, 0, st, a->V, Vt, P, d);
   TcParams p{};
   p.B = a->B; p.span = a->span; p.Zt = Zt; p.Mt = Mt; p.Vt = Vt; p.bias = bias;
   p.n = n; p.d = d; p.P = P; p.n_pad = pad16(n); p.d_pad = pad16(d);
@@ -638,12 +638,12 @@ int extract_tc(const mape_extract_args* a, cudaStream_t st) {
   if (smem < 116 * 1024) smem = 116 * 1024;
   MAPE_CUDA_TRY(cudaFuncSetAttribute(extract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   unsigned grid = (unsigned)ceil_div(P, kTileM);
-  extract_tc_kernel<<<grid, kThreads, smem, st>>>(p);
+  mape_detail::launch(extract_tc_kernel, grid, kThreads, smem, st, p);
   MAPE_LAUNCH_CHECK();
   dim3 gout((unsigned)ceil_div(P, 32), (unsigned)ceil_div(d, 32));
-  transpose_tc_kernel<<<gout, tb, 0, st>>>(Zt, a->Z, d, P);
-  transpose_tc_kernel<<<gout, tb, 0, st>>>(Mt, a->M, d, P);
-  transpose_tc_kernel<<<gout, tb, 0, st>>>(Vt, a->V, d, P);
+  mape_detail::launch(transpose_tc_kernel, gout, tb, 0, st, Zt, a->Z, d, P);
+  mape_detail::launch(transpose_tc_kernel, gout, tb, 0, st, Mt, a->M, d, P);
+  mape_detail::launch(transpose_tc_kernel, gout, tb, 0, st, Vt, a->V, d, P);
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
 }

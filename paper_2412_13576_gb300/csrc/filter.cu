@@ -170,7 +170,7 @@ extern "C" int mape_kernel_test(const int32_t* A, int32_t m, int32_t n, const in
   if (!cv.ok) return MAPE_ERR_CAPACITY;
   cudaStream_t st = as_stream(stream);
   MAPE_CUDA_TRY(cudaMemsetAsync(d_fail, 0, sizeof(unsigned long long), st));
-  kernel_test_kernel<<<(unsigned)ceil_div(K, 128), 128, 0, st>>>(A, m, n, G, K, ldg, ok, d_fail);
+  mape_detail::launch(kernel_test_kernel, (unsigned)ceil_div(K, 128), 128, 0, st, A, m, n, G, K, ldg, ok, d_fail);
   MAPE_LAUNCH_CHECK();
   unsigned long long f = 0;
   MAPE_CUDA_TRY(cudaMemcpyAsync(&f, d_fail, sizeof(f), cudaMemcpyDeviceToHost, st));
@@ -206,9 +206,9 @@ extern "C" int mape_minimal_filter(const int8_t* G, int64_t K, int32_t n, int32_
   if (!cv.ok) return MAPE_ERR_CAPACITY;
   cudaStream_t st = as_stream(stream);
   unsigned g = (unsigned)ceil_div(K, kTile);
-  prep_kernel<<<g, kTile, 0, st>>>(G, K, n, ldg, W, valid, l1, masks);
-  dominance_kernel<<<g, kTile, 0, st>>>(G, K, n, ldg, W, l1, masks, keep);
-  compact_kept_kernel<<<1, 1024, 0, st>>>(G, K, ldg, keep, out, dK);
+  mape_detail::launch(prep_kernel, g, kTile, 0, st, G, K, n, ldg, W, valid, l1, masks);
+  mape_detail::launch(dominance_kernel, g, kTile, 0, st, G, K, n, ldg, W, l1, masks, keep);
+  mape_detail::launch(compact_kept_kernel, 1, 1024, 0, st, G, K, ldg, keep, out, dK);
   MAPE_LAUNCH_CHECK();
   unsigned long long kk = 0;
   MAPE_CUDA_TRY(cudaMemcpyAsync(&kk, dK, sizeof(kk), cudaMemcpyDeviceToHost, st));

@@ -370,7 +370,7 @@ extern "C" int mape_create_instance(const int32_t* A, const int64_t* b, const in
       (rc = upload(h, h->du, u, (size_t)n * 4)) || (rc = upload(h, h->dspan, span.data(), (size_t)n * 4)))
     return fail(rc);
   if (cudaMemsetAsync(dbad, 0, 4, h->stream) != cudaSuccess) return fail(MAPE_ERR_CUDA);
-  basis_check_kernel<<<dim3((unsigned)mape_detail::ceil_div(d, 128), (unsigned)m), 128, 0, h->stream>>>(
+  mape_detail::launch(basis_check_kernel, dim3((unsigned)mape_detail::ceil_div(d, 128), (unsigned)m), 128, 0, h->stream, 
       h->dA, h->dB, m, n, d, dbad);
   int32_t bad = 0;
   if (cudaMemcpyAsync(&bad, dbad, 4, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
@@ -472,7 +472,7 @@ extern "C" int mape_augment(mape_handle h, const int32_t* X0, int32_t S, const m
   int rc = upload(h, h->dX, X0, sizeof(int32_t) * (size_t)S * n);
   if (rc) return rc;
   MAPE_CUDA_TRY(cudaMemsetAsync(dbad, 0, 4, h->stream));
-  feasible_check_kernel<<<S, 128, 0, h->stream>>>(h->dA, h->db, h->dX, h->m, n, S, dbad);
+  mape_detail::launch(feasible_check_kernel, S, 128, 0, h->stream, h->dA, h->db, h->dX, h->m, n, S, dbad);
   MAPE_LAUNCH_CHECK();
   int32_t bad = 0;
   MAPE_CUDA_TRY(cudaMemcpyAsync(&bad, dbad, 4, cudaMemcpyDeviceToHost, h->stream));
@@ -526,7 +526,7 @@ extern "C" int mape_get_directions(mape_handle h, int32_t* G, int64_t cap, int64
   int32_t* tmp = static_cast<int32_t*>(h->alloc(sizeof(int32_t) * (size_t)h->K * h->n));
   if (!tmp) return MAPE_ERR_OOM;
   int64_t tot = h->K * h->n;
-  i8_to_i32_kernel<<<(unsigned)ceil_div(tot, 256), 256, 0, h->stream>>>(h->dirs, h->K, h->n, h->ldg, tmp);
+  mape_detail::launch(i8_to_i32_kernel, (unsigned)ceil_div(tot, 256), 256, 0, h->stream, h->dirs, h->K, h->n, h->ldg, tmp);
   cudaError_t e = cudaMemcpyAsync(G, tmp, sizeof(int32_t) * (size_t)tot, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   h->release(tmp, sizeof(int32_t) * (size_t)tot);

@@ -92,9 +92,9 @@ extern "C" int mape_project_starts(const int32_t* B, int32_t n, int32_t d, const
   if (!cv.ok) return MAPE_ERR_CAPACITY;
   cudaStream_t st = as_stream(stream);
   MAPE_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
-  gram_kernel<<<dim3((unsigned)ceil_div(d, 128), (unsigned)d), 128, 0, st>>>(B, n, d, H);
-  cholesky_kernel<<<1, 1024, 0, st>>>(H, d, status);
-  if (P > 0) solve_kernel<<<(unsigned)ceil_div(P, 128), 128, 0, st>>>(B, H, G0, n, d, P, Z0);
+  mape_detail::launch(gram_kernel, dim3((unsigned)ceil_div(d, 128), (unsigned)d), 128, 0, st, B, n, d, H);
+  mape_detail::launch(cholesky_kernel, 1, 1024, 0, st, H, d, status);
+  if (P > 0) mape_detail::launch(solve_kernel, (unsigned)ceil_div(P, 128), 128, 0, st, B, H, G0, n, d, P, Z0);
   MAPE_LAUNCH_CHECK();
   int32_t h_status = 0;
   MAPE_CUDA_TRY(cudaMemcpyAsync(&h_status, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));

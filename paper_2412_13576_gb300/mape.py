@@ -88,6 +88,7 @@ _SIGS = {
     "mape_default_config": (None, [C.POINTER(Config)]),
     "mape_version": (C.c_char_p, []),
     "mape_last_cuda_error": (C.c_char_p, []),
+    "mape_launch_count": (C.c_ulonglong, []),
     "mape_project_workspace_bytes": (C.c_size_t, [I32, I32]),
     "mape_project_starts": (C.c_int, [P_, I32, I32, P_, I32, P_, P_, C.c_size_t, P_]),
     "mape_phi_grad": (C.c_int, [P_, I32, I32, P_, I32, F32, F32, P_, P_, P_]),
