@@ -17,7 +17,8 @@
 //        B is read through an MN-major descriptor of the same shared tile
 //        (a transposed K-major copy is kept instead when it fits)
 //   grad = G + lambda1 (ceil z + floor z - 2 z) + inverse-norm term; Adam on
-//   the FP32 master z, m, v (coordinate-major in global memory, L2 resident);
+//   the FP32 master z, m, v (blocked [tile][d/4][128][4] in global memory, L2
+//   resident, one 16-byte access per 4 coordinates);
 //   the new bf16(z), bf16(round z) operands are written for the next step.
 // The candidate of step t (D2 of step t+1) is tested (C4, nonzero), signed
 // canonically and appended while the G MMA runs.
@@ -34,6 +35,7 @@
 #include "extract_internal.cuh"
 
 #include <cuda_bf16.h>
+#include <cmath>
 #include <vector>
 
 namespace {
@@ -158,13 +160,19 @@ __device__ __forceinline__ void store_row16(uint8_t* tile, int r, int k0, int K,
   *reinterpret_cast<uint4*>(tile + op_off(r, k0 + 8, K)) = hi;
 }
 
+// same, from 8 words of two packed bf16 each (element 2i in the low half)
+__device__ __forceinline__ void store_row16w(uint8_t* tile, int r, int k0, int K, const uint32_t (&w)[8]) {
+  *reinterpret_cast<uint4*>(tile + op_off(r, k0, K)) = make_uint4(w[0], w[1], w[2], w[3]);
+  *reinterpret_cast<uint4*>(tile + op_off(r, k0 + 8, K)) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
 struct TcParams {
   const int32_t* B;
   const int32_t* span;
   float* Zt;
   float* Mt;
   float* Vt;
-  const float2* bias;  // (1 - beta1^t, 1 - beta2^t) per step of this call
+  const float2* bias;  // (lr / (1 - beta1^t), 1 / sqrt(1 - beta2^t)) per step of this call
   int n, d, P, n_pad, d_pad;
   int t0, T, period;
   float lambda1, lambda2, lr, eps, beta1, beta2, omb1, omb2;
@@ -277,15 +285,27 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
   bool bail = s_bad != 0;
   if (bail && tid == 0) atomicOr(p.flags, 8);
 
+  // FP32 master state of this thread's start: blocked [tile][d_pad/4][128][4],
+  // four consecutive coordinates per 16-byte access, coalesced across a warp
+  float4* const zb = reinterpret_cast<float4*>(p.Zt) + (size_t)blockIdx.x * (d_pad / 4) * kTileM + r;
+  float4* const mb = reinterpret_cast<float4*>(p.Mt) + (size_t)blockIdx.x * (d_pad / 4) * kTileM + r;
+  float4* const vb = reinterpret_cast<float4*>(p.Vt) + (size_t)blockIdx.x * (d_pad / 4) * kTileM + r;
+
   // ---- initial operand: bf16(z0) and the partial ||z0||_inf ----
   float zinf_part = 0.f;
   int kmax_part = kNoNz;
   for (int ch = split; ch < dch && !bail; ch += kSplits) {
     uint16_t h[16], hl[16];
+    float zc[16];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float4 q = zb[(ch * 4 + k) * kTileM];
+      zc[4 * k] = q.x; zc[4 * k + 1] = q.y; zc[4 * k + 2] = q.z; zc[4 * k + 3] = q.w;
+    }
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       int j = ch * 16 + c;
-      float z = (active && j < d) ? p.Zt[(int64_t)j * P + pg] : 0.f;
+      float z = zc[c];
       h[c] = bf16_bits(z);
       hl[c] = bf16_bits(z - bf16_value(h[c]));
       float a = fabsf(z);
@@ -466,7 +486,10 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
     }
     if (!wait_mma()) { bail = true; break; }
     // (4) Adam on the FP32 master state; next operands
-    const float2 bc = p.bias[s];
+    // Adam in the form z -= (lr / bc1) m / (sqrt(v) / sqrt(bc2) + eps), with
+    // lr / bc1 and 1 / sqrt(bc2) formed in double on the host
+    const float2 ad = p.bias[s];
+    const float step = ad.x, rsb2 = ad.y;
     float inv_term = 0.f;
     if (zinf < 1.f && zinf > 0.f) inv_term = -p.lambda2 / (zinf * zinf);  // times sign(z_kmax)
     float nzinf = 0.f, frac = 0.f;
@@ -474,41 +497,67 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
     bool changed = false, unexact = false;
     for (int ch = split; ch < dch; ch += kSplits) {
       uint32_t v[16];
-      tmem_ld16(tmem + lane_off + ch * 16, v);
-      tc_wait_ld();
-      uint16_t h1[16], hl[16], h2[16];
+      tmem_ld16(tmem + lane_off + ch * 16, v);  // completes under the global loads below
+      float zc[16], mc[16], vc[16], zo[16], mo[16], vo[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        int j = ch * 16 + c;
-        float zn = 0.f, rn = 0.f;
-        if (active && j < d) {
-          int64_t at = (int64_t)j * P + pg;
-          float z = p.Zt[at];
-          float grad = __uint_as_float(v[c]) + p.lambda1 * (ceilf(z) + floorf(z) - 2.f * z);
+      for (int k = 0; k < 4; ++k) {
+        const float4 qz = zb[(ch * 4 + k) * kTileM], qm = mb[(ch * 4 + k) * kTileM], qv = vb[(ch * 4 + k) * kTileM];
+        zc[4 * k] = qz.x; zc[4 * k + 1] = qz.y; zc[4 * k + 2] = qz.z; zc[4 * k + 3] = qz.w;
+        mc[4 * k] = qm.x; mc[4 * k + 1] = qm.y; mc[4 * k + 2] = qm.z; mc[4 * k + 3] = qm.w;
+        vc[4 * k] = qv.x; vc[4 * k + 1] = qv.y; vc[4 * k + 2] = qv.z; vc[4 * k + 3] = qv.w;
+      }
+      tc_wait_ld();
+      uint32_t w1[8], wl[8], w2[8];
+#pragma unroll
+      for (int c = 0; c < 16; c += 2) {
+        float zn[2], rn[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int cc = c + q, j = ch * 16 + cc;
+          const bool live = active && j < d;
+          const float z = zc[cc];
+          const float fl = floorf(z);
+          // ceil z + floor z = 2 floor z + [z not an integer]
+          float grad = __uint_as_float(v[cc]) + p.lambda1 * (2.f * fl + (z != fl ? 1.f : 0.f) - 2.f * z);
           if (j == kmax) grad += inv_term * (float)mape_sign_f(z);
-          if (dbg_step) {
-            frac += (z - floorf(z)) * (ceilf(z) - z);
+          if (dbg_step && live) {
+            frac += (z - fl) * (ceilf(z) - z);
             if (p.dbg_grad) p.dbg_grad[pg * d + j] = grad;
           }
-          float m = p.beta1 * p.Mt[at] + p.omb1 * grad;
-          float vv = p.beta2 * p.Vt[at] + p.omb2 * grad * grad;
-          zn = z - p.lr * (m / bc.x) / (sqrtf(vv / bc.y) + p.eps);
-          p.Mt[at] = m;
-          p.Vt[at] = vv;
-          p.Zt[at] = zn;
-          rn = rintf(zn);
-          changed |= rn != rintf(z);
-          unexact |= fabsf(rn) > 256.f;
-          float a = fabsf(zn);
-          if (nkmax == kNoNz || a > nzinf) { nzinf = a; nkmax = j; }
+          const float m = p.beta1 * mc[cc] + p.omb1 * grad;
+          const float vv = p.beta2 * vc[cc] + p.omb2 * grad * grad;
+          const float den = (vv > 0.f ? vv * rsqrtf(vv) : 0.f) * rsb2 + p.eps;
+          // padding coordinates (j >= d) have zero gradient and stay at 0
+          const float znew = z - step * __fdividef(m, den);
+          zo[cc] = znew;
+          mo[cc] = m;
+          vo[cc] = vv;
+          zn[q] = znew;
+          rn[q] = rintf(znew);
+          if (live) {
+            changed |= rn[q] != rintf(z);
+            unexact |= fabsf(rn[q]) > 256.f;
+            const float a = fabsf(znew);
+            if (nkmax == kNoNz || a > nzinf) { nzinf = a; nkmax = j; }
+          }
         }
-        h1[c] = bf16_bits(zn);
-        hl[c] = bf16_bits(zn - bf16_value(h1[c]));
-        h2[c] = bf16_bits(rn);
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(zn[0], zn[1]);
+        const float2 hf = __bfloat1622float2(hi);
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(zn[0] - hf.x, zn[1] - hf.y);
+        const __nv_bfloat162 rr = __floats2bfloat162_rn(rn[0], rn[1]);
+        w1[c >> 1] = *reinterpret_cast<const uint32_t*>(&hi);
+        wl[c >> 1] = *reinterpret_cast<const uint32_t*>(&lo);
+        w2[c >> 1] = *reinterpret_cast<const uint32_t*>(&rr);
       }
-      store_row16(A1, r, ch * 16, d_pad, h1);
-      if (p.nterms > 1) store_row16(A1lo, r, ch * 16, d_pad, hl);
-      store_row16(A2, r, ch * 16, d_pad, h2);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        zb[(ch * 4 + k) * kTileM] = make_float4(zo[4 * k], zo[4 * k + 1], zo[4 * k + 2], zo[4 * k + 3]);
+        mb[(ch * 4 + k) * kTileM] = make_float4(mo[4 * k], mo[4 * k + 1], mo[4 * k + 2], mo[4 * k + 3]);
+        vb[(ch * 4 + k) * kTileM] = make_float4(vo[4 * k], vo[4 * k + 1], vo[4 * k + 2], vo[4 * k + 3]);
+      }
+      store_row16w(A1, r, ch * 16, d_pad, w1);
+      if (p.nterms > 1) store_row16w(A1lo, r, ch * 16, d_pad, wl);
+      store_row16w(A2, r, ch * 16, d_pad, w2);
     }
     s_pz[split * kTileM + r] = nzinf;
     s_pk[split * kTileM + r] = nkmax;
@@ -554,18 +603,29 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
   }
 }
 
-__global__ void transpose_tc_kernel(const float* __restrict__ in, float* __restrict__ out, int rows, int cols) {
-  __shared__ float tile[32][33];
-  int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    int rr = r0 + k, c = c0 + threadIdx.x;
-    if (rr < rows && c < cols) tile[k][threadIdx.x] = in[(int64_t)rr * cols + c];
-  }
-  __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    int c = c0 + k, rr = r0 + threadIdx.x;
-    if (rr < rows && c < cols) out[(int64_t)c * rows + rr] = tile[threadIdx.x][k];
-  }
+// [P x d] row-major  <->  blocked [ceil(P/128)][d_pad/4][128][4] (zero padded)
+__global__ void pack_blocked_kernel(const float* __restrict__ in, float* __restrict__ out, int P, int d, int d_pad,
+                                    int64_t total) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int c = (int)(e & 3);
+  const int r = (int)((e >> 2) & (kTileM - 1));
+  const int64_t g = e / (4 * kTileM);
+  const int g4 = (int)(g % (d_pad / 4));
+  const int64_t tile = g / (d_pad / 4);
+  const int64_t row = tile * kTileM + r;
+  const int j = g4 * 4 + c;
+  out[e] = (row < P && j < d) ? in[row * d + j] : 0.f;
+}
+
+__global__ void unpack_blocked_kernel(const float* __restrict__ in, float* __restrict__ out, int P, int d, int d_pad) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)P * d) return;
+  const int64_t row = e / d;
+  const int j = (int)(e % d);
+  const int64_t tile = row / kTileM;
+  const int r = (int)(row % kTileM);
+  out[e] = in[((tile * (d_pad / 4) + j / 4) * kTileM + r) * 4 + (j & 3)];
 }
 
 int pad16(int x) { return (x + 15) / 16 * 16; }
@@ -599,7 +659,8 @@ bool extract_tc_supported(int32_t n, int32_t d, int32_t precision) {
 size_t extract_tc_workspace(int32_t n, int32_t d, int32_t P, int32_t precision) {
   if (!extract_tc_supported(n, d, precision)) return 0;
   Sizer s;
-  for (int k = 0; k < 3; ++k) s.take<float>((size_t)d * P);  // Zt, Mt, Vt (carved separately)
+  const size_t blocked = (size_t)ceil_div(P, kTileM) * kTileM * pad16(d);
+  for (int k = 0; k < 3; ++k) s.take<float>(blocked);  // z, m, v blocked (carved separately)
   s.take<float2>((size_t)1 << 20);  // bias-correction table, up to 2^20 steps per call
   return s.bytes();
 }
@@ -608,19 +669,25 @@ int extract_tc(const mape_extract_args* a, cudaStream_t st) {
   const int n = a->n, d = a->d, P = a->P;
   if (a->T > (1 << 20)) return MAPE_ERR_SHAPE;
   Carver cv(a->workspace, a->workspace_bytes);
-  float* Zt = cv.take<float>((size_t)d * P);
-  float* Mt = cv.take<float>((size_t)d * P);
-  float* Vt = cv.take<float>((size_t)d * P);
+  const int d_pad = pad16(d);
+  const int64_t blocked = ceil_div(P, kTileM) * kTileM * (int64_t)d_pad;
+  float* Zt = cv.take<float>((size_t)blocked);
+  float* Mt = cv.take<float>((size_t)blocked);
+  float* Vt = cv.take<float>((size_t)blocked);
   float2* bias = cv.take<float2>((size_t)1 << 20);
   if (!cv.ok) return MAPE_ERR_CAPACITY;
   std::vector<float2> bc;
   adam_bias_table(a, bc);
+  for (int s = 0; s < a->T; ++s) {
+    double t = (double)a->t0 + s + 1;
+    double bc1 = 1.0 - std::pow(a->beta1, t), bc2 = 1.0 - std::pow(a->beta2, t);
+    bc[s] = make_float2((float)((double)a->lr / bc1), (float)(1.0 / std::sqrt(bc2)));
+  }
   MAPE_CUDA_TRY(cudaMemcpyAsync(bias, bc.data(), sizeof(float2) * bc.size(), cudaMemcpyHostToDevice, st));
-  dim3 tb(32, 8);
-  dim3 gin((unsigned)ceil_div(d, 32), (unsigned)ceil_div(P, 32));
-  mape_detail::launch(transpose_tc_kernel, gin, tb, 0, st, a->Z, Zt, P, d);
-  mape_detail::launch(transpose_tc_kernel, gin, tb, 0, st, a->M, Mt, P, d);
-  mape_detail::launch(transpose_tc_kernel, gin, tb, 0, st, a->V, Vt, P, d);
+  const unsigned gpack = (unsigned)ceil_div(blocked, 256);
+  mape_detail::launch(pack_blocked_kernel, gpack, 256, 0, st, a->Z, Zt, P, d, d_pad, blocked);
+  mape_detail::launch(pack_blocked_kernel, gpack, 256, 0, st, a->M, Mt, P, d, d_pad, blocked);
+  mape_detail::launch(pack_blocked_kernel, gpack, 256, 0, st, a->V, Vt, P, d, d_pad, blocked);
   TcParams p{};
   p.B = a->B; p.span = a->span; p.Zt = Zt; p.Mt = Mt; p.Vt = Vt; p.bias = bias;
   p.n = n; p.d = d; p.P = P; p.n_pad = pad16(n); p.d_pad = pad16(d);
@@ -640,10 +707,10 @@ int extract_tc(const mape_extract_args* a, cudaStream_t st) {
   unsigned grid = (unsigned)ceil_div(P, kTileM);
   mape_detail::launch(extract_tc_kernel, grid, kThreads, smem, st, p);
   MAPE_LAUNCH_CHECK();
-  dim3 gout((unsigned)ceil_div(P, 32), (unsigned)ceil_div(d, 32));
-  mape_detail::launch(transpose_tc_kernel, gout, tb, 0, st, Zt, a->Z, d, P);
-  mape_detail::launch(transpose_tc_kernel, gout, tb, 0, st, Mt, a->M, d, P);
-  mape_detail::launch(transpose_tc_kernel, gout, tb, 0, st, Vt, a->V, d, P);
+  const unsigned gun = (unsigned)ceil_div((int64_t)P * d, 256);
+  mape_detail::launch(unpack_blocked_kernel, gun, 256, 0, st, Zt, a->Z, P, d, d_pad);
+  mape_detail::launch(unpack_blocked_kernel, gun, 256, 0, st, Mt, a->M, P, d, d_pad);
+  mape_detail::launch(unpack_blocked_kernel, gun, 256, 0, st, Vt, a->V, P, d, d_pad);
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
 }
