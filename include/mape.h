@@ -102,6 +102,18 @@ int mape_project_starts(const int32_t* B, int32_t n, int32_t d,
                         const float* G0, int32_t P, float* Z0,
                         void* workspace, size_t workspace_bytes, void* stream);
 
+/* The two halves of mape_project_starts, for callers that project many
+ * batches with the same B:
+ *   prepare: W = B (B^T B)^{-1}  (W [n x d] float32, per instance; Cholesky
+ *            in FP32; NUMERIC if B^T B is not positive definite).  Synchronous.
+ *   apply:   Z0 = G0 W, i.e. z0 = W^T g per start (a tiled FP32 GEMM).
+ *            Asynchronous. */
+size_t mape_project_prepare_workspace_bytes(int32_t n, int32_t d);
+int mape_project_prepare(const int32_t* B, int32_t n, int32_t d, float* W,
+                         void* workspace, size_t workspace_bytes, void* stream);
+int mape_project_apply(const float* W, int32_t n, int32_t d, const float* G0,
+                       int32_t P, float* Z0, void* stream);
+
 /* a3-a5 -- Eq. (3) and its gradient in FP32 for every start row z of Z:
  *   phi[p]      = ||B z||_1 + lambda1 sum_i (z_i - floor z_i)(ceil z_i - z_i)
  *                 + lambda2 max{1/||z||_inf - 1, 0}

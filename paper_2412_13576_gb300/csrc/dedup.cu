@@ -115,6 +115,35 @@ __global__ void bitonic_step_kernel(const int8_t* __restrict__ rows, int ldc, ui
   }
 }
 
+constexpr int kSeg = 2048;
+
+// Bitonic stages k = kfirst .. klast (doubling), distances j < seg, on the
+// segment of seg indices owned by this block (seg <= kSeg, a power of two).
+__global__ void bitonic_local_kernel(const int8_t* __restrict__ rows, int ldc, uint32_t* __restrict__ idx, int64_t seg,
+                                     int64_t kfirst, int64_t klast) {
+  __shared__ uint32_t s[kSeg];
+  const int64_t base = blockIdx.x * seg;
+  for (int t = threadIdx.x; t < seg; t += blockDim.x) s[t] = idx[base + t];
+  __syncthreads();
+  for (int64_t k = kfirst; k <= klast; k <<= 1) {
+    for (int64_t j = ((k >> 1) < (seg >> 1) ? (k >> 1) : (seg >> 1)); j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < seg / 2; t += blockDim.x) {
+        const int64_t i = (t / j) * 2 * j + (t % j);  // lower element of the pair
+        const int64_t l = i + j;
+        const bool ascending = ((base + i) & k) == 0;
+        const uint32_t a = s[i], b = s[l];
+        const int c = cmp_rows(rows, ldc, a, b);
+        if ((ascending && c > 0) || (!ascending && c < 0)) {
+          s[i] = b;
+          s[l] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < seg; t += blockDim.x) idx[base + t] = s[t];
+}
+
 __global__ void gather_rows_kernel(const int8_t* __restrict__ rows, int ldc, const uint32_t* __restrict__ idx,
                                    int64_t K, int8_t* __restrict__ out) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -137,11 +166,20 @@ namespace mape_detail {
 
 // Sorts rows[idx[0..K)] lexicographically in place of idx (npad >= K, power of 2,
 // idx[K..npad) set to the sentinel by this call).
+// The network is the plain bitonic one; all stages with distance j < seg run
+// inside one launch on shared-memory segments of seg = min(npad, 2048) indices
+// (the compare direction still comes from the global index).
 int sort_row_indices(const int8_t* rows, int ldc, uint32_t* idx, int64_t K, int64_t npad, cudaStream_t st) {
   if (npad > K) mape_detail::launch(pad_idx_kernel, (unsigned)ceil_div(npad - K, 256), 256, 0, st, idx, K, npad);
-  for (int64_t k = 2; k <= npad; k <<= 1)
-    for (int64_t j = k >> 1; j > 0; j >>= 1)
+  if (npad < 2) return MAPE_OK;
+  const int64_t seg = npad < kSeg ? npad : kSeg;
+  const unsigned nseg = (unsigned)(npad / seg);
+  mape_detail::launch(bitonic_local_kernel, nseg, kSeg / 2, 0, st, rows, ldc, idx, seg, (int64_t)2, seg);
+  for (int64_t k = 2 * seg; k <= npad; k <<= 1) {
+    for (int64_t j = k >> 1; j >= seg; j >>= 1)
       mape_detail::launch(bitonic_step_kernel, (unsigned)ceil_div(npad, 256), 256, 0, st, rows, ldc, idx, npad, j, k);
+    mape_detail::launch(bitonic_local_kernel, nseg, kSeg / 2, 0, st, rows, ldc, idx, seg, k, k);
+  }
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
 }

@@ -173,7 +173,8 @@ struct TcParams {
   float* Mt;
   float* Vt;
   const float2* bias;  // (lr / (1 - beta1^t), 1 / sqrt(1 - beta2^t)) per step of this call
-  int n, d, P, n_pad, d_pad;
+  int n, d, P, n_pad, d_pad;  // n_pad: rows of B in the MMA tile, padded to 16
+  int span_pad;               // entries of the span table, pad16(n)
   int t0, T, period;
   float lambda1, lambda2, lr, eps, beta1, beta2, omb1, omb2;
   int nterms;   // 1: hi only, 2: hi + lo
@@ -191,11 +192,17 @@ struct Smem {  // byte offsets into dynamic shared memory
   uint32_t bf, bb, opa, opa2, span, pz, pk, pl1, pfr, fl, fnz, slot, bar, tmem, total;
 };
 
+// per-start flag word bits
+constexpr uint32_t kChanged = 1;    // rounding changed since the last collection
+constexpr uint32_t kUnexact = 2;    // |round z| > 256 since the last collection
+constexpr uint32_t kOutOfBox = 4;   // the current candidate fails C4 (rows in the MMA tile)
+constexpr uint32_t kOutId = 8;      // ... fails C4 on the identity rows (identity-topped B)
+
 __host__ __device__ inline uint32_t al(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
 // Operand area: [hi | lo] of bf16(z) (nterms tiles of 128 x d_pad), later
 // overwritten by S (128 x n_pad); then bf16(round z) (128 x d_pad).
-__host__ __device__ inline Smem smem_layout(int n_pad, int d_pad, int nterms, int use_bb) {
+__host__ __device__ inline Smem smem_layout(int n_pad, int d_pad, int nterms, int use_bb, int span_pad) {
   Smem s{};
   uint32_t o = 0;
   s.bf = o;   o = al(o + (uint32_t)n_pad * d_pad * 2, 1024);
@@ -204,7 +211,7 @@ __host__ __device__ inline Smem smem_layout(int n_pad, int d_pad, int nterms, in
   uint32_t zs = (uint32_t)nterms * d_pad > (uint32_t)n_pad ? (uint32_t)nterms * d_pad : (uint32_t)n_pad;
   s.opa2 = o + (uint32_t)kTileM * zs * 2;
   o = al(s.opa2 + (uint32_t)kTileM * d_pad * 2, 128);
-  s.span = o; o = al(o + (uint32_t)n_pad * 4, 128);
+  s.span = o; o = al(o + (uint32_t)span_pad * 4, 128);
   s.pz = o;   o = al(o + kSplits * kTileM * 4, 128);
   s.pk = o;   o = al(o + kSplits * kTileM * 4, 128);
   s.pl1 = o;  o = al(o + kSplits * kTileM * 4, 128);
@@ -218,14 +225,14 @@ __host__ __device__ inline Smem smem_layout(int n_pad, int d_pad, int nterms, in
   return s;
 }
 
-// per-start flag word bits
-constexpr uint32_t kChanged = 1;    // rounding changed since the last collection
-constexpr uint32_t kUnexact = 2;    // |round z| > 256 since the last collection
-constexpr uint32_t kOutOfBox = 4;   // the current candidate fails C4
-
+// kId: B = [I_d ; B'] (the basis of A = [C | I_m] is [I ; -C]).  The MMA tile
+// then holds only B' (rows d .. n-1); the identity rows give (Bz)_j = z_j
+// exactly, so their sign, bound test and the first nonzero entry of
+// g = [round z ; B' round z] come from the FP32 master z in the Adam epilogue.
+template <bool kId>
 __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  const Smem L = smem_layout(p.n_pad, p.d_pad, p.nterms, p.use_bb);
+  const Smem L = smem_layout(p.n_pad, p.d_pad, p.nterms, p.use_bb, p.span_pad);
   uint8_t* Bf = smem + L.bf;
   uint8_t* Bb = smem + L.bb;
   uint8_t* A1 = smem + L.opa;                        // hi(z)
@@ -252,20 +259,20 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
   const bool active = pg < p.P;
   const int n = p.n, d = p.d, n_pad = p.n_pad, d_pad = p.d_pad;
   const int nch = n_pad / 16, dch = d_pad / 16;
-  const int64_t P = p.P;
+  const int r0 = kId ? d : 0;  // row of B held in row 0 of the MMA tile
 
   // ---- set-up: B in both operand layouts, span, flags ----
   if (tid == 0) s_bad = 0;
   __syncthreads();
   for (int e = tid; e < n_pad * d_pad; e += kThreads) {
     int i = e / d_pad, j = e % d_pad;
-    int v = (i < n && j < d) ? p.B[(int64_t)i * d + j] : 0;
+    int v = (r0 + i < n && j < d) ? p.B[(int64_t)(r0 + i) * d + j] : 0;
     if (v > 256 || v < -256) s_bad = 1;
     uint16_t h = bf16_bits((float)v);
     *reinterpret_cast<uint16_t*>(Bf + op_off(i, j, d_pad)) = h;  // N = n rows, K = d
     if (p.use_bb) *reinterpret_cast<uint16_t*>(Bb + op_off(j, i, n_pad)) = h;  // N = d rows, K = n
   }
-  for (int i = tid; i < n_pad; i += kThreads) s_span[i] = i < n ? p.span[i] : 0;
+  for (int i = tid; i < p.span_pad; i += kThreads) s_span[i] = i < n ? p.span[i] : 0;
   if (tid < kTileM) {
     s_fl[tid] = kChanged;  // the first collection of a call always counts
     s_fnz[tid] = kNoNz;
@@ -352,16 +359,16 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
       tc_wait_ld();
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
-        int i = ch * 16 + c;
+        const int i = r0 + ch * 16 + c;  // row of B
         int g = __float2int_rn(__uint_as_float(v[c]));
         if (i < n) {
           if (g > s_span[i] || -g > s_span[i]) out = true;
-          if (g != 0 && (i << 1) < first) first = (i << 1) | (g < 0 ? 1 : 0);
+          if (!kId && g != 0 && (i << 1) < first) first = (i << 1) | (g < 0 ? 1 : 0);
         }
       }
     }
     if (out) atomicOr(&s_fl[r], kOutOfBox);
-    if (first != kNoNz) atomicMin(&s_fnz[r], first);
+    if (!kId && first != kNoNz) atomicMin(&s_fnz[r], first);
   };
   // ... and appends it in canonical sign (needs a barrier between the two)
   auto decide_slot = [&]() {
@@ -369,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
     long long slot = -1;
     uint32_t f = s_fl[r];
     int fnz = s_fnz[r];
-    if (active && (f & kChanged) && !(f & kOutOfBox) && fnz != kNoNz) {
+    if (active && (f & kChanged) && !(f & (kOutOfBox | kOutId)) && fnz != kNoNz) {
       if (f & kUnexact) {
         atomicOr(p.flags, 2);
       } else {
@@ -386,25 +393,53 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
     long long slot = s_slot[r];
     int sgn = (s_fnz[r] & 1) ? -1 : 1;
     int8_t* row = slot >= 0 ? p.cand + slot * p.ldc : nullptr;
-    for (int ch = split; ch < nch; ch += kSplits) {
-      uint32_t v[16];
-      tmem_ld16(tmem + lane_off + kColD2 + ch * 16, v);
-      tc_wait_ld();
-      uint32_t w[4] = {0, 0, 0, 0};
+    if (kId) {
+      // identity rows: g_j = round z_j, held as BF16 in the round(z) operand tile
+      for (int ch = split; ch < dch && row; ch += kSplits) {
+        const uint4 lo = *reinterpret_cast<const uint4*>(A2 + op_off(r, ch * 16, d_pad));
+        const uint4 hi = *reinterpret_cast<const uint4*>(A2 + op_off(r, ch * 16 + 8, d_pad));
+        const uint32_t wv[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        int g = sgn * __float2int_rn(__uint_as_float(v[c]));
-        w[c >> 2] |= ((uint32_t)(g & 0xff)) << ((c & 3) * 8);
+        for (int c = 0; c < 16; ++c) {
+          const int j = ch * 16 + c;
+          const float zr = __uint_as_float((c & 1) ? (wv[c >> 1] & 0xffff0000u) : (wv[c >> 1] << 16));
+          if (j < d) row[j] = (int8_t)(sgn * __float2int_rn(zr));
+        }
       }
-      if (row) *reinterpret_cast<uint4*>(row + ch * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+      // rows of B' from D2 (warp-collective loads: every lane executes them)
+      for (int ch = split; ch < nch; ch += kSplits) {
+        uint32_t v[16];
+        tmem_ld16(tmem + lane_off + kColD2 + ch * 16, v);
+        tc_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int i = r0 + ch * 16 + c;
+          if (row && i < n) row[i] = (int8_t)(sgn * __float2int_rn(__uint_as_float(v[c])));
+        }
+      }
+      if (row && split == 0)
+        for (int b = n; b < p.ldc; ++b) row[b] = 0;
+    } else {
+      for (int ch = split; ch < nch; ch += kSplits) {
+        uint32_t v[16];
+        tmem_ld16(tmem + lane_off + kColD2 + ch * 16, v);
+        tc_wait_ld();
+        uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          int g = sgn * __float2int_rn(__uint_as_float(v[c]));
+          w[c >> 2] |= ((uint32_t)(g & 0xff)) << ((c & 3) * 8);
+        }
+        if (row) *reinterpret_cast<uint4*>(row + ch * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      if (row && split == 0)
+        for (int off = n_pad; off < p.ldc; off += 16) *reinterpret_cast<uint4*>(row + off) = make_uint4(0, 0, 0, 0);
     }
-    if (row && split == 0)
-      for (int off = n_pad; off < p.ldc; off += 16) *reinterpret_cast<uint4*>(row + off) = make_uint4(0, 0, 0, 0);
   };
   auto reset_collection = [&]() {
     if (split == 0) {
       s_fl[r] = 0;
-      s_fnz[r] = kNoNz;
+      if (!kId) s_fnz[r] = kNoNz;
     }
   };
   auto issue_d2 = [&]() {
@@ -484,6 +519,10 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
       __syncthreads();
       reset_collection();
     }
+    if (kId && split == 0) {  // the Adam epilogue recomputes these for round(z) of this step
+      s_fnz[r] = kNoNz;
+      s_fl[r] &= ~kOutId;
+    }
     if (!wait_mma()) { bail = true; break; }
     // (4) Adam on the FP32 master state; next operands
     // Adam in the form z -= (lr / bc1) m / (sqrt(v) / sqrt(bc2) + eps), with
@@ -492,9 +531,9 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
     const float step = ad.x, rsb2 = ad.y;
     float inv_term = 0.f;
     if (zinf < 1.f && zinf > 0.f) inv_term = -p.lambda2 / (zinf * zinf);  // times sign(z_kmax)
-    float nzinf = 0.f, frac = 0.f;
-    int nkmax = kNoNz;
-    bool changed = false, unexact = false;
+    float nzinf = 0.f, frac = 0.f, l1_id = 0.f;
+    int nkmax = kNoNz, first_id = kNoNz;
+    bool changed = false, unexact = false, out_id = false;
     for (int ch = split; ch < dch; ch += kSplits) {
       uint32_t v[16];
       tmem_ld16(tmem + lane_off + ch * 16, v);  // completes under the global loads below
@@ -520,8 +559,10 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
           // ceil z + floor z = 2 floor z + [z not an integer]
           float grad = __uint_as_float(v[cc]) + p.lambda1 * (2.f * fl + (z != fl ? 1.f : 0.f) - 2.f * z);
           if (j == kmax) grad += inv_term * (float)mape_sign_f(z);
+          if (kId) grad += (float)mape_sign_f(z);  // identity row j of B: sign((Bz)_j) = sign(z_j)
           if (dbg_step && live) {
             frac += (z - fl) * (ceilf(z) - z);
+            if (kId) l1_id += fabsf(z);
             if (p.dbg_grad) p.dbg_grad[pg * d + j] = grad;
           }
           const float m = p.beta1 * mc[cc] + p.omb1 * grad;
@@ -539,6 +580,10 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
             unexact |= fabsf(rn[q]) > 256.f;
             const float a = fabsf(znew);
             if (nkmax == kNoNz || a > nzinf) { nzinf = a; nkmax = j; }
+            if (kId) {  // identity rows of g = B round(z): bound test and first nonzero entry
+              out_id |= fabsf(rn[q]) > (float)s_span[j];
+              if (first_id == kNoNz && rn[q] != 0.f) first_id = (j << 1) | (rn[q] < 0.f ? 1 : 0);
+            }
           }
         }
         const __nv_bfloat162 hi = __floats2bfloat162_rn(zn[0], zn[1]);
@@ -561,9 +606,13 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
     }
     s_pz[split * kTileM + r] = nzinf;
     s_pk[split * kTileM + r] = nkmax;
-    if (dbg_step) s_pfr[split * kTileM + r] = frac;
-    uint32_t fbits = (changed ? kChanged : 0u) | (unexact ? kUnexact : 0u);
+    if (dbg_step) {
+      s_pfr[split * kTileM + r] = frac;
+      if (kId) s_pl1[split * kTileM + r] += l1_id;
+    }
+    uint32_t fbits = (changed ? kChanged : 0u) | (unexact ? kUnexact : 0u) | (out_id ? kOutId : 0u);
     if (fbits) atomicOr(&s_fl[r], fbits);
+    if (kId && first_id != kNoNz) atomicMin(&s_fnz[r], first_id);
     tc_wait_ld();
     tc_fence_before();
     fence_async_smem();
@@ -630,6 +679,17 @@ __global__ void unpack_blocked_kernel(const float* __restrict__ in, float* __res
 
 int pad16(int x) { return (x + 15) / 16 * 16; }
 
+// flag = 1 unless the top d x d block of B is the identity
+__global__ void identity_top_kernel(const int32_t* __restrict__ B, int d, int32_t* __restrict__ flag) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)d * d) return;
+  int i = (int)(e / d), j = (int)(e % d);
+  if (B[(int64_t)i * d + j] != (i == j ? 1 : 0)) atomicOr(flag, 1);
+}
+
+// rows of B held in the MMA tile: all n, or the n - d rows below the identity
+int tile_rows(int n, int d, bool id) { return pad16(id ? (n - d > 0 ? n - d : 1) : n); }
+
 }  // namespace
 
 namespace mape_detail {
@@ -641,19 +701,23 @@ constexpr uint32_t kSmemLimit = 232448 - 2048;  // opt-in maximum less static sh
 #endif
 
 // The transposed copy of B is used when it fits, else the MN-major view.
-int tc_use_bb(int n_pad, int d_pad, int nterms) {
+int tc_use_bb(int n_pad, int d_pad, int nterms, int span_pad) {
   if (MAPE_TC_FORCE_MN) return 0;
-  return smem_layout(n_pad, d_pad, nterms, 1).total <= kSmemLimit ? 1 : 0;
+  return smem_layout(n_pad, d_pad, nterms, 1, span_pad).total <= kSmemLimit ? 1 : 0;
 }
 
-bool tc_fits(int32_t n, int32_t d, int nterms) {
-  int n_pad = pad16(n), d_pad = pad16(d);
+bool tc_fits(int32_t n, int32_t d, int nterms, bool id) {
+  int n_pad = tile_rows(n, d, id), d_pad = pad16(d), span_pad = pad16(n);
   if (n_pad > 256 || d_pad > 256) return false;
-  return smem_layout(n_pad, d_pad, nterms, tc_use_bb(n_pad, d_pad, nterms)).total <= kSmemLimit;
+  return smem_layout(n_pad, d_pad, nterms, tc_use_bb(n_pad, d_pad, nterms, span_pad), span_pad).total <= kSmemLimit;
 }
 
+// Supported when some B of this shape runs: identity-topped bases need the
+// smaller tile; a general B of a shape only the identity-topped tile fits is
+// refused with MAPE_ERR_SHAPE at launch.
 bool extract_tc_supported(int32_t n, int32_t d, int32_t precision) {
-  return tc_fits(n, d, precision == MAPE_PREC_BF16X1 ? 1 : 2);
+  const int nterms = precision == MAPE_PREC_BF16X1 ? 1 : 2;
+  return tc_fits(n, d, nterms, true) || tc_fits(n, d, nterms, false);
 }
 
 size_t extract_tc_workspace(int32_t n, int32_t d, int32_t P, int32_t precision) {
@@ -662,6 +726,7 @@ size_t extract_tc_workspace(int32_t n, int32_t d, int32_t P, int32_t precision) 
   const size_t blocked = (size_t)ceil_div(P, kTileM) * kTileM * pad16(d);
   for (int k = 0; k < 3; ++k) s.take<float>(blocked);  // z, m, v blocked (carved separately)
   s.take<float2>((size_t)1 << 20);  // bias-correction table, up to 2^20 steps per call
+  s.take<int32_t>(1);               // identity-top flag
   return s.bytes();
 }
 
@@ -675,7 +740,18 @@ int extract_tc(const mape_extract_args* a, cudaStream_t st) {
   float* Mt = cv.take<float>((size_t)blocked);
   float* Vt = cv.take<float>((size_t)blocked);
   float2* bias = cv.take<float2>((size_t)1 << 20);
+  int32_t* idflag = cv.take<int32_t>(1);
   if (!cv.ok) return MAPE_ERR_CAPACITY;
+  // which kernel: identity-topped B or general B
+  MAPE_CUDA_TRY(cudaMemsetAsync(idflag, 0, sizeof(int32_t), st));
+  mape_detail::launch(identity_top_kernel, (unsigned)ceil_div((int64_t)d * d, 256), 256, 0, st, a->B, d, idflag);
+  MAPE_LAUNCH_CHECK();
+  int32_t h_notid = 1;
+  MAPE_CUDA_TRY(cudaMemcpyAsync(&h_notid, idflag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  const bool id = h_notid == 0;
+  const int nterms = a->precision == MAPE_PREC_BF16X1 ? 1 : 2;
+  if (!tc_fits(n, d, nterms, id)) return MAPE_ERR_SHAPE;
   std::vector<float2> bc;
   adam_bias_table(a, bc);
   for (int s = 0; s < a->T; ++s) {
@@ -690,22 +766,27 @@ int extract_tc(const mape_extract_args* a, cudaStream_t st) {
   mape_detail::launch(pack_blocked_kernel, gpack, 256, 0, st, a->V, Vt, P, d, d_pad, blocked);
   TcParams p{};
   p.B = a->B; p.span = a->span; p.Zt = Zt; p.Mt = Mt; p.Vt = Vt; p.bias = bias;
-  p.n = n; p.d = d; p.P = P; p.n_pad = pad16(n); p.d_pad = pad16(d);
+  p.n = n; p.d = d; p.P = P; p.n_pad = tile_rows(n, d, id); p.d_pad = pad16(d); p.span_pad = pad16(n);
   p.t0 = a->t0; p.T = a->T; p.period = a->period;
   p.lambda1 = a->lambda1; p.lambda2 = a->lambda2; p.lr = a->lr; p.eps = a->eps;
   p.beta1 = (float)a->beta1; p.beta2 = (float)a->beta2;
   p.omb1 = (float)(1.0 - a->beta1); p.omb2 = (float)(1.0 - a->beta2);
   p.cand = a->cand; p.ldc = a->ldc; p.cap = a->cand_cap; p.count = a->cand_count; p.flags = a->flags;
   p.dbg_phi = a->dbg_phi; p.dbg_grad = a->dbg_grad;
-  p.nterms = a->precision == MAPE_PREC_BF16X1 ? 1 : 2;
-  p.use_bb = tc_use_bb(p.n_pad, p.d_pad, p.nterms);
+  p.nterms = nterms;
+  p.use_bb = tc_use_bb(p.n_pad, p.d_pad, p.nterms, p.span_pad);
   // at least 116 KB of shared memory keeps one CTA per SM, so the 512-column
   // TMEM allocation never waits for another CTA
-  uint32_t smem = smem_layout(p.n_pad, p.d_pad, p.nterms, p.use_bb).total;
+  uint32_t smem = smem_layout(p.n_pad, p.d_pad, p.nterms, p.use_bb, p.span_pad).total;
   if (smem < 116 * 1024) smem = 116 * 1024;
-  MAPE_CUDA_TRY(cudaFuncSetAttribute(extract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   unsigned grid = (unsigned)ceil_div(P, kTileM);
-  mape_detail::launch(extract_tc_kernel, grid, kThreads, smem, st, p);
+  if (id) {
+    MAPE_CUDA_TRY(cudaFuncSetAttribute(extract_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    mape_detail::launch(extract_tc_kernel<true>, grid, kThreads, smem, st, p);
+  } else {
+    MAPE_CUDA_TRY(cudaFuncSetAttribute(extract_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    mape_detail::launch(extract_tc_kernel<false>, grid, kThreads, smem, st, p);
+  }
   MAPE_LAUNCH_CHECK();
   const unsigned gun = (unsigned)ceil_div((int64_t)P * d, 256);
   mape_detail::launch(unpack_blocked_kernel, gun, 256, 0, st, Zt, a->Z, P, d, d_pad);

@@ -76,6 +76,7 @@ struct mape_instance {
   int32_t *dA = nullptr, *dB = nullptr, *dl = nullptr, *du = nullptr, *dspan = nullptr;
   int64_t* db = nullptr;
   int32_t *dc = nullptr, *dw = nullptr, *dqr = nullptr, *dqc = nullptr, *dqv = nullptr;
+  float* dWproj = nullptr;  // B (B^T B)^{-1}, computed once per instance for the start projection
 
   // extraction job buffers (replaced per extract call)
   std::vector<std::pair<void*, size_t>> job_bufs;
@@ -174,7 +175,7 @@ int mape_instance::run_extract() {
   cudaStream_t s = stream;
   double t_start = now_ms();
   set_phase(MAPE_PHASE_EXTRACTING);
-  if (dG0) H_TRY(mape_project_starts(dB, n, d, dG0, P, dZ, dWork, work_bytes, s));
+  if (dG0) H_TRY(mape_project_apply(dWproj, n, d, dG0, P, dZ, s));
   MAPE_CUDA_TRY(cudaMemsetAsync(dM, 0, sizeof(float) * (size_t)P * d, s));
   MAPE_CUDA_TRY(cudaMemsetAsync(dV, 0, sizeof(float) * (size_t)P * d, s));
   int64_t U = 0, total_cand = 0;
@@ -378,6 +379,13 @@ extern "C" int mape_create_instance(const int32_t* A, const int64_t* b, const in
     return fail(MAPE_ERR_CUDA);
   if (bad) return fail(MAPE_ERR_NOT_KERNEL_BASIS);
   if ((rc = set_objective(h, f))) return fail(rc);
+  {
+    size_t pb = mape_project_prepare_workspace_bytes(n, d);
+    h->dWproj = h->take<float>(h->owned, (size_t)n * d);
+    char* pw = h->take<char>(h->owned, pb);
+    if (!h->dWproj || !pw) return fail(MAPE_ERR_OOM);
+    if ((rc = mape_project_prepare(h->dB, n, d, h->dWproj, pw, pb, h->stream))) return fail(rc);
+  }
   h->st.phase = MAPE_PHASE_IDLE;
   *out = h;
   return MAPE_OK;
@@ -413,7 +421,6 @@ extern "C" int mape_extract_directions(mape_handle h, int32_t P, const float* Z0
   h->dCount = h->take<unsigned long long>(h->job_bufs, 1);
   h->dFlags = h->take<int32_t>(h->job_bufs, 1);
   size_t w = 0;
-  w = std::max(w, mape_project_workspace_bytes(n, d));
   w = std::max(w, mape_extract_workspace_bytes(n, d, P, h->cfg.precision));
   w = std::max(w, mape_dedup_workspace_bytes(cap, ldg));
   w = std::max(w, mape_kernel_test_workspace_bytes());

@@ -135,27 +135,26 @@ __global__ void __launch_bounds__(256) gemm_kernel(const float* __restrict__ G0,
 
 }  // namespace
 
-extern "C" size_t mape_project_workspace_bytes(int32_t n, int32_t d) {
-  if (d <= 0 || n <= 0) return 0;
+extern "C" size_t mape_project_prepare_workspace_bytes(int32_t n, int32_t d) {
+  (void)n;
+  if (d <= 0) return 0;
   mape_detail::Sizer s;
   s.take<float>((size_t)d * d);   // H, then its Cholesky factor
   s.take<float>((size_t)d * d);   // L^{-1}
   s.take<float>((size_t)d * d);   // H^{-1}
-  s.take<float>((size_t)n * d);   // W
   s.take<int32_t>(1);
   return s.bytes();
 }
 
-extern "C" int mape_project_starts(const int32_t* B, int32_t n, int32_t d, const float* G0, int32_t P,
-                                   float* Z0, void* workspace, size_t workspace_bytes, void* stream) {
+extern "C" int mape_project_prepare(const int32_t* B, int32_t n, int32_t d, float* W, void* workspace,
+                                    size_t workspace_bytes, void* stream) {
   using namespace mape_detail;
-  if (!B || n <= 0 || d <= 0 || d > n || P < 0 || (P > 0 && (!G0 || !Z0))) return MAPE_ERR_INVALID_ARG;
+  if (!B || !W || n <= 0 || d <= 0 || d > n) return MAPE_ERR_INVALID_ARG;
   if (d > 4096) return MAPE_ERR_SHAPE;
   Carver cv(workspace, workspace_bytes);
   float* H = cv.take<float>((size_t)d * d);
   float* Y = cv.take<float>((size_t)d * d);
   float* Hi = cv.take<float>((size_t)d * d);
-  float* W = cv.take<float>((size_t)n * d);
   int32_t* status = cv.take<int32_t>(1);
   if (!cv.ok) return MAPE_ERR_CAPACITY;
   cudaStream_t st = as_stream(stream);
@@ -166,12 +165,43 @@ extern "C" int mape_project_starts(const int32_t* B, int32_t n, int32_t d, const
   mape_detail::launch(lower_inverse_kernel, gd, 128, 0, st, H, d, Y);
   mape_detail::launch(hinv_kernel, dim3(gd, (unsigned)d), 128, 0, st, Y, d, Hi);
   mape_detail::launch(w_kernel, dim3(gd, (unsigned)n), 128, 0, st, B, Hi, n, d, W);
-  if (P > 0)
-    mape_detail::launch(gemm_kernel, dim3((unsigned)ceil_div(d, kTN), (unsigned)ceil_div(P, kTM)), 256, 0, st, G0, W,
-                        P, n, d, Z0);
   MAPE_LAUNCH_CHECK();
   int32_t h_status = 0;
   MAPE_CUDA_TRY(cudaMemcpyAsync(&h_status, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   MAPE_CUDA_TRY(cudaStreamSynchronize(st));
   return h_status ? MAPE_ERR_NUMERIC : MAPE_OK;
+}
+
+extern "C" int mape_project_apply(const float* W, int32_t n, int32_t d, const float* G0, int32_t P, float* Z0,
+                                  void* stream) {
+  using namespace mape_detail;
+  if (!W || n <= 0 || d <= 0 || d > n || P < 0 || (P > 0 && (!G0 || !Z0))) return MAPE_ERR_INVALID_ARG;
+  if (P == 0) return MAPE_OK;
+  mape_detail::launch(gemm_kernel, dim3((unsigned)ceil_div(d, kTN), (unsigned)ceil_div(P, kTM)), 256, 0,
+                      as_stream(stream), G0, W, P, n, d, Z0);
+  MAPE_LAUNCH_CHECK();
+  return MAPE_OK;
+}
+
+extern "C" size_t mape_project_workspace_bytes(int32_t n, int32_t d) {
+  if (d <= 0 || n <= 0) return 0;
+  mape_detail::Sizer s;
+  s.take<float>((size_t)n * d);                                   // W
+  s.take<char>(mape_project_prepare_workspace_bytes(n, d));
+  return s.bytes();
+}
+
+extern "C" int mape_project_starts(const int32_t* B, int32_t n, int32_t d, const float* G0, int32_t P,
+                                   float* Z0, void* workspace, size_t workspace_bytes, void* stream) {
+  using namespace mape_detail;
+  if (!B || n <= 0 || d <= 0 || d > n || P < 0 || (P > 0 && (!G0 || !Z0))) return MAPE_ERR_INVALID_ARG;
+  if (d > 4096) return MAPE_ERR_SHAPE;
+  Carver cv(workspace, workspace_bytes);
+  float* W = cv.take<float>((size_t)n * d);
+  size_t pb = mape_project_prepare_workspace_bytes(n, d);
+  char* pw = cv.take<char>(pb);
+  if (!cv.ok) return MAPE_ERR_CAPACITY;
+  int rc = mape_project_prepare(B, n, d, W, pw, pb, stream);
+  if (rc != MAPE_OK) return rc;
+  return mape_project_apply(W, n, d, G0, P, Z0, stream);
 }

@@ -91,6 +91,9 @@ _SIGS = {
     "mape_launch_count": (C.c_ulonglong, []),
     "mape_project_workspace_bytes": (C.c_size_t, [I32, I32]),
     "mape_project_starts": (C.c_int, [P_, I32, I32, P_, I32, P_, P_, C.c_size_t, P_]),
+    "mape_project_prepare_workspace_bytes": (C.c_size_t, [I32, I32]),
+    "mape_project_prepare": (C.c_int, [P_, I32, I32, P_, P_, C.c_size_t, P_]),
+    "mape_project_apply": (C.c_int, [P_, I32, I32, P_, I32, P_, P_]),
     "mape_phi_grad": (C.c_int, [P_, I32, I32, P_, I32, F32, F32, P_, P_, P_]),
     "mape_extract_workspace_bytes": (C.c_size_t, [I32, I32, I32, I32]),
     "mape_extract": (C.c_int, [C.POINTER(ExtractArgs), P_]),
