@@ -343,18 +343,26 @@ def roofline(mape, inst, starts, stream, args, reps=3):
         if i > 0:
             times.append(e0.elapsed_time(e1))
     ms = statistics.median(times)
-    n, d = inst.n, inst.d
+    n, d, m = inst.n, inst.d, inst.n - inst.d
     if prec == 0:
         return {"kernel": "extract_fp32 (3 kernels per step)", "bound": "alu", "ms": ms}
     nterms = 2 if prec == 1 else 1
-    flops = 2.0 * n * d * P_FULL * T_FULL * (nterms + 2)   # forward terms, B round(z), gradient
-    achieved = flops / (ms / 1e3) / 1e12
-    peak = peaks["bf16_tflops"]
-    return {"bound": "tensor", "kernel": "extract_tc_kernel", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "ms_per_launch": ms,
-            "flops_per_launch": flops, "peak_source": f"{src} bf16 burst (MEASURED_PEAKS.json)",
-            "note": "dense MMA flops of one launch (T=1000 steps, P=8192): 2*n*d*P*T*(2 forward terms + "
-                    "B round(z) + gradient); the launch includes its 6 layout transposes (<0.1%)"}
+    # algorithmic bytes: the FP32 master z, m, v read and written once per
+    # coordinate, start and step (24 d bytes per start-step)
+    state_bytes = 24.0 * d * P_FULL * T_FULL
+    achieved = state_bytes / (ms / 1e3) / 1e9
+    peak = peaks["hbm_gbs"]
+    # MMA work actually issued: the basis is [I; -C], so the tensor cores
+    # contract the m = n - d rows of -C (nterms forward terms, B round(z), gradient)
+    mma_flops = 2.0 * m * d * P_FULL * T_FULL * (nterms + 2)
+    return {"bound": "hbm", "kernel": "extract_tc_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "ms_per_launch": ms, "bytes_per_launch": state_bytes,
+            "peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "tensor_tflops": mma_flops / (ms / 1e3) / 1e12,
+            "tensor_frac_of_bf16_burst": mma_flops / (ms / 1e3) / 1e12 / peaks["bf16_tflops"],
+            "note": "one launch = T=1000 steps for P=8192 starts; algorithmic bytes = 24*d per start-step "
+                    "(FP32 z, m, v read + write); the 15.7 MB state stays in L2, so HBM is the bound of "
+                    "the traffic, not the wire it uses; the launch includes its 6 layout kernels (<0.1%)"}
 
 
 def plain_fp32(mape, inst, G0, x0, stream):
