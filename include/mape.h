@@ -180,6 +180,29 @@ int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t ldc,
                int8_t* uniq, int64_t uniq_cap, int64_t* K_out,
                void* workspace, size_t workspace_bytes, void* stream);
 
+/* mape_dedup without any device allocation (this entry point has no
+ * counterpart in the paper; it is an interface for callers).  Some callers
+ * cannot allocate device memory where they dedup: code running while a stream
+ * is captured into a CUDA graph (cudaMalloc is not allowed there), hosts that
+ * reserve all device memory up front and forbid later allocations, plugins
+ * whose host owns the allocator.  This variant takes no workspace: its
+ * scratch is a static device array of 6 MiB inside the library, which every
+ * GPU that loads the library holds until the process exits.
+ *   Limit: count <= mape_dedup_static_max_rows() (2^18 rows); larger counts
+ *   return MAPE_ERR_CAPACITY before any device work.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   All calls share the array and it keeps the previous call's contents; the
+ *   call clears what must start empty itself.  Calls that overlap on the GPU
+ *   (different streams or threads at the same time) race on the array and
+ *   must not be issued.
+ * Arguments, output and errors otherwise as mape_dedup.  Synchronous. */
+int64_t mape_dedup_static_max_rows(void);
+int mape_dedup_static(const int8_t* cand, int64_t count, int32_t n, int32_t ldc,
+                      int8_t* uniq, int64_t uniq_cap, int64_t* K_out,
+                      void* stream);
+
 /* a9 -- condition C1 (§3): ok[k] = 1 iff A g_k = 0 exactly (int32
  * arithmetic, |A_ij| <= 2^23 and n <= 4096 keep every partial sum exact).
  *   A [m x n] int32, G [K x ldg] int8.  *fail_count = rows with A g != 0.

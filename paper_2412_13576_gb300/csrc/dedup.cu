@@ -13,6 +13,8 @@
 //    which fixes the output order independently of the atomics.
 #include "common.cuh"
 
+#include <mutex>
+
 namespace {
 
 constexpr uint32_t kEmpty = 0xffffffffu;
@@ -239,4 +241,67 @@ extern "C" int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t 
   MAPE_LAUNCH_CHECK();
   MAPE_CUDA_TRY(cudaStreamSynchronize(st));
   return MAPE_OK;
+}
+
+// ---- the same stage without any device allocation ----------------------------
+//
+// For callers that cannot allocate device memory at the point where they
+// dedup: code running while a stream is being captured into a CUDA graph
+// (where cudaMalloc is not allowed), hosts that reserve all device memory up
+// front and forbid allocations later (fixed-memory real-time loops), or
+// plugins whose host owns the device allocator.  The scratch lives in a
+// file-scope device array that every GPU loading this library holds until the
+// process exits.  Host code cannot pass that array's name to a kernel (in host
+// code it is only a host-side stand-in), so its device address is looked up
+// once per device, with that device current, by cudaGetSymbolAddress.
+
+namespace {
+
+constexpr int64_t kStaticDedupRows = (int64_t)1 << 18;       // candidate rows per call
+constexpr size_t kStaticDedupBytes = (size_t)6 << 20;        // >= mape_dedup_workspace_bytes(2^18, any ldc)
+static __device__ __align__(256) unsigned char g_dedup_scratch[kStaticDedupBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_dedup_scratch on the current device (looked up once).
+int static_dedup_scratch(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    mape_detail::record_cuda_error(e, "cudaGetDevice", __FILE__, __LINE__);
+    return MAPE_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) return MAPE_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (g_scratch_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_dedup_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      mape_detail::record_cuda_error(e, "cudaGetSymbolAddress(g_dedup_scratch)", __FILE__, __LINE__);
+      return MAPE_ERR_CUDA;
+    }
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return MAPE_OK;
+}
+
+}  // namespace
+
+extern "C" int64_t mape_dedup_static_max_rows(void) { return kStaticDedupRows; }
+
+extern "C" int mape_dedup_static(const int8_t* cand, int64_t count, int32_t n, int32_t ldc, int8_t* uniq,
+                                 int64_t uniq_cap, int64_t* K_out, void* stream) {
+  if (!K_out || count < 0 || n <= 0 || ldc < n || ldc % 16 != 0 || uniq_cap < 0) return MAPE_ERR_INVALID_ARG;
+  *K_out = 0;
+  if (count > kStaticDedupRows) return MAPE_ERR_CAPACITY;  // more rows than the static scratch holds
+  if (mape_dedup_workspace_bytes(count, ldc) > kStaticDedupBytes) return MAPE_ERR_CAPACITY;
+  if (count == 0) return MAPE_OK;
+  void* scratch = nullptr;
+  int rc = static_dedup_scratch(&scratch);
+  if (rc != MAPE_OK) return rc;
+  // the table and the counter are cleared by the stage itself on every call
+  return mape_dedup(cand, count, n, ldc, uniq, uniq_cap, K_out, scratch, kStaticDedupBytes, stream);
 }

@@ -99,6 +99,8 @@ _SIGS = {
     "mape_extract": (C.c_int, [C.POINTER(ExtractArgs), P_]),
     "mape_dedup_workspace_bytes": (C.c_size_t, [I64, I32]),
     "mape_dedup": (C.c_int, [P_, I64, I32, I32, P_, I64, C.POINTER(I64), P_, C.c_size_t, P_]),
+    "mape_dedup_static_max_rows": (I64, []),
+    "mape_dedup_static": (C.c_int, [P_, I64, I32, I32, P_, I64, C.POINTER(I64), P_]),
     "mape_kernel_test_workspace_bytes": (C.c_size_t, []),
     "mape_kernel_test": (C.c_int, [P_, I32, I32, P_, I64, I32, P_, C.POINTER(I64), P_, C.c_size_t, P_]),
     "mape_minimal_workspace_bytes": (C.c_size_t, [I64, I32]),
