@@ -1,11 +1,10 @@
 // Algorithm 2 (§3.2) on the 5th-generation tensor cores: one persistent
-// kernel runs all T Adam steps; each CTA owns 128 starts for the whole run.
+// kernel runs all T Adam steps; each CTA owns 64 starts for the whole run.
 //
-// Start p of the tile is row p of every MMA (M = 128) and lane p of TMEM, so
-// every per-start reduction (||z||_inf, its first maximiser, the bound test,
-// the first nonzero entry) stays inside the lanes that own that start.  Per
-// step, with B held in shared memory as BF16 (exact: |B_ij| <= 256):
-//   D1 = hi(Z) . B^T + lo(Z) . B^T  (M=128, N=n_pad, K=d_pad) -> TMEM cols [0, n_pad)
+// Start r of the tile is row r of every MMA (M = 64), held by TMEM lane
+// 32 * (r / 16) + r % 16 (lanes 0-15 of each 32-lane quarter).  Per step, with
+// B in shared memory as BF16 (exact: |B_ij| <= 256):
+//   D1 = hi(Z) . B^T + lo(Z) . B^T  (M=64, N=n_pad, K=d_pad) -> TMEM cols [0, n_pad)
 //        with hi = bf16(z), lo = bf16(z - hi): z carried to ~16 significant
 //        bits, so B z is as accurate as an FP32 dot product (one term, hi only,
 //        is the faster and coarser MAPE_PREC_BF16X1)
@@ -13,21 +12,23 @@
 //        exact: |round z| <= 256 is exact in BF16, every partial sum is an
 //        integer below 2^24 and FP32 accumulation is exact; D2 holds g = B round(z)
 //   S  = sign(D1) as BF16 {-1,0,1} written to shared memory
-//   G  = S . B                   (M=128, N=d_pad, K=n_pad)  -> TMEM cols [0, d_pad)
+//   G  = S . B                   (M=64, N=d_pad, K=n_pad)   -> TMEM cols [0, d_pad)
 //        B is read through an MN-major descriptor of the same shared tile
 //        (a transposed K-major copy is kept instead when it fits)
 //   grad = G + lambda1 (ceil z + floor z - 2 z) + inverse-norm term; Adam on
-//   the FP32 master z, m, v (blocked [tile][d/4][128][4] in global memory, L2
+//   the FP32 master z, m, v (blocked [tile][d/4][64][4] in global memory, L2
 //   resident, one 16-byte access per 4 coordinates);
 //   the new bf16(z), bf16(round z) operands are written for the next step.
 // The candidate of step t (D2 of step t+1) is tested (C4, nonzero), signed
 // canonically and appended while the G MMA runs.
 //
-// 16 warps: warp w serves TMEM lane quarter w % 4 (the only lanes it may
-// access) and every 4th 16-column chunk starting at chunk w / 4.  Operands are
-// stored in the canonical no-swizzle K-major layout: 8 rows x 16 bytes core
-// matrices, K-adjacent core matrices 128 bytes apart (LBO), 8-row groups
-// (K/8) * 128 bytes apart (SBO).
+// 16 warps: warp w reads TMEM lane quarter w % 4 (the only lanes it may
+// access) with the 16x32bx2 shape, so its two half-warps take the two 8-column
+// halves of one 16-column chunk for the same 16 starts; warp w handles every
+// 4th chunk starting at chunk w / 4.  Each start is thus served by 8 threads
+// (4 chunk groups x 2 halves).  Operands are stored in the canonical
+// no-swizzle K-major layout: 8 rows x 16 bytes core matrices, K-adjacent core
+// matrices 128 bytes apart (LBO), 8-row groups (K/8) * 128 bytes apart (SBO).
 //
 // Every wait on the MMA barrier is bounded; on time-out the CTA records flag
 // 16, leaves the loop together (block-wide vote), frees its TMEM and returns.
@@ -40,10 +41,11 @@
 
 namespace {
 
-constexpr int kTileM = 128;
+constexpr int kTileM = 64;
 constexpr int kWarps = 16;
 constexpr int kThreads = kWarps * 32;
 constexpr int kSplits = kWarps / 4;
+constexpr int kParts = kSplits * 2;  // threads per start
 constexpr int kColD2 = 256;
 constexpr int kTmemCols = 512;
 constexpr uint32_t kWaitLimit = 1u << 20;
@@ -87,12 +89,12 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+// 8 consecutive FP32 columns of one M=64 row: half-warp 0 reads columns
+// [col, col+8) of lanes 0-15 of the quarter, half-warp 1 columns [col+8, col+16)
+__device__ __forceinline__ void tmem_ld8x2(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.16x32bx2.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], 8;"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -126,12 +128,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
   return false;
 }
 
-__device__ __forceinline__ uint16_t bf16_bits(float x) {
-  __nv_bfloat16 h = __float2bfloat16_rn(x);
-  return *reinterpret_cast<uint16_t*>(&h);
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
 }
-
-__device__ __forceinline__ float bf16_value(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
 
 // MN-major no-swizzle canonical layout ((T,1,m),(8,k)):((1,T,SBO),(1T,LBO)):
 // the 8-row K groups are LBO apart and the 16-byte MN groups SBO apart.
@@ -145,25 +145,9 @@ __device__ __forceinline__ uint32_t op_off(int r, int k, int K) {
   return (uint32_t)((((r >> 3) * (K >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
 }
 
-// writes 16 bf16 values (columns k0..k0+15 of row r) as two 16-byte stores
-__device__ __forceinline__ void store_row16(uint8_t* tile, int r, int k0, int K, const uint16_t (&h)[16]) {
-  uint4 lo, hi;
-  lo.x = h[0] | ((uint32_t)h[1] << 16);
-  lo.y = h[2] | ((uint32_t)h[3] << 16);
-  lo.z = h[4] | ((uint32_t)h[5] << 16);
-  lo.w = h[6] | ((uint32_t)h[7] << 16);
-  hi.x = h[8] | ((uint32_t)h[9] << 16);
-  hi.y = h[10] | ((uint32_t)h[11] << 16);
-  hi.z = h[12] | ((uint32_t)h[13] << 16);
-  hi.w = h[14] | ((uint32_t)h[15] << 16);
-  *reinterpret_cast<uint4*>(tile + op_off(r, k0, K)) = lo;
-  *reinterpret_cast<uint4*>(tile + op_off(r, k0 + 8, K)) = hi;
-}
-
-// same, from 8 words of two packed bf16 each (element 2i in the low half)
-__device__ __forceinline__ void store_row16w(uint8_t* tile, int r, int k0, int K, const uint32_t (&w)[8]) {
+// 8 bf16 (columns k0..k0+7, k0 a multiple of 8) of row r: one 16-byte store
+__device__ __forceinline__ void store_row8(uint8_t* tile, int r, int k0, int K, const uint32_t (&w)[4]) {
   *reinterpret_cast<uint4*>(tile + op_off(r, k0, K)) = make_uint4(w[0], w[1], w[2], w[3]);
-  *reinterpret_cast<uint4*>(tile + op_off(r, k0 + 8, K)) = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
 struct TcParams {
@@ -200,8 +184,8 @@ constexpr uint32_t kOutId = 8;      // ... fails C4 on the identity rows (identi
 
 __host__ __device__ inline uint32_t al(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
-// Operand area: [hi | lo] of bf16(z) (nterms tiles of 128 x d_pad), later
-// overwritten by S (128 x n_pad); then bf16(round z) (128 x d_pad).
+// Operand area: [hi | lo] of bf16(z) (nterms tiles of 64 x d_pad), later
+// overwritten by S (64 x n_pad); then bf16(round z) (64 x d_pad).
 __host__ __device__ inline Smem smem_layout(int n_pad, int d_pad, int nterms, int use_bb, int span_pad) {
   Smem s{};
   uint32_t o = 0;
@@ -212,10 +196,10 @@ __host__ __device__ inline Smem smem_layout(int n_pad, int d_pad, int nterms, in
   s.opa2 = o + (uint32_t)kTileM * zs * 2;
   o = al(s.opa2 + (uint32_t)kTileM * d_pad * 2, 128);
   s.span = o; o = al(o + (uint32_t)span_pad * 4, 128);
-  s.pz = o;   o = al(o + kSplits * kTileM * 4, 128);
-  s.pk = o;   o = al(o + kSplits * kTileM * 4, 128);
-  s.pl1 = o;  o = al(o + kSplits * kTileM * 4, 128);
-  s.pfr = o;  o = al(o + kSplits * kTileM * 4, 128);
+  s.pz = o;   o = al(o + kParts * kTileM * 4, 128);
+  s.pk = o;   o = al(o + kParts * kTileM * 4, 128);
+  s.pl1 = o;  o = al(o + kParts * kTileM * 4, 128);
+  s.pfr = o;  o = al(o + kParts * kTileM * 4, 128);
   s.fl = o;   o = al(o + kTileM * 4, 128);
   s.fnz = o;  o = al(o + kTileM * 4, 128);
   s.slot = o; o = al(o + kTileM * 8, 128);
@@ -235,9 +219,9 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
   const Smem L = smem_layout(p.n_pad, p.d_pad, p.nterms, p.use_bb, p.span_pad);
   uint8_t* Bf = smem + L.bf;
   uint8_t* Bb = smem + L.bb;
-  uint8_t* A1 = smem + L.opa;                        // hi(z)
+  uint8_t* A1 = smem + L.opa;                           // hi(z)
   uint8_t* A1lo = smem + L.opa + kTileM * p.d_pad * 2;  // lo(z)
-  uint8_t* A2 = smem + L.opa2;
+  uint8_t* A2 = smem + L.opa2;                          // round(z)
   uint8_t* Sop = smem + L.opa;
   int32_t* s_span = reinterpret_cast<int32_t*>(smem + L.span);
   float* s_pz = reinterpret_cast<float*>(smem + L.pz);
@@ -253,13 +237,15 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int quarter = warp & 3, split = warp >> 2;
-  const int r = quarter * 32 + lane;                 // start row in the tile
-  const int64_t pg = (int64_t)blockIdx.x * kTileM + r;  // global start
+  const int quarter = warp & 3, split = warp >> 2, half = lane >> 4;
+  const int part = split * 2 + half;                      // which of the 8 threads of a start
+  const int r = quarter * 16 + (lane & 15);               // start row in the tile
+  const int64_t pg = (int64_t)blockIdx.x * kTileM + r;    // global start
   const bool active = pg < p.P;
   const int n = p.n, d = p.d, n_pad = p.n_pad, d_pad = p.d_pad;
   const int nch = n_pad / 16, dch = d_pad / 16;
   const int r0 = kId ? d : 0;  // row of B held in row 0 of the MMA tile
+  const int hoff = 8 * half;   // column offset of this half-warp inside a 16-column chunk
 
   // ---- set-up: B in both operand layouts, span, flags ----
   if (tid == 0) s_bad = 0;
@@ -268,9 +254,10 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
     int i = e / d_pad, j = e % d_pad;
     int v = (r0 + i < n && j < d) ? p.B[(int64_t)(r0 + i) * d + j] : 0;
     if (v > 256 || v < -256) s_bad = 1;
-    uint16_t h = bf16_bits((float)v);
-    *reinterpret_cast<uint16_t*>(Bf + op_off(i, j, d_pad)) = h;  // N = n rows, K = d
-    if (p.use_bb) *reinterpret_cast<uint16_t*>(Bb + op_off(j, i, n_pad)) = h;  // N = d rows, K = n
+    __nv_bfloat16 hb = __float2bfloat16_rn((float)v);
+    const uint16_t h = *reinterpret_cast<const uint16_t*>(&hb);
+    *reinterpret_cast<uint16_t*>(Bf + op_off(i, j, d_pad)) = h;                // N = rows, K = d
+    if (p.use_bb) *reinterpret_cast<uint16_t*>(Bb + op_off(j, i, n_pad)) = h;  // N = d, K = rows
   }
   for (int i = tid; i < p.span_pad; i += kThreads) s_span[i] = i < n ? p.span[i] : 0;
   if (tid < kTileM) {
@@ -292,8 +279,8 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
   bool bail = s_bad != 0;
   if (bail && tid == 0) atomicOr(p.flags, 8);
 
-  // FP32 master state of this thread's start: blocked [tile][d_pad/4][128][4],
-  // four consecutive coordinates per 16-byte access, coalesced across a warp
+  // FP32 master state of this thread's start: blocked [tile][d_pad/4][64][4],
+  // four consecutive coordinates per 16-byte access, coalesced over 16 starts
   float4* const zb = reinterpret_cast<float4*>(p.Zt) + (size_t)blockIdx.x * (d_pad / 4) * kTileM + r;
   float4* const mb = reinterpret_cast<float4*>(p.Mt) + (size_t)blockIdx.x * (d_pad / 4) * kTileM + r;
   float4* const vb = reinterpret_cast<float4*>(p.Vt) + (size_t)blockIdx.x * (d_pad / 4) * kTileM + r;
@@ -302,27 +289,32 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
   float zinf_part = 0.f;
   int kmax_part = kNoNz;
   for (int ch = split; ch < dch && !bail; ch += kSplits) {
-    uint16_t h[16], hl[16];
-    float zc[16];
+    const int c0 = ch * 16 + hoff;
+    float zc[8];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float4 q = zb[(ch * 4 + k) * kTileM];
+    for (int k = 0; k < 2; ++k) {
+      const float4 q = zb[(c0 / 4 + k) * kTileM];
       zc[4 * k] = q.x; zc[4 * k + 1] = q.y; zc[4 * k + 2] = q.z; zc[4 * k + 3] = q.w;
     }
+    uint32_t wh[4], wl[4];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      int j = ch * 16 + c;
-      float z = zc[c];
-      h[c] = bf16_bits(z);
-      hl[c] = bf16_bits(z - bf16_value(h[c]));
-      float a = fabsf(z);
+    for (int c = 0; c < 8; c += 2) {
+      wh[c >> 1] = pack_bf16x2(zc[c], zc[c + 1]);
+      const __nv_bfloat162 hh = *reinterpret_cast<const __nv_bfloat162*>(&wh[c >> 1]);
+      const float2 hf = __bfloat1622float2(hh);
+      wl[c >> 1] = pack_bf16x2(zc[c] - hf.x, zc[c + 1] - hf.y);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int j = c0 + c;
+      const float a = fabsf(zc[c]);
       if (j < d && (a > zinf_part || kmax_part == kNoNz)) { zinf_part = a; kmax_part = j; }
     }
-    store_row16(A1, r, ch * 16, d_pad, h);
-    if (p.nterms > 1) store_row16(A1lo, r, ch * 16, d_pad, hl);
+    store_row8(A1, r, c0, d_pad, wh);
+    if (p.nterms > 1) store_row8(A1lo, r, c0, d_pad, wl);
   }
-  s_pz[split * kTileM + r] = zinf_part;
-  s_pk[split * kTileM + r] = kmax_part;
+  s_pz[part * kTileM + r] = zinf_part;
+  s_pk[part * kTileM + r] = kmax_part;
   fence_async_smem();
   __syncthreads();
 
@@ -338,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
   auto combine_zinf = [&](float& zinf, int& kmax) {
     zinf = 0.f;
     kmax = kNoNz;
-    for (int s = 0; s < kSplits; ++s) {
+    for (int s = 0; s < kParts; ++s) {
       float z = s_pz[s * kTileM + r];
       int k = s_pk[s * kTileM + r];
       if (k == kNoNz) continue;
@@ -354,12 +346,12 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
     int first = kNoNz;
     bool out = false;
     for (int ch = split; ch < nch; ch += kSplits) {
-      uint32_t v[16];
-      tmem_ld16(tmem + lane_off + kColD2 + ch * 16, v);
+      uint32_t v[8];
+      tmem_ld8x2(tmem + lane_off + kColD2 + ch * 16, v);
       tc_wait_ld();
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int i = r0 + ch * 16 + c;  // row of B
+      for (int c = 0; c < 8; ++c) {
+        const int i = r0 + ch * 16 + hoff + c;  // row of B
         int g = __float2int_rn(__uint_as_float(v[c]));
         if (i < n) {
           if (g > s_span[i] || -g > s_span[i]) out = true;
@@ -372,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
   };
   // ... and appends it in canonical sign (needs a barrier between the two)
   auto decide_slot = [&]() {
-    if (split != 0) return;
+    if (part != 0) return;
     long long slot = -1;
     uint32_t f = s_fl[r];
     int fnz = s_fnz[r];
@@ -396,48 +388,48 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
     if (kId) {
       // identity rows: g_j = round z_j, held as BF16 in the round(z) operand tile
       for (int ch = split; ch < dch && row; ch += kSplits) {
-        const uint4 lo = *reinterpret_cast<const uint4*>(A2 + op_off(r, ch * 16, d_pad));
-        const uint4 hi = *reinterpret_cast<const uint4*>(A2 + op_off(r, ch * 16 + 8, d_pad));
-        const uint32_t wv[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+        const int c0 = ch * 16 + hoff;
+        const uint4 q = *reinterpret_cast<const uint4*>(A2 + op_off(r, c0, d_pad));
+        const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int j = ch * 16 + c;
+        for (int c = 0; c < 8; ++c) {
+          const int j = c0 + c;
           const float zr = __uint_as_float((c & 1) ? (wv[c >> 1] & 0xffff0000u) : (wv[c >> 1] << 16));
           if (j < d) row[j] = (int8_t)(sgn * __float2int_rn(zr));
         }
       }
       // rows of B' from D2 (warp-collective loads: every lane executes them)
       for (int ch = split; ch < nch; ch += kSplits) {
-        uint32_t v[16];
-        tmem_ld16(tmem + lane_off + kColD2 + ch * 16, v);
+        uint32_t v[8];
+        tmem_ld8x2(tmem + lane_off + kColD2 + ch * 16, v);
         tc_wait_ld();
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int i = r0 + ch * 16 + c;
+        for (int c = 0; c < 8; ++c) {
+          const int i = r0 + ch * 16 + hoff + c;
           if (row && i < n) row[i] = (int8_t)(sgn * __float2int_rn(__uint_as_float(v[c])));
         }
       }
-      if (row && split == 0)
+      if (row && part == 0)
         for (int b = n; b < p.ldc; ++b) row[b] = 0;
     } else {
       for (int ch = split; ch < nch; ch += kSplits) {
-        uint32_t v[16];
-        tmem_ld16(tmem + lane_off + kColD2 + ch * 16, v);
+        uint32_t v[8];
+        tmem_ld8x2(tmem + lane_off + kColD2 + ch * 16, v);
         tc_wait_ld();
-        uint32_t w[4] = {0, 0, 0, 0};
+        uint32_t w[2] = {0, 0};
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
+        for (int c = 0; c < 8; ++c) {
           int g = sgn * __float2int_rn(__uint_as_float(v[c]));
           w[c >> 2] |= ((uint32_t)(g & 0xff)) << ((c & 3) * 8);
         }
-        if (row) *reinterpret_cast<uint4*>(row + ch * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+        if (row) *reinterpret_cast<uint2*>(row + ch * 16 + hoff) = make_uint2(w[0], w[1]);
       }
-      if (row && split == 0)
+      if (row && part == 0)
         for (int off = n_pad; off < p.ldc; off += 16) *reinterpret_cast<uint4*>(row + off) = make_uint4(0, 0, 0, 0);
     }
   };
   auto reset_collection = [&]() {
-    if (split == 0) {
+    if (part == 0) {
       s_fl[r] = 0;
       if (!kId) s_fnz[r] = kNoNz;
     }
@@ -482,19 +474,19 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
     // (2) S = sign(D1) into shared memory; test the previous step's candidate
     float l1 = 0.f;
     for (int ch = split; ch < nch; ch += kSplits) {
-      uint32_t v[16];
-      tmem_ld16(tmem + lane_off + ch * 16, v);
+      uint32_t v[8];
+      tmem_ld8x2(tmem + lane_off + ch * 16, v);
       tc_wait_ld();
-      uint16_t h[16];
+      uint32_t w[4];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        float y = __uint_as_float(v[c]);
-        h[c] = y > 0.f ? (uint16_t)0x3F80 : (y < 0.f ? (uint16_t)0xBF80 : (uint16_t)0);
-        l1 += fabsf(y);
+      for (int c = 0; c < 8; c += 2) {
+        const float y0 = __uint_as_float(v[c]), y1 = __uint_as_float(v[c + 1]);
+        w[c >> 1] = pack_bf16x2((float)mape_sign_f(y0), (float)mape_sign_f(y1));
+        l1 += fabsf(y0) + fabsf(y1);
       }
-      store_row16(Sop, r, ch * 16, n_pad, h);
+      store_row8(Sop, r, ch * 16 + hoff, n_pad, w);
     }
-    if (dbg_step) s_pl1[split * kTileM + r] = l1;
+    if (dbg_step) s_pl1[part * kTileM + r] = l1;
     if (collect_prev) test_candidate();
     tc_wait_ld();
     tc_fence_before();
@@ -519,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
       __syncthreads();
       reset_collection();
     }
-    if (kId && split == 0) {  // the Adam epilogue recomputes these for round(z) of this step
+    if (kId && part == 0) {  // the Adam epilogue recomputes these for round(z) of this step
       s_fnz[r] = kNoNz;
       s_fl[r] &= ~kOutId;
     }
@@ -535,24 +527,26 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
     int nkmax = kNoNz, first_id = kNoNz;
     bool changed = false, unexact = false, out_id = false;
     for (int ch = split; ch < dch; ch += kSplits) {
-      uint32_t v[16];
-      tmem_ld16(tmem + lane_off + ch * 16, v);  // completes under the global loads below
-      float zc[16], mc[16], vc[16], zo[16], mo[16], vo[16];
+      const int c0 = ch * 16 + hoff;
+      uint32_t v[8];
+      tmem_ld8x2(tmem + lane_off + ch * 16, v);  // completes under the global loads below
+      float zc[8], mc[8], vc[8], zo[8], mo[8], vo[8];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float4 qz = zb[(ch * 4 + k) * kTileM], qm = mb[(ch * 4 + k) * kTileM], qv = vb[(ch * 4 + k) * kTileM];
+      for (int k = 0; k < 2; ++k) {
+        const int g4 = c0 / 4 + k;
+        const float4 qz = zb[g4 * kTileM], qm = mb[g4 * kTileM], qv = vb[g4 * kTileM];
         zc[4 * k] = qz.x; zc[4 * k + 1] = qz.y; zc[4 * k + 2] = qz.z; zc[4 * k + 3] = qz.w;
         mc[4 * k] = qm.x; mc[4 * k + 1] = qm.y; mc[4 * k + 2] = qm.z; mc[4 * k + 3] = qm.w;
         vc[4 * k] = qv.x; vc[4 * k + 1] = qv.y; vc[4 * k + 2] = qv.z; vc[4 * k + 3] = qv.w;
       }
       tc_wait_ld();
-      uint32_t w1[8], wl[8], w2[8];
+      uint32_t w1[4], wl[4], w2[4];
 #pragma unroll
-      for (int c = 0; c < 16; c += 2) {
+      for (int c = 0; c < 8; c += 2) {
         float zn[2], rn[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          const int cc = c + q, j = ch * 16 + cc;
+          const int cc = c + q, j = c0 + cc;
           const bool live = active && j < d;
           const float z = zc[cc];
           const float fl = floorf(z);
@@ -586,29 +580,27 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
             }
           }
         }
-        const __nv_bfloat162 hi = __floats2bfloat162_rn(zn[0], zn[1]);
-        const float2 hf = __bfloat1622float2(hi);
-        const __nv_bfloat162 lo = __floats2bfloat162_rn(zn[0] - hf.x, zn[1] - hf.y);
-        const __nv_bfloat162 rr = __floats2bfloat162_rn(rn[0], rn[1]);
-        w1[c >> 1] = *reinterpret_cast<const uint32_t*>(&hi);
-        wl[c >> 1] = *reinterpret_cast<const uint32_t*>(&lo);
-        w2[c >> 1] = *reinterpret_cast<const uint32_t*>(&rr);
+        w1[c >> 1] = pack_bf16x2(zn[0], zn[1]);
+        const float2 hf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w1[c >> 1]));
+        wl[c >> 1] = pack_bf16x2(zn[0] - hf.x, zn[1] - hf.y);
+        w2[c >> 1] = pack_bf16x2(rn[0], rn[1]);
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        zb[(ch * 4 + k) * kTileM] = make_float4(zo[4 * k], zo[4 * k + 1], zo[4 * k + 2], zo[4 * k + 3]);
-        mb[(ch * 4 + k) * kTileM] = make_float4(mo[4 * k], mo[4 * k + 1], mo[4 * k + 2], mo[4 * k + 3]);
-        vb[(ch * 4 + k) * kTileM] = make_float4(vo[4 * k], vo[4 * k + 1], vo[4 * k + 2], vo[4 * k + 3]);
+      for (int k = 0; k < 2; ++k) {
+        const int g4 = c0 / 4 + k;
+        zb[g4 * kTileM] = make_float4(zo[4 * k], zo[4 * k + 1], zo[4 * k + 2], zo[4 * k + 3]);
+        mb[g4 * kTileM] = make_float4(mo[4 * k], mo[4 * k + 1], mo[4 * k + 2], mo[4 * k + 3]);
+        vb[g4 * kTileM] = make_float4(vo[4 * k], vo[4 * k + 1], vo[4 * k + 2], vo[4 * k + 3]);
       }
-      store_row16w(A1, r, ch * 16, d_pad, w1);
-      if (p.nterms > 1) store_row16w(A1lo, r, ch * 16, d_pad, wl);
-      store_row16w(A2, r, ch * 16, d_pad, w2);
+      store_row8(A1, r, c0, d_pad, w1);
+      if (p.nterms > 1) store_row8(A1lo, r, c0, d_pad, wl);
+      store_row8(A2, r, c0, d_pad, w2);
     }
-    s_pz[split * kTileM + r] = nzinf;
-    s_pk[split * kTileM + r] = nkmax;
+    s_pz[part * kTileM + r] = nzinf;
+    s_pk[part * kTileM + r] = nkmax;
     if (dbg_step) {
-      s_pfr[split * kTileM + r] = frac;
-      if (kId) s_pl1[split * kTileM + r] += l1_id;
+      s_pfr[part * kTileM + r] = frac;
+      if (kId) s_pl1[part * kTileM + r] += l1_id;
     }
     uint32_t fbits = (changed ? kChanged : 0u) | (unexact ? kUnexact : 0u) | (out_id ? kOutId : 0u);
     if (fbits) atomicOr(&s_fl[r], fbits);
@@ -617,9 +609,9 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
     tc_fence_before();
     fence_async_smem();
     __syncthreads();
-    if (dbg_step && split == 0 && active && p.dbg_phi) {
+    if (dbg_step && part == 0 && active && p.dbg_phi) {
       float L1 = 0.f, FR = 0.f;
-      for (int q = 0; q < kSplits; ++q) { L1 += s_pl1[q * kTileM + r]; FR += s_pfr[q * kTileM + r]; }
+      for (int q = 0; q < kParts; ++q) { L1 += s_pl1[q * kTileM + r]; FR += s_pfr[q * kTileM + r]; }
       float inv = zinf > 0.f ? fmaxf(1.f / zinf - 1.f, 0.f) : INFINITY;
       p.dbg_phi[pg] = L1 + p.lambda1 * FR + p.lambda2 * inv;
     }
@@ -652,13 +644,13 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
   }
 }
 
-// [P x d] row-major  <->  blocked [ceil(P/128)][d_pad/4][128][4] (zero padded)
+// [P x d] row-major  <->  blocked [ceil(P/64)][d_pad/4][64][4] (zero padded)
 __global__ void pack_blocked_kernel(const float* __restrict__ in, float* __restrict__ out, int P, int d, int d_pad,
                                     int64_t total) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= total) return;
   const int c = (int)(e & 3);
-  const int r = (int)((e >> 2) & (kTileM - 1));
+  const int r = (int)((e >> 2) % kTileM);
   const int64_t g = e / (4 * kTileM);
   const int g4 = (int)(g % (d_pad / 4));
   const int64_t tile = g / (d_pad / 4);
@@ -766,7 +758,7 @@ int extract_tc(const mape_extract_args* a, cudaStream_t st) {
   mape_detail::launch(pack_blocked_kernel, gpack, 256, 0, st, a->V, Vt, P, d, d_pad, blocked);
   TcParams p{};
   p.B = a->B; p.span = a->span; p.Zt = Zt; p.Mt = Mt; p.Vt = Vt; p.bias = bias;
-  p.n = n; p.d = d; p.P = P; p.n_pad = tile_rows(n, d, id); p.d_pad = pad16(d); p.span_pad = pad16(n);
+  p.n = n; p.d = d; p.P = P; p.n_pad = tile_rows(n, d, id); p.d_pad = d_pad; p.span_pad = pad16(n);
   p.t0 = a->t0; p.T = a->T; p.period = a->period;
   p.lambda1 = a->lambda1; p.lambda2 = a->lambda2; p.lr = a->lr; p.eps = a->eps;
   p.beta1 = (float)a->beta1; p.beta2 = (float)a->beta2;
