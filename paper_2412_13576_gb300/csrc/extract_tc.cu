@@ -16,8 +16,10 @@
 //        B is read through an MN-major descriptor of the same shared tile
 //        (a transposed K-major copy is kept instead when it fits)
 //   grad = G + lambda1 (ceil z + floor z - 2 z) + inverse-norm term; Adam on
-//   the FP32 master z, m, v (blocked [tile][d/4][64][4] in global memory, L2
-//   resident, one 16-byte access per 4 coordinates);
+//   the FP32 master z, m, v, held for the whole run in TMEM lanes 16-31 of
+//   each quarter (the lanes an M=64 accumulator leaves free: z, m, v of the
+//   tile's starts in columns [0, d), [d, 2d), [2d, 3d)) when 3 d_pad <= 512,
+//   else blocked [tile][d/4][64][4] in global memory (L2 resident);
 //   the new bf16(z), bf16(round z) operands are written for the next step.
 // The candidate of step t (D2 of step t+1) is tested (C4, nonzero), signed
 // canonically and appended while the G MMA runs.
@@ -96,6 +98,14 @@ __device__ __forceinline__ void tmem_ld8x2(uint32_t taddr, uint32_t (&r)[8]) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                : "r"(taddr));
 }
+
+// the store of the same shape
+__device__ __forceinline__ void tmem_st8x2(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.16x32bx2.x8.b32 [%0], 8, {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
@@ -213,7 +223,8 @@ __host__ __device__ inline Smem smem_layout(int n_pad, int d_pad, int nterms, in
 // then holds only B' (rows d .. n-1); the identity rows give (Bz)_j = z_j
 // exactly, so their sign, bound test and the first nonzero entry of
 // g = [round z ; B' round z] come from the FP32 master z in the Adam epilogue.
-template <bool kId>
+// kRes: z, m, v live in TMEM lanes 16-31 for the whole launch.
+template <bool kId, bool kRes>
 __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const Smem L = smem_layout(p.n_pad, p.d_pad, p.nterms, p.use_bb, p.span_pad);
@@ -276,6 +287,9 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
   const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+  // upper 16 lanes of the quarter: this thread's start, columns z | m | v
+  const uint32_t st_off = (uint32_t)(quarter * 32 + 16) << 16;
+  const uint32_t col_m = (uint32_t)p.d_pad, col_v = 2u * (uint32_t)p.d_pad;
   bool bail = s_bad != 0;
   if (bail && tid == 0) atomicOr(p.flags, 8);
 
@@ -296,6 +310,22 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
       const float4 q = zb[(c0 / 4 + k) * kTileM];
       zc[4 * k] = q.x; zc[4 * k + 1] = q.y; zc[4 * k + 2] = q.z; zc[4 * k + 3] = q.w;
     }
+    if (kRes) {
+      uint32_t wz[8], wm[8], wv[8];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const float4 qm = mb[(c0 / 4 + k) * kTileM], qv = vb[(c0 / 4 + k) * kTileM];
+        wm[4 * k] = __float_as_uint(qm.x); wm[4 * k + 1] = __float_as_uint(qm.y);
+        wm[4 * k + 2] = __float_as_uint(qm.z); wm[4 * k + 3] = __float_as_uint(qm.w);
+        wv[4 * k] = __float_as_uint(qv.x); wv[4 * k + 1] = __float_as_uint(qv.y);
+        wv[4 * k + 2] = __float_as_uint(qv.z); wv[4 * k + 3] = __float_as_uint(qv.w);
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) wz[c] = __float_as_uint(zc[c]);
+      tmem_st8x2(tmem + st_off + ch * 16, wz);
+      tmem_st8x2(tmem + st_off + col_m + ch * 16, wm);
+      tmem_st8x2(tmem + st_off + col_v + ch * 16, wv);
+    }
     uint32_t wh[4], wl[4];
 #pragma unroll
     for (int c = 0; c < 8; c += 2) {
@@ -315,8 +345,11 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
   }
   s_pz[part * kTileM + r] = zinf_part;
   s_pk[part * kTileM + r] = kmax_part;
+  if (kRes) tc_wait_st();
   fence_async_smem();
+  tc_fence_before();
   __syncthreads();
+  tc_fence_after();
 
   const bool dbg_on = (p.dbg_phi != nullptr || p.dbg_grad != nullptr);
   uint32_t phase = 0;
@@ -530,16 +563,31 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
       const int c0 = ch * 16 + hoff;
       uint32_t v[8];
       tmem_ld8x2(tmem + lane_off + ch * 16, v);  // completes under the global loads below
-      float zc[8], mc[8], vc[8], zo[8], mo[8], vo[8];
+      float zc[8], mc[8], vc[8];
+      uint32_t zo[8], mo[8], vo[8];
+      if (kRes) {
+        uint32_t tz[8], tm[8], tv[8];
+        tmem_ld8x2(tmem + st_off + ch * 16, tz);
+        tmem_ld8x2(tmem + st_off + col_m + ch * 16, tm);
+        tmem_ld8x2(tmem + st_off + col_v + ch * 16, tv);
+        tc_wait_ld();
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int g4 = c0 / 4 + k;
-        const float4 qz = zb[g4 * kTileM], qm = mb[g4 * kTileM], qv = vb[g4 * kTileM];
-        zc[4 * k] = qz.x; zc[4 * k + 1] = qz.y; zc[4 * k + 2] = qz.z; zc[4 * k + 3] = qz.w;
-        mc[4 * k] = qm.x; mc[4 * k + 1] = qm.y; mc[4 * k + 2] = qm.z; mc[4 * k + 3] = qm.w;
-        vc[4 * k] = qv.x; vc[4 * k + 1] = qv.y; vc[4 * k + 2] = qv.z; vc[4 * k + 3] = qv.w;
+        for (int c = 0; c < 8; ++c) {
+          zc[c] = __uint_as_float(tz[c]);
+          mc[c] = __uint_as_float(tm[c]);
+          vc[c] = __uint_as_float(tv[c]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int g4 = c0 / 4 + k;
+          const float4 qz = zb[g4 * kTileM], qm = mb[g4 * kTileM], qv = vb[g4 * kTileM];
+          zc[4 * k] = qz.x; zc[4 * k + 1] = qz.y; zc[4 * k + 2] = qz.z; zc[4 * k + 3] = qz.w;
+          mc[4 * k] = qm.x; mc[4 * k + 1] = qm.y; mc[4 * k + 2] = qm.z; mc[4 * k + 3] = qm.w;
+          vc[4 * k] = qv.x; vc[4 * k + 1] = qv.y; vc[4 * k + 2] = qv.z; vc[4 * k + 3] = qv.w;
+        }
+        tc_wait_ld();
       }
-      tc_wait_ld();
       uint32_t w1[4], wl[4], w2[4];
 #pragma unroll
       for (int c = 0; c < 8; c += 2) {
@@ -564,9 +612,9 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
           const float den = (vv > 0.f ? vv * rsqrtf(vv) : 0.f) * rsb2 + p.eps;
           // padding coordinates (j >= d) have zero gradient and stay at 0
           const float znew = z - step * __fdividef(m, den);
-          zo[cc] = znew;
-          mo[cc] = m;
-          vo[cc] = vv;
+          zo[cc] = __float_as_uint(znew);
+          mo[cc] = __float_as_uint(m);
+          vo[cc] = __float_as_uint(vv);
           zn[q] = znew;
           rn[q] = rintf(znew);
           if (live) {
@@ -585,12 +633,21 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
         wl[c >> 1] = pack_bf16x2(zn[0] - hf.x, zn[1] - hf.y);
         w2[c >> 1] = pack_bf16x2(rn[0], rn[1]);
       }
+      if (kRes) {
+        tmem_st8x2(tmem + st_off + ch * 16, zo);
+        tmem_st8x2(tmem + st_off + col_m + ch * 16, mo);
+        tmem_st8x2(tmem + st_off + col_v + ch * 16, vo);
+      } else {
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int g4 = c0 / 4 + k;
-        zb[g4 * kTileM] = make_float4(zo[4 * k], zo[4 * k + 1], zo[4 * k + 2], zo[4 * k + 3]);
-        mb[g4 * kTileM] = make_float4(mo[4 * k], mo[4 * k + 1], mo[4 * k + 2], mo[4 * k + 3]);
-        vb[g4 * kTileM] = make_float4(vo[4 * k], vo[4 * k + 1], vo[4 * k + 2], vo[4 * k + 3]);
+        for (int k = 0; k < 2; ++k) {
+          const int g4 = c0 / 4 + k;
+          zb[g4 * kTileM] = make_float4(__uint_as_float(zo[4 * k]), __uint_as_float(zo[4 * k + 1]),
+                                        __uint_as_float(zo[4 * k + 2]), __uint_as_float(zo[4 * k + 3]));
+          mb[g4 * kTileM] = make_float4(__uint_as_float(mo[4 * k]), __uint_as_float(mo[4 * k + 1]),
+                                        __uint_as_float(mo[4 * k + 2]), __uint_as_float(mo[4 * k + 3]));
+          vb[g4 * kTileM] = make_float4(__uint_as_float(vo[4 * k]), __uint_as_float(vo[4 * k + 1]),
+                                        __uint_as_float(vo[4 * k + 2]), __uint_as_float(vo[4 * k + 3]));
+        }
       }
       store_row8(A1, r, c0, d_pad, w1);
       if (p.nterms > 1) store_row8(A1lo, r, c0, d_pad, wl);
@@ -606,6 +663,7 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
     if (fbits) atomicOr(&s_fl[r], fbits);
     if (kId && first_id != kNoNz) atomicMin(&s_fnz[r], first_id);
     tc_wait_ld();
+    if (kRes) tc_wait_st();
     tc_fence_before();
     fence_async_smem();
     __syncthreads();
@@ -635,6 +693,26 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
     }
   }
   if (timed_out) mbar_wait_bounded(bar, phase ^ 1);  // let an MMA still in flight drain
+  if (kRes) {  // the state leaves TMEM for the caller's arrays
+    for (int ch = split; ch < dch; ch += kSplits) {
+      const int c0 = ch * 16 + hoff;
+      uint32_t tz[8], tm[8], tv[8];
+      tmem_ld8x2(tmem + st_off + ch * 16, tz);
+      tmem_ld8x2(tmem + st_off + col_m + ch * 16, tm);
+      tmem_ld8x2(tmem + st_off + col_v + ch * 16, tv);
+      tc_wait_ld();
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int g4 = c0 / 4 + k;
+        zb[g4 * kTileM] = make_float4(__uint_as_float(tz[4 * k]), __uint_as_float(tz[4 * k + 1]),
+                                      __uint_as_float(tz[4 * k + 2]), __uint_as_float(tz[4 * k + 3]));
+        mb[g4 * kTileM] = make_float4(__uint_as_float(tm[4 * k]), __uint_as_float(tm[4 * k + 1]),
+                                      __uint_as_float(tm[4 * k + 2]), __uint_as_float(tm[4 * k + 3]));
+        vb[g4 * kTileM] = make_float4(__uint_as_float(tv[4 * k]), __uint_as_float(tv[4 * k + 1]),
+                                      __uint_as_float(tv[4 * k + 2]), __uint_as_float(tv[4 * k + 3]));
+      }
+    }
+  }
   tc_wait_ld();
   tc_fence_before();
   __syncthreads();
@@ -772,13 +850,13 @@ int extract_tc(const mape_extract_args* a, cudaStream_t st) {
   uint32_t smem = smem_layout(p.n_pad, p.d_pad, p.nterms, p.use_bb, p.span_pad).total;
   if (smem < 116 * 1024) smem = 116 * 1024;
   unsigned grid = (unsigned)ceil_div(P, kTileM);
-  if (id) {
-    MAPE_CUDA_TRY(cudaFuncSetAttribute(extract_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    mape_detail::launch(extract_tc_kernel<true>, grid, kThreads, smem, st, p);
-  } else {
-    MAPE_CUDA_TRY(cudaFuncSetAttribute(extract_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    mape_detail::launch(extract_tc_kernel<false>, grid, kThreads, smem, st, p);
-  }
+  // the FP32 state fits in the free TMEM lanes when its three d_pad-wide
+  // blocks fit in 512 columns
+  const bool res = 3 * d_pad <= kTmemCols;
+  auto kern = id ? (res ? extract_tc_kernel<true, true> : extract_tc_kernel<true, false>)
+                 : (res ? extract_tc_kernel<false, true> : extract_tc_kernel<false, false>);
+  MAPE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  mape_detail::launch(kern, grid, kThreads, smem, st, p);
   MAPE_LAUNCH_CHECK();
   const unsigned gun = (unsigned)ceil_div((int64_t)P * d, 256);
   mape_detail::launch(unpack_blocked_kernel, gun, 256, 0, st, Zt, a->Z, P, d, d_pad);
