@@ -50,6 +50,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--cpu-sample", type=int, nargs=2, metavar=("P", "T"), help=argparse.SUPPRESS)
+    ap.add_argument("--kernel-case", type=int, nargs=2, metavar=("P", "T"),
+                    help="time the fused extraction kernel alone on P starts of the workload for T steps "
+                         "(two launches; a small case for profilers) and exit")
     return ap.parse_args(argv)
 
 
@@ -306,63 +309,115 @@ def run_ours(args):
     return result
 
 
-def roofline(mape, inst, starts, stream, args, reps=3):
-    """Times the dominant kernel (the fused extraction launch, T = 1000 steps)
-    alone with CUDA events on its stream; algorithmic work = the dense MMA
-    flops per launch."""
+def time_extract_kernel(mape, inst, G0, P, T, prec, stream, reps):
+    """CUDA-event times (ms, on `stream`) of `reps` + 1 launches of the fused
+    extraction on the first P rows of G0 for T steps from the same projected
+    starts; the first launch is a warm-up and is dropped."""
     import numpy as np
     import torch
-    peaks, src = measured_peaks()
     dev = torch.device("cuda", torch.cuda.current_device())
     B = torch.from_numpy(inst.B).to(dev)
     span = torch.from_numpy((inst.u - inst.l).astype(np.int32)).to(dev)
-    prec = PREC[args.precision]
-    cfg = mape.default_config(T=T_FULL, precision=prec)
+    cfg = mape.default_config(T=T, precision=prec)
     with torch.cuda.stream(stream):
-        Z0 = mape.project_starts(B, torch.from_numpy(starts.G0).to(dev), stream=stream)
+        Z0 = mape.project_starts(B, torch.from_numpy(G0[:P]).to(dev), stream=stream)
     ldc = mape.round16(inst.n)
-    cand = torch.empty((P_FULL * 64, ldc), dtype=torch.int8, device=dev)
+    cand = torch.empty((P * T + 16, ldc), dtype=torch.int8, device=dev)  # every start-step fits
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
     flags = torch.zeros(1, dtype=torch.int32, device=dev)
-    ws = torch.empty(mape.lib().mape_extract_workspace_bytes(inst.n, inst.d, P_FULL, prec), dtype=torch.uint8,
+    ws = torch.empty(mape.lib().mape_extract_workspace_bytes(inst.n, inst.d, P, prec), dtype=torch.uint8,
                      device=dev)
-    times = []
+    times, counts = [], []
     for i in range(reps + 1):
         Z = Z0.clone()
         Mm = torch.zeros_like(Z)
         V = torch.zeros_like(Z)
         cnt.zero_()
+        flags.zero_()
         stream.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        mape.extract(B, span, Z, Mm, V, t0=0, T=T_FULL, cfg=cfg, cand=cand, cand_count=cnt, flags=flags, ldc=ldc,
+        mape.extract(B, span, Z, Mm, V, t0=0, T=T, cfg=cfg, cand=cand, cand_count=cnt, flags=flags, ldc=ldc,
                      workspace=ws, stream=stream)
         e1.record(stream)
         stream.synchronize()
+        if int(flags.item()) != 0:
+            raise RuntimeError(f"extraction flags {int(flags.item())}")
         if i > 0:
             times.append(e0.elapsed_time(e1))
+            counts.append(int(cnt.item()))
+    return times, counts
+
+
+def kernel_case(args):
+    """The fused extraction alone on a small case (P starts, T steps): the
+    command profilers run."""
+    import torch
+    from paper_2412_13576_gb300 import instances as I
+    from paper_2412_13576_gb300 import mape
+    torch.cuda.set_device(0)
+    mape.lib(build_if_missing=True)
+    inst = I.medium_sparse()
+    P, T = args.kernel_case
+    starts = I.uniform_samples(inst, P_FULL, seed=2002)
+    stream = torch.cuda.Stream()
+    times, counts = time_extract_kernel(mape, inst, starts.G0, P, T, PREC[args.precision], stream, reps=1)
+    return {"kernel_case": {"workload": "medium_sparse", "P": P, "T": T, "precision": args.precision,
+                            "ms_per_launch": times, "candidates": counts}}
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "extract_tc_kernel_medium_sparse_P8192_T1000_traffic.md")
+
+
+def measured_traffic(src_path):
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    record, if that record was taken on the current source (same SHA-256)."""
+    import hashlib
+    import re
+    try:
+        text = open(TRAFFIC_FILE).read()
+        sha = hashlib.sha256(open(src_path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != sha:
+        return None
+    return int(m_b.group(1))
+
+
+def roofline(mape, inst, starts, stream, args, reps=3):
+    """The dominant kernel, the fused extraction launch (T = 1000 steps), timed
+    alone with CUDA events on its stream.  Its state (z, m, v) stays on chip
+    for the whole launch, so the bound is the tensor-core roofline and the
+    algorithmic work is the dense contraction count per start and step:
+    B.z (2nd), B^T.sign(Bz) (2nd) and B.round(z) (2nd)."""
+    peaks, src = measured_peaks()
+    prec = PREC[args.precision]
+    times, _ = time_extract_kernel(mape, inst, starts.G0, P_FULL, T_FULL, prec, stream, reps)
     ms = statistics.median(times)
     n, d, m = inst.n, inst.d, inst.n - inst.d
     if prec == 0:
         return {"kernel": "extract_fp32 (3 kernels per step)", "bound": "alu", "ms": ms}
     nterms = 2 if prec == 1 else 1
-    # algorithmic bytes: the FP32 master z, m, v read and written once per
-    # coordinate, start and step (24 d bytes per start-step)
-    state_bytes = 24.0 * d * P_FULL * T_FULL
-    achieved = state_bytes / (ms / 1e3) / 1e9
-    peak = peaks["hbm_gbs"]
-    # MMA work actually issued: the basis is [I; -C], so the tensor cores
-    # contract the m = n - d rows of -C (nterms forward terms, B round(z), gradient)
+    flops = 6.0 * n * d * P_FULL * T_FULL
+    achieved = flops / (ms / 1e3) / 1e12
+    peak = peaks["bf16_tflops"]
+    # what the tensor pipe actually issues: the basis is [I; -C], so only the
+    # m = n - d rows of -C are contracted (nterms forward terms, B round(z), gradient)
     mma_flops = 2.0 * m * d * P_FULL * T_FULL * (nterms + 2)
-    return {"bound": "hbm", "kernel": "extract_tc_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "ms_per_launch": ms, "bytes_per_launch": state_bytes,
-            "peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-            "tensor_tflops": mma_flops / (ms / 1e3) / 1e12,
-            "tensor_frac_of_bf16_burst": mma_flops / (ms / 1e3) / 1e12 / peaks["bf16_tflops"],
-            "note": "one launch = T=1000 steps for P=8192 starts; algorithmic bytes = 24*d per start-step "
-                    "(FP32 z, m, v read + write); the 15.7 MB state stays in L2, so HBM is the bound of "
-                    "the traffic, not the wire it uses; the launch includes its 6 layout kernels (<0.1%)"}
+    src_path = os.path.join(ROOT, "paper_2412_13576_gb300", "csrc", "extract_tc.cu")
+    return {"bound": "tensor", "kernel": "extract_tc_kernel", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": measured_traffic(src_path), "ms_per_launch": ms,
+            "flops_per_launch": flops,
+            "peak_source": f"{src} cuBLAS BF16 dense burst (MEASURED_PEAKS.json bf16_tflops)",
+            "issued_mma_tflops": mma_flops / (ms / 1e3) / 1e12,
+            "state_bytes_per_s": 24.0 * d * P_FULL * T_FULL / (ms / 1e3),
+            "note": "one launch = T=1000 steps for P=8192 starts; algorithmic work = 6*n*d flops per start-step "
+                    "(B z, B^T sign(Bz), B round(z) as dense products); z, m, v stay in TMEM for the launch, so "
+                    "HBM carries only the state in and out and the candidates; traffic = ncu dram read+write "
+                    "bytes of one full launch, null unless taken on this source"}
 
 
 def plain_fp32(mape, inst, G0, x0, stream):
@@ -417,6 +472,9 @@ def main(argv=None):
     args = parse_args(argv)
     if args.cpu_sample:
         cpu_sample(*args.cpu_sample)
+        return 0
+    if args.kernel_case:
+        print(json.dumps(kernel_case(args)), flush=True)
         return 0
     res = run_reference(args) if args.impl == "reference" else run_ours(args)
     if res is not None:
