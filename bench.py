@@ -50,6 +50,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--cpu-sample", type=int, nargs=2, metavar=("P", "T"), help=argparse.SUPPRESS)
+    ap.add_argument("--streamed-case", nargs=3, metavar=("NAME", "P", "T"),
+                    help="time the streamed tensor-core extraction on a named instance (large: n=2000 m=400; "
+                         "uneven1000: n=1000 m=200) for P starts and T steps, and exit")
     ap.add_argument("--kernel-case", type=int, nargs=2, metavar=("P", "T"),
                     help="time the fused extraction kernel alone on P starts of the workload for T steps "
                          "(two launches; a small case for profilers) and exit")
@@ -367,6 +370,38 @@ def kernel_case(args):
                             "ms_per_launch": times, "candidates": counts}}
 
 
+STREAMED_CASES = {"large": "large_quartic", "uneven1000": "uneven1000"}
+
+
+def streamed_case(args):
+    """The streamed kernels (three per step) alone on a named instance: per
+    step, the forward pass reads z (4 d bytes per start) and writes sign(Bm z)
+    (2 R bytes), the gradient pass reads it back and reads and writes z, m, v
+    (24 d bytes): the algorithmic bytes are 28 d + 4 R per start-step."""
+    import numpy as np
+    import torch
+    from paper_2412_13576_gb300 import instances as I
+    from paper_2412_13576_gb300 import mape
+    torch.cuda.set_device(0)
+    mape.lib(build_if_missing=True)
+    name, P, T = args.streamed_case[0], int(args.streamed_case[1]), int(args.streamed_case[2])
+    inst = I.large_quartic() if name == "large" else I.uneven_single(1000, density=0.05)
+    prec = PREC[args.precision] | mape.PREC_STREAMED
+    G0 = I.uniform_samples(inst, P, seed=2004).G0
+    stream = torch.cuda.Stream()
+    times, counts = time_extract_kernel(mape, inst, G0, P, T, prec, stream, reps=2)
+    ms = statistics.median(times)
+    R = inst.n - inst.d
+    algo = (28.0 * inst.d + 4.0 * R) * P * T
+    peaks, src = measured_peaks()
+    gbs = algo / (ms / 1e3) / 1e9
+    return {"streamed_case": {"instance": inst.name, "n": inst.n, "d": inst.d, "P": P, "T": T,
+                              "precision": args.precision, "ms_per_call": times, "ms_per_step": ms / T,
+                              "candidates": counts, "algorithmic_bytes_per_call": algo, "achieved_gbs": gbs,
+                              "hbm_peak_gbs": peaks["hbm_gbs"], "frac_of_hbm": gbs / peaks["hbm_gbs"],
+                              "peak_source": src}}
+
+
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "extract_tc_kernel_medium_sparse_P8192_T1000_traffic.md")
 
 
@@ -475,6 +510,9 @@ def main(argv=None):
         return 0
     if args.kernel_case:
         print(json.dumps(kernel_case(args)), flush=True)
+        return 0
+    if args.streamed_case:
+        print(json.dumps(streamed_case(args)), flush=True)
         return 0
     res = run_reference(args) if args.impl == "reference" else run_ours(args)
     if res is not None:

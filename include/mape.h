@@ -65,6 +65,18 @@ extern "C" {
                              accurate to about FP32                             */
 #define MAPE_PREC_BF16X1 2 /* as MAPE_PREC_BF16 with z as one BF16 term (hi):
                              half the forward MMAs, 8-bit z in B z            */
+/* The BF16 precisions run one of two tensor-core implementations, with the
+ * same arithmetic per step:
+ *   resident: one persistent fused kernel for all T steps, B and the tile's
+ *             z, m, v on chip; for tiles that fit (rows of B through the MMA
+ *             and d at most 256, the operands within shared memory);
+ *   streamed: three kernels per step (forward + map, collect, gradient +
+ *             Adam) over tiles of 128 starts, with B and the state streamed
+ *             through shared memory by bulk copies; any n, d <= 4096.
+ * The resident kernel is chosen when it fits; OR-ing MAPE_PREC_STREAMED into
+ * the precision forces the streamed one. */
+#define MAPE_PREC_STREAMED 0x100
+#define MAPE_PREC_MASK 0xff
 
 /* ---- hyper-parameters (§3.2, §4: lambda1 = 0.85, lambda2 = 1, lr = 0.003) - */
 typedef struct {
@@ -164,8 +176,10 @@ typedef struct {
   void* workspace;
   size_t workspace_bytes;
 } mape_extract_args;
-/* Errors: INVALID_ARG, SHAPE (BF16 path: n > 256 or d > 256 or the operand
- * tiles exceed shared memory), CAPACITY (workspace), CUDA.  Asynchronous. */
+/* Errors: INVALID_ARG, SHAPE (n or d above 4096 on the BF16 paths; n above
+ * 49152 on the FP32 path), CAPACITY (workspace), CUDA.  Asynchronous, except
+ * that the BF16 paths synchronise `stream` once to inspect B (identity top,
+ * exactness) before the steps are queued. */
 size_t mape_extract_workspace_bytes(int32_t n, int32_t d, int32_t P, int32_t precision);
 int mape_extract(const mape_extract_args* args, void* stream);
 

@@ -14,4 +14,8 @@ int extract_fp32(const mape_extract_args* a, cudaStream_t st);
 size_t extract_tc_workspace(int32_t n, int32_t d, int32_t P, int32_t precision);
 bool extract_tc_supported(int32_t n, int32_t d, int32_t precision);
 int extract_tc(const mape_extract_args* a, cudaStream_t st);
+
+bool extract_stream_supported(int32_t n, int32_t d);
+size_t extract_stream_workspace(int32_t n, int32_t d, int32_t P);
+int extract_stream(const mape_extract_args* a, cudaStream_t st);
 }  // namespace mape_detail

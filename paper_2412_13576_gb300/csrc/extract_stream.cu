@@ -1,0 +1,773 @@
+// Algorithm 2 (§3.2) on the tensor cores for shapes whose per-tile state and
+// basis do not fit on chip (rows of the MMA tile or d above 256, e.g. n = 2000,
+// d = 1600): the "streamed" path.  The fused kernel keeps B and a tile's
+// z, m, v on chip for all T steps; here every step streams them.
+//
+// Per step, three kernels over tiles of 128 starts (M = 128 MMAs, FP32
+// accumulators in TMEM), with Bm the rows of B that go through the tensor
+// cores (the m rows of B' below an identity top, else all n rows):
+//   forward  (grid: tile x 256-row block of Bm)  D1 = hi(Z) Bm^T + lo(Z) Bm^T,
+//            K = d streamed in chunks of 64 coordinates: z is read from the
+//            blocked FP32 state and split into BF16 operands in shared memory,
+//            the Bm chunk arrives by a bulk (TMA) copy; S = sign(D1) is written
+//            as the BF16 A operand of the gradient.  On collection steps the
+//            same pass forms D2 = round(Z) Bm^T (exact: |round z| <= 256, integer
+//            partial sums below 2^24) and stages the candidate rows.
+//   collect  (one warp per start) the C4, nonzero and changed tests, a slot in
+//            the candidate buffer, the row in canonical sign.
+//   gradient (grid: tile x 256-coordinate block)  G = S Bm, K = rows of Bm in
+//            chunks of 64, both operands by bulk copy into a two-stage ring
+//            (one producer thread, one MMA thread); the epilogue adds the
+//            identity rows, lambda1 (ceil z + floor z - 2 z) and the inverse-norm
+//            term and runs Adam on the FP32 master z, m, v (read and written
+//            once per step), forming the per-start reductions of the next step
+//            (||z||_inf and its first index, rounding changed, bound test and
+//            first nonzero entry of the identity rows) with atomics.
+// Operand chunks use the no-swizzle K-major layout of tc_ptx.cuh.  Every
+// mbarrier wait is bounded (2 s); on time-out the CTA sets flag 16, skips its
+// outputs, drains what it issued and frees its TMEM.
+#include "common.cuh"
+#include "extract_internal.cuh"
+#include "tc_ptx.cuh"
+
+#include <cmath>
+#include <vector>
+
+namespace {
+using namespace mape_tc;
+
+constexpr int kTM = 128;       // starts per tile: the MMA M
+constexpr int kThreads = 256;  // 8 warps: two per TMEM lane quarter
+constexpr int kKC = 64;        // K chunk
+constexpr int kNB = 256;       // N block: the largest MMA N
+constexpr int kChunkA = kTM * kKC * 2;        // one 128 x 64 BF16 operand chunk (16 KB)
+constexpr int kFStage = 3 * kChunkA + kNB * kKC * 2;  // hi, lo, round(z), Bm chunk
+constexpr int kFSmem = 2 * kFStage;
+constexpr int kGStage = kChunkA + kNB * kKC * 2;      // S chunk, Bm chunk
+constexpr int kGSmem = 2 * kGStage;
+constexpr int kNoNz = 0x7fffffff;
+constexpr uint32_t kChanged = 1, kUnexact = 2;
+
+struct StParams {
+  int n, d, P, R;       // R: rows of Bm
+  int r0;               // row of B held in row 0 of Bm (d for an identity top, else 0)
+  int d64, R64;         // padded to the K chunk
+  int tiles, nbF, nbG;  // tiles of 128 starts; N blocks over R64 and d64
+  int ldc, mapoff, lds; // candidate pitch; offset of the Bm rows in a staged row; staged pitch
+  const uint8_t* BmF;   // forward B operand: [nbF][d64/64][N x 64] chunks (N = Bm rows)
+  const uint8_t* BmG;   // gradient B operand: [nbG][R64/64][N x 64] chunks (N = coordinates)
+  const int32_t* span;
+  float* Zt;
+  float* Mt;
+  float* Vt;            // blocked [tiles][d64/4][128][4]
+  uint8_t* S;           // [tiles][R64/64] chunks of sign(Bm z), 128 x 64 BF16
+  int8_t* stage;        // [tiles*128][lds] staged candidate rows
+  unsigned long long* zkey;  // [2][tiles*128]: (|z|_inf bits << 32) | (~first argmax)
+  uint32_t* acc;        // rounding changed / unexact since the last collection
+  uint32_t* oob;        // Bm rows of the staged candidate out of the box (C4)
+  uint32_t* idw;        // [2][..] identity rows of round(z) out of the box
+  int32_t* first;       // [2][..] first nonzero entry of round(z) on the identity rows
+  int32_t* first_map;   // general B: first nonzero entry of B round(z)
+  const float2* bias;   // (lr / (1 - beta1^t), 1 / sqrt(1 - beta2^t)) per step
+  float lambda1, lambda2, eps, beta1, beta2, omb1, omb2;
+  int nterms;
+  int8_t* cand;
+  int64_t cap;
+  unsigned long long* count;
+  int32_t* flags;
+  float* dbg_phi;
+  float* dbg_grad;
+};
+
+__device__ __forceinline__ int ptot(const StParams& p) { return p.tiles * kTM; }
+
+// ---------------------------------------------------------------- forward
+
+template <bool kId>
+__global__ void __launch_bounds__(kThreads, 1) stream_fwd_kernel(StParams p, int s, int fwd, int collect) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bars[4];  // full[2], done[2]
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile = blockIdx.x / p.nbF, rb = blockIdx.x % p.nbF;
+  const int N = rb < p.nbF - 1 ? kNB : p.R64 - kNB * (p.nbF - 1);
+  const int row0 = rb * kNB;
+  const int nk = p.d64 / kKC;
+  const int P2 = ptot(p);
+  const uint32_t full0 = smem_u32(&bars[0]), done0 = smem_u32(&bars[2]);
+  if (*(volatile int32_t*)p.flags & 16) return;  // an earlier CTA timed out: the call is abandoned
+
+  // buffers of the next step's per-start reductions start empty
+  if (rb == 0 && tid < kTM) {
+    const int pg = tile * kTM + tid;
+    const int nb = ((s + 1) & 1) * P2 + pg;
+    p.zkey[nb] = 0ull;
+    p.idw[nb] = 0u;
+    p.first[nb] = kNoNz;
+  }
+  if (tid == 0) {
+    mbar_init(full0, 1); mbar_init(full0 + 8, 1);
+    mbar_init(done0, 1); mbar_init(done0 + 8, 1);
+    s_abort = 0;
+  }
+  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), 512);
+  mbar_init_fence();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t idesc = idesc_bf16(kTM, N);
+  bool ok = true;
+  int issued_copies = 0, issued_commits = 0;  // thread 0 only
+
+  for (int c = 0; c < nk; ++c) {
+    const int stg = c & 1;
+    uint8_t* Ahi = smem + stg * kFStage;
+    uint8_t* Alo = Ahi + kChunkA;
+    uint8_t* Ard = Alo + kChunkA;
+    uint8_t* Bc = Ard + kChunkA;
+    if (c >= 2) {  // the MMAs of chunk c - 2 read this stage
+      const bool w = mbar_wait_bounded(done0 + 8 * stg, ((c - 2) >> 1) & 1);
+      if (__syncthreads_or(!w || s_abort)) { ok = false; break; }
+    }
+    if (tid == 0) {
+      mbar_arrive_expect_tx(full0 + 8 * stg, (uint32_t)N * kKC * 2);
+      bulk_g2s(smem_u32(Bc), p.BmF + ((size_t)rb * kNB * p.d64 + (size_t)c * N * kKC) * 2, (uint32_t)N * kKC * 2,
+               full0 + 8 * stg);
+      ++issued_copies;
+    }
+    // z chunk -> BF16 operands: item e covers 8 coordinates of one start;
+    // a warp writes 512 contiguous bytes of each operand
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + kThreads * i;
+      const int r = (e & 7) | ((e >> 6) << 3);
+      const int kc = (e >> 3) & 7;
+      const float4* zt = reinterpret_cast<const float4*>(p.Zt) +
+                         ((size_t)tile * (p.d64 / 4) + (size_t)c * (kKC / 4) + 2 * kc) * kTM + r;
+      const float4 q0 = zt[0], q1 = zt[kTM];
+      const float z8[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+      const uint32_t o = chunk_off(r, kc * 8);
+      if (fwd) {
+        uint32_t wh[4], wl[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          wh[k] = pack_bf16x2(z8[2 * k], z8[2 * k + 1]);
+          const float2 hf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wh[k]));
+          wl[k] = pack_bf16x2(z8[2 * k] - hf.x, z8[2 * k + 1] - hf.y);
+        }
+        *reinterpret_cast<uint4*>(Ahi + o) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+        if (p.nterms > 1) *reinterpret_cast<uint4*>(Alo + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+      }
+      if (collect) {
+        uint32_t wr[4];
+        float rz[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) rz[k] = rintf(z8[k]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) wr[k] = pack_bf16x2(rz[2 * k], rz[2 * k + 1]);
+        *reinterpret_cast<uint4*>(Ard + o) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+        // identity rows of the candidate: g_j = round z_j
+        const int64_t pg = (int64_t)tile * kTM + r;
+        const int j0 = c * kKC + kc * 8;
+        if (kId && rb == 0 && pg < p.P && j0 < p.d) {
+          int8_t* row = p.stage + pg * p.lds;
+          if (j0 + 8 <= p.d) {
+            uint32_t b[2] = {0, 0};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) b[k >> 2] |= ((uint32_t)((int)rz[k] & 0xff)) << (8 * (k & 3));
+            *reinterpret_cast<uint2*>(row + j0) = make_uint2(b[0], b[1]);
+          } else {
+            for (int k = 0; j0 + k < p.d; ++k) row[j0 + k] = (int8_t)(int)rz[k];
+          }
+        }
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0 && !s_abort) {
+      if (!mbar_wait_bounded(full0 + 8 * stg, (c >> 1) & 1)) {
+        s_abort = 1;
+      } else {
+        tc_fence_after();
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t b = make_desc(smem_u32(Bc) + kk * 256, kChunkLbo, kChunkSbo);
+          const uint32_t a0 = (c | kk) ? 1u : 0u;
+          if (fwd) {
+            mma_bf16(tmem, make_desc(smem_u32(Ahi) + kk * 256, kChunkLbo, kChunkSbo), b, idesc, a0);
+            if (p.nterms > 1) mma_bf16(tmem, make_desc(smem_u32(Alo) + kk * 256, kChunkLbo, kChunkSbo), b, idesc, 1u);
+          }
+          if (collect) mma_bf16(tmem + 256, make_desc(smem_u32(Ard) + kk * 256, kChunkLbo, kChunkSbo), b, idesc, a0);
+        }
+        mma_commit(done0 + 8 * stg);
+        ++issued_commits;
+      }
+    }
+  }
+  if (ok) {
+    const int cl = nk - 1;
+    const bool w = mbar_wait_bounded(done0 + 8 * (cl & 1), (cl >> 1) & 1);
+    if (__syncthreads_or(!w || s_abort)) ok = false;
+  }
+
+  if (ok) {
+    tc_fence_after();
+    const int q = warp & 3, h = warp >> 2;
+    const int r = q * 32 + lane;
+    const int64_t pg = (int64_t)tile * kTM + r;
+    const bool live = pg < p.P;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    float l1 = 0.f;
+    bool out = false;
+    int firstc = kNoNz;
+    for (int ch = h; ch < N / 16; ch += 2) {
+      uint32_t v[16];
+      if (fwd) {
+        tmem_ld16(tmem + lane_base + ch * 16, v);
+        tc_wait_ld();
+        uint32_t w[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float y0 = __uint_as_float(v[2 * k]), y1 = __uint_as_float(v[2 * k + 1]);
+          w[k] = pack_bf16x2((float)mape_sign_f(y0), (float)mape_sign_f(y1));
+          l1 += fabsf(y0) + fabsf(y1);
+        }
+        const int kg = row0 + ch * 16;  // column of S: row of Bm
+        uint8_t* Sp = p.S + ((size_t)tile * (p.R64 / kKC) + kg / kKC) * kChunkA;
+        *reinterpret_cast<uint4*>(Sp + chunk_off(r, kg % kKC)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(Sp + chunk_off(r, kg % kKC + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
+      }
+      if (collect) {
+        tmem_ld16(tmem + lane_base + 256 + ch * 16, v);
+        tc_wait_ld();
+        const int i0 = row0 + ch * 16;
+        uint32_t pk[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int i = i0 + k;
+          const int g = __float2int_rn(__uint_as_float(v[k]));
+          if (i < p.R) {
+            const int row = p.r0 + i;
+            const int sp = p.span[row];
+            if (g > sp || -g > sp) out = true;
+            if (!kId && g != 0 && (row << 1) < firstc) firstc = (row << 1) | (g < 0 ? 1 : 0);
+          }
+          pk[k >> 2] |= ((uint32_t)(g & 0xff)) << (8 * (k & 3));
+        }
+        // padding rows of Bm are zero, so their entries are 0
+        if (live) *reinterpret_cast<uint4*>(p.stage + pg * p.lds + p.mapoff + i0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+    }
+    if (live) {
+      if (out) atomicOr(&p.oob[pg], 1u);
+      if (!kId && firstc != kNoNz) atomicMin(&p.first_map[pg], firstc);
+      if (fwd && s == 0 && p.dbg_phi) atomicAdd(&p.dbg_phi[pg], l1);
+    }
+  } else if (tid == 0) {
+    atomicOr(p.flags, 16);
+  }
+  if (!ok && tid == 0) {  // drain what this thread issued before the memory goes away
+    for (int c = 0; c < issued_copies; ++c) mbar_wait_bounded(full0 + 8 * (c & 1), (c >> 1) & 1);
+    if (issued_commits > 0) {
+      const int cl = issued_commits - 1;
+      mbar_wait_bounded(done0 + 8 * (cl & 1), (cl >> 1) & 1);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ---------------------------------------------------------------- collect
+
+template <bool kId>
+__global__ void stream_collect_kernel(StParams p, int s) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t pg = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (pg >= p.P) return;
+  const int P2 = ptot(p);
+  long long slot = -1;
+  int neg = 0;
+  if (lane == 0) {
+    const uint32_t a = p.acc[pg], o = p.oob[pg];
+    const uint32_t idout = kId ? p.idw[(s & 1) * P2 + pg] : 0u;
+    const int fz = kId ? p.first[(s & 1) * P2 + pg] : p.first_map[pg];
+    if ((a & kChanged) && !o && !idout && fz != kNoNz) {
+      if (a & kUnexact) {
+        atomicOr(p.flags, 2);
+      } else {
+        const unsigned long long at = atomicAdd(p.count, 1ull);
+        if ((int64_t)at < p.cap) slot = (long long)at;
+        else atomicOr(p.flags, 1);
+      }
+    }
+    neg = (fz != kNoNz && (fz & 1)) ? 1 : 0;
+    p.acc[pg] = 0u;
+    p.oob[pg] = 0u;
+    if (!kId) p.first_map[pg] = kNoNz;
+  }
+  slot = __shfl_sync(0xffffffffu, slot, 0);
+  neg = __shfl_sync(0xffffffffu, neg, 0);
+  if (slot < 0) return;
+  const int8_t* src = p.stage + pg * p.lds;
+  int8_t* dst = p.cand + slot * p.ldc;
+  for (int b = lane; b < p.ldc; b += 32) {
+    int v = 0;
+    if (b < p.n) v = (kId && b >= p.d) ? src[p.mapoff + (b - p.d)] : src[b];
+    dst[b] = (int8_t)(neg ? -v : v);
+  }
+}
+
+// ---------------------------------------------------------------- gradient + Adam
+
+template <bool kId>
+__global__ void __launch_bounds__(kThreads, 1) stream_grad_kernel(StParams p, int s) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bars[5];  // full[2], done[2], accumulator ready
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile = blockIdx.x / p.nbG, db = blockIdx.x % p.nbG;
+  const int N = db < p.nbG - 1 ? kNB : p.d64 - kNB * (p.nbG - 1);
+  const int col0 = db * kNB;
+  const int nk = p.R64 / kKC;
+  const int P2 = ptot(p);
+  const uint32_t full0 = smem_u32(&bars[0]), done0 = smem_u32(&bars[2]), accr = smem_u32(&bars[4]);
+  if (*(volatile int32_t*)p.flags & 16) return;  // an earlier CTA timed out: the call is abandoned
+
+  if (tid == 0) {
+    mbar_init(full0, 1); mbar_init(full0 + 8, 1);
+    mbar_init(done0, 1); mbar_init(done0 + 8, 1);
+    mbar_init(accr, 1);
+    s_abort = 0;
+  }
+  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), 256);
+  mbar_init_fence();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  int copies = 0, commits = 0;  // issued by the producer / MMA thread
+
+  if (warp == 0 && lane == 0) {  // producer: both operands of chunk c by bulk copy
+    for (int c = 0; c < nk; ++c) {
+      const int stg = c & 1;
+      if (c >= 2 && !mbar_wait_bounded(done0 + 8 * stg, ((c - 2) >> 1) & 1)) {
+        s_abort = 1;
+        break;
+      }
+      if (*(volatile int*)&s_abort) break;
+      uint8_t* A = smem + stg * kGStage;
+      uint8_t* Bc = A + kChunkA;
+      mbar_arrive_expect_tx(full0 + 8 * stg, (uint32_t)(kChunkA + N * kKC * 2));
+      bulk_g2s(smem_u32(A), p.S + ((size_t)tile * nk + c) * kChunkA, kChunkA, full0 + 8 * stg);
+      bulk_g2s(smem_u32(Bc), p.BmG + ((size_t)db * kNB * p.R64 + (size_t)c * N * kKC) * 2, (uint32_t)N * kKC * 2,
+               full0 + 8 * stg);
+      ++copies;
+    }
+  } else if (warp == 1 && lane == 0) {  // MMA issuer
+    const uint32_t idesc = idesc_bf16(kTM, N);
+    int c = 0;
+    for (; c < nk; ++c) {
+      const int stg = c & 1;
+      if (*(volatile int*)&s_abort || !mbar_wait_bounded(full0 + 8 * stg, (c >> 1) & 1)) {
+        s_abort = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t A = smem_u32(smem + stg * kGStage), Bc = A + kChunkA;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        mma_bf16(tmem, make_desc(A + kk * 256, kChunkLbo, kChunkSbo), make_desc(Bc + kk * 256, kChunkLbo, kChunkSbo),
+                 idesc, (c | kk) ? 1u : 0u);
+      mma_commit(done0 + 8 * stg);
+      ++commits;
+    }
+    if (c == nk) mma_commit(accr);
+  }
+  __syncwarp();
+  const bool w = mbar_wait_bounded(accr, 0);
+  const bool ok = !__syncthreads_or(!w || s_abort);
+
+  if (ok) {
+    tc_fence_after();
+    const int q = warp & 3, h = warp >> 2;
+    const int r = q * 32 + lane;
+    const int64_t pg = (int64_t)tile * kTM + r;
+    const bool row_live = pg < p.P;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const unsigned long long zk = p.zkey[(s & 1) * P2 + pg];
+    const float zinf = __uint_as_float((uint32_t)(zk >> 32));
+    const int kmax = zk ? (int)(0xffffffffu - (uint32_t)zk) : -1;
+    float inv_term = 0.f;
+    if (zinf < 1.f && zinf > 0.f) inv_term = -p.lambda2 / (zinf * zinf);  // times sign(z_kmax)
+    const float2 ad = p.bias[s];
+    const float step = ad.x, rsb2 = ad.y;
+    const bool dbg = s == 0 && (p.dbg_phi || p.dbg_grad);
+    float nzinf = 0.f, frac = 0.f, l1_id = 0.f;
+    int nkmax = kNoNz, first_id = kNoNz;
+    bool changed = false, unexact = false, out_id = false;
+    float4* const zt = reinterpret_cast<float4*>(p.Zt) + (size_t)tile * (p.d64 / 4) * kTM + r;
+    float4* const mt = reinterpret_cast<float4*>(p.Mt) + (size_t)tile * (p.d64 / 4) * kTM + r;
+    float4* const vt = reinterpret_cast<float4*>(p.Vt) + (size_t)tile * (p.d64 / 4) * kTM + r;
+    for (int ch = h; ch < N / 16; ch += 2) {
+      const int j0 = col0 + ch * 16;
+      uint32_t gv[16];
+      tmem_ld16(tmem + lane_base + ch * 16, gv);
+      float zc[16], mc[16], vc[16];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const size_t g4 = (size_t)(j0 / 4 + k) * kTM;
+        const float4 qz = zt[g4], qm = mt[g4], qv = vt[g4];
+        zc[4 * k] = qz.x; zc[4 * k + 1] = qz.y; zc[4 * k + 2] = qz.z; zc[4 * k + 3] = qz.w;
+        mc[4 * k] = qm.x; mc[4 * k + 1] = qm.y; mc[4 * k + 2] = qm.z; mc[4 * k + 3] = qm.w;
+        vc[4 * k] = qv.x; vc[4 * k + 1] = qv.y; vc[4 * k + 2] = qv.z; vc[4 * k + 3] = qv.w;
+      }
+      tc_wait_ld();
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int j = j0 + k;
+        const bool live = row_live && j < p.d;
+        const float z = zc[k];
+        const float fl = floorf(z);
+        // ceil z + floor z = 2 floor z + [z not an integer]
+        float grad = __uint_as_float(gv[k]) + p.lambda1 * (2.f * fl + (z != fl ? 1.f : 0.f) - 2.f * z);
+        if (j == kmax) grad += inv_term * (float)mape_sign_f(z);
+        if (kId) grad += (float)mape_sign_f(z);  // identity row j of B: sign((Bz)_j) = sign(z_j)
+        if (dbg && live) {
+          frac += (z - fl) * (ceilf(z) - z);
+          if (kId) l1_id += fabsf(z);
+          if (p.dbg_grad) p.dbg_grad[pg * p.d + j] = grad;
+        }
+        const float m = p.beta1 * mc[k] + p.omb1 * grad;
+        const float vv = p.beta2 * vc[k] + p.omb2 * grad * grad;
+        const float den = (vv > 0.f ? vv * rsqrtf(vv) : 0.f) * rsb2 + p.eps;
+        const float znew = z - step * __fdividef(m, den);  // padding coordinates stay at 0
+        zc[k] = znew;
+        mc[k] = m;
+        vc[k] = vv;
+        if (live) {
+          const float rn = rintf(znew);
+          changed |= rn != rintf(z);
+          unexact |= fabsf(rn) > 256.f;
+          const float a = fabsf(znew);
+          if (nkmax == kNoNz || a > nzinf) { nzinf = a; nkmax = j; }
+          if (kId) {
+            out_id |= fabsf(rn) > (float)p.span[j];
+            if (first_id == kNoNz && rn != 0.f) first_id = (j << 1) | (rn < 0.f ? 1 : 0);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const size_t g4 = (size_t)(j0 / 4 + k) * kTM;
+        zt[g4] = make_float4(zc[4 * k], zc[4 * k + 1], zc[4 * k + 2], zc[4 * k + 3]);
+        mt[g4] = make_float4(mc[4 * k], mc[4 * k + 1], mc[4 * k + 2], mc[4 * k + 3]);
+        vt[g4] = make_float4(vc[4 * k], vc[4 * k + 1], vc[4 * k + 2], vc[4 * k + 3]);
+      }
+    }
+    if (row_live) {
+      const int nb = ((s + 1) & 1) * P2 + (int)pg;
+      if (nkmax != kNoNz)
+        atomicMax(&p.zkey[nb], ((unsigned long long)__float_as_uint(nzinf) << 32) | (0xffffffffu - (uint32_t)nkmax));
+      const uint32_t fb = (changed ? kChanged : 0u) | (unexact ? kUnexact : 0u);
+      if (fb) atomicOr(&p.acc[pg], fb);
+      if (kId) {
+        if (out_id) atomicOr(&p.idw[nb], 1u);
+        if (first_id != kNoNz) atomicMin(&p.first[nb], first_id);
+      }
+      if (dbg && p.dbg_phi) {
+        float add = p.lambda1 * frac + l1_id;
+        if (db == 0 && h == 0) add += p.lambda2 * (zinf > 0.f ? fmaxf(1.f / zinf - 1.f, 0.f) : INFINITY);
+        atomicAdd(&p.dbg_phi[pg], add);
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(p.flags, 16);
+  }
+  if (!ok) {  // drain what the producer and the MMA thread issued
+    if (warp == 0 && lane == 0)
+      for (int c = 0; c < copies; ++c) mbar_wait_bounded(full0 + 8 * (c & 1), (c >> 1) & 1);
+    if (warp == 1 && lane == 0 && commits > 0) {
+      const int cl = commits - 1;
+      mbar_wait_bounded(done0 + 8 * (cl & 1), (cl >> 1) & 1);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 256);
+  }
+}
+
+// ---------------------------------------------------------------- set-up kernels
+
+// Bm in both operand layouts; flags |= 8 (and *bad = 1) if an entry is not
+// exact in BF16 (|B_ij| > 256)
+__global__ void pack_bm_kernel(const int32_t* __restrict__ B, int d, int R, int r0, int d64, int R64, int nbF,
+                               int nbG, uint8_t* __restrict__ BmF, uint8_t* __restrict__ BmG, int32_t* bad,
+                               int32_t* flags) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)R64 * d64) return;
+  const int i = (int)(e / d64), j = (int)(e % d64);
+  const int v = (i < R && j < d) ? B[(int64_t)(r0 + i) * d + j] : 0;
+  if (v > 256 || v < -256) {
+    atomicOr(bad, 1);
+    atomicOr(flags, 8);
+  }
+  const __nv_bfloat16 hb = __float2bfloat16_rn((float)v);
+  const uint16_t hv = *reinterpret_cast<const uint16_t*>(&hb);
+  {
+    const int rb = i / kNB, rl = i % kNB;
+    const int Nr = rb < nbF - 1 ? kNB : R64 - kNB * (nbF - 1);
+    const size_t off = ((size_t)rb * kNB * d64 + (size_t)(j / kKC) * Nr * kKC) * 2 + chunk_off(rl, j % kKC);
+    *reinterpret_cast<uint16_t*>(BmF + off) = hv;
+  }
+  {
+    const int gb = j / kNB, jl = j % kNB;
+    const int Nd = gb < nbG - 1 ? kNB : d64 - kNB * (nbG - 1);
+    const size_t off = ((size_t)gb * kNB * R64 + (size_t)(i / kKC) * Nd * kKC) * 2 + chunk_off(jl, i % kKC);
+    *reinterpret_cast<uint16_t*>(BmG + off) = hv;
+  }
+}
+
+// [P x d] row-major  <->  blocked [tiles][d64/4][128][4] (zero padded)
+__global__ void pack128_kernel(const float* __restrict__ in, float* __restrict__ out, int P, int d, int d64,
+                               int64_t total) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int c = (int)(e & 3);
+  const int r = (int)((e >> 2) % kTM);
+  const int64_t g = e / (4 * kTM);
+  const int g4 = (int)(g % (d64 / 4));
+  const int64_t tile = g / (d64 / 4);
+  const int64_t row = tile * kTM + r;
+  const int j = g4 * 4 + c;
+  out[e] = (row < P && j < d) ? in[row * d + j] : 0.f;
+}
+
+__global__ void unpack128_kernel(const float* __restrict__ in, float* __restrict__ out, int P, int d, int d64) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)P * d) return;
+  const int64_t row = e / d;
+  const int j = (int)(e % d);
+  const int64_t tile = row / kTM;
+  const int r = (int)(row % kTM);
+  out[e] = in[((tile * (d64 / 4) + j / 4) * kTM + r) * 4 + (j & 3)];
+}
+
+// per-start words of the first step: ||z0||_inf and its first index, the
+// collection state
+__global__ void stream_init_kernel(StParams p) {
+  const int64_t pg = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int P2 = ptot(p);
+  if (pg >= P2) return;
+  unsigned long long key = 0ull;
+  if (pg < p.P) {
+    const int tile = (int)(pg / kTM), r = (int)(pg % kTM);
+    const float4* zt = reinterpret_cast<const float4*>(p.Zt) + (size_t)tile * (p.d64 / 4) * kTM + r;
+    float best = 0.f;
+    int kb = -1;
+    for (int g = 0; g < p.d64 / 4; ++g) {
+      const float4 q = zt[(size_t)g * kTM];
+      const float a4[4] = {fabsf(q.x), fabsf(q.y), fabsf(q.z), fabsf(q.w)};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int j = 4 * g + k;
+        if (j < p.d && (kb < 0 || a4[k] > best)) { best = a4[k]; kb = j; }
+      }
+    }
+    key = ((unsigned long long)__float_as_uint(best) << 32) | (0xffffffffu - (uint32_t)kb);
+  }
+  p.zkey[pg] = key;
+  p.zkey[P2 + pg] = 0ull;
+  p.acc[pg] = kChanged;  // the first collection of a call always counts
+  p.oob[pg] = 0u;
+  p.idw[pg] = 0u;
+  p.idw[P2 + pg] = 0u;
+  p.first[pg] = kNoNz;
+  p.first[P2 + pg] = kNoNz;
+  p.first_map[pg] = kNoNz;
+}
+
+__global__ void stream_identity_top_kernel(const int32_t* __restrict__ B, int d, int32_t* __restrict__ flag) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)d * d) return;
+  const int i = (int)(e / d), j = (int)(e % d);
+  if (B[(int64_t)i * d + j] != (i == j ? 1 : 0)) atomicOr(flag, 1);
+}
+
+int r64(int x) { return (x + kKC - 1) / kKC * kKC; }
+int r16(int x) { return (x + 15) / 16 * 16; }
+
+struct StreamShape {
+  int R, r0, d64, R64, tiles, nbF, nbG, mapoff, lds;
+};
+
+StreamShape stream_shape(int n, int d, int P, bool id) {
+  StreamShape s{};
+  s.R = id ? n - d : n;
+  s.r0 = id ? d : 0;
+  s.d64 = r64(d);
+  s.R64 = s.R > 0 ? r64(s.R) : kKC;
+  s.tiles = (int)mape_detail::ceil_div(P, kTM);
+  s.nbF = (int)mape_detail::ceil_div(s.R64, kNB);
+  s.nbG = (int)mape_detail::ceil_div(s.d64, kNB);
+  s.mapoff = id ? r16(d) : 0;
+  s.lds = s.mapoff + s.R64;
+  return s;
+}
+
+// elementwise maximum of the layouts of a general and an identity-topped B:
+// the workspace is sized before B is inspected
+StreamShape stream_bound(int n, int d, int P) {
+  StreamShape g = stream_shape(n, d, P, false), i = stream_shape(n, d, P, true);
+  g.R64 = g.R64 > i.R64 ? g.R64 : i.R64;
+  g.lds = g.lds > i.lds ? g.lds : i.lds;
+  return g;
+}
+
+constexpr int32_t kBiasSteps = 1 << 20;  // bias-correction table: up to 2^20 steps per call
+
+template <typename Carve>
+void carve_stream(Carve& cv, const StreamShape& sh) {
+  const size_t P2 = (size_t)sh.tiles * kTM;
+  const size_t blocked = P2 * sh.d64;
+  for (int k = 0; k < 3; ++k) cv.template take<float>(blocked);
+  cv.template take<uint8_t>(P2 * sh.R64 * 2);             // S
+  cv.template take<int8_t>(P2 * sh.lds);                  // staged rows
+  cv.template take<uint8_t>((size_t)sh.R64 * sh.d64 * 2); // BmF
+  cv.template take<uint8_t>((size_t)sh.R64 * sh.d64 * 2); // BmG
+  cv.template take<unsigned long long>(2 * P2);           // zkey
+  cv.template take<uint32_t>(P2);                         // acc
+  cv.template take<uint32_t>(P2);                         // oob
+  cv.template take<uint32_t>(2 * P2);                     // idw
+  cv.template take<int32_t>(2 * P2);                      // first
+  cv.template take<int32_t>(P2);                          // first_map
+  cv.template take<float2>((size_t)kBiasSteps);           // bias table
+  cv.template take<int32_t>(2);                           // identity flag, inexact flag
+}
+
+}  // namespace
+
+namespace mape_detail {
+
+bool extract_stream_supported(int32_t n, int32_t d) { return n <= 4096 && d <= 4096; }
+
+// sized for a general B (all n rows through the tensor cores), which covers
+// the identity-topped case
+size_t extract_stream_workspace(int32_t n, int32_t d, int32_t P) {
+  if (!extract_stream_supported(n, d)) return 0;
+  Sizer s;
+  carve_stream(s, stream_bound(n, d, P));
+  return s.bytes();
+}
+
+int extract_stream(const mape_extract_args* a, cudaStream_t st) {
+  const int n = a->n, d = a->d, P = a->P;
+  if (a->T > kBiasSteps) return MAPE_ERR_SHAPE;
+  if (!extract_stream_supported(n, d)) return MAPE_ERR_SHAPE;
+  const StreamShape gen = stream_bound(n, d, P);
+  Carver cv(a->workspace, a->workspace_bytes);
+  const size_t P2 = (size_t)gen.tiles * kTM;
+  float* Zt = cv.take<float>(P2 * gen.d64);
+  float* Mt = cv.take<float>(P2 * gen.d64);
+  float* Vt = cv.take<float>(P2 * gen.d64);
+  uint8_t* S = cv.take<uint8_t>(P2 * gen.R64 * 2);
+  int8_t* stage = cv.take<int8_t>(P2 * gen.lds);
+  uint8_t* BmF = cv.take<uint8_t>((size_t)gen.R64 * gen.d64 * 2);
+  uint8_t* BmG = cv.take<uint8_t>((size_t)gen.R64 * gen.d64 * 2);
+  unsigned long long* zkey = cv.take<unsigned long long>(2 * P2);
+  uint32_t* acc = cv.take<uint32_t>(P2);
+  uint32_t* oob = cv.take<uint32_t>(P2);
+  uint32_t* idw = cv.take<uint32_t>(2 * P2);
+  int32_t* first = cv.take<int32_t>(2 * P2);
+  int32_t* first_map = cv.take<int32_t>(P2);
+  float2* bias = cv.take<float2>((size_t)kBiasSteps);
+  int32_t* hflags = cv.take<int32_t>(2);
+  if (!cv.ok) return MAPE_ERR_CAPACITY;
+
+  MAPE_CUDA_TRY(cudaMemsetAsync(hflags, 0, 2 * sizeof(int32_t), st));
+  launch(stream_identity_top_kernel, (unsigned)ceil_div((int64_t)d * d, 256), 256, 0, st, a->B, d, hflags);
+  MAPE_LAUNCH_CHECK();
+  int32_t h_notid = 1;
+  MAPE_CUDA_TRY(cudaMemcpyAsync(&h_notid, hflags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  const bool id = h_notid == 0;
+  const StreamShape sh = stream_shape(n, d, P, id);
+
+  launch(pack_bm_kernel, (unsigned)ceil_div((int64_t)sh.R64 * sh.d64, 256), 256, 0, st, a->B, d, sh.R, sh.r0,
+         sh.d64, sh.R64, sh.nbF, sh.nbG, BmF, BmG, hflags + 1, a->flags);
+  MAPE_LAUNCH_CHECK();
+  int32_t h_bad = 0;
+  MAPE_CUDA_TRY(cudaMemcpyAsync(&h_bad, hflags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h_bad) return MAPE_OK;  // flag 8 is set; nothing runs, nothing is collected
+
+  std::vector<float2> bc((size_t)a->T);
+  for (int s = 0; s < a->T; ++s) {
+    const double t = (double)a->t0 + s + 1;
+    const double bc1 = 1.0 - std::pow(a->beta1, t), bc2 = 1.0 - std::pow(a->beta2, t);
+    bc[s] = make_float2((float)((double)a->lr / bc1), (float)(1.0 / std::sqrt(bc2)));
+  }
+  MAPE_CUDA_TRY(cudaMemcpyAsync(bias, bc.data(), sizeof(float2) * bc.size(), cudaMemcpyHostToDevice, st));
+  const int64_t blocked = (int64_t)P2 * sh.d64;
+  const unsigned gpack = (unsigned)ceil_div(blocked, 256);
+  launch(pack128_kernel, gpack, 256, 0, st, a->Z, Zt, P, d, sh.d64, blocked);
+  launch(pack128_kernel, gpack, 256, 0, st, a->M, Mt, P, d, sh.d64, blocked);
+  launch(pack128_kernel, gpack, 256, 0, st, a->V, Vt, P, d, sh.d64, blocked);
+  MAPE_CUDA_TRY(cudaMemsetAsync(stage, 0, P2 * sh.lds, st));
+  if (a->dbg_phi) MAPE_CUDA_TRY(cudaMemsetAsync(a->dbg_phi, 0, sizeof(float) * P, st));
+
+  StParams p{};
+  p.n = n; p.d = d; p.P = P; p.R = sh.R; p.r0 = sh.r0; p.d64 = sh.d64; p.R64 = sh.R64;
+  p.tiles = sh.tiles; p.nbF = sh.nbF; p.nbG = sh.nbG;
+  p.ldc = a->ldc; p.mapoff = sh.mapoff; p.lds = sh.lds;
+  p.BmF = BmF; p.BmG = BmG; p.span = a->span; p.Zt = Zt; p.Mt = Mt; p.Vt = Vt; p.S = S; p.stage = stage;
+  p.zkey = zkey; p.acc = acc; p.oob = oob; p.idw = idw; p.first = first; p.first_map = first_map; p.bias = bias;
+  p.lambda1 = a->lambda1; p.lambda2 = a->lambda2; p.eps = a->eps;
+  p.beta1 = (float)a->beta1; p.beta2 = (float)a->beta2;
+  p.omb1 = (float)(1.0 - a->beta1); p.omb2 = (float)(1.0 - a->beta2);
+  p.nterms = a->precision == MAPE_PREC_BF16X1 ? 1 : 2;
+  p.cand = a->cand; p.cap = a->cand_cap; p.count = a->cand_count; p.flags = a->flags;
+  p.dbg_phi = a->dbg_phi; p.dbg_grad = a->dbg_grad;
+
+  launch(stream_init_kernel, (unsigned)ceil_div((int64_t)P2, 256), 256, 0, st, p);
+  MAPE_LAUNCH_CHECK();
+
+  auto fwd = id ? stream_fwd_kernel<true> : stream_fwd_kernel<false>;
+  auto grad = id ? stream_grad_kernel<true> : stream_grad_kernel<false>;
+  auto coll = id ? stream_collect_kernel<true> : stream_collect_kernel<false>;
+  // one CTA per SM for the forward pass (512 TMEM columns), at most two for
+  // the gradient pass (256 columns each): every TMEM allocation fits
+  MAPE_CUDA_TRY(cudaFuncSetAttribute(fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmem));
+  MAPE_CUDA_TRY(cudaFuncSetAttribute(grad, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem));
+  const unsigned gF = (unsigned)(sh.tiles * sh.nbF), gG = (unsigned)(sh.tiles * sh.nbG);
+  const unsigned gC = (unsigned)ceil_div(P, 8);
+  for (int s = 0; s < a->T; ++s) {
+    const int t = a->t0 + s + 1;
+    const int collect = (s >= 1 && (t - 1) % a->period == 0) ? 1 : 0;
+    launch(fwd, gF, kThreads, kFSmem, st, p, s, 1, collect);
+    if (collect) launch(coll, gC, 256, 0, st, p, s);
+    launch(grad, gG, kThreads, kGSmem, st, p, s);
+  }
+  MAPE_LAUNCH_CHECK();
+  if ((a->t0 + a->T) % a->period == 0) {  // the candidate of the last step
+    launch(fwd, gF, kThreads, kFSmem, st, p, a->T, 0, 1);
+    launch(coll, gC, 256, 0, st, p, a->T);
+  }
+  const unsigned gun = (unsigned)ceil_div((int64_t)P * d, 256);
+  launch(unpack128_kernel, gun, 256, 0, st, Zt, a->Z, P, d, sh.d64);
+  launch(unpack128_kernel, gun, 256, 0, st, Mt, a->M, P, d, sh.d64);
+  launch(unpack128_kernel, gun, 256, 0, st, Vt, a->V, P, d, sh.d64);
+  MAPE_LAUNCH_CHECK();
+  return MAPE_OK;
+}
+
+}  // namespace mape_detail

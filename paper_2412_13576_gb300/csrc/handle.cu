@@ -333,8 +333,7 @@ extern "C" int mape_create_instance(const int32_t* A, const int64_t* b, const in
   if (n <= 0 || m <= 0 || m >= n) return MAPE_ERR_SHAPE;
   if (n > 4096) return MAPE_ERR_SHAPE;
   if (cfg->T < 0 || cfg->period <= 0 || cfg->lr <= 0.f || cfg->max_aug_iters < 0) return MAPE_ERR_INVALID_ARG;
-  if (cfg->precision != MAPE_PREC_FP32 && cfg->precision != MAPE_PREC_BF16 && cfg->precision != MAPE_PREC_BF16X1)
-    return MAPE_ERR_INVALID_ARG;
+  if (mape_extract_workspace_bytes(n, n - m, 1, cfg->precision) == 0) return MAPE_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i)
     if (u[i] < l[i] || (int64_t)u[i] - l[i] > 127) return MAPE_ERR_BOUNDS;
   auto* h = new mape_instance();
@@ -396,8 +395,7 @@ extern "C" int mape_extract_directions(mape_handle h, int32_t P, const float* Z0
   if (!h || P <= 0 || (Z0 == nullptr) == (G0 == nullptr)) return MAPE_ERR_INVALID_ARG;
   if (!idle(h)) return MAPE_ERR_STATE;
   h->join();
-  if (h->cfg.precision != MAPE_PREC_FP32 && mape_extract_workspace_bytes(h->n, h->d, P, h->cfg.precision) == 0)
-    return MAPE_ERR_SHAPE;
+  if (mape_extract_workspace_bytes(h->n, h->d, P, h->cfg.precision) == 0) return MAPE_ERR_SHAPE;
   h->release_all(h->job_bufs);
   h->K = 0;
   h->dirs = nullptr;

@@ -156,6 +156,12 @@ def uneven_batch(count=64, n_lo=50, n_hi=1000, seed=1003):
     return out
 
 
+def uneven_single(n, density=0.1, seed=1003):
+    """One instance of the uneven family at a chosen n (m = n/5, box [-5,5])."""
+    return make_instance(f"uneven_n{n}", n, max(1, n // 5), c_k=3, c_density=density,
+                         lo=-5, hi=5, q_k=3, q_density=0.3, lin_k=10, seed=seed * 100 + n)
+
+
 def tiny_graver_case(seed=7):
     """6 variables, 2 rows: A = [C | I_2] with C 2x4 in {-1,0,1}; box [-1,2],
     so that bound consistency (C4) admits exactly the entries |g_i| <= 3."""

@@ -161,18 +161,20 @@ def test_bf16_rejects_inexact_basis(M):
 
 
 def test_bf16_shape_limits(M):
-    """d above 256 (and so any n) is refused with MAPE_ERR_SHAPE before any
-    launch; n above 256 is accepted when B is identity-topped and n - d fits."""
+    """n or d above 4096 is refused with MAPE_ERR_SHAPE before any launch;
+    shapes beyond the resident kernel's tile (d = 280 here) run on the
+    streamed kernels instead (covered in test_gpu_streamed)."""
     import torch
-    n, d = 300, 280
+    n, d = 5000, 4100
     B = torch.zeros((n, d), dtype=torch.int32, device="cuda")
     span = torch.ones(n, dtype=torch.int32, device="cuda")
     Z = torch.zeros((128, d), dtype=torch.float32, device="cuda")
-    cand = torch.zeros((16, 304), dtype=torch.int8, device="cuda")
+    cand = torch.zeros((16, 5008), dtype=torch.int8, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     flags = torch.zeros(1, dtype=torch.int32, device="cuda")
     cfg = M.default_config(precision=M.PREC_BF16)
     with pytest.raises(M.MapeError) as e:
         M.extract(B, span, Z, Z.clone(), Z.clone(), t0=0, T=1, cfg=cfg, cand=cand, cand_count=cnt, flags=flags,
-                  ldc=304, workspace=torch.zeros(64, dtype=torch.uint8, device="cuda"))
+                  ldc=5008, workspace=torch.zeros(64, dtype=torch.uint8, device="cuda"))
     assert e.value.code == -2
+    assert M.lib().mape_extract_workspace_bytes(300, 280, 128, M.PREC_BF16) > 0

@@ -1,0 +1,210 @@
+"""The streamed tensor-core path of Algorithm 2 (three kernels per step, B and
+z, m, v streamed through shared memory) against the FP64 oracle, on the shapes
+only it takes (d or the MMA rows above 256: the uneven family up to n = 1000,
+the large n = 2000 instance) and, forced with MAPE_PREC_STREAMED, on the
+shapes the resident kernel also takes.  Same bar as the resident path: the
+gradient within 1e-5 on the starts whose sign(Bz) the arithmetic fixes, Phi
+on all starts, Adam within 1e-5, candidates bit-exact."""
+import numpy as np
+import pytest
+
+from oracle import mape_oracle as O
+from paper_2412_13576_gb300 import instances as I
+
+from .gpu_common import dev, rel_fro, rows_set
+from .test_gpu_bf16 import FP32_TOL, PRECISIONS, _general_basis, _starts, bf16_stable_rows
+from .test_gpu_stages import _extract_steps
+
+pytestmark = pytest.mark.gpu
+
+STREAMED = 0x100
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_13576_gb300 import mape
+    mape.lib(build_if_missing=True)
+    return mape
+
+
+def uneven500():
+    return I.uneven_single(500)
+
+
+def uneven1000():
+    return I.uneven_single(1000, density=0.05)
+
+
+def _z0(inst, P, seed, std):
+    """std None: the paper's projected uniform starts; else Z0 ~ N(0, std),
+    small enough that the rounded points meet the box within a few steps."""
+    if std is None:
+        return _starts(inst, P, seed)
+    return I.normal_starts(inst, P, std=std, seed=seed).Z0
+
+
+# (instance, P, T, ambiguity factor, force the streamed path, start scale)
+CASES = [
+    (I.small_dense, 256, 20, 1.0, True, None),
+    (I.medium_sparse, 300, 5, 1.0, True, None),          # 3 tiles, the last one ragged
+    (I.tiny_graver_case, 130, 30, 1.0, True, None),
+    (_general_basis(I.small_dense), 256, 20, 1.0, True, None),
+    (uneven500, 200, 4, 4.0, False, None),               # d = 400: streamed by necessity
+    (uneven500, 200, 6, 4.0, False, 0.3),
+    (uneven1000, 130, 2, 6.0, False, None),              # d = 800, 160 rows of B'
+    (uneven1000, 130, 3, 6.0, False, 0.3),
+    (I.large_quartic, 256, 2, 6.0, False, None),         # n = 2000, d = 1600: 2 row blocks, 7 coordinate blocks
+    (I.large_quartic, 256, 3, 6.0, False, 0.3),
+    (_general_basis(uneven500), 130, 4, 6.0, False, 0.3),  # general B: all 500 rows through the MMA
+]
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("make,P,T,amb,force,std", CASES)
+def test_streamed_per_step(M, make, P, T, amb, force, std, precision):
+    inst = make()
+    Z0 = _z0(inst, P, 2003, std)
+    ldc = M.round16(inst.n)
+    bits, _, max_ambiguous = PRECISIONS[precision]
+    prec = precision | (STREAMED if force else 0)
+    states, grads, phis, cand = _extract_steps(M, inst, Z0, T, prec, ldc, cap=P * (T + 1) + 16)
+    expect = set()
+    ambiguous = 0
+    for t, ((z, m, v), (z1, m1, v1)) in enumerate(states):
+        go = O.phi_grad(inst.B, z, 0.85, 1.0)
+        ok = bf16_stable_rows(inst.B, z, bits)
+        ambiguous += int((~ok).sum())
+        if ok.any():
+            assert rel_fro(grads[t][ok], go[ok]) < FP32_TOL
+        # Phi: within the spec BF16 tolerance overall, and per start within
+        # the error bound of z carried to `bits` bits and summed in FP32
+        po = O.phi(inst.B, z, 0.85, 1.0)
+        assert rel_fro(phis[t], po) < 2e-2
+        bound = (2.0 ** -bits + inst.d * 2.0 ** -23) * (np.abs(z) @ np.abs(inst.B.astype(np.float64)).T).sum(1)
+        assert np.all(np.abs(phis[t] - po) <= 1.01 * bound + 1e-5 * np.abs(po) + 1e-4)
+        zo, mo, vo = O.adam_update(z.astype(np.float64), m, v, grads[t].astype(np.float64), t + 1, 0.003)
+        assert rel_fro(z1, zo) < FP32_TOL
+        assert rel_fro(m1, mo) < FP32_TOL
+        assert rel_fro(v1, vo) < FP32_TOL
+        expect |= O.collect(inst.A, inst.B, inst.l, inst.u, z1)
+    assert ambiguous <= min(1.0, amb * max_ambiguous) * P * T
+    assert rows_set(cand, inst.n) == expect
+
+
+@pytest.mark.parametrize("make,P,T,period,force,std", [(uneven500, 300, 12, 1, False, 0.3),
+                                                       (I.medium_sparse, 1000, 10, 3, True, None),
+                                                       (_general_basis(I.small_dense), 300, 15, 1, True, None)])
+def test_streamed_one_call_equals_single_steps(M, make, P, T, period, force, std):
+    """T steps in one call give bitwise the same Z, M, V as T calls of one
+    step, and the same set of collected directions."""
+    import torch
+    inst = make()
+    Z0 = _z0(inst, P, 7, std)
+    ldc = M.round16(inst.n)
+    B, span = dev(inst.B), dev((inst.u - inst.l).astype(np.int32))
+    prec = M.PREC_BF16 | (STREAMED if force else 0)
+    results = []
+    for single in (False, True):
+        cfg = M.default_config(precision=prec, period=period)
+        Z = dev(Z0)
+        Mm = torch.zeros_like(Z)
+        V = torch.zeros_like(Z)
+        cand = torch.zeros((P * T + 8, ldc), dtype=torch.int8, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+        if single:
+            for t in range(T):
+                M.extract(B, span, Z, Mm, V, t0=t, T=1, cfg=cfg, cand=cand, cand_count=cnt, flags=flags, ldc=ldc)
+        else:
+            M.extract(B, span, Z, Mm, V, t0=0, T=T, cfg=cfg, cand=cand, cand_count=cnt, flags=flags, ldc=ldc)
+        torch.cuda.synchronize()
+        assert int(flags.item()) == 0
+        c = cand[: int(cnt.item())].cpu().numpy()
+        results.append((Z.cpu().numpy(), Mm.cpu().numpy(), V.cpu().numpy(), rows_set(c, inst.n), c))
+    (z1, m1, v1, s1, c1), (z2, m2, v2, s2, _) = results
+    assert np.array_equal(z1, z2) and np.array_equal(m1, m2) and np.array_equal(v1, v2)
+    assert s1 == s2
+    assert len(s1) > 0
+    assert np.all(c1[:, inst.n:] == 0)
+    G = np.array(sorted(s1), dtype=np.int64)
+    assert np.all(O.kernel_condition(inst.A, G)) and np.all(O.bound_consistent(G, inst.l, inst.u))
+
+
+def test_streamed_rejects_inexact_basis(M):
+    """|B_ij| > 256 is not exact in BF16: flag 8, nothing collected, state untouched."""
+    import torch
+    inst = uneven500()
+    Bbig = inst.B.copy()
+    Bbig[-1, 3] = 300
+    Z0 = _starts(inst, 64, 1)
+    Z = dev(Z0)
+    cand = torch.zeros((1024, M.round16(inst.n)), dtype=torch.int8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cfg = M.default_config(precision=M.PREC_BF16)
+    M.extract(dev(Bbig), dev((inst.u - inst.l).astype(np.int32)), Z, torch.zeros_like(Z), torch.zeros_like(Z),
+              t0=0, T=3, cfg=cfg, cand=cand, cand_count=cnt, flags=flags, ldc=M.round16(inst.n))
+    torch.cuda.synchronize()
+    assert int(flags.item()) & 8
+    assert int(cnt.item()) == 0
+    assert np.array_equal(Z.cpu().numpy(), Z0)
+
+
+def _no_improving_move(inst, D, x, fx):
+    """Termination of Algorithm 1: no g in +-D and integer lambda >= 1 keeps
+    x + lambda g in the box and lowers f (A g = 0 keeps A x = b).  f is
+    quadratic here, so f(x + lambda g) - f(x) = lambda^2 g'Qg + lambda (2 g'Qx + c'g),
+    evaluated in float64 (exact: every term is an integer below 2^53)."""
+    Dg = D.astype(np.float64)
+    QG = Dg @ inst.Q.astype(np.float64)
+    a = np.sum(QG * Dg, axis=1)
+    xf = x.astype(np.float64)
+    lin = 2.0 * (QG @ xf) + Dg @ inst.c.astype(np.float64)
+    span = int(np.max(inst.u - inst.l))
+    for sgn in (1.0, -1.0):
+        for lam in range(1, span + 1):
+            Y = xf[None, :] + lam * sgn * Dg
+            inside = np.all((Y >= inst.l) & (Y <= inst.u), axis=1)
+            delta = lam * lam * a + lam * sgn * lin
+            assert not np.any(inside & (delta < 0))
+
+
+def test_streamed_handle_end_to_end(M):
+    """The handle on an instance only the streamed path takes (n = 500,
+    d = 400): the returned set passes C1, C4, nonzero, canonical sign, order
+    and distinctness, minimality on a sample of rows (the oracle's pairwise
+    test), and augmentation from xbar ends feasible, no worse than xbar, with
+    no improving move left in the set."""
+    from .test_gpu_handle import check_direction_set
+    inst = uneven500()
+    cfg = M.default_config(T=60, precision=M.PREC_BF16)
+    Z0 = _z0(inst, 512, 2003, 0.3)
+    with M.Instance.from_generated(inst, cfg) as h:
+        h.extract_directions(512, Z0=Z0)
+        h.wait(600)
+        s = h.poll()
+        assert s["phase"] == "DONE" and s["error"] == 0
+        D = h.directions()
+        check_direction_set(inst, D)
+        assert s["kernel_failures"] == 0
+        rng = np.random.default_rng(0)
+        sample = rng.choice(D.shape[0], size=min(200, D.shape[0]), replace=False)
+        absD = np.abs(D.astype(np.int64))
+        for i in sample:
+            g = D[i].astype(np.int64)
+            pos = np.all((D * g >= 0) & (absD <= absD[i]), axis=1)
+            neg = np.all((-D * g >= 0) & (absD <= absD[i]), axis=1)
+            hit = pos | neg
+            hit[i] = False
+            assert not hit.any()
+        h.augment(inst.xbar[None, :])
+        h.wait(600)
+        x, fx = h.solution()
+    assert np.array_equal(inst.A.astype(np.int64) @ x, inst.b)
+    assert np.all((x >= inst.l) & (x <= inst.u))
+    assert fx == O.f_value(inst.Q, inst.c, None, x)
+    assert fx <= O.f_value(inst.Q, inst.c, None, inst.xbar)
+    _no_improving_move(inst, D, x, fx)
