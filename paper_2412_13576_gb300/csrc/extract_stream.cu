@@ -121,6 +121,22 @@ __global__ void __launch_bounds__(kThreads, 1) stream_fwd_kernel(StParams p, int
   bool ok = true;
   int issued_copies = 0, issued_commits = 0;  // thread 0 only
 
+  // item i of this thread: 8 coordinates (core matrix kc) of start r, so that
+  // a warp writes 512 contiguous bytes of each operand
+  const float4* zbase = reinterpret_cast<const float4*>(p.Zt) + (size_t)tile * (p.d64 / 4) * kTM;
+  auto item_r = [&](int i) { const int e = tid + kThreads * i; return (e & 7) | ((e >> 6) << 3); };
+  auto item_kc = [&](int i) { return ((tid + kThreads * i) >> 3) & 7; };
+  float4 cur[4][2], nxt[4][2] = {};
+  auto load_chunk = [&](int c, float4 (&q)[4][2]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4* zt = zbase + ((size_t)c * (kKC / 4) + 2 * item_kc(i)) * kTM + item_r(i);
+      q[i][0] = zt[0];
+      q[i][1] = zt[kTM];
+    }
+  };
+  load_chunk(0, cur);
+
   for (int c = 0; c < nk; ++c) {
     const int stg = c & 1;
     uint8_t* Ahi = smem + stg * kFStage;
@@ -137,16 +153,12 @@ __global__ void __launch_bounds__(kThreads, 1) stream_fwd_kernel(StParams p, int
                full0 + 8 * stg);
       ++issued_copies;
     }
-    // z chunk -> BF16 operands: item e covers 8 coordinates of one start;
-    // a warp writes 512 contiguous bytes of each operand
+    // the next chunk's z is in flight while this one becomes BF16 operands
+    if (c + 1 < nk) load_chunk(c + 1, nxt);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int e = tid + kThreads * i;
-      const int r = (e & 7) | ((e >> 6) << 3);
-      const int kc = (e >> 3) & 7;
-      const float4* zt = reinterpret_cast<const float4*>(p.Zt) +
-                         ((size_t)tile * (p.d64 / 4) + (size_t)c * (kKC / 4) + 2 * kc) * kTM + r;
-      const float4 q0 = zt[0], q1 = zt[kTM];
+      const int r = item_r(i), kc = item_kc(i);
+      const float4 q0 = cur[i][0], q1 = cur[i][1];
       const float z8[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
       const uint32_t o = chunk_off(r, kc * 8);
       if (fwd) {
@@ -204,6 +216,11 @@ __global__ void __launch_bounds__(kThreads, 1) stream_fwd_kernel(StParams p, int
         mma_commit(done0 + 8 * stg);
         ++issued_commits;
       }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      cur[i][0] = nxt[i][0];
+      cur[i][1] = nxt[i][1];
     }
   }
   if (ok) {
@@ -329,6 +346,7 @@ template <bool kId>
 __global__ void __launch_bounds__(kThreads, 1) stream_grad_kernel(StParams p, int s) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bars[5];  // full[2], done[2], accumulator ready
+  __shared__ int32_t s_span[kNB];             // C4 bounds of this block's coordinates
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -391,16 +409,34 @@ __global__ void __launch_bounds__(kThreads, 1) stream_grad_kernel(StParams p, in
     if (c == nk) mma_commit(accr);
   }
   __syncwarp();
+
+  // epilogue geometry: warp w reads TMEM lane quarter w % 4 (its 32 starts);
+  // the two warps of a quarter take alternate 8-coordinate chunks
+  const int q = warp & 3, h = warp >> 2;
+  const int r = q * 32 + lane;
+  const int64_t pg = (int64_t)tile * kTM + r;
+  const bool row_live = pg < p.P;
+  const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+  const int nch = N / 8;
+  float4* const zt = reinterpret_cast<float4*>(p.Zt) + (size_t)tile * (p.d64 / 4) * kTM + r;
+  float4* const mt = reinterpret_cast<float4*>(p.Mt) + (size_t)tile * (p.d64 / 4) * kTM + r;
+  float4* const vt = reinterpret_cast<float4*>(p.Vt) + (size_t)tile * (p.d64 / 4) * kTM + r;
+  auto load_state = [&](int ch, float4(&z)[2], float4(&m)[2], float4(&v)[2]) {
+    const size_t g = (size_t)((col0 + ch * 8) / 4) * kTM;
+    z[0] = zt[g]; z[1] = zt[g + kTM];
+    m[0] = mt[g]; m[1] = mt[g + kTM];
+    v[0] = vt[g]; v[1] = vt[g + kTM];
+  };
+  // the first chunk's state is in flight while the MMAs run
+  float4 cz[2], cm[2], cv[2];
+  if (h < nch) load_state(h, cz, cm, cv);
+  if (kId)
+    for (int k = tid; k < N; k += kThreads) s_span[k] = col0 + k < p.d ? p.span[col0 + k] : 0;
   const bool w = mbar_wait_bounded(accr, 0);
   const bool ok = !__syncthreads_or(!w || s_abort);
 
   if (ok) {
     tc_fence_after();
-    const int q = warp & 3, h = warp >> 2;
-    const int r = q * 32 + lane;
-    const int64_t pg = (int64_t)tile * kTM + r;
-    const bool row_live = pg < p.P;
-    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     const unsigned long long zk = p.zkey[(s & 1) * P2 + pg];
     const float zinf = __uint_as_float((uint32_t)(zk >> 32));
     const int kmax = zk ? (int)(0xffffffffu - (uint32_t)zk) : -1;
@@ -412,25 +448,18 @@ __global__ void __launch_bounds__(kThreads, 1) stream_grad_kernel(StParams p, in
     float nzinf = 0.f, frac = 0.f, l1_id = 0.f;
     int nkmax = kNoNz, first_id = kNoNz;
     bool changed = false, unexact = false, out_id = false;
-    float4* const zt = reinterpret_cast<float4*>(p.Zt) + (size_t)tile * (p.d64 / 4) * kTM + r;
-    float4* const mt = reinterpret_cast<float4*>(p.Mt) + (size_t)tile * (p.d64 / 4) * kTM + r;
-    float4* const vt = reinterpret_cast<float4*>(p.Vt) + (size_t)tile * (p.d64 / 4) * kTM + r;
-    for (int ch = h; ch < N / 16; ch += 2) {
-      const int j0 = col0 + ch * 16;
-      uint32_t gv[16];
-      tmem_ld16(tmem + lane_base + ch * 16, gv);
-      float zc[16], mc[16], vc[16];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const size_t g4 = (size_t)(j0 / 4 + k) * kTM;
-        const float4 qz = zt[g4], qm = mt[g4], qv = vt[g4];
-        zc[4 * k] = qz.x; zc[4 * k + 1] = qz.y; zc[4 * k + 2] = qz.z; zc[4 * k + 3] = qz.w;
-        mc[4 * k] = qm.x; mc[4 * k + 1] = qm.y; mc[4 * k + 2] = qm.z; mc[4 * k + 3] = qm.w;
-        vc[4 * k] = qv.x; vc[4 * k + 1] = qv.y; vc[4 * k + 2] = qv.z; vc[4 * k + 3] = qv.w;
-      }
+    for (int ch = h; ch < nch; ch += 2) {
+      const int j0 = col0 + ch * 8;
+      float4 nz[2] = {cz[0], cz[1]}, nm[2] = {cm[0], cm[1]}, nv[2] = {cv[0], cv[1]};
+      if (ch + 2 < nch) load_state(ch + 2, nz, nm, nv);
+      uint32_t gv[8];
+      tmem_ld8(tmem + lane_base + ch * 8, gv);
+      float zc[8] = {cz[0].x, cz[0].y, cz[0].z, cz[0].w, cz[1].x, cz[1].y, cz[1].z, cz[1].w};
+      float mc[8] = {cm[0].x, cm[0].y, cm[0].z, cm[0].w, cm[1].x, cm[1].y, cm[1].z, cm[1].w};
+      float vc[8] = {cv[0].x, cv[0].y, cv[0].z, cv[0].w, cv[1].x, cv[1].y, cv[1].z, cv[1].w};
       tc_wait_ld();
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
+      for (int k = 0; k < 8; ++k) {
         const int j = j0 + k;
         const bool live = row_live && j < p.d;
         const float z = zc[k];
@@ -458,18 +487,21 @@ __global__ void __launch_bounds__(kThreads, 1) stream_grad_kernel(StParams p, in
           const float a = fabsf(znew);
           if (nkmax == kNoNz || a > nzinf) { nzinf = a; nkmax = j; }
           if (kId) {
-            out_id |= fabsf(rn) > (float)p.span[j];
+            out_id |= fabsf(rn) > (float)s_span[ch * 8 + k];
             if (first_id == kNoNz && rn != 0.f) first_id = (j << 1) | (rn < 0.f ? 1 : 0);
           }
         }
       }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const size_t g4 = (size_t)(j0 / 4 + k) * kTM;
-        zt[g4] = make_float4(zc[4 * k], zc[4 * k + 1], zc[4 * k + 2], zc[4 * k + 3]);
-        mt[g4] = make_float4(mc[4 * k], mc[4 * k + 1], mc[4 * k + 2], mc[4 * k + 3]);
-        vt[g4] = make_float4(vc[4 * k], vc[4 * k + 1], vc[4 * k + 2], vc[4 * k + 3]);
-      }
+      const size_t g = (size_t)(j0 / 4) * kTM;
+      zt[g] = make_float4(zc[0], zc[1], zc[2], zc[3]);
+      zt[g + kTM] = make_float4(zc[4], zc[5], zc[6], zc[7]);
+      mt[g] = make_float4(mc[0], mc[1], mc[2], mc[3]);
+      mt[g + kTM] = make_float4(mc[4], mc[5], mc[6], mc[7]);
+      vt[g] = make_float4(vc[0], vc[1], vc[2], vc[3]);
+      vt[g + kTM] = make_float4(vc[4], vc[5], vc[6], vc[7]);
+      cz[0] = nz[0]; cz[1] = nz[1];
+      cm[0] = nm[0]; cm[1] = nm[1];
+      cv[0] = nv[0]; cv[1] = nv[1];
     }
     if (row_live) {
       const int nb = ((s + 1) & 1) * P2 + (int)pg;
