@@ -26,12 +26,13 @@ def M():
 
 
 def _inst(name):
-    return {"small": I.small_dense, "medium": I.medium_sparse, "tiny": I.tiny_graver_case}[name]()
+    return {"small": I.small_dense, "medium": I.medium_sparse, "tiny": I.tiny_graver_case,
+            "large": I.large_quartic}[name]()
 
 
 # --- a2 ----------------------------------------------------------------------
 
-@pytest.mark.parametrize("name,P", [("small", 300), ("medium", 1000)])
+@pytest.mark.parametrize("name,P", [("small", 300), ("medium", 1000), ("large", 256)])
 def test_project_starts(M, name, P):
     inst = _inst(name)
     G0 = I.uniform_samples(inst, P, seed=7).G0
