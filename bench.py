@@ -53,6 +53,10 @@ def parse_args(argv=None):
     ap.add_argument("--streamed-case", nargs=3, metavar=("NAME", "P", "T"),
                     help="time the streamed tensor-core extraction on a named instance (large: n=2000 m=400; "
                          "uneven1000: n=1000 m=200) for P starts and T steps, and exit")
+    ap.add_argument("--serve", type=int, default=24, metavar="N",
+                    help="requests in the serving measurement (Poisson stream at 200/s, n log-uniform in "
+                         "[30, 3000], m = n/5, P = 4096); 0 skips it")
+    ap.add_argument("--serve-T", type=int, default=1000, help="Adam steps per request in the serving measurement")
     ap.add_argument("--kernel-case", type=int, nargs=2, metavar=("P", "T"),
                     help="time the fused extraction kernel alone on P starts of the workload for T steps "
                          "(two launches; a small case for profilers) and exit")
@@ -304,6 +308,8 @@ def run_ours(args):
         result["roofline"] = roofline(mape, inst, starts, stream, args)
         if not args.no_plain and args.precision != "fp32":
             result["vs_plain_fp32"] = plain_fp32(mape, inst, G0, x0, stream)
+        if args.serve > 0 and world == 1:
+            result["serving"] = serve_measure(args.serve, args.serve_T)
         if not args.no_cpu_baseline and world == 1:
             result["cpu_baseline"] = cpu_baseline_obj(run_cpu_sample(CPU_SAMPLE_P, T_FULL))
     if world > 1:
@@ -400,6 +406,70 @@ def streamed_case(args):
                               "candidates": counts, "algorithmic_bytes_per_call": algo, "achieved_gbs": gbs,
                               "hbm_peak_gbs": peaks["hbm_gbs"], "frac_of_hbm": gbs / peaks["hbm_gbs"],
                               "peak_source": src}}
+
+
+SERVE_RATE = 200.0    # requests per second (Poisson)
+SERVE_P = 4096
+
+
+def _pct(v, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
+
+
+def serve_measure(N, T, seed=3000):
+    """The serving workload: N requests arriving as a Poisson stream at 200/s,
+    instances with n log-uniform in [30, 3000], m = n/5, C in [-3,3] at a
+    density uniform in [0.05, 0.2], box [-5,5], P = 4096 projected starts,
+    Algorithm 1 from x̄.  Runs them through the request server (continuous
+    batching, BF16 paths) and, for comparison, one at a time through the plain
+    FP32 single-instance path; reports instances/s and p50/p99 time to first
+    improving direction and to termination (from arrival), and verified
+    directions/s."""
+    import numpy as np
+    from paper_2412_13576_gb300 import instances as I
+    from paper_2412_13576_gb300 import mape
+    rng = np.random.default_rng(seed)
+    insts = I.uneven_batch(count=N, n_lo=30, n_hi=3000, seed=seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / SERVE_RATE, size=N))
+    G0s = [I.uniform_samples(inst, SERVE_P, seed=seed + 1 + k).G0 for k, inst in enumerate(insts)]
+
+    def run_server(cfg, slots):
+        with mape.Server(cfg, mem_cap_bytes=150 << 30, max_slots=slots) as srv:
+            t0 = time.perf_counter()
+            ids = []
+            for k, inst in enumerate(insts):
+                wait = arrivals[k] - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+                ids.append(srv.submit(inst, SERVE_P, G0=G0s[k]))
+            srv.wait_all(3600)
+            wall = time.perf_counter() - t0
+            infos = [srv.info(i) for i in ids]
+            stats = srv.stats()
+        return infos, wall, stats
+
+    out = {}
+    for name, prec, slots in (("served_bf16", PREC["bf16"], 16), ("plain_fp32_one_at_a_time", 0, 1)):
+        cfg = mape.default_config(T=T, precision=prec)
+        infos, wall, stats = run_server(cfg, slots)
+        ok = [i for i in infos if i["state"] == "DONE"]
+        ttfid = [i["t_first_improve_ms"] - i["t_submit_ms"] for i in ok]
+        ttt = [i["t_done_ms"] - i["t_submit_ms"] for i in ok]
+        out[name] = {"instances_per_s": len(ok) / wall, "wall_s": wall, "completed": len(ok),
+                     "failed": len(infos) - len(ok),
+                     "ttfid_ms_p50": _pct(ttfid, 50), "ttfid_ms_p99": _pct(ttfid, 99),
+                     "ttt_ms_p50": _pct(ttt, 50), "ttt_ms_p99": _pct(ttt, 99),
+                     "directions_per_s": sum(i["directions"] for i in ok) / wall,
+                     "peak_running": stats["peak_running"], "mem_peak_gb": stats["mem_peak"] / 1e9,
+                     "best_f": [i["best_f"] for i in infos]}
+    a, b = out["served_bf16"]["best_f"], out["plain_fp32_one_at_a_time"]["best_f"]
+    out["f_not_worse_than_plain"] = float(np.mean([x <= y for x, y in zip(a, b)]))
+    for k in ("served_bf16", "plain_fp32_one_at_a_time"):
+        out[k].pop("best_f")
+    out["workload"] = (f"{N} requests, Poisson arrivals at {SERVE_RATE:.0f}/s, n log-uniform in [30, 3000] "
+                       f"(uneven_batch seed {seed}), m = n/5, P = {SERVE_P}, T = {T}, 150 GB admission cap")
+    return out
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "extract_tc_kernel_medium_sparse_P8192_T1000_traffic.md")

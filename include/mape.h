@@ -58,7 +58,9 @@ extern "C" {
 #define MAPE_ERR_CANCELLED       -14  /* mape_cancel was called */
 
 /* ---- precision of the extraction contractions ---------------------------- */
-#define MAPE_PREC_FP32 0  /* CUDA-core FP32, unfused per-step kernels           */
+#define MAPE_PREC_FP32 0  /* the plain FP32 baseline: per step, strict-FP32
+                             cuBLAS GEMMs for B z, B^T sign(Bz), B round(z)
+                             and unfused elementwise kernels                  */
 #define MAPE_PREC_BF16 1  /* tcgen05 BF16 MMAs with FP32 accumulation in TMEM,
                              persistent fused kernel over all T steps; z enters
                              the forward product as hi + lo (two BF16 terms),
@@ -89,7 +91,8 @@ typedef struct {
   int32_t period;              /* collect every `period` steps (Algorithm 2)    */
   int32_t precision;           /* MAPE_PREC_*                                   */
   int32_t reserved;
-  int64_t cand_capacity;       /* max collected candidates (0 = P*T bound)      */
+  int64_t cand_capacity;       /* candidate-buffer rows of a handle (0: P*(T+1),
+                                  at most 2^22 rows and 1 GiB per buffer)    */
   int64_t max_aug_iters;       /* cap on Algorithm 1 iterations per call        */
 } mape_config;
 
@@ -170,7 +173,10 @@ typedef struct {
                               2 = |round(z)| > 256 met on the BF16 path (the
                               exactness bound of B round(z) in BF16; that
                               start's rounding is not collected),
-                              4 = |round(z)| > 2^20 met on the FP32 path   */
+                              4 = on the FP32 path, |round(z)| above
+                              (2^24 - 1) / max_i sum_j |B_ij|, beyond which
+                              B round(z) is not exact in FP32 (that start's
+                              rounding is not collected)                 */
   float* dbg_phi;          /* optional [P]: Phi at the input point            */
   float* dbg_grad;         /* optional [P x d]: gradient at the input point   */
   void* workspace;
@@ -364,6 +370,93 @@ int mape_get_solution(mape_handle h, int32_t* x, int64_t* fval);
 int mape_get_solutions(mape_handle h, int32_t* X, int64_t* fval, int32_t S);
 
 void mape_destroy(mape_handle h);
+
+/* ========================================================================== *
+ * Request server: continuous batching of instances on one GPU                *
+ * ========================================================================== */
+
+/* Requests (an instance with its starts and augmentation starts) are copied
+ * at submission and queued.  A scheduler thread admits them in arrival order
+ * while one of `max_slots` slots is free and the device-memory estimate
+ * (mape_request_bytes) of the running requests plus the next stays within
+ * `mem_cap_bytes`.  An admitted request runs on its slot's own stream through
+ * an instance handle: Algorithm 2 with dedup, kernel test and minimality
+ * filter, then Algorithm 1 from its starts.  The running requests' kernels
+ * overlap on the device; a request arriving while others run is admitted as
+ * soon as a slot and memory free up.  Each request's result is independent of
+ * what runs beside it.  (The paper has no server; this is an interface.) */
+typedef struct mape_server* mape_server_h;
+
+typedef struct {
+  mape_config cfg;          /* hyper-parameters of every request             */
+  size_t mem_cap_bytes;     /* admission budget of device memory             */
+  int32_t max_slots;        /* requests on the device at once (1..256)       */
+  int32_t keep_directions;  /* 1: keep each request's direction set on the
+                               host for mape_server_result                  */
+} mape_server_config;
+
+#define MAPE_REQ_QUEUED  0
+#define MAPE_REQ_RUNNING 1
+#define MAPE_REQ_DONE    2
+#define MAPE_REQ_FAILED  3
+
+typedef struct {
+  int32_t state, error;       /* MAPE_REQ_*, status of a failed request    */
+  int32_t n, m, P, pad0;
+  int64_t directions;         /* size of the direction set                  */
+  int64_t best_f;             /* best f over the augmentation starts        */
+  int64_t aug_iters;
+  size_t bytes;               /* admission estimate                         */
+  /* server clock, milliseconds: submission, admission, end of extraction
+   * (direction set ready), first improving move found, completion; time to
+   * first improving direction = t_first_improve - t_submit, time to
+   * termination = t_done - t_submit */
+  double t_submit_ms, t_admit_ms, t_extracted_ms, t_first_improve_ms, t_done_ms;
+} mape_request_info;
+
+typedef struct {
+  int64_t submitted, completed, failed, queued, running, peak_running;
+  size_t mem_in_use, mem_peak, mem_cap;
+} mape_server_stats;
+
+/* Device bytes a request of these sizes holds while it runs (what the handle
+ * allocates for the instance, its extraction and its augmentation), or 0 for
+ * invalid sizes.  Host-only arithmetic. */
+size_t mape_request_bytes(int32_t n, int32_t m, int32_t P, int32_t S, const mape_config* cfg);
+
+/* Errors: INVALID_ARG, CUDA. */
+int mape_server_create(const mape_server_config* cfg, mape_server_h* out);
+
+/* Queues a request; arguments as mape_create_instance, mape_extract_directions
+ * (Z0 [P x d] or G0 [P x n], host memory) and mape_augment (X0 [S x n]), all
+ * copied before the call returns.  *id identifies the request.
+ * Errors: INVALID_ARG, SHAPE, OOM (the request alone exceeds the memory cap,
+ * so it could never be admitted). */
+int mape_server_submit(mape_server_h s, const int32_t* A, const int64_t* b,
+                       const int32_t* l, const int32_t* u, const mape_problem* f,
+                       const int32_t* B, int32_t P, const float* Z0,
+                       const float* G0, const int32_t* X0, int32_t S,
+                       uint64_t* id);
+
+int mape_server_poll(mape_server_h s, uint64_t id, mape_request_info* info); /* never blocks */
+int mape_server_wait(mape_server_h s, uint64_t id, int64_t timeout_ns);      /* TIMEOUT, or the
+                                                                                request's status */
+int mape_server_wait_all(mape_server_h s, int64_t timeout_ns);               /* queue empty and
+                                                                                nothing running */
+
+/* Best x [n] and f of a finished request; with keep_directions, K and (if
+ * G != NULL) the direction set as int8 rows G [cap x n], sorted
+ * lexicographically.  CAPACITY if cap < K. */
+int mape_server_result(mape_server_h s, uint64_t id, int32_t* x, int64_t* fval,
+                       int8_t* G, int64_t cap, int64_t* K);
+
+/* Forgets a finished request (its host results). */
+int mape_server_release(mape_server_h s, uint64_t id);
+
+int mape_server_get_stats(mape_server_h s, mape_server_stats* st);
+
+/* Waits (up to 10 minutes) for the running requests, then stops. */
+void mape_server_destroy(mape_server_h s);
 
 /* Version string of the library build. */
 const char* mape_version(void);

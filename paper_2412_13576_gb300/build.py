@@ -55,7 +55,9 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         for f in futs:
             f.result()
     tmp = LIB + ".tmp"
-    cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
+    # cuBLAS serves the plain FP32 baseline path's GEMMs only
+    cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcublas", "-Xlinker", "-rpath", "-Xlinker",
+           "/usr/local/cuda/lib64", "-lpthread"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

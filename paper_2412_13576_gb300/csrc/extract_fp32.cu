@@ -1,25 +1,25 @@
-// Algorithm 2 (§3.2) on CUDA cores in FP32: the plain per-step path.
-//
-// Per Adam step three unfused kernels run over all P starts:
-//   forward_sign   S = sign(B z) (int8, coordinate-major), partial ||Bz||_1
-//   backward_adam  grad = B^T S + lambda1 (ceil z + floor z - 2 z) + inverse
-//                  norm term (Eq. (3)); Adam update of z, m, v; marks starts
-//                  whose rounding changed
-//   collect        for marked starts (one warp each): g = B round(z) in int32,
-//                  nonzero and C4 tests, canonical sign, append
-// State is kept coordinate-major ([d][P]) so that one thread per start reads
-// and writes coalesced rows; B is read through L1 as warp-wide broadcasts.
+// Algorithm 2 (§3.2) in FP32: the plain single-instance per-step path, the
+// baseline the tensor-core paths are measured against.  It is what a direct
+// PyTorch version of the method does on a GPU: per Adam step, the products
+// are FP32 GEMMs from cuBLAS (strict FP32, no TF32) and everything else is a
+// separate elementwise kernel:
+//   Y = B Z (GEMM), S = sign(Y), G = B^T S (GEMM), ||z||_inf and its first
+//   index per start, the gradient terms of Eq. (3) and the Adam update (marks
+//   starts whose rounding changed); on collection steps R = round(Z),
+//   B R (GEMM, exact: every |partial sum| stays below 2^24, else the start
+//   is flagged), the bound test (C4), the first nonzero entry and the
+//   append in canonical sign.
+// State is coordinate-major ([d][P]): elementwise kernels read and write it
+// coalesced, and it is the column-major P x d operand of the GEMMs.
 #include "common.cuh"
 #include "extract_internal.cuh"
 
-#include <vector>
+#include <cublas_v2.h>
+
 #include <cmath>
+#include <vector>
 
 namespace {
-
-constexpr int kThreads = 128;
-constexpr int kRowBlock = 16;   // rows of B per forward thread
-constexpr int kColBlock = 16;   // coordinates per backward pass
 
 __global__ void to_float_kernel(const int32_t* __restrict__ B, float* __restrict__ Bf, int64_t count) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -41,163 +41,141 @@ __global__ void transpose_kernel(const float* __restrict__ in, float* __restrict
   }
 }
 
-__global__ void forward_sign_kernel(const float* __restrict__ Bf, const float* __restrict__ Zt,
-                                    int8_t* __restrict__ S, float* __restrict__ l1_part,
-                                    int n, int d, int P) {
-  int p = blockIdx.x * kThreads + threadIdx.x;
-  int i0 = blockIdx.y * kRowBlock;
+// S = sign(Y), elementwise over [n][P]
+__global__ void sign_kernel(const float* __restrict__ Y, float* __restrict__ S, int64_t count) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < count) S[e] = (float)mape_sign_f(Y[e]);
+}
+
+// per start: ||z||_inf and its first index; with dbg, Phi at z (||Bz||_1 from Y)
+__global__ void zinf_kernel(const float* __restrict__ Zt, const float* __restrict__ Y, int n, int d, int P,
+                            float* __restrict__ zinf, int32_t* __restrict__ kmax, float lambda1, float lambda2,
+                            float* __restrict__ dbg_phi) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  float acc[kRowBlock];
-#pragma unroll
-  for (int r = 0; r < kRowBlock; ++r) acc[r] = 0.f;
-  int rows = min(kRowBlock, n - i0);
+  float zi = 0.f, frac = 0.f;
+  int k = 0;
   for (int j = 0; j < d; ++j) {
-    float zj = Zt[(int64_t)j * P + p];
-#pragma unroll
-    for (int r = 0; r < kRowBlock; ++r)
-      if (r < rows) acc[r] = fmaf(Bf[(int64_t)(i0 + r) * d + j], zj, acc[r]);
+    const float zj = Zt[(int64_t)j * P + p];
+    const float a = fabsf(zj);
+    if (a > zi) { zi = a; k = j; }
+    if (dbg_phi) frac += (zj - floorf(zj)) * (ceilf(zj) - zj);
   }
-  float l1 = 0.f;
-#pragma unroll
-  for (int r = 0; r < kRowBlock; ++r) {
-    if (r < rows) {
-      S[(int64_t)(i0 + r) * P + p] = (int8_t)mape_sign_f(acc[r]);
-      l1 += fabsf(acc[r]);
-    }
+  zinf[p] = zi;
+  kmax[p] = k;
+  if (dbg_phi) {
+    float l1 = 0.f;
+    for (int i = 0; i < n; ++i) l1 += fabsf(Y[(int64_t)i * P + p]);
+    const float inv = zi > 0.f ? fmaxf(1.f / zi - 1.f, 0.f) : INFINITY;
+    dbg_phi[p] = l1 + lambda1 * frac + lambda2 * inv;
   }
-  if (l1_part) l1_part[(int64_t)blockIdx.y * P + p] = l1;
 }
 
 struct StepParams {
   float lambda1, lambda2, lr, beta1, beta2, omb1, omb2, eps, bc1, bc2;
 };
 
-__global__ void backward_adam_kernel(const float* __restrict__ Bf, const int8_t* __restrict__ S,
-                                     float* __restrict__ Zt, float* __restrict__ Mt, float* __restrict__ Vt,
-                                     uint8_t* __restrict__ changed, StepParams sp,
-                                     int n, int d, int P, const float* __restrict__ l1_part, int nblk,
-                                     float* __restrict__ dbg_phi, float* __restrict__ dbg_grad) {
-  int p = blockIdx.x * kThreads + threadIdx.x;
-  if (p >= P) return;
-  // ||z||_inf and its first maximiser (inverse-norm term of Eq. (3))
-  float zinf = 0.f;
-  int kmax = 0;
-  float frac = 0.f;
-  for (int j = 0; j < d; ++j) {
-    float zj = Zt[(int64_t)j * P + p];
-    float a = fabsf(zj);
-    if (a > zinf) { zinf = a; kmax = j; }
-    if (dbg_phi) frac += (zj - floorf(zj)) * (ceilf(zj) - zj);
-  }
-  float inv_term = 0.f;  // gradient entry added at kmax
-  if (zinf < 1.f && zinf > 0.f) {
-    float zk = Zt[(int64_t)kmax * P + p];
-    inv_term = -sp.lambda2 * (float)mape_sign_f(zk) / (zinf * zinf);
-  }
-  if (dbg_phi) {
-    float l1 = 0.f;
-    for (int b = 0; b < nblk; ++b) l1 += l1_part[(int64_t)b * P + p];
-    float inv = zinf > 0.f ? fmaxf(1.f / zinf - 1.f, 0.f) : INFINITY;
-    dbg_phi[p] = l1 + sp.lambda1 * frac + sp.lambda2 * inv;
-  }
-  bool moved = false;
-  for (int j0 = 0; j0 < d; j0 += kColBlock) {
-    float g[kColBlock];
-#pragma unroll
-    for (int c = 0; c < kColBlock; ++c) g[c] = 0.f;
-    int cols = min(kColBlock, d - j0);
-    for (int i = 0; i < n; ++i) {
-      int s = S[(int64_t)i * P + p];
-      if (s == 0) continue;
-      float fs = (float)s;
-      const float* brow = Bf + (int64_t)i * d + j0;
-#pragma unroll
-      for (int c = 0; c < kColBlock; ++c)
-        if (c < cols) g[c] = fmaf(brow[c], fs, g[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < kColBlock; ++c) {
-      if (c >= cols) continue;
-      int j = j0 + c;
-      int64_t at = (int64_t)j * P + p;
-      float z = Zt[at];
-      float grad = g[c] + sp.lambda1 * (ceilf(z) + floorf(z) - 2.f * z);
-      if (j == kmax) grad += inv_term;
-      if (dbg_grad) dbg_grad[(int64_t)p * d + j] = grad;
-      float m = sp.beta1 * Mt[at] + sp.omb1 * grad;
-      float v = sp.beta2 * Vt[at] + sp.omb2 * grad * grad;
-      float mhat = m / sp.bc1;
-      float vhat = v / sp.bc2;
-      float zn = z - sp.lr * mhat / (sqrtf(vhat) + sp.eps);
-      Mt[at] = m;
-      Vt[at] = v;
-      Zt[at] = zn;
-      moved |= (rintf(zn) != rintf(z));
-    }
-  }
-  if (moved) changed[p] = 1;
+// the rest of the gradient and the Adam update, elementwise over [d][P]
+__global__ void adam_kernel(const float* __restrict__ G, float* __restrict__ Zt, float* __restrict__ Mt,
+                            float* __restrict__ Vt, const float* __restrict__ zinf, const int32_t* __restrict__ kmax,
+                            uint8_t* __restrict__ changed, StepParams sp, int d, int P,
+                            float* __restrict__ dbg_grad) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)d * P) return;
+  const int j = (int)(e / P), p = (int)(e % P);
+  const float z = Zt[e];
+  float grad = G[e] + sp.lambda1 * (ceilf(z) + floorf(z) - 2.f * z);
+  const float zi = zinf[p];
+  if (j == kmax[p] && zi < 1.f && zi > 0.f) grad += -sp.lambda2 * (float)mape_sign_f(z) / (zi * zi);
+  if (dbg_grad) dbg_grad[(int64_t)p * d + j] = grad;
+  const float m = sp.beta1 * Mt[e] + sp.omb1 * grad;
+  const float v = sp.beta2 * Vt[e] + sp.omb2 * grad * grad;
+  const float mhat = m / sp.bc1;
+  const float vhat = v / sp.bc2;
+  const float zn = z - sp.lr * mhat / (sqrtf(vhat) + sp.eps);
+  Mt[e] = m;
+  Vt[e] = v;
+  Zt[e] = zn;
+  if (rintf(zn) != rintf(z)) changed[p] = 1;
 }
 
-// One warp per start: g = B round(z) exactly in int32, tests, append.
-__global__ void collect_kernel(const int32_t* __restrict__ B, const float* __restrict__ Zt,
-                               const int32_t* __restrict__ span, uint8_t* __restrict__ changed,
-                               int n, int d, int P, int8_t* __restrict__ cand, int ldc,
-                               int64_t cap, unsigned long long* __restrict__ count,
-                               int32_t* __restrict__ flags) {
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (warp >= P) return;
-  int p = warp;
-  if (!changed[p]) return;
-  __syncwarp();
-  if (lane == 0) changed[p] = 0;
-  // per-lane rows i = lane, lane + 32, ...
-  bool valid = true, nonzero = false;
-  int first_i = 1 << 30, first_sign = 0;
-  bool range_bad = false;
-  for (int i = lane; i < n; i += 32) {
-    int acc = 0;
-    for (int j = 0; j < d; ++j) {
-      float zr = rintf(Zt[(int64_t)j * P + p]);
-      if (fabsf(zr) > 1048576.f) { range_bad = true; zr = 0.f; }
-      acc += B[(int64_t)i * d + j] * (int)zr;
+// R = round(Z) for the exact map; a start with |round z| above rlim (so that
+// B round(z) could leave the exact FP32 range) is flagged and mapped as 0
+__global__ void round_kernel(const float* __restrict__ Zt, float* __restrict__ R, int d, int P, float rlim,
+                             const uint8_t* __restrict__ changed, uint32_t* __restrict__ bad) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)d * P) return;
+  const int p = (int)(e % P);
+  float r = rintf(Zt[e]);
+  if (fabsf(r) > rlim) {
+    if (changed[p]) atomicOr(&bad[p], 4u);
+    r = 0.f;
+  }
+  R[e] = r;
+}
+
+// max_i sum_j |B_ij|
+__global__ void row_norm_kernel(const int32_t* __restrict__ B, int n, int d, int32_t* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t s = 0;
+  for (int j = 0; j < d; ++j) s += abs(B[(int64_t)i * d + j]);
+  atomicMax(out, (int32_t)(s < 0x7fffffff ? s : 0x7fffffff));
+}
+
+// The collection of Algorithm 2 after the GEMM B round(Z): map (one thread
+// per start whose rounding changed) tests C4, finds the first nonzero entry
+// and stages the row as int8 [n x P]; append (one warp per such start) takes
+// a slot for a valid row and writes it in canonical sign.
+constexpr int kNoFirst = 0x7f7f7f7f;  // a byte pattern, so that cudaMemset can write it
+
+__global__ void map_kernel(const float* __restrict__ Gm, const int32_t* __restrict__ span,
+                           const uint8_t* __restrict__ changed, int n, int P, int8_t* __restrict__ S8,
+                           uint32_t* __restrict__ bad, int32_t* __restrict__ first) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P || !changed[p]) return;
+  uint32_t fl = 0u;
+  int fz = kNoFirst;
+  for (int i = 0; i < n; ++i) {
+    const int g = (int)Gm[(int64_t)i * P + p];
+    if (g > span[i] || -g > span[i]) fl |= 1u;
+    if (g != 0 && fz == kNoFirst) fz = (i << 1) | (g < 0 ? 1 : 0);
+    S8[(int64_t)i * P + p] = (int8_t)g;
+  }
+  if (fl) atomicOr(&bad[p], fl);
+  first[p] = fz;
+}
+
+__global__ void append_kernel(uint8_t* __restrict__ changed, uint32_t* __restrict__ bad, int32_t* __restrict__ first,
+                              const int8_t* __restrict__ S8, int n, int P, int8_t* __restrict__ cand, int ldc,
+                              int64_t cap, unsigned long long* __restrict__ count, int32_t* __restrict__ flags) {
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (p >= P || !changed[p]) return;
+  long long slot = -1;
+  int neg = 0;
+  if (lane == 0) {
+    const uint32_t b = bad[p];
+    const int f = first[p];
+    changed[p] = 0;
+    bad[p] = 0u;
+    first[p] = kNoFirst;
+    if (b & 4u) {
+      atomicOr(flags, 4);
+    } else if (!(b & 1u) && f != kNoFirst) {
+      const unsigned long long at = atomicAdd(count, 1ull);
+      if ((int64_t)at < cap) slot = (long long)at;
+      else atomicOr(flags, 1);
     }
-    if (acc != 0) {
-      nonzero = true;
-      if (i < first_i) { first_i = i; first_sign = acc > 0 ? 1 : -1; }
-    }
-    if (abs(acc) > span[i]) valid = false;
+    neg = f & 1;
   }
-  valid = __all_sync(0xffffffffu, valid);
-  nonzero = __any_sync(0xffffffffu, nonzero);
-  range_bad = __any_sync(0xffffffffu, range_bad);
-  if (range_bad) {
-    if (lane == 0) atomicOr(flags, 4);
-    return;
-  }
-  // canonical sign: sign of the first nonzero entry
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    int oi = __shfl_xor_sync(0xffffffffu, first_i, off);
-    int os = __shfl_xor_sync(0xffffffffu, first_sign, off);
-    if (oi < first_i) { first_i = oi; first_sign = os; }
-  }
-  if (!valid || !nonzero) return;
-  unsigned long long slot = 0;
-  if (lane == 0) slot = atomicAdd(count, 1ull);
   slot = __shfl_sync(0xffffffffu, slot, 0);
-  if ((int64_t)slot >= cap) {
-    if (lane == 0) atomicOr(flags, 1);
-    return;
-  }
-  int8_t* row = cand + (int64_t)slot * ldc;
+  neg = __shfl_sync(0xffffffffu, neg, 0);
+  if (slot < 0) return;
+  int8_t* row = cand + slot * ldc;
   for (int i = lane; i < ldc; i += 32) {
-    int v = 0;
-    if (i < n) {
-      for (int j = 0; j < d; ++j) v += B[(int64_t)i * d + j] * (int)rintf(Zt[(int64_t)j * P + p]);
-      v *= first_sign;
-    }
-    row[i] = (int8_t)v;
+    const int v = i < n ? (int)S8[(int64_t)i * P + p] : 0;
+    row[i] = (int8_t)(neg ? -v : v);
   }
 }
 
@@ -267,6 +245,31 @@ __global__ void phi_grad_kernel(const int32_t* __restrict__ B, const float* __re
   }
 }
 
+template <typename Carve>
+void carve_fp32(Carve& cv, int32_t n, int32_t d, int32_t P) {
+  cv.template take<float>((size_t)n * d);                           // Bf
+  for (int k = 0; k < 3; ++k) cv.template take<float>((size_t)d * P);  // Zt, Mt, Vt
+  cv.template take<float>((size_t)n * P);                           // Y, then B round(Z)
+  cv.template take<float>((size_t)n * P);                           // S
+  cv.template take<float>((size_t)d * P);                           // G, then round(Z)
+  cv.template take<float>((size_t)P);                               // ||z||_inf
+  cv.template take<int32_t>((size_t)P);                             // its first index
+  cv.template take<uint8_t>((size_t)P);                             // changed
+  cv.template take<int8_t>((size_t)n * P);                          // staged candidate rows
+  cv.template take<uint32_t>((size_t)P);                            // bound / range flags
+  cv.template take<int32_t>((size_t)P);                             // first nonzero entry
+  cv.template take<int32_t>(1);                                     // max row sum of |B|
+}
+
+// one cuBLAS handle per host thread (handles are not shared between threads)
+struct BlasHandle {
+  cublasHandle_t h = nullptr;
+  ~BlasHandle() {
+    if (h) cublasDestroy(h);
+  }
+};
+thread_local BlasHandle t_blas;
+
 }  // namespace
 
 namespace mape_detail {
@@ -282,13 +285,17 @@ void adam_bias_table(const mape_extract_args* a, std::vector<float2>& out) {
 
 size_t extract_fp32_workspace(int32_t n, int32_t d, int32_t P) {
   Sizer s;
-  s.take<float>((size_t)n * d);                // Bf
-  for (int k = 0; k < 3; ++k) s.take<float>((size_t)d * P);  // Zt, Mt, Vt (carved separately)
-  s.take<int8_t>((size_t)n * P);               // S
-  s.take<float>((size_t)ceil_div(n, kRowBlock) * P);  // l1 partials
-  s.take<uint8_t>((size_t)P);                  // changed
+  carve_fp32(s, n, d, P);
   return s.bytes();
 }
+
+#define MAPE_BLAS_TRY(expr)                                                               \
+  do {                                                                                    \
+    if ((expr) != CUBLAS_STATUS_SUCCESS) {                                                \
+      mape_detail::record_cuda_error(cudaErrorUnknown, #expr " (cuBLAS)", __FILE__, __LINE__); \
+      return MAPE_ERR_CUDA;                                                               \
+    }                                                                                     \
+  } while (0)
 
 int extract_fp32(const mape_extract_args* a, cudaStream_t st) {
   const int n = a->n, d = a->d, P = a->P;
@@ -297,43 +304,72 @@ int extract_fp32(const mape_extract_args* a, cudaStream_t st) {
   float* Zt = cv.take<float>((size_t)d * P);
   float* Mt = cv.take<float>((size_t)d * P);
   float* Vt = cv.take<float>((size_t)d * P);
-  int8_t* S = cv.take<int8_t>((size_t)n * P);
-  int nblk = (int)ceil_div(n, kRowBlock);
-  float* l1p = cv.take<float>((size_t)nblk * P);
+  float* Y = cv.take<float>((size_t)n * P);
+  float* S = cv.take<float>((size_t)n * P);
+  float* G = cv.take<float>((size_t)d * P);
+  float* zinf = cv.take<float>((size_t)P);
+  int32_t* kmax = cv.take<int32_t>((size_t)P);
   uint8_t* changed = cv.take<uint8_t>((size_t)P);
+  int8_t* S8 = cv.take<int8_t>((size_t)n * P);
+  uint32_t* badw = cv.take<uint32_t>((size_t)P);
+  int32_t* firstw = cv.take<int32_t>((size_t)P);
+  int32_t* bnorm = cv.take<int32_t>(1);
   if (!cv.ok) return MAPE_ERR_CAPACITY;
+  if (!t_blas.h) {
+    MAPE_BLAS_TRY(cublasCreate(&t_blas.h));
+    MAPE_BLAS_TRY(cublasSetMathMode(t_blas.h, CUBLAS_PEDANTIC_MATH));  // strict FP32
+  }
+  cublasHandle_t hb = t_blas.h;
+  MAPE_BLAS_TRY(cublasSetStream(hb, st));
+  MAPE_CUDA_TRY(cudaMemsetAsync(badw, 0, sizeof(uint32_t) * P, st));
+  MAPE_CUDA_TRY(cudaMemsetAsync(firstw, 0x7f, sizeof(int32_t) * P, st));
+  MAPE_CUDA_TRY(cudaMemsetAsync(bnorm, 0, sizeof(int32_t), st));
 
   std::vector<float2> bc;
   adam_bias_table(a, bc);
 
-  mape_detail::launch(to_float_kernel, (unsigned)ceil_div((int64_t)n * d, 256), 256, 0, st, a->B, Bf, (int64_t)n * d);
+  launch(to_float_kernel, (unsigned)ceil_div((int64_t)n * d, 256), 256, 0, st, a->B, Bf, (int64_t)n * d);
+  launch(row_norm_kernel, (unsigned)ceil_div(n, 128), 128, 0, st, a->B, n, d, bnorm);
   dim3 tb(32, 8);
-  mape_detail::launch(transpose_kernel, dim3((unsigned)ceil_div(d, 32), (unsigned)ceil_div(P, 32)), tb, 0, st, a->Z, Zt, P, d);
-  mape_detail::launch(transpose_kernel, dim3((unsigned)ceil_div(d, 32), (unsigned)ceil_div(P, 32)), tb, 0, st, a->M, Mt, P, d);
-  mape_detail::launch(transpose_kernel, dim3((unsigned)ceil_div(d, 32), (unsigned)ceil_div(P, 32)), tb, 0, st, a->V, Vt, P, d);
-  mape_detail::launch(fill_u8_kernel, (unsigned)ceil_div(P, 256), 256, 0, st, changed, 1, P);
+  launch(transpose_kernel, dim3((unsigned)ceil_div(d, 32), (unsigned)ceil_div(P, 32)), tb, 0, st, a->Z, Zt, P, d);
+  launch(transpose_kernel, dim3((unsigned)ceil_div(d, 32), (unsigned)ceil_div(P, 32)), tb, 0, st, a->M, Mt, P, d);
+  launch(transpose_kernel, dim3((unsigned)ceil_div(d, 32), (unsigned)ceil_div(P, 32)), tb, 0, st, a->V, Vt, P, d);
+  launch(fill_u8_kernel, (unsigned)ceil_div(P, 256), 256, 0, st, changed, 1, P);
   MAPE_LAUNCH_CHECK();
+  int32_t h_bnorm = 0;
+  MAPE_CUDA_TRY(cudaMemcpyAsync(&h_bnorm, bnorm, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  // |round z_j| <= rlim keeps every partial sum of B round(z) below 2^24
+  const float rlim = h_bnorm > 0 ? std::floor(16777215.f / (float)h_bnorm) : 16777215.f;
 
-  dim3 fgrid((unsigned)ceil_div(P, kThreads), (unsigned)nblk);
-  unsigned bgrid = (unsigned)ceil_div(P, kThreads);
-  unsigned cgrid = (unsigned)ceil_div((int64_t)P * 32, 256);
+  const float one = 1.f, zero = 0.f;
+  const int64_t nP = (int64_t)n * P, dP = (int64_t)d * P;
+  const unsigned g_n = (unsigned)ceil_div(nP, 256), g_d = (unsigned)ceil_div(dP, 256);
+  const unsigned g_p = (unsigned)ceil_div(P, 128), g_pw = (unsigned)ceil_div((int64_t)P * 32, 256);
   for (int s = 0; s < a->T; ++s) {
-    const bool first = (s == 0);
+    const bool dbg = s == 0;
     StepParams sp{a->lambda1, a->lambda2, a->lr, (float)a->beta1, (float)a->beta2, (float)(1.0 - a->beta1),
                   (float)(1.0 - a->beta2), a->eps, bc[s].x, bc[s].y};
-    mape_detail::launch(forward_sign_kernel, fgrid, kThreads, 0, st, Bf, Zt, S, first && a->dbg_phi ? l1p : nullptr, n, d, P);
-    mape_detail::launch(backward_adam_kernel, bgrid, kThreads, 0, st, Bf, S, Zt, Mt, Vt, changed, sp, n, d, P, l1p, nblk,
-                                                     first ? a->dbg_phi : nullptr,
-                                                     first ? a->dbg_grad : nullptr);
-    int t = a->t0 + s + 1;
-    if (t % a->period == 0)
-      mape_detail::launch(collect_kernel, cgrid, 256, 0, st, a->B, Zt, a->span, changed, n, d, P, a->cand, a->ldc,
-                                            a->cand_cap, a->cand_count, a->flags);
+    // column-major views: Zt is P x d (ld P), Bf is d x n (ld d), Y and S are P x n, G is P x d
+    MAPE_BLAS_TRY(cublasSgemm(hb, CUBLAS_OP_N, CUBLAS_OP_N, P, n, d, &one, Zt, P, Bf, d, &zero, Y, P));
+    launch(sign_kernel, g_n, 256, 0, st, Y, S, nP);
+    MAPE_BLAS_TRY(cublasSgemm(hb, CUBLAS_OP_N, CUBLAS_OP_T, P, d, n, &one, S, P, Bf, d, &zero, G, P));
+    launch(zinf_kernel, g_p, 128, 0, st, Zt, Y, n, d, P, zinf, kmax, a->lambda1, a->lambda2,
+           dbg ? a->dbg_phi : nullptr);
+    launch(adam_kernel, g_d, 256, 0, st, G, Zt, Mt, Vt, zinf, kmax, changed, sp, d, P, dbg ? a->dbg_grad : nullptr);
+    const int t = a->t0 + s + 1;
+    if (t % a->period == 0) {
+      launch(round_kernel, g_d, 256, 0, st, Zt, G, d, P, rlim, changed, badw);
+      MAPE_BLAS_TRY(cublasSgemm(hb, CUBLAS_OP_N, CUBLAS_OP_N, P, n, d, &one, G, P, Bf, d, &zero, Y, P));
+      launch(map_kernel, g_p, 128, 0, st, Y, a->span, changed, n, P, S8, badw, firstw);
+      launch(append_kernel, g_pw, 256, 0, st, changed, badw, firstw, S8, n, P, a->cand, a->ldc, a->cand_cap,
+             a->cand_count, a->flags);
+    }
     MAPE_LAUNCH_CHECK();
   }
-  mape_detail::launch(transpose_kernel, dim3((unsigned)ceil_div(P, 32), (unsigned)ceil_div(d, 32)), tb, 0, st, Zt, a->Z, d, P);
-  mape_detail::launch(transpose_kernel, dim3((unsigned)ceil_div(P, 32), (unsigned)ceil_div(d, 32)), tb, 0, st, Mt, a->M, d, P);
-  mape_detail::launch(transpose_kernel, dim3((unsigned)ceil_div(P, 32), (unsigned)ceil_div(d, 32)), tb, 0, st, Vt, a->V, d, P);
+  launch(transpose_kernel, dim3((unsigned)ceil_div(P, 32), (unsigned)ceil_div(d, 32)), tb, 0, st, Zt, a->Z, d, P);
+  launch(transpose_kernel, dim3((unsigned)ceil_div(P, 32), (unsigned)ceil_div(d, 32)), tb, 0, st, Mt, a->M, d, P);
+  launch(transpose_kernel, dim3((unsigned)ceil_div(P, 32), (unsigned)ceil_div(d, 32)), tb, 0, st, Vt, a->V, d, P);
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
 }

@@ -401,7 +401,7 @@ extern "C" int mape_extract_directions(mape_handle h, int32_t P, const float* Z0
   h->dirs = nullptr;
   const int n = h->n, d = h->d, ldg = h->ldg;
   const int64_t T = h->cfg.T;
-  int64_t cap = h->cfg.cand_capacity > 0 ? h->cfg.cand_capacity : std::min<int64_t>((int64_t)P * T + P, (int64_t)1 << 22);
+  int64_t cap = h->cfg.cand_capacity > 0 ? h->cfg.cand_capacity : default_cand_capacity(P, T, ldg);
   cap = std::max<int64_t>(cap, (int64_t)P + 1);
   h->cap = cap;
   h->P = P;

@@ -83,6 +83,33 @@ class Status(C.Structure):
         return d
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("cfg", Config), ("mem_cap_bytes", C.c_size_t), ("max_slots", I32), ("keep_directions", I32)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("state", I32), ("error", I32), ("n", I32), ("m", I32), ("P", I32), ("pad0", I32),
+                ("directions", I64), ("best_f", I64), ("aug_iters", I64), ("bytes", C.c_size_t),
+                ("t_submit_ms", C.c_double), ("t_admit_ms", C.c_double), ("t_extracted_ms", C.c_double),
+                ("t_first_improve_ms", C.c_double), ("t_done_ms", C.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
+        d["state"] = REQ_STATES[self.state] if 0 <= self.state < len(REQ_STATES) else self.state
+        return d
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", I64), ("completed", I64), ("failed", I64), ("queued", I64), ("running", I64),
+                ("peak_running", I64), ("mem_in_use", C.c_size_t), ("mem_peak", C.c_size_t),
+                ("mem_cap", C.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+REQ_STATES = ("QUEUED", "RUNNING", "DONE", "FAILED")
+
 _LIB = None
 
 _SIGS = {
@@ -121,6 +148,17 @@ _SIGS = {
     "mape_get_solution": (C.c_int, [P_, P_, C.POINTER(I64)]),
     "mape_get_solutions": (C.c_int, [P_, P_, P_, I32]),
     "mape_destroy": (None, [P_]),
+    "mape_request_bytes": (C.c_size_t, [I32, I32, I32, I32, C.POINTER(Config)]),
+    "mape_server_create": (C.c_int, [C.POINTER(ServerConfig), C.POINTER(P_)]),
+    "mape_server_submit": (C.c_int, [P_, P_, P_, P_, P_, C.POINTER(Problem), P_, I32, P_, P_, P_, I32,
+                                     C.POINTER(C.c_uint64)]),
+    "mape_server_poll": (C.c_int, [P_, C.c_uint64, C.POINTER(RequestInfo)]),
+    "mape_server_wait": (C.c_int, [P_, C.c_uint64, I64]),
+    "mape_server_wait_all": (C.c_int, [P_, I64]),
+    "mape_server_result": (C.c_int, [P_, C.c_uint64, P_, C.POINTER(I64), P_, I64, C.POINTER(I64)]),
+    "mape_server_release": (C.c_int, [P_, C.c_uint64]),
+    "mape_server_get_stats": (C.c_int, [P_, C.POINTER(ServerStats)]),
+    "mape_server_destroy": (None, [P_]),
 }
 
 
@@ -422,3 +460,93 @@ class Instance:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ---- request server (host numpy arrays) --------------------------------------
+
+class Server:
+    """mape_server_create ... mape_server_destroy: continuous batching of
+    instances on one GPU, admitted by device memory."""
+
+    def __init__(self, cfg: Config | None = None, mem_cap_bytes: int = 150 << 30, max_slots: int = 8,
+                 keep_directions: bool = False):
+        sc = ServerConfig()
+        sc.cfg = cfg if cfg is not None else default_config()
+        sc.mem_cap_bytes, sc.max_slots, sc.keep_directions = int(mem_cap_bytes), int(max_slots), int(keep_directions)
+        self.cfg = sc.cfg
+        h = C.c_void_p()
+        _check(lib().mape_server_create(C.byref(sc), C.byref(h)), "mape_server_create")
+        self.h = h
+        self._n = {}
+
+    def submit(self, inst, P, Z0=None, G0=None, X0=None) -> int:
+        """Queues a generated instance with P starts (Z0 [P x d] or G0 [P x n])
+        and augmentation starts X0 [S x n] (default: x̄)."""
+        A, b, l, u, B = (_np(inst.A, np.int32), _np(inst.b, np.int64), _np(inst.l, np.int32),
+                         _np(inst.u, np.int32), _np(inst.B, np.int32))
+        Q, c = _np(inst.Q, np.int32), _np(inst.c, np.int32)
+        w = None if inst.w is None else _np(inst.w, np.int32)
+        X0 = _np(np.atleast_2d(inst.xbar if X0 is None else X0), np.int32)
+        Z0 = None if Z0 is None else _np(Z0, np.float32)
+        G0 = None if G0 is None else _np(G0, np.float32)
+        m, n = A.shape
+        prob = Problem(n, m, _host(Q), _host(c), _host(w))
+        rid = C.c_uint64(0)
+        _check(lib().mape_server_submit(self.h, _host(A), _host(b), _host(l), _host(u), C.byref(prob), _host(B), P,
+                                        _host(Z0), _host(G0), _host(X0), X0.shape[0], C.byref(rid)),
+               "mape_server_submit")
+        self._n[rid.value] = n
+        return rid.value
+
+    def info(self, rid) -> dict:
+        st = RequestInfo()
+        _check(lib().mape_server_poll(self.h, rid, C.byref(st)), "mape_server_poll")
+        return st.as_dict()
+
+    def wait(self, rid, timeout_s: float = 600.0):
+        _check(lib().mape_server_wait(self.h, rid, int(timeout_s * 1e9)), "mape_server_wait")
+
+    def wait_all(self, timeout_s: float = 3600.0):
+        _check(lib().mape_server_wait_all(self.h, int(timeout_s * 1e9)), "mape_server_wait_all")
+
+    def result(self, rid, directions: bool = False):
+        n = self._n[rid]
+        x = np.empty(n, dtype=np.int32)
+        f = I64(0)
+        K = I64(0)
+        _check(lib().mape_server_result(self.h, rid, _host(x), C.byref(f), None, 0, C.byref(K)), "mape_server_result")
+        if not directions:
+            return x, f.value
+        G = np.empty((K.value, n), dtype=np.int8)
+        _check(lib().mape_server_result(self.h, rid, None, None, _host(G), K.value, C.byref(K)), "mape_server_result")
+        return x, f.value, G
+
+    def release(self, rid):
+        _check(lib().mape_server_release(self.h, rid), "mape_server_release")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().mape_server_get_stats(self.h, C.byref(st)), "mape_server_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mape_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def request_bytes(n, m, P, S, cfg: Config | None = None) -> int:
+    cfg = cfg if cfg is not None else default_config()
+    return int(lib().mape_request_bytes(n, m, P, S, C.byref(cfg)))

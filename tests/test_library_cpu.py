@@ -51,6 +51,57 @@ def test_struct_layouts_match_binding(tmp_path, lib):
     assert got == expect
 
 
+def test_server_struct_layouts_match_binding(tmp_path, lib):
+    from paper_2412_13576_gb300 import mape
+    prog = tmp_path / "sizes2.c"
+    prog.write_text('#include "mape.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){'
+                    'printf("%zu %zu %zu %zu %zu\\n", sizeof(mape_server_config), sizeof(mape_request_info),'
+                    'sizeof(mape_server_stats), offsetof(mape_server_config, max_slots),'
+                    'offsetof(mape_request_info, t_first_improve_ms));return 0;}')
+    exe = tmp_path / "sizes2"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()))
+    expect = [ctypes.sizeof(mape.ServerConfig), ctypes.sizeof(mape.RequestInfo), ctypes.sizeof(mape.ServerStats),
+              mape.ServerConfig.max_slots.offset, mape.RequestInfo.t_first_improve_ms.offset]
+    assert got == expect
+
+
+def test_request_bytes_estimate(lib):
+    """The admission estimate covers at least the FP32 state and the three
+    candidate buffers, grows with P and n, and is 0 for invalid sizes."""
+    from paper_2412_13576_gb300 import mape
+    cfg = mape.default_config(T=1000)
+    n, m, P = 500, 100, 1024
+    b = mape.request_bytes(n, m, P, 1, cfg)
+    ldg = 512
+    cap = min(P * 1001, 1 << 22, (1 << 30) // ldg)
+    assert b >= 3 * P * (n - m) * 4 + 3 * cap * ldg
+    assert mape.request_bytes(n, m, 2 * P, 1, cfg) > b
+    assert mape.request_bytes(2 * n, 2 * m, P, 1, cfg) > b
+    assert mape.request_bytes(n, m, P, 8, cfg) > b
+    small = mape.default_config(T=1000, cand_capacity=4096)
+    assert mape.request_bytes(n, m, P, 1, small) < b
+    assert mape.request_bytes(n, n, P, 1, cfg) == 0
+    assert mape.request_bytes(n, m, 0, 1, cfg) == 0
+    assert lib.mape_request_bytes(n, m, P, 1, None) == 0
+
+
+def test_server_argument_checks_without_device(lib):
+    from paper_2412_13576_gb300 import mape
+    h = ctypes.c_void_p()
+    assert lib.mape_server_create(None, ctypes.byref(h)) == -1
+    sc = mape.ServerConfig()
+    sc.cfg = mape.default_config()
+    sc.mem_cap_bytes, sc.max_slots = 1 << 30, 0
+    assert lib.mape_server_create(ctypes.byref(sc), ctypes.byref(h)) == -1
+    rid = ctypes.c_uint64(0)
+    assert lib.mape_server_submit(None, None, None, None, None, None, None, 1, None, None, None, 1,
+                                  ctypes.byref(rid)) == -1
+    assert lib.mape_server_poll(None, 1, None) == -1
+    assert lib.mape_server_wait_all(None, 0) == -1
+    lib.mape_server_destroy(None)
+
+
 def test_default_config_is_the_papers(lib):
     from paper_2412_13576_gb300 import mape
     c = mape.default_config()
