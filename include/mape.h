@@ -189,6 +189,23 @@ typedef struct {
 size_t mape_extract_workspace_bytes(int32_t n, int32_t d, int32_t P, int32_t precision);
 int mape_extract(const mape_extract_args* args, void* stream);
 
+/* a3-a8 for many instances at once (uneven n, d and P): every call of
+ * `items` as in mape_extract (each with its own B, state, candidate buffer,
+ * counter, flags and workspace of mape_extract_workspace_bytes), all with the
+ * same t0, T, period and BF16 precision.  The calls that fit the resident
+ * kernel run as one persistent launch per kernel variant (identity-topped or
+ * general B, state in TMEM or not) over all their tiles; the others run the
+ * streamed kernels with three launches per step covering all of them; all of
+ * it is captured into one CUDA graph and launched (not on the legacy default
+ * stream, which is not capturable: there the kernels are launched directly).
+ * Each call's results are identical to its own mape_extract.  `workspace`
+ * holds the batch's tables (mape_extract_batch_workspace_bytes).
+ * Errors: as mape_extract, plus INVALID_ARG for differing t0, T, period or
+ * precision, or an FP32 precision.  Synchronous. */
+size_t mape_extract_batch_workspace_bytes(const mape_extract_args* items, int32_t count);
+int mape_extract_batch(const mape_extract_args* items, int32_t count,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
 /* a10 -- set union of Algorithm 2: removes repeated rows of `cand` (count
  * rows, pitch ldc, n meaningful bytes) with a device hash table, and writes
  * the distinct rows to `uniq` sorted lexicographically (signed bytes, first

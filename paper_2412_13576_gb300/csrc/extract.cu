@@ -3,10 +3,13 @@
 #include "common.cuh"
 #include "extract_internal.cuh"
 
+#include <memory>
+
 #include <cstdio>
 #include <cstring>
 #include <atomic>
 #include <mutex>
+#include <vector>
 
 namespace mape_detail {
 
@@ -93,4 +96,146 @@ extern "C" int mape_extract(const mape_extract_args* a, void* stream) {
   }
   if (a->workspace_bytes < mape_detail::extract_fp32_workspace(a->n, a->d, a->P)) return MAPE_ERR_CAPACITY;
   return mape_detail::extract_fp32(a, st);
+}
+
+namespace {
+
+int check_item(const mape_extract_args* a) {
+  if (a->n <= 0 || a->d <= 0 || a->d > a->n || a->P < 0 || a->T < 0 || a->t0 < 0 || a->period <= 0)
+    return MAPE_ERR_INVALID_ARG;
+  if (!a->B || !a->span || !a->cand_count || !a->flags) return MAPE_ERR_INVALID_ARG;
+  if (a->P > 0 && (!a->Z || !a->M || !a->V)) return MAPE_ERR_INVALID_ARG;
+  if (a->ldc < a->n || a->ldc % 16 != 0 || a->cand_cap < 0 || (a->cand_cap > 0 && !a->cand))
+    return MAPE_ERR_INVALID_ARG;
+  const int32_t base = a->precision & MAPE_PREC_MASK;
+  if (!valid_precision(a->precision) || base == MAPE_PREC_FP32) return MAPE_ERR_INVALID_ARG;
+  if (!mape_detail::extract_stream_supported(a->n, a->d)) return MAPE_ERR_SHAPE;
+  if (a->workspace_bytes < mape_extract_workspace_bytes(a->n, a->d, a->P, a->precision)) return MAPE_ERR_CAPACITY;
+  return MAPE_OK;
+}
+
+}  // namespace
+
+extern "C" size_t mape_extract_batch_workspace_bytes(const mape_extract_args* items, int32_t count) {
+  if (!items || count <= 0) return 0;
+  std::vector<const mape_extract_args*> ptrs;
+  for (int i = 0; i < count; ++i) ptrs.push_back(&items[i]);
+  mape_detail::Sizer s;
+  s.take<int32_t>((size_t)count);
+  s.take<char>(mape_detail::extract_tc_batch_workspace(ptrs.data(), count));
+  s.take<char>(mape_detail::extract_stream_batch_workspace(ptrs.data(), count));
+  return s.bytes();
+}
+
+extern "C" int mape_extract_batch(const mape_extract_args* items, int32_t count, void* workspace,
+                                  size_t workspace_bytes, void* stream) {
+  using namespace mape_detail;
+  if (!items || count < 0) return MAPE_ERR_INVALID_ARG;
+  if (count == 0) return MAPE_OK;
+  std::vector<const mape_extract_args*> live;
+  for (int i = 0; i < count; ++i) {
+    const mape_extract_args* a = &items[i];
+    int rc = check_item(a);
+    if (rc != MAPE_OK) return rc;
+    if (a->T != items[0].T || a->t0 != items[0].t0 || a->period != items[0].period ||
+        (a->precision & MAPE_PREC_MASK) != (items[0].precision & MAPE_PREC_MASK))
+      return MAPE_ERR_INVALID_ARG;
+    if (a->P > 0 && a->T > 0) live.push_back(a);
+  }
+  if (live.empty()) return MAPE_OK;
+  if (workspace_bytes < mape_extract_batch_workspace_bytes(items, count)) return MAPE_ERR_CAPACITY;
+  cudaStream_t st = as_stream(stream);
+  // the per-call precision word carries only the base precision into the kernels
+  std::vector<mape_extract_args> calls;
+  calls.reserve(live.size());
+  for (auto* a : live) {
+    calls.push_back(*a);
+    calls.back().precision = a->precision & MAPE_PREC_MASK;
+  }
+  const int nl = (int)calls.size();
+  std::vector<const mape_extract_args*> cp;
+  for (auto& c : calls) cp.push_back(&c);
+  Carver cv(workspace, workspace_bytes);
+  int32_t* dflags = cv.take<int32_t>((size_t)count);
+  const size_t tws = extract_tc_batch_workspace(cp.data(), nl), sws = extract_stream_batch_workspace(cp.data(), nl);
+  char* tw = cv.take<char>(tws);
+  char* sw = cv.take<char>(sws);
+  if (!cv.ok) return MAPE_ERR_CAPACITY;
+  std::vector<bool> ids;
+  int rc = identity_tops(cp.data(), nl, dflags, st, ids);
+  if (rc != MAPE_OK) return rc;
+  std::vector<const mape_extract_args*> res_items, st_items;
+  std::vector<char> res_ids, st_ids;
+  for (int i = 0; i < nl; ++i) {
+    const bool forced = (live[i]->precision & MAPE_PREC_STREAMED) != 0;
+    if (!forced && extract_tc_fits(cp[i], ids[i])) {
+      res_items.push_back(cp[i]);
+      res_ids.push_back(ids[i]);
+    } else {
+      st_items.push_back(cp[i]);
+      st_ids.push_back(ids[i]);
+    }
+  }
+  std::vector<bool> rb(res_ids.begin(), res_ids.end()), sb(st_ids.begin(), st_ids.end());
+  std::unique_ptr<bool[]> rba(new bool[rb.size() + 1]), sba(new bool[sb.size() + 1]);
+  for (size_t i = 0; i < rb.size(); ++i) rba[i] = rb[i];
+  for (size_t i = 0; i < sb.size(); ++i) sba[i] = sb[i];
+  TcBatch* tplan = nullptr;
+  StBatch* splan = nullptr;
+  auto cleanup = [&]() {
+    if (tplan) extract_tc_batch_free(tplan);
+    if (splan) extract_stream_batch_free(splan);
+  };
+  if (!res_items.empty() &&
+      (rc = extract_tc_batch_prepare(res_items.data(), rba.get(), (int)res_items.size(), tw, tws, st, &tplan))) {
+    cleanup();
+    return rc;
+  }
+  if (!st_items.empty() &&
+      (rc = extract_stream_batch_prepare(st_items.data(), sba.get(), (int)st_items.size(), sw, sws, st, &splan))) {
+    cleanup();
+    return rc;
+  }
+  auto enqueue = [&]() -> int {
+    int r = MAPE_OK;
+    if (tplan && (r = extract_tc_batch_enqueue(tplan, st)) != MAPE_OK) return r;
+    if (splan && (r = extract_stream_batch_enqueue(splan, st)) != MAPE_OK) return r;
+    return MAPE_OK;
+  };
+  if (st == nullptr) {  // the legacy default stream cannot be captured: launch directly
+    rc = enqueue();
+    cleanup();
+    return rc;
+  }
+  // every step of every call in one CUDA graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    record_cuda_error(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+    cleanup();
+    return MAPE_ERR_CUDA;
+  }
+  rc = enqueue();
+  e = cudaStreamEndCapture(st, &graph);
+  if (rc == MAPE_OK && e != cudaSuccess) {
+    record_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    rc = MAPE_ERR_CUDA;
+  }
+  if (rc == MAPE_OK && (e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) {
+    record_cuda_error(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+    rc = MAPE_ERR_CUDA;
+  }
+  if (rc == MAPE_OK && (e = cudaGraphLaunch(exec, st)) != cudaSuccess) {
+    record_cuda_error(e, "cudaGraphLaunch", __FILE__, __LINE__);
+    rc = MAPE_ERR_CUDA;
+  }
+  if (rc == MAPE_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+    record_cuda_error(e, "batch graph", __FILE__, __LINE__);
+    rc = MAPE_ERR_CUDA;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cleanup();
+  return rc;
 }

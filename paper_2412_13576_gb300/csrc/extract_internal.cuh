@@ -15,7 +15,29 @@ size_t extract_tc_workspace(int32_t n, int32_t d, int32_t P, int32_t precision);
 bool extract_tc_supported(int32_t n, int32_t d, int32_t precision);
 int extract_tc(const mape_extract_args* a, cudaStream_t st);
 
+// Batches of calls (same T, t0, period, precision) on the resident kernel:
+// prepare uploads and synchronises; enqueue only launches kernels.
+struct TcBatch;
+bool extract_tc_fits(const mape_extract_args* a, bool id);
+size_t extract_tc_batch_workspace(const mape_extract_args* const* items, int count);
+int extract_tc_batch_prepare(const mape_extract_args* const* items, const bool* ids, int count, void* ws,
+                             size_t ws_bytes, cudaStream_t st, TcBatch** out);
+int extract_tc_batch_enqueue(const TcBatch* plan, cudaStream_t st);
+void extract_tc_batch_free(TcBatch* plan);
+
 bool extract_stream_supported(int32_t n, int32_t d);
 size_t extract_stream_workspace(int32_t n, int32_t d, int32_t P);
 int extract_stream(const mape_extract_args* a, cudaStream_t st);
+
+// Batches of calls on the streamed kernels: three launches per step for all
+// calls of one basis kind.
+struct StBatch;
+size_t extract_stream_batch_workspace(const mape_extract_args* const* items, int count);
+int extract_stream_batch_prepare(const mape_extract_args* const* items, const bool* ids, int count, void* ws,
+                                 size_t ws_bytes, cudaStream_t st, StBatch** out);
+int extract_stream_batch_enqueue(const StBatch* plan, cudaStream_t st);
+void extract_stream_batch_free(StBatch* plan);
+// identity-topped test of every call's B (one launch each, one synchronisation)
+int identity_tops(const mape_extract_args* const* items, int count, int32_t* dflags, cudaStream_t st,
+                  std::vector<bool>& ids);
 }  // namespace mape_detail

@@ -31,6 +31,7 @@
 #include "tc_ptx.cuh"
 
 #include <cmath>
+#include <memory>
 #include <vector>
 
 namespace {
@@ -83,14 +84,15 @@ __device__ __forceinline__ int ptot(const StParams& p) { return p.tiles * kTM; }
 
 // ---------------------------------------------------------------- forward
 
+// blk: tile * nbF + row block of this CTA
 template <bool kId>
-__global__ void __launch_bounds__(kThreads, 1) stream_fwd_kernel(StParams p, int s, int fwd, int collect) {
+__device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk, int s, int fwd, int collect) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bars[4];  // full[2], done[2]
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tile = blockIdx.x / p.nbF, rb = blockIdx.x % p.nbF;
+  const int tile = blk / p.nbF, rb = blk % p.nbF;
   const int N = rb < p.nbF - 1 ? kNB : p.R64 - kNB * (p.nbF - 1);
   const int row0 = rb * kNB;
   const int nk = p.d64 / kKC;
@@ -302,10 +304,11 @@ __global__ void __launch_bounds__(kThreads, 1) stream_fwd_kernel(StParams p, int
 
 // ---------------------------------------------------------------- collect
 
+// blk: block of 8 starts (one warp each)
 template <bool kId>
-__global__ void stream_collect_kernel(StParams p, int s) {
+__device__ __forceinline__ void stream_collect_body(const StParams& p, const int blk, int s) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t pg = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  const int64_t pg = (int64_t)blk * (blockDim.x >> 5) + warp;
   if (pg >= p.P) return;
   const int P2 = ptot(p);
   long long slot = -1;
@@ -342,15 +345,16 @@ __global__ void stream_collect_kernel(StParams p, int s) {
 
 // ---------------------------------------------------------------- gradient + Adam
 
+// blk: tile * nbG + coordinate block of this CTA
 template <bool kId>
-__global__ void __launch_bounds__(kThreads, 1) stream_grad_kernel(StParams p, int s) {
+__device__ __forceinline__ void stream_grad_body(const StParams& p, const int blk, int s) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bars[5];  // full[2], done[2], accumulator ready
   __shared__ int32_t s_span[kNB];             // C4 bounds of this block's coordinates
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tile = blockIdx.x / p.nbG, db = blockIdx.x % p.nbG;
+  const int tile = blk / p.nbG, db = blk % p.nbG;
   const int N = db < p.nbG - 1 ? kNB : p.d64 - kNB * (p.nbG - 1);
   const int col0 = db * kNB;
   const int nk = p.R64 / kKC;
@@ -538,6 +542,51 @@ __global__ void __launch_bounds__(kThreads, 1) stream_grad_kernel(StParams p, in
   }
 }
 
+// ---------------------------------------------------------------- launch wrappers
+
+template <bool kId>
+__global__ void __launch_bounds__(kThreads, 1) stream_fwd_kernel(StParams p, int s, int fwd, int collect) {
+  stream_fwd_body<kId>(p, blockIdx.x, s, fwd, collect);
+}
+template <bool kId>
+__global__ void stream_collect_kernel(StParams p, int s) {
+  stream_collect_body<kId>(p, blockIdx.x, s);
+}
+template <bool kId>
+__global__ void __launch_bounds__(kThreads, 1) stream_grad_kernel(StParams p, int s) {
+  stream_grad_body<kId>(p, blockIdx.x, s);
+}
+
+// Many instances per launch: CTA b works on block work[b].y of instance
+// work[b].x, whose parameters are table[work[b].x] (a CTA that finds an
+// instance with fewer steps than the launch's step does nothing).
+__device__ __forceinline__ const StParams& load_params(const StParams* table, int item, StParams& s_p) {
+  if (threadIdx.x == 0) s_p = table[item];
+  __syncthreads();
+  return s_p;
+}
+template <bool kId>
+__global__ void __launch_bounds__(kThreads, 1) stream_fwd_batch_kernel(const StParams* __restrict__ table,
+                                                                       const int2* __restrict__ work, int s, int fwd,
+                                                                       int collect) {
+  __shared__ StParams s_p;
+  const int2 w = work[blockIdx.x];
+  stream_fwd_body<kId>(load_params(table, w.x, s_p), w.y, s, fwd, collect);
+}
+template <bool kId>
+__global__ void stream_collect_batch_kernel(const StParams* __restrict__ table, const int2* __restrict__ work, int s) {
+  __shared__ StParams s_p;
+  const int2 w = work[blockIdx.x];
+  stream_collect_body<kId>(load_params(table, w.x, s_p), w.y, s);
+}
+template <bool kId>
+__global__ void __launch_bounds__(kThreads, 1) stream_grad_batch_kernel(const StParams* __restrict__ table,
+                                                                        const int2* __restrict__ work, int s) {
+  __shared__ StParams s_p;
+  const int2 w = work[blockIdx.x];
+  stream_grad_body<kId>(load_params(table, w.x, s_p), w.y, s);
+}
+
 // ---------------------------------------------------------------- set-up kernels
 
 // Bm in both operand layouts; flags |= 8 (and *bad = 1) if an entry is not
@@ -701,104 +750,293 @@ size_t extract_stream_workspace(int32_t n, int32_t d, int32_t P) {
   return s.bytes();
 }
 
-int extract_stream(const mape_extract_args* a, cudaStream_t st) {
+// One call's pieces of its workspace, carved with the bounding layout.
+struct StCarved {
+  StreamShape sh;
+  float *Zt, *Mt, *Vt;
+  uint8_t *S, *BmF, *BmG;
+  int8_t* stage;
+  unsigned long long* zkey;
+  uint32_t *acc, *oob, *idw;
+  int32_t *first, *first_map, *hflags;
+  float2* bias;
+};
+
+static int st_carve(const mape_extract_args* a, bool id, StCarved& c) {
   const int n = a->n, d = a->d, P = a->P;
-  if (a->T > kBiasSteps) return MAPE_ERR_SHAPE;
-  if (!extract_stream_supported(n, d)) return MAPE_ERR_SHAPE;
+  if (a->T > kBiasSteps || !extract_stream_supported(n, d)) return MAPE_ERR_SHAPE;
   const StreamShape gen = stream_bound(n, d, P);
   Carver cv(a->workspace, a->workspace_bytes);
   const size_t P2 = (size_t)gen.tiles * kTM;
-  float* Zt = cv.take<float>(P2 * gen.d64);
-  float* Mt = cv.take<float>(P2 * gen.d64);
-  float* Vt = cv.take<float>(P2 * gen.d64);
-  uint8_t* S = cv.take<uint8_t>(P2 * gen.R64 * 2);
-  int8_t* stage = cv.take<int8_t>(P2 * gen.lds);
-  uint8_t* BmF = cv.take<uint8_t>((size_t)gen.R64 * gen.d64 * 2);
-  uint8_t* BmG = cv.take<uint8_t>((size_t)gen.R64 * gen.d64 * 2);
-  unsigned long long* zkey = cv.take<unsigned long long>(2 * P2);
-  uint32_t* acc = cv.take<uint32_t>(P2);
-  uint32_t* oob = cv.take<uint32_t>(P2);
-  uint32_t* idw = cv.take<uint32_t>(2 * P2);
-  int32_t* first = cv.take<int32_t>(2 * P2);
-  int32_t* first_map = cv.take<int32_t>(P2);
-  float2* bias = cv.take<float2>((size_t)kBiasSteps);
-  int32_t* hflags = cv.take<int32_t>(2);
+  c.Zt = cv.take<float>(P2 * gen.d64);
+  c.Mt = cv.take<float>(P2 * gen.d64);
+  c.Vt = cv.take<float>(P2 * gen.d64);
+  c.S = cv.take<uint8_t>(P2 * gen.R64 * 2);
+  c.stage = cv.take<int8_t>(P2 * gen.lds);
+  c.BmF = cv.take<uint8_t>((size_t)gen.R64 * gen.d64 * 2);
+  c.BmG = cv.take<uint8_t>((size_t)gen.R64 * gen.d64 * 2);
+  c.zkey = cv.take<unsigned long long>(2 * P2);
+  c.acc = cv.take<uint32_t>(P2);
+  c.oob = cv.take<uint32_t>(P2);
+  c.idw = cv.take<uint32_t>(2 * P2);
+  c.first = cv.take<int32_t>(2 * P2);
+  c.first_map = cv.take<int32_t>(P2);
+  c.bias = cv.take<float2>((size_t)kBiasSteps);
+  c.hflags = cv.take<int32_t>(2);
   if (!cv.ok) return MAPE_ERR_CAPACITY;
+  c.sh = stream_shape(n, d, P, id);
+  return MAPE_OK;
+}
 
-  MAPE_CUDA_TRY(cudaMemsetAsync(hflags, 0, 2 * sizeof(int32_t), st));
-  launch(stream_identity_top_kernel, (unsigned)ceil_div((int64_t)d * d, 256), 256, 0, st, a->B, d, hflags);
+// B in both operand layouts; hflags[1] = 1 (and flags |= 8) if B is not exact in BF16
+static int st_pack_b(const StCarved& c, const mape_extract_args* a, cudaStream_t st) {
+  const StreamShape& sh = c.sh;
+  MAPE_CUDA_TRY(cudaMemsetAsync(c.hflags + 1, 0, sizeof(int32_t), st));
+  launch(pack_bm_kernel, (unsigned)ceil_div((int64_t)sh.R64 * sh.d64, 256), 256, 0, st, a->B, a->d, sh.R, sh.r0,
+         sh.d64, sh.R64, sh.nbF, sh.nbG, c.BmF, c.BmG, c.hflags + 1, a->flags);
   MAPE_LAUNCH_CHECK();
-  int32_t h_notid = 1;
-  MAPE_CUDA_TRY(cudaMemcpyAsync(&h_notid, hflags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
-  const bool id = h_notid == 0;
-  const StreamShape sh = stream_shape(n, d, P, id);
+  return MAPE_OK;
+}
 
-  launch(pack_bm_kernel, (unsigned)ceil_div((int64_t)sh.R64 * sh.d64, 256), 256, 0, st, a->B, d, sh.R, sh.r0,
-         sh.d64, sh.R64, sh.nbF, sh.nbG, BmF, BmG, hflags + 1, a->flags);
-  MAPE_LAUNCH_CHECK();
-  int32_t h_bad = 0;
-  MAPE_CUDA_TRY(cudaMemcpyAsync(&h_bad, hflags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
-  if (h_bad) return MAPE_OK;  // flag 8 is set; nothing runs, nothing is collected
-
+// bias table, blocked state, staged rows, per-start words; the parameters
+static int st_setup(const StCarved& c, const mape_extract_args* a, cudaStream_t st, StParams& p) {
+  const StreamShape& sh = c.sh;
+  const int n = a->n, d = a->d, P = a->P;
   std::vector<float2> bc((size_t)a->T);
   for (int s = 0; s < a->T; ++s) {
     const double t = (double)a->t0 + s + 1;
     const double bc1 = 1.0 - std::pow(a->beta1, t), bc2 = 1.0 - std::pow(a->beta2, t);
     bc[s] = make_float2((float)((double)a->lr / bc1), (float)(1.0 / std::sqrt(bc2)));
   }
-  MAPE_CUDA_TRY(cudaMemcpyAsync(bias, bc.data(), sizeof(float2) * bc.size(), cudaMemcpyHostToDevice, st));
+  MAPE_CUDA_TRY(cudaMemcpyAsync(c.bias, bc.data(), sizeof(float2) * bc.size(), cudaMemcpyHostToDevice, st));
+  const size_t P2 = (size_t)sh.tiles * kTM;
   const int64_t blocked = (int64_t)P2 * sh.d64;
   const unsigned gpack = (unsigned)ceil_div(blocked, 256);
-  launch(pack128_kernel, gpack, 256, 0, st, a->Z, Zt, P, d, sh.d64, blocked);
-  launch(pack128_kernel, gpack, 256, 0, st, a->M, Mt, P, d, sh.d64, blocked);
-  launch(pack128_kernel, gpack, 256, 0, st, a->V, Vt, P, d, sh.d64, blocked);
-  MAPE_CUDA_TRY(cudaMemsetAsync(stage, 0, P2 * sh.lds, st));
+  launch(pack128_kernel, gpack, 256, 0, st, a->Z, c.Zt, P, d, sh.d64, blocked);
+  launch(pack128_kernel, gpack, 256, 0, st, a->M, c.Mt, P, d, sh.d64, blocked);
+  launch(pack128_kernel, gpack, 256, 0, st, a->V, c.Vt, P, d, sh.d64, blocked);
+  MAPE_CUDA_TRY(cudaMemsetAsync(c.stage, 0, P2 * sh.lds, st));
   if (a->dbg_phi) MAPE_CUDA_TRY(cudaMemsetAsync(a->dbg_phi, 0, sizeof(float) * P, st));
-
-  StParams p{};
+  p = StParams{};
   p.n = n; p.d = d; p.P = P; p.R = sh.R; p.r0 = sh.r0; p.d64 = sh.d64; p.R64 = sh.R64;
   p.tiles = sh.tiles; p.nbF = sh.nbF; p.nbG = sh.nbG;
   p.ldc = a->ldc; p.mapoff = sh.mapoff; p.lds = sh.lds;
-  p.BmF = BmF; p.BmG = BmG; p.span = a->span; p.Zt = Zt; p.Mt = Mt; p.Vt = Vt; p.S = S; p.stage = stage;
-  p.zkey = zkey; p.acc = acc; p.oob = oob; p.idw = idw; p.first = first; p.first_map = first_map; p.bias = bias;
+  p.BmF = c.BmF; p.BmG = c.BmG; p.span = a->span; p.Zt = c.Zt; p.Mt = c.Mt; p.Vt = c.Vt; p.S = c.S;
+  p.stage = c.stage; p.zkey = c.zkey; p.acc = c.acc; p.oob = c.oob; p.idw = c.idw; p.first = c.first;
+  p.first_map = c.first_map; p.bias = c.bias;
   p.lambda1 = a->lambda1; p.lambda2 = a->lambda2; p.eps = a->eps;
   p.beta1 = (float)a->beta1; p.beta2 = (float)a->beta2;
   p.omb1 = (float)(1.0 - a->beta1); p.omb2 = (float)(1.0 - a->beta2);
   p.nterms = a->precision == MAPE_PREC_BF16X1 ? 1 : 2;
   p.cand = a->cand; p.cap = a->cand_cap; p.count = a->cand_count; p.flags = a->flags;
   p.dbg_phi = a->dbg_phi; p.dbg_grad = a->dbg_grad;
-
   launch(stream_init_kernel, (unsigned)ceil_div((int64_t)P2, 256), 256, 0, st, p);
   MAPE_LAUNCH_CHECK();
+  return MAPE_OK;
+}
 
-  auto fwd = id ? stream_fwd_kernel<true> : stream_fwd_kernel<false>;
-  auto grad = id ? stream_grad_kernel<true> : stream_grad_kernel<false>;
-  auto coll = id ? stream_collect_kernel<true> : stream_collect_kernel<false>;
-  // one CTA per SM for the forward pass (512 TMEM columns), at most two for
-  // the gradient pass (256 columns each): every TMEM allocation fits
-  MAPE_CUDA_TRY(cudaFuncSetAttribute(fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmem));
-  MAPE_CUDA_TRY(cudaFuncSetAttribute(grad, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem));
+static int st_unpack(const StCarved& c, const mape_extract_args* a, cudaStream_t st) {
+  const unsigned gun = (unsigned)ceil_div((int64_t)a->P * a->d, 256);
+  launch(unpack128_kernel, gun, 256, 0, st, c.Zt, a->Z, a->P, a->d, c.sh.d64);
+  launch(unpack128_kernel, gun, 256, 0, st, c.Mt, a->M, a->P, a->d, c.sh.d64);
+  launch(unpack128_kernel, gun, 256, 0, st, c.Vt, a->V, a->P, a->d, c.sh.d64);
+  MAPE_LAUNCH_CHECK();
+  return MAPE_OK;
+}
+
+// one CTA per SM for the forward pass (512 TMEM columns), at most two for
+// the gradient pass (256 columns each): every TMEM allocation fits
+static int st_attributes(bool batch) {
+  for (int id = 0; id < 2; ++id) {
+    const void* f = batch ? (id ? (const void*)stream_fwd_batch_kernel<true> : (const void*)stream_fwd_batch_kernel<false>)
+                          : (id ? (const void*)stream_fwd_kernel<true> : (const void*)stream_fwd_kernel<false>);
+    const void* g = batch ? (id ? (const void*)stream_grad_batch_kernel<true> : (const void*)stream_grad_batch_kernel<false>)
+                          : (id ? (const void*)stream_grad_kernel<true> : (const void*)stream_grad_kernel<false>);
+    MAPE_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmem));
+    MAPE_CUDA_TRY(cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem));
+  }
+  return MAPE_OK;
+}
+
+// the steps a call of T steps from t0 takes: forward (+ collection of the
+// previous rounding when due), gradient; the last rounding when due
+template <typename Fwd, typename Coll, typename Grad>
+static void st_schedule(int t0, int T, int period, Fwd fwd, Coll coll, Grad grad) {
+  for (int s = 0; s < T; ++s) {
+    const int t = t0 + s + 1;
+    const int collect = (s >= 1 && (t - 1) % period == 0) ? 1 : 0;
+    fwd(s, 1, collect);
+    if (collect) coll(s);
+    grad(s);
+  }
+  if ((t0 + T) % period == 0) {
+    fwd(T, 0, 1);
+    coll(T);
+  }
+}
+
+int extract_stream(const mape_extract_args* a, cudaStream_t st) {
+  const int d = a->d, P = a->P;
+  StCarved c;
+  int rc = st_carve(a, false, c);
+  if (rc != MAPE_OK) return rc;
+  MAPE_CUDA_TRY(cudaMemsetAsync(c.hflags, 0, sizeof(int32_t), st));
+  launch(stream_identity_top_kernel, (unsigned)ceil_div((int64_t)d * d, 256), 256, 0, st, a->B, d, c.hflags);
+  MAPE_LAUNCH_CHECK();
+  int32_t h_notid = 1;
+  MAPE_CUDA_TRY(cudaMemcpyAsync(&h_notid, c.hflags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  const bool id = h_notid == 0;
+  c.sh = stream_shape(a->n, d, P, id);
+  if ((rc = st_pack_b(c, a, st)) != MAPE_OK) return rc;
+  int32_t h_bad = 0;
+  MAPE_CUDA_TRY(cudaMemcpyAsync(&h_bad, c.hflags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h_bad) return MAPE_OK;  // flag 8 is set; nothing runs, nothing is collected
+  StParams p;
+  if ((rc = st_setup(c, a, st, p)) != MAPE_OK) return rc;
+  if ((rc = st_attributes(false)) != MAPE_OK) return rc;
+  const StreamShape& sh = c.sh;
   const unsigned gF = (unsigned)(sh.tiles * sh.nbF), gG = (unsigned)(sh.tiles * sh.nbG);
   const unsigned gC = (unsigned)ceil_div(P, 8);
-  for (int s = 0; s < a->T; ++s) {
-    const int t = a->t0 + s + 1;
-    const int collect = (s >= 1 && (t - 1) % a->period == 0) ? 1 : 0;
-    launch(fwd, gF, kThreads, kFSmem, st, p, s, 1, collect);
-    if (collect) launch(coll, gC, 256, 0, st, p, s);
-    launch(grad, gG, kThreads, kGSmem, st, p, s);
+  auto fwdk = id ? stream_fwd_kernel<true> : stream_fwd_kernel<false>;
+  auto gradk = id ? stream_grad_kernel<true> : stream_grad_kernel<false>;
+  auto collk = id ? stream_collect_kernel<true> : stream_collect_kernel<false>;
+  st_schedule(
+      a->t0, a->T, a->period, [&](int s, int f, int col) { launch(fwdk, gF, kThreads, kFSmem, st, p, s, f, col); },
+      [&](int s) { launch(collk, gC, 256, 0, st, p, s); },
+      [&](int s) { launch(gradk, gG, kThreads, kGSmem, st, p, s); });
+  MAPE_LAUNCH_CHECK();
+  return st_unpack(c, a, st);
+}
+
+struct StBatch {
+  struct Class {  // the calls of one basis kind (identity-topped or general)
+    bool id = false;
+    StParams* table = nullptr;
+    int2 *wF = nullptr, *wC = nullptr, *wG = nullptr;
+    int64_t nF = 0, nC = 0, nG = 0;
+  };
+  std::vector<Class> classes;
+  std::vector<const mape_extract_args*> items;
+  std::vector<StCarved> carved;
+  std::vector<bool> run;  // false: B not exact in BF16 (flag 8 set, nothing runs)
+  int t0 = 0, T = 0, period = 1;
+};
+
+void extract_stream_batch_free(StBatch* b) { delete b; }
+
+int identity_tops(const mape_extract_args* const* items, int count, int32_t* dflags, cudaStream_t st,
+                  std::vector<bool>& ids) {
+  ids.assign((size_t)count, false);
+  if (count == 0) return MAPE_OK;
+  MAPE_CUDA_TRY(cudaMemsetAsync(dflags, 0, sizeof(int32_t) * count, st));
+  for (int i = 0; i < count; ++i) {
+    const int d = items[i]->d;
+    launch(stream_identity_top_kernel, (unsigned)ceil_div((int64_t)d * d, 256), 256, 0, st, items[i]->B, d, dflags + i);
   }
   MAPE_LAUNCH_CHECK();
-  if ((a->t0 + a->T) % a->period == 0) {  // the candidate of the last step
-    launch(fwd, gF, kThreads, kFSmem, st, p, a->T, 0, 1);
-    launch(coll, gC, 256, 0, st, p, a->T);
+  std::vector<int32_t> h((size_t)count, 1);
+  MAPE_CUDA_TRY(cudaMemcpyAsync(h.data(), dflags, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, st));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < count; ++i) ids[i] = h[i] == 0;
+  return MAPE_OK;
+}
+
+size_t extract_stream_batch_workspace(const mape_extract_args* const* items, int count) {
+  Sizer s;
+  int64_t nF = 0, nC = 0, nG = 0;
+  for (int i = 0; i < count; ++i) {
+    const StreamShape b = stream_bound(items[i]->n, items[i]->d, items[i]->P);
+    const int64_t nbF = ceil_div(b.R64, kNB);
+    nF += (int64_t)b.tiles * nbF;
+    nG += (int64_t)b.tiles * b.nbG;
+    nC += ceil_div(items[i]->P, 8);
   }
-  const unsigned gun = (unsigned)ceil_div((int64_t)P * d, 256);
-  launch(unpack128_kernel, gun, 256, 0, st, Zt, a->Z, P, d, sh.d64);
-  launch(unpack128_kernel, gun, 256, 0, st, Mt, a->M, P, d, sh.d64);
-  launch(unpack128_kernel, gun, 256, 0, st, Vt, a->V, P, d, sh.d64);
-  MAPE_LAUNCH_CHECK();
+  for (int k = 0; k < 2; ++k) {  // per basis kind
+    s.take<StParams>((size_t)count);
+    s.take<int2>((size_t)nF);
+    s.take<int2>((size_t)nC);
+    s.take<int2>((size_t)nG);
+  }
+  return s.bytes();
+}
+
+int extract_stream_batch_prepare(const mape_extract_args* const* items, const bool* ids, int count, void* ws,
+                                 size_t ws_bytes, cudaStream_t st, StBatch** out) {
+  *out = nullptr;
+  std::unique_ptr<StBatch> plan(new StBatch());
+  plan->items.assign(items, items + count);
+  plan->carved.resize((size_t)count);
+  plan->run.assign((size_t)count, true);
+  if (count > 0) {
+    plan->t0 = items[0]->t0;
+    plan->T = items[0]->T;
+    plan->period = items[0]->period;
+  }
+  int rc;
+  for (int i = 0; i < count; ++i) {
+    if ((rc = st_carve(items[i], ids[i], plan->carved[i])) != MAPE_OK) return rc;
+    if ((rc = st_pack_b(plan->carved[i], items[i], st)) != MAPE_OK) return rc;
+  }
+  std::vector<int32_t> bad((size_t)count, 0);
+  for (int i = 0; i < count; ++i)
+    MAPE_CUDA_TRY(cudaMemcpyAsync(&bad[i], plan->carved[i].hflags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  Carver cv(ws, ws_bytes);
+  for (int k = 0; k < 2; ++k) {
+    const bool id = k == 1;
+    std::vector<StParams> table;
+    std::vector<int2> wF, wC, wG;
+    for (int i = 0; i < count; ++i) {
+      if (ids[i] != id) continue;
+      if (bad[i]) { plan->run[i] = false; continue; }
+      StParams p;
+      if ((rc = st_setup(plan->carved[i], items[i], st, p)) != MAPE_OK) return rc;
+      const int slot = (int)table.size();
+      table.push_back(p);
+      for (int b = 0; b < p.tiles * p.nbF; ++b) wF.push_back(make_int2(slot, b));
+      for (int b = 0; b < p.tiles * p.nbG; ++b) wG.push_back(make_int2(slot, b));
+      for (int b = 0; b < (int)ceil_div(p.P, 8); ++b) wC.push_back(make_int2(slot, b));
+    }
+    StBatch::Class C;
+    C.id = id;
+    C.table = cv.take<StParams>((size_t)count);
+    C.wF = cv.take<int2>(wF.size());
+    C.wC = cv.take<int2>(wC.size());
+    C.wG = cv.take<int2>(wG.size());
+    if (!cv.ok) return MAPE_ERR_CAPACITY;
+    if (table.empty()) continue;
+    C.nF = (int64_t)wF.size(); C.nC = (int64_t)wC.size(); C.nG = (int64_t)wG.size();
+    MAPE_CUDA_TRY(cudaMemcpyAsync(C.table, table.data(), sizeof(StParams) * table.size(), cudaMemcpyHostToDevice, st));
+    MAPE_CUDA_TRY(cudaMemcpyAsync(C.wF, wF.data(), sizeof(int2) * wF.size(), cudaMemcpyHostToDevice, st));
+    MAPE_CUDA_TRY(cudaMemcpyAsync(C.wC, wC.data(), sizeof(int2) * wC.size(), cudaMemcpyHostToDevice, st));
+    MAPE_CUDA_TRY(cudaMemcpyAsync(C.wG, wG.data(), sizeof(int2) * wG.size(), cudaMemcpyHostToDevice, st));
+    plan->classes.push_back(C);
+  }
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  if ((rc = st_attributes(true)) != MAPE_OK) return rc;
+  *out = plan.release();
+  return MAPE_OK;
+}
+
+int extract_stream_batch_enqueue(const StBatch* plan, cudaStream_t st) {
+  for (const auto& C : plan->classes) {
+    auto fwdk = C.id ? stream_fwd_batch_kernel<true> : stream_fwd_batch_kernel<false>;
+    auto gradk = C.id ? stream_grad_batch_kernel<true> : stream_grad_batch_kernel<false>;
+    auto collk = C.id ? stream_collect_batch_kernel<true> : stream_collect_batch_kernel<false>;
+    st_schedule(
+        plan->t0, plan->T, plan->period,
+        [&](int s, int f, int col) { launch(fwdk, (unsigned)C.nF, kThreads, kFSmem, st, C.table, C.wF, s, f, col); },
+        [&](int s) { launch(collk, (unsigned)C.nC, 256, 0, st, C.table, C.wC, s); },
+        [&](int s) { launch(gradk, (unsigned)C.nG, kThreads, kGSmem, st, C.table, C.wG, s); });
+    MAPE_LAUNCH_CHECK();
+  }
+  for (size_t i = 0; i < plan->items.size(); ++i) {
+    if (!plan->run[i]) continue;
+    int rc = st_unpack(plan->carved[i], plan->items[i], st);
+    if (rc != MAPE_OK) return rc;
+  }
   return MAPE_OK;
 }
 

@@ -36,9 +36,12 @@
 // 16, leaves the loop together (block-wide vote), frees its TMEM and returns.
 #include "common.cuh"
 #include "extract_internal.cuh"
+#include "tc_ptx.cuh"
 
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cmath>
+#include <memory>
 #include <vector>
 
 namespace {
@@ -50,98 +53,9 @@ constexpr int kSplits = kWarps / 4;
 constexpr int kParts = kSplits * 2;  // threads per start
 constexpr int kColD2 = 256;
 constexpr int kTmemCols = 512;
-constexpr uint32_t kWaitLimit = 1u << 20;
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: an MMA chain takes microseconds
 constexpr int kNoNz = 0x7fffffff;
 
-// ---- PTX wrappers ------------------------------------------------------------
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05; base offset 0, no swizzle
-  return d;
-}
-
-// kind::f16 instruction descriptor: D f32, A/B bf16, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// 8 consecutive FP32 columns of one M=64 row: half-warp 0 reads columns
-// [col, col+8) of lanes 0-15 of the quarter, half-warp 1 columns [col+8, col+16)
-__device__ __forceinline__ void tmem_ld8x2(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.16x32bx2.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], 8;"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-}
-
-// the store of the same shape
-__device__ __forceinline__ void tmem_st8x2(uint32_t taddr, const uint32_t (&r)[8]) {
-  asm volatile("tcgen05.st.sync.aligned.16x32bx2.x8.b32 [%0], 8, {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
-               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
-               : "memory");
-}
-__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Wait bounded in time (kWaitNs of the global timer) and in iterations;
-// returns true if the phase completed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  const uint64_t t0 = global_ns();
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
-  }
-  return false;
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<const uint32_t*>(&h);
-}
+using namespace mape_tc;
 
 // MN-major no-swizzle canonical layout ((T,1,m),(8,k)):((1,T,SBO),(1T,LBO)):
 // the 8-row K groups are LBO apart and the 16-byte MN groups SBO apart.
@@ -225,7 +139,7 @@ __host__ __device__ inline Smem smem_layout(int n_pad, int d_pad, int nterms, in
 // g = [round z ; B' round z] come from the FP32 master z in the Adam epilogue.
 // kRes: z, m, v live in TMEM lanes 16-31 for the whole launch.
 template <bool kId, bool kRes>
-__global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
+__device__ __forceinline__ void extract_tc_body(const TcParams& p, const int tile) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const Smem L = smem_layout(p.n_pad, p.d_pad, p.nterms, p.use_bb, p.span_pad);
   uint8_t* Bf = smem + L.bf;
@@ -251,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
   const int quarter = warp & 3, split = warp >> 2, half = lane >> 4;
   const int part = split * 2 + half;                      // which of the 8 threads of a start
   const int r = quarter * 16 + (lane & 15);               // start row in the tile
-  const int64_t pg = (int64_t)blockIdx.x * kTileM + r;    // global start
+  const int64_t pg = (int64_t)tile * kTileM + r;          // global start
   const bool active = pg < p.P;
   const int n = p.n, d = p.d, n_pad = p.n_pad, d_pad = p.d_pad;
   const int nch = n_pad / 16, dch = d_pad / 16;
@@ -295,9 +209,9 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
 
   // FP32 master state of this thread's start: blocked [tile][d_pad/4][64][4],
   // four consecutive coordinates per 16-byte access, coalesced over 16 starts
-  float4* const zb = reinterpret_cast<float4*>(p.Zt) + (size_t)blockIdx.x * (d_pad / 4) * kTileM + r;
-  float4* const mb = reinterpret_cast<float4*>(p.Mt) + (size_t)blockIdx.x * (d_pad / 4) * kTileM + r;
-  float4* const vb = reinterpret_cast<float4*>(p.Vt) + (size_t)blockIdx.x * (d_pad / 4) * kTileM + r;
+  float4* const zb = reinterpret_cast<float4*>(p.Zt) + (size_t)tile * (d_pad / 4) * kTileM + r;
+  float4* const mb = reinterpret_cast<float4*>(p.Mt) + (size_t)tile * (d_pad / 4) * kTileM + r;
+  float4* const vb = reinterpret_cast<float4*>(p.Vt) + (size_t)tile * (d_pad / 4) * kTileM + r;
 
   // ---- initial operand: bf16(z0) and the partial ||z0||_inf ----
   float zinf_part = 0.f;
@@ -722,6 +636,24 @@ __global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
   }
 }
 
+template <bool kId, bool kRes>
+__global__ void __launch_bounds__(kThreads, 1) extract_tc_kernel(TcParams p) {
+  extract_tc_body<kId, kRes>(p, blockIdx.x);
+}
+
+// Many instances in one launch: CTA b runs tile work[b].y of instance
+// work[b].x, whose parameters (own B, state, candidate buffer, steps) are
+// table[work[b].x]; the dynamic shared memory is sized for the largest tile.
+template <bool kId, bool kRes>
+__global__ void __launch_bounds__(kThreads, 1) extract_tc_batch_kernel(const TcParams* __restrict__ table,
+                                                                       const int2* __restrict__ work) {
+  __shared__ TcParams s_p;
+  const int2 w = work[blockIdx.x];
+  if (threadIdx.x == 0) s_p = table[w.x];
+  __syncthreads();
+  extract_tc_body<kId, kRes>(s_p, w.y);
+}
+
 // [P x d] row-major  <->  blocked [ceil(P/64)][d_pad/4][64][4] (zero padded)
 __global__ void pack_blocked_kernel(const float* __restrict__ in, float* __restrict__ out, int P, int d, int d_pad,
                                     int64_t total) {
@@ -800,9 +732,14 @@ size_t extract_tc_workspace(int32_t n, int32_t d, int32_t P, int32_t precision) 
   return s.bytes();
 }
 
-int extract_tc(const mape_extract_args* a, cudaStream_t st) {
+// Carves one call's workspace, uploads its Adam bias table, packs its state
+// into the blocked layout and fills its kernel parameters (no launch of the
+// extraction itself, no synchronisation).
+static int tc_prepare(const mape_extract_args* a, bool id, cudaStream_t st, TcParams& p, uint32_t& smem) {
   const int n = a->n, d = a->d, P = a->P;
   if (a->T > (1 << 20)) return MAPE_ERR_SHAPE;
+  const int nterms = a->precision == MAPE_PREC_BF16X1 ? 1 : 2;
+  if (!tc_fits(n, d, nterms, id)) return MAPE_ERR_SHAPE;
   Carver cv(a->workspace, a->workspace_bytes);
   const int d_pad = pad16(d);
   const int64_t blocked = ceil_div(P, kTileM) * kTileM * (int64_t)d_pad;
@@ -810,20 +747,9 @@ int extract_tc(const mape_extract_args* a, cudaStream_t st) {
   float* Mt = cv.take<float>((size_t)blocked);
   float* Vt = cv.take<float>((size_t)blocked);
   float2* bias = cv.take<float2>((size_t)1 << 20);
-  int32_t* idflag = cv.take<int32_t>(1);
+  cv.take<int32_t>(1);
   if (!cv.ok) return MAPE_ERR_CAPACITY;
-  // which kernel: identity-topped B or general B
-  MAPE_CUDA_TRY(cudaMemsetAsync(idflag, 0, sizeof(int32_t), st));
-  mape_detail::launch(identity_top_kernel, (unsigned)ceil_div((int64_t)d * d, 256), 256, 0, st, a->B, d, idflag);
-  MAPE_LAUNCH_CHECK();
-  int32_t h_notid = 1;
-  MAPE_CUDA_TRY(cudaMemcpyAsync(&h_notid, idflag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
-  const bool id = h_notid == 0;
-  const int nterms = a->precision == MAPE_PREC_BF16X1 ? 1 : 2;
-  if (!tc_fits(n, d, nterms, id)) return MAPE_ERR_SHAPE;
-  std::vector<float2> bc;
-  adam_bias_table(a, bc);
+  std::vector<float2> bc((size_t)a->T);
   for (int s = 0; s < a->T; ++s) {
     double t = (double)a->t0 + s + 1;
     double bc1 = 1.0 - std::pow(a->beta1, t), bc2 = 1.0 - std::pow(a->beta2, t);
@@ -834,7 +760,8 @@ int extract_tc(const mape_extract_args* a, cudaStream_t st) {
   mape_detail::launch(pack_blocked_kernel, gpack, 256, 0, st, a->Z, Zt, P, d, d_pad, blocked);
   mape_detail::launch(pack_blocked_kernel, gpack, 256, 0, st, a->M, Mt, P, d, d_pad, blocked);
   mape_detail::launch(pack_blocked_kernel, gpack, 256, 0, st, a->V, Vt, P, d, d_pad, blocked);
-  TcParams p{};
+  MAPE_LAUNCH_CHECK();
+  p = TcParams{};
   p.B = a->B; p.span = a->span; p.Zt = Zt; p.Mt = Mt; p.Vt = Vt; p.bias = bias;
   p.n = n; p.d = d; p.P = P; p.n_pad = tile_rows(n, d, id); p.d_pad = d_pad; p.span_pad = pad16(n);
   p.t0 = a->t0; p.T = a->T; p.period = a->period;
@@ -847,22 +774,155 @@ int extract_tc(const mape_extract_args* a, cudaStream_t st) {
   p.use_bb = tc_use_bb(p.n_pad, p.d_pad, p.nterms, p.span_pad);
   // at least 116 KB of shared memory keeps one CTA per SM, so the 512-column
   // TMEM allocation never waits for another CTA
-  uint32_t smem = smem_layout(p.n_pad, p.d_pad, p.nterms, p.use_bb, p.span_pad).total;
+  smem = smem_layout(p.n_pad, p.d_pad, p.nterms, p.use_bb, p.span_pad).total;
   if (smem < 116 * 1024) smem = 116 * 1024;
-  unsigned grid = (unsigned)ceil_div(P, kTileM);
-  // the FP32 state fits in the free TMEM lanes when its three d_pad-wide
-  // blocks fit in 512 columns
-  const bool res = 3 * d_pad <= kTmemCols;
+  return MAPE_OK;
+}
+
+static int tc_unpack(const TcParams& p, const mape_extract_args* a, cudaStream_t st) {
+  const unsigned gun = (unsigned)ceil_div((int64_t)a->P * a->d, 256);
+  mape_detail::launch(unpack_blocked_kernel, gun, 256, 0, st, p.Zt, a->Z, a->P, a->d, p.d_pad);
+  mape_detail::launch(unpack_blocked_kernel, gun, 256, 0, st, p.Mt, a->M, a->P, a->d, p.d_pad);
+  mape_detail::launch(unpack_blocked_kernel, gun, 256, 0, st, p.Vt, a->V, a->P, a->d, p.d_pad);
+  MAPE_LAUNCH_CHECK();
+  return MAPE_OK;
+}
+
+// the FP32 state fits in the free TMEM lanes when its three d_pad-wide blocks
+// fit in 512 columns
+static bool tc_resident_state(const TcParams& p) { return 3 * p.d_pad <= kTmemCols; }
+
+int extract_tc(const mape_extract_args* a, cudaStream_t st) {
+  const int d = a->d;
+  if (a->T > (1 << 20)) return MAPE_ERR_SHAPE;
+  // which kernel: identity-topped B or general B (the flag word is the
+  // workspace's last piece)
+  Carver cv(a->workspace, a->workspace_bytes);
+  const int64_t blocked = ceil_div(a->P, kTileM) * kTileM * (int64_t)pad16(d);
+  for (int k = 0; k < 3; ++k) cv.take<float>((size_t)blocked);
+  cv.take<float2>((size_t)1 << 20);
+  int32_t* idflag = cv.take<int32_t>(1);
+  if (!cv.ok) return MAPE_ERR_CAPACITY;
+  MAPE_CUDA_TRY(cudaMemsetAsync(idflag, 0, sizeof(int32_t), st));
+  mape_detail::launch(identity_top_kernel, (unsigned)ceil_div((int64_t)d * d, 256), 256, 0, st, a->B, d, idflag);
+  MAPE_LAUNCH_CHECK();
+  int32_t h_notid = 1;
+  MAPE_CUDA_TRY(cudaMemcpyAsync(&h_notid, idflag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  const bool id = h_notid == 0;
+  TcParams p;
+  uint32_t smem = 0;
+  int rc = tc_prepare(a, id, st, p, smem);
+  if (rc != MAPE_OK) return rc;
+  const bool res = tc_resident_state(p);
   auto kern = id ? (res ? extract_tc_kernel<true, true> : extract_tc_kernel<true, false>)
                  : (res ? extract_tc_kernel<false, true> : extract_tc_kernel<false, false>);
   MAPE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  mape_detail::launch(kern, grid, kThreads, smem, st, p);
+  mape_detail::launch(kern, (unsigned)ceil_div(a->P, kTileM), kThreads, smem, st, p);
   MAPE_LAUNCH_CHECK();
-  const unsigned gun = (unsigned)ceil_div((int64_t)P * d, 256);
-  mape_detail::launch(unpack_blocked_kernel, gun, 256, 0, st, Zt, a->Z, P, d, d_pad);
-  mape_detail::launch(unpack_blocked_kernel, gun, 256, 0, st, Mt, a->M, P, d, d_pad);
-  mape_detail::launch(unpack_blocked_kernel, gun, 256, 0, st, Vt, a->V, P, d, d_pad);
-  MAPE_LAUNCH_CHECK();
+  return tc_unpack(p, a, st);
+}
+
+struct TcBatch {
+  struct Launch {
+    int variant = 0;  // bit 0: identity-topped B, bit 1: state in TMEM
+    int64_t first = 0, ctas = 0;
+    uint32_t smem = 0;
+  };
+  std::vector<Launch> launches;
+  void* table = nullptr;
+  void* work = nullptr;
+  std::vector<const mape_extract_args*> items;
+  std::vector<TcParams> params;
+};
+
+static void (*batch_kernel(int v))(const TcParams*, const int2*) {
+  switch (v) {
+    case 0: return extract_tc_batch_kernel<false, false>;
+    case 1: return extract_tc_batch_kernel<true, false>;
+    case 2: return extract_tc_batch_kernel<false, true>;
+    default: return extract_tc_batch_kernel<true, true>;
+  }
+}
+
+void extract_tc_batch_free(TcBatch* b) { delete b; }
+
+bool extract_tc_fits(const mape_extract_args* a, bool id) {
+  return tc_fits(a->n, a->d, a->precision == MAPE_PREC_BF16X1 ? 1 : 2, id);
+}
+
+size_t extract_tc_batch_workspace(const mape_extract_args* const* items, int count) {
+  Sizer s;
+  int64_t tiles = 0;
+  for (int i = 0; i < count; ++i) tiles += ceil_div(items[i]->P, kTileM);
+  s.take<TcParams>((size_t)count);
+  s.take<int2>((size_t)tiles);
+  return s.bytes();
+}
+
+// Every call of `items` (resident-kernel shapes; ids[i]: B identity-topped) in
+// as few launches as kernel variants: one persistent launch per variant over
+// all the variant's tiles.  prepare (uploads; synchronises `st` once) and
+// enqueue (launches only: capturable into a CUDA graph).
+int extract_tc_batch_prepare(const mape_extract_args* const* items, const bool* ids, int count, void* ws,
+                             size_t ws_bytes, cudaStream_t st, TcBatch** out) {
+  *out = nullptr;
+  std::unique_ptr<TcBatch> hold(new TcBatch());
+  TcBatch& plan = *hold;
+  std::vector<TcParams> params((size_t)count);
+  std::vector<uint32_t> smem((size_t)count);
+  for (int i = 0; i < count; ++i) {
+    int rc = tc_prepare(items[i], ids[i], st, params[i], smem[i]);
+    if (rc != MAPE_OK) return rc;
+  }
+  Carver cv(ws, ws_bytes);
+  TcParams* dtab = cv.take<TcParams>((size_t)count);
+  int64_t tiles = 0;
+  for (int i = 0; i < count; ++i) tiles += ceil_div(items[i]->P, kTileM);
+  int2* dwork = cv.take<int2>((size_t)tiles);
+  if (!cv.ok) return MAPE_ERR_CAPACITY;
+  // work lists grouped by variant: (identity-topped, state in TMEM)
+  std::vector<int2> work;
+  work.reserve((size_t)tiles);
+  for (int v = 0; v < 4; ++v) {
+    const bool vid = v & 1, vres = (v >> 1) & 1;
+    TcBatch::Launch L{};
+    L.variant = v;
+    L.first = (int64_t)work.size();
+    for (int i = 0; i < count; ++i) {
+      if (ids[i] != vid || tc_resident_state(params[i]) != vres) continue;
+      for (int t = 0; t < ceil_div(items[i]->P, kTileM); ++t) work.push_back(make_int2(i, t));
+      L.smem = std::max(L.smem, smem[i]);
+    }
+    L.ctas = (int64_t)work.size() - L.first;
+    if (L.ctas > 0) plan.launches.push_back(L);
+  }
+  MAPE_CUDA_TRY(cudaMemcpyAsync(dtab, params.data(), sizeof(TcParams) * count, cudaMemcpyHostToDevice, st));
+  MAPE_CUDA_TRY(cudaMemcpyAsync(dwork, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, st));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  plan.table = dtab;
+  plan.work = dwork;
+  plan.items.assign(items, items + count);
+  plan.params = std::move(params);
+  for (auto& L : plan.launches) {
+    auto kern = batch_kernel(L.variant);
+    MAPE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+  }
+  *out = hold.release();
+  return MAPE_OK;
+}
+
+int extract_tc_batch_enqueue(const TcBatch* pl, cudaStream_t st) {
+  const TcBatch& plan = *pl;
+  for (const auto& L : plan.launches) {
+    mape_detail::launch(batch_kernel(L.variant), (unsigned)L.ctas, kThreads, L.smem, st,
+                        static_cast<const TcParams*>(plan.table), static_cast<const int2*>(plan.work) + L.first);
+    MAPE_LAUNCH_CHECK();
+  }
+  for (size_t i = 0; i < plan.items.size(); ++i) {
+    int rc = tc_unpack(plan.params[i], plan.items[i], st);
+    if (rc != MAPE_OK) return rc;
+  }
   return MAPE_OK;
 }
 

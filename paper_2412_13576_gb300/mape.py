@@ -247,6 +247,44 @@ def phi_grad(B, Z, lambda1=0.85, lambda2=1.0, stream=None):
     return phi, grad
 
 
+def _extract_args(B, span, Z, M, V, *, t0, T, cfg: Config, cand, cand_count, flags, ldc,
+                  dbg_phi=None, dbg_grad=None, workspace=None):
+    n, d = B.shape
+    P = Z.shape[0]
+    a = ExtractArgs()
+    a.n, a.d, a.P = n, d, P
+    a.B, a.span, a.Z, a.M, a.V = _ptr(B), _ptr(span), _ptr(Z), _ptr(M), _ptr(V)
+    a.t0, a.T, a.period, a.precision = t0, T, cfg.period, cfg.precision
+    a.lambda1, a.lambda2, a.lr = cfg.lambda1, cfg.lambda2, cfg.lr
+    a.beta1, a.beta2, a.eps = cfg.beta1, cfg.beta2, cfg.eps
+    a.cand = _ptr(cand)
+    a.ldc = ldc
+    a.cand_cap = cand.shape[0] if cand is not None else 0
+    a.cand_count, a.flags = _ptr(cand_count), _ptr(flags)
+    a.dbg_phi, a.dbg_grad = _ptr(dbg_phi), _ptr(dbg_grad)
+    if workspace is None:
+        workspace = _workspace(lib().mape_extract_workspace_bytes(n, d, P, cfg.precision), B.device)
+    a.workspace, a.workspace_bytes = _ptr(workspace), workspace.numel()
+    return a, workspace
+
+
+def extract_batch(calls, *, t0, T, cfg: Config, stream=None):
+    """a3-a8 for many instances in one batched, graph-captured run.  calls:
+    dicts with the keyword arguments of extract() except t0, T, cfg (B, span,
+    Z, M, V, cand, cand_count, flags, ldc)."""
+    keep = []
+    arr = (ExtractArgs * len(calls))()
+    for i, c in enumerate(calls):
+        a, ws = _extract_args(t0=t0, T=T, cfg=cfg, **c)
+        arr[i] = a
+        keep.append(ws)
+    nb = lib().mape_extract_batch_workspace_bytes(arr, len(calls))
+    dev = calls[0]["B"].device
+    bws = _workspace(max(nb, 16), dev)
+    _check(lib().mape_extract_batch(arr, len(calls), _ptr(bws), bws.numel(), _stream(stream)), "mape_extract_batch")
+    return keep
+
+
 def extract(B, span, Z, M, V, *, t0, T, cfg: Config, cand, cand_count, flags, ldc,
             dbg_phi=None, dbg_grad=None, workspace=None, stream=None):
     """a3-a8: T Adam steps of Algorithm 2 in place on Z/M/V; appends to cand."""
