@@ -57,6 +57,9 @@ def parse_args(argv=None):
                     help="requests in the serving measurement (Poisson stream at 200/s, n log-uniform in "
                          "[30, 3000], m = n/5, P = 4096); 0 skips it")
     ap.add_argument("--serve-T", type=int, default=1000, help="Adam steps per request in the serving measurement")
+    ap.add_argument("--batch", type=int, default=64, metavar="N",
+                    help="instances in the batched-extraction measurement (n log-uniform in [50, 1000], m = n/5, "
+                         "P in {1024, 4096, 16384}, T = 1000); 0 skips it")
     ap.add_argument("--kernel-case", type=int, nargs=2, metavar=("P", "T"),
                     help="time the fused extraction kernel alone on P starts of the workload for T steps "
                          "(two launches; a small case for profilers) and exit")
@@ -308,6 +311,8 @@ def run_ours(args):
         result["roofline"] = roofline(mape, inst, starts, stream, args)
         if not args.no_plain and args.precision != "fp32":
             result["vs_plain_fp32"] = plain_fp32(mape, inst, G0, x0, stream)
+        if args.batch > 0 and world == 1:
+            result["batched"] = batch_measure(args.batch)
         if args.serve > 0 and world == 1:
             result["serving"] = serve_measure(args.serve, args.serve_T)
         if not args.no_cpu_baseline and world == 1:
@@ -436,6 +441,12 @@ def serve_measure(N, T, seed=3000):
 
     def run_server(cfg, slots):
         with mape.Server(cfg, mem_cap_bytes=150 << 30, max_slots=slots) as srv:
+            # warm-up: the smallest and the largest instance, 10 steps each (loads every kernel used)
+            warm_cfg = mape.default_config(T=10, precision=cfg.precision)
+            with mape.Server(warm_cfg, mem_cap_bytes=150 << 30, max_slots=2) as ws:
+                for k in (int(np.argmin([i.n for i in insts])), int(np.argmax([i.n for i in insts]))):
+                    ws.submit(insts[k], SERVE_P, G0=G0s[k])
+                ws.wait_all(600)
             t0 = time.perf_counter()
             ids = []
             for k, inst in enumerate(insts):
@@ -470,6 +481,84 @@ def serve_measure(N, T, seed=3000):
     out["workload"] = (f"{N} requests, Poisson arrivals at {SERVE_RATE:.0f}/s, n log-uniform in [30, 3000] "
                        f"(uneven_batch seed {seed}), m = n/5, P = {SERVE_P}, T = {T}, 150 GB admission cap")
     return out
+
+
+def batch_measure(N, T=1000, seed=1003):
+    """Batched extraction of uneven instances: N instances with n log-uniform in
+    [50, 1000], m = n/5, C in [-3,3] at a density uniform in [0.05, 0.2], box
+    [-5,5], P drawn from {1024, 4096, 16384}, projected uniform starts, T Adam
+    steps (a3-a8).  Times one mape_extract_batch call (one CUDA graph: one
+    persistent launch per resident-kernel variant, three launches per step for
+    the streamed shapes) against the same calls made one after another with
+    mape_extract, on the same stream, from the same starting state."""
+    import numpy as np
+    import torch
+    from paper_2412_13576_gb300 import instances as I
+    from paper_2412_13576_gb300 import mape
+    rng = np.random.default_rng(seed + 1000)
+    insts = I.uneven_batch(count=N, n_lo=50, n_hi=1000, seed=seed)
+    Ps = rng.choice([1024, 4096, 16384], size=N)
+    cfg = mape.default_config(T=T, precision=PREC["bf16"])
+    stream = torch.cuda.Stream()
+    calls, starts = [], []
+    with torch.cuda.stream(stream):
+        for k, (inst, P) in enumerate(zip(insts, Ps)):
+            P = int(P)
+            B = torch.from_numpy(inst.B).cuda()
+            G0 = torch.from_numpy(I.uniform_samples(inst, P, seed=seed + 2000 + k).G0).cuda()
+            Z0 = mape.project_starts(B, G0, stream=stream)
+            ldc = mape.round16(inst.n)
+            Z = torch.empty_like(Z0)
+            calls.append(dict(B=B, span=torch.from_numpy((inst.u - inst.l).astype(np.int32)).cuda(), Z=Z,
+                              M=torch.empty_like(Z0), V=torch.empty_like(Z0),
+                              cand=torch.empty((min(P * (T + 1), (512 << 20) // ldc), ldc), dtype=torch.int8,
+                                               device="cuda"),
+                              cand_count=torch.zeros(1, dtype=torch.int64, device="cuda"),
+                              flags=torch.zeros(1, dtype=torch.int32, device="cuda"), ldc=ldc,
+                              workspace=torch.empty(mape.lib().mape_extract_workspace_bytes(inst.n, inst.d, P,
+                                                                                           cfg.precision),
+                                                    dtype=torch.uint8, device="cuda")))
+            starts.append(Z0)
+
+    def reset():
+        with torch.cuda.stream(stream):
+            for c, Z0 in zip(calls, starts):
+                c["Z"].copy_(Z0)
+                c["M"].zero_()
+                c["V"].zero_()
+                c["cand_count"].zero_()
+                c["flags"].zero_()
+        stream.synchronize()
+
+    def timed(fn):
+        reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1)
+
+    def batched():
+        mape.extract_batch(calls, t0=0, T=T, cfg=cfg, stream=stream)
+
+    def sequential():
+        for c in calls:
+            mape.extract(t0=0, T=T, cfg=cfg, stream=stream, **c)
+
+    timed(batched)
+    tb = timed(batched)
+    flags = [int(c["flags"].item()) for c in calls]
+    zb = [c["Z"].clone() for c in calls]
+    timed(sequential)
+    ts = timed(sequential)
+    same = all(torch.equal(a, c["Z"]) for a, c in zip(zb, calls))
+    starts_steps = float(sum(int(p) for p in Ps)) * T
+    return {"instances": N, "T": T, "batched_ms": tb, "sequential_ms": ts, "speedup": ts / tb,
+            "start_steps_per_s": starts_steps / (tb / 1e3), "same_state_as_sequential": same,
+            "flags": sorted(set(flags)), "n_range": [min(i.n for i in insts), max(i.n for i in insts)],
+            "workload": (f"uneven_batch(count={N}, n in [50,1000], seed {seed}); P from {{1024,4096,16384}}; "
+                         f"projected uniform starts; T = {T}; a3-a8 only")}
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "extract_tc_kernel_medium_sparse_P8192_T1000_traffic.md")
@@ -526,20 +615,22 @@ def roofline(mape, inst, starts, stream, args, reps=3):
 
 
 def plain_fp32(mape, inst, G0, x0, stream):
-    """One step of the plain FP32 single-instance path (unfused CUDA-core
-    kernels, one launch per stage and Adam step) for comparison."""
+    """One pass of the plain FP32 single-instance path (per step: strict-FP32
+    cuBLAS GEMMs and unfused elementwise kernels) for comparison, timed after
+    one untimed warm-up pass."""
     import torch
     cfg = mape.default_config(T=T_FULL, precision=0)
     with mape.Instance.from_generated(inst, cfg, stream=stream) as h:
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        h.extract_directions(P_FULL, G0=G0)
-        h.wait(900)
-        h.augment(x0)
-        h.wait(900)
-        e1.record(stream)
-        stream.synchronize()
+        for rep in range(2):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.extract_directions(P_FULL, G0=G0)
+            h.wait(900)
+            h.augment(x0)
+            h.wait(900)
+            e1.record(stream)
+            stream.synchronize()
         st = h.poll()
     ms = e0.elapsed_time(e1)
     return {"value": st["directions"] / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "best_f": st["best_f"],

@@ -196,17 +196,43 @@ extern "C" int mape_extract_batch(const mape_extract_args* items, int32_t count,
     cleanup();
     return rc;
   }
-  auto enqueue = [&]() -> int {
-    int r = MAPE_OK;
-    if (tplan && (r = extract_tc_batch_enqueue(tplan, st)) != MAPE_OK) return r;
-    if (splan && (r = extract_stream_batch_enqueue(splan, st)) != MAPE_OK) return r;
-    return MAPE_OK;
-  };
   if (st == nullptr) {  // the legacy default stream cannot be captured: launch directly
-    rc = enqueue();
+    if (tplan) rc = extract_tc_batch_enqueue(tplan, st);
+    if (rc == MAPE_OK && splan) rc = extract_stream_batch_enqueue(splan, st);
     cleanup();
     return rc;
   }
+  // the resident launches and the streamed steps are independent: they run as
+  // two branches (a second stream forked from and joined back into `st`), so
+  // the SMs one leaves idle take the other's CTAs
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  if (tplan && splan) {
+    if (cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      if (aux) cudaStreamDestroy(aux);
+      if (ev_fork) cudaEventDestroy(ev_fork);
+      cleanup();
+      return MAPE_ERR_CUDA;
+    }
+  }
+  auto enqueue = [&]() -> int {
+    int r = MAPE_OK;
+    cudaStream_t tst = st;
+    if (aux) {
+      if (cudaEventRecord(ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(aux, ev_fork, 0) != cudaSuccess)
+        return MAPE_ERR_CUDA;
+      tst = aux;
+    }
+    if (tplan && (r = extract_tc_batch_enqueue(tplan, tst)) != MAPE_OK) return r;
+    if (splan && (r = extract_stream_batch_enqueue(splan, st)) != MAPE_OK) return r;
+    if (aux) {
+      if (cudaEventRecord(ev_join, aux) != cudaSuccess || cudaStreamWaitEvent(st, ev_join, 0) != cudaSuccess)
+        return MAPE_ERR_CUDA;
+    }
+    return MAPE_OK;
+  };
   // every step of every call in one CUDA graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -236,6 +262,9 @@ extern "C" int mape_extract_batch(const mape_extract_args* items, int32_t count,
   }
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
+  if (aux) cudaStreamDestroy(aux);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
   cleanup();
   return rc;
 }

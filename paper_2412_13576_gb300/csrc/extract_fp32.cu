@@ -17,6 +17,8 @@
 #include <cublas_v2.h>
 
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <vector>
 
 namespace {
@@ -261,14 +263,17 @@ void carve_fp32(Carve& cv, int32_t n, int32_t d, int32_t P) {
   cv.template take<int32_t>(1);                                     // max row sum of |B|
 }
 
-// one cuBLAS handle per host thread (handles are not shared between threads)
-struct BlasHandle {
-  cublasHandle_t h = nullptr;
-  ~BlasHandle() {
-    if (h) cublasDestroy(h);
-  }
+// One cuBLAS handle per device for the process, created on first use; a
+// call holds its mutex while it sets the handle's stream and enqueues (a
+// cuBLAS handle must not be used by two threads at once).
+struct BlasHandles {
+  std::mutex mu;
+  std::map<int, cublasHandle_t> by_dev;
 };
-thread_local BlasHandle t_blas;
+BlasHandles& blas_handles() {
+  static BlasHandles* h = new BlasHandles();  // never destroyed: lives until the process exits
+  return *h;
+}
 
 }  // namespace
 
@@ -315,11 +320,15 @@ int extract_fp32(const mape_extract_args* a, cudaStream_t st) {
   int32_t* firstw = cv.take<int32_t>((size_t)P);
   int32_t* bnorm = cv.take<int32_t>(1);
   if (!cv.ok) return MAPE_ERR_CAPACITY;
-  if (!t_blas.h) {
-    MAPE_BLAS_TRY(cublasCreate(&t_blas.h));
-    MAPE_BLAS_TRY(cublasSetMathMode(t_blas.h, CUBLAS_PEDANTIC_MATH));  // strict FP32
+  int dev = 0;
+  MAPE_CUDA_TRY(cudaGetDevice(&dev));
+  BlasHandles& H = blas_handles();
+  std::lock_guard<std::mutex> blas_lock(H.mu);
+  cublasHandle_t& hb = H.by_dev[dev];
+  if (!hb) {
+    MAPE_BLAS_TRY(cublasCreate(&hb));
+    MAPE_BLAS_TRY(cublasSetMathMode(hb, CUBLAS_PEDANTIC_MATH));  // strict FP32
   }
-  cublasHandle_t hb = t_blas.h;
   MAPE_BLAS_TRY(cublasSetStream(hb, st));
   MAPE_CUDA_TRY(cudaMemsetAsync(badw, 0, sizeof(uint32_t) * P, st));
   MAPE_CUDA_TRY(cudaMemsetAsync(firstw, 0x7f, sizeof(int32_t) * P, st));
