@@ -52,7 +52,7 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-sample", type=int, nargs=2, metavar=("P", "T"), help=argparse.SUPPRESS)
     ap.add_argument("--streamed-case", nargs=3, metavar=("NAME", "P", "T"),
                     help="time the streamed tensor-core extraction on a named instance (large: n=2000 m=400; "
-                         "uneven1000: n=1000 m=200) for P starts and T steps, and exit")
+                         "uneven1000: n=1000 m=200; medium: n=200 m=40) for P starts and T steps, and exit")
     ap.add_argument("--serve", type=int, default=24, metavar="N",
                     help="requests in the serving measurement (Poisson stream at 200/s, n log-uniform in "
                          "[30, 3000], m = n/5, P = 4096); 0 skips it")
@@ -381,7 +381,7 @@ def kernel_case(args):
                             "ms_per_launch": times, "candidates": counts}}
 
 
-STREAMED_CASES = {"large": "large_quartic", "uneven1000": "uneven1000"}
+STREAMED_CASES = {"large": "large_quartic", "uneven1000": "uneven1000", "medium": "medium_sparse"}
 
 
 def streamed_case(args):
@@ -396,7 +396,8 @@ def streamed_case(args):
     torch.cuda.set_device(0)
     mape.lib(build_if_missing=True)
     name, P, T = args.streamed_case[0], int(args.streamed_case[1]), int(args.streamed_case[2])
-    inst = I.large_quartic() if name == "large" else I.uneven_single(1000, density=0.05)
+    inst = {"large": I.large_quartic, "medium": I.medium_sparse,
+            "uneven1000": lambda: I.uneven_single(1000, density=0.05)}[name]()
     prec = PREC[args.precision] | mape.PREC_STREAMED
     G0 = I.uniform_samples(inst, P, seed=2004).G0
     stream = torch.cuda.Stream()
