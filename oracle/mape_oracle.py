@@ -30,7 +30,11 @@ notes of the repository):
     sign, with the first nonzero entry positive;
   * Algorithm 1 tries both +g and -g for every stored direction, with
     lambda >= 1; among optimal moves it takes the lowest direction index (in
-    the sorted direction list), +g before -g, then the smallest lambda.
+    the sorted direction list), +g before -g, then the smallest lambda;
+  * Eq. (4): x in [l, u] is kept by projecting (clipping) after every Adam
+    step; the starts are clipped into the box first; the rounded iterate is
+    collected when it is exactly feasible for model (1), after every
+    `period`-th step like Algorithm 2's collection; lambda3 = 0.1 (§4).
 """
 from __future__ import annotations
 
@@ -273,6 +277,60 @@ def augment(A, b, l, u, Q, c, w, directions, x0, max_iters=100000):
         fx = fy
         moves.append((k, sgn, lam, fy))
     return x, fx, moves
+
+
+# ---------------------------------------------------------------------------
+# Initial feasible solutions, Eq. (4) (§3.3)
+
+
+def init_objective(A, b, X, lam3):
+    """||A x - b||_2^2 + lam3 * sum_i (x_i - floor x_i)(ceil x_i - x_i), per
+    row x of X."""
+    X = np.asarray(X, np.float64)
+    R = X @ np.asarray(A, np.float64).T - np.asarray(b, np.float64)
+    frac = (X - np.floor(X)) * (np.ceil(X) - X)
+    return np.sum(R * R, axis=1) + lam3 * np.sum(frac, axis=1)
+
+
+def init_gradient(A, b, X, lam3):
+    """Gradient of Eq. (4) in x: 2 A^T (A x - b) + lam3 (ceil x + floor x - 2 x)
+    (the same reading of the floor/ceil product as for Eq. (3))."""
+    X = np.asarray(X, np.float64)
+    Af = np.asarray(A, np.float64)
+    R = X @ Af.T - np.asarray(b, np.float64)
+    return 2.0 * R @ Af + lam3 * (np.ceil(X) + np.floor(X) - 2.0 * X)
+
+
+def projected_adam_update(x, m, v, grad, t, lr, l, u, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step on x followed by the projection onto the box [l, u]
+    (Eq. (4) constrains x to [l, u]; Adam itself is unconstrained)."""
+    z, m, v = adam_update(x, m, v, grad, t, lr, beta1, beta2, eps)
+    return np.clip(z, np.asarray(l, np.float64), np.asarray(u, np.float64)), m, v
+
+
+def feasible_roundings(A, b, l, u, X):
+    """The set of rounded rows round(x) (ties to even) that are feasible for
+    model (1): A round(x) = b exactly and l <= round(x) <= u."""
+    Xr = np.rint(np.asarray(X, np.float64)).astype(np.int64)
+    ok = np.all(Xr @ np.asarray(A, np.int64).T == np.asarray(b, np.int64), axis=1)
+    ok &= np.all((Xr >= np.asarray(l, np.int64)) & (Xr <= np.asarray(u, np.int64)), axis=1)
+    return {tuple(x) for x in Xr[ok]}
+
+
+def initial_solutions(A, b, l, u, X0, T, lam3=0.1, lr=0.003, beta1=0.9, beta2=0.999, eps=1e-8, period=1):
+    """Eq. (4) from every start row of X0 by projected Adam for T steps; after
+    every `period`-th step the rounded points feasible for model (1) are
+    collected.  Returns (final X, set of feasible integer points)."""
+    X = np.clip(np.asarray(X0, np.float64), np.asarray(l, np.float64), np.asarray(u, np.float64))
+    M = np.zeros_like(X)
+    V = np.zeros_like(X)
+    found = set()
+    for t in range(1, T + 1):
+        G = init_gradient(A, b, X, lam3)
+        X, M, V = projected_adam_update(X, M, V, G, t, lr, l, u, beta1, beta2, eps)
+        if t % period == 0:
+            found |= feasible_roundings(A, b, l, u, X)
+    return X, found
 
 
 # ---------------------------------------------------------------------------

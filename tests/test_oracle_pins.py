@@ -2,6 +2,7 @@
 itself -- a hand-evaluated example, a textbook Graver basis, a closed form, a
 library routine (torch.optim.Adam), finite differences, an invariant or brute
 force on tiny inputs.  CPU only."""
+import itertools
 import os
 
 import numpy as np
@@ -295,3 +296,82 @@ def test_augment_moves_keep_feasibility_and_strictly_decrease():
         assert O.f_value(inst.Q, inst.c, None, x) == fval < prev
         prev = fval
     assert np.array_equal(x, xf)
+
+
+# --- Eq. (4): initial feasible solutions ----------------------------------------
+
+def test_init_objective_hand_example():
+    """A = [1 2], b = 3: at x = (0.5, 1.25) A x = b, so only the integrality
+    term remains, lambda3 (0.5*0.5 + 0.25*0.75) = 0.1 * 0.4375; at the integer
+    feasible point (1, 1) the objective is 0, its global minimum."""
+    A, b = np.array([[1, 2]]), np.array([3])
+    f = O.init_objective(A, b, np.array([[0.5, 1.25], [1.0, 1.0], [0.0, 0.0]]), 0.1)
+    assert f[0] == pytest.approx(0.04375, abs=1e-15)
+    assert f[1] == 0.0
+    assert f[2] == pytest.approx(9.0)
+
+
+def test_init_gradient_matches_finite_differences():
+    rng = np.random.default_rng(3)
+    A = rng.integers(-3, 4, size=(4, 9))
+    b = rng.integers(-5, 6, size=4)
+    X = rng.uniform(-4, 4, size=(6, 9))
+    X[np.abs(X - np.rint(X)) < 0.05] += 0.1  # stay off the kinks of the integrality term
+    G = O.init_gradient(A, b, X, 0.1)
+    h = 1e-6
+    for j in range(9):
+        E = np.zeros_like(X)
+        E[:, j] = h
+        fd = (O.init_objective(A, b, X + E, 0.1) - O.init_objective(A, b, X - E, 0.1)) / (2 * h)
+        np.testing.assert_allclose(G[:, j], fd, rtol=1e-6, atol=1e-5)
+
+
+def test_projected_adam_first_step_and_box():
+    """First Adam step moves every coordinate by lr against the gradient sign;
+    the projection keeps the iterate in [l, u]."""
+    x = np.array([[0.0, 5.0, 2.5]])
+    g = np.array([[1.0, -3.0, 0.5]])
+    l, u = np.array([0, 0, 0]), np.array([5, 5, 5])
+    z, m, v = O.projected_adam_update(x, np.zeros_like(x), np.zeros_like(x), g, 1, 0.003, l, u)
+    np.testing.assert_allclose(z, [[0.0, 5.0, 2.497]], atol=1e-9)  # 0 - 0.003 clipped to 0, 5 + 0.003 to 5
+
+
+def test_feasible_roundings_agree_with_enumeration():
+    inst = I.tiny_graver_case()
+    pts = np.array(list(itertools.product(*[range(lo, hi + 1) for lo, hi in zip(inst.l, inst.u)])), dtype=np.int64)
+    feas = pts[np.all(pts @ inst.A.T.astype(np.int64) == inst.b, axis=1)]
+    assert len(feas) > 0
+    expect = {tuple(x) for x in feas}
+    assert O.feasible_roundings(inst.A, inst.b, inst.l, inst.u, feas) == expect
+    rng = np.random.default_rng(1)
+    noisy = feas + rng.uniform(-0.49, 0.49, size=feas.shape)
+    assert O.feasible_roundings(inst.A, inst.b, inst.l, inst.u, noisy) == expect
+    # every infeasible box point is rejected
+    other = pts[~np.all(pts @ inst.A.T.astype(np.int64) == inst.b, axis=1)]
+    assert O.feasible_roundings(inst.A, inst.b, inst.l, inst.u, other) == set()
+
+
+def test_initial_solutions_identity_system_reaches_b():
+    """A = I, b integer in the box: Eq. (4) is ||x - b||^2 plus the integrality
+    term, whose unique minimiser is b; projected Adam from the box reaches it
+    and the only feasible rounding is b."""
+    n = 5
+    A = np.eye(n, dtype=np.int64)
+    b = np.array([1, -2, 0, 3, -1])
+    l, u = np.full(n, -4), np.full(n, 4)
+    X0 = np.random.default_rng(2).uniform(-4, 4, size=(16, n))
+    X, found = O.initial_solutions(A, b, l, u, X0, T=3000, lr=0.01)
+    assert found == {tuple(b)}
+    assert np.max(np.abs(X - b)) < 0.1
+    assert np.all((X >= l) & (X <= u))
+
+
+def test_initial_solutions_on_tiny_instance_are_feasible():
+    inst = I.tiny_graver_case()
+    X0 = np.random.default_rng(4).uniform(inst.l, inst.u, size=(64, inst.n))
+    _, found = O.initial_solutions(inst.A, inst.b, inst.l, inst.u, X0, T=1500, lr=0.01)
+    assert len(found) > 0
+    for x in found:
+        x = np.array(x)
+        assert np.array_equal(inst.A.astype(np.int64) @ x, inst.b)
+        assert np.all((x >= inst.l) & (x <= inst.u))
