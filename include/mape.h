@@ -305,6 +305,46 @@ size_t mape_augment_workspace_bytes(int32_t n, int32_t S, int64_t K);
 int mape_augment_run(const mape_augment_args* args, int64_t* iters_out,
                      void* stream);
 
+/* Eq. (4) (§3.3) -- initial feasible solutions of model (1): projected Adam
+ * on ||A x - b||_2^2 + lambda3 sum_i (x_i - floor x_i)(ceil x_i - x_i) over
+ * the box [l, u] from every start row of X (starts outside the box are
+ * clipped into it first).  After every step whose number is a multiple of
+ * `period` the rounded iterate (ties to even) is tested exactly, A round(x)
+ * = b in int64 (the box holds by the projection), and, when it changed since
+ * the start's previous collection in this call (the first collection of a
+ * call always counts), appended to `sol` as n bytes round(x) - l (so u - l
+ * must be at most 255).  FP32 CUDA-core arithmetic, one warp per start.
+ * Continuing a run: pass X, M, V back with t0 = steps taken. */
+typedef struct {
+  int32_t n, m, P;
+  int32_t pad0;
+  const int32_t* A;        /* [m x n] int32                                  */
+  const int64_t* b;        /* [m]                                            */
+  const int32_t* l;        /* [n]                                            */
+  const int32_t* u;        /* [n]                                            */
+  float* X;                /* [P x n] in/out                                 */
+  float* M;                /* [P x n] in/out, Adam first moment              */
+  float* V;                /* [P x n] in/out, Adam second moment             */
+  int32_t t0, T, period;
+  float lambda3;           /* 0.1 in §4                                      */
+  float lr, eps;
+  double beta1, beta2;
+  uint8_t* sol;            /* [sol_cap x lds] output rows round(x) - l        */
+  int32_t lds;             /* row pitch in bytes, >= n                       */
+  int32_t pad1;
+  int64_t sol_cap;
+  unsigned long long* sol_count;  /* device counter, appended to            */
+  int32_t* flags;          /* device word, OR-ed: 1 = sol overflow           */
+  float* dbg_f;            /* optional [P]: objective at the input point     */
+  float* dbg_grad;         /* optional [P x n]: gradient at the input point  */
+  void* workspace;
+  size_t workspace_bytes;
+} mape_init_args;
+/* Errors: INVALID_ARG, SHAPE (n > 49152, or n + m too large for the warps'
+ * shared memory), CAPACITY (workspace), CUDA.  Asynchronous. */
+size_t mape_initial_solutions_workspace_bytes(int32_t n, int32_t m, int32_t T);
+int mape_initial_solutions(const mape_init_args* args, void* stream);
+
 /* ========================================================================== *
  * Instance handle (host pointers)                                             *
  * ========================================================================== */

@@ -58,6 +58,14 @@ class ExtractArgs(C.Structure):
                 ("workspace", P_), ("workspace_bytes", C.c_size_t)]
 
 
+class InitArgs(C.Structure):
+    _fields_ = [("n", I32), ("m", I32), ("P", I32), ("pad0", I32), ("A", P_), ("b", P_), ("l", P_), ("u", P_),
+                ("X", P_), ("M", P_), ("V", P_), ("t0", I32), ("T", I32), ("period", I32), ("lambda3", F32),
+                ("lr", F32), ("eps", F32), ("beta1", C.c_double), ("beta2", C.c_double), ("sol", P_),
+                ("lds", I32), ("pad1", I32), ("sol_cap", I64), ("sol_count", P_), ("flags", P_),
+                ("dbg_f", P_), ("dbg_grad", P_), ("workspace", P_), ("workspace_bytes", C.c_size_t)]
+
+
 class AugmentArgs(C.Structure):
     _fields_ = [("n", I32), ("S", I32), ("K", I64), ("G", P_), ("ldg", I32), ("pad0", I32),
                 ("a", P_), ("q4", P_), ("q_row", P_), ("q_col", P_), ("q_val", P_), ("nnz", I32),
@@ -125,6 +133,8 @@ _SIGS = {
     "mape_phi_grad": (C.c_int, [P_, I32, I32, P_, I32, F32, F32, P_, P_, P_]),
     "mape_extract_workspace_bytes": (C.c_size_t, [I32, I32, I32, I32]),
     "mape_extract": (C.c_int, [C.POINTER(ExtractArgs), P_]),
+    "mape_initial_solutions_workspace_bytes": (C.c_size_t, [I32, I32, I32]),
+    "mape_initial_solutions": (C.c_int, [C.POINTER(InitArgs), P_]),
     "mape_dedup_workspace_bytes": (C.c_size_t, [I64, I32]),
     "mape_dedup": (C.c_int, [P_, I64, I32, I32, P_, I64, C.POINTER(I64), P_, C.c_size_t, P_]),
     "mape_dedup_static_max_rows": (I64, []),
@@ -283,6 +293,24 @@ def extract_batch(calls, *, t0, T, cfg: Config, stream=None):
     bws = _workspace(max(nb, 16), dev)
     _check(lib().mape_extract_batch(arr, len(calls), _ptr(bws), bws.numel(), _stream(stream)), "mape_extract_batch")
     return keep
+
+
+def initial_solutions(A, b, l, u, X, M, V, *, t0, T, sol, sol_count, flags, lds, lambda3=0.1, lr=0.003,
+                      period=1, dbg_f=None, dbg_grad=None, stream=None):
+    """Eq. (4): T projected Adam steps in place on X/M/V (device tensors);
+    appends the exactly feasible roundings to sol as bytes round(x) - l."""
+    m, n = A.shape
+    a = InitArgs()
+    a.n, a.m, a.P = n, m, X.shape[0]
+    a.A, a.b, a.l, a.u, a.X, a.M, a.V = _ptr(A), _ptr(b), _ptr(l), _ptr(u), _ptr(X), _ptr(M), _ptr(V)
+    a.t0, a.T, a.period, a.lambda3, a.lr, a.eps = t0, T, period, lambda3, lr, 1e-8
+    a.beta1, a.beta2 = 0.9, 0.999
+    a.sol, a.lds, a.sol_cap = _ptr(sol), lds, sol.shape[0]
+    a.sol_count, a.flags, a.dbg_f, a.dbg_grad = _ptr(sol_count), _ptr(flags), _ptr(dbg_f), _ptr(dbg_grad)
+    ws = _workspace(max(16, lib().mape_initial_solutions_workspace_bytes(n, m, T)), X.device)
+    a.workspace, a.workspace_bytes = _ptr(ws), ws.numel()
+    _check(lib().mape_initial_solutions(C.byref(a), _stream(stream)), "mape_initial_solutions")
+    return ws
 
 
 def extract(B, span, Z, M, V, *, t0, T, cfg: Config, cand, cand_count, flags, ldc,
