@@ -426,6 +426,17 @@ int mape_get_solution(mape_handle h, int32_t* x, int64_t* fval);
 /* Copies every start's final point X [S x n] and value fval [S]. */
 int mape_get_solutions(mape_handle h, int32_t* X, int64_t* fval, int32_t S);
 
+/* Eq. (4) on the handle's instance: P starts X0 [P x n] (host or device
+ * pointer, copied; e.g. uniform in [l, u]), T steps of projected Adam with
+ * lambda3 = 0.1 and the handle's Adam settings, collection every `period`
+ * steps; the distinct exactly feasible points found are written to
+ * X_out [cap x n] (sorted by the bytes round(x) - l) and counted in *S_out,
+ * ready to be the starts of mape_augment (multi-start augmentation, §3.3).
+ * CAPACITY if cap < *S_out.  Synchronous; the handle must be idle. */
+int mape_find_initial_solutions(mape_handle h, int32_t P, const float* X0, int32_t T,
+                                int32_t period, int32_t* X_out, int32_t cap,
+                                int32_t* S_out);
+
 void mape_destroy(mape_handle h);
 
 /* ========================================================================== *

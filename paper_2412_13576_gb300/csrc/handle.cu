@@ -561,6 +561,78 @@ extern "C" int mape_get_solutions(mape_handle h, int32_t* X, int64_t* fval, int3
   return MAPE_OK;
 }
 
+namespace {
+__global__ void sol_rows_kernel(const int8_t* __restrict__ rows, int64_t K, int n, int lds,
+                                const int32_t* __restrict__ l, int32_t* __restrict__ out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= K * n) return;
+  const int64_t k = t / n;
+  const int i = (int)(t % n);
+  out[t] = (int32_t)(uint8_t)rows[k * lds + i] + l[i];
+}
+}  // namespace
+
+extern "C" int mape_find_initial_solutions(mape_handle h, int32_t P, const float* X0, int32_t T, int32_t period,
+                                           int32_t* X_out, int32_t cap, int32_t* S_out) {
+  using namespace mape_detail;
+  if (!h || !X0 || !S_out || P <= 0 || T < 0 || period <= 0 || cap < 0 || (cap > 0 && !X_out))
+    return MAPE_ERR_INVALID_ARG;
+  if (!idle(h)) return MAPE_ERR_STATE;
+  h->join();
+  const int n = h->n, m = h->m, lds = h->ldg;
+  const int64_t rows = std::max<int64_t>(1, std::min<int64_t>((int64_t)P * (T / period + 1), (int64_t)1 << 22));
+  std::vector<std::pair<void*, size_t>> bufs;
+  auto cleanup = [&]() { h->release_all(bufs); };
+  float* dX = h->take<float>(bufs, (size_t)P * n);
+  float* dM = h->take<float>(bufs, (size_t)P * n);
+  float* dV = h->take<float>(bufs, (size_t)P * n);
+  int8_t* dSol = h->take<int8_t>(bufs, (size_t)rows * lds);
+  int8_t* dUniq = h->take<int8_t>(bufs, (size_t)rows * lds);
+  unsigned long long* dCount = h->take<unsigned long long>(bufs, 1);
+  int32_t* dFlags = h->take<int32_t>(bufs, 1);
+  const size_t iw = mape_initial_solutions_workspace_bytes(n, m, T);
+  const size_t dw = mape_dedup_workspace_bytes(rows, lds);
+  char* dWork = h->take<char>(bufs, std::max(iw, dw));
+  if (!dX || !dM || !dV || !dSol || !dUniq || !dCount || !dFlags || !dWork) { cleanup(); return MAPE_ERR_OOM; }
+  cudaStream_t s = h->stream;
+  int rc = upload(h, dX, X0, sizeof(float) * (size_t)P * n);
+  if (rc) { cleanup(); return rc; }
+  if (cudaMemsetAsync(dM, 0, sizeof(float) * (size_t)P * n, s) != cudaSuccess ||
+      cudaMemsetAsync(dV, 0, sizeof(float) * (size_t)P * n, s) != cudaSuccess ||
+      cudaMemsetAsync(dSol, 0, (size_t)rows * lds, s) != cudaSuccess ||
+      cudaMemsetAsync(dCount, 0, sizeof(unsigned long long), s) != cudaSuccess ||
+      cudaMemsetAsync(dFlags, 0, sizeof(int32_t), s) != cudaSuccess) { cleanup(); return MAPE_ERR_CUDA; }
+  mape_init_args a{};
+  a.n = n; a.m = m; a.P = P; a.A = h->dA; a.b = h->db; a.l = h->dl; a.u = h->du; a.X = dX; a.M = dM; a.V = dV;
+  a.t0 = 0; a.T = T; a.period = period; a.lambda3 = 0.1f; a.lr = h->cfg.lr; a.eps = h->cfg.eps;
+  a.beta1 = h->cfg.beta1; a.beta2 = h->cfg.beta2;
+  a.sol = reinterpret_cast<uint8_t*>(dSol); a.lds = lds; a.sol_cap = rows; a.sol_count = dCount; a.flags = dFlags;
+  a.workspace = dWork; a.workspace_bytes = std::max(iw, dw);
+  if ((rc = mape_initial_solutions(&a, s))) { cleanup(); return rc; }
+  unsigned long long cnt = 0;
+  int32_t flags = 0;
+  if (cudaMemcpyAsync(&cnt, dCount, sizeof(cnt), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&flags, dFlags, sizeof(flags), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) { cleanup(); return MAPE_ERR_CUDA; }
+  const int64_t got = std::min<int64_t>((int64_t)cnt, rows);
+  int64_t K = 0;
+  if (got > 0 && (rc = mape_dedup(dSol, got, n, lds, dUniq, rows, &K, dWork, std::max(iw, dw), s))) {
+    cleanup();
+    return rc;
+  }
+  *S_out = (int32_t)K;
+  if (K > cap) { cleanup(); return MAPE_ERR_CAPACITY; }
+  if (K > 0) {
+    int32_t* dOut = h->take<int32_t>(bufs, (size_t)K * n);
+    if (!dOut) { cleanup(); return MAPE_ERR_OOM; }
+    launch(sol_rows_kernel, (unsigned)ceil_div(K * n, 256), 256, 0, s, dUniq, K, n, lds, h->dl, dOut);
+    if (cudaMemcpyAsync(X_out, dOut, sizeof(int32_t) * (size_t)K * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { cleanup(); return MAPE_ERR_CUDA; }
+  }
+  cleanup();
+  return (flags & 1) ? MAPE_ERR_CAPACITY : MAPE_OK;
+}
+
 extern "C" void mape_destroy(mape_handle h) {
   if (!h) return;
   h->cancel.store(true);

@@ -158,6 +158,7 @@ _SIGS = {
     "mape_get_solution": (C.c_int, [P_, P_, C.POINTER(I64)]),
     "mape_get_solutions": (C.c_int, [P_, P_, P_, I32]),
     "mape_destroy": (None, [P_]),
+    "mape_find_initial_solutions": (C.c_int, [P_, I32, P_, I32, I32, P_, I32, C.POINTER(I32)]),
     "mape_request_bytes": (C.c_size_t, [I32, I32, I32, I32, C.POINTER(Config)]),
     "mape_server_create": (C.c_int, [C.POINTER(ServerConfig), C.POINTER(P_)]),
     "mape_server_submit": (C.c_int, [P_, P_, P_, P_, P_, C.POINTER(Problem), P_, I32, P_, P_, P_, I32,
@@ -497,6 +498,21 @@ class Instance:
         out = np.empty((K.value, self.n), dtype=np.int32)
         _check(lib().mape_get_directions(self.h, _host(out), K.value, C.byref(K)), "mape_get_directions")
         return out
+
+    def initial_solutions(self, X0, T=1000, period=1):
+        """Eq. (4) from the starts X0 [P x n] (host float32): the distinct
+        feasible points found, [S x n] int32."""
+        X0 = _np(X0, np.float32)
+        S = I32(0)
+        cap = min(X0.shape[0] * (T // period + 1), 1 << 16)
+        out = np.empty((cap, self.n), dtype=np.int32)
+        rc = lib().mape_find_initial_solutions(self.h, X0.shape[0], _host(X0), T, period, _host(out), cap, C.byref(S))
+        if rc == -7 and S.value > cap:  # more distinct points than the first buffer held: run again with room
+            out = np.empty((S.value, self.n), dtype=np.int32)
+            rc = lib().mape_find_initial_solutions(self.h, X0.shape[0], _host(X0), T, period, _host(out), S.value,
+                                                   C.byref(S))
+        _check(rc, "mape_find_initial_solutions")
+        return out[: S.value]
 
     def solution(self):
         x = np.empty(self.n, dtype=np.int32)

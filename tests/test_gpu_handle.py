@@ -80,3 +80,34 @@ def test_handle_errors(M):
         with pytest.raises(M.MapeError) as e:
             h.augment(x[None, :])
         assert e.value.code == -5
+
+
+def test_handle_initial_solutions_and_multistart_augmentation(M):
+    """Eq. (4) on the handle gives distinct, exactly feasible starts S0; the
+    multi-start augmentation from all of them (§3.3) gives, per start, the
+    oracle's Algorithm 1 result on the same direction set, and the best of
+    them is reported."""
+    inst = I.small_dense()
+    rng = np.random.default_rng(9)
+    X0 = rng.uniform(inst.l, inst.u, size=(256, inst.n)).astype(np.float32)
+    X0[:64] = inst.xbar + rng.uniform(-0.45, 0.45, size=(64, inst.n))
+    cfg = M.default_config(T=200, precision=1)
+    with M.Instance.from_generated(inst, cfg) as h:
+        S0 = h.initial_solutions(X0, T=400, period=10)
+        assert S0.shape[0] >= 1
+        S0i = S0.astype(np.int64)
+        assert np.all(S0i @ inst.A.T.astype(np.int64) == inst.b)
+        assert np.all((S0i >= inst.l) & (S0i <= inst.u))
+        assert np.unique(S0i, axis=0).shape[0] == S0.shape[0]
+        S0 = S0[:16]
+        h.extract_directions(256, Z0=I.normal_starts(inst, 256, seed=2001).Z0)
+        h.wait(300)
+        D = h.directions()
+        h.augment(S0)
+        h.wait(300)
+        X, F = h.solutions(S0.shape[0])
+        for k in range(S0.shape[0]):
+            xo, fo, _ = O.augment(inst.A, inst.b, inst.l, inst.u, inst.Q, inst.c, None, D, S0[k])
+            assert F[k] == fo and np.array_equal(X[k], xo)
+        x, fx = h.solution()
+        assert fx == F.min()
