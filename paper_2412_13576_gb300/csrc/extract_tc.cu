@@ -127,7 +127,7 @@ __host__ __device__ inline Smem smem_layout(int n_pad, int d_pad, int nterms, in
   s.fl = o;   o = al(o + kTileM * 4, 128);
   s.fnz = o;  o = al(o + kTileM * 4, 128);
   s.slot = o; o = al(o + kTileM * 8, 128);
-  s.bar = o;  o = al(o + 8, 16);
+  s.bar = o;  o = al(o + 16, 16);  // two mbarriers: forward/gradient MMAs, B round(z) MMAs
   s.tmem = o; o = al(o + 4, 16);
   s.total = o;
   return s;
@@ -189,7 +189,10 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     s_fl[tid] = kChanged;  // the first collection of a call always counts
     s_fnz[tid] = kNoNz;
   }
-  if (tid == 0) mbar_init(bar, 1);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 8, 1);
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
                  "r"(kTmemCols));
@@ -389,6 +392,11 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     }
   };
   bool timed_out = false;
+  // the B round(z) MMAs of a collection step complete on their own barrier, so
+  // that the sign phase does not wait for them
+  const uint32_t bar2 = bar + 8;
+  uint32_t phase2 = 0;
+  bool d2_pending = false;
   auto wait_mma = [&]() -> bool {
     bool ok = mbar_wait_bounded(bar, phase);
     phase ^= 1;
@@ -414,9 +422,13 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
           mma_bf16(tmem, a, b, idesc_fwd, (term > 0 || kk > 0) ? 1u : 0u);
         }
       }
-      if (collect_prev) issue_d2();
       mma_commit(bar);
+      if (collect_prev) {
+        issue_d2();
+        mma_commit(bar2);
+      }
     }
+    d2_pending = collect_prev;
     if (!wait_mma()) { bail = true; break; }
     // (2) S = sign(D1) into shared memory; test the previous step's candidate
     float l1 = 0.f;
@@ -434,11 +446,23 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       store_row8(Sop, r, ch * 16 + hoff, n_pad, w);
     }
     if (dbg_step) s_pl1[part * kTileM + r] = l1;
-    if (collect_prev) test_candidate();
+    bool d2_late = false;
+    if (collect_prev) {
+      d2_late = __any_sync(0xffffffffu, !mbar_wait_bounded(bar2, phase2));  // warp-uniform: the loads are collective
+      phase2 ^= 1;
+      d2_pending = false;
+      tc_fence_after();
+      if (!d2_late) test_candidate();
+    }
     tc_wait_ld();
     tc_fence_before();
     fence_async_smem();
-    __syncthreads();
+    if (__syncthreads_or(d2_late)) {
+      if (tid == 0) atomicOr(p.flags, 16);
+      timed_out = true;
+      bail = true;
+      break;
+    }
     // (3) gradient MMA, overlapped with appending the previous candidate
     if (tid == 0) {
       tc_fence_after();
@@ -514,8 +538,9 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
           const float fl = floorf(z);
           // ceil z + floor z = 2 floor z + [z not an integer]
           float grad = __uint_as_float(v[cc]) + p.lambda1 * (2.f * fl + (z != fl ? 1.f : 0.f) - 2.f * z);
-          if (j == kmax) grad += inv_term * (float)mape_sign_f(z);
-          if (kId) grad += (float)mape_sign_f(z);  // identity row j of B: sign((Bz)_j) = sign(z_j)
+          const float sz = (float)mape_sign_f(z);
+          if (j == kmax) grad += inv_term * sz;
+          if (kId) grad += sz;  // identity row j of B: sign((Bz)_j) = sign(z_j)
           if (dbg_step && live) {
             frac += (z - fl) * (ceilf(z) - z);
             if (kId) l1_id += fabsf(z);
@@ -531,7 +556,10 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
           vo[cc] = __float_as_uint(vv);
           zn[q] = znew;
           rn[q] = rintf(znew);
-          if (live) {
+          // padding coordinates (z = 0 throughout) and inactive starts leave
+          // every tracker unchanged: their roundings never change, are 0, are
+          // within any box and never beat a real coordinate's |z| or index
+          {
             changed |= rn[q] != rintf(z);
             unexact |= fabsf(rn[q]) > 256.f;
             const float a = fabsf(znew);
@@ -606,7 +634,10 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       write_candidate();
     }
   }
-  if (timed_out) mbar_wait_bounded(bar, phase ^ 1);  // let an MMA still in flight drain
+  if (timed_out) {  // let MMAs still in flight drain before TMEM is freed
+    mbar_wait_bounded(bar, phase ^ 1);
+    if (d2_pending) mbar_wait_bounded(bar2, phase2);
+  }
   if (kRes) {  // the state leaves TMEM for the caller's arrays
     for (int ch = split; ch < dch; ch += kSplits) {
       const int c0 = ch * 16 + hoff;
