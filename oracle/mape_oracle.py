@@ -334,6 +334,42 @@ def initial_solutions(A, b, l, u, X0, T, lam3=0.1, lr=0.003, beta1=0.9, beta2=0.
 
 
 # ---------------------------------------------------------------------------
+# Linear inequalities G x >= h (§3.4, Corollary 3.3)
+
+
+def inequality_extension(A, b, l, u, G, h, B):
+    """The equality form of model (1) with G x >= h: slack s = G x - h >= 0,
+    constraint matrix [A 0; G -I], right-hand side (b, h), kernel basis
+    [B; G B] (Corollary 3.3).  x is boxed, so each slack is bounded above by
+    its largest value over the box, max_x (G x)_k - h_k.  Returns
+    (A', b', l', u', B'); raises if some inequality cannot hold in the box."""
+    A, G, B = (np.asarray(M, np.int64) for M in (A, G, B))
+    b, h, l, u = (np.asarray(v, np.int64) for v in (b, h, l, u))
+    m, n = A.shape
+    m2 = G.shape[0]
+    smax = np.sum(np.maximum(G * l, G * u), axis=1) - h
+    if np.any(smax < 0):
+        raise ValueError("an inequality cannot hold anywhere in the box")
+    A2 = np.block([[A, np.zeros((m, m2), np.int64)], [G, -np.eye(m2, dtype=np.int64)]])
+    b2 = np.concatenate([b, h])
+    l2 = np.concatenate([l, np.zeros(m2, np.int64)])
+    u2 = np.concatenate([u, smax])
+    B2 = np.concatenate([B, G @ B], axis=0)
+    return A2, b2, l2, u2, B2
+
+
+def lattice_contains(B, g):
+    """True if the integer vector g is an integer combination of the columns
+    of B (full column rank): solve B z = g exactly in rationals via least
+    squares and check that z is integral and reproduces g."""
+    B = np.asarray(B, np.float64)
+    z, *_ = np.linalg.lstsq(B, np.asarray(g, np.float64), rcond=None)
+    zi = np.rint(z)
+    return bool(np.allclose(z, zi, atol=1e-9) and np.array_equal(np.asarray(B, np.int64) @ zi.astype(np.int64),
+                                                                   np.asarray(g, np.int64)))
+
+
+# ---------------------------------------------------------------------------
 # Definition of the Graver basis (§1), by enumeration, for tiny instances
 
 

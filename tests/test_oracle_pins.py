@@ -375,3 +375,42 @@ def test_initial_solutions_on_tiny_instance_are_feasible():
         x = np.array(x)
         assert np.array_equal(inst.A.astype(np.int64) @ x, inst.b)
         assert np.all((x >= inst.l) & (x <= inst.u))
+
+
+# --- §3.4: linear inequalities through slack variables ---------------------------
+
+def _tiny_with_inequality():
+    inst = I.tiny_graver_case()
+    G = np.array([[1, 1, 0, 0, 0, 0], [0, 0, 1, -1, 0, 1]])
+    h = G @ inst.xbar.astype(np.int64) - np.array([1, 2])  # xbar satisfies both with slack 1 and 2
+    return inst, G, h
+
+
+def test_inequality_extension_kernel_basis():
+    """Corollary 3.3: A' [B; GB] = 0, and every kernel element of
+    A' = [A 0; G -I] in a box is an integer combination of [B; GB]
+    (enumeration on the 6-variable instance with two inequalities)."""
+    inst, G, h = _tiny_with_inequality()
+    A2, b2, l2, u2, B2 = O.inequality_extension(inst.A, inst.b, inst.l, inst.u, G, h, inst.B)
+    assert A2.shape == (4, 8) and B2.shape == (8, 4)
+    assert np.all(A2 @ B2 == 0)
+    x2 = np.concatenate([inst.xbar, G @ inst.xbar - h])
+    assert np.array_equal(A2 @ x2, b2) and np.all((x2 >= l2) & (x2 <= u2))
+    K = O.kernel_box(A2, 2)
+    assert len(K) > 0
+    assert all(O.lattice_contains(B2, g) for g in K)
+    # a vector outside the kernel is not in the lattice
+    assert not O.lattice_contains(B2, np.eye(8, dtype=np.int64)[0])
+
+
+def test_inequality_extension_slack_bounds():
+    """u' of a slack is its largest value over the box; an inequality that no
+    point of the box satisfies is refused."""
+    A = np.array([[1, 1]])
+    B = np.array([[1], [-1]])
+    G = np.array([[2, -1]])
+    l, u = np.array([0, 0]), np.array([3, 4])
+    _, _, l2, u2, _ = O.inequality_extension(A, [2], l, u, G, [1], B)
+    assert l2[-1] == 0 and u2[-1] == 2 * 3 - 0 - 1
+    with pytest.raises(ValueError):
+        O.inequality_extension(A, [2], l, u, G, [7], B)
