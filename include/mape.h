@@ -345,6 +345,21 @@ typedef struct {
 size_t mape_initial_solutions_workspace_bytes(int32_t n, int32_t m, int32_t T);
 int mape_initial_solutions(const mape_init_args* args, void* stream);
 
+/* §3.4, Corollary 3.3 -- linear inequalities G x >= h (G [m2 x n], h [m2]):
+ * writes the equality form of the instance with slack s = G x - h >= 0,
+ *   A2 [(m+m2) x (n+m2)] = [A 0; G -I],  b2 = (b, h),
+ *   l2 = (l, 0), u2 = (u, smax) with smax_k = max over the box of (G x)_k - h_k,
+ *   B2 [(n+m2) x d] = [B; G B]  (a basis of Ker_Z(A2), with B's identity top),
+ * all host arrays (row-major) owned by the caller.  The objective of the
+ * extended instance is f of the first n coordinates (zero rows and columns
+ * for the slacks).  Errors: INVALID_ARG, BOUNDS (some inequality holds
+ * nowhere in the box), SHAPE (G B or smax beyond int32).  Host-only. */
+int mape_inequality_extension(int32_t n, int32_t m, int32_t m2, const int32_t* A,
+                              const int64_t* b, const int32_t* l, const int32_t* u,
+                              const int32_t* G, const int64_t* h, const int32_t* B,
+                              int32_t* A2, int64_t* b2, int32_t* l2, int32_t* u2,
+                              int32_t* B2);
+
 /* ========================================================================== *
  * Instance handle (host pointers)                                             *
  * ========================================================================== */

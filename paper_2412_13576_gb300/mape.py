@@ -158,6 +158,7 @@ _SIGS = {
     "mape_get_solution": (C.c_int, [P_, P_, C.POINTER(I64)]),
     "mape_get_solutions": (C.c_int, [P_, P_, P_, I32]),
     "mape_destroy": (None, [P_]),
+    "mape_inequality_extension": (C.c_int, [I32, I32, I32, P_, P_, P_, P_, P_, P_, P_, P_, P_, P_, P_, P_]),
     "mape_find_initial_solutions": (C.c_int, [P_, I32, P_, I32, I32, P_, I32, C.POINTER(I32)]),
     "mape_request_bytes": (C.c_size_t, [I32, I32, I32, I32, C.POINTER(Config)]),
     "mape_server_create": (C.c_int, [C.POINTER(ServerConfig), C.POINTER(P_)]),
@@ -632,3 +633,30 @@ class Server:
 def request_bytes(n, m, P, S, cfg: Config | None = None) -> int:
     cfg = cfg if cfg is not None else default_config()
     return int(lib().mape_request_bytes(n, m, P, S, C.byref(cfg)))
+
+
+def inequality_extension(inst, G, h):
+    """The instance with G x >= h added, in equality form with slacks
+    (mape_inequality_extension): a copy of `inst` with n + m2 variables whose
+    objective ignores the slacks and whose xbar carries the slacks G xbar - h."""
+    import dataclasses
+    G = _np(np.atleast_2d(G), np.int32)
+    h = _np(np.atleast_1d(h), np.int64)
+    n, m, m2, d = inst.n, inst.m, G.shape[0], inst.d
+    A, b, l, u, B = (_np(inst.A, np.int32), _np(inst.b, np.int64), _np(inst.l, np.int32), _np(inst.u, np.int32),
+                     _np(inst.B, np.int32))
+    A2 = np.empty((m + m2, n + m2), np.int32)
+    b2 = np.empty(m + m2, np.int64)
+    l2 = np.empty(n + m2, np.int32)
+    u2 = np.empty(n + m2, np.int32)
+    B2 = np.empty((n + m2, d), np.int32)
+    _check(lib().mape_inequality_extension(n, m, m2, _host(A), _host(b), _host(l), _host(u), _host(G), _host(h),
+                                           _host(B), _host(A2), _host(b2), _host(l2), _host(u2), _host(B2)),
+           "mape_inequality_extension")
+    Q2 = np.zeros((n + m2, n + m2), np.int32)
+    Q2[:n, :n] = inst.Q
+    c2 = np.concatenate([inst.c, np.zeros(m2, np.int32)]).astype(np.int32)
+    w2 = None if inst.w is None else np.concatenate([inst.w, np.zeros(m2, np.int32)]).astype(np.int32)
+    xbar2 = np.concatenate([inst.xbar, (G.astype(np.int64) @ inst.xbar - h)]).astype(np.int32)
+    return dataclasses.replace(inst, name=inst.name + f"_ineq{m2}", n=n + m2, m=m + m2, A=A2, b=b2, l=l2, u=u2,
+                               B=B2, Q=Q2, c=c2, w=w2, xbar=xbar2)

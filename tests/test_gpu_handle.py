@@ -111,3 +111,31 @@ def test_handle_initial_solutions_and_multistart_augmentation(M):
             assert F[k] == fo and np.array_equal(X[k], xo)
         x, fx = h.solution()
         assert fx == F.min()
+
+
+def test_handle_with_linear_inequalities(M):
+    """§3.4: the small instance with three inequalities G x >= h, run as its
+    equality form with slacks: every direction lies in Ker([A 0; G -I]), the
+    augmentation equals the oracle's Algorithm 1 on that set, and the final x
+    satisfies G x >= h."""
+    inst = I.small_dense()
+    rng = np.random.default_rng(4)
+    G = rng.choice([-1, 0, 1], p=[0.15, 0.7, 0.15], size=(3, inst.n))
+    h = G @ inst.xbar.astype(np.int64) - rng.integers(0, 4, size=3)
+    e = M.inequality_extension(inst, G, h)
+    assert np.max(e.u - e.l) <= 127  # direction entries are stored as int8
+    cfg = M.default_config(T=200, precision=1)
+    with M.Instance.from_generated(e, cfg) as hd:
+        hd.extract_directions(256, Z0=I.normal_starts(e, 256, seed=2001).Z0)
+        hd.wait(300)
+        D = hd.directions()
+        check_direction_set(e, D)
+        hd.augment(e.xbar[None, :])
+        hd.wait(300)
+        x, fx = hd.solution()
+    xo, fo, _ = O.augment(e.A, e.b, e.l, e.u, e.Q, e.c, None, D, e.xbar)
+    assert fx == fo and np.array_equal(x, xo)
+    xs = x[: inst.n].astype(np.int64)
+    assert np.all(G @ xs >= h)
+    assert np.array_equal(inst.A.astype(np.int64) @ xs, inst.b)
+    assert fx <= O.f_value(inst.Q, inst.c, None, inst.xbar)

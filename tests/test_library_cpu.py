@@ -144,3 +144,26 @@ def test_bounds_rejected_before_upload(lib):
                                   ctypes.c_void_p(l.ctypes.data), ctypes.c_void_p(u.ctypes.data), ctypes.byref(prob),
                                   ctypes.c_void_p(B.ctypes.data), ctypes.byref(cfg), None, ctypes.byref(h))
     assert rc == -4
+
+
+def test_inequality_extension_matches_oracle(lib):
+    """mape_inequality_extension (host-only) writes the oracle's equality form
+    of G x >= h: [A 0; G -I], (b, h), slack bounds, [B; G B]."""
+    import numpy as np
+    from oracle import mape_oracle as O
+    from paper_2412_13576_gb300 import instances as I
+    from paper_2412_13576_gb300 import mape
+    for inst, seed in ((I.tiny_graver_case(), 1), (I.small_dense(), 2), (I.medium_sparse(), 3)):
+        rng = np.random.default_rng(seed)
+        G = rng.integers(-2, 3, size=(3, inst.n))
+        h = G @ inst.xbar.astype(np.int64) - rng.integers(0, 4, size=3)
+        e = mape.inequality_extension(inst, G, h)
+        A2, b2, l2, u2, B2 = O.inequality_extension(inst.A, inst.b, inst.l, inst.u, G, h, inst.B)
+        for got, want in ((e.A, A2), (e.b, b2), (e.l, l2), (e.u, u2), (e.B, B2)):
+            assert np.array_equal(got, want)
+        assert np.all(e.A.astype(np.int64) @ e.B == 0)
+        assert np.array_equal(e.A.astype(np.int64) @ e.xbar, e.b)
+    inst = I.tiny_graver_case()
+    with pytest.raises(mape.MapeError) as err:
+        mape.inequality_extension(inst, np.ones((1, inst.n), np.int32), [10 ** 6])
+    assert err.value.code == -4
