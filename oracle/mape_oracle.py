@@ -370,6 +370,122 @@ def lattice_contains(B, g):
 
 
 # ---------------------------------------------------------------------------
+# A kernel basis of a general A (Lemma 3.1, Theorem 3.2) and LLL (Appendix A)
+
+
+def _egcd(a, b):
+    """(g, x, y) with x a + y b = g = gcd(a, b) >= 0 (Python integers)."""
+    x0, y0, x1, y1 = 1, 0, 0, 1
+    while b != 0:
+        q = a // b
+        a, b = b, a - q * b
+        x0, x1 = x1, x0 - q * x1
+        y0, y1 = y1, y0 - q * y1
+    if a < 0:
+        a, x0, y0 = -a, -x0, -y0
+    return a, x0, y0
+
+
+def hnf_kernel_basis(A):
+    """Lemma 3.1: unimodular integer column operations K bring A to (H | 0)
+    with H lower triangular (row by row, each row's entries right of the pivot
+    are cleared by extended-gcd combinations of two columns); the last
+    d = n - m columns of K are a basis of Ker_Z(A) (Theorem 3.2).  Exact
+    Python integers; A must have full row rank.  Returns (B [n x d], K)."""
+    A = [[int(v) for v in row] for row in np.asarray(A, np.int64)]
+    m, n = len(A), len(A[0])
+    M = [row[:] for row in A]
+    K = [[int(i == j) for j in range(n)] for i in range(n)]
+
+    def combine(c, j, x, y, p, q):  # col_c <- x col_c + y col_j, col_j <- p col_c + q col_j
+        for R in (M, K):
+            for row in R:
+                a, b = row[c], row[j]
+                row[c], row[j] = x * a + y * b, p * a + q * b
+
+    for i in range(m):
+        c = i
+        for j in range(c + 1, n):
+            b = M[i][j]
+            if b == 0:
+                continue
+            a = M[i][c]
+            g, x, y = _egcd(a, b)
+            combine(c, j, x, y, -b // g, a // g)
+        if M[i][c] == 0:
+            raise ValueError("A does not have full row rank")
+        if M[i][c] < 0:
+            for R in (M, K):
+                for row in R:
+                    row[c] = -row[c]
+    B = np.array([[K[r][j] for j in range(m, n)] for r in range(n)], dtype=object)
+    return B, np.array(K, dtype=object)
+
+
+def lll_reduce(B, factor=2):
+    """Appendix A's LLL in exact rationals: size-reduce column i against
+    columns i-1, ..., 1 (mu_ij rounded to the nearest integer, halves away
+    from zero), then exchange columns i-1 and i when
+    ||B*_{i-1}||^2 > factor ||B*_i||^2 and step back, else step forward.  The
+    Gram-Schmidt data are recomputed from scratch after every change (plain,
+    slow, obviously the definition).  Returns the reduced basis (object ints)."""
+    from fractions import Fraction
+    Bc = [[int(B[r][j]) for r in range(len(B))] for j in range(len(B[0]))]  # columns
+    d = len(Bc)
+
+    def dot(u, v):
+        return sum(Fraction(a) * b for a, b in zip(u, v))
+
+    def gso():
+        star, mu = [], [[Fraction(0)] * d for _ in range(d)]
+        for i in range(d):
+            v = [Fraction(a) for a in Bc[i]]
+            for j in range(i):
+                mu[i][j] = dot(Bc[i], star[j]) / dot(star[j], star[j])
+                v = [a - mu[i][j] * b for a, b in zip(v, star[j])]
+            star.append(v)
+        return star, mu
+
+    def nearest(q):
+        f = q.numerator // q.denominator
+        r = q - f
+        return f + 1 if r > Fraction(1, 2) or (r == Fraction(1, 2) and q > 0) else f
+
+    i = 1
+    while i < d:
+        for j in range(i - 1, -1, -1):
+            _, mu = gso()
+            k = nearest(mu[i][j])
+            if k != 0:
+                Bc[i] = [a - k * b for a, b in zip(Bc[i], Bc[j])]
+        star, _ = gso()
+        if dot(star[i - 1], star[i - 1]) > factor * dot(star[i], star[i]):
+            Bc[i - 1], Bc[i] = Bc[i], Bc[i - 1]
+            i = max(i - 1, 1)
+        else:
+            i += 1
+    return np.array([[Bc[j][r] for j in range(d)] for r in range(len(Bc[0]))], dtype=object)
+
+
+def lll_conditions(B, factor=2):
+    """(size_reduced, exchange_condition) of Appendix A's definition, exact."""
+    from fractions import Fraction
+    Bc = [[Fraction(int(B[r][j])) for r in range(len(B))] for j in range(len(B[0]))]
+    d = len(Bc)
+    star, ok_size = [], True
+    for i in range(d):
+        v = Bc[i][:]
+        for j in range(i):
+            mu = sum(a * b for a, b in zip(Bc[i], star[j])) / sum(b * b for b in star[j])
+            ok_size &= abs(mu) <= Fraction(1, 2)
+            v = [a - mu * b for a, b in zip(v, star[j])]
+        star.append(v)
+    norms = [sum(a * a for a in v) for v in star]
+    ok_ex = all(norms[j] <= factor * norms[j + 1] for j in range(d - 1))
+    return ok_size, ok_ex
+
+
+# ---------------------------------------------------------------------------
 # Definition of the Graver basis (§1), by enumeration, for tiny instances
 
 

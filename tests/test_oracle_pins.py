@@ -414,3 +414,80 @@ def test_inequality_extension_slack_bounds():
     assert l2[-1] == 0 and u2[-1] == 2 * 3 - 0 - 1
     with pytest.raises(ValueError):
         O.inequality_extension(A, [2], l, u, G, [7], B)
+
+
+# --- Lemma 3.1 / Theorem 3.2 (kernel basis of a general A) and Appendix A (LLL) ---
+
+def _same_lattice(B1, B2):
+    B1 = np.asarray(B1, np.int64)
+    B2 = np.asarray(B2, np.int64)
+    return all(O.lattice_contains(B1, B2[:, j]) for j in range(B2.shape[1])) and \
+        all(O.lattice_contains(B2, B1[:, j]) for j in range(B1.shape[1]))
+
+
+def _det_exact(M):
+    """Determinant of an integer matrix by fraction-free (Bareiss) elimination."""
+    M = [[int(v) for v in row] for row in M]
+    n, sign, prev = len(M), 1, 1
+    for k in range(n - 1):
+        if M[k][k] == 0:
+            sw = next((r for r in range(k + 1, n) if M[r][k] != 0), None)
+            if sw is None:
+                return 0
+            M[k], M[sw] = M[sw], M[k]
+            sign = -sign
+        for i in range(k + 1, n):
+            for j in range(k + 1, n):
+                M[i][j] = (M[i][j] * M[k][k] - M[i][k] * M[k][j]) // prev
+        prev = M[k][k]
+    return sign * M[n - 1][n - 1]
+
+
+def test_hnf_kernel_basis_is_a_kernel_basis():
+    """A K = (H | 0) with K unimodular (|det K| = 1); B = K's last d columns
+    spans the same lattice as the closed-form basis [I; -C] of A = [C | I]."""
+    assert _det_exact([[2, 1], [7, 4]]) == 1 and _det_exact([[1, 2, 3], [4, 5, 6], [7, 8, 10]]) == -3
+    for inst in (I.tiny_graver_case(), I.small_dense()):
+        A = inst.A.astype(np.int64)
+        B, K = O.hnf_kernel_basis(A)
+        AK = np.array(A.astype(object).dot(K), dtype=object)
+        m = A.shape[0]
+        assert all(v == 0 for v in AK[:, m:].ravel())
+        assert all(AK[i, j] == 0 for i in range(m) for j in range(i + 1, m))  # H lower triangular
+        assert abs(_det_exact(K.tolist())) == 1
+        assert _same_lattice(np.array(B, dtype=np.int64), inst.B)
+
+
+def test_hnf_kernel_basis_general_matrix_contains_every_kernel_element():
+    """A general full-row-rank A (not of the form [C | I]): every kernel
+    element in a box is an integer combination of the HNF basis."""
+    A = np.array([[2, 3, -1, 4], [1, -2, 5, 0]])
+    B, _ = O.hnf_kernel_basis(A)
+    B = np.array(B, dtype=np.int64)
+    assert B.shape == (4, 2) and np.all(A @ B == 0)
+    for g in O.kernel_box(A, 6):
+        assert O.lattice_contains(B, g)
+    with pytest.raises(ValueError):
+        O.hnf_kernel_basis(np.array([[1, 2, 3], [2, 4, 6]]))
+
+
+def test_lll_hand_example_and_conditions():
+    """(1,0), (7,1) size-reduces to (1,0), (0,1); every output satisfies
+    Appendix A's conditions and spans the input's lattice."""
+    out = np.array(O.lll_reduce(np.array([[1, 7], [0, 1]])), dtype=np.int64)
+    assert np.array_equal(out, np.array([[1, 0], [0, 1]]))
+    rng = np.random.default_rng(8)
+    for _ in range(5):
+        B = rng.integers(-20, 21, size=(6, 4))
+        if np.linalg.matrix_rank(B) < 4:
+            continue
+        R = O.lll_reduce(B)
+        assert O.lll_conditions(R) == (True, True)
+        assert _same_lattice(np.array(R, dtype=np.int64), B)
+    # the first reduced vector of a reduced basis is short: within
+    # 2^((d-1)/2) of the shortest kernel element of the tiny instance
+    inst = I.tiny_graver_case()
+    Bh, _ = O.hnf_kernel_basis(inst.A)
+    R = np.array(O.lll_reduce(Bh), dtype=np.int64)
+    shortest = min(np.linalg.norm(g) for g in O.kernel_box(inst.A, 2))
+    assert np.linalg.norm(R[:, 0]) <= 2 ** ((R.shape[1] - 1) / 2) * shortest + 1e-9
