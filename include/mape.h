@@ -345,6 +345,16 @@ typedef struct {
 size_t mape_initial_solutions_workspace_bytes(int32_t n, int32_t m, int32_t T);
 int mape_initial_solutions(const mape_init_args* args, void* stream);
 
+/* Lemma 3.1, Theorem 3.2 -- a basis of Ker_Z(A) for a general A [m x n]
+ * (full row rank, int32, row-major): unimodular integer column operations K
+ * bring A to (H | 0); the last d = n - m columns of K are written to
+ * B [n x d] (row-major).  reduce != 0 then applies the LLL reduction of
+ * Appendix A (size reduction, exchange while ||B*_{i-1}||^2 > 2 ||B*_i||^2)
+ * with double-precision Gram-Schmidt data.  A B = 0 is checked exactly.
+ * Errors: INVALID_ARG (also: A not of full row rank), SHAPE (an intermediate
+ * entry beyond 2^62 or a basis entry beyond int32), NUMERIC.  Host-only. */
+int mape_kernel_basis(int32_t m, int32_t n, const int32_t* A, int32_t reduce, int32_t* B);
+
 /* §3.4, Corollary 3.3 -- linear inequalities G x >= h (G [m2 x n], h [m2]):
  * writes the equality form of the instance with slack s = G x - h >= 0,
  *   A2 [(m+m2) x (n+m2)] = [A 0; G -I],  b2 = (b, h),

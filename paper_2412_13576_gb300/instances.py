@@ -162,6 +162,26 @@ def uneven_single(n, density=0.1, seed=1003):
                          lo=-5, hi=5, q_k=3, q_density=0.3, lin_k=10, seed=seed * 100 + n)
 
 
+def general_instance(n=12, m=4, seed=1005):
+    """A general A (not of the form [C | I]): entries uniform in [-2, 2],
+    drawn until it has full row rank; box [-3, 3]; Q sym [-3,3] at 0.3,
+    c in [-10,10].  B is left empty: a kernel basis of A is the caller's to
+    compute (Lemma 3.1)."""
+    rng = np.random.default_rng(seed)
+    while True:
+        A = rng.integers(-2, 3, size=(m, n))
+        if np.linalg.matrix_rank(A) == m:
+            break
+    l, u = np.full(n, -3, dtype=np.int64), np.full(n, 3, dtype=np.int64)
+    xbar = rng.integers(l, u + 1)
+    Q = _sym_matrix(rng, n, 3, 0.3)
+    c = rng.integers(-10, 11, size=n)
+    return Instance(name=f"general_n{n}_m{m}", n=n, m=m, A=A.astype(np.int32),
+                    B=np.zeros((n, n - m), np.int32), b=(A @ xbar).astype(np.int64),
+                    l=l.astype(np.int32), u=u.astype(np.int32), Q=Q.astype(np.int32),
+                    c=c.astype(np.int32), w=None, xbar=xbar.astype(np.int32))
+
+
 def tiny_graver_case(seed=7):
     """6 variables, 2 rows: A = [C | I_2] with C 2x4 in {-1,0,1}; box [-1,2],
     so that bound consistency (C4) admits exactly the entries |g_i| <= 3."""

@@ -159,6 +159,7 @@ _SIGS = {
     "mape_get_solutions": (C.c_int, [P_, P_, P_, I32]),
     "mape_destroy": (None, [P_]),
     "mape_inequality_extension": (C.c_int, [I32, I32, I32, P_, P_, P_, P_, P_, P_, P_, P_, P_, P_, P_, P_]),
+    "mape_kernel_basis": (C.c_int, [I32, I32, P_, I32, P_]),
     "mape_find_initial_solutions": (C.c_int, [P_, I32, P_, I32, I32, P_, I32, C.POINTER(I32)]),
     "mape_request_bytes": (C.c_size_t, [I32, I32, I32, I32, C.POINTER(Config)]),
     "mape_server_create": (C.c_int, [C.POINTER(ServerConfig), C.POINTER(P_)]),
@@ -660,3 +661,13 @@ def inequality_extension(inst, G, h):
     xbar2 = np.concatenate([inst.xbar, (G.astype(np.int64) @ inst.xbar - h)]).astype(np.int32)
     return dataclasses.replace(inst, name=inst.name + f"_ineq{m2}", n=n + m2, m=m + m2, A=A2, b=b2, l=l2, u=u2,
                                B=B2, Q=Q2, c=c2, w=w2, xbar=xbar2)
+
+
+def kernel_basis(A, reduce: bool = True) -> np.ndarray:
+    """A basis of Ker_Z(A) for a general full-row-rank A (mape_kernel_basis):
+    [n x (n - m)] int32, LLL-reduced unless reduce=False."""
+    A = _np(np.atleast_2d(A), np.int32)
+    m, n = A.shape
+    B = np.empty((n, n - m), np.int32)
+    _check(lib().mape_kernel_basis(m, n, _host(A), int(reduce), _host(B)), "mape_kernel_basis")
+    return B

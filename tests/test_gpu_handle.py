@@ -139,3 +139,25 @@ def test_handle_with_linear_inequalities(M):
     assert np.all(G @ xs >= h)
     assert np.array_equal(inst.A.astype(np.int64) @ xs, inst.b)
     assert fx <= O.f_value(inst.Q, inst.c, None, inst.xbar)
+
+
+def test_handle_on_general_A_with_computed_basis(M):
+    """A general A (not [C | I]) with the LLL-reduced kernel basis from
+    mape_kernel_basis (Lemma 3.1, Appendix A): the extracted directions pass
+    C1, C4 and minimality, and augmentation equals the oracle's Algorithm 1."""
+    import dataclasses
+    inst = I.general_instance(n=16, m=5, seed=11)
+    inst = dataclasses.replace(inst, B=M.kernel_basis(inst.A))
+    assert np.abs(inst.B).max() <= 256  # exact in BF16
+    cfg = M.default_config(T=300, precision=1)
+    with M.Instance.from_generated(inst, cfg) as h:
+        h.extract_directions(512, Z0=I.normal_starts(inst, 512, seed=3).Z0)
+        h.wait(300)
+        D = h.directions()
+        check_direction_set(inst, D)
+        assert np.all(O.minimal_elements(D))
+        h.augment(inst.xbar[None, :])
+        h.wait(300)
+        x, fx = h.solution()
+    xo, fo, _ = O.augment(inst.A, inst.b, inst.l, inst.u, inst.Q, inst.c, None, D, inst.xbar)
+    assert fx == fo and np.array_equal(x, xo)

@@ -167,3 +167,29 @@ def test_inequality_extension_matches_oracle(lib):
     with pytest.raises(mape.MapeError) as err:
         mape.inequality_extension(inst, np.ones((1, inst.n), np.int32), [10 ** 6])
     assert err.value.code == -4
+
+
+def test_kernel_basis_matches_oracle(lib):
+    """mape_kernel_basis (host-only): the HNF basis equals the oracle's exactly,
+    the LLL-reduced one equals the oracle's exact-rational LLL on these
+    matrices and satisfies Appendix A's conditions; A B = 0; a rank-deficient
+    A is refused."""
+    import numpy as np
+    from oracle import mape_oracle as O
+    from paper_2412_13576_gb300 import instances as I
+    from paper_2412_13576_gb300 import mape
+    for A in (np.array([[2, 3, -1, 4], [1, -2, 5, 0]]), I.tiny_graver_case().A, I.small_dense().A,
+              I.general_instance().A, I.general_instance(n=20, m=6, seed=3).A):
+        Bo, _ = O.hnf_kernel_basis(A)
+        if max(abs(int(v)) for v in Bo.ravel()) <= 2 ** 31 - 1:
+            assert np.array_equal(mape.kernel_basis(A, reduce=False), np.array(Bo, dtype=np.int64))
+        else:  # the unreduced basis does not fit the int32 output
+            with pytest.raises(mape.MapeError):
+                mape.kernel_basis(A, reduce=False)
+        B = mape.kernel_basis(A, reduce=True)
+        assert np.all(A.astype(np.int64) @ B == 0)
+        assert np.array_equal(B, np.array(O.lll_reduce(Bo), dtype=np.int64))
+        assert O.lll_conditions(B) == (True, True)
+    with pytest.raises(mape.MapeError) as err:
+        mape.kernel_basis(np.array([[1, 2, 3], [2, 4, 6]]))
+    assert err.value.code == -1
