@@ -46,7 +46,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["bf16", "bf16x1", "fp32"], default="bf16")
+    ap.add_argument("--precision", choices=["bf16", "bf16x1", "fp32", "sparse"], default="bf16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--cpu-sample", type=int, nargs=2, metavar=("P", "T"), help=argparse.SUPPRESS)
@@ -202,7 +202,7 @@ def cpu_baseline_obj(r):
 
 # ---------------------------------------------------------------- our arm
 
-PREC = {"bf16": 1, "bf16x1": 2, "fp32": 0}
+PREC = {"bf16": 1, "bf16x1": 2, "fp32": 0, "sparse": 3}
 
 
 def run_ours(args):
@@ -294,7 +294,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"bf16": "bf16", "bf16x1": "bf16", "fp32": "f32"}[args.precision],
+            "dtype": {"bf16": "bf16", "bf16x1": "bf16", "fp32": "f32", "sparse": "f32"}[args.precision],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "P": P_FULL, "T": T_FULL, "n": N_FULL, "m": M_FULL,
                        "precision": args.precision, "l2": "flushed (256 MiB write) before each timed step",
@@ -398,7 +398,7 @@ def streamed_case(args):
     name, P, T = args.streamed_case[0], int(args.streamed_case[1]), int(args.streamed_case[2])
     inst = {"large": I.large_quartic, "medium": I.medium_sparse,
             "uneven1000": lambda: I.uneven_single(1000, density=0.05)}[name]()
-    prec = PREC[args.precision] | mape.PREC_STREAMED
+    prec = PREC[args.precision] | (mape.PREC_STREAMED if args.precision in ("bf16", "bf16x1") else 0)
     G0 = I.uniform_samples(inst, P, seed=2004).G0
     stream = torch.cuda.Stream()
     times, counts = time_extract_kernel(mape, inst, G0, P, T, prec, stream, reps=2)

@@ -67,6 +67,10 @@ extern "C" {
                              accurate to about FP32                             */
 #define MAPE_PREC_BF16X1 2 /* as MAPE_PREC_BF16 with z as one BF16 term (hi):
                              half the forward MMAs, 8-bit z in B z            */
+#define MAPE_PREC_SPARSE 3 /* FP32 on CUDA cores for an identity-topped B =
+                             [I ; B'] with sparse B' (compressed rows and
+                             columns): one block per start with its z, m, v
+                             in shared memory for all T steps             */
 /* The BF16 precisions run one of two tensor-core implementations, with the
  * same arithmetic per step:
  *   resident: one persistent fused kernel for all T steps, B and the tile's
@@ -183,9 +187,11 @@ typedef struct {
   size_t workspace_bytes;
 } mape_extract_args;
 /* Errors: INVALID_ARG, SHAPE (n or d above 4096 on the BF16 paths; n above
- * 49152 on the FP32 path), CAPACITY (workspace), CUDA.  Asynchronous, except
- * that the BF16 paths synchronise `stream` once to inspect B (identity top,
- * exactness) before the steps are queued. */
+ * 49152 on the FP32 path; on the sparse path a B without identity top or a
+ * start's state beyond shared memory), NUMERIC (sparse path: an entry of B'
+ * beyond 2^23), CAPACITY (workspace), CUDA.  Asynchronous, except that the
+ * BF16 and sparse paths synchronise `stream` once to inspect B (identity
+ * top, exactness, sparsity) before the steps are queued. */
 size_t mape_extract_workspace_bytes(int32_t n, int32_t d, int32_t P, int32_t precision);
 int mape_extract(const mape_extract_args* args, void* stream);
 

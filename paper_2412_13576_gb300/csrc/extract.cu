@@ -52,7 +52,7 @@ extern "C" void mape_default_config(mape_config* cfg) {
 namespace {
 bool valid_precision(int32_t precision) {
   const int32_t base = precision & MAPE_PREC_MASK, extra = precision & ~MAPE_PREC_MASK;
-  if (base == MAPE_PREC_FP32) return extra == 0;
+  if (base == MAPE_PREC_FP32 || base == MAPE_PREC_SPARSE) return extra == 0;
   return (base == MAPE_PREC_BF16 || base == MAPE_PREC_BF16X1) && (extra & ~MAPE_PREC_STREAMED) == 0;
 }
 }  // namespace
@@ -61,6 +61,7 @@ extern "C" size_t mape_extract_workspace_bytes(int32_t n, int32_t d, int32_t P, 
   if (n <= 0 || d <= 0 || P < 0 || !valid_precision(precision)) return 0;
   const int32_t base = precision & MAPE_PREC_MASK;
   if (base == MAPE_PREC_FP32) return mape_detail::extract_fp32_workspace(n, d, P);
+  if (base == MAPE_PREC_SPARSE) return mape_detail::extract_sparse_workspace(n, d, P);
   // the streamed path also serves a general B of a shape whose resident tile
   // fits only when B is identity-topped, so its workspace is always included
   size_t w = mape_detail::extract_stream_workspace(n, d, P);
@@ -83,6 +84,11 @@ extern "C" int mape_extract(const mape_extract_args* a, void* stream) {
   if (a->P == 0 || a->T == 0) return MAPE_OK;
   cudaStream_t st = mape_detail::as_stream(stream);
   const int32_t base = a->precision & MAPE_PREC_MASK;
+  if (base == MAPE_PREC_SPARSE) {
+    if (!mape_detail::extract_sparse_supported(a->n, a->d)) return MAPE_ERR_SHAPE;
+    if (a->workspace_bytes < mape_detail::extract_sparse_workspace(a->n, a->d, a->P)) return MAPE_ERR_CAPACITY;
+    return mape_detail::extract_sparse(a, st);
+  }
   if (base != MAPE_PREC_FP32) {
     if (!mape_detail::extract_stream_supported(a->n, a->d)) return MAPE_ERR_SHAPE;
     if (a->workspace_bytes < mape_extract_workspace_bytes(a->n, a->d, a->P, a->precision)) return MAPE_ERR_CAPACITY;
@@ -108,7 +114,8 @@ int check_item(const mape_extract_args* a) {
   if (a->ldc < a->n || a->ldc % 16 != 0 || a->cand_cap < 0 || (a->cand_cap > 0 && !a->cand))
     return MAPE_ERR_INVALID_ARG;
   const int32_t base = a->precision & MAPE_PREC_MASK;
-  if (!valid_precision(a->precision) || base == MAPE_PREC_FP32) return MAPE_ERR_INVALID_ARG;
+  if (!valid_precision(a->precision) || base == MAPE_PREC_FP32 || base == MAPE_PREC_SPARSE)
+    return MAPE_ERR_INVALID_ARG;
   if (!mape_detail::extract_stream_supported(a->n, a->d)) return MAPE_ERR_SHAPE;
   if (a->workspace_bytes < mape_extract_workspace_bytes(a->n, a->d, a->P, a->precision)) return MAPE_ERR_CAPACITY;
   return MAPE_OK;

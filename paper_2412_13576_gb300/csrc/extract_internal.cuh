@@ -25,6 +25,10 @@ int extract_tc_batch_prepare(const mape_extract_args* const* items, const bool* 
 int extract_tc_batch_enqueue(const TcBatch* plan, cudaStream_t st);
 void extract_tc_batch_free(TcBatch* plan);
 
+bool extract_sparse_supported(int32_t n, int32_t d);
+size_t extract_sparse_workspace(int32_t n, int32_t d, int32_t P);
+int extract_sparse(const mape_extract_args* a, cudaStream_t st);
+
 bool extract_stream_supported(int32_t n, int32_t d);
 size_t extract_stream_workspace(int32_t n, int32_t d, int32_t P);
 int extract_stream(const mape_extract_args* a, cudaStream_t st);

@@ -23,6 +23,7 @@ ERR = {
 PREC_FP32 = 0
 PREC_BF16 = 1
 PREC_BF16X1 = 2
+PREC_SPARSE = 3
 PREC_STREAMED = 0x100   # OR into a BF16 precision: force the streamed tensor-core kernels
 PHASES = ["IDLE", "EXTRACTING", "FILTERING", "AUGMENTING", "DONE", "ERROR"]
 

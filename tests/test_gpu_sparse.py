@@ -1,0 +1,115 @@
+"""The sparse path of Algorithm 2 (identity-topped B with sparse B', one
+block per start with its state in shared memory for all T steps) against
+the FP64 oracle: per step the gradient within 1e-5 on the starts whose
+sign(Bz) FP32 determines, Phi and the Adam update within 1e-5, the
+collected rows exactly the oracle's collection of the GPU's own iterates; T
+steps in one launch bitwise equal to T launches of one step."""
+import numpy as np
+import pytest
+
+from oracle import mape_oracle as O
+from paper_2412_13576_gb300 import instances as I
+
+from .gpu_common import dev, rel_fro, rows_set, sign_stable_rows
+from .test_gpu_bf16 import _general_basis
+from .test_gpu_stages import _extract_steps
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+SPARSE = 3
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_13576_gb300 import mape
+    mape.lib(build_if_missing=True)
+    return mape
+
+
+def _z0(inst, P, seed, std):
+    if std is None:
+        return O.project_to_coordinates(inst.B, I.uniform_samples(inst, P, seed=seed).G0).astype(np.float32)
+    return I.normal_starts(inst, P, std=std, seed=seed).Z0
+
+
+@pytest.mark.parametrize("make,P,T,std", [(I.small_dense, 256, 30, 2.0), (I.medium_sparse, 300, 8, None),
+                                          (I.medium_sparse, 300, 8, 0.3), (I.tiny_graver_case, 130, 30, 2.0),
+                                          (lambda: I.uneven_single(500), 200, 5, 0.3),
+                                          (I.large_quartic, 64, 3, 0.3)])
+def test_sparse_per_step(M, make, P, T, std):
+    inst = make()
+    Z0 = _z0(inst, P, 2005, std)
+    states, grads, phis, cand = _extract_steps(M, inst, Z0, T, SPARSE, M.round16(inst.n), cap=P * (T + 1) + 16)
+    expect = set()
+    for t, ((z, m, v), (z1, m1, v1)) in enumerate(states):
+        go = O.phi_grad(inst.B, z, 0.85, 1.0)
+        ok = sign_stable_rows(inst.B, z)
+        assert ok.mean() > 0.5
+        assert rel_fro(grads[t][ok], go[ok]) < TOL
+        assert rel_fro(phis[t][ok], O.phi(inst.B, z, 0.85, 1.0)[ok]) < TOL
+        zo, mo, vo = O.adam_update(z.astype(np.float64), m, v, grads[t].astype(np.float64), t + 1, 0.003)
+        assert rel_fro(z1, zo) < TOL and rel_fro(m1, mo) < TOL and rel_fro(v1, vo) < TOL
+        expect |= O.collect(inst.A, inst.B, inst.l, inst.u, z1)
+    assert rows_set(cand, inst.n) == expect
+
+
+def test_sparse_one_launch_equals_single_steps(M):
+    import torch
+    inst = I.medium_sparse()
+    Z0 = _z0(inst, 500, 7, 0.3)
+    ldc = M.round16(inst.n)
+    B, span = dev(inst.B), dev((inst.u - inst.l).astype(np.int32))
+    T = 20
+    out = []
+    for single in (False, True):
+        cfg = M.default_config(precision=SPARSE, period=2)
+        Z = dev(Z0)
+        Mm, V = torch.zeros_like(Z), torch.zeros_like(Z)
+        cand = torch.zeros((500 * (T + 1), ldc), dtype=torch.int8, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+        if single:
+            for t in range(T):
+                M.extract(B, span, Z, Mm, V, t0=t, T=1, cfg=cfg, cand=cand, cand_count=cnt, flags=flags, ldc=ldc)
+        else:
+            M.extract(B, span, Z, Mm, V, t0=0, T=T, cfg=cfg, cand=cand, cand_count=cnt, flags=flags, ldc=ldc)
+        torch.cuda.synchronize()
+        assert int(flags.item()) == 0
+        out.append((Z.cpu().numpy(), Mm.cpu().numpy(), V.cpu().numpy(),
+                    rows_set(cand[: int(cnt.item())].cpu().numpy(), inst.n)))
+    (z1, m1, v1, s1), (z2, m2, v2, s2) = out
+    assert np.array_equal(z1, z2) and np.array_equal(m1, m2) and np.array_equal(v1, v2)
+    assert s1 == s2 and len(s1) > 0
+
+
+def test_sparse_refuses_general_basis(M):
+    import torch
+    inst = _general_basis(I.small_dense)()
+    Z = dev(_z0(inst, 64, 1, 2.0))
+    cfg = M.default_config(precision=SPARSE)
+    with pytest.raises(M.MapeError) as e:
+        M.extract(dev(inst.B), dev((inst.u - inst.l).astype(np.int32)), Z, torch.zeros_like(Z), torch.zeros_like(Z),
+                  t0=0, T=2, cfg=cfg, cand=torch.zeros((64, 32), dtype=torch.int8, device="cuda"),
+                  cand_count=torch.zeros(1, dtype=torch.int64, device="cuda"),
+                  flags=torch.zeros(1, dtype=torch.int32, device="cuda"), ldc=32)
+    assert e.value.code == -2
+
+
+def test_sparse_handle_end_to_end(M):
+    from .test_gpu_handle import check_direction_set
+    inst = I.medium_sparse()
+    cfg = M.default_config(T=300, precision=SPARSE)
+    with M.Instance.from_generated(inst, cfg) as h:
+        h.extract_directions(2048, Z0=_z0(inst, 2048, 11, 0.3))
+        h.wait(300)
+        D = h.directions()
+        check_direction_set(inst, D)
+        h.augment(inst.xbar[None, :])
+        h.wait(300)
+        x, fx = h.solution()
+    assert fx <= O.f_value(inst.Q, inst.c, None, inst.xbar)
+    assert np.array_equal(inst.A.astype(np.int64) @ x, inst.b)
