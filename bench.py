@@ -60,6 +60,8 @@ def parse_args(argv=None):
     ap.add_argument("--batch", type=int, default=64, metavar="N",
                     help="instances in the batched-extraction measurement (n log-uniform in [50, 1000], m = n/5, "
                          "P in {1024, 4096, 16384}, T = 1000); 0 skips it")
+    ap.add_argument("--autotune", action="store_true",
+                    help="with --streamed-case: let the library choose the implementation and tile widths")
     ap.add_argument("--kernel-case", type=int, nargs=2, metavar=("P", "T"),
                     help="time the fused extraction kernel alone on P starts of the workload for T steps "
                          "(two launches; a small case for profilers) and exit")
@@ -398,7 +400,8 @@ def streamed_case(args):
     name, P, T = args.streamed_case[0], int(args.streamed_case[1]), int(args.streamed_case[2])
     inst = {"large": I.large_quartic, "medium": I.medium_sparse,
             "uneven1000": lambda: I.uneven_single(1000, density=0.05)}[name]()
-    prec = PREC[args.precision] | (mape.PREC_STREAMED if args.precision in ("bf16", "bf16x1") else 0)
+    bf = args.precision in ("bf16", "bf16x1")
+    prec = PREC[args.precision] | (0 if not bf else (mape.PREC_AUTOTUNE if args.autotune else mape.PREC_STREAMED))
     G0 = I.uniform_samples(inst, P, seed=2004).G0
     stream = torch.cuda.Stream()
     times, counts = time_extract_kernel(mape, inst, G0, P, T, prec, stream, reps=2)
@@ -411,7 +414,9 @@ def streamed_case(args):
                               "precision": args.precision, "ms_per_call": times, "ms_per_step": ms / T,
                               "candidates": counts, "algorithmic_bytes_per_call": algo, "achieved_gbs": gbs,
                               "hbm_peak_gbs": peaks["hbm_gbs"], "frac_of_hbm": gbs / peaks["hbm_gbs"],
-                              "peak_source": src}}
+                              "peak_source": src,
+                              "autotune": mape.autotune_info(inst.n, inst.d, P, PREC[args.precision])
+                              if args.autotune else None}}
 
 
 SERVE_RATE = 200.0    # requests per second (Poisson)

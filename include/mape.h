@@ -82,6 +82,15 @@ extern "C" {
  * The resident kernel is chosen when it fits; OR-ing MAPE_PREC_STREAMED into
  * the precision forces the streamed one. */
 #define MAPE_PREC_STREAMED 0x100
+/* OR-ing MAPE_PREC_AUTOTUNE into a BF16 precision lets the library choose the
+ * implementation and the streamed kernels' N-block widths (64, 128 or 256
+ * rows of B per forward CTA, coordinates per gradient CTA) for this shape: the
+ * first call for a (n, d, P rounded up to a power of two, precision) times a
+ * few steps of every candidate on scratch copies of the call's state (inside
+ * the workspace, which is larger with this bit) and keeps the fastest for the
+ * process; later calls reuse it.  Results are those of the chosen
+ * implementation; mape_autotune_lookup reports the choice and the probes. */
+#define MAPE_PREC_AUTOTUNE 0x200
 #define MAPE_PREC_MASK 0xff
 
 /* ---- hyper-parameters (§3.2, §4: lambda1 = 0.85, lambda2 = 1, lr = 0.003) - */
@@ -211,6 +220,19 @@ int mape_extract(const mape_extract_args* args, void* stream);
 size_t mape_extract_batch_workspace_bytes(const mape_extract_args* items, int32_t count);
 int mape_extract_batch(const mape_extract_args* items, int32_t count,
                        void* workspace, size_t workspace_bytes, void* stream);
+
+typedef struct {
+  int32_t path;             /* chosen: 0 resident fused kernel, 1 streamed    */
+  int32_t wF, wG;           /* streamed: forward / gradient N-block widths    */
+  int32_t candidates;       /* candidates that ran                            */
+  int32_t probe_steps;      /* Adam steps each candidate was timed on         */
+  int32_t cand_path[16], cand_wF[16], cand_wG[16];
+  float probe_ms[16];       /* their times                                    */
+} mape_tune_info;
+/* The autotuned choice for a shape, or STATE if none was made yet. */
+int mape_autotune_lookup(int32_t n, int32_t d, int32_t P, int32_t precision, mape_tune_info* out);
+/* Forgets every autotuned choice of the process. */
+void mape_autotune_clear(void);
 
 /* a10 -- set union of Algorithm 2: removes repeated rows of `cand` (count
  * rows, pitch ldc, n meaningful bytes) with a device hash table, and writes

@@ -3,6 +3,7 @@
 #include "common.cuh"
 #include "extract_internal.cuh"
 
+#include <map>
 #include <memory>
 
 #include <cstdio>
@@ -53,12 +54,141 @@ namespace {
 bool valid_precision(int32_t precision) {
   const int32_t base = precision & MAPE_PREC_MASK, extra = precision & ~MAPE_PREC_MASK;
   if (base == MAPE_PREC_FP32 || base == MAPE_PREC_SPARSE) return extra == 0;
-  return (base == MAPE_PREC_BF16 || base == MAPE_PREC_BF16X1) && (extra & ~MAPE_PREC_STREAMED) == 0;
+  if ((extra & MAPE_PREC_STREAMED) && (extra & MAPE_PREC_AUTOTUNE)) return false;
+  return (base == MAPE_PREC_BF16 || base == MAPE_PREC_BF16X1) &&
+         (extra & ~(MAPE_PREC_STREAMED | MAPE_PREC_AUTOTUNE)) == 0;
 }
+
+// ---- autotuning of the BF16 implementation and the streamed tile widths ----
+
+struct TuneKey {
+  int32_t n, d, pb, base;
+  bool operator<(const TuneKey& o) const {
+    if (n != o.n) return n < o.n;
+    if (d != o.d) return d < o.d;
+    if (pb != o.pb) return pb < o.pb;
+    return base < o.base;
+  }
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, mape_tune_info> g_tuned;
+
+int32_t p_bucket(int32_t P) {
+  int32_t b = 1;
+  while (b < P && b < (1 << 30)) b <<= 1;
+  return b;
+}
+
+constexpr int kProbeSteps = 6;
+
+// scratch the probes need beyond the implementation's own workspace
+size_t tune_scratch_bytes(int32_t n, int32_t d, int32_t P) {
+  mape_detail::Sizer s;
+  for (int k = 0; k < 3; ++k) s.take<float>((size_t)P * d);
+  s.take<int8_t>((size_t)(P + 16) * mape_detail::align_up((size_t)n, 16));
+  s.take<unsigned long long>(1);
+  s.take<int32_t>(1);
+  return s.bytes();
+}
+
+int run_choice(const mape_extract_args* a, cudaStream_t st, const mape_tune_info& c) {
+  if (c.path == 0) return mape_detail::extract_tc(a, st);
+  return mape_detail::extract_stream_widths(a, st, c.wF, c.wG);
+}
+
 }  // namespace
+
+// Times kProbeSteps steps of every candidate from the call's state on scratch
+// copies (the call's own arrays are not touched) and caches the fastest.
+static int autotune(const mape_extract_args* a, cudaStream_t st, size_t impl_bytes, mape_tune_info& out) {
+  using namespace mape_detail;
+  const int n = a->n, d = a->d, P = a->P;
+  const size_t ldc = align_up((size_t)n, 16);
+  Carver cv(static_cast<char*>(a->workspace) + impl_bytes, a->workspace_bytes - impl_bytes);
+  float* Zs = cv.take<float>((size_t)P * d);
+  float* Ms = cv.take<float>((size_t)P * d);
+  float* Vs = cv.take<float>((size_t)P * d);
+  int8_t* cs = cv.take<int8_t>((size_t)(P + 16) * ldc);
+  unsigned long long* cnt = cv.take<unsigned long long>(1);
+  int32_t* fl = cv.take<int32_t>(1);
+  if (!cv.ok) return MAPE_ERR_CAPACITY;
+  std::vector<mape_tune_info> cands;
+  mape_tune_info c{};
+  if (extract_tc_supported(n, d, a->precision & MAPE_PREC_MASK)) {
+    c.path = 0;
+    cands.push_back(c);
+  }
+  for (int wf : {64, 128, 256})
+    for (int wg : {64, 128, 256}) {
+      c.path = 1; c.wF = wf; c.wG = wg;
+      cands.push_back(c);
+    }
+  cudaEvent_t e0, e1;
+  MAPE_CUDA_TRY(cudaEventCreate(&e0));
+  MAPE_CUDA_TRY(cudaEventCreate(&e1));
+  mape_extract_args b = *a;
+  b.precision = a->precision & MAPE_PREC_MASK;
+  b.Z = Zs; b.M = Ms; b.V = Vs;
+  b.cand = cs; b.ldc = (int32_t)ldc; b.cand_cap = P + 16; b.cand_count = cnt; b.flags = fl;
+  b.dbg_phi = nullptr; b.dbg_grad = nullptr;
+  b.T = a->T < kProbeSteps ? a->T : kProbeSteps;
+  b.workspace_bytes = impl_bytes;
+  float best = 1e30f;
+  int nc = 0;
+  out = mape_tune_info{};
+  for (const auto& k : cands) {
+    int rc = MAPE_OK;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && rc == MAPE_OK; ++rep) {  // the first run loads the kernels
+      MAPE_CUDA_TRY(cudaMemcpyAsync(Zs, a->Z, sizeof(float) * (size_t)P * d, cudaMemcpyDeviceToDevice, st));
+      MAPE_CUDA_TRY(cudaMemcpyAsync(Ms, a->M, sizeof(float) * (size_t)P * d, cudaMemcpyDeviceToDevice, st));
+      MAPE_CUDA_TRY(cudaMemcpyAsync(Vs, a->V, sizeof(float) * (size_t)P * d, cudaMemcpyDeviceToDevice, st));
+      MAPE_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+      MAPE_CUDA_TRY(cudaMemsetAsync(fl, 0, sizeof(int32_t), st));
+      MAPE_CUDA_TRY(cudaEventRecord(e0, st));
+      rc = run_choice(&b, st, k);
+      MAPE_CUDA_TRY(cudaEventRecord(e1, st));
+      MAPE_CUDA_TRY(cudaEventSynchronize(e1));
+      MAPE_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    }
+    if (rc != MAPE_OK) continue;  // e.g. a general B the resident tile cannot take
+    if (nc < 16) {
+      out.cand_path[nc] = k.path; out.cand_wF[nc] = k.wF; out.cand_wG[nc] = k.wG; out.probe_ms[nc] = ms;
+      ++nc;
+    }
+    if (ms < best) {
+      best = ms;
+      out.path = k.path; out.wF = k.wF; out.wG = k.wG;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  out.candidates = nc;
+  out.probe_steps = b.T;
+  return nc > 0 ? MAPE_OK : MAPE_ERR_SHAPE;
+}
+
+extern "C" int mape_autotune_lookup(int32_t n, int32_t d, int32_t P, int32_t precision, mape_tune_info* out) {
+  if (!out) return MAPE_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(TuneKey{n, d, p_bucket(P), precision & MAPE_PREC_MASK});
+  if (it == g_tuned.end()) return MAPE_ERR_STATE;
+  *out = it->second;
+  return MAPE_OK;
+}
+
+extern "C" void mape_autotune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned.clear();
+}
 
 extern "C" size_t mape_extract_workspace_bytes(int32_t n, int32_t d, int32_t P, int32_t precision) {
   if (n <= 0 || d <= 0 || P < 0 || !valid_precision(precision)) return 0;
+  if (precision & MAPE_PREC_AUTOTUNE) {
+    const size_t w = mape_extract_workspace_bytes(n, d, P, precision & ~MAPE_PREC_AUTOTUNE);
+    return w ? mape_detail::align_up(w, 256) + tune_scratch_bytes(n, d, P) : 0;
+  }
   const int32_t base = precision & MAPE_PREC_MASK;
   if (base == MAPE_PREC_FP32) return mape_detail::extract_fp32_workspace(n, d, P);
   if (base == MAPE_PREC_SPARSE) return mape_detail::extract_sparse_workspace(n, d, P);
@@ -94,6 +224,25 @@ extern "C" int mape_extract(const mape_extract_args* a, void* stream) {
     if (a->workspace_bytes < mape_extract_workspace_bytes(a->n, a->d, a->P, a->precision)) return MAPE_ERR_CAPACITY;
     mape_extract_args b = *a;
     b.precision = base;
+    if (a->precision & MAPE_PREC_AUTOTUNE) {
+      const size_t impl = mape_detail::align_up(mape_extract_workspace_bytes(a->n, a->d, a->P, base), 256);
+      const TuneKey key{a->n, a->d, p_bucket(a->P), base};
+      mape_tune_info choice{};
+      bool have = false;
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) { choice = it->second; have = true; }
+      }
+      if (!have) {
+        int rc = autotune(a, st, impl, choice);
+        if (rc != MAPE_OK) return rc;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = choice;
+      }
+      b.workspace_bytes = impl;
+      return run_choice(&b, st, choice);
+    }
     if (!(a->precision & MAPE_PREC_STREAMED) && mape_detail::extract_tc_supported(a->n, a->d, base)) {
       const int rc = mape_detail::extract_tc(&b, st);
       if (rc != MAPE_ERR_SHAPE) return rc;  // SHAPE: a general B that only the streamed path takes

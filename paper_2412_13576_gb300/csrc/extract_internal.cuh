@@ -32,6 +32,8 @@ int extract_sparse(const mape_extract_args* a, cudaStream_t st);
 bool extract_stream_supported(int32_t n, int32_t d);
 size_t extract_stream_workspace(int32_t n, int32_t d, int32_t P);
 int extract_stream(const mape_extract_args* a, cudaStream_t st);
+// the same with the forward and gradient N-block widths chosen (64..256, multiples of 64)
+int extract_stream_widths(const mape_extract_args* a, cudaStream_t st, int wF, int wG);
 
 // Batches of calls on the streamed kernels: three launches per step for all
 // calls of one basis kind.

@@ -40,12 +40,12 @@ using namespace mape_tc;
 constexpr int kTM = 128;       // starts per tile: the MMA M
 constexpr int kThreads = 256;  // 8 warps: two per TMEM lane quarter
 constexpr int kKC = 64;        // K chunk
-constexpr int kNB = 256;       // N block: the largest MMA N
+constexpr int kNB = 256;       // the widest N block: the largest MMA N
 constexpr int kChunkA = kTM * kKC * 2;        // one 128 x 64 BF16 operand chunk (16 KB)
-constexpr int kFStage = 3 * kChunkA + kNB * kKC * 2;  // hi, lo, round(z), Bm chunk
-constexpr int kFSmem = 2 * kFStage;
-constexpr int kGStage = kChunkA + kNB * kKC * 2;      // S chunk, Bm chunk
-constexpr int kGSmem = 2 * kGStage;
+// shared memory of the two-stage rings for N blocks of width w
+__host__ __device__ constexpr int fwd_stage(int w) { return 3 * kChunkA + w * kKC * 2; }  // hi, lo, round(z), Bm chunk
+__host__ __device__ constexpr int grad_stage(int w) { return kChunkA + w * kKC * 2; }    // S chunk, Bm chunk
+__host__ __device__ constexpr int tmem_cols(int c) { return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512; }
 constexpr int kNoNz = 0x7fffffff;
 constexpr uint32_t kChanged = 1, kUnexact = 2;
 
@@ -54,6 +54,7 @@ struct StParams {
   int r0;               // row of B held in row 0 of Bm (d for an identity top, else 0)
   int d64, R64;         // padded to the K chunk
   int tiles, nbF, nbG;  // tiles of 128 starts; N blocks over R64 and d64
+  int wF, wG;           // N block widths (multiples of 64, at most 256)
   int ldc, mapoff, lds; // candidate pitch; offset of the Bm rows in a staged row; staged pitch
   const uint8_t* BmF;   // forward B operand: [nbF][d64/64][N x 64] chunks (N = Bm rows)
   const uint8_t* BmG;   // gradient B operand: [nbG][R64/64][N x 64] chunks (N = coordinates)
@@ -93,8 +94,10 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tile = blk / p.nbF, rb = blk % p.nbF;
-  const int N = rb < p.nbF - 1 ? kNB : p.R64 - kNB * (p.nbF - 1);
-  const int row0 = rb * kNB;
+  const int N = rb < p.nbF - 1 ? p.wF : p.R64 - p.wF * (p.nbF - 1);
+  const int row0 = rb * p.wF;
+  const int fstage = fwd_stage(p.wF);
+  const uint32_t fcols = (uint32_t)tmem_cols(2 * p.wF);  // D1 at 0, D2 at wF
   const int nk = p.d64 / kKC;
   const int P2 = ptot(p);
   const uint32_t full0 = smem_u32(&bars[0]), done0 = smem_u32(&bars[2]);
@@ -113,7 +116,7 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
     mbar_init(done0, 1); mbar_init(done0 + 8, 1);
     s_abort = 0;
   }
-  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), 512);
+  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), fcols);
   mbar_init_fence();
   tc_fence_before();
   __syncthreads();
@@ -141,7 +144,7 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
 
   for (int c = 0; c < nk; ++c) {
     const int stg = c & 1;
-    uint8_t* Ahi = smem + stg * kFStage;
+    uint8_t* Ahi = smem + stg * fstage;
     uint8_t* Alo = Ahi + kChunkA;
     uint8_t* Ard = Alo + kChunkA;
     uint8_t* Bc = Ard + kChunkA;
@@ -151,7 +154,7 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
     }
     if (tid == 0) {
       mbar_arrive_expect_tx(full0 + 8 * stg, (uint32_t)N * kKC * 2);
-      bulk_g2s(smem_u32(Bc), p.BmF + ((size_t)rb * kNB * p.d64 + (size_t)c * N * kKC) * 2, (uint32_t)N * kKC * 2,
+      bulk_g2s(smem_u32(Bc), p.BmF + ((size_t)rb * p.wF * p.d64 + (size_t)c * N * kKC) * 2, (uint32_t)N * kKC * 2,
                full0 + 8 * stg);
       ++issued_copies;
     }
@@ -213,7 +216,7 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
             mma_bf16(tmem, make_desc(smem_u32(Ahi) + kk * 256, kChunkLbo, kChunkSbo), b, idesc, a0);
             if (p.nterms > 1) mma_bf16(tmem, make_desc(smem_u32(Alo) + kk * 256, kChunkLbo, kChunkSbo), b, idesc, 1u);
           }
-          if (collect) mma_bf16(tmem + 256, make_desc(smem_u32(Ard) + kk * 256, kChunkLbo, kChunkSbo), b, idesc, a0);
+          if (collect) mma_bf16(tmem + p.wF, make_desc(smem_u32(Ard) + kk * 256, kChunkLbo, kChunkSbo), b, idesc, a0);
         }
         mma_commit(done0 + 8 * stg);
         ++issued_commits;
@@ -259,7 +262,7 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
         *reinterpret_cast<uint4*>(Sp + chunk_off(r, kg % kKC + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
       }
       if (collect) {
-        tmem_ld16(tmem + lane_base + 256 + ch * 16, v);
+        tmem_ld16(tmem + lane_base + p.wF + ch * 16, v);
         tc_wait_ld();
         const int i0 = row0 + ch * 16;
         uint32_t pk[4] = {0, 0, 0, 0};
@@ -298,7 +301,7 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, 512);
+    tmem_dealloc(tmem, fcols);
   }
 }
 
@@ -355,8 +358,10 @@ __device__ __forceinline__ void stream_grad_body(const StParams& p, const int bl
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tile = blk / p.nbG, db = blk % p.nbG;
-  const int N = db < p.nbG - 1 ? kNB : p.d64 - kNB * (p.nbG - 1);
-  const int col0 = db * kNB;
+  const int N = db < p.nbG - 1 ? p.wG : p.d64 - p.wG * (p.nbG - 1);
+  const int col0 = db * p.wG;
+  const int gstage = grad_stage(p.wG);
+  const uint32_t gcols = (uint32_t)tmem_cols(p.wG);
   const int nk = p.R64 / kKC;
   const int P2 = ptot(p);
   const uint32_t full0 = smem_u32(&bars[0]), done0 = smem_u32(&bars[2]), accr = smem_u32(&bars[4]);
@@ -368,7 +373,7 @@ __device__ __forceinline__ void stream_grad_body(const StParams& p, const int bl
     mbar_init(accr, 1);
     s_abort = 0;
   }
-  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), 256);
+  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), gcols);
   mbar_init_fence();
   tc_fence_before();
   __syncthreads();
@@ -384,11 +389,11 @@ __device__ __forceinline__ void stream_grad_body(const StParams& p, const int bl
         break;
       }
       if (*(volatile int*)&s_abort) break;
-      uint8_t* A = smem + stg * kGStage;
+      uint8_t* A = smem + stg * gstage;
       uint8_t* Bc = A + kChunkA;
       mbar_arrive_expect_tx(full0 + 8 * stg, (uint32_t)(kChunkA + N * kKC * 2));
       bulk_g2s(smem_u32(A), p.S + ((size_t)tile * nk + c) * kChunkA, kChunkA, full0 + 8 * stg);
-      bulk_g2s(smem_u32(Bc), p.BmG + ((size_t)db * kNB * p.R64 + (size_t)c * N * kKC) * 2, (uint32_t)N * kKC * 2,
+      bulk_g2s(smem_u32(Bc), p.BmG + ((size_t)db * p.wG * p.R64 + (size_t)c * N * kKC) * 2, (uint32_t)N * kKC * 2,
                full0 + 8 * stg);
       ++copies;
     }
@@ -402,7 +407,7 @@ __device__ __forceinline__ void stream_grad_body(const StParams& p, const int bl
         break;
       }
       tc_fence_after();
-      const uint32_t A = smem_u32(smem + stg * kGStage), Bc = A + kChunkA;
+      const uint32_t A = smem_u32(smem + stg * gstage), Bc = A + kChunkA;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
         mma_bf16(tmem, make_desc(A + kk * 256, kChunkLbo, kChunkSbo), make_desc(Bc + kk * 256, kChunkLbo, kChunkSbo),
@@ -538,7 +543,7 @@ __device__ __forceinline__ void stream_grad_body(const StParams& p, const int bl
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, 256);
+    tmem_dealloc(tmem, gcols);
   }
 }
 
@@ -592,8 +597,8 @@ __global__ void __launch_bounds__(kThreads, 1) stream_grad_batch_kernel(const St
 // Bm in both operand layouts; flags |= 8 (and *bad = 1) if an entry is not
 // exact in BF16 (|B_ij| > 256)
 __global__ void pack_bm_kernel(const int32_t* __restrict__ B, int d, int R, int r0, int d64, int R64, int nbF,
-                               int nbG, uint8_t* __restrict__ BmF, uint8_t* __restrict__ BmG, int32_t* bad,
-                               int32_t* flags) {
+                               int nbG, int wF, int wG, uint8_t* __restrict__ BmF, uint8_t* __restrict__ BmG,
+                               int32_t* bad, int32_t* flags) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= (int64_t)R64 * d64) return;
   const int i = (int)(e / d64), j = (int)(e % d64);
@@ -605,15 +610,15 @@ __global__ void pack_bm_kernel(const int32_t* __restrict__ B, int d, int R, int 
   const __nv_bfloat16 hb = __float2bfloat16_rn((float)v);
   const uint16_t hv = *reinterpret_cast<const uint16_t*>(&hb);
   {
-    const int rb = i / kNB, rl = i % kNB;
-    const int Nr = rb < nbF - 1 ? kNB : R64 - kNB * (nbF - 1);
-    const size_t off = ((size_t)rb * kNB * d64 + (size_t)(j / kKC) * Nr * kKC) * 2 + chunk_off(rl, j % kKC);
+    const int rb = i / wF, rl = i % wF;
+    const int Nr = rb < nbF - 1 ? wF : R64 - wF * (nbF - 1);
+    const size_t off = ((size_t)rb * wF * d64 + (size_t)(j / kKC) * Nr * kKC) * 2 + chunk_off(rl, j % kKC);
     *reinterpret_cast<uint16_t*>(BmF + off) = hv;
   }
   {
-    const int gb = j / kNB, jl = j % kNB;
-    const int Nd = gb < nbG - 1 ? kNB : d64 - kNB * (nbG - 1);
-    const size_t off = ((size_t)gb * kNB * R64 + (size_t)(i / kKC) * Nd * kKC) * 2 + chunk_off(jl, i % kKC);
+    const int gb = j / wG, jl = j % wG;
+    const int Nd = gb < nbG - 1 ? wG : d64 - wG * (nbG - 1);
+    const size_t off = ((size_t)gb * wG * R64 + (size_t)(i / kKC) * Nd * kKC) * 2 + chunk_off(jl, i % kKC);
     *reinterpret_cast<uint16_t*>(BmG + off) = hv;
   }
 }
@@ -688,18 +693,20 @@ int r64(int x) { return (x + kKC - 1) / kKC * kKC; }
 int r16(int x) { return (x + 15) / 16 * 16; }
 
 struct StreamShape {
-  int R, r0, d64, R64, tiles, nbF, nbG, mapoff, lds;
+  int R, r0, d64, R64, tiles, nbF, nbG, wF, wG, mapoff, lds;
 };
 
-StreamShape stream_shape(int n, int d, int P, bool id) {
+StreamShape stream_shape(int n, int d, int P, bool id, int wF = kNB, int wG = kNB) {
   StreamShape s{};
   s.R = id ? n - d : n;
   s.r0 = id ? d : 0;
   s.d64 = r64(d);
   s.R64 = s.R > 0 ? r64(s.R) : kKC;
   s.tiles = (int)mape_detail::ceil_div(P, kTM);
-  s.nbF = (int)mape_detail::ceil_div(s.R64, kNB);
-  s.nbG = (int)mape_detail::ceil_div(s.d64, kNB);
+  s.wF = wF;
+  s.wG = wG;
+  s.nbF = (int)mape_detail::ceil_div(s.R64, wF);
+  s.nbG = (int)mape_detail::ceil_div(s.d64, wG);
   s.mapoff = id ? r16(d) : 0;
   s.lds = s.mapoff + s.R64;
   return s;
@@ -793,7 +800,7 @@ static int st_pack_b(const StCarved& c, const mape_extract_args* a, cudaStream_t
   const StreamShape& sh = c.sh;
   MAPE_CUDA_TRY(cudaMemsetAsync(c.hflags + 1, 0, sizeof(int32_t), st));
   launch(pack_bm_kernel, (unsigned)ceil_div((int64_t)sh.R64 * sh.d64, 256), 256, 0, st, a->B, a->d, sh.R, sh.r0,
-         sh.d64, sh.R64, sh.nbF, sh.nbG, c.BmF, c.BmG, c.hflags + 1, a->flags);
+         sh.d64, sh.R64, sh.nbF, sh.nbG, sh.wF, sh.wG, c.BmF, c.BmG, c.hflags + 1, a->flags);
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
 }
@@ -819,7 +826,7 @@ static int st_setup(const StCarved& c, const mape_extract_args* a, cudaStream_t 
   if (a->dbg_phi) MAPE_CUDA_TRY(cudaMemsetAsync(a->dbg_phi, 0, sizeof(float) * P, st));
   p = StParams{};
   p.n = n; p.d = d; p.P = P; p.R = sh.R; p.r0 = sh.r0; p.d64 = sh.d64; p.R64 = sh.R64;
-  p.tiles = sh.tiles; p.nbF = sh.nbF; p.nbG = sh.nbG;
+  p.tiles = sh.tiles; p.nbF = sh.nbF; p.nbG = sh.nbG; p.wF = sh.wF; p.wG = sh.wG;
   p.ldc = a->ldc; p.mapoff = sh.mapoff; p.lds = sh.lds;
   p.BmF = c.BmF; p.BmG = c.BmG; p.span = a->span; p.Zt = c.Zt; p.Mt = c.Mt; p.Vt = c.Vt; p.S = c.S;
   p.stage = c.stage; p.zkey = c.zkey; p.acc = c.acc; p.oob = c.oob; p.idw = c.idw; p.first = c.first;
@@ -844,16 +851,18 @@ static int st_unpack(const StCarved& c, const mape_extract_args* a, cudaStream_t
   return MAPE_OK;
 }
 
-// one CTA per SM for the forward pass (512 TMEM columns), at most two for
-// the gradient pass (256 columns each): every TMEM allocation fits
+// The forward pass's shared memory (at least 115 KB: three operand chunks
+// and a B chunk per stage) keeps it at one CTA per SM, so its TMEM (2 wF
+// columns, at most 512) always fits; the gradient pass holds wG columns per
+// CTA and its registers (about 116 per thread) keep it at two CTAs per SM.
 static int st_attributes(bool batch) {
   for (int id = 0; id < 2; ++id) {
     const void* f = batch ? (id ? (const void*)stream_fwd_batch_kernel<true> : (const void*)stream_fwd_batch_kernel<false>)
                           : (id ? (const void*)stream_fwd_kernel<true> : (const void*)stream_fwd_kernel<false>);
     const void* g = batch ? (id ? (const void*)stream_grad_batch_kernel<true> : (const void*)stream_grad_batch_kernel<false>)
                           : (id ? (const void*)stream_grad_kernel<true> : (const void*)stream_grad_kernel<false>);
-    MAPE_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmem));
-    MAPE_CUDA_TRY(cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem));
+    MAPE_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * fwd_stage(kNB)));
+    MAPE_CUDA_TRY(cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * grad_stage(kNB)));
   }
   return MAPE_OK;
 }
@@ -875,8 +884,9 @@ static void st_schedule(int t0, int T, int period, Fwd fwd, Coll coll, Grad grad
   }
 }
 
-int extract_stream(const mape_extract_args* a, cudaStream_t st) {
+int extract_stream_widths(const mape_extract_args* a, cudaStream_t st, int wF, int wG) {
   const int d = a->d, P = a->P;
+  if (wF < kKC || wF > kNB || wF % kKC || wG < kKC || wG > kNB || wG % kKC) return MAPE_ERR_INVALID_ARG;
   StCarved c;
   int rc = st_carve(a, false, c);
   if (rc != MAPE_OK) return rc;
@@ -887,7 +897,7 @@ int extract_stream(const mape_extract_args* a, cudaStream_t st) {
   MAPE_CUDA_TRY(cudaMemcpyAsync(&h_notid, c.hflags, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   MAPE_CUDA_TRY(cudaStreamSynchronize(st));
   const bool id = h_notid == 0;
-  c.sh = stream_shape(a->n, d, P, id);
+  c.sh = stream_shape(a->n, d, P, id, wF, wG);
   if ((rc = st_pack_b(c, a, st)) != MAPE_OK) return rc;
   int32_t h_bad = 0;
   MAPE_CUDA_TRY(cudaMemcpyAsync(&h_bad, c.hflags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -902,13 +912,16 @@ int extract_stream(const mape_extract_args* a, cudaStream_t st) {
   auto fwdk = id ? stream_fwd_kernel<true> : stream_fwd_kernel<false>;
   auto gradk = id ? stream_grad_kernel<true> : stream_grad_kernel<false>;
   auto collk = id ? stream_collect_kernel<true> : stream_collect_kernel<false>;
+  const int fsm = 2 * fwd_stage(sh.wF), gsm = 2 * grad_stage(sh.wG);
   st_schedule(
-      a->t0, a->T, a->period, [&](int s, int f, int col) { launch(fwdk, gF, kThreads, kFSmem, st, p, s, f, col); },
+      a->t0, a->T, a->period, [&](int s, int f, int col) { launch(fwdk, gF, kThreads, fsm, st, p, s, f, col); },
       [&](int s) { launch(collk, gC, 256, 0, st, p, s); },
-      [&](int s) { launch(gradk, gG, kThreads, kGSmem, st, p, s); });
+      [&](int s) { launch(gradk, gG, kThreads, gsm, st, p, s); });
   MAPE_LAUNCH_CHECK();
   return st_unpack(c, a, st);
 }
+
+int extract_stream(const mape_extract_args* a, cudaStream_t st) { return extract_stream_widths(a, st, kNB, kNB); }
 
 struct StBatch {
   struct Class {  // the calls of one basis kind (identity-topped or general)
@@ -1027,9 +1040,11 @@ int extract_stream_batch_enqueue(const StBatch* plan, cudaStream_t st) {
     auto collk = C.id ? stream_collect_batch_kernel<true> : stream_collect_batch_kernel<false>;
     st_schedule(
         plan->t0, plan->T, plan->period,
-        [&](int s, int f, int col) { launch(fwdk, (unsigned)C.nF, kThreads, kFSmem, st, C.table, C.wF, s, f, col); },
+        [&](int s, int f, int col) {
+          launch(fwdk, (unsigned)C.nF, kThreads, 2 * fwd_stage(kNB), st, C.table, C.wF, s, f, col);
+        },
         [&](int s) { launch(collk, (unsigned)C.nC, 256, 0, st, C.table, C.wC, s); },
-        [&](int s) { launch(gradk, (unsigned)C.nG, kThreads, kGSmem, st, C.table, C.wG, s); });
+        [&](int s) { launch(gradk, (unsigned)C.nG, kThreads, 2 * grad_stage(kNB), st, C.table, C.wG, s); });
     MAPE_LAUNCH_CHECK();
   }
   for (size_t i = 0; i < plan->items.size(); ++i) {

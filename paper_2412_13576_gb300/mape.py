@@ -25,6 +25,7 @@ PREC_BF16 = 1
 PREC_BF16X1 = 2
 PREC_SPARSE = 3
 PREC_STREAMED = 0x100   # OR into a BF16 precision: force the streamed tensor-core kernels
+PREC_AUTOTUNE = 0x200   # OR into a BF16 precision: choose the implementation and tile widths by timing
 PHASES = ["IDLE", "EXTRACTING", "FILTERING", "AUGMENTING", "DONE", "ERROR"]
 
 
@@ -73,6 +74,18 @@ class AugmentArgs(C.Structure):
                 ("pad1", I32), ("c", P_), ("w", P_), ("l", P_), ("u", P_), ("X", P_), ("fval", P_),
                 ("moves", P_), ("nmoves", P_), ("moves_cap", I32), ("pad2", I32),
                 ("max_iters", I64), ("workspace", P_), ("workspace_bytes", C.c_size_t)]
+
+
+class TuneInfo(C.Structure):
+    _fields_ = [("path", I32), ("wF", I32), ("wG", I32), ("candidates", I32), ("probe_steps", I32),
+                ("cand_path", I32 * 16), ("cand_wF", I32 * 16), ("cand_wG", I32 * 16), ("probe_ms", F32 * 16)]
+
+    def as_dict(self):
+        k = self.candidates
+        return {"path": ("resident", "streamed")[self.path], "wF": self.wF, "wG": self.wG,
+                "probe_steps": self.probe_steps,
+                "candidates": [{"path": ("resident", "streamed")[self.cand_path[i]], "wF": self.cand_wF[i],
+                                "wG": self.cand_wG[i], "ms": self.probe_ms[i]} for i in range(k)]}
 
 
 class Problem(C.Structure):
@@ -136,6 +149,8 @@ _SIGS = {
     "mape_extract": (C.c_int, [C.POINTER(ExtractArgs), P_]),
     "mape_initial_solutions_workspace_bytes": (C.c_size_t, [I32, I32, I32]),
     "mape_initial_solutions": (C.c_int, [C.POINTER(InitArgs), P_]),
+    "mape_autotune_lookup": (C.c_int, [I32, I32, I32, I32, C.POINTER(TuneInfo)]),
+    "mape_autotune_clear": (None, []),
     "mape_dedup_workspace_bytes": (C.c_size_t, [I64, I32]),
     "mape_dedup": (C.c_int, [P_, I64, I32, I32, P_, I64, C.POINTER(I64), P_, C.c_size_t, P_]),
     "mape_dedup_static_max_rows": (I64, []),
@@ -672,3 +687,10 @@ def kernel_basis(A, reduce: bool = True) -> np.ndarray:
     B = np.empty((n, n - m), np.int32)
     _check(lib().mape_kernel_basis(m, n, _host(A), int(reduce), _host(B)), "mape_kernel_basis")
     return B
+
+
+def autotune_info(n, d, P, precision=PREC_BF16):
+    """The autotuned choice for a shape (mape_autotune_lookup), or None."""
+    info = TuneInfo()
+    rc = lib().mape_autotune_lookup(n, d, P, precision, C.byref(info))
+    return None if rc != OK else info.as_dict()
