@@ -140,13 +140,22 @@ __global__ void bin_scan_kernel(const uint32_t* __restrict__ hist, int nbins, ui
 __global__ void scatter_kernel(const int32_t* __restrict__ l1, const uint64_t* __restrict__ masks, int64_t K, int W,
                                const uint32_t* __restrict__ start, uint32_t* __restrict__ cursor,
                                uint32_t* __restrict__ s_idx, uint64_t* __restrict__ s_pk,
-                               uint32_t* __restrict__ s_lim) {
+                               ulonglong2* __restrict__ s_sig, uint32_t* __restrict__ s_lim) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= K || l1[k] == kInvalidL1) return;
   uint32_t q = atomicAdd(&cursor[l1[k]], 1u);
   s_idx[q] = (uint32_t)k;
   // sign masks of coordinates 0..31: pos in the low half, neg in the high half
   s_pk[q] = (masks[k * 2 * W] & 0xffffffffull) | (masks[k * 2 * W + W] << 32);
+  // second filter: every coordinate i folded onto bit i mod 64 (OR of the
+  // mask words), pos and neg apart; support and signs of h within those of
+  // +-g imply the same for these signatures
+  uint64_t pos = 0, neg = 0;
+  for (int w = 0; w < W; ++w) {
+    pos |= masks[k * 2 * W + w];
+    neg |= masks[k * 2 * W + W + w];
+  }
+  s_sig[q] = make_ulonglong2(pos, neg);
   s_lim[q] = start[l1[k]];
 }
 
@@ -177,13 +186,16 @@ constexpr int kChunk = 4096;  // shorter rows scanned by one block
 // Work unit (blockIdx.x, blockIdx.y): the 256 sorted rows of row block x
 // against the shorter rows [y * kChunk, (y + 1) * kChunk).  Every unit has
 // the same size, so the quadratic work spreads evenly over the SMs however the
-// rows' limits grow along the l1 order.  Prefilter per pair: sign masks of
-// coordinates 0..31 packed in one word (pos | neg << 32).  A dominated row
-// gets dom[k] = 1 (several units may write it).
+// rows' limits grow along the l1 order.  Prefilters per pair: sign masks of
+// coordinates 0..31 packed in one word (pos | neg << 32), then, for the pairs
+// that pass, the folded 64-bit signatures of all coordinates, before the full
+// test.  A dominated row gets dom[k] = 1 (several units may write it).
 __global__ void dominance_kernel(const int8_t* __restrict__ G, int n, int ldg, int W, const uint64_t* __restrict__ masks,
                                  int64_t nvalid, const uint32_t* __restrict__ s_idx, const uint64_t* __restrict__ s_pk,
-                                 const uint32_t* __restrict__ s_lim, uint8_t* __restrict__ dom) {
+                                 const ulonglong2* __restrict__ s_sig, const uint32_t* __restrict__ s_lim,
+                                 uint8_t* __restrict__ dom) {
   __shared__ uint64_t t_pk[kTile];
+  __shared__ ulonglong2 t_sig[kTile];
   __shared__ uint32_t s_blim;
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const uint32_t lo = blockIdx.y * (uint32_t)kChunk;
@@ -201,12 +213,17 @@ __global__ void dominance_kernel(const int8_t* __restrict__ G, int n, int ldg, i
   const uint32_t k = mine ? s_idx[q] : 0;
   const uint64_t pk = mine ? s_pk[q] : 0;
   const uint32_t np = ~(uint32_t)pk, nn = ~(uint32_t)(pk >> 32);
+  const ulonglong2 gs = mine ? s_sig[q] : make_ulonglong2(0, 0);
+  const uint64_t gsp = ~gs.x, gsn = ~gs.y;
   bool done = !mine || lim <= lo || dom[k];
   for (uint32_t base = lo; base < hi; base += kTile) {
     __syncthreads();
     for (int t = threadIdx.x; t < kTile; t += blockDim.x) {
       uint32_t h = base + t;
-      if (h < hi) t_pk[t] = s_pk[h];
+      if (h < hi) {
+        t_pk[t] = s_pk[h];
+        t_sig[t] = s_sig[h];
+      }
     }
     __syncthreads();
     if (done) continue;
@@ -217,7 +234,10 @@ __global__ void dominance_kernel(const int8_t* __restrict__ G, int n, int ldg, i
       const uint64_t hk = t_pk[t];
       const uint32_t hp = (uint32_t)hk, hn = (uint32_t)(hk >> 32);
       const bool cand = (((hp & np) | (hn & nn)) == 0) || (((hp & nn) | (hn & np)) == 0);
-      if (cand && dominates(G, n, ldg, W, masks, s_idx[base + t], k)) {
+      if (!cand) continue;
+      const ulonglong2 hs = t_sig[t];
+      const bool cand2 = (((hs.x & gsp) | (hs.y & gsn)) == 0) || (((hs.x & gsn) | (hs.y & gsp)) == 0);
+      if (cand2 && dominates(G, n, ldg, W, masks, s_idx[base + t], k)) {
         done = true;
         dom[k] = 1;
         break;
@@ -321,6 +341,7 @@ extern "C" size_t mape_minimal_workspace_bytes(int64_t K, int32_t n) {
   s.take<uint32_t>((size_t)nb);               // cursors
   s.take<uint32_t>((size_t)K);                // sorted row index
   s.take<uint64_t>((size_t)K);                // sorted packed sign masks
+  s.take<ulonglong2>((size_t)K);              // sorted folded signatures
   s.take<uint32_t>((size_t)K);                // sorted limits
   s.take<uint32_t>((size_t)ceil_div(K, kCompact) + 1);  // block counts
   s.take<uint32_t>((size_t)ceil_div(K, kCompact) + 1);  // block starts
@@ -348,6 +369,7 @@ extern "C" int mape_minimal_filter(const int8_t* G, int64_t K, int32_t n, int32_
   uint32_t* cursor = cv.take<uint32_t>((size_t)nb);
   uint32_t* s_idx = cv.take<uint32_t>((size_t)K);
   uint64_t* s_pk = cv.take<uint64_t>((size_t)K);
+  ulonglong2* s_sig = cv.take<ulonglong2>((size_t)K);
   uint32_t* s_lim = cv.take<uint32_t>((size_t)K);
   uint32_t* bcount = cv.take<uint32_t>((size_t)nblk + 1);
   uint32_t* bstart = cv.take<uint32_t>((size_t)nblk + 1);
@@ -358,7 +380,7 @@ extern "C" int mape_minimal_filter(const int8_t* G, int64_t K, int32_t n, int32_
   const unsigned g = (unsigned)ceil_div(K, kTile);
   mape_detail::launch(prep_kernel, g, kTile, 0, st, G, K, n, ldg, W, valid, l1, masks, hist);
   mape_detail::launch(bin_scan_kernel, 1, 1024, 0, st, hist, (int)nb, start, cursor);
-  mape_detail::launch(scatter_kernel, g, kTile, 0, st, l1, masks, K, W, start, cursor, s_idx, s_pk, s_lim);
+  mape_detail::launch(scatter_kernel, g, kTile, 0, st, l1, masks, K, W, start, cursor, s_idx, s_pk, s_sig, s_lim);
   mape_detail::launch(clear_keep_kernel, g, kTile, 0, st, keep, K);
   MAPE_LAUNCH_CHECK();
   // number of valid rows = end of the last bin
@@ -369,7 +391,7 @@ extern "C" int mape_minimal_filter(const int8_t* G, int64_t K, int32_t n, int32_
   const int64_t nvalid = (int64_t)last_start + last_count;
   if (nvalid > 0)
     mape_detail::launch(dominance_kernel, dim3((unsigned)ceil_div(nvalid, kTile), (unsigned)ceil_div(nvalid, kChunk)),
-                        kTile, 0, st, G, n, ldg, W, masks, nvalid, s_idx, s_pk, s_lim, keep);
+                        kTile, 0, st, G, n, ldg, W, masks, nvalid, s_idx, s_pk, s_sig, s_lim, keep);
   mape_detail::launch(finalize_keep_kernel, g, kTile, 0, st, l1, keep, K, keep);
   mape_detail::launch(count_kept_kernel, (unsigned)nblk, kCompact, 0, st, keep, K, bcount);
   // block starts: exclusive prefix of the counts, entry nblk = total
