@@ -74,6 +74,36 @@ __device__ __forceinline__ void store_row8(uint8_t* tile, int r, int k0, int K, 
   *reinterpret_cast<uint4*>(tile + op_off(r, k0, K)) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+// sign as a float: +-1, and 0 for 0 (and NaN)
+__device__ __forceinline__ float sgn1(float x) { return fabsf(x) > 0.f ? copysignf(1.f, x) : 0.f; }
+
+// bf16 pair {sign(a), sign(b)} (low half a): 0x3f80 = 1, 0xbf80 = -1, 0 for 0 and NaN
+__device__ __forceinline__ uint32_t sign_bf16x2(float a, float b) {
+  const uint32_t sa = fabsf(a) > 0.f ? (((__float_as_uint(a) >> 16) & 0x8000u) | 0x3f80u) : 0u;
+  const uint32_t sb = fabsf(b) > 0.f ? ((__float_as_uint(b) & 0x80000000u) | 0x3f800000u) : 0u;
+  return sa | sb;
+}
+
+// d/dz of the integrality term (ceil z - z)(z - floor z) of Eq. (3):
+// ceil z + floor z - 2 z, which with e = z - rint(z) is sign(e) - 2 e (0 at
+// the integers, +-1 - 2 e between them); every step is exact in FP32
+__device__ __forceinline__ float frac_grad(float z, float rz) {
+  const float e = z - rz;
+  return fmaf(-2.f, e, sgn1(e));
+}
+
+// square root and reciprocal of the Adam denominator (v >= 0, den >= eps > 0)
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 struct TcParams {
   const int32_t* B;
   const int32_t* span;
@@ -148,7 +178,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
   uint8_t* A1lo = smem + L.opa + kTileM * p.d_pad * 2;  // lo(z)
   uint8_t* A2 = smem + L.opa2;                          // round(z)
   uint8_t* Sop = smem + L.opa;
-  int32_t* s_span = reinterpret_cast<int32_t*>(smem + L.span);
+  float* s_span = reinterpret_cast<float*>(smem + L.span);  // box spans u - l, exact in FP32
   float* s_pz = reinterpret_cast<float*>(smem + L.pz);
   int32_t* s_pk = reinterpret_cast<int32_t*>(smem + L.pk);
   float* s_pl1 = reinterpret_cast<float*>(smem + L.pl1);
@@ -184,7 +214,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     *reinterpret_cast<uint16_t*>(Bf + op_off(i, j, d_pad)) = h;                // N = rows, K = d
     if (p.use_bb) *reinterpret_cast<uint16_t*>(Bb + op_off(j, i, n_pad)) = h;  // N = d, K = rows
   }
-  for (int i = tid; i < p.span_pad; i += kThreads) s_span[i] = i < n ? p.span[i] : 0;
+  for (int i = tid; i < p.span_pad; i += kThreads) s_span[i] = i < n ? (float)p.span[i] : 0.f;
   if (tid < kTileM) {
     s_fl[tid] = kChanged;  // the first collection of a call always counts
     s_fnz[tid] = kNoNz;
@@ -217,6 +247,9 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
   float4* const vb = reinterpret_cast<float4*>(p.Vt) + (size_t)tile * (d_pad / 4) * kTileM + r;
 
   // ---- initial operand: bf16(z0) and the partial ||z0||_inf ----
+  // Each thread keeps the largest |z_j| over its coordinates and the first of
+  // its 8-column groups that holds it; padding coordinates and inactive starts
+  // are 0 and never beat a real coordinate.
   float zinf_part = 0.f;
   int kmax_part = kNoNz;
   for (int ch = split; ch < dch && !bail; ch += kSplits) {
@@ -251,12 +284,10 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       const float2 hf = __bfloat1622float2(hh);
       wl[c >> 1] = pack_bf16x2(zc[c] - hf.x, zc[c + 1] - hf.y);
     }
+    float cmax = fabsf(zc[0]);
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int j = c0 + c;
-      const float a = fabsf(zc[c]);
-      if (j < d && (a > zinf_part || kmax_part == kNoNz)) { zinf_part = a; kmax_part = j; }
-    }
+    for (int c = 1; c < 8; ++c) cmax = fmaxf(cmax, fabsf(zc[c]));
+    if (kmax_part == kNoNz || cmax > zinf_part) { zinf_part = cmax; kmax_part = c0; }
     store_row8(A1, r, c0, d_pad, wh);
     if (p.nterms > 1) store_row8(A1lo, r, c0, d_pad, wl);
   }
@@ -276,7 +307,8 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
   const uint32_t idesc_bwd = idesc_bf16(kTileM, d_pad) | (p.use_bb ? 0u : (1u << 16));
   const uint32_t sbo_d = (uint32_t)(d_pad / 8) * 128, sbo_n = (uint32_t)(n_pad / 8) * 128;
 
-  // combine the partials of ||z||_inf: max, ties to the lower index (first maximiser)
+  // combine the partials of ||z||_inf: max, ties to the lower group, so that
+  // kmax is the 8-column group holding the first maximiser of |z|
   auto combine_zinf = [&](float& zinf, int& kmax) {
     zinf = 0.f;
     kmax = kNoNz;
@@ -302,10 +334,10 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int i = r0 + ch * 16 + hoff + c;  // row of B
-        int g = __float2int_rn(__uint_as_float(v[c]));
+        const float g = __uint_as_float(v[c]);  // an integer, exact
         if (i < n) {
-          if (g > s_span[i] || -g > s_span[i]) out = true;
-          if (!kId && g != 0 && (i << 1) < first) first = (i << 1) | (g < 0 ? 1 : 0);
+          out |= fabsf(g) > s_span[i];
+          if (!kId && g != 0.f && (i << 1) < first) first = (i << 1) | (g < 0.f ? 1 : 0);
         }
       }
     }
@@ -438,10 +470,10 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       tc_wait_ld();
       uint32_t w[4];
 #pragma unroll
-      for (int c = 0; c < 8; c += 2) {
-        const float y0 = __uint_as_float(v[c]), y1 = __uint_as_float(v[c + 1]);
-        w[c >> 1] = pack_bf16x2((float)mape_sign_f(y0), (float)mape_sign_f(y1));
-        l1 += fabsf(y0) + fabsf(y1);
+      for (int c = 0; c < 8; c += 2) w[c >> 1] = sign_bf16x2(__uint_as_float(v[c]), __uint_as_float(v[c + 1]));
+      if (dbg_step) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) l1 += fabsf(__uint_as_float(v[c]));
       }
       store_row8(Sop, r, ch * 16 + hoff, n_pad, w);
     }
@@ -492,17 +524,14 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     // lr / bc1 and 1 / sqrt(bc2) formed in double on the host
     const float2 ad = p.bias[s];
     const float step = ad.x, rsb2 = ad.y;
-    float inv_term = 0.f;
-    if (zinf < 1.f && zinf > 0.f) inv_term = -p.lambda2 / (zinf * zinf);  // times sign(z_kmax)
-    float nzinf = 0.f, frac = 0.f, l1_id = 0.f;
-    int nkmax = kNoNz, first_id = kNoNz;
-    bool changed = false, unexact = false, out_id = false;
-    for (int ch = split; ch < dch; ch += kSplits) {
-      const int c0 = ch * 16 + hoff;
-      uint32_t v[8];
-      tmem_ld8x2(tmem + lane_off + ch * 16, v);  // completes under the global loads below
-      float zc[8], mc[8], vc[8];
-      uint32_t zo[8], mo[8], vo[8];
+    // The inverse-norm term of Eq. (3), -lambda2 / ||z||_inf^2 times the sign
+    // of z at the first maximiser of |z|, is nonzero only while
+    // 0 < ||z||_inf < 1; kmax is the 8-column group holding that maximiser.
+    const bool inv_on = zinf < 1.f && zinf > 0.f;
+    const float inv_term = inv_on ? -p.lambda2 / (zinf * zinf) : 0.f;
+    // G (TMEM) and the master z, m, v of coordinates c0 .. c0+7
+    auto load_state = [&](int ch, int c0, uint32_t (&v)[8], float (&zc)[8], float (&mc)[8], float (&vc)[8]) {
+      tmem_ld8x2(tmem + lane_off + ch * 16, v);  // completes under the loads below
       if (kRes) {
         uint32_t tz[8], tm[8], tv[8];
         tmem_ld8x2(tmem + st_off + ch * 16, tz);
@@ -526,54 +555,109 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
         }
         tc_wait_ld();
       }
+    };
+    // the gradient of Eq. (3) at coordinates c0 .. c0+7: G + lambda1 (ceil z +
+    // floor z - 2 z), the inverse-norm term, and for identity-topped B the
+    // identity rows' sign(z_j)
+    auto chunk_grad = [&](int c0, const uint32_t (&v)[8], const float (&zc)[8], const float (&rz)[8],
+                          float (&g)[8]) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) g[c] = fmaf(p.lambda1, frac_grad(zc[c], rz[c]), __uint_as_float(v[c]));
+      if (inv_on && c0 == kmax) {
+        bool hit = false;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          if (!hit && fabsf(zc[c]) == zinf) {
+            g[c] += inv_term * sgn1(zc[c]);
+            hit = true;
+          }
+        }
+      }
+      if (kId) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) g[c] += sgn1(zc[c]);
+      }
+    };
+    // debug outputs of the first step: the integrality sum of Phi, the l1 norm
+    // of the identity rows and the gradient, before the state is overwritten
+    float frac = 0.f, l1_id = 0.f;
+    if (dbg_step) {
+      for (int ch = split; ch < dch; ch += kSplits) {
+        const int c0 = ch * 16 + hoff;
+        uint32_t v[8];
+        float zc[8], mc[8], vc[8], rz[8], g[8];
+        load_state(ch, c0, v, zc, mc, vc);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) rz[c] = rintf(zc[c]);
+        chunk_grad(c0, v, zc, rz, g);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int j = c0 + c;
+          if (!active || j >= d) continue;
+          const float z = zc[c], fl = floorf(z);
+          frac += (z - fl) * (ceilf(z) - z);
+          if (kId) l1_id += fabsf(z);
+          if (p.dbg_grad) p.dbg_grad[pg * d + j] = g[c];
+        }
+      }
+    }
+    float nzinf = 0.f;
+    int nkmax = kNoNz, first_id = kNoNz;
+    bool changed = false, unexact = false, out_id = false;
+    for (int ch = split; ch < dch; ch += kSplits) {
+      const int c0 = ch * 16 + hoff;
+      uint32_t v[8];
+      float zc[8], mc[8], vc[8], rz[8], g[8];
+      load_state(ch, c0, v, zc, mc, vc);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) rz[c] = rintf(zc[c]);
+      chunk_grad(c0, v, zc, rz, g);
+      float zn[8], rn[8];
+      uint32_t zo[8], mo[8], vo[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float m = fmaf(p.beta1, mc[c], p.omb1 * g[c]);
+        const float vv = fmaf(p.beta2, vc[c], p.omb2 * g[c] * g[c]);
+        const float den = fmaf(sqrt_approx(vv), rsb2, p.eps);
+        // padding coordinates (j >= d) have zero gradient and stay at 0
+        zn[c] = fmaf(-step, m * rcp_approx(den), zc[c]);
+        rn[c] = rintf(zn[c]);
+        zo[c] = __float_as_uint(zn[c]);
+        mo[c] = __float_as_uint(m);
+        vo[c] = __float_as_uint(vv);
+        // padding coordinates (z = 0 throughout) and inactive starts leave
+        // every tracker unchanged: their roundings never change, are 0, are
+        // within any box and never beat a real coordinate's |z| or index
+        changed |= rn[c] != rz[c];
+        unexact |= fabsf(rn[c]) > 256.f;
+      }
+      float cmax = fabsf(zn[0]);
+#pragma unroll
+      for (int c = 1; c < 8; ++c) cmax = fmaxf(cmax, fabsf(zn[c]));
+      if (nkmax == kNoNz || cmax > nzinf) { nzinf = cmax; nkmax = c0; }
+      if (kId) {  // identity rows of g = B round(z): bound test and first nonzero entry
+        const float4 sa = *reinterpret_cast<const float4*>(s_span + c0);
+        const float4 sb = *reinterpret_cast<const float4*>(s_span + c0 + 4);
+        const float sp[8] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w};
+        bool nz = false;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          out_id |= fabsf(rn[c]) > sp[c];
+          nz |= rn[c] != 0.f;
+        }
+        if (first_id == kNoNz && nz) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (first_id == kNoNz && rn[c] != 0.f) first_id = ((c0 + c) << 1) | (rn[c] < 0.f ? 1 : 0);
+        }
+      }
       uint32_t w1[4], wl[4], w2[4];
 #pragma unroll
       for (int c = 0; c < 8; c += 2) {
-        float zn[2], rn[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int cc = c + q, j = c0 + cc;
-          const bool live = active && j < d;
-          const float z = zc[cc];
-          const float fl = floorf(z);
-          // ceil z + floor z = 2 floor z + [z not an integer]
-          float grad = __uint_as_float(v[cc]) + p.lambda1 * (2.f * fl + (z != fl ? 1.f : 0.f) - 2.f * z);
-          const float sz = (float)mape_sign_f(z);
-          if (j == kmax) grad += inv_term * sz;
-          if (kId) grad += sz;  // identity row j of B: sign((Bz)_j) = sign(z_j)
-          if (dbg_step && live) {
-            frac += (z - fl) * (ceilf(z) - z);
-            if (kId) l1_id += fabsf(z);
-            if (p.dbg_grad) p.dbg_grad[pg * d + j] = grad;
-          }
-          const float m = p.beta1 * mc[cc] + p.omb1 * grad;
-          const float vv = p.beta2 * vc[cc] + p.omb2 * grad * grad;
-          const float den = (vv > 0.f ? vv * rsqrtf(vv) : 0.f) * rsb2 + p.eps;
-          // padding coordinates (j >= d) have zero gradient and stay at 0
-          const float znew = z - step * __fdividef(m, den);
-          zo[cc] = __float_as_uint(znew);
-          mo[cc] = __float_as_uint(m);
-          vo[cc] = __float_as_uint(vv);
-          zn[q] = znew;
-          rn[q] = rintf(znew);
-          // padding coordinates (z = 0 throughout) and inactive starts leave
-          // every tracker unchanged: their roundings never change, are 0, are
-          // within any box and never beat a real coordinate's |z| or index
-          {
-            changed |= rn[q] != rintf(z);
-            unexact |= fabsf(rn[q]) > 256.f;
-            const float a = fabsf(znew);
-            if (nkmax == kNoNz || a > nzinf) { nzinf = a; nkmax = j; }
-            if (kId) {  // identity rows of g = B round(z): bound test and first nonzero entry
-              out_id |= fabsf(rn[q]) > (float)s_span[j];
-              if (first_id == kNoNz && rn[q] != 0.f) first_id = (j << 1) | (rn[q] < 0.f ? 1 : 0);
-            }
-          }
-        }
-        w1[c >> 1] = pack_bf16x2(zn[0], zn[1]);
+        w1[c >> 1] = pack_bf16x2(zn[c], zn[c + 1]);
         const float2 hf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w1[c >> 1]));
-        wl[c >> 1] = pack_bf16x2(zn[0] - hf.x, zn[1] - hf.y);
-        w2[c >> 1] = pack_bf16x2(rn[0], rn[1]);
+        wl[c >> 1] = pack_bf16x2(zn[c] - hf.x, zn[c + 1] - hf.y);
+        w2[c >> 1] = pack_bf16x2(rn[c], rn[c + 1]);
       }
       if (kRes) {
         tmem_st8x2(tmem + st_off + ch * 16, zo);
@@ -583,8 +667,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
           const int g4 = c0 / 4 + k;
-          zb[g4 * kTileM] = make_float4(__uint_as_float(zo[4 * k]), __uint_as_float(zo[4 * k + 1]),
-                                        __uint_as_float(zo[4 * k + 2]), __uint_as_float(zo[4 * k + 3]));
+          zb[g4 * kTileM] = make_float4(zn[4 * k], zn[4 * k + 1], zn[4 * k + 2], zn[4 * k + 3]);
           mb[g4 * kTileM] = make_float4(__uint_as_float(mo[4 * k]), __uint_as_float(mo[4 * k + 1]),
                                         __uint_as_float(mo[4 * k + 2]), __uint_as_float(mo[4 * k + 3]));
           vb[g4 * kTileM] = make_float4(__uint_as_float(vo[4 * k]), __uint_as_float(vo[4 * k + 1]),
