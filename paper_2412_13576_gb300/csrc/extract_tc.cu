@@ -51,7 +51,8 @@ constexpr int kWarps = 16;
 constexpr int kThreads = kWarps * 32;
 constexpr int kSplits = kWarps / 4;
 constexpr int kParts = kSplits * 2;  // threads per start
-constexpr int kColD2 = 256;
+constexpr int kColD2 = 256;  // D2 when the accumulators cannot all have their own columns
+constexpr int kIssuer = 32 * (kWarps - 4);  // issues every MMA: lane 0 of warp 12
 constexpr int kTmemCols = 512;
 constexpr int kNoNz = 0x7fffffff;
 
@@ -127,8 +128,15 @@ struct TcParams {
 };
 
 struct Smem {  // byte offsets into dynamic shared memory
-  uint32_t bf, bb, opa, opa2, span, pz, pk, pl1, pfr, fl, fnz, slot, bar, tmem, total;
+  uint32_t bf, bb, opa, opa2, ss, span, pz, pk, pl1, pfr, fl, fnz, slot, misc, bar, tmem, total;
 };
+
+// Transposed forward product, for tiles of at most 64 rows of B: one MMA
+// chain D^T = B_tile . [hi(Z); lo(Z); round(Z)]^T (M = 64 rows of B, N = 64
+// starts per operand, K = d) gives B hi(z), B lo(z) and B round(z) of every
+// start in 10 instructions for d = 160 instead of 30 (an MMA instruction
+// costs about the same whatever its M and N).
+__host__ __device__ inline bool tc_transposed(int n_pad) { return n_pad <= 64; }
 
 // per-start flag word bits
 constexpr uint32_t kChanged = 1;    // rounding changed since the last collection
@@ -138,17 +146,23 @@ constexpr uint32_t kOutId = 8;      // ... fails C4 on the identity rows (identi
 
 __host__ __device__ inline uint32_t al(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
-// Operand area: [hi | lo] of bf16(z) (nterms tiles of 64 x d_pad), later
-// overwritten by S (64 x n_pad); then bf16(round z) (64 x d_pad).
+// Operand area: [hi | lo] of bf16(z) (nterms tiles of 64 x d_pad), then
+// bf16(round z) (64 x d_pad).  S (64 starts x n_pad) overwrites the [hi | lo]
+// tiles, or, in the transposed form, has its own MN-major tile (so that the
+// three z tiles stay one N = 192 operand and are never overwritten).
 __host__ __device__ inline Smem smem_layout(int n_pad, int d_pad, int nterms, int use_bb, int span_pad) {
   Smem s{};
+  const bool tr = tc_transposed(n_pad);
+  const uint32_t bf_rows = tr ? (uint32_t)kTileM : (uint32_t)n_pad;
   uint32_t o = 0;
-  s.bf = o;   o = al(o + (uint32_t)n_pad * d_pad * 2, 1024);
+  s.bf = o;   o = al(o + bf_rows * d_pad * 2, 1024);
   s.bb = o;   if (use_bb) o = al(o + (uint32_t)n_pad * d_pad * 2, 1024);
   s.opa = o;
   uint32_t zs = (uint32_t)nterms * d_pad > (uint32_t)n_pad ? (uint32_t)nterms * d_pad : (uint32_t)n_pad;
+  if (tr) zs = (uint32_t)nterms * d_pad;
   s.opa2 = o + (uint32_t)kTileM * zs * 2;
-  o = al(s.opa2 + (uint32_t)kTileM * d_pad * 2, 128);
+  o = al(s.opa2 + (uint32_t)kTileM * d_pad * 2, 1024);
+  s.ss = o;   if (tr) o = al(o + (uint32_t)kTileM * 64 * 2, 128);
   s.span = o; o = al(o + (uint32_t)span_pad * 4, 128);
   s.pz = o;   o = al(o + kParts * kTileM * 4, 128);
   s.pk = o;   o = al(o + kParts * kTileM * 4, 128);
@@ -157,7 +171,8 @@ __host__ __device__ inline Smem smem_layout(int n_pad, int d_pad, int nterms, in
   s.fl = o;   o = al(o + kTileM * 4, 128);
   s.fnz = o;  o = al(o + kTileM * 4, 128);
   s.slot = o; o = al(o + kTileM * 8, 128);
-  s.bar = o;  o = al(o + 16, 16);  // two mbarriers: forward/gradient MMAs, B round(z) MMAs
+  s.misc = o; o = al(o + 16, 16);  // out-of-box mask of the transposed test, any-slot flag
+  s.bar = o;  o = al(o + 32, 16);  // mbarriers: gradient, B round(z), forward, drain
   s.tmem = o; o = al(o + 4, 16);
   s.total = o;
   return s;
@@ -177,7 +192,10 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
   uint8_t* A1 = smem + L.opa;                           // hi(z)
   uint8_t* A1lo = smem + L.opa + kTileM * p.d_pad * 2;  // lo(z)
   uint8_t* A2 = smem + L.opa2;                          // round(z)
-  uint8_t* Sop = smem + L.opa;
+  uint8_t* Sop = smem + L.opa;                          // S, K-major (not transposed)
+  uint8_t* sS = smem + L.ss;                            // S, MN-major (transposed)
+  unsigned long long* s_outm = reinterpret_cast<unsigned long long*>(smem + L.misc);
+  int* s_any = reinterpret_cast<int*>(smem + L.misc + 8);
   float* s_span = reinterpret_cast<float*>(smem + L.span);  // box spans u - l, exact in FP32
   float* s_pz = reinterpret_cast<float*>(smem + L.pz);
   int32_t* s_pk = reinterpret_cast<int32_t*>(smem + L.pk);
@@ -201,18 +219,20 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
   const int nch = n_pad / 16, dch = d_pad / 16;
   const int r0 = kId ? d : 0;  // row of B held in row 0 of the MMA tile
   const int hoff = 8 * half;   // column offset of this half-warp inside a 16-column chunk
+  const bool tr = tc_transposed(n_pad);
+  const int bf_rows = tr ? kTileM : n_pad;  // the transposed form's M is 64 rows of B
 
   // ---- set-up: B in both operand layouts, span, flags ----
   if (tid == 0) s_bad = 0;
   __syncthreads();
-  for (int e = tid; e < n_pad * d_pad; e += kThreads) {
+  for (int e = tid; e < bf_rows * d_pad; e += kThreads) {
     int i = e / d_pad, j = e % d_pad;
-    int v = (r0 + i < n && j < d) ? p.B[(int64_t)(r0 + i) * d + j] : 0;
+    int v = (i < n_pad && r0 + i < n && j < d) ? p.B[(int64_t)(r0 + i) * d + j] : 0;
     if (v > 256 || v < -256) s_bad = 1;
     __nv_bfloat16 hb = __float2bfloat16_rn((float)v);
     const uint16_t h = *reinterpret_cast<const uint16_t*>(&hb);
-    *reinterpret_cast<uint16_t*>(Bf + op_off(i, j, d_pad)) = h;                // N = rows, K = d
-    if (p.use_bb) *reinterpret_cast<uint16_t*>(Bb + op_off(j, i, n_pad)) = h;  // N = d, K = rows
+    *reinterpret_cast<uint16_t*>(Bf + op_off(i, j, d_pad)) = h;                              // N = rows, K = d
+    if (p.use_bb && i < n_pad) *reinterpret_cast<uint16_t*>(Bb + op_off(j, i, n_pad)) = h;  // N = d, K = rows
   }
   for (int i = tid; i < p.span_pad; i += kThreads) s_span[i] = i < n ? (float)p.span[i] : 0.f;
   if (tid < kTileM) {
@@ -220,8 +240,11 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     s_fnz[tid] = kNoNz;
   }
   if (tid == 0) {
-    mbar_init(bar, 1);
-    mbar_init(bar + 8, 1);
+    *s_outm = 0ull;
+    *s_any = 0;
+  }
+  if (tid == 0) {
+    for (int b = 0; b < 4; ++b) mbar_init(bar + 8 * b, 1);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
@@ -240,25 +263,76 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
   bool bail = s_bad != 0;
   if (bail && tid == 0) atomicOr(p.flags, 8);
 
+  // Accumulator columns (TMEM lanes 0-15 of each quarter).  Transposed form:
+  // D^T = [B hi(z) | B lo(z) | B round(z)] in 64-column blocks from column 0
+  // (lanes: rows of B), G from column 64 (nterms + 1) rounded up to 32, so
+  // that the gradient MMA does not overwrite B round(z) while the candidate
+  // is written.  Otherwise D1 (n_pad columns) and G share column 0 and D2 is
+  // at column 256.  Every MMA of the CTA is issued by one thread.  (Issuing
+  // the next step's forward MMAs during the Adam epilogue, as its operand
+  // chunks are written, measured slower: MMAs running beside the epilogue
+  // slow its TMEM traffic by more than they save.)
+  const uint32_t colG_ = tr ? al(64u * (uint32_t)(p.nterms + 1), 32) : 0u;
+  const uint32_t colD2 = tr ? 64u * (uint32_t)p.nterms : (uint32_t)kColD2;
+  const bool issuer = tid == kIssuer;
+  const uint32_t barG = bar, bar2 = bar + 8, barF = bar + 16, barD = bar + 24;
+
   // FP32 master state of this thread's start: blocked [tile][d_pad/4][64][4],
   // four consecutive coordinates per 16-byte access, coalesced over 16 starts
   float4* const zb = reinterpret_cast<float4*>(p.Zt) + (size_t)tile * (d_pad / 4) * kTileM + r;
   float4* const mb = reinterpret_cast<float4*>(p.Mt) + (size_t)tile * (d_pad / 4) * kTileM + r;
   float4* const vb = reinterpret_cast<float4*>(p.Vt) + (size_t)tile * (d_pad / 4) * kTileM + r;
 
+  const bool state_loaded = !bail;  // kRes: z, m, v are in TMEM from here on
   // ---- initial operand: bf16(z0) and the partial ||z0||_inf ----
   // Each thread keeps the largest |z_j| over its coordinates and the first of
   // its 8-column groups that holds it; padding coordinates and inactive starts
   // are 0 and never beat a real coordinate.
   float zinf_part = 0.f;
   int kmax_part = kNoNz;
+  const uint32_t sbo_d = (uint32_t)(d_pad / 8) * 128, sbo_n = (uint32_t)(n_pad / 8) * 128;
+  const uint32_t idesc_fwd = idesc_bf16(kTileM, n_pad);
+  // forward MMAs (hi, then lo) of K-chunks [k0, k1) into D1 and B round(z)
+  // MMAs of the same chunks into D2; D1 and D2 are overwritten by chunk 0
+  auto issue_chunks = [&](int k0, int k1, bool fwd, bool d2) {
+    if (tr) {  // one chain: A = the tile of B (M = 64), B = the z operand tiles (N = 64 per tile)
+      const int nb = (fwd ? p.nterms : 0) + (d2 ? 1 : 0);
+      if (nb == 0) return;
+      const uint32_t bstart = smem_u32(fwd ? A1 : A2);
+      const uint32_t idesc = idesc_bf16(kTileM, 64 * nb);
+      const uint32_t dcol = fwd ? 0u : colD2;
+      for (int kk = k0; kk < k1; ++kk) {
+        const uint64_t a = make_desc(smem_u32(Bf) + kk * 256, 128, sbo_d);
+        const uint64_t b = make_desc(bstart + kk * 256, 128, sbo_d);
+        mma_bf16(tmem + dcol, a, b, idesc, kk > 0 ? 1u : 0u);
+      }
+      return;
+    }
+    if (fwd) {
+      for (int term = 0; term < p.nterms; ++term) {
+        const uint32_t abase = smem_u32(term == 0 ? A1 : A1lo);
+        for (int kk = k0; kk < k1; ++kk) {
+          const uint64_t a = make_desc(abase + kk * 256, 128, sbo_d);
+          const uint64_t b = make_desc(smem_u32(Bf) + kk * 256, 128, sbo_d);
+          mma_bf16(tmem, a, b, idesc_fwd, (term > 0 || kk > 0) ? 1u : 0u);
+        }
+      }
+    }
+    if (d2) {
+      for (int kk = k0; kk < k1; ++kk) {
+        const uint64_t a = make_desc(smem_u32(A2) + kk * 256, 128, sbo_d);
+        const uint64_t b = make_desc(smem_u32(Bf) + kk * 256, 128, sbo_d);
+        mma_bf16(tmem + colD2, a, b, idesc_fwd, kk > 0 ? 1u : 0u);
+      }
+    }
+  };
   for (int ch = split; ch < dch && !bail; ch += kSplits) {
     const int c0 = ch * 16 + hoff;
     float zc[8];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const float4 q = zb[(c0 / 4 + k) * kTileM];
-      zc[4 * k] = q.x; zc[4 * k + 1] = q.y; zc[4 * k + 2] = q.z; zc[4 * k + 3] = q.w;
+      const float4 qz = zb[(c0 / 4 + k) * kTileM];
+      zc[4 * k] = qz.x; zc[4 * k + 1] = qz.y; zc[4 * k + 2] = qz.z; zc[4 * k + 3] = qz.w;
     }
     if (kRes) {
       uint32_t wz[8], wm[8], wv[8];
@@ -300,12 +374,10 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
   tc_fence_after();
 
   const bool dbg_on = (p.dbg_phi != nullptr || p.dbg_grad != nullptr);
-  uint32_t phase = 0;
-  const uint32_t idesc_fwd = idesc_bf16(kTileM, n_pad);
   // gradient MMA: B operand K-major from the transposed copy, or MN-major
-  // (bit 16) straight from the forward tile
-  const uint32_t idesc_bwd = idesc_bf16(kTileM, d_pad) | (p.use_bb ? 0u : (1u << 16));
-  const uint32_t sbo_d = (uint32_t)(d_pad / 8) * 128, sbo_n = (uint32_t)(n_pad / 8) * 128;
+  // (bit 16) straight from the forward tile; A = S MN-major (bit 15) in the
+  // transposed form
+  const uint32_t idesc_bwd = idesc_bf16(kTileM, d_pad) | (p.use_bb ? 0u : (1u << 16)) | (tr ? (1u << 15) : 0u);
 
   // combine the partials of ||z||_inf: max, ties to the lower group, so that
   // kmax is the 8-column group holding the first maximiser of |z|
@@ -324,12 +396,44 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
   combine_zinf(zinf, kmax);
 
   // tests the candidate held in D2 (bound test, first nonzero entry) ...
+  // transposed form: v holds B round(z) of row i of B (lane) for the 8 starts
+  // 16 split + hoff + c (columns), loaded with the sign phase's operands;
+  // every lane calls this (warp-collective reductions)
+  auto test_candidate_tr = [&](const uint32_t (&v)[8]) {
+      uint32_t outm = 0;  // bit 8 half + c: that start fails C4 on row i
+      int key[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) key[c] = kNoNz;
+      if (quarter < nch) {  // warp-uniform: the quarter holds rows of the tile
+        const int i = r0 + quarter * 16 + (lane & 15);
+        if (i < n) {
+          const float sp = s_span[i];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float g = __uint_as_float(v[c]);  // an integer, exact
+            if (fabsf(g) > sp) outm |= 1u << (8 * half + c);
+            if (!kId && g != 0.f) key[c] = (i << 1) | (g < 0.f ? 1 : 0);
+          }
+        }
+      }
+      outm = __reduce_or_sync(0xffffffffu, outm);
+      if (lane == 0 && outm) atomicOr(s_outm, (unsigned long long)outm << (16 * split));
+      if (!kId) {  // first nonzero row: minimum over the 16 rows of the half-warp
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          int k = key[c];
+#pragma unroll
+          for (int o = 1; o < 16; o <<= 1) k = min(k, __shfl_xor_sync(0xffffffffu, k, o));
+          if ((lane & 15) == 0 && k != kNoNz) atomicMin(&s_fnz[16 * split + hoff + c], k);
+        }
+      }
+  };
   auto test_candidate = [&]() {
     int first = kNoNz;
     bool out = false;
     for (int ch = split; ch < nch; ch += kSplits) {
       uint32_t v[8];
-      tmem_ld8x2(tmem + lane_off + kColD2 + ch * 16, v);
+      tmem_ld8x2(tmem + lane_off + colD2 + ch * 16, v);
       tc_wait_ld();
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
@@ -349,6 +453,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     if (part != 0) return;
     long long slot = -1;
     uint32_t f = s_fl[r];
+    if (tr && ((*s_outm >> r) & 1ull)) f |= kOutOfBox;
     int fnz = s_fnz[r];
     if (active && (f & kChanged) && !(f & (kOutOfBox | kOutId)) && fnz != kNoNz) {
       if (f & kUnexact) {
@@ -360,10 +465,12 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       }
     }
     s_slot[r] = slot;
+    if (slot >= 0) *s_any = 1;
   };
   // every lane of the warp executes the (warp-collective) TMEM loads; only
   // lanes whose start has a slot store
   auto write_candidate = [&]() {
+    if (*s_any == 0) return;  // CTA-uniform: no start of the tile has a slot
     long long slot = s_slot[r];
     int sgn = (s_fnz[r] & 1) ? -1 : 1;
     int8_t* row = slot >= 0 ? p.cand + slot * p.ldc : nullptr;
@@ -380,10 +487,34 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
           if (j < d) row[j] = (int8_t)(sgn * __float2int_rn(zr));
         }
       }
+    }
+    if (tr) {
+      // rows of the tile from D2^T: this thread holds row i of B for the 8
+      // starts 16 split + hoff + c (warp-collective loads)
+      if (quarter < nch) {
+        uint32_t v[8];
+        tmem_ld8x2(tmem + lane_off + colD2 + 16 * split, v);
+        tc_wait_ld();
+        const int i = r0 + quarter * 16 + (lane & 15);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int rs = 16 * split + hoff + c;
+          const long long sl = s_slot[rs];
+          if (sl >= 0 && i < n) {
+            const int sg = (s_fnz[rs] & 1) ? -1 : 1;
+            p.cand[sl * p.ldc + i] = (int8_t)(sg * __float2int_rn(__uint_as_float(v[c])));
+          }
+        }
+      }
+      if (row && part == 0)
+        for (int b = n; b < p.ldc; ++b) row[b] = 0;
+      return;
+    }
+    if (kId) {
       // rows of B' from D2 (warp-collective loads: every lane executes them)
       for (int ch = split; ch < nch; ch += kSplits) {
         uint32_t v[8];
-        tmem_ld8x2(tmem + lane_off + kColD2 + ch * 16, v);
+        tmem_ld8x2(tmem + lane_off + colD2 + ch * 16, v);
         tc_wait_ld();
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -396,7 +527,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     } else {
       for (int ch = split; ch < nch; ch += kSplits) {
         uint32_t v[8];
-        tmem_ld8x2(tmem + lane_off + kColD2 + ch * 16, v);
+        tmem_ld8x2(tmem + lane_off + colD2 + ch * 16, v);
         tc_wait_ld();
         uint32_t w[2] = {0, 0};
 #pragma unroll
@@ -415,26 +546,18 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       s_fl[r] = 0;
       if (!kId) s_fnz[r] = kNoNz;
     }
-  };
-  auto issue_d2 = [&]() {
-    for (int kk = 0; kk < dch; ++kk) {
-      uint64_t a = make_desc(smem_u32(A2) + kk * 256, 128, sbo_d);
-      uint64_t b = make_desc(smem_u32(Bf) + kk * 256, 128, sbo_d);
-      mma_bf16(tmem + kColD2, a, b, idesc_fwd, kk > 0);
+    if (tid == 0) {
+      *s_outm = 0ull;
+      *s_any = 0;
     }
   };
-  bool timed_out = false;
-  // the B round(z) MMAs of a collection step complete on their own barrier, so
-  // that the sign phase does not wait for them
-  const uint32_t bar2 = bar + 8;
-  uint32_t phase2 = 0;
-  bool d2_pending = false;
-  auto wait_mma = [&]() -> bool {
-    bool ok = mbar_wait_bounded(bar, phase);
-    phase ^= 1;
-    bool any_bad = __syncthreads_or(!ok) != 0;
+  uint32_t phaseG = 0, phaseF = 0, phase2 = 0;
+  // gradient MMA wait; a time-out anywhere ends the launch for the whole CTA
+  auto wait_grad = [&]() -> bool {
+    const bool ok = mbar_wait_bounded(barG, phaseG);
+    phaseG ^= 1;
+    const bool any_bad = __syncthreads_or(!ok) != 0;
     if (any_bad && tid == 0) atomicOr(p.flags, 16);
-    if (any_bad) timed_out = true;
     tc_fence_after();
     return !any_bad;
   };
@@ -443,28 +566,63 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     const int t = p.t0 + s + 1;              // global step number
     const bool collect_prev = s >= 1 && ((t - 1) % p.period == 0);
     const bool dbg_step = dbg_on && s == 0;
-    // (1) forward MMAs
-    if (tid == 0) {
+    // (1) forward MMAs (and B round(z) of the previous step's candidate)
+    if (issuer) {
       tc_fence_after();
-      for (int term = 0; term < p.nterms; ++term) {
-        uint32_t abase = smem_u32(term == 0 ? A1 : A1lo);
-        for (int kk = 0; kk < dch; ++kk) {
-          uint64_t a = make_desc(abase + kk * 256, 128, sbo_d);
-          uint64_t b = make_desc(smem_u32(Bf) + kk * 256, 128, sbo_d);
-          mma_bf16(tmem, a, b, idesc_fwd, (term > 0 || kk > 0) ? 1u : 0u);
-        }
-      }
-      mma_commit(bar);
-      if (collect_prev) {
-        issue_d2();
+      issue_chunks(0, dch, true, tr && collect_prev);  // transposed: one chain
+      mma_commit(barF);
+      if (!tr && collect_prev) {
+        issue_chunks(0, dch, false, true);
         mma_commit(bar2);
       }
     }
-    d2_pending = collect_prev;
-    if (!wait_mma()) { bail = true; break; }
+    // every thread waits itself; the time-out vote joins the barrier after
+    // the sign phase (warp-uniform: the TMEM loads are collective)
+    bool late = __any_sync(0xffffffffu, !mbar_wait_bounded(barF, phaseF));
+    phaseF ^= 1;
+    tc_fence_after();
     // (2) S = sign(D1) into shared memory; test the previous step's candidate
     float l1 = 0.f;
-    for (int ch = split; ch < nch; ch += kSplits) {
+    if (tr) {
+      // this thread: row i of the tile (lane), starts 16 split + hoff + c
+      // (columns); B z = B hi(z) + B lo(z)
+      float y[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) y[c] = 0.f;
+      uint32_t vd[8];  // B round(z) of the previous step's candidate
+      if (quarter < nch) {  // warp-uniform: the quarter holds rows of the tile
+        uint32_t vh[8], vl[8];
+        tmem_ld8x2(tmem + lane_off + 16 * split, vh);
+        if (p.nterms > 1) tmem_ld8x2(tmem + lane_off + 64 + 16 * split, vl);
+        if (collect_prev) tmem_ld8x2(tmem + lane_off + colD2 + 16 * split, vd);
+        tc_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          y[c] = p.nterms > 1 ? __uint_as_float(vh[c]) + __uint_as_float(vl[c]) : __uint_as_float(vh[c]);
+        uint32_t w[4];
+#pragma unroll
+        for (int c = 0; c < 8; c += 2) w[c >> 1] = sign_bf16x2(y[c], y[c + 1]);
+        // MN-major S: element (start rs, row i) at (i / 8) 1024 + (rs / 8) 128 + (i % 8) 16 + (rs % 8) 2
+        const int i = quarter * 16 + (lane & 15), rs = 16 * split + hoff;
+        *reinterpret_cast<uint4*>(sS + (i >> 3) * 1024 + (rs >> 3) * 128 + (i & 7) * 16) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      if (dbg_step) {  // l1 of the tile rows per start: parts 0-3 are the quarters' row sums
+        float a[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          a[c] = fabsf(y[c]);
+#pragma unroll
+          for (int o = 1; o < 16; o <<= 1) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+        }
+        if ((lane & 15) == 0)
+          for (int c = 0; c < 8; ++c) s_pl1[quarter * kTileM + 16 * split + hoff + c] = a[c];
+        if ((lane & 15) == 1)
+          for (int c = 0; c < 8; ++c) s_pl1[(quarter + 4) * kTileM + 16 * split + hoff + c] = 0.f;
+      }
+      if (collect_prev) test_candidate_tr(vd);
+    }
+    for (int ch = split; ch < nch && !tr; ch += kSplits) {
       uint32_t v[8];
       tmem_ld8x2(tmem + lane_off + ch * 16, v);
       tc_wait_ld();
@@ -477,35 +635,35 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       }
       store_row8(Sop, r, ch * 16 + hoff, n_pad, w);
     }
-    if (dbg_step) s_pl1[part * kTileM + r] = l1;
-    bool d2_late = false;
-    if (collect_prev) {
-      d2_late = __any_sync(0xffffffffu, !mbar_wait_bounded(bar2, phase2));  // warp-uniform: the loads are collective
+    if (dbg_step && !tr) s_pl1[part * kTileM + r] = l1;
+    if (collect_prev && !tr) {  // transposed: D2 came with the forward chain, tested above
+      late |= __any_sync(0xffffffffu, !mbar_wait_bounded(bar2, phase2));
       phase2 ^= 1;
-      d2_pending = false;
       tc_fence_after();
-      if (!d2_late) test_candidate();
+      if (!late) test_candidate();
     }
     tc_wait_ld();
     tc_fence_before();
     fence_async_smem();
-    if (__syncthreads_or(d2_late)) {
+    if (__syncthreads_or(late)) {
       if (tid == 0) atomicOr(p.flags, 16);
-      timed_out = true;
       bail = true;
       break;
     }
     // (3) gradient MMA, overlapped with appending the previous candidate
-    if (tid == 0) {
+    if (issuer) {
       tc_fence_after();
       for (int kk = 0; kk < nch; ++kk) {
-        uint64_t a = make_desc(smem_u32(Sop) + kk * 256, 128, sbo_n);
+        // A = S: K-major, or MN-major (transposed form; K groups 1024 bytes
+        // apart, 8-start groups 128 bytes apart)
+        uint64_t a = tr ? make_desc(smem_u32(sS) + kk * 2048, kMnLbo ? 1024 : 128, kMnLbo ? 128 : 1024)
+                        : make_desc(smem_u32(Sop) + kk * 256, 128, sbo_n);
         // K step kk covers rows 16kk..16kk+15 of B: two 8-row core-matrix groups
         uint64_t b = p.use_bb ? make_desc(smem_u32(Bb) + kk * 256, 128, sbo_n)
                               : make_desc(smem_u32(Bf) + kk * 2 * sbo_d, kMnLbo ? sbo_d : 128, kMnLbo ? 128 : sbo_d);
-        mma_bf16(tmem, a, b, idesc_bwd, kk > 0);
+        mma_bf16(tmem + colG_, a, b, idesc_bwd, kk > 0);
       }
-      mma_commit(bar);
+      mma_commit(barG);
     }
     if (collect_prev) {
       decide_slot();
@@ -518,7 +676,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       s_fnz[r] = kNoNz;
       s_fl[r] &= ~kOutId;
     }
-    if (!wait_mma()) { bail = true; break; }
+    if (!wait_grad()) { bail = true; break; }
     // (4) Adam on the FP32 master state; next operands
     // Adam in the form z -= (lr / bc1) m / (sqrt(v) / sqrt(bc2) + eps), with
     // lr / bc1 and 1 / sqrt(bc2) formed in double on the host
@@ -531,7 +689,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     const float inv_term = inv_on ? -p.lambda2 / (zinf * zinf) : 0.f;
     // G (TMEM) and the master z, m, v of coordinates c0 .. c0+7
     auto load_state = [&](int ch, int c0, uint32_t (&v)[8], float (&zc)[8], float (&mc)[8], float (&vc)[8]) {
-      tmem_ld8x2(tmem + lane_off + ch * 16, v);  // completes under the loads below
+      tmem_ld8x2(tmem + lane_off + colG_ + ch * 16, v);  // completes under the loads below
       if (kRes) {
         uint32_t tz[8], tm[8], tv[8];
         tmem_ld8x2(tmem + st_off + ch * 16, tz);
@@ -703,25 +861,37 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
 
   // the candidate of the last step
   if (!bail && p.T > 0 && ((p.t0 + p.T) % p.period == 0)) {
-    if (tid == 0) {
+    if (issuer) {
       tc_fence_after();
-      issue_d2();
-      mma_commit(bar);
+      issue_chunks(0, dch, false, true);
+      mma_commit(bar2);
     }
-    if (wait_mma()) {
+    bool late = __any_sync(0xffffffffu, !mbar_wait_bounded(bar2, phase2));
+    phase2 ^= 1;
+    tc_fence_after();
+    if (tr) {
+      uint32_t vd[8];
+      if (quarter < nch && !late) {
+        tmem_ld8x2(tmem + lane_off + colD2 + 16 * split, vd);
+        tc_wait_ld();
+      }
+      if (!late) test_candidate_tr(vd);
+    } else if (!late) {
       test_candidate();
-      tc_wait_ld();
-      __syncthreads();
+    }
+    tc_wait_ld();
+    if (__syncthreads_or(late)) {
+      if (tid == 0) atomicOr(p.flags, 16);
+    } else {
       decide_slot();
       __syncthreads();
       write_candidate();
     }
   }
-  if (timed_out) {  // let MMAs still in flight drain before TMEM is freed
-    mbar_wait_bounded(bar, phase ^ 1);
-    if (d2_pending) mbar_wait_bounded(bar2, phase2);
-  }
-  if (kRes) {  // the state leaves TMEM for the caller's arrays
+  // arrives once every MMA of the CTA has completed (all were issued by this
+  // thread); TMEM is freed only then, also after a time-out
+  if (issuer) mma_commit(barD);
+  if (kRes && state_loaded) {  // the state leaves TMEM for the caller's arrays
     for (int ch = split; ch < dch; ch += kSplits) {
       const int c0 = ch * 16 + hoff;
       uint32_t tz[8], tm[8], tv[8];
@@ -745,6 +915,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
+    mbar_wait_bounded(barD, 0);
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
   }
