@@ -13,6 +13,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <vector>
 
 namespace {
 
@@ -135,12 +136,11 @@ __global__ void bin_scan_kernel(const uint32_t* __restrict__ hist, int nbins, ui
   }
 }
 
-// sorted arrays: row index, first mask words, and the number of strictly
-// shorter rows (the start of the row's bin)
+// sorted arrays: row index, first mask words, folded signatures, l1
 __global__ void scatter_kernel(const int32_t* __restrict__ l1, const uint64_t* __restrict__ masks, int64_t K, int W,
-                               const uint32_t* __restrict__ start, uint32_t* __restrict__ cursor,
-                               uint32_t* __restrict__ s_idx, uint64_t* __restrict__ s_pk,
-                               ulonglong2* __restrict__ s_sig, uint32_t* __restrict__ s_lim) {
+                               uint32_t* __restrict__ cursor, uint32_t* __restrict__ s_idx,
+                               uint64_t* __restrict__ s_pk, ulonglong2* __restrict__ s_sig,
+                               int32_t* __restrict__ s_l1) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= K || l1[k] == kInvalidL1) return;
   uint32_t q = atomicAdd(&cursor[l1[k]], 1u);
@@ -156,7 +156,140 @@ __global__ void scatter_kernel(const int32_t* __restrict__ l1, const uint64_t* _
     neg |= masks[k * 2 * W + W + w];
   }
   s_sig[q] = make_ulonglong2(pos, neg);
-  s_lim[q] = start[l1[k]];
+  s_l1[q] = l1[k];
+}
+
+// ---- sign patterns -------------------------------------------------------------
+//
+// The pairwise test is pruned by the signs on kb key coordinates (the
+// densest, at most 6).  Each row has a pattern there: t_b = 0 (zero), 1
+// (positive), 2 (negative) on key coordinate b, index sum_b t_b 3^b.  h ⊑ g
+// needs, on every key coordinate, h zero or of g's sign (and h zero where g
+// is); -h ⊑ g the same with h's signs reversed.  So for g the candidate rows
+// h lie in the 2^|nz(g)| lists whose pattern keeps a subset N of g's nonzero
+// key coordinates, with g's signs (h ⊑ g) or the reversed ones (-h ⊑ g), and
+// zero elsewhere.  Rows are split into the 3^kb pattern lists, each kept in l1
+// order, and every row is compared only with the shorter rows of those
+// lists.  Only pairs that cannot dominate are skipped, so the kept set is the
+// one all pairs give.
+
+constexpr int kKeyCoords = 6;
+constexpr int kLists = 729;       // 3^kKeyCoords pattern lists
+constexpr int kPartBlock = 1024;  // positions per block of the stable partition
+
+// per-coordinate nonzero counts of the valid rows (64 rows per block)
+__global__ void coord_count_kernel(const int8_t* __restrict__ G, int64_t K, int n, int ldg,
+                                   const int32_t* __restrict__ l1, uint32_t* __restrict__ cnt) {
+  extern __shared__ uint32_t s_cnt[];  // n
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s_cnt[i] = 0;
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * 64;
+  for (int64_t e = threadIdx.x; e < 64 * (int64_t)n; e += blockDim.x) {
+    const int64_t k = r0 + e / n;
+    const int i = (int)(e % n);
+    if (k < K && l1[k] != kInvalidL1 && G[k * ldg + i] != 0) atomicAdd(&s_cnt[i], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (s_cnt[i]) atomicAdd(&cnt[i], s_cnt[i]);
+}
+
+// the kb densest coordinates (ties to the lower index); one block of 1024
+__global__ void select_keys_kernel(const uint32_t* __restrict__ cnt, int n, int kb, int32_t* __restrict__ keys) {
+  __shared__ unsigned long long s_best[32];
+  __shared__ int s_taken[kKeyCoords];
+  for (int b = 0; b < kb; ++b) {
+    // count in the high word, ~index in the low word: the maximum is the
+    // largest count with the lowest index
+    unsigned long long best = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      bool taken = false;
+      for (int c = 0; c < b; ++c) taken |= s_taken[c] == i;
+      if (taken) continue;
+      const unsigned long long v = ((unsigned long long)cnt[i] << 32) | (0xffffffffu - (uint32_t)i) | (1ull << 63);
+      best = v > best ? v : best;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, best, o);
+      best = w > best ? w : best;
+    }
+    if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long m = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = s_best[w] > m ? s_best[w] : m;
+      const int idx = (int)(0xffffffffu - (uint32_t)(m & 0xffffffffull));
+      s_taken[b] = idx;
+      keys[b] = idx;
+    }
+    __syncthreads();
+  }
+}
+
+// pattern list of the row at sorted position q
+__global__ void key_kernel(const int8_t* __restrict__ G, int ldg, const uint32_t* __restrict__ s_idx, int64_t nvalid,
+                           const int32_t* __restrict__ keys, int kb, uint16_t* __restrict__ s_list) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nvalid) return;
+  const int8_t* g = G + (int64_t)s_idx[q] * ldg;
+  int idx = 0, p3 = 1;
+  for (int b = 0; b < kb; ++b) {
+    const int v = g[keys[b]];
+    idx += (v > 0 ? 1 : (v < 0 ? 2 : 0)) * p3;
+    p3 *= 3;
+  }
+  s_list[q] = (uint16_t)idx;
+}
+
+// stable partition by list, step 1: counts per (list, block of positions)
+__global__ void part_count_kernel(const uint16_t* __restrict__ s_list, int64_t nvalid, int nlists, int nblk,
+                                  uint32_t* __restrict__ bc) {
+  __shared__ uint32_t s_c[kLists];
+  for (int L = threadIdx.x; L < nlists; L += blockDim.x) s_c[L] = 0;
+  __syncthreads();
+  const int64_t q = (int64_t)blockIdx.x * kPartBlock + threadIdx.x;
+  if (q < nvalid) atomicAdd(&s_c[s_list[q]], 1u);
+  __syncthreads();
+  for (int L = threadIdx.x; L < nlists; L += blockDim.x) bc[(int64_t)L * nblk + blockIdx.x] = s_c[L];
+}
+
+// step 2 (one warp per block of positions, in position order): rank among
+// the earlier rows of the same list, then move the row's sorted data
+__global__ void part_scatter_kernel(const uint16_t* __restrict__ s_list, int64_t nvalid, int nlists, int nblk,
+                                    const uint32_t* __restrict__ boff, const uint32_t* __restrict__ s_idx,
+                                    const uint64_t* __restrict__ s_pk, const ulonglong2* __restrict__ s_sig,
+                                    const int32_t* __restrict__ s_l1, uint32_t* __restrict__ p_idx,
+                                    uint64_t* __restrict__ p_pk, ulonglong2* __restrict__ p_sig,
+                                    int32_t* __restrict__ p_l1) {
+  __shared__ uint32_t s_run[kLists];
+  const int lane = threadIdx.x;
+  for (int L = lane; L < nlists; L += 32) s_run[L] = boff[(int64_t)L * nblk + blockIdx.x];
+  __syncwarp();
+  for (int it = 0; it < kPartBlock / 32; ++it) {
+    const int64_t q = (int64_t)blockIdx.x * kPartBlock + it * 32 + lane;
+    const int L = q < nvalid ? (int)s_list[q] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, L);
+    const uint32_t rank = __popc(peers & ((1u << lane) - 1));
+    uint32_t dst = 0;
+    if (L >= 0) dst = s_run[L] + rank;
+    __syncwarp();
+    if (L >= 0 && (32 - __clz(peers)) - 1 == lane) s_run[L] += __popc(peers);
+    __syncwarp();
+    if (L >= 0) {
+      p_idx[dst] = s_idx[q];
+      p_pk[dst] = s_pk[q];
+      p_sig[dst] = s_sig[q];
+      p_l1[dst] = s_l1[q];
+    }
+  }
+}
+
+// list starts: lstart[L] = boff[L * nblk], lstart[nlists] = nvalid
+__global__ void list_start_kernel(const uint32_t* __restrict__ boff, int nlists, int nblk, int64_t nvalid,
+                                  uint32_t* __restrict__ lstart) {
+  const int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L < nlists) lstart[L] = boff[(int64_t)L * nblk];
+  if (L == nlists) lstart[L] = (uint32_t)nvalid;
 }
 
 constexpr int kTile = 256;
@@ -167,7 +300,7 @@ __device__ __forceinline__ bool magnitudes_fit(const int8_t* h, const int8_t* g,
   return true;
 }
 
-// full test of h against g once the 32-coordinate prefilter passed
+// full test of h against g once the prefilters passed
 __device__ __forceinline__ bool dominates(const int8_t* __restrict__ G, int n, int ldg, int W,
                                           const uint64_t* __restrict__ masks, uint32_t h, uint32_t k) {
   const uint64_t* hm = masks + (int64_t)h * 2 * W;
@@ -181,63 +314,87 @@ __device__ __forceinline__ bool dominates(const int8_t* __restrict__ G, int n, i
   return (same || flip) && magnitudes_fit(G + (int64_t)h * ldg, G + (int64_t)k * ldg, n);
 }
 
-constexpr int kChunk = 4096;  // shorter rows scanned by one block
+constexpr int kChunk = 4096;  // rows of a source list scanned by one block
 
-// Work unit (blockIdx.x, blockIdx.y): the 256 sorted rows of row block x
-// against the shorter rows [y * kChunk, (y + 1) * kChunk).  Every unit has
-// the same size, so the quadratic work spreads evenly over the SMs however the
-// rows' limits grow along the l1 order.  Prefilters per pair: sign masks of
-// coordinates 0..31 packed in one word (pos | neg << 32), then, for the pairs
-// that pass, the folded 64-bit signatures of all coordinates, before the full
-// test.  A dominated row gets dom[k] = 1 (several units may write it).
+// Work unit (blockIdx.x, .y, .z): the up to 256 rows of g-block x (a run of
+// one pattern list) against chunk z of one source list.  y = o 2^kb + N: N
+// the key coordinates where the source rows are nonzero (a subset of g's
+// nonzero key coordinates, else the unit is empty), o = 0 for h ⊑ g (g's
+// signs) and o = 1 for -h ⊑ g (reversed signs); N = 0 takes both
+// orientations at once.  Lists are in l1 order, so a row stops at the first
+// source row that is not shorter.  Prefilters per pair: sign masks of
+// coordinates 0..31 packed in one word (pos | neg << 32), then the folded
+// 64-bit signatures of all coordinates, before the full test.  A dominated
+// row gets dom[k] = 1 (several units may write it).
 __global__ void dominance_kernel(const int8_t* __restrict__ G, int n, int ldg, int W, const uint64_t* __restrict__ masks,
-                                 int64_t nvalid, const uint32_t* __restrict__ s_idx, const uint64_t* __restrict__ s_pk,
-                                 const ulonglong2* __restrict__ s_sig, const uint32_t* __restrict__ s_lim,
+                                 const int4* __restrict__ gblk, const uint32_t* __restrict__ lstart, int kb,
+                                 const uint32_t* __restrict__ p_idx, const uint64_t* __restrict__ p_pk,
+                                 const ulonglong2* __restrict__ p_sig, const int32_t* __restrict__ p_l1,
                                  uint8_t* __restrict__ dom) {
   __shared__ uint64_t t_pk[kTile];
   __shared__ ulonglong2 t_sig[kTile];
-  __shared__ uint32_t s_blim;
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const uint32_t lo = blockIdx.y * (uint32_t)kChunk;
-  if (threadIdx.x == 0) {
-    int64_t last = blockIdx.x * (int64_t)blockDim.x + blockDim.x - 1;
-    if (last >= nvalid) last = nvalid - 1;
-    s_blim = s_lim[last];  // rows are in l1 order: the last has the largest limit
+  __shared__ int32_t t_l1[kTile];
+  __shared__ int s_maxl1;
+  const int4 gb = gblk[blockIdx.x];  // first position, rows, pattern list
+  const int nsub = 1 << kb;
+  const int o = (int)blockIdx.y / nsub, N = (int)blockIdx.y % nsub;
+  // g's pattern digits; the source pattern keeps digits in N (reversed for o = 1)
+  int nzmask = 0, S = 0;
+  {
+    int rest = gb.z, p3 = 1;
+    for (int b = 0; b < kb; ++b) {
+      const int t = rest % 3;
+      rest /= 3;
+      if (t != 0) nzmask |= 1 << b;
+      if ((N >> b) & 1) S += (o == 0 ? t : 3 - t) * p3;
+      p3 *= 3;
+    }
   }
+  if ((N & ~nzmask) != 0 || (N == 0 && o == 1)) return;  // uniform over the block
+  const int mode = N == 0 ? 3 : (o == 0 ? 1 : 2);  // bit 0: h ⊑ g, bit 1: -h ⊑ g
+  const uint32_t lo = lstart[S] + blockIdx.z * (uint32_t)kChunk, s_end = lstart[S + 1];
+  if (lo >= s_end) return;
+  const uint32_t hi = lo + kChunk < s_end ? lo + kChunk : s_end;
+  const bool mine = (int)threadIdx.x < gb.y;
+  const uint32_t q = (uint32_t)gb.x + threadIdx.x;
+  const int32_t gl1 = mine ? p_l1[q] : 0;
+  if (threadIdx.x == 0) s_maxl1 = 0;
   __syncthreads();
-  const uint32_t blim = s_blim;
-  if (lo >= blim) return;  // uniform over the block
-  const uint32_t hi = (lo + kChunk < blim) ? lo + kChunk : blim;
-  const bool mine = q < nvalid;
-  const uint32_t lim = mine ? s_lim[q] : 0;
-  const uint32_t k = mine ? s_idx[q] : 0;
-  const uint64_t pk = mine ? s_pk[q] : 0;
+  if (mine) atomicMax(&s_maxl1, gl1);
+  __syncthreads();
+  if (p_l1[lo] >= s_maxl1) return;  // no source row of the chunk is shorter than any g
+  const uint32_t k = mine ? p_idx[q] : 0;
+  const uint64_t pk = mine ? p_pk[q] : 0;
   const uint32_t np = ~(uint32_t)pk, nn = ~(uint32_t)(pk >> 32);
-  const ulonglong2 gs = mine ? s_sig[q] : make_ulonglong2(0, 0);
+  const ulonglong2 gs = mine ? p_sig[q] : make_ulonglong2(0, 0);
   const uint64_t gsp = ~gs.x, gsn = ~gs.y;
-  bool done = !mine || lim <= lo || dom[k];
+  const bool want_same = (mode & 1) != 0, want_flip = (mode & 2) != 0;
+  bool done = !mine || dom[k];
   for (uint32_t base = lo; base < hi; base += kTile) {
     __syncthreads();
     for (int t = threadIdx.x; t < kTile; t += blockDim.x) {
-      uint32_t h = base + t;
+      const uint32_t h = base + t;
       if (h < hi) {
-        t_pk[t] = s_pk[h];
-        t_sig[t] = s_sig[h];
+        t_pk[t] = p_pk[h];
+        t_sig[t] = p_sig[h];
+        t_l1[t] = p_l1[h];
+      } else {
+        t_l1[t] = 0x7fffffff;
       }
     }
     __syncthreads();
     if (done) continue;
-    const uint32_t stop = lim < hi ? lim : hi;
-    const int cnt = stop > base ? (int)((stop - base) < (uint32_t)kTile ? (stop - base) : (uint32_t)kTile) : 0;
 #pragma unroll 4
-    for (int t = 0; t < cnt; ++t) {
+    for (int t = 0; t < kTile; ++t) {
+      if (t_l1[t] >= gl1) break;  // the rest of the list is not shorter
       const uint64_t hk = t_pk[t];
       const uint32_t hp = (uint32_t)hk, hn = (uint32_t)(hk >> 32);
-      const bool cand = (((hp & np) | (hn & nn)) == 0) || (((hp & nn) | (hn & np)) == 0);
+      const bool cand = (want_same && ((hp & np) | (hn & nn)) == 0) || (want_flip && ((hp & nn) | (hn & np)) == 0);
       if (!cand) continue;
       const ulonglong2 hs = t_sig[t];
-      const bool cand2 = (((hs.x & gsp) | (hs.y & gsn)) == 0) || (((hs.x & gsn) | (hs.y & gsp)) == 0);
-      if (cand2 && dominates(G, n, ldg, W, masks, s_idx[base + t], k)) {
+      const bool cand2 = (want_same && ((hs.x & gsp) | (hs.y & gsn)) == 0) ||
+                         (want_flip && ((hs.x & gsn) | (hs.y & gsp)) == 0);
+      if (cand2 && dominates(G, n, ldg, W, masks, p_idx[base + t], k)) {
         done = true;
         dom[k] = 1;
         break;
@@ -333,16 +490,28 @@ extern "C" size_t mape_minimal_workspace_bytes(int64_t K, int32_t n) {
   if (K < 0 || n <= 0) return 0;
   int W = (n + 63) / 64;
   int64_t nb = l1_bins(n);
+  const int64_t nblk_part = ceil_div(K, kPartBlock);
   Sizer s;
   s.take<int32_t>((size_t)K);                 // l1
   s.take<uint64_t>((size_t)K * 2 * W);        // masks
   s.take<uint32_t>((size_t)nb);               // histogram
   s.take<uint32_t>((size_t)nb);               // bin starts
   s.take<uint32_t>((size_t)nb);               // cursors
-  s.take<uint32_t>((size_t)K);                // sorted row index
-  s.take<uint64_t>((size_t)K);                // sorted packed sign masks
-  s.take<ulonglong2>((size_t)K);              // sorted folded signatures
-  s.take<uint32_t>((size_t)K);                // sorted limits
+  s.take<uint32_t>((size_t)K);                // l1-sorted: row index
+  s.take<uint64_t>((size_t)K);                //   packed sign masks
+  s.take<ulonglong2>((size_t)K);              //   folded signatures
+  s.take<int32_t>((size_t)K);                 //   l1
+  s.take<uint16_t>((size_t)K);                //   list
+  s.take<uint32_t>((size_t)K);                // partitioned by list: row index
+  s.take<uint64_t>((size_t)K);                //   packed sign masks
+  s.take<ulonglong2>((size_t)K);              //   folded signatures
+  s.take<int32_t>((size_t)K);                 //   l1
+  s.take<uint32_t>((size_t)n);                // coordinate nonzero counts
+  s.take<int32_t>((size_t)kKeyCoords);        // key coordinates
+  s.take<uint32_t>((size_t)kLists * nblk_part);      // counts per (list, block)
+  s.take<uint32_t>((size_t)kLists * nblk_part + 1);  // their exclusive prefix
+  s.take<uint32_t>((size_t)kLists + 1);              // list starts
+  s.take<int4>((size_t)ceil_div(K, kTile) + kLists);  // g-blocks
   s.take<uint32_t>((size_t)ceil_div(K, kCompact) + 1);  // block counts
   s.take<uint32_t>((size_t)ceil_div(K, kCompact) + 1);  // block starts
   return s.bytes();
@@ -361,6 +530,10 @@ extern "C" int mape_minimal_filter(const int8_t* G, int64_t K, int32_t n, int32_
   const int W = (n + 63) / 64;
   const int64_t nb = l1_bins(n);
   const int64_t nblk = ceil_div(K, kCompact);
+  const int64_t nblk_part_max = ceil_div(K, kPartBlock);
+  const int kb = n < kKeyCoords ? n : kKeyCoords;
+  int nlists = 1;
+  for (int b = 0; b < kb; ++b) nlists *= 3;
   Carver cv(workspace, workspace_bytes);
   int32_t* l1 = cv.take<int32_t>((size_t)K);
   uint64_t* masks = cv.take<uint64_t>((size_t)K * 2 * W);
@@ -370,18 +543,33 @@ extern "C" int mape_minimal_filter(const int8_t* G, int64_t K, int32_t n, int32_
   uint32_t* s_idx = cv.take<uint32_t>((size_t)K);
   uint64_t* s_pk = cv.take<uint64_t>((size_t)K);
   ulonglong2* s_sig = cv.take<ulonglong2>((size_t)K);
-  uint32_t* s_lim = cv.take<uint32_t>((size_t)K);
+  int32_t* s_l1 = cv.take<int32_t>((size_t)K);
+  uint16_t* s_list = cv.take<uint16_t>((size_t)K);
+  uint32_t* p_idx = cv.take<uint32_t>((size_t)K);
+  uint64_t* p_pk = cv.take<uint64_t>((size_t)K);
+  ulonglong2* p_sig = cv.take<ulonglong2>((size_t)K);
+  int32_t* p_l1 = cv.take<int32_t>((size_t)K);
+  uint32_t* cnt = cv.take<uint32_t>((size_t)n);
+  int32_t* keys = cv.take<int32_t>((size_t)kKeyCoords);
+  uint32_t* bc = cv.take<uint32_t>((size_t)kLists * nblk_part_max);
+  uint32_t* boff = cv.take<uint32_t>((size_t)kLists * nblk_part_max + 1);
+  uint32_t* lstart = cv.take<uint32_t>((size_t)kLists + 1);
+  int4* gblk = cv.take<int4>((size_t)ceil_div(K, kTile) + kLists);
   uint32_t* bcount = cv.take<uint32_t>((size_t)nblk + 1);
   uint32_t* bstart = cv.take<uint32_t>((size_t)nblk + 1);
   if (!cv.ok) return MAPE_ERR_CAPACITY;
   cudaStream_t st = as_stream(stream);
   MAPE_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * nb, st));
   MAPE_CUDA_TRY(cudaMemsetAsync(bcount, 0, sizeof(uint32_t) * (nblk + 1), st));
+  MAPE_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n, st));
   const unsigned g = (unsigned)ceil_div(K, kTile);
   mape_detail::launch(prep_kernel, g, kTile, 0, st, G, K, n, ldg, W, valid, l1, masks, hist);
   mape_detail::launch(bin_scan_kernel, 1, 1024, 0, st, hist, (int)nb, start, cursor);
-  mape_detail::launch(scatter_kernel, g, kTile, 0, st, l1, masks, K, W, start, cursor, s_idx, s_pk, s_sig, s_lim);
+  mape_detail::launch(scatter_kernel, g, kTile, 0, st, l1, masks, K, W, cursor, s_idx, s_pk, s_sig, s_l1);
   mape_detail::launch(clear_keep_kernel, g, kTile, 0, st, keep, K);
+  mape_detail::launch(coord_count_kernel, (unsigned)ceil_div(K, 64), 256, sizeof(uint32_t) * n, st, G, K, n, ldg, l1,
+                      cnt);
+  mape_detail::launch(select_keys_kernel, 1, 1024, 0, st, cnt, n, kb, keys);
   MAPE_LAUNCH_CHECK();
   // number of valid rows = end of the last bin
   uint32_t last_start = 0, last_count = 0;
@@ -389,9 +577,37 @@ extern "C" int mape_minimal_filter(const int8_t* G, int64_t K, int32_t n, int32_
   MAPE_CUDA_TRY(cudaMemcpyAsync(&last_count, hist + nb - 1, 4, cudaMemcpyDeviceToHost, st));
   MAPE_CUDA_TRY(cudaStreamSynchronize(st));
   const int64_t nvalid = (int64_t)last_start + last_count;
-  if (nvalid > 0)
-    mape_detail::launch(dominance_kernel, dim3((unsigned)ceil_div(nvalid, kTile), (unsigned)ceil_div(nvalid, kChunk)),
-                        kTile, 0, st, G, n, ldg, W, masks, nvalid, s_idx, s_pk, s_sig, s_lim, keep);
+  if (nvalid > 0) {
+    // pattern lists, each in l1 order (stable partition of the l1 order)
+    const int nblk_part = (int)ceil_div(nvalid, kPartBlock);
+    mape_detail::launch(key_kernel, (unsigned)ceil_div(nvalid, kTile), kTile, 0, st, G, ldg, s_idx, nvalid, keys, kb,
+                        s_list);
+    mape_detail::launch(part_count_kernel, (unsigned)nblk_part, kPartBlock, 0, st, s_list, nvalid, nlists, nblk_part,
+                        bc);
+    mape_detail::launch(bin_scan_kernel, 1, 1024, 0, st, bc, nlists * nblk_part, boff, boff);
+    mape_detail::launch(part_scatter_kernel, (unsigned)nblk_part, 32, 0, st, s_list, nvalid, nlists, nblk_part, boff,
+                        s_idx, s_pk, s_sig, s_l1, p_idx, p_pk, p_sig, p_l1);
+    mape_detail::launch(list_start_kernel, (unsigned)ceil_div(nlists + 1, 256), 256, 0, st, boff, nlists, nblk_part,
+                        nvalid, lstart);
+    MAPE_LAUNCH_CHECK();
+    std::vector<uint32_t> ls((size_t)nlists + 1);
+    MAPE_CUDA_TRY(cudaMemcpyAsync(ls.data(), lstart, sizeof(uint32_t) * ls.size(), cudaMemcpyDeviceToHost, st));
+    MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+    // g-blocks: runs of at most kTile rows of one list
+    std::vector<int4> gb;
+    uint32_t max_list = 0;
+    for (int L = 0; L < nlists; ++L) {
+      const uint32_t a = ls[L], b = ls[L + 1];
+      max_list = std::max(max_list, b - a);
+      for (uint32_t o = a; o < b; o += kTile) gb.push_back(make_int4((int)o, (int)std::min<uint32_t>(kTile, b - o), L, 0));
+    }
+    if (!gb.empty()) {
+      MAPE_CUDA_TRY(cudaMemcpyAsync(gblk, gb.data(), sizeof(int4) * gb.size(), cudaMemcpyHostToDevice, st));
+      const dim3 grid((unsigned)gb.size(), 2u << kb, (unsigned)ceil_div(max_list, kChunk));
+      mape_detail::launch(dominance_kernel, grid, kTile, 0, st, G, n, ldg, W, masks, gblk, lstart, kb, p_idx, p_pk,
+                          p_sig, p_l1, keep);
+    }
+  }
   mape_detail::launch(finalize_keep_kernel, g, kTile, 0, st, l1, keep, K, keep);
   mape_detail::launch(count_kept_kernel, (unsigned)nblk, kCompact, 0, st, keep, K, bcount);
   // block starts: exclusive prefix of the counts, entry nblk = total

@@ -195,6 +195,46 @@ def test_minimal_filter_exact(M, K, n):
     assert 0 < expect.sum() < valid.sum()
 
 
+def _planted_dense(rng, K, n):
+    """Dense rows (about 5% zeros; half the rows zero on coordinates 0-1),
+    plus rows s with a ⊑ s and, for about half of them, -a ⊑ s with s
+    canonical through an extra leading entry where a is zero: pairs meet in
+    the pattern lists of the key coordinates in both orientations, with and
+    without zeros there."""
+    base = rng.integers(1, 4, size=(K, n)) * rng.choice([-1, 1], size=(K, n))
+    base = base * (rng.random((K, n)) > 0.05)
+    base[:, :2] *= (rng.random((K, 1)) < 0.5)
+    base = base[np.any(base != 0, axis=1)]
+    base = np.array([O.canonical_sign(g) for g in base])
+    extra = []
+    for _ in range(K // 3):
+        a = base[rng.integers(0, base.shape[0])]
+        s = a + np.sign(a) * rng.integers(0, 3, size=n)  # a ⊑ s
+        if rng.random() < 0.5 and a[0] == 0:
+            s = -s
+            s[0] = rng.integers(1, 3)  # canonical; -a ⊑ s
+        extra.append(s)
+    G = np.concatenate([base, np.array(extra)])
+    G = np.array([O.canonical_sign(g) for g in G])
+    return O.sort_directions(np.unique(G[np.any(G != 0, axis=1)], axis=0))
+
+
+@pytest.mark.parametrize("K,n", [(2000, 64), (1000, 200), (400, 5)])
+def test_minimal_filter_dense_buckets(M, K, n):
+    """Dense rows spread the set over the sign-pattern lists of the key
+    coordinates; the kept set equals the brute-force ⊑-minimal set."""
+    rng = np.random.default_rng(7 * K + n)
+    G = _planted_dense(rng, K, n)
+    ldg = M.round16(n)
+    buf = np.zeros((G.shape[0], ldg), np.int8)
+    buf[:, :n] = G
+    keep, out = M.minimal_filter(dev(buf), n)
+    expect = O.minimal_elements(G)
+    assert np.array_equal(keep.cpu().numpy().astype(bool), expect)
+    assert np.array_equal(out.cpu().numpy()[:, :n].astype(np.int64), G[expect])
+    assert 0 < expect.sum() < G.shape[0]
+
+
 # --- a12-a14 ---------------------------------------------------------------------
 
 def _directions_for(inst, P=256, T=60, seed=2001):
