@@ -268,9 +268,14 @@ def run_ours(args):
     units_all, ms_max = reduce_over_ranks(directions, total_ms, world)
     value = units_all / (ms_max / 1e3)
 
-    # e2e: the public handle API with host buffers, every copy inside the region
-    G0_host = starts.G0
+    # e2e: the public handle API with host buffers, every copy inside the
+    # region: the instance and the starts go up from pinned host memory, the
+    # direction set (int8 rows) and the best point come back into pinned
+    # host memory (buffers pinned once, before the region)
+    G0_host = torch.from_numpy(np.ascontiguousarray(starts.G0)).pin_memory().numpy()
     x0_host = inst.xbar[None, :].astype(np.int32)
+    D_host = torch.empty((max(2 * int(directions / max(args.steps, 1)), 1024), inst.n),
+                         dtype=torch.int8).pin_memory().numpy()
     e2e_times, e2e_units = [], 0
     h2d = (inst.A.nbytes + inst.b.nbytes + inst.l.nbytes + inst.u.nbytes + inst.B.nbytes + inst.Q.nbytes
            + inst.c.nbytes + G0_host.nbytes + x0_host.nbytes)
@@ -283,7 +288,7 @@ def run_ours(args):
             he.wait(600)
             he.augment(x0_host)
             he.wait(600)
-            D = he.directions()
+            D = he.directions_i8(out=D_host)
             x, fx = he.solution()
         e2e_times.append(time.perf_counter() - t0)
         e2e_units += D.shape[0]

@@ -473,6 +473,13 @@ int mape_cancel(mape_handle h);                          /* stops at next stage
  * G [cap x n].  CAPACITY if cap < K (K is still set). */
 int mape_get_directions(mape_handle h, int32_t* G, int64_t cap, int64_t* K);
 
+/* The same rows as int8, the library's own storage type (every entry lies in
+ * the box spans of C4, |g_i| <= 127): row k at G + k * ldg_out, n bytes each
+ * (ldg_out >= n).  One strided device-to-host copy, no conversion; pinned
+ * host memory makes it a single DMA.  CAPACITY if cap < K (K is still set);
+ * INVALID_ARG if ldg_out < n. */
+int mape_get_directions_i8(mape_handle h, int8_t* G, int64_t cap, int64_t ldg_out, int64_t* K);
+
 /* Copies the best solution x [n] and f(x) of the last augment. */
 int mape_get_solution(mape_handle h, int32_t* x, int64_t* fval);
 

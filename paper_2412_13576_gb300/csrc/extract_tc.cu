@@ -172,7 +172,7 @@ __host__ __device__ inline Smem smem_layout(int n_pad, int d_pad, int nterms, in
   s.fnz = o;  o = al(o + kTileM * 4, 128);
   s.slot = o; o = al(o + kTileM * 8, 128);
   s.misc = o; o = al(o + 16, 16);  // out-of-box mask of the transposed test, any-slot flag
-  s.bar = o;  o = al(o + 32, 16);  // mbarriers: gradient, B round(z), forward, drain
+  s.bar = o;  o = al(o + 40, 16);  // mbarriers: gradient, B round(z), forward, drain, early chunks
   s.tmem = o; o = al(o + 4, 16);
   s.total = o;
   return s;
@@ -245,6 +245,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
   }
   if (tid == 0) {
     for (int b = 0; b < 4; ++b) mbar_init(bar + 8 * b, 1);
+    mbar_init(bar + 32, kWarps);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
@@ -275,7 +276,17 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
   const uint32_t colG_ = tr ? al(64u * (uint32_t)(p.nterms + 1), 32) : 0u;
   const uint32_t colD2 = tr ? 64u * (uint32_t)p.nterms : (uint32_t)kColD2;
   const bool issuer = tid == kIssuer;
-  const uint32_t barG = bar, bar2 = bar + 8, barF = bar + 16, barD = bar + 24;
+  const uint32_t barG = bar, bar2 = bar + 8, barF = bar + 16, barD = bar + 24, barE = bar + 32;
+  // Transposed form: when the last of the epilogue's rounds of 4 chunks
+  // leaves split 3 (the issuer's) without a chunk, the forward chain's MMAs
+  // for the chunks of the earlier rounds are issued as soon as all 16 warps
+  // have written those chunks (barrier barE), while splits 0-1 still work on
+  // the last round; the rest follow at the top of the next step.  The chain
+  // and its order are the same either way.
+  const int n_rounds = (dch + kSplits - 1) / kSplits;
+  const int k_early = (tr && n_rounds >= 2 && dch - kSplits * (n_rounds - 1) < kSplits) ? kSplits * (n_rounds - 1) : 0;
+  int issued_early = 0;  // issuer: forward chunks already issued for the coming step, -1 after a time-out
+  uint32_t phaseE = 0;
 
   // FP32 master state of this thread's start: blocked [tile][d_pad/4][64][4],
   // four consecutive coordinates per 16-byte access, coalesced over 16 starts
@@ -567,15 +578,16 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     const bool collect_prev = s >= 1 && ((t - 1) % p.period == 0);
     const bool dbg_step = dbg_on && s == 0;
     // (1) forward MMAs (and B round(z) of the previous step's candidate)
-    if (issuer) {
+    if (issuer && issued_early >= 0) {
       tc_fence_after();
-      issue_chunks(0, dch, true, tr && collect_prev);  // transposed: one chain
+      issue_chunks(issued_early, dch, true, tr && collect_prev);  // transposed: one chain
       mma_commit(barF);
       if (!tr && collect_prev) {
         issue_chunks(0, dch, false, true);
         mma_commit(bar2);
       }
     }
+    issued_early = 0;
     // every thread waits itself; the time-out vote joins the barrier after
     // the sign phase (warp-uniform: the TMEM loads are collective)
     bool late = __any_sync(0xffffffffu, !mbar_wait_bounded(barF, phaseF));
@@ -687,6 +699,8 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     // 0 < ||z||_inf < 1; kmax is the 8-column group holding that maximiser.
     const bool inv_on = zinf < 1.f && zinf > 0.f;
     const float inv_term = inv_on ? -p.lambda2 / (zinf * zinf) : 0.f;
+    const bool early = k_early > 0 && s + 1 < p.T;  // CTA-uniform
+    const bool d2_next = t % p.period == 0;         // the next step collects this step's candidate
     // G (TMEM) and the master z, m, v of coordinates c0 .. c0+7
     auto load_state = [&](int ch, int c0, uint32_t (&v)[8], float (&zc)[8], float (&mc)[8], float (&vc)[8]) {
       tmem_ld8x2(tmem + lane_off + colG_ + ch * 16, v);  // completes under the loads below
@@ -835,6 +849,22 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       store_row8(A1, r, c0, d_pad, w1);
       if (p.nterms > 1) store_row8(A1lo, r, c0, d_pad, wl);
       store_row8(A2, r, c0, d_pad, w2);
+      if (early && ch + kSplits == k_early + split) {  // this warp's chunks before the last round are written
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(barE);
+        if (issuer) {
+          const bool ok = mbar_wait_bounded(barE, phaseE);
+          phaseE ^= 1;
+          if (ok) {
+            tc_fence_after();
+            issue_chunks(0, k_early, true, d2_next);
+            issued_early = k_early;
+          } else {
+            issued_early = -1;  // no commit: the forward wait times out and the CTA stops
+          }
+        }
+      }
     }
     s_pz[part * kTileM + r] = nzinf;
     s_pk[part * kTileM + r] = nkmax;

@@ -107,32 +107,39 @@ __global__ void prep_kernel(const int8_t* __restrict__ G, int64_t K, int n, int 
   if (v_ok) atomicAdd(&hist[s], 1u);
 }
 
-// exclusive prefix over bins (one block); cursor receives a copy of the starts
+// exclusive prefix over bins (one block of 1024); cursor receives a copy of
+// the starts.  Each thread sums a contiguous segment, the 1024 segment sums
+// are scanned with warp shuffles, and each thread writes its segment.
 __global__ void bin_scan_kernel(const uint32_t* __restrict__ hist, int nbins, uint32_t* __restrict__ start,
                                 uint32_t* __restrict__ cursor) {
-  __shared__ uint32_t s_part[1024];
-  __shared__ uint32_t s_base;
-  if (threadIdx.x == 0) s_base = 0;
+  __shared__ uint32_t s_warp[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int per = (nbins + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int b0 = tid * per, b1 = min(b0 + per, nbins);
+  uint32_t sum = 0;
+  for (int b = b0; b < b1; ++b) sum += hist[b];
+  uint32_t x = sum;  // inclusive scan over the warp
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[wid] = x;
   __syncthreads();
-  for (int b0 = 0; b0 < nbins; b0 += blockDim.x) {
-    int b = b0 + threadIdx.x;
-    uint32_t v = b < nbins ? hist[b] : 0;
-    s_part[threadIdx.x] = v;
-    __syncthreads();
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {  // Hillis-Steele inclusive scan
-      uint32_t add = threadIdx.x >= (unsigned)off ? s_part[threadIdx.x - off] : 0;
-      __syncthreads();
-      s_part[threadIdx.x] += add;
-      __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
     }
-    uint32_t excl = s_base + s_part[threadIdx.x] - v;
-    __syncthreads();
-    if (b < nbins) {
-      start[b] = excl;
-      cursor[b] = excl;
-    }
-    if (threadIdx.x == blockDim.x - 1) s_base += s_part[threadIdx.x];
-    __syncthreads();
+    s_warp[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  uint32_t run = x - sum + (wid > 0 ? s_warp[wid - 1] : 0);  // exclusive start of this segment
+  for (int b = b0; b < b1; ++b) {
+    const uint32_t v = hist[b];
+    start[b] = run;
+    cursor[b] = run;
+    run += v;
   }
 }
 
@@ -176,8 +183,11 @@ __global__ void scatter_kernel(const int32_t* __restrict__ l1, const uint64_t* _
 constexpr int kKeyCoords = 6;
 constexpr int kLists = 729;       // 3^kKeyCoords pattern lists
 constexpr int kPartBlock = 1024;  // positions per block of the stable partition
+constexpr int64_t kDensitySample = 16384;  // rows that choose the key coordinates
 
-// per-coordinate nonzero counts of the valid rows (64 rows per block)
+// per-coordinate nonzero counts of the valid rows among the first rows (64
+// rows per block); any choice of key coordinates gives the same kept set, so
+// a sample is enough to find the densest
 __global__ void coord_count_kernel(const int8_t* __restrict__ G, int64_t K, int n, int ldg,
                                    const int32_t* __restrict__ l1, uint32_t* __restrict__ cnt) {
   extern __shared__ uint32_t s_cnt[];  // n
@@ -567,8 +577,9 @@ extern "C" int mape_minimal_filter(const int8_t* G, int64_t K, int32_t n, int32_
   mape_detail::launch(bin_scan_kernel, 1, 1024, 0, st, hist, (int)nb, start, cursor);
   mape_detail::launch(scatter_kernel, g, kTile, 0, st, l1, masks, K, W, cursor, s_idx, s_pk, s_sig, s_l1);
   mape_detail::launch(clear_keep_kernel, g, kTile, 0, st, keep, K);
-  mape_detail::launch(coord_count_kernel, (unsigned)ceil_div(K, 64), 256, sizeof(uint32_t) * n, st, G, K, n, ldg, l1,
-                      cnt);
+  const int64_t K_sample = K < kDensitySample ? K : kDensitySample;
+  mape_detail::launch(coord_count_kernel, (unsigned)ceil_div(K_sample, 64), 256, sizeof(uint32_t) * n, st, G, K_sample,
+                      n, ldg, l1, cnt);
   mape_detail::launch(select_keys_kernel, 1, 1024, 0, st, cnt, n, kb, keys);
   MAPE_LAUNCH_CHECK();
   // number of valid rows = end of the last bin

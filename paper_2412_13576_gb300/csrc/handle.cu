@@ -542,6 +542,25 @@ extern "C" int mape_get_directions(mape_handle h, int32_t* G, int64_t cap, int64
   return MAPE_OK;
 }
 
+extern "C" int mape_get_directions_i8(mape_handle h, int8_t* G, int64_t cap, int64_t ldg_out, int64_t* K) {
+  using namespace mape_detail;
+  if (!h || !K) return MAPE_ERR_INVALID_ARG;
+  if (!idle(h)) return MAPE_ERR_STATE;
+  *K = h->K;
+  if (h->dirs == nullptr) return MAPE_ERR_STATE;
+  if (cap < h->K) return MAPE_ERR_CAPACITY;
+  if (h->K == 0) return MAPE_OK;
+  if (!G || ldg_out < h->n) return MAPE_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpy2DAsync(G, (size_t)ldg_out, h->dirs, (size_t)h->ldg, (size_t)h->n, (size_t)h->K,
+                                    cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    record_cuda_error(e, "get_directions_i8", __FILE__, __LINE__);
+    return MAPE_ERR_CUDA;
+  }
+  return MAPE_OK;
+}
+
 extern "C" int mape_get_solution(mape_handle h, int32_t* x, int64_t* fval) {
   if (!h || !x || !fval) return MAPE_ERR_INVALID_ARG;
   if (!idle(h)) return MAPE_ERR_STATE;

@@ -171,6 +171,7 @@ _SIGS = {
     "mape_wait": (C.c_int, [P_, I64]),
     "mape_cancel": (C.c_int, [P_]),
     "mape_get_directions": (C.c_int, [P_, P_, I64, C.POINTER(I64)]),
+    "mape_get_directions_i8": (C.c_int, [P_, P_, I64, I64, C.POINTER(I64)]),
     "mape_get_solution": (C.c_int, [P_, P_, C.POINTER(I64)]),
     "mape_get_solutions": (C.c_int, [P_, P_, P_, I32]),
     "mape_destroy": (None, [P_]),
@@ -516,6 +517,24 @@ class Instance:
         out = np.empty((K.value, self.n), dtype=np.int32)
         _check(lib().mape_get_directions(self.h, _host(out), K.value, C.byref(K)), "mape_get_directions")
         return out
+
+    def directions_i8(self, out=None) -> np.ndarray:
+        """The direction set as int8 rows [K x n] (no conversion on the
+        device).  `out` may be a caller-owned host array (e.g. the numpy view
+        of a pinned torch tensor) with at least K rows of at least n int8;
+        the rows are written there and a view of the first K is returned."""
+        K = I64(0)
+        rc = lib().mape_get_directions_i8(self.h, None, 0, self.n, C.byref(K))
+        if rc not in (OK, -7):
+            _check(rc, "mape_get_directions_i8")
+        if out is None:
+            out = np.empty((K.value, self.n), dtype=np.int8)
+        if out.dtype != np.int8 or out.ndim != 2 or out.shape[0] < K.value or out.shape[1] < self.n \
+                or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a C-contiguous int8 array of at least K x n")
+        _check(lib().mape_get_directions_i8(self.h, out.ctypes.data_as(C.c_void_p), out.shape[0], out.shape[1],
+                                            C.byref(K)), "mape_get_directions_i8")
+        return out[: K.value, : self.n]
 
     def initial_solutions(self, X0, T=1000, period=1):
         """Eq. (4) from the starts X0 [P x n] (host float32): the distinct

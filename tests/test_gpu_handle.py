@@ -45,6 +45,14 @@ def test_handle_small(M, precision):
         check_direction_set(inst, D)
         assert np.all(O.minimal_elements(D))
         assert s["directions"] == D.shape[0] <= s["unique"] <= s["candidates"]
+        # the int8 copy: the same rows, into a wider caller buffer
+        D8 = h.directions_i8()
+        assert D8.dtype == np.int8 and np.array_equal(D8.astype(np.int32), D)
+        wide = np.full((D.shape[0] + 3, inst.n + 5), 77, dtype=np.int8)
+        D8w = h.directions_i8(out=wide)
+        assert np.array_equal(D8w, D8) and np.all(wide[:, inst.n:] == 77) and np.all(wide[D.shape[0]:] == 77)
+        with pytest.raises(ValueError):
+            h.directions_i8(out=np.zeros((max(D.shape[0] - 1, 0), inst.n), dtype=np.int8))
         assert s["kernel_failures"] == 0
         h.augment(inst.xbar[None, :])
         h.wait(300)
