@@ -40,6 +40,7 @@
 
 #include <cuda_bf16.h>
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <memory>
 #include <vector>
@@ -74,6 +75,14 @@ __device__ __forceinline__ uint32_t op_off(int r, int k, int K) {
 __device__ __forceinline__ void store_row8(uint8_t* tile, int r, int k0, int K, const uint32_t (&w)[4]) {
   *reinterpret_cast<uint4*>(tile + op_off(r, k0, K)) = make_uint4(w[0], w[1], w[2], w[3]);
 }
+// W bf16 (W = 8 or 4; k0 a multiple of W) of row r
+template <int W>
+__device__ __forceinline__ void store_roww(uint8_t* tile, int r, int k0, int K, const uint32_t (&w)[W / 2]) {
+  if constexpr (W == 8) *reinterpret_cast<uint4*>(tile + op_off(r, k0, K)) = make_uint4(w[0], w[1], w[2], w[3]);
+  else *reinterpret_cast<uint2*>(tile + op_off(r, k0, K)) = make_uint2(w[0], w[1]);
+}
+template <int W>
+using Width = std::integral_constant<int, W>;
 
 // sign as a float: +-1, and 0 for 0 (and NaN)
 __device__ __forceinline__ float sgn1(float x) { return fabsf(x) > 0.f ? copysignf(1.f, x) : 0.f; }
@@ -172,7 +181,7 @@ __host__ __device__ inline Smem smem_layout(int n_pad, int d_pad, int nterms, in
   s.fnz = o;  o = al(o + kTileM * 4, 128);
   s.slot = o; o = al(o + kTileM * 8, 128);
   s.misc = o; o = al(o + 16, 16);  // out-of-box mask of the transposed test, any-slot flag
-  s.bar = o;  o = al(o + 40, 16);  // mbarriers: gradient, B round(z), forward, drain, early chunks
+  s.bar = o;  o = al(o + 32, 16);  // mbarriers: gradient, B round(z), forward, drain
   s.tmem = o; o = al(o + 4, 16);
   s.total = o;
   return s;
@@ -245,7 +254,6 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
   }
   if (tid == 0) {
     for (int b = 0; b < 4; ++b) mbar_init(bar + 8 * b, 1);
-    mbar_init(bar + 32, kWarps);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
@@ -276,17 +284,20 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
   const uint32_t colG_ = tr ? al(64u * (uint32_t)(p.nterms + 1), 32) : 0u;
   const uint32_t colD2 = tr ? 64u * (uint32_t)p.nterms : (uint32_t)kColD2;
   const bool issuer = tid == kIssuer;
-  const uint32_t barG = bar, bar2 = bar + 8, barF = bar + 16, barD = bar + 24, barE = bar + 32;
-  // Transposed form: when the last of the epilogue's rounds of 4 chunks
-  // leaves split 3 (the issuer's) without a chunk, the forward chain's MMAs
-  // for the chunks of the earlier rounds are issued as soon as all 16 warps
-  // have written those chunks (barrier barE), while splits 0-1 still work on
-  // the last round; the rest follow at the top of the next step.  The chain
-  // and its order are the same either way.
+  const uint32_t barG = bar, bar2 = bar + 8, barF = bar + 16, barD = bar + 24;
+  // Column units of the initial pass and the epilogue, split u % 4 taking
+  // unit u: 16 columns (8 per half-warp) for the rounds of four chunks; a last
+  // round of fewer than four chunks is cut into units of 8 columns (4 per
+  // half-warp), so that every split gets a share of it (with d_pad = 160 each
+  // thread has 20 coordinates instead of 24 or 16).  Unit u covers columns
+  // [ub, ub + 16) or [ub, ub + 8); the thread's own columns start at ub + W half.
   const int n_rounds = (dch + kSplits - 1) / kSplits;
-  const int k_early = (tr && n_rounds >= 2 && dch - kSplits * (n_rounds - 1) < kSplits) ? kSplits * (n_rounds - 1) : 0;
-  int issued_early = 0;  // issuer: forward chunks already issued for the coming step, -1 after a time-out
-  uint32_t phaseE = 0;
+  const int last_chunks = dch - kSplits * (n_rounds - 1);
+  const int nu16 = last_chunks < kSplits ? kSplits * (n_rounds - 1) : dch;
+  const int nu = last_chunks < kSplits ? nu16 + 2 * last_chunks : nu16;
+  // A row's largest |z_j| is tracked per W-column group (the thread's columns
+  // of one unit); the group bases are the same in every pass, so the group
+  // holding the first maximiser is found again in the next epilogue.
 
   // FP32 master state of this thread's start: blocked [tile][d_pad/4][64][4],
   // four consecutive coordinates per 16-byte access, coalesced over 16 starts
@@ -337,18 +348,19 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       }
     }
   };
-  for (int ch = split; ch < dch && !bail; ch += kSplits) {
-    const int c0 = ch * 16 + hoff;
-    float zc[8];
+  auto init_unit = [&](auto Wc, int ub) {
+    constexpr int W = decltype(Wc)::value;
+    const int c0 = ub + W * half;
+    float zc[W];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < W / 4; ++k) {
       const float4 qz = zb[(c0 / 4 + k) * kTileM];
       zc[4 * k] = qz.x; zc[4 * k + 1] = qz.y; zc[4 * k + 2] = qz.z; zc[4 * k + 3] = qz.w;
     }
     if (kRes) {
-      uint32_t wz[8], wm[8], wv[8];
+      uint32_t wz[W], wm[W], wv[W];
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
+      for (int k = 0; k < W / 4; ++k) {
         const float4 qm = mb[(c0 / 4 + k) * kTileM], qv = vb[(c0 / 4 + k) * kTileM];
         wm[4 * k] = __float_as_uint(qm.x); wm[4 * k + 1] = __float_as_uint(qm.y);
         wm[4 * k + 2] = __float_as_uint(qm.z); wm[4 * k + 3] = __float_as_uint(qm.w);
@@ -356,14 +368,14 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
         wv[4 * k + 2] = __float_as_uint(qv.z); wv[4 * k + 3] = __float_as_uint(qv.w);
       }
 #pragma unroll
-      for (int c = 0; c < 8; ++c) wz[c] = __float_as_uint(zc[c]);
-      tmem_st8x2(tmem + st_off + ch * 16, wz);
-      tmem_st8x2(tmem + st_off + col_m + ch * 16, wm);
-      tmem_st8x2(tmem + st_off + col_v + ch * 16, wv);
+      for (int c = 0; c < W; ++c) wz[c] = __float_as_uint(zc[c]);
+      tmem_stw<W>(tmem + st_off + ub, wz);
+      tmem_stw<W>(tmem + st_off + col_m + ub, wm);
+      tmem_stw<W>(tmem + st_off + col_v + ub, wv);
     }
-    uint32_t wh[4], wl[4];
+    uint32_t wh[W / 2], wl[W / 2];
 #pragma unroll
-    for (int c = 0; c < 8; c += 2) {
+    for (int c = 0; c < W; c += 2) {
       wh[c >> 1] = pack_bf16x2(zc[c], zc[c + 1]);
       const __nv_bfloat162 hh = *reinterpret_cast<const __nv_bfloat162*>(&wh[c >> 1]);
       const float2 hf = __bfloat1622float2(hh);
@@ -371,10 +383,14 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     }
     float cmax = fabsf(zc[0]);
 #pragma unroll
-    for (int c = 1; c < 8; ++c) cmax = fmaxf(cmax, fabsf(zc[c]));
+    for (int c = 1; c < W; ++c) cmax = fmaxf(cmax, fabsf(zc[c]));
     if (kmax_part == kNoNz || cmax > zinf_part) { zinf_part = cmax; kmax_part = c0; }
-    store_row8(A1, r, c0, d_pad, wh);
-    if (p.nterms > 1) store_row8(A1lo, r, c0, d_pad, wl);
+    store_roww<W>(A1, r, c0, d_pad, wh);
+    if (p.nterms > 1) store_roww<W>(A1lo, r, c0, d_pad, wl);
+  };
+  for (int u = split; u < nu && !bail; u += kSplits) {
+    if (u < nu16) init_unit(Width<8>{}, 16 * u);
+    else init_unit(Width<4>{}, 16 * nu16 + 8 * (u - nu16));
   }
   s_pz[part * kTileM + r] = zinf_part;
   s_pk[part * kTileM + r] = kmax_part;
@@ -578,16 +594,15 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     const bool collect_prev = s >= 1 && ((t - 1) % p.period == 0);
     const bool dbg_step = dbg_on && s == 0;
     // (1) forward MMAs (and B round(z) of the previous step's candidate)
-    if (issuer && issued_early >= 0) {
+    if (issuer) {
       tc_fence_after();
-      issue_chunks(issued_early, dch, true, tr && collect_prev);  // transposed: one chain
+      issue_chunks(0, dch, true, tr && collect_prev);  // transposed: one chain
       mma_commit(barF);
       if (!tr && collect_prev) {
         issue_chunks(0, dch, false, true);
         mma_commit(bar2);
       }
     }
-    issued_early = 0;
     // every thread waits itself; the time-out vote joins the barrier after
     // the sign phase (warp-uniform: the TMEM loads are collective)
     bool late = __any_sync(0xffffffffu, !mbar_wait_bounded(barF, phaseF));
@@ -696,29 +711,28 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     const float step = ad.x, rsb2 = ad.y;
     // The inverse-norm term of Eq. (3), -lambda2 / ||z||_inf^2 times the sign
     // of z at the first maximiser of |z|, is nonzero only while
-    // 0 < ||z||_inf < 1; kmax is the 8-column group holding that maximiser.
+    // 0 < ||z||_inf < 1; kmax is the column group holding that maximiser.
     const bool inv_on = zinf < 1.f && zinf > 0.f;
     const float inv_term = inv_on ? -p.lambda2 / (zinf * zinf) : 0.f;
-    const bool early = k_early > 0 && s + 1 < p.T;  // CTA-uniform
-    const bool d2_next = t % p.period == 0;         // the next step collects this step's candidate
-    // G (TMEM) and the master z, m, v of coordinates c0 .. c0+7
-    auto load_state = [&](int ch, int c0, uint32_t (&v)[8], float (&zc)[8], float (&mc)[8], float (&vc)[8]) {
-      tmem_ld8x2(tmem + lane_off + colG_ + ch * 16, v);  // completes under the loads below
+    // G (TMEM) and the master z, m, v of the W coordinates c0 .. c0+W-1 (unit base ub)
+    auto load_state = [&](int ub, int c0, auto& v, auto& zc, auto& mc, auto& vc) {
+      constexpr int W = std::extent<std::remove_reference_t<decltype(v)>>::value;
+      tmem_ldw<W>(tmem + lane_off + colG_ + ub, v);  // completes under the loads below
       if (kRes) {
-        uint32_t tz[8], tm[8], tv[8];
-        tmem_ld8x2(tmem + st_off + ch * 16, tz);
-        tmem_ld8x2(tmem + st_off + col_m + ch * 16, tm);
-        tmem_ld8x2(tmem + st_off + col_v + ch * 16, tv);
+        uint32_t tz[W], tm[W], tv[W];
+        tmem_ldw<W>(tmem + st_off + ub, tz);
+        tmem_ldw<W>(tmem + st_off + col_m + ub, tm);
+        tmem_ldw<W>(tmem + st_off + col_v + ub, tv);
         tc_wait_ld();
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < W; ++c) {
           zc[c] = __uint_as_float(tz[c]);
           mc[c] = __uint_as_float(tm[c]);
           vc[c] = __uint_as_float(tv[c]);
         }
       } else {
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < W / 4; ++k) {
           const int g4 = c0 / 4 + k;
           const float4 qz = zb[g4 * kTileM], qm = mb[g4 * kTileM], qv = vb[g4 * kTileM];
           zc[4 * k] = qz.x; zc[4 * k + 1] = qz.y; zc[4 * k + 2] = qz.z; zc[4 * k + 3] = qz.w;
@@ -728,17 +742,17 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
         tc_wait_ld();
       }
     };
-    // the gradient of Eq. (3) at coordinates c0 .. c0+7: G + lambda1 (ceil z +
-    // floor z - 2 z), the inverse-norm term, and for identity-topped B the
+    // the gradient of Eq. (3) at coordinates c0 .. c0+W-1: G + lambda1 (ceil z
+    // + floor z - 2 z), the inverse-norm term, and for identity-topped B the
     // identity rows' sign(z_j)
-    auto chunk_grad = [&](int c0, const uint32_t (&v)[8], const float (&zc)[8], const float (&rz)[8],
-                          float (&g)[8]) {
+    auto unit_grad = [&](int c0, const auto& v, const auto& zc, const auto& rz, auto& g) {
+      constexpr int W = std::extent<std::remove_reference_t<decltype(g)>>::value;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) g[c] = fmaf(p.lambda1, frac_grad(zc[c], rz[c]), __uint_as_float(v[c]));
+      for (int c = 0; c < W; ++c) g[c] = fmaf(p.lambda1, frac_grad(zc[c], rz[c]), __uint_as_float(v[c]));
       if (inv_on && c0 == kmax) {
         bool hit = false;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < W; ++c) {
           if (!hit && fabsf(zc[c]) == zinf) {
             g[c] += inv_term * sgn1(zc[c]);
             hit = true;
@@ -747,47 +761,53 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       }
       if (kId) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) g[c] += sgn1(zc[c]);
+        for (int c = 0; c < W; ++c) g[c] += sgn1(zc[c]);
       }
     };
     // debug outputs of the first step: the integrality sum of Phi, the l1 norm
     // of the identity rows and the gradient, before the state is overwritten
     float frac = 0.f, l1_id = 0.f;
+    auto dbg_unit = [&](auto Wc, int ub) {
+      constexpr int W = decltype(Wc)::value;
+      const int c0 = ub + W * half;
+      uint32_t v[W];
+      float zc[W], mc[W], vc[W], rz[W], g[W];
+      load_state(ub, c0, v, zc, mc, vc);
+#pragma unroll
+      for (int c = 0; c < W; ++c) rz[c] = rintf(zc[c]);
+      unit_grad(c0, v, zc, rz, g);
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        const int j = c0 + c;
+        if (!active || j >= d) continue;
+        const float z = zc[c], fl = floorf(z);
+        frac += (z - fl) * (ceilf(z) - z);
+        if (kId) l1_id += fabsf(z);
+        if (p.dbg_grad) p.dbg_grad[pg * d + j] = g[c];
+      }
+    };
     if (dbg_step) {
-      for (int ch = split; ch < dch; ch += kSplits) {
-        const int c0 = ch * 16 + hoff;
-        uint32_t v[8];
-        float zc[8], mc[8], vc[8], rz[8], g[8];
-        load_state(ch, c0, v, zc, mc, vc);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) rz[c] = rintf(zc[c]);
-        chunk_grad(c0, v, zc, rz, g);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int j = c0 + c;
-          if (!active || j >= d) continue;
-          const float z = zc[c], fl = floorf(z);
-          frac += (z - fl) * (ceilf(z) - z);
-          if (kId) l1_id += fabsf(z);
-          if (p.dbg_grad) p.dbg_grad[pg * d + j] = g[c];
-        }
+      for (int u = split; u < nu; u += kSplits) {
+        if (u < nu16) dbg_unit(Width<8>{}, 16 * u);
+        else dbg_unit(Width<4>{}, 16 * nu16 + 8 * (u - nu16));
       }
     }
     float nzinf = 0.f;
     int nkmax = kNoNz, first_id = kNoNz;
     bool changed = false, unexact = false, out_id = false;
-    for (int ch = split; ch < dch; ch += kSplits) {
-      const int c0 = ch * 16 + hoff;
-      uint32_t v[8];
-      float zc[8], mc[8], vc[8], rz[8], g[8];
-      load_state(ch, c0, v, zc, mc, vc);
+    auto epi_unit = [&](auto Wc, int ub) {
+      constexpr int W = decltype(Wc)::value;
+      const int c0 = ub + W * half;
+      uint32_t v[W];
+      float zc[W], mc[W], vc[W], rz[W], g[W];
+      load_state(ub, c0, v, zc, mc, vc);
 #pragma unroll
-      for (int c = 0; c < 8; ++c) rz[c] = rintf(zc[c]);
-      chunk_grad(c0, v, zc, rz, g);
-      float zn[8], rn[8];
-      uint32_t zo[8], mo[8], vo[8];
+      for (int c = 0; c < W; ++c) rz[c] = rintf(zc[c]);
+      unit_grad(c0, v, zc, rz, g);
+      float zn[W], rn[W];
+      uint32_t zo[W], mo[W], vo[W];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < W; ++c) {
         const float m = fmaf(p.beta1, mc[c], p.omb1 * g[c]);
         const float vv = fmaf(p.beta2, vc[c], p.omb2 * g[c] * g[c]);
         const float den = fmaf(sqrt_approx(vv), rsb2, p.eps);
@@ -805,39 +825,42 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       }
       float cmax = fabsf(zn[0]);
 #pragma unroll
-      for (int c = 1; c < 8; ++c) cmax = fmaxf(cmax, fabsf(zn[c]));
+      for (int c = 1; c < W; ++c) cmax = fmaxf(cmax, fabsf(zn[c]));
       if (nkmax == kNoNz || cmax > nzinf) { nzinf = cmax; nkmax = c0; }
       if (kId) {  // identity rows of g = B round(z): bound test and first nonzero entry
-        const float4 sa = *reinterpret_cast<const float4*>(s_span + c0);
-        const float4 sb = *reinterpret_cast<const float4*>(s_span + c0 + 4);
-        const float sp[8] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w};
+        float sp[W];
+#pragma unroll
+        for (int k = 0; k < W / 4; ++k) {
+          const float4 q4 = *reinterpret_cast<const float4*>(s_span + c0 + 4 * k);
+          sp[4 * k] = q4.x; sp[4 * k + 1] = q4.y; sp[4 * k + 2] = q4.z; sp[4 * k + 3] = q4.w;
+        }
         bool nz = false;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < W; ++c) {
           out_id |= fabsf(rn[c]) > sp[c];
           nz |= rn[c] != 0.f;
         }
         if (first_id == kNoNz && nz) {
 #pragma unroll
-          for (int c = 0; c < 8; ++c)
+          for (int c = 0; c < W; ++c)
             if (first_id == kNoNz && rn[c] != 0.f) first_id = ((c0 + c) << 1) | (rn[c] < 0.f ? 1 : 0);
         }
       }
-      uint32_t w1[4], wl[4], w2[4];
+      uint32_t w1[W / 2], wl[W / 2], w2[W / 2];
 #pragma unroll
-      for (int c = 0; c < 8; c += 2) {
+      for (int c = 0; c < W; c += 2) {
         w1[c >> 1] = pack_bf16x2(zn[c], zn[c + 1]);
         const float2 hf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w1[c >> 1]));
         wl[c >> 1] = pack_bf16x2(zn[c] - hf.x, zn[c + 1] - hf.y);
         w2[c >> 1] = pack_bf16x2(rn[c], rn[c + 1]);
       }
       if (kRes) {
-        tmem_st8x2(tmem + st_off + ch * 16, zo);
-        tmem_st8x2(tmem + st_off + col_m + ch * 16, mo);
-        tmem_st8x2(tmem + st_off + col_v + ch * 16, vo);
+        tmem_stw<W>(tmem + st_off + ub, zo);
+        tmem_stw<W>(tmem + st_off + col_m + ub, mo);
+        tmem_stw<W>(tmem + st_off + col_v + ub, vo);
       } else {
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < W / 4; ++k) {
           const int g4 = c0 / 4 + k;
           zb[g4 * kTileM] = make_float4(zn[4 * k], zn[4 * k + 1], zn[4 * k + 2], zn[4 * k + 3]);
           mb[g4 * kTileM] = make_float4(__uint_as_float(mo[4 * k]), __uint_as_float(mo[4 * k + 1]),
@@ -846,25 +869,13 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
                                         __uint_as_float(vo[4 * k + 2]), __uint_as_float(vo[4 * k + 3]));
         }
       }
-      store_row8(A1, r, c0, d_pad, w1);
-      if (p.nterms > 1) store_row8(A1lo, r, c0, d_pad, wl);
-      store_row8(A2, r, c0, d_pad, w2);
-      if (early && ch + kSplits == k_early + split) {  // this warp's chunks before the last round are written
-        fence_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(barE);
-        if (issuer) {
-          const bool ok = mbar_wait_bounded(barE, phaseE);
-          phaseE ^= 1;
-          if (ok) {
-            tc_fence_after();
-            issue_chunks(0, k_early, true, d2_next);
-            issued_early = k_early;
-          } else {
-            issued_early = -1;  // no commit: the forward wait times out and the CTA stops
-          }
-        }
-      }
+      store_roww<W>(A1, r, c0, d_pad, w1);
+      if (p.nterms > 1) store_roww<W>(A1lo, r, c0, d_pad, wl);
+      store_roww<W>(A2, r, c0, d_pad, w2);
+    };
+    for (int u = split; u < nu; u += kSplits) {
+      if (u < nu16) epi_unit(Width<8>{}, 16 * u);
+      else epi_unit(Width<4>{}, 16 * nu16 + 8 * (u - nu16));
     }
     s_pz[part * kTileM + r] = nzinf;
     s_pk[part * kTileM + r] = nkmax;

@@ -94,6 +94,31 @@ __device__ __forceinline__ void tmem_st8x2(uint32_t taddr, const uint32_t (&r)[8
 }
 __device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// 4 consecutive FP32 columns of one M = 64 accumulator row: half-warp 0 reads
+// columns [col, col+4) of lanes 0-15 of the quarter, half-warp 1 [col+4, col+8)
+__device__ __forceinline__ void tmem_ld4x2(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.16x32bx2.x4.b32 {%0,%1,%2,%3}, [%4], 4;"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st4x2(uint32_t taddr, const uint32_t (&r)[4]) {
+  asm volatile("tcgen05.st.sync.aligned.16x32bx2.x4.b32 [%0], 4, {%1,%2,%3,%4};" ::"r"(taddr), "r"(r[0]), "r"(r[1]),
+               "r"(r[2]), "r"(r[3])
+               : "memory");
+}
+
+// W (8 or 4) columns per half-warp: [col + W h, col + W h + W) for half h
+template <int W>
+__device__ __forceinline__ void tmem_ldw(uint32_t taddr, uint32_t (&r)[W]) {
+  if constexpr (W == 8) tmem_ld8x2(taddr, r);
+  else tmem_ld4x2(taddr, r);
+}
+template <int W>
+__device__ __forceinline__ void tmem_stw(uint32_t taddr, const uint32_t (&r)[W]) {
+  if constexpr (W == 8) tmem_st8x2(taddr, r);
+  else tmem_st4x2(taddr, r);
+}
+
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
