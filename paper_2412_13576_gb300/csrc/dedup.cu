@@ -9,8 +9,12 @@
 //    twice as many slots as rows, so every probe sequence meets an empty slot
 //    and the loop is bounded by the table size;
 // 3. representatives are compacted (order not fixed by the hardware) and
-//    then sorted lexicographically with a bitonic network over row indices,
-//    which fixes the output order independently of the atomics.
+//    then sorted lexicographically with a bitonic network over (key, row
+//    index) pairs, which fixes the output order independently of the
+//    atomics.  The key is the row's first 8 bytes as one unsigned number
+//    (first byte most significant, sign bits flipped), so most comparisons
+//    are one 64-bit compare on data in shared memory; equal keys fall back to
+//    the rows' remaining bytes.
 #include "common.cuh"
 
 #include <mutex>
@@ -86,46 +90,72 @@ __global__ void pad_idx_kernel(uint32_t* idx, int64_t from, int64_t to) {
   if (i < to) idx[i] = kEmpty;
 }
 
-// Lexicographic order on signed bytes; kEmpty sorts last.
-__device__ __forceinline__ int cmp_rows(const int8_t* rows, int ldc, uint32_t a, uint32_t b) {
+// The first 8 bytes of a row, first byte most significant, sign bits flipped:
+// unsigned order of keys = lexicographic order of the signed bytes
+__device__ __forceinline__ uint64_t row_key(const int8_t* row) {
+  const uint2 w = *reinterpret_cast<const uint2*>(row);
+  const uint32_t hi = __byte_perm(w.x, 0, 0x0123) ^ 0x80808080u;
+  const uint32_t lo = __byte_perm(w.y, 0, 0x0123) ^ 0x80808080u;
+  return ((uint64_t)hi << 32) | lo;
+}
+
+// Lexicographic order on signed bytes of (key, row) pairs; kEmpty sorts last.
+// Rows with equal keys are compared from byte 8 on, 16 bytes at a time.
+__device__ __forceinline__ int cmp_keyed(const int8_t* rows, int ldc, uint64_t ka, uint32_t a, uint64_t kb,
+                                         uint32_t b) {
   if (a == b) return 0;
   if (a == kEmpty) return 1;
   if (b == kEmpty) return -1;
+  if (ka != kb) return ka < kb ? -1 : 1;
   const uint32_t* pa = reinterpret_cast<const uint32_t*>(rows + (int64_t)a * ldc);
   const uint32_t* pb = reinterpret_cast<const uint32_t*>(rows + (int64_t)b * ldc);
-  for (int c = 0; c < ldc / 4; ++c) {
-    // first byte most significant; flip the sign bits so unsigned order = signed order
-    uint32_t x = __byte_perm(pa[c], 0, 0x0123) ^ 0x80808080u;
-    uint32_t y = __byte_perm(pb[c], 0, 0x0123) ^ 0x80808080u;
+  for (int c = 2; c < ldc / 4; ++c) {
+    const uint32_t x = __byte_perm(pa[c], 0, 0x0123) ^ 0x80808080u;
+    const uint32_t y = __byte_perm(pb[c], 0, 0x0123) ^ 0x80808080u;
     if (x != y) return x < y ? -1 : 1;
   }
   return 0;
 }
 
-__global__ void bitonic_step_kernel(const int8_t* __restrict__ rows, int ldc, uint32_t* __restrict__ idx,
-                                    int64_t npad, int64_t j, int64_t k) {
+__global__ void key_rows_kernel(const int8_t* __restrict__ rows, int ldc, const uint32_t* __restrict__ idx,
+                                int64_t npad, uint64_t* __restrict__ key) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  const uint32_t a = idx[i];
+  key[i] = a == kEmpty ? ~0ull : row_key(rows + (int64_t)a * ldc);
+}
+
+__global__ void bitonic_step_kernel(const int8_t* __restrict__ rows, int ldc, uint64_t* __restrict__ key,
+                                    uint32_t* __restrict__ idx, int64_t npad, int64_t j, int64_t k) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= npad) return;
   int64_t l = i ^ j;
   if (l <= i) return;
-  uint32_t a = idx[i], b = idx[l];
+  const uint32_t a = idx[i], b = idx[l];
+  const uint64_t ka = key[i], kb = key[l];
   bool ascending = (i & k) == 0;
-  int c = cmp_rows(rows, ldc, a, b);
+  int c = cmp_keyed(rows, ldc, ka, a, kb, b);
   if ((ascending && c > 0) || (!ascending && c < 0)) {
     idx[i] = b;
     idx[l] = a;
+    key[i] = kb;
+    key[l] = ka;
   }
 }
 
 constexpr int kSeg = 2048;
 
 // Bitonic stages k = kfirst .. klast (doubling), distances j < seg, on the
-// segment of seg indices owned by this block (seg <= kSeg, a power of two).
-__global__ void bitonic_local_kernel(const int8_t* __restrict__ rows, int ldc, uint32_t* __restrict__ idx, int64_t seg,
-                                     int64_t kfirst, int64_t klast) {
+// segment of seg pairs owned by this block (seg <= kSeg, a power of two).
+__global__ void bitonic_local_kernel(const int8_t* __restrict__ rows, int ldc, uint64_t* __restrict__ key,
+                                     uint32_t* __restrict__ idx, int64_t seg, int64_t kfirst, int64_t klast) {
+  __shared__ uint64_t sk[kSeg];
   __shared__ uint32_t s[kSeg];
   const int64_t base = blockIdx.x * seg;
-  for (int t = threadIdx.x; t < seg; t += blockDim.x) s[t] = idx[base + t];
+  for (int t = threadIdx.x; t < seg; t += blockDim.x) {
+    s[t] = idx[base + t];
+    sk[t] = key[base + t];
+  }
   __syncthreads();
   for (int64_t k = kfirst; k <= klast; k <<= 1) {
     for (int64_t j = ((k >> 1) < (seg >> 1) ? (k >> 1) : (seg >> 1)); j > 0; j >>= 1) {
@@ -134,16 +164,22 @@ __global__ void bitonic_local_kernel(const int8_t* __restrict__ rows, int ldc, u
         const int64_t l = i + j;
         const bool ascending = ((base + i) & k) == 0;
         const uint32_t a = s[i], b = s[l];
-        const int c = cmp_rows(rows, ldc, a, b);
+        const uint64_t ka = sk[i], kb = sk[l];
+        const int c = cmp_keyed(rows, ldc, ka, a, kb, b);
         if ((ascending && c > 0) || (!ascending && c < 0)) {
           s[i] = b;
           s[l] = a;
+          sk[i] = kb;
+          sk[l] = ka;
         }
       }
       __syncthreads();
     }
   }
-  for (int t = threadIdx.x; t < seg; t += blockDim.x) idx[base + t] = s[t];
+  for (int t = threadIdx.x; t < seg; t += blockDim.x) {
+    idx[base + t] = s[t];
+    key[base + t] = sk[t];
+  }
 }
 
 __global__ void gather_rows_kernel(const int8_t* __restrict__ rows, int ldc, const uint32_t* __restrict__ idx,
@@ -167,20 +203,23 @@ uint64_t next_pow2(uint64_t x) {
 namespace mape_detail {
 
 // Sorts rows[idx[0..K)] lexicographically in place of idx (npad >= K, power of 2,
-// idx[K..npad) set to the sentinel by this call).
+// idx[K..npad) set to the sentinel by this call; key: npad words of scratch).
 // The network is the plain bitonic one; all stages with distance j < seg run
-// inside one launch on shared-memory segments of seg = min(npad, 2048) indices
+// inside one launch on shared-memory segments of seg = min(npad, 2048) pairs
 // (the compare direction still comes from the global index).
-int sort_row_indices(const int8_t* rows, int ldc, uint32_t* idx, int64_t K, int64_t npad, cudaStream_t st) {
+int sort_row_indices(const int8_t* rows, int ldc, uint32_t* idx, uint64_t* key, int64_t K, int64_t npad,
+                     cudaStream_t st) {
   if (npad > K) mape_detail::launch(pad_idx_kernel, (unsigned)ceil_div(npad - K, 256), 256, 0, st, idx, K, npad);
   if (npad < 2) return MAPE_OK;
+  mape_detail::launch(key_rows_kernel, (unsigned)ceil_div(npad, 256), 256, 0, st, rows, ldc, idx, npad, key);
   const int64_t seg = npad < kSeg ? npad : kSeg;
   const unsigned nseg = (unsigned)(npad / seg);
-  mape_detail::launch(bitonic_local_kernel, nseg, kSeg / 2, 0, st, rows, ldc, idx, seg, (int64_t)2, seg);
+  mape_detail::launch(bitonic_local_kernel, nseg, kSeg / 2, 0, st, rows, ldc, key, idx, seg, (int64_t)2, seg);
   for (int64_t k = 2 * seg; k <= npad; k <<= 1) {
     for (int64_t j = k >> 1; j >= seg; j >>= 1)
-      mape_detail::launch(bitonic_step_kernel, (unsigned)ceil_div(npad, 256), 256, 0, st, rows, ldc, idx, npad, j, k);
-    mape_detail::launch(bitonic_local_kernel, nseg, kSeg / 2, 0, st, rows, ldc, idx, seg, k, k);
+      mape_detail::launch(bitonic_step_kernel, (unsigned)ceil_div(npad, 256), 256, 0, st, rows, ldc, key, idx, npad, j,
+                          k);
+    mape_detail::launch(bitonic_local_kernel, nseg, kSeg / 2, 0, st, rows, ldc, key, idx, seg, k, k);
   }
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
@@ -198,6 +237,7 @@ extern "C" size_t mape_dedup_workspace_bytes(int64_t count, int32_t ldc) {
   s.take<uint32_t>((size_t)mape_detail::dedup_table_slots(count)); // table
   s.take<uint8_t>((size_t)count);                                 // representative flags
   s.take<uint32_t>((size_t)next_pow2((uint64_t)(count > 0 ? count : 1)));  // sorted indices
+  s.take<uint64_t>((size_t)next_pow2((uint64_t)(count > 0 ? count : 1)));  // their sort keys
   s.take<unsigned long long>(1);                                  // counter
   return s.bytes();
 }
@@ -218,6 +258,7 @@ extern "C" int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t 
   uint8_t* is_rep = cv.take<uint8_t>((size_t)count);
   uint64_t npad_cap = next_pow2((uint64_t)count);
   uint32_t* idx = cv.take<uint32_t>((size_t)npad_cap);
+  uint64_t* keys = cv.take<uint64_t>((size_t)npad_cap);
   unsigned long long* dK = cv.take<unsigned long long>(1);
   if (!cv.ok) return MAPE_ERR_CAPACITY;
   cudaStream_t st = as_stream(stream);
@@ -234,7 +275,7 @@ extern "C" int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t 
   *K_out = (int64_t)K;
   if ((int64_t)K > uniq_cap) return MAPE_ERR_CAPACITY;
   if (!uniq) return MAPE_ERR_INVALID_ARG;
-  int rc = sort_row_indices(cand, ldc, idx, (int64_t)K, (int64_t)next_pow2(K), st);
+  int rc = sort_row_indices(cand, ldc, idx, keys, (int64_t)K, (int64_t)next_pow2(K), st);
   if (rc != MAPE_OK) return rc;
   int64_t chunks = (int64_t)K * (ldc / 16);
   mape_detail::launch(gather_rows_kernel, (unsigned)ceil_div(chunks, 256), 256, 0, st, cand, ldc, idx, (int64_t)K, uniq);
@@ -258,7 +299,7 @@ extern "C" int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t 
 namespace {
 
 constexpr int64_t kStaticDedupRows = (int64_t)1 << 18;       // candidate rows per call
-constexpr size_t kStaticDedupBytes = (size_t)6 << 20;        // >= mape_dedup_workspace_bytes(2^18, any ldc)
+constexpr size_t kStaticDedupBytes = (size_t)8 << 20;        // >= mape_dedup_workspace_bytes(2^18, any ldc)
 static __device__ __align__(256) unsigned char g_dedup_scratch[kStaticDedupBytes];
 
 constexpr int kMaxDevices = 64;
