@@ -20,7 +20,8 @@
  *      arguments are HOST pointers owned by the caller and copied during the
  *      call; the library owns every device buffer of the handle, allocated
  *      through the allocator set with mape_set_allocator (default:
- *      cudaMallocAsync on the handle's stream).  extract_directions and
+ *      stream-ordered allocation on the handle's stream from a library pool
+ *      that keeps freed memory).  extract_directions and
  *      augment return at once and run on a worker thread of the handle;
  *      mape_poll reads progress, mape_wait blocks with a timeout.
  *
@@ -105,7 +106,7 @@ typedef struct {
   int32_t precision;           /* MAPE_PREC_*                                   */
   int32_t reserved;
   int64_t cand_capacity;       /* candidate-buffer rows of a handle (0: P*(T+1),
-                                  at most 2^22 rows and 1 GiB per buffer)    */
+                                  at most 2^23 rows and 2 GiB per buffer)    */
   int64_t max_aug_iters;       /* cap on Algorithm 1 iterations per call        */
 } mape_config;
 
@@ -406,10 +407,18 @@ typedef struct mape_instance* mape_handle;
 
 /* Device memory hooks used by every handle created afterwards.
  * alloc(bytes, stream, ctx) returns a device pointer or NULL; free(ptr,
- * bytes, stream, ctx).  Passing NULLs restores cudaMallocAsync/cudaFreeAsync. */
+ * bytes, stream, ctx).  Passing NULLs restores the default: stream-ordered
+ * allocation (cudaMallocFromPoolAsync / cudaFreeAsync) from a memory pool
+ * per device that the library owns and that keeps freed memory reserved for
+ * the next handle (no new page mappings when handles come and go). */
 typedef void* (*mape_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*mape_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
 int mape_set_allocator(mape_alloc_fn alloc_fn, mape_free_fn free_fn, void* ctx);
+
+/* Returns the memory the current device's library pool holds beyond what
+ * live handles use (cudaMemPoolTrimTo(pool, 0) after a device
+ * synchronisation).  OK when the pool was never created. */
+int mape_trim_memory(void);
 
 typedef struct {
   int32_t n, m;

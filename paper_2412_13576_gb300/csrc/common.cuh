@@ -56,12 +56,12 @@ struct Sizer {
 };
 
 // Default candidate-buffer rows of a handle: one row per start and step,
-// at most 2^22 rows and at most 1 GiB per buffer (a handle holds three); the
+// at most 2^23 rows and at most 2 GiB per buffer (a handle holds three); the
 // extraction runs in chunks of steps that fit.
 inline int64_t default_cand_capacity(int64_t P, int64_t T, int64_t ldg) {
   int64_t cap = P * (T > 0 ? T : 1) + P;
-  cap = cap < ((int64_t)1 << 22) ? cap : ((int64_t)1 << 22);
-  const int64_t by_bytes = ((int64_t)1 << 30) / (ldg > 0 ? ldg : 16);
+  cap = cap < ((int64_t)1 << 23) ? cap : ((int64_t)1 << 23);
+  const int64_t by_bytes = ((int64_t)1 << 31) / (ldg > 0 ? ldg : 16);
   cap = cap < by_bytes ? cap : by_bytes;
   return cap > P + 1 ? cap : P + 1;
 }

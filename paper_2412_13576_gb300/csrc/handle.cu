@@ -27,6 +27,31 @@ mape_alloc_fn g_alloc = nullptr;
 mape_free_fn g_free = nullptr;
 void* g_alloc_ctx = nullptr;
 
+// Default allocation: a stream-ordered memory pool per device owned by the
+// library, whose release threshold keeps freed memory reserved, so that
+// handles created one after another (a request per handle) reuse it instead
+// of mapping new pages; mape_trim_memory hands it back.
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxPoolDevices] = {};
+
+cudaMemPool_t library_pool(int dev) {
+  if (dev < 0 || dev >= kMaxPoolDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = pool;
+  }
+  return g_pool[dev];
+}
+
 __global__ void basis_check_kernel(const int32_t* __restrict__ A, const int32_t* __restrict__ B, int m, int n,
                                    int d, int32_t* __restrict__ bad) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -82,7 +107,7 @@ struct mape_instance {
   std::vector<std::pair<void*, size_t>> job_bufs;
   int P = 0;
   float *dZ = nullptr, *dM = nullptr, *dV = nullptr, *dG0 = nullptr;
-  int8_t *dBuf0 = nullptr, *dBuf1 = nullptr, *dD = nullptr;
+  int8_t *dBuf0 = nullptr, *dBuf1 = nullptr;
   int64_t cap = 0;
   uint8_t *dOk = nullptr, *dKeep = nullptr;
   int64_t *da = nullptr, *dq4 = nullptr;
@@ -90,7 +115,7 @@ struct mape_instance {
   size_t work_bytes = 0;
   unsigned long long* dCount = nullptr;
   int32_t* dFlags = nullptr;
-  int8_t* dirs = nullptr;  // current direction set (points into dD)
+  int8_t* dirs = nullptr;  // current direction set (the candidate buffer free after the last merge)
   int64_t K = 0;
 
   // augmentation buffers
@@ -120,7 +145,8 @@ struct mape_instance {
         return p;
       }
     }
-    if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) return nullptr;
+    cudaMemPool_t pool = library_pool(dev);
+    if (!pool || cudaMallocFromPoolAsync(&p, bytes, pool, stream) != cudaSuccess) return nullptr;
     return p;
   }
   void release(void* p, size_t bytes) {
@@ -219,11 +245,12 @@ int mape_instance::run_extract() {
   int64_t fails = 0;
   H_TRY(mape_kernel_test(dA, m, n, cur, U, ldg, dOk, &fails, dWork, work_bytes, s));
   int64_t Kk = 0;
-  H_TRY(mape_minimal_filter(cur, U, n, ldg, dOk, dKeep, dD, &Kk, dWork, work_bytes, s));
-  H_TRY(mape_direction_coeffs(dqr, dqc, dqv, nnz, has_w ? dw : nullptr, n, dD, Kk, ldg, da, dq4, s));
+  // the kept rows go to the buffer of the pair that the last merge left free
+  H_TRY(mape_minimal_filter(cur, U, n, ldg, dOk, dKeep, other, &Kk, dWork, work_bytes, s));
+  H_TRY(mape_direction_coeffs(dqr, dqc, dqv, nnz, has_w ? dw : nullptr, n, other, Kk, ldg, da, dq4, s));
   MAPE_CUDA_TRY(cudaStreamSynchronize(s));
   double t_fil = now_ms();
-  dirs = dD;
+  dirs = other;
   K = Kk;
   std::lock_guard<std::mutex> lk(mu);
   st.kernel_failures = fails;
@@ -323,6 +350,24 @@ extern "C" int mape_set_allocator(mape_alloc_fn a, mape_free_fn f, void* ctx) {
   return MAPE_OK;
 }
 
+extern "C" int mape_trim_memory(void) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxPoolDevices) return MAPE_ERR_CUDA;
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    pool = g_pool[dev];
+  }
+  if (!pool) return MAPE_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+  if (e != cudaSuccess) {
+    mape_detail::record_cuda_error(e, "mape_trim_memory", __FILE__, __LINE__);
+    return MAPE_ERR_CUDA;
+  }
+  return MAPE_OK;
+}
+
 extern "C" int mape_create_instance(const int32_t* A, const int64_t* b, const int32_t* l, const int32_t* u,
                                     const mape_problem* f, const int32_t* B, const mape_config* cfg,
                                     void* stream, mape_handle* out) {
@@ -411,7 +456,6 @@ extern "C" int mape_extract_directions(mape_handle h, int32_t P, const float* Z0
   h->dG0 = G0 ? h->take<float>(h->job_bufs, (size_t)P * n) : nullptr;
   h->dBuf0 = h->take<int8_t>(h->job_bufs, (size_t)cap * ldg);
   h->dBuf1 = h->take<int8_t>(h->job_bufs, (size_t)cap * ldg);
-  h->dD = h->take<int8_t>(h->job_bufs, (size_t)cap * ldg);
   h->dOk = h->take<uint8_t>(h->job_bufs, (size_t)cap);
   h->dKeep = h->take<uint8_t>(h->job_bufs, (size_t)cap);
   h->da = h->take<int64_t>(h->job_bufs, (size_t)cap);
@@ -425,7 +469,7 @@ extern "C" int mape_extract_directions(mape_handle h, int32_t P, const float* Z0
   w = std::max(w, mape_minimal_workspace_bytes(cap, n));
   h->work_bytes = w;
   h->dWork = h->take<char>(h->job_bufs, w);
-  if (!h->dZ || !h->dM || !h->dV || (G0 && !h->dG0) || !h->dBuf0 || !h->dBuf1 || !h->dD || !h->dOk ||
+  if (!h->dZ || !h->dM || !h->dV || (G0 && !h->dG0) || !h->dBuf0 || !h->dBuf1 || !h->dOk ||
       !h->dKeep || !h->da || !h->dq4 || !h->dCount || !h->dFlags || !h->dWork)
     return MAPE_ERR_OOM;
   int rc = G0 ? upload(h, h->dG0, G0, sizeof(float) * (size_t)P * n) : upload(h, h->dZ, Z0, sizeof(float) * (size_t)P * d);

@@ -89,7 +89,7 @@ extern "C" size_t mape_request_bytes(int32_t n, int32_t m, int32_t P, int32_t S,
   inst += N * N * 12 / 8 + 2 * N * 4;                                            // Q as COO (bound), c, w
   inst += N * d * 4 + mape_project_prepare_workspace_bytes(n, (int32_t)d);      // W and its workspace
   size_t job = 3 * (size_t)P * d * 4 + (size_t)P * N * 4;                        // Z, M, V, G0
-  job += 3 * (size_t)cap * ldg + 2 * (size_t)cap + 2 * (size_t)cap * 8 + 16;     // candidate buffers, flags, a, q4
+  job += 2 * (size_t)cap * ldg + 2 * (size_t)cap + 2 * (size_t)cap * 8 + 16;     // candidate buffers, flags, a, q4
   size_t w = mape_extract_workspace_bytes(n, (int32_t)d, P, cfg->precision);
   w = std::max(w, mape_dedup_workspace_bytes(cap, (int32_t)ldg));
   w = std::max(w, mape_kernel_test_workspace_bytes());

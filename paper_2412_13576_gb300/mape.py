@@ -163,6 +163,7 @@ _SIGS = {
     "mape_augment_workspace_bytes": (C.c_size_t, [I32, I32, I64]),
     "mape_augment_run": (C.c_int, [C.POINTER(AugmentArgs), C.POINTER(I64), P_]),
     "mape_set_allocator": (C.c_int, [P_, P_, P_]),
+    "mape_trim_memory": (C.c_int, []),
     "mape_create_instance": (C.c_int, [P_, P_, P_, P_, C.POINTER(Problem), P_, C.POINTER(Config), P_,
                                        C.POINTER(P_)]),
     "mape_extract_directions": (C.c_int, [P_, I32, P_, P_]),
@@ -664,6 +665,12 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def trim_memory():
+    """Hands back the memory that the library's pool on the current device
+    keeps reserved beyond the live handles (mape_trim_memory)."""
+    _check(lib().mape_trim_memory(), "mape_trim_memory")
 
 
 def request_bytes(n, m, P, S, cfg: Config | None = None) -> int:

@@ -31,6 +31,25 @@ def check_direction_set(inst, D):
     assert np.unique(D, axis=0).shape[0] == D.shape[0]
 
 
+def test_handles_reuse_pool_memory(M):
+    """Handles created one after another reuse the library pool's memory;
+    trimming hands it back and later handles still work."""
+    import torch
+    inst = I.small_dense()
+    st = I.normal_starts(inst, 128, seed=3)
+    cfg = M.default_config(T=50)
+    sets = []
+    for k in range(3):
+        with M.Instance.from_generated(inst, cfg) as h:
+            h.extract_directions(128, Z0=st.Z0)
+            h.wait(300)
+            sets.append(h.directions())
+        if k == 1:
+            M.trim_memory()
+    torch.cuda.synchronize()
+    assert all(np.array_equal(sets[0], D) for D in sets[1:]) and sets[0].shape[0] > 0
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_handle_small(M, precision):
     inst = I.small_dense()

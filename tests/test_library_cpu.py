@@ -67,15 +67,15 @@ def test_server_struct_layouts_match_binding(tmp_path, lib):
 
 
 def test_request_bytes_estimate(lib):
-    """The admission estimate covers at least the FP32 state and the three
+    """The admission estimate covers at least the FP32 state and the two
     candidate buffers, grows with P and n, and is 0 for invalid sizes."""
     from paper_2412_13576_gb300 import mape
     cfg = mape.default_config(T=1000)
     n, m, P = 500, 100, 1024
     b = mape.request_bytes(n, m, P, 1, cfg)
     ldg = 512
-    cap = min(P * 1001, 1 << 22, (1 << 30) // ldg)
-    assert b >= 3 * P * (n - m) * 4 + 3 * cap * ldg
+    cap = min(P * 1001, 1 << 23, (1 << 31) // ldg)
+    assert b >= 3 * P * (n - m) * 4 + 2 * cap * ldg
     assert mape.request_bytes(n, m, 2 * P, 1, cfg) > b
     assert mape.request_bytes(2 * n, 2 * m, P, 1, cfg) > b
     assert mape.request_bytes(n, m, P, 8, cfg) > b
