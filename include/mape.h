@@ -252,7 +252,7 @@ int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t ldc,
  * is captured into a CUDA graph (cudaMalloc is not allowed there), hosts that
  * reserve all device memory up front and forbid later allocations, plugins
  * whose host owns the allocator.  This variant takes no workspace: its
- * scratch is a static device array of 8 MiB inside the library, which every
+ * scratch is a static device array of 10 MiB inside the library, which every
  * GPU that loads the library holds until the process exits.
  *   Limit: count <= mape_dedup_static_max_rows() (2^18 rows); larger counts
  *   return MAPE_ERR_CAPACITY before any device work.

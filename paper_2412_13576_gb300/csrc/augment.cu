@@ -43,27 +43,48 @@ __device__ __forceinline__ Best warp_min(Best v) {
   return v;
 }
 
+// One warp per direction: the lanes take the entries of Q (coalesced) and of
+// w, the direction's row is staged in shared memory, a warp reduction sums
+// (integer arithmetic, exact in any order).
+constexpr int kCoefWarps = 8;
+constexpr int kCoefMaxRow = 4096;  // ldg <= 4096 bytes (n <= 4096)
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __global__ void coeffs_kernel(const int32_t* __restrict__ qr, const int32_t* __restrict__ qc,
                               const int32_t* __restrict__ qv, int nnz, const int32_t* __restrict__ w, int n,
                               const int8_t* __restrict__ G, int64_t K, int ldg, int64_t* __restrict__ a,
                               int64_t* __restrict__ q4) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  const int8_t* g = G + k * ldg;
+  __shared__ __align__(16) int8_t s_row[kCoefWarps][kCoefMaxRow];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t k = (int64_t)blockIdx.x * kCoefWarps + wid;
+  if (k >= K) return;  // warp-uniform
+  int8_t* g = s_row[wid];
+  const uint4* src = reinterpret_cast<const uint4*>(G + k * ldg);
+  for (int c = lane; c < ldg / 16; c += 32) reinterpret_cast<uint4*>(g)[c] = src[c];
+  __syncwarp();
   long long acc = 0;
-  for (int e = 0; e < nnz; ++e) {
-    int i = qr[e], j = qc[e];
-    long long t = (long long)qv[e] * g[i] * g[j];
+  for (int e = lane; e < nnz; e += 32) {
+    const int i = qr[e], j = qc[e];
+    const long long t = (long long)qv[e] * g[i] * g[j];
     acc += (i == j) ? t : 2 * t;
   }
-  a[k] = acc;
+  acc = warp_sum_ll(acc);
   long long s4 = 0;
   if (w)
-    for (int i = 0; i < n; ++i) {
-      long long gi = g[i];
+    for (int i = lane; i < n; i += 32) {
+      const long long gi = g[i];
       s4 += (long long)w[i] * gi * gi * gi * gi;
     }
-  q4[k] = s4;
+  s4 = warp_sum_ll(s4);
+  if (lane == 0) {
+    a[k] = acc;
+    q4[k] = s4;
+  }
 }
 
 // r = 2 Q x + c and f(x), one block per start; checks l <= x <= u.
@@ -285,8 +306,9 @@ extern "C" int mape_direction_coeffs(const int32_t* q_row, const int32_t* q_col,
       (K > 0 && (!G || !a || !q4)))
     return MAPE_ERR_INVALID_ARG;
   if (K == 0) return MAPE_OK;
-  mape_detail::launch(coeffs_kernel, (unsigned)ceil_div(K, 128), 128, 0, as_stream(stream), q_row, q_col, q_val, nnz, w, n, G, K,
-                                                                         ldg, a, q4);
+  if (ldg > kCoefMaxRow) return MAPE_ERR_SHAPE;
+  mape_detail::launch(coeffs_kernel, (unsigned)ceil_div(K, kCoefWarps), 32 * kCoefWarps, 0, as_stream(stream), q_row,
+                      q_col, q_val, nnz, w, n, G, K, ldg, a, q4);
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
 }

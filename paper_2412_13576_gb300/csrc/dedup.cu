@@ -9,12 +9,14 @@
 //    twice as many slots as rows, so every probe sequence meets an empty slot
 //    and the loop is bounded by the table size;
 // 3. representatives are compacted (order not fixed by the hardware) and
-//    then sorted lexicographically with a bitonic network over (key, row
-//    index) pairs, which fixes the output order independently of the
-//    atomics.  The key is the row's first 8 bytes as one unsigned number
-//    (first byte most significant, sign bits flipped), so most comparisons
-//    are one 64-bit compare on data in shared memory; equal keys fall back to
-//    the rows' remaining bytes.
+//    then sorted lexicographically, which fixes the output order
+//    independently of the atomics.  The key of a row is its first 8 bytes as
+//    one unsigned number (first byte most significant, sign bits flipped).
+//    A bitonic network sorts (key, row index) pairs, one 64-bit compare on
+//    data in shared memory each; then every run of equal keys (rows that
+//    share their first 8 bytes) is sorted by the rows' remaining bytes, one
+//    block per run.  Should a run be longer than a block sorts, the whole
+//    array is sorted again with the comparison that reads the rows.
 #include "common.cuh"
 
 #include <mutex>
@@ -125,6 +127,15 @@ __global__ void key_rows_kernel(const int8_t* __restrict__ rows, int ldc, const 
   key[i] = a == kEmpty ? ~0ull : row_key(rows + (int64_t)a * ldc);
 }
 
+// (key, index) order, or the rows' lexicographic order (kFull)
+template <bool kFull>
+__device__ __forceinline__ int cmp_pair(const int8_t* rows, int ldc, uint64_t ka, uint32_t a, uint64_t kb, uint32_t b) {
+  if (kFull) return cmp_keyed(rows, ldc, ka, a, kb, b);
+  if (ka != kb) return ka < kb ? -1 : 1;
+  return a == b ? 0 : (a < b ? -1 : 1);
+}
+
+template <bool kFull>
 __global__ void bitonic_step_kernel(const int8_t* __restrict__ rows, int ldc, uint64_t* __restrict__ key,
                                     uint32_t* __restrict__ idx, int64_t npad, int64_t j, int64_t k) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -134,7 +145,7 @@ __global__ void bitonic_step_kernel(const int8_t* __restrict__ rows, int ldc, ui
   const uint32_t a = idx[i], b = idx[l];
   const uint64_t ka = key[i], kb = key[l];
   bool ascending = (i & k) == 0;
-  int c = cmp_keyed(rows, ldc, ka, a, kb, b);
+  int c = cmp_pair<kFull>(rows, ldc, ka, a, kb, b);
   if ((ascending && c > 0) || (!ascending && c < 0)) {
     idx[i] = b;
     idx[l] = a;
@@ -147,6 +158,7 @@ constexpr int kSeg = 2048;
 
 // Bitonic stages k = kfirst .. klast (doubling), distances j < seg, on the
 // segment of seg pairs owned by this block (seg <= kSeg, a power of two).
+template <bool kFull>
 __global__ void bitonic_local_kernel(const int8_t* __restrict__ rows, int ldc, uint64_t* __restrict__ key,
                                      uint32_t* __restrict__ idx, int64_t seg, int64_t kfirst, int64_t klast) {
   __shared__ uint64_t sk[kSeg];
@@ -165,7 +177,7 @@ __global__ void bitonic_local_kernel(const int8_t* __restrict__ rows, int ldc, u
         const bool ascending = ((base + i) & k) == 0;
         const uint32_t a = s[i], b = s[l];
         const uint64_t ka = sk[i], kb = sk[l];
-        const int c = cmp_keyed(rows, ldc, ka, a, kb, b);
+        const int c = cmp_pair<kFull>(rows, ldc, ka, a, kb, b);
         if ((ascending && c > 0) || (!ascending && c < 0)) {
           s[i] = b;
           s[l] = a;
@@ -180,6 +192,52 @@ __global__ void bitonic_local_kernel(const int8_t* __restrict__ rows, int ldc, u
     idx[base + t] = s[t];
     key[base + t] = sk[t];
   }
+}
+
+// runs of equal keys among the first K sorted pairs: (start, length) of
+// every run of two or more, and the longest length
+__global__ void key_runs_kernel(const uint64_t* __restrict__ key, int64_t K, int2* __restrict__ runs,
+                                unsigned int* __restrict__ nruns, unsigned int* __restrict__ maxlen) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= K) return;
+  if (i > 0 && key[i] == key[i - 1]) return;      // not the start of a run
+  if (i + 1 >= K || key[i + 1] != key[i]) return;  // a run of one
+  int64_t j = i + 2;
+  while (j < K && key[j] == key[i]) ++j;
+  const unsigned int len = (unsigned int)(j - i);
+  atomicMax(maxlen, len);
+  const unsigned int at = atomicAdd(nruns, 1u);
+  runs[at] = make_int2((int)i, (int)len);
+}
+
+constexpr int kRunMax = 2048;  // longest run one block sorts
+
+// one block per run: bitonic on the run's row indices (padded with the
+// sentinel to a power of two) comparing the rows from byte 8 on
+__global__ void run_sort_kernel(const int8_t* __restrict__ rows, int ldc, const int2* __restrict__ runs,
+                                uint32_t* __restrict__ idx) {
+  __shared__ uint32_t s[kRunMax];
+  const int2 rr = runs[blockIdx.x];
+  int np = 2;
+  while (np < rr.y) np <<= 1;
+  for (int t = threadIdx.x; t < np; t += blockDim.x) s[t] = t < rr.y ? idx[rr.x + t] : kEmpty;
+  __syncthreads();
+  for (int k = 2; k <= np; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < np / 2; t += blockDim.x) {
+        const int i = (t / j) * 2 * j + (t % j), l = i + j;
+        const bool ascending = (i & k) == 0;
+        const uint32_t a = s[i], b = s[l];
+        const int c = cmp_keyed(rows, ldc, 0, a, 0, b);  // equal keys: bytes 8 on
+        if ((ascending && c > 0) || (!ascending && c < 0)) {
+          s[i] = b;
+          s[l] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < rr.y; t += blockDim.x) idx[rr.x + t] = s[t];
 }
 
 __global__ void gather_rows_kernel(const int8_t* __restrict__ rows, int ldc, const uint32_t* __restrict__ idx,
@@ -207,19 +265,35 @@ namespace mape_detail {
 // The network is the plain bitonic one; all stages with distance j < seg run
 // inside one launch on shared-memory segments of seg = min(npad, 2048) pairs
 // (the compare direction still comes from the global index).
-int sort_row_indices(const int8_t* rows, int ldc, uint32_t* idx, uint64_t* key, int64_t K, int64_t npad,
-                     cudaStream_t st) {
+template <bool kFull>
+void bitonic_sort(const int8_t* rows, int ldc, uint32_t* idx, uint64_t* key, int64_t npad, cudaStream_t st) {
+  const int64_t seg = npad < kSeg ? npad : kSeg;
+  const unsigned nseg = (unsigned)(npad / seg);
+  mape_detail::launch(bitonic_local_kernel<kFull>, nseg, kSeg / 2, 0, st, rows, ldc, key, idx, seg, (int64_t)2, seg);
+  for (int64_t k = 2 * seg; k <= npad; k <<= 1) {
+    for (int64_t j = k >> 1; j >= seg; j >>= 1)
+      mape_detail::launch(bitonic_step_kernel<kFull>, (unsigned)ceil_div(npad, 256), 256, 0, st, rows, ldc, key, idx,
+                          npad, j, k);
+    mape_detail::launch(bitonic_local_kernel<kFull>, nseg, kSeg / 2, 0, st, rows, ldc, key, idx, seg, k, k);
+  }
+}
+
+int sort_row_indices(const int8_t* rows, int ldc, uint32_t* idx, uint64_t* key, int2* runs, unsigned int* counters,
+                     int64_t K, int64_t npad, cudaStream_t st) {
   if (npad > K) mape_detail::launch(pad_idx_kernel, (unsigned)ceil_div(npad - K, 256), 256, 0, st, idx, K, npad);
   if (npad < 2) return MAPE_OK;
   mape_detail::launch(key_rows_kernel, (unsigned)ceil_div(npad, 256), 256, 0, st, rows, ldc, idx, npad, key);
-  const int64_t seg = npad < kSeg ? npad : kSeg;
-  const unsigned nseg = (unsigned)(npad / seg);
-  mape_detail::launch(bitonic_local_kernel, nseg, kSeg / 2, 0, st, rows, ldc, key, idx, seg, (int64_t)2, seg);
-  for (int64_t k = 2 * seg; k <= npad; k <<= 1) {
-    for (int64_t j = k >> 1; j >= seg; j >>= 1)
-      mape_detail::launch(bitonic_step_kernel, (unsigned)ceil_div(npad, 256), 256, 0, st, rows, ldc, key, idx, npad, j,
-                          k);
-    mape_detail::launch(bitonic_local_kernel, nseg, kSeg / 2, 0, st, rows, ldc, key, idx, seg, k, k);
+  bitonic_sort<false>(rows, ldc, idx, key, npad, st);
+  MAPE_CUDA_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned int), st));
+  mape_detail::launch(key_runs_kernel, (unsigned)ceil_div(K, 256), 256, 0, st, key, K, runs, counters, counters + 1);
+  MAPE_LAUNCH_CHECK();
+  unsigned int hc[2] = {0, 0};
+  MAPE_CUDA_TRY(cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hc[1] > (unsigned)kRunMax) {
+    bitonic_sort<true>(rows, ldc, idx, key, npad, st);  // the rows decide every comparison
+  } else if (hc[0] > 0) {
+    mape_detail::launch(run_sort_kernel, hc[0], 256, 0, st, rows, ldc, runs, idx);
   }
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
@@ -238,6 +312,8 @@ extern "C" size_t mape_dedup_workspace_bytes(int64_t count, int32_t ldc) {
   s.take<uint8_t>((size_t)count);                                 // representative flags
   s.take<uint32_t>((size_t)next_pow2((uint64_t)(count > 0 ? count : 1)));  // sorted indices
   s.take<uint64_t>((size_t)next_pow2((uint64_t)(count > 0 ? count : 1)));  // their sort keys
+  s.take<int2>((size_t)(count > 0 ? count : 1) / 2 + 1);          // runs of equal keys
+  s.take<unsigned int>(2);                                        // run count, longest run
   s.take<unsigned long long>(1);                                  // counter
   return s.bytes();
 }
@@ -259,6 +335,8 @@ extern "C" int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t 
   uint64_t npad_cap = next_pow2((uint64_t)count);
   uint32_t* idx = cv.take<uint32_t>((size_t)npad_cap);
   uint64_t* keys = cv.take<uint64_t>((size_t)npad_cap);
+  int2* runs = cv.take<int2>((size_t)count / 2 + 1);
+  unsigned int* run_counters = cv.take<unsigned int>(2);
   unsigned long long* dK = cv.take<unsigned long long>(1);
   if (!cv.ok) return MAPE_ERR_CAPACITY;
   cudaStream_t st = as_stream(stream);
@@ -275,7 +353,7 @@ extern "C" int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t 
   *K_out = (int64_t)K;
   if ((int64_t)K > uniq_cap) return MAPE_ERR_CAPACITY;
   if (!uniq) return MAPE_ERR_INVALID_ARG;
-  int rc = sort_row_indices(cand, ldc, idx, keys, (int64_t)K, (int64_t)next_pow2(K), st);
+  int rc = sort_row_indices(cand, ldc, idx, keys, runs, run_counters, (int64_t)K, (int64_t)next_pow2(K), st);
   if (rc != MAPE_OK) return rc;
   int64_t chunks = (int64_t)K * (ldc / 16);
   mape_detail::launch(gather_rows_kernel, (unsigned)ceil_div(chunks, 256), 256, 0, st, cand, ldc, idx, (int64_t)K, uniq);
@@ -299,7 +377,7 @@ extern "C" int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t 
 namespace {
 
 constexpr int64_t kStaticDedupRows = (int64_t)1 << 18;       // candidate rows per call
-constexpr size_t kStaticDedupBytes = (size_t)8 << 20;        // >= mape_dedup_workspace_bytes(2^18, any ldc)
+constexpr size_t kStaticDedupBytes = (size_t)10 << 20;        // >= mape_dedup_workspace_bytes(2^18, any ldc)
 static __device__ __align__(256) unsigned char g_dedup_scratch[kStaticDedupBytes];
 
 constexpr int kMaxDevices = 64;

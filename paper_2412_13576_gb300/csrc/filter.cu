@@ -108,38 +108,44 @@ __global__ void prep_kernel(const int8_t* __restrict__ G, int64_t K, int n, int 
 }
 
 // exclusive prefix over bins (one block of 1024); cursor receives a copy of
-// the starts.  Each thread sums a contiguous segment, the 1024 segment sums
-// are scanned with warp shuffles, and each thread writes its segment.
+// the starts.  Warp w owns a contiguous segment; its lanes read it 32
+// consecutive words at a time (coalesced): a first sweep sums the segment, the
+// 32 segment sums are scanned by warp 0, and a second sweep scans the
+// segment with warp shuffles and writes it.
 __global__ void bin_scan_kernel(const uint32_t* __restrict__ hist, int nbins, uint32_t* __restrict__ start,
                                 uint32_t* __restrict__ cursor) {
   __shared__ uint32_t s_warp[32];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int per = (nbins + (int)blockDim.x - 1) / (int)blockDim.x;
-  const int b0 = tid * per, b1 = min(b0 + per, nbins);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  const int per = (nbins + nw - 1) / nw;
+  const int b0 = wid * per, b1 = min(b0 + per, nbins);
   uint32_t sum = 0;
-  for (int b = b0; b < b1; ++b) sum += hist[b];
-  uint32_t x = sum;  // inclusive scan over the warp
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_warp[wid] = x;
+  for (int b = b0 + lane; b < b1; b += 32) sum += hist[b];
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) s_warp[wid] = sum;
   __syncthreads();
   if (wid == 0) {
-    uint32_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+    uint32_t x = lane < nw ? s_warp[lane] : 0;
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-    s_warp[lane] = w;  // inclusive over warps
+    s_warp[lane] = x;  // inclusive over warps
   }
   __syncthreads();
-  uint32_t run = x - sum + (wid > 0 ? s_warp[wid - 1] : 0);  // exclusive start of this segment
-  for (int b = b0; b < b1; ++b) {
-    const uint32_t v = hist[b];
-    start[b] = run;
-    cursor[b] = run;
-    run += v;
+  uint32_t run = wid > 0 ? s_warp[wid - 1] : 0;  // exclusive start of the segment
+  for (int base = b0; base < b1; base += 32) {
+    const int b = base + lane;
+    const uint32_t v = b < b1 ? hist[b] : 0;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (b < b1) {
+      start[b] = run + x - v;
+      cursor[b] = run + x - v;
+    }
+    run += __shfl_sync(0xffffffffu, x, 31);
   }
 }
 

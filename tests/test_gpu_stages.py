@@ -139,6 +139,24 @@ def test_dedup_exact(M, count, n):
     assert np.all(uniq[:, n:] == 0)
 
 
+@pytest.mark.parametrize("count,n,groups", [(6000, 40, 1), (20000, 64, 300), (3000, 8, 5)])
+def test_dedup_shared_prefixes(M, count, n, groups):
+    """Rows sharing their first 8 bytes: many short runs of equal sort keys
+    (sorted per run by the remaining bytes), one run longer than a block
+    sorts (the whole array sorted again by the rows), rows of 8 bytes."""
+    rng = np.random.default_rng(count + n)
+    ldc = M.round16(n)
+    base = rng.integers(-2, 3, size=(max(1, count // 3), n))
+    base[:, : min(8, n)] = rng.integers(-3, 4, size=(groups, min(8, n)))[rng.integers(0, groups, size=base.shape[0])]
+    rows = base[rng.integers(0, base.shape[0], size=count)].astype(np.int8)
+    buf = np.zeros((count, ldc), np.int8)
+    buf[:, :n] = rows
+    uniq = M.dedup(dev(buf), count, n).cpu().numpy()
+    expect = O.sort_directions(np.unique(rows.astype(np.int64), axis=0))
+    assert np.array_equal(uniq[:, :n].astype(np.int64), expect)
+    assert np.all(uniq[:, n:] == 0)
+
+
 # --- a9 ------------------------------------------------------------------------
 
 def test_kernel_test_exact(M):
