@@ -44,6 +44,9 @@ constexpr int kNB = 256;       // the widest N block: the largest MMA N
 constexpr int kChunkA = kTM * kKC * 2;        // one 128 x 64 BF16 operand chunk (16 KB)
 // shared memory of the two-stage rings for N blocks of width w
 __host__ __device__ constexpr int fwd_stage(int w) { return 3 * kChunkA + w * kKC * 2; }  // hi, lo, round(z), Bm chunk
+constexpr int kChunkZ = kTM * kKC * 4;  // one 128 x 64 FP32 chunk of the blocked state (32 KB, contiguous)
+// forward pass: two operand stages, then two FP32 z stages
+__host__ __device__ constexpr int fwd_smem(int w) { return 2 * fwd_stage(w) + 2 * kChunkZ; }
 __host__ __device__ constexpr int grad_stage(int w) { return kChunkA + w * kKC * 2; }    // S chunk, Bm chunk
 __host__ __device__ constexpr int tmem_cols(int c) { return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512; }
 constexpr int kNoNz = 0x7fffffff;
@@ -89,7 +92,7 @@ __device__ __forceinline__ int ptot(const StParams& p) { return p.tiles * kTM; }
 template <bool kId>
 __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk, int s, int fwd, int collect) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bars[4];  // full[2], done[2]
+  __shared__ __align__(8) uint64_t bars[6];  // full[2], done[2], zfull[2]
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -100,7 +103,7 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
   const uint32_t fcols = (uint32_t)tmem_cols(2 * p.wF);  // D1 at 0, D2 at wF
   const int nk = p.d64 / kKC;
   const int P2 = ptot(p);
-  const uint32_t full0 = smem_u32(&bars[0]), done0 = smem_u32(&bars[2]);
+  const uint32_t full0 = smem_u32(&bars[0]), done0 = smem_u32(&bars[2]), zfull0 = smem_u32(&bars[4]);
   if (*(volatile int32_t*)p.flags & 16) return;  // an earlier CTA timed out: the call is abandoned
 
   // buffers of the next step's per-start reductions start empty
@@ -114,6 +117,7 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
   if (tid == 0) {
     mbar_init(full0, 1); mbar_init(full0 + 8, 1);
     mbar_init(done0, 1); mbar_init(done0 + 8, 1);
+    mbar_init(zfull0, 1); mbar_init(zfull0 + 8, 1);
     s_abort = 0;
   }
   if (warp == 0) tmem_alloc(smem_u32(&s_tmem), fcols);
@@ -124,46 +128,57 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
   const uint32_t tmem = s_tmem;
   const uint32_t idesc = idesc_bf16(kTM, N);
   bool ok = true;
-  int issued_copies = 0, issued_commits = 0;  // thread 0 only
+  int issued_copies = 0, issued_commits = 0, issued_z = 0;  // thread 0 only
 
   // item i of this thread: 8 coordinates (core matrix kc) of start r, so that
   // a warp writes 512 contiguous bytes of each operand
   const float4* zbase = reinterpret_cast<const float4*>(p.Zt) + (size_t)tile * (p.d64 / 4) * kTM;
   auto item_r = [&](int i) { const int e = tid + kThreads * i; return (e & 7) | ((e >> 6) << 3); };
   auto item_kc = [&](int i) { return ((tid + kThreads * i) >> 3) & 7; };
-  float4 cur[4][2], nxt[4][2] = {};
-  auto load_chunk = [&](int c, float4 (&q)[4][2]) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float4* zt = zbase + ((size_t)c * (kKC / 4) + 2 * item_kc(i)) * kTM + item_r(i);
-      q[i][0] = zt[0];
-      q[i][1] = zt[kTM];
-    }
+  // z chunk c (coordinates 64c .. 64c+63 of the tile's 128 starts: 32 KB,
+  // contiguous in the blocked layout) goes to z stage c & 1 by bulk copy,
+  // one chunk ahead of its conversion
+  uint8_t* const zst = smem + 2 * fstage;
+  auto copy_z = [&](int c) {
+    const int zs = c & 1;
+    mbar_arrive_expect_tx(zfull0 + 8 * zs, (uint32_t)kChunkZ);
+    bulk_g2s(smem_u32(zst + zs * kChunkZ), zbase + (size_t)c * (kKC / 4) * kTM, (uint32_t)kChunkZ, zfull0 + 8 * zs);
+    ++issued_z;
   };
-  load_chunk(0, cur);
+  if (tid == 0) copy_z(0);
 
+  // the Bm chunk of chunk c goes to stage c & 1 by bulk copy, issued one
+  // chunk ahead: chunk c + 1 right after chunk c's MMAs are issued, once
+  // those of chunk c - 1 have left its stage, so that the copy overlaps
+  // chunk c's MMAs and chunk c + 1's conversion
+  auto copy_bm = [&](int c) {
+    const int stg = c & 1;
+    uint8_t* Bc = smem + stg * fstage + 3 * kChunkA;
+    mbar_arrive_expect_tx(full0 + 8 * stg, (uint32_t)N * kKC * 2);
+    bulk_g2s(smem_u32(Bc), p.BmF + ((size_t)rb * p.wF * p.d64 + (size_t)c * N * kKC) * 2, (uint32_t)N * kKC * 2,
+             full0 + 8 * stg);
+    ++issued_copies;
+  };
+  if (tid == 0) copy_bm(0);
   for (int c = 0; c < nk; ++c) {
     const int stg = c & 1;
     uint8_t* Ahi = smem + stg * fstage;
     uint8_t* Alo = Ahi + kChunkA;
     uint8_t* Ard = Alo + kChunkA;
     uint8_t* Bc = Ard + kChunkA;
-    if (c >= 2) {  // the MMAs of chunk c - 2 read this stage
+    if (c >= 2) {  // the MMAs of chunk c - 2 read this stage's operands
       const bool w = mbar_wait_bounded(done0 + 8 * stg, ((c - 2) >> 1) & 1);
       if (__syncthreads_or(!w || s_abort)) { ok = false; break; }
     }
-    if (tid == 0) {
-      mbar_arrive_expect_tx(full0 + 8 * stg, (uint32_t)N * kKC * 2);
-      bulk_g2s(smem_u32(Bc), p.BmF + ((size_t)rb * p.wF * p.d64 + (size_t)c * N * kKC) * 2, (uint32_t)N * kKC * 2,
-               full0 + 8 * stg);
-      ++issued_copies;
-    }
-    // the next chunk's z is in flight while this one becomes BF16 operands
-    if (c + 1 < nk) load_chunk(c + 1, nxt);
+    // the z stage of chunk c + 1 was read by chunk c - 1's conversion, which
+    // every thread finished before the last barrier
+    if (tid == 0 && c + 1 < nk) copy_z(c + 1);
+    if (__syncthreads_or(!mbar_wait_bounded(zfull0 + 8 * (c & 1), (c >> 1) & 1))) { ok = false; break; }
+    const float4* zs4 = reinterpret_cast<const float4*>(zst + (c & 1) * kChunkZ);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int r = item_r(i), kc = item_kc(i);
-      const float4 q0 = cur[i][0], q1 = cur[i][1];
+      const float4 q0 = zs4[(2 * kc) * kTM + r], q1 = zs4[(2 * kc + 1) * kTM + r];
       const float z8[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
       const uint32_t o = chunk_off(r, kc * 8);
       if (fwd) {
@@ -220,12 +235,11 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
         }
         mma_commit(done0 + 8 * stg);
         ++issued_commits;
+        if (c + 1 < nk) {
+          if (c >= 1 && !mbar_wait_bounded(done0 + 8 * ((c - 1) & 1), ((c - 1) >> 1) & 1)) s_abort = 1;
+          else copy_bm(c + 1);
+        }
       }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      cur[i][0] = nxt[i][0];
-      cur[i][1] = nxt[i][1];
     }
   }
   if (ok) {
@@ -292,6 +306,7 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
   }
   if (!ok && tid == 0) {  // drain what this thread issued before the memory goes away
     for (int c = 0; c < issued_copies; ++c) mbar_wait_bounded(full0 + 8 * (c & 1), (c >> 1) & 1);
+    for (int c = 0; c < issued_z; ++c) mbar_wait_bounded(zfull0 + 8 * (c & 1), (c >> 1) & 1);
     if (issued_commits > 0) {
       const int cl = issued_commits - 1;
       mbar_wait_bounded(done0 + 8 * (cl & 1), (cl >> 1) & 1);
@@ -624,28 +639,48 @@ __global__ void pack_bm_kernel(const int32_t* __restrict__ B, int d, int R, int 
 }
 
 // [P x d] row-major  <->  blocked [tiles][d64/4][128][4] (zero padded)
-__global__ void pack128_kernel(const float* __restrict__ in, float* __restrict__ out, int P, int d, int d64,
-                               int64_t total) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= total) return;
-  const int c = (int)(e & 3);
-  const int r = (int)((e >> 2) % kTM);
-  const int64_t g = e / (4 * kTM);
-  const int g4 = (int)(g % (d64 / 4));
-  const int64_t tile = g / (d64 / 4);
-  const int64_t row = tile * kTM + r;
-  const int j = g4 * 4 + c;
-  out[e] = (row < P && j < d) ? in[row * d + j] : 0.f;
+// [P x d] row-major <-> blocked [tiles][d64/4][128][4] (zero padded).  Grid
+// (tiles, d64 / 8) x 128 threads: thread r moves coordinates 8 y .. 8 y + 7 of
+// start x * 128 + r, 32 contiguous bytes of its row (16-byte vector accesses
+// when d % 4 == 0 and the row-major array is 16-byte aligned), and the blocked
+// side is two float4 rows of 128 starts, coalesced over the threads.
+__global__ void pack128_kernel(const float* __restrict__ in, float* __restrict__ out, int P, int d, int d64) {
+  const int r = threadIdx.x, g8 = blockIdx.y;
+  const int64_t tile = blockIdx.x, row = tile * kTM + r;
+  const int j0 = 8 * g8;
+  const bool vec = (d & 3) == 0 && ((uintptr_t)in & 15) == 0;
+  float v[8];
+  if (row < P && j0 + 8 <= d && vec) {
+    const float4* src = reinterpret_cast<const float4*>(in + row * d + j0);
+    const float4 a = src[0], b = src[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = (row < P && j0 + k < d) ? in[row * d + j0 + k] : 0.f;
+  }
+  float4* dst = reinterpret_cast<float4*>(out) + (tile * (d64 / 4) + 2 * g8) * kTM + r;
+  dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+  dst[kTM] = make_float4(v[4], v[5], v[6], v[7]);
 }
 
 __global__ void unpack128_kernel(const float* __restrict__ in, float* __restrict__ out, int P, int d, int d64) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= (int64_t)P * d) return;
-  const int64_t row = e / d;
-  const int j = (int)(e % d);
-  const int64_t tile = row / kTM;
-  const int r = (int)(row % kTM);
-  out[e] = in[((tile * (d64 / 4) + j / 4) * kTM + r) * 4 + (j & 3)];
+  const int r = threadIdx.x, g8 = blockIdx.y;
+  const int64_t tile = blockIdx.x, row = tile * kTM + r;
+  const bool vec = (d & 3) == 0 && ((uintptr_t)out & 15) == 0;
+  if (row >= P) return;
+  const int j0 = 8 * g8;
+  const float4* src = reinterpret_cast<const float4*>(in) + (tile * (d64 / 4) + 2 * g8) * kTM + r;
+  const float4 a = src[0], b = src[kTM];
+  const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  if (j0 + 8 <= d && vec) {
+    float4* dst = reinterpret_cast<float4*>(out + row * d + j0);
+    dst[0] = a;
+    dst[1] = b;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (j0 + k < d) out[row * d + j0 + k] = v[k];
+  }
 }
 
 // per-start words of the first step: ||z0||_inf and its first index, the
@@ -817,11 +852,10 @@ static int st_setup(const StCarved& c, const mape_extract_args* a, cudaStream_t 
   }
   MAPE_CUDA_TRY(cudaMemcpyAsync(c.bias, bc.data(), sizeof(float2) * bc.size(), cudaMemcpyHostToDevice, st));
   const size_t P2 = (size_t)sh.tiles * kTM;
-  const int64_t blocked = (int64_t)P2 * sh.d64;
-  const unsigned gpack = (unsigned)ceil_div(blocked, 256);
-  launch(pack128_kernel, gpack, 256, 0, st, a->Z, c.Zt, P, d, sh.d64, blocked);
-  launch(pack128_kernel, gpack, 256, 0, st, a->M, c.Mt, P, d, sh.d64, blocked);
-  launch(pack128_kernel, gpack, 256, 0, st, a->V, c.Vt, P, d, sh.d64, blocked);
+  const dim3 gpack((unsigned)sh.tiles, (unsigned)(sh.d64 / 8));
+  launch(pack128_kernel, gpack, kTM, 0, st, a->Z, c.Zt, P, d, sh.d64);
+  launch(pack128_kernel, gpack, kTM, 0, st, a->M, c.Mt, P, d, sh.d64);
+  launch(pack128_kernel, gpack, kTM, 0, st, a->V, c.Vt, P, d, sh.d64);
   MAPE_CUDA_TRY(cudaMemsetAsync(c.stage, 0, P2 * sh.lds, st));
   if (a->dbg_phi) MAPE_CUDA_TRY(cudaMemsetAsync(a->dbg_phi, 0, sizeof(float) * P, st));
   p = StParams{};
@@ -843,10 +877,10 @@ static int st_setup(const StCarved& c, const mape_extract_args* a, cudaStream_t 
 }
 
 static int st_unpack(const StCarved& c, const mape_extract_args* a, cudaStream_t st) {
-  const unsigned gun = (unsigned)ceil_div((int64_t)a->P * a->d, 256);
-  launch(unpack128_kernel, gun, 256, 0, st, c.Zt, a->Z, a->P, a->d, c.sh.d64);
-  launch(unpack128_kernel, gun, 256, 0, st, c.Mt, a->M, a->P, a->d, c.sh.d64);
-  launch(unpack128_kernel, gun, 256, 0, st, c.Vt, a->V, a->P, a->d, c.sh.d64);
+  const dim3 gun((unsigned)c.sh.tiles, (unsigned)(c.sh.d64 / 8));
+  launch(unpack128_kernel, gun, kTM, 0, st, c.Zt, a->Z, a->P, a->d, c.sh.d64);
+  launch(unpack128_kernel, gun, kTM, 0, st, c.Mt, a->M, a->P, a->d, c.sh.d64);
+  launch(unpack128_kernel, gun, kTM, 0, st, c.Vt, a->V, a->P, a->d, c.sh.d64);
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
 }
@@ -861,7 +895,7 @@ static int st_attributes(bool batch) {
                           : (id ? (const void*)stream_fwd_kernel<true> : (const void*)stream_fwd_kernel<false>);
     const void* g = batch ? (id ? (const void*)stream_grad_batch_kernel<true> : (const void*)stream_grad_batch_kernel<false>)
                           : (id ? (const void*)stream_grad_kernel<true> : (const void*)stream_grad_kernel<false>);
-    MAPE_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * fwd_stage(kNB)));
+    MAPE_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd_smem(kNB)));
     MAPE_CUDA_TRY(cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * grad_stage(kNB)));
   }
   return MAPE_OK;
@@ -912,7 +946,7 @@ int extract_stream_widths(const mape_extract_args* a, cudaStream_t st, int wF, i
   auto fwdk = id ? stream_fwd_kernel<true> : stream_fwd_kernel<false>;
   auto gradk = id ? stream_grad_kernel<true> : stream_grad_kernel<false>;
   auto collk = id ? stream_collect_kernel<true> : stream_collect_kernel<false>;
-  const int fsm = 2 * fwd_stage(sh.wF), gsm = 2 * grad_stage(sh.wG);
+  const int fsm = fwd_smem(sh.wF), gsm = 2 * grad_stage(sh.wG);
   st_schedule(
       a->t0, a->T, a->period, [&](int s, int f, int col) { launch(fwdk, gF, kThreads, fsm, st, p, s, f, col); },
       [&](int s) { launch(collk, gC, 256, 0, st, p, s); },
@@ -1041,7 +1075,7 @@ int extract_stream_batch_enqueue(const StBatch* plan, cudaStream_t st) {
     st_schedule(
         plan->t0, plan->T, plan->period,
         [&](int s, int f, int col) {
-          launch(fwdk, (unsigned)C.nF, kThreads, 2 * fwd_stage(kNB), st, C.table, C.wF, s, f, col);
+          launch(fwdk, (unsigned)C.nF, kThreads, fwd_smem(kNB), st, C.table, C.wF, s, f, col);
         },
         [&](int s) { launch(collk, (unsigned)C.nC, 256, 0, st, C.table, C.wC, s); },
         [&](int s) { launch(gradk, (unsigned)C.nG, kThreads, 2 * grad_stage(kNB), st, C.table, C.wG, s); });
