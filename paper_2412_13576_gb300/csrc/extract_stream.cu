@@ -39,6 +39,7 @@ using namespace mape_tc;
 
 constexpr int kTM = 128;       // starts per tile: the MMA M
 constexpr int kThreads = 256;  // 8 warps: two per TMEM lane quarter
+constexpr int kThreadsF = kThreads + 32;  // forward kernel: plus the issuing warp
 constexpr int kKC = 64;        // K chunk
 constexpr int kNB = 256;       // the widest N block: the largest MMA N
 constexpr int kChunkA = kTM * kKC * 2;        // one 128 x 64 BF16 operand chunk (16 KB)
@@ -88,14 +89,31 @@ __device__ __forceinline__ int ptot(const StParams& p) { return p.tiles * kTM; }
 
 // ---------------------------------------------------------------- forward
 
-// blk: tile * nbF + row block of this CTA
+// Barrier among the converter warps of the forward kernel (named barrier 1),
+// returning whether any of them passed true
+__device__ __forceinline__ bool conv_barrier_or(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(kThreads)
+      : "memory");
+  return r != 0;
+}
+
+// blk: tile * nbF + row block of this CTA.  Warps 0-7 (the converters) turn
+// the z chunks into BF16 operands and afterwards read the accumulators; warp 8
+// only issues: the Bm chunk copies and the MMAs.  A stage's operands are
+// handed over through the ready barrier (one arrival per converter warp), so
+// the conversion of chunk c + 1 runs while the MMAs of chunk c are issued.
 template <bool kId>
 __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk, int s, int fwd, int collect) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bars[6];  // full[2], done[2], zfull[2]
+  __shared__ __align__(8) uint64_t bars[8];  // full[2] (Bm copy), done[2] (MMAs), zfull[2] (z copy), ready[2]
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool conv = tid < kThreads;
   const int tile = blk / p.nbF, rb = blk % p.nbF;
   const int N = rb < p.nbF - 1 ? p.wF : p.R64 - p.wF * (p.nbF - 1);
   const int row0 = rb * p.wF;
@@ -103,8 +121,8 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
   const uint32_t fcols = (uint32_t)tmem_cols(2 * p.wF);  // D1 at 0, D2 at wF
   const int nk = p.d64 / kKC;
   const int P2 = ptot(p);
-  const uint32_t full0 = smem_u32(&bars[0]), done0 = smem_u32(&bars[2]), zfull0 = smem_u32(&bars[4]);
-  if (*(volatile int32_t*)p.flags & 16) return;  // an earlier CTA timed out: the call is abandoned
+  const uint32_t full0 = smem_u32(&bars[0]), done0 = smem_u32(&bars[2]), zfull0 = smem_u32(&bars[4]),
+                 ready0 = smem_u32(&bars[6]);
 
   // buffers of the next step's per-start reductions start empty
   if (rb == 0 && tid < kTM) {
@@ -118,7 +136,8 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
     mbar_init(full0, 1); mbar_init(full0 + 8, 1);
     mbar_init(done0, 1); mbar_init(done0 + 8, 1);
     mbar_init(zfull0, 1); mbar_init(zfull0 + 8, 1);
-    s_abort = 0;
+    mbar_init(ready0, kThreads / 32); mbar_init(ready0 + 8, kThreads / 32);
+    s_abort = (*(volatile int32_t*)p.flags & 16) ? 1 : 0;  // an earlier CTA timed out: the call is abandoned
   }
   if (warp == 0) tmem_alloc(smem_u32(&s_tmem), fcols);
   mbar_init_fence();
@@ -127,8 +146,9 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
   tc_fence_after();
   const uint32_t tmem = s_tmem;
   const uint32_t idesc = idesc_bf16(kTM, N);
-  bool ok = true;
-  int issued_copies = 0, issued_commits = 0, issued_z = 0;  // thread 0 only
+  bool ok = s_abort == 0;
+  int issued_copies = 0, issued_commits = 0;  // issuer thread
+  int issued_z = 0;                           // converter thread 0
 
   // item i of this thread: 8 coordinates (core matrix kc) of start r, so that
   // a warp writes 512 contiguous bytes of each operand
@@ -145,12 +165,9 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
     bulk_g2s(smem_u32(zst + zs * kChunkZ), zbase + (size_t)c * (kKC / 4) * kTM, (uint32_t)kChunkZ, zfull0 + 8 * zs);
     ++issued_z;
   };
-  if (tid == 0) copy_z(0);
-
-  // the Bm chunk of chunk c goes to stage c & 1 by bulk copy, issued one
-  // chunk ahead: chunk c + 1 right after chunk c's MMAs are issued, once
-  // those of chunk c - 1 have left its stage, so that the copy overlaps
-  // chunk c's MMAs and chunk c + 1's conversion
+  // the Bm chunk of chunk c goes to stage c & 1, issued one chunk ahead:
+  // chunk c + 1 right after chunk c's MMAs, once those of chunk c - 1 have
+  // left its stage
   auto copy_bm = [&](int c) {
     const int stg = c & 1;
     uint8_t* Bc = smem + stg * fstage + 3 * kChunkA;
@@ -159,96 +176,113 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
              full0 + 8 * stg);
     ++issued_copies;
   };
-  if (tid == 0) copy_bm(0);
-  for (int c = 0; c < nk; ++c) {
-    const int stg = c & 1;
-    uint8_t* Ahi = smem + stg * fstage;
-    uint8_t* Alo = Ahi + kChunkA;
-    uint8_t* Ard = Alo + kChunkA;
-    uint8_t* Bc = Ard + kChunkA;
-    if (c >= 2) {  // the MMAs of chunk c - 2 read this stage's operands
-      const bool w = mbar_wait_bounded(done0 + 8 * stg, ((c - 2) >> 1) & 1);
-      if (__syncthreads_or(!w || s_abort)) { ok = false; break; }
-    }
-    // the z stage of chunk c + 1 was read by chunk c - 1's conversion, which
-    // every thread finished before the last barrier
-    if (tid == 0 && c + 1 < nk) copy_z(c + 1);
-    if (__syncthreads_or(!mbar_wait_bounded(zfull0 + 8 * (c & 1), (c >> 1) & 1))) { ok = false; break; }
-    const float4* zs4 = reinterpret_cast<const float4*>(zst + (c & 1) * kChunkZ);
+
+  if (ok && conv) {  // ---- converters ----
+    if (tid == 0) copy_z(0);
+    for (int c = 0; c < nk; ++c) {
+      const int stg = c & 1;
+      uint8_t* Ahi = smem + stg * fstage;
+      uint8_t* Alo = Ahi + kChunkA;
+      uint8_t* Ard = Alo + kChunkA;
+      bool w = true;
+      if (c >= 2) w = mbar_wait_bounded(done0 + 8 * stg, ((c - 2) >> 1) & 1);  // chunk c - 2's MMAs left the stage
+      // every converter finished chunk c - 1, so the z stage of chunk c + 1 is free
+      if (conv_barrier_or(!w || *(volatile int*)&s_abort)) { ok = false; break; }
+      if (tid == 0 && c + 1 < nk) copy_z(c + 1);
+      // a time-out here is voted at the next barrier (every converter must
+      // reach it); this chunk's operands then go unused
+      if (!mbar_wait_bounded(zfull0 + 8 * (c & 1), (c >> 1) & 1)) s_abort = 1;
+      const float4* zs4 = reinterpret_cast<const float4*>(zst + (c & 1) * kChunkZ);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = item_r(i), kc = item_kc(i);
-      const float4 q0 = zs4[(2 * kc) * kTM + r], q1 = zs4[(2 * kc + 1) * kTM + r];
-      const float z8[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-      const uint32_t o = chunk_off(r, kc * 8);
-      if (fwd) {
-        uint32_t wh[4], wl[4];
+      for (int i = 0; i < 4; ++i) {
+        const int r = item_r(i), kc = item_kc(i);
+        const float4 q0 = zs4[(2 * kc) * kTM + r], q1 = zs4[(2 * kc + 1) * kTM + r];
+        const float z8[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+        const uint32_t o = chunk_off(r, kc * 8);
+        if (fwd) {
+          uint32_t wh[4], wl[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          wh[k] = pack_bf16x2(z8[2 * k], z8[2 * k + 1]);
-          const float2 hf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wh[k]));
-          wl[k] = pack_bf16x2(z8[2 * k] - hf.x, z8[2 * k + 1] - hf.y);
+          for (int k = 0; k < 4; ++k) {
+            wh[k] = pack_bf16x2(z8[2 * k], z8[2 * k + 1]);
+            const float2 hf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wh[k]));
+            wl[k] = pack_bf16x2(z8[2 * k] - hf.x, z8[2 * k + 1] - hf.y);
+          }
+          *reinterpret_cast<uint4*>(Ahi + o) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+          if (p.nterms > 1) *reinterpret_cast<uint4*>(Alo + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
         }
-        *reinterpret_cast<uint4*>(Ahi + o) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
-        if (p.nterms > 1) *reinterpret_cast<uint4*>(Alo + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
-      }
-      if (collect) {
-        uint32_t wr[4];
-        float rz[8];
+        if (collect) {
+          uint32_t wr[4];
+          float rz[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) rz[k] = rintf(z8[k]);
+          for (int k = 0; k < 8; ++k) rz[k] = rintf(z8[k]);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) wr[k] = pack_bf16x2(rz[2 * k], rz[2 * k + 1]);
-        *reinterpret_cast<uint4*>(Ard + o) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
-        // identity rows of the candidate: g_j = round z_j
-        const int64_t pg = (int64_t)tile * kTM + r;
-        const int j0 = c * kKC + kc * 8;
-        if (kId && rb == 0 && pg < p.P && j0 < p.d) {
-          int8_t* row = p.stage + pg * p.lds;
-          if (j0 + 8 <= p.d) {
-            uint32_t b[2] = {0, 0};
+          for (int k = 0; k < 4; ++k) wr[k] = pack_bf16x2(rz[2 * k], rz[2 * k + 1]);
+          *reinterpret_cast<uint4*>(Ard + o) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+          // identity rows of the candidate: g_j = round z_j
+          const int64_t pg = (int64_t)tile * kTM + r;
+          const int j0 = c * kKC + kc * 8;
+          if (kId && rb == 0 && pg < p.P && j0 < p.d) {
+            int8_t* row = p.stage + pg * p.lds;
+            if (j0 + 8 <= p.d) {
+              uint32_t bb[2] = {0, 0};
 #pragma unroll
-            for (int k = 0; k < 8; ++k) b[k >> 2] |= ((uint32_t)((int)rz[k] & 0xff)) << (8 * (k & 3));
-            *reinterpret_cast<uint2*>(row + j0) = make_uint2(b[0], b[1]);
-          } else {
-            for (int k = 0; j0 + k < p.d; ++k) row[j0 + k] = (int8_t)(int)rz[k];
+              for (int k = 0; k < 8; ++k) bb[k >> 2] |= ((uint32_t)((int)rz[k] & 0xff)) << (8 * (k & 3));
+              *reinterpret_cast<uint2*>(row + j0) = make_uint2(bb[0], bb[1]);
+            } else {
+              for (int k = 0; j0 + k < p.d; ++k) row[j0 + k] = (int8_t)(int)rz[k];
+            }
           }
         }
       }
+      // the stage's operands go to the issuer (async proxy)
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(ready0 + 8 * stg);
     }
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0 && !s_abort) {
-      if (!mbar_wait_bounded(full0 + 8 * stg, (c >> 1) & 1)) {
+  } else if (ok && tid == kThreads) {  // ---- issuer ----
+    copy_bm(0);
+    for (int c = 0; c < nk; ++c) {
+      const int stg = c & 1;
+      const uint32_t A0 = smem_u32(smem + stg * fstage);
+      const uint32_t Bc = A0 + 3 * kChunkA;
+      if (!mbar_wait_bounded(ready0 + 8 * stg, (c >> 1) & 1) || !mbar_wait_bounded(full0 + 8 * stg, (c >> 1) & 1) ||
+          *(volatile int*)&s_abort) {
         s_abort = 1;
-      } else {
-        tc_fence_after();
+        break;
+      }
+      tc_fence_after();
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t b = make_desc(smem_u32(Bc) + kk * 256, kChunkLbo, kChunkSbo);
-          const uint32_t a0 = (c | kk) ? 1u : 0u;
-          if (fwd) {
-            mma_bf16(tmem, make_desc(smem_u32(Ahi) + kk * 256, kChunkLbo, kChunkSbo), b, idesc, a0);
-            if (p.nterms > 1) mma_bf16(tmem, make_desc(smem_u32(Alo) + kk * 256, kChunkLbo, kChunkSbo), b, idesc, 1u);
-          }
-          if (collect) mma_bf16(tmem + p.wF, make_desc(smem_u32(Ard) + kk * 256, kChunkLbo, kChunkSbo), b, idesc, a0);
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t b = make_desc(Bc + kk * 256, kChunkLbo, kChunkSbo);
+        const uint32_t a0 = (c | kk) ? 1u : 0u;
+        if (fwd) {
+          mma_bf16(tmem, make_desc(A0 + kk * 256, kChunkLbo, kChunkSbo), b, idesc, a0);
+          if (p.nterms > 1) mma_bf16(tmem, make_desc(A0 + kChunkA + kk * 256, kChunkLbo, kChunkSbo), b, idesc, 1u);
         }
-        mma_commit(done0 + 8 * stg);
-        ++issued_commits;
-        if (c + 1 < nk) {
-          if (c >= 1 && !mbar_wait_bounded(done0 + 8 * ((c - 1) & 1), ((c - 1) >> 1) & 1)) s_abort = 1;
-          else copy_bm(c + 1);
+        if (collect) mma_bf16(tmem + p.wF, make_desc(A0 + 2 * kChunkA + kk * 256, kChunkLbo, kChunkSbo), b, idesc, a0);
+      }
+      mma_commit(done0 + 8 * stg);
+      ++issued_commits;
+      if (c + 1 < nk) {
+        if (c >= 1 && !mbar_wait_bounded(done0 + 8 * ((c - 1) & 1), ((c - 1) >> 1) & 1)) {
+          s_abort = 1;
+          break;
         }
+        copy_bm(c + 1);
       }
     }
   }
-  if (ok) {
-    const int cl = nk - 1;
-    const bool w = mbar_wait_bounded(done0 + 8 * (cl & 1), (cl >> 1) & 1);
-    if (__syncthreads_or(!w || s_abort)) ok = false;
+  // the last chunk's MMAs, then the accumulators (every thread takes part in the vote)
+  {
+    bool w = true;
+    if (ok && conv) {
+      const int cl = nk - 1;
+      w = mbar_wait_bounded(done0 + 8 * (cl & 1), (cl >> 1) & 1);
+    }
+    if (__syncthreads_or(!w || s_abort || !ok)) ok = false;
   }
 
-  if (ok) {
+  if (ok && conv) {
     tc_fence_after();
     const int q = warp & 3, h = warp >> 2;
     const int r = q * 32 + lane;
@@ -304,12 +338,15 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
   } else if (tid == 0) {
     atomicOr(p.flags, 16);
   }
-  if (!ok && tid == 0) {  // drain what this thread issued before the memory goes away
-    for (int c = 0; c < issued_copies; ++c) mbar_wait_bounded(full0 + 8 * (c & 1), (c >> 1) & 1);
-    for (int c = 0; c < issued_z; ++c) mbar_wait_bounded(zfull0 + 8 * (c & 1), (c >> 1) & 1);
-    if (issued_commits > 0) {
-      const int cl = issued_commits - 1;
-      mbar_wait_bounded(done0 + 8 * (cl & 1), (cl >> 1) & 1);
+  if (!ok) {  // drain what the copying and issuing threads started before the memory goes away
+    if (tid == 0)
+      for (int c = 0; c < issued_z; ++c) mbar_wait_bounded(zfull0 + 8 * (c & 1), (c >> 1) & 1);
+    if (tid == kThreads) {
+      for (int c = 0; c < issued_copies; ++c) mbar_wait_bounded(full0 + 8 * (c & 1), (c >> 1) & 1);
+      if (issued_commits > 0) {
+        const int cl = issued_commits - 1;
+        mbar_wait_bounded(done0 + 8 * (cl & 1), (cl >> 1) & 1);
+      }
     }
   }
   tc_fence_before();
@@ -565,7 +602,7 @@ __device__ __forceinline__ void stream_grad_body(const StParams& p, const int bl
 // ---------------------------------------------------------------- launch wrappers
 
 template <bool kId>
-__global__ void __launch_bounds__(kThreads, 1) stream_fwd_kernel(StParams p, int s, int fwd, int collect) {
+__global__ void __launch_bounds__(kThreadsF, 1) stream_fwd_kernel(StParams p, int s, int fwd, int collect) {
   stream_fwd_body<kId>(p, blockIdx.x, s, fwd, collect);
 }
 template <bool kId>
@@ -586,7 +623,7 @@ __device__ __forceinline__ const StParams& load_params(const StParams* table, in
   return s_p;
 }
 template <bool kId>
-__global__ void __launch_bounds__(kThreads, 1) stream_fwd_batch_kernel(const StParams* __restrict__ table,
+__global__ void __launch_bounds__(kThreadsF, 1) stream_fwd_batch_kernel(const StParams* __restrict__ table,
                                                                        const int2* __restrict__ work, int s, int fwd,
                                                                        int collect) {
   __shared__ StParams s_p;
@@ -948,7 +985,7 @@ int extract_stream_widths(const mape_extract_args* a, cudaStream_t st, int wF, i
   auto collk = id ? stream_collect_kernel<true> : stream_collect_kernel<false>;
   const int fsm = fwd_smem(sh.wF), gsm = 2 * grad_stage(sh.wG);
   st_schedule(
-      a->t0, a->T, a->period, [&](int s, int f, int col) { launch(fwdk, gF, kThreads, fsm, st, p, s, f, col); },
+      a->t0, a->T, a->period, [&](int s, int f, int col) { launch(fwdk, gF, kThreadsF, fsm, st, p, s, f, col); },
       [&](int s) { launch(collk, gC, 256, 0, st, p, s); },
       [&](int s) { launch(gradk, gG, kThreads, gsm, st, p, s); });
   MAPE_LAUNCH_CHECK();
@@ -1075,7 +1112,7 @@ int extract_stream_batch_enqueue(const StBatch* plan, cudaStream_t st) {
     st_schedule(
         plan->t0, plan->T, plan->period,
         [&](int s, int f, int col) {
-          launch(fwdk, (unsigned)C.nF, kThreads, fwd_smem(kNB), st, C.table, C.wF, s, f, col);
+          launch(fwdk, (unsigned)C.nF, kThreadsF, fwd_smem(kNB), st, C.table, C.wF, s, f, col);
         },
         [&](int s) { launch(collk, (unsigned)C.nC, 256, 0, st, C.table, C.wC, s); },
         [&](int s) { launch(gradk, (unsigned)C.nG, kThreads, 2 * grad_stage(kNB), st, C.table, C.wG, s); });
