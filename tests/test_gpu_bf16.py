@@ -62,6 +62,22 @@ def _general_basis(make, seed=5):
     return build
 
 
+def tile64_last3():
+    """n = 100, m = 60: the MMA tile holds 60 rows of B' (64 padded, the
+    largest transposed tile); d = 40 (d_pad = 48) leaves a last epilogue round
+    of three 16-column chunks, cut into 8-column units."""
+    return I.make_instance("tile64_n100_m60", 100, 60, c_k=2, c_density=0.2, lo=-4, hi=4, q_k=2, q_density=0.05,
+                           lin_k=5, seed=11)
+
+
+def tile80_resident():
+    """n = 180, m = 80: an identity-topped tile of 80 rows of B' (above the
+    transposed form's 64), state resident in TMEM (d = 100, d_pad = 112: two
+    rounds, the last of three chunks)."""
+    return I.make_instance("tile80_n180_m80", 180, 80, c_k=2, c_density=0.1, lo=-4, hi=4, q_k=2, q_density=0.05,
+                           lin_k=5, seed=12)
+
+
 def _starts(inst, P, seed):
     if inst.n <= 20:
         return I.normal_starts(inst, P, seed=seed).Z0
@@ -72,7 +88,8 @@ def _starts(inst, P, seed):
 @pytest.mark.parametrize("make,P,T,amb", [(I.small_dense, 256, 40, 1.0), (I.medium_sparse, 300, 8, 1.0),
                                           (I.tiny_graver_case, 130, 40, 1.0),
                                           (_general_basis(I.small_dense), 256, 30, 1.0),
-                                          (_general_basis(I.medium_sparse), 200, 6, 4.0)])
+                                          (_general_basis(I.medium_sparse), 200, 6, 4.0),
+                                          (tile64_last3, 200, 10, 2.0), (tile80_resident, 200, 8, 2.0)])
 def test_bf16_per_step(M, make, P, T, amb, precision):
     """The gradient of Eq. (3) jumps by 2 B_i where (Bz)_i changes sign, so it
     is compared on the starts whose sign(Bz) the arithmetic fixes (every
@@ -105,7 +122,8 @@ def test_bf16_per_step(M, make, P, T, amb, precision):
 
 @pytest.mark.parametrize("make,P,T,period", [(I.small_dense, 300, 25, 1), (I.medium_sparse, 1000, 20, 1),
                                              (I.small_dense, 200, 24, 3),
-                                             (_general_basis(I.small_dense), 300, 25, 1)])
+                                             (_general_basis(I.small_dense), 300, 25, 1),
+                                             (tile64_last3, 300, 20, 1), (tile80_resident, 300, 20, 1)])
 def test_bf16_one_launch_equals_single_steps(M, make, P, T, period):
     """T steps in one persistent launch give bitwise the same Z, M, V as T
     launches of one step, and the same set of collected directions (P not a
