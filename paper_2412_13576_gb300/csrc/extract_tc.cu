@@ -180,7 +180,7 @@ __host__ __device__ inline Smem smem_layout(int n_pad, int d_pad, int nterms, in
   s.fl = o;   o = al(o + kTileM * 4, 128);
   s.fnz = o;  o = al(o + kTileM * 4, 128);
   s.slot = o; o = al(o + kTileM * 8, 128);
-  s.misc = o; o = al(o + 16, 16);  // out-of-box mask of the transposed test, any-slot flag
+  s.misc = o; o = al(o + 16 * 4 + 16, 16);  // out-of-box masks of the transposed test (one per warp), any-slot flag
   s.bar = o;  o = al(o + 32, 16);  // mbarriers: gradient, B round(z), forward, drain
   s.tmem = o; o = al(o + 4, 16);
   s.total = o;
@@ -203,8 +203,10 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
   uint8_t* A2 = smem + L.opa2;                          // round(z)
   uint8_t* Sop = smem + L.opa;                          // S, K-major (not transposed)
   uint8_t* sS = smem + L.ss;                            // S, MN-major (transposed)
-  unsigned long long* s_outm = reinterpret_cast<unsigned long long*>(smem + L.misc);
-  int* s_any = reinterpret_cast<int*>(smem + L.misc + 8);
+  // transposed test: warp (quarter q, split k) writes the out-of-box bits of
+  // starts 16 k .. 16 k + 15 over the rows of quarter q to slot 4 q + k
+  uint32_t* s_outw = reinterpret_cast<uint32_t*>(smem + L.misc);
+  int* s_any = reinterpret_cast<int*>(smem + L.misc + 16 * 4);
   float* s_span = reinterpret_cast<float*>(smem + L.span);  // box spans u - l, exact in FP32
   float* s_pz = reinterpret_cast<float*>(smem + L.pz);
   int32_t* s_pk = reinterpret_cast<int32_t*>(smem + L.pk);
@@ -248,10 +250,8 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     s_fl[tid] = kChanged;  // the first collection of a call always counts
     s_fnz[tid] = kNoNz;
   }
-  if (tid == 0) {
-    *s_outm = 0ull;
-    *s_any = 0;
-  }
+  if (tid < 16) s_outw[tid] = 0u;
+  if (tid == 0) *s_any = 0;
   if (tid == 0) {
     for (int b = 0; b < 4; ++b) mbar_init(bar + 8 * b, 1);
   }
@@ -444,7 +444,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
         }
       }
       outm = __reduce_or_sync(0xffffffffu, outm);
-      if (lane == 0 && outm) atomicOr(s_outm, (unsigned long long)outm << (16 * split));
+      if (lane == 0) s_outw[quarter * 4 + split] = outm;  // every warp writes its slot on every test
       if (!kId) {  // first nonzero row: minimum over the 16 rows of the half-warp
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -480,7 +480,10 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     if (part != 0) return;
     long long slot = -1;
     uint32_t f = s_fl[r];
-    if (tr && ((*s_outm >> r) & 1ull)) f |= kOutOfBox;
+    if (tr) {
+      const int k = r >> 4, b = r & 15;
+      if (((s_outw[k] | s_outw[4 + k] | s_outw[8 + k] | s_outw[12 + k]) >> b) & 1u) f |= kOutOfBox;
+    }
     int fnz = s_fnz[r];
     if (active && (f & kChanged) && !(f & (kOutOfBox | kOutId)) && fnz != kNoNz) {
       if (f & kUnexact) {
@@ -573,10 +576,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       s_fl[r] = 0;
       if (!kId) s_fnz[r] = kNoNz;
     }
-    if (tid == 0) {
-      *s_outm = 0ull;
-      *s_any = 0;
-    }
+    if (tid == 0) *s_any = 0;
   };
   uint32_t phaseG = 0, phaseF = 0, phase2 = 0;
   // gradient MMA wait; a time-out anywhere ends the launch for the whole CTA
