@@ -475,7 +475,10 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     if (out) atomicOr(&s_fl[r], kOutOfBox);
     if (!kId && first != kNoNz) atomicMin(&s_fnz[r], first);
   };
-  // ... and appends it in canonical sign (needs a barrier between the two)
+  // ... and appends it in canonical sign (needs a barrier between the two).
+  // decide_slot leaves the slot and the sign in s_slot (2 slot + [negative],
+  // -1 for none) and clears the start's collection state; s_any was cleared
+  // before the barrier that precedes it.
   auto decide_slot = [&]() {
     if (part != 0) return;
     long long slot = -1;
@@ -494,15 +497,18 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
         else atomicOr(p.flags, 1);
       }
     }
-    s_slot[r] = slot;
+    s_slot[r] = slot >= 0 ? (slot << 1) | (fnz & 1) : -1;
     if (slot >= 0) *s_any = 1;
+    s_fl[r] = 0;
+    s_fnz[r] = kNoNz;
   };
   // every lane of the warp executes the (warp-collective) TMEM loads; only
   // lanes whose start has a slot store
   auto write_candidate = [&]() {
     if (*s_any == 0) return;  // CTA-uniform: no start of the tile has a slot
-    long long slot = s_slot[r];
-    int sgn = (s_fnz[r] & 1) ? -1 : 1;
+    const long long sv = s_slot[r];
+    const long long slot = sv >= 0 ? sv >> 1 : -1;
+    const int sgn = (sv & 1) ? -1 : 1;
     int8_t* row = slot >= 0 ? p.cand + slot * p.ldc : nullptr;
     if (kId) {
       // identity rows: g_j = round z_j, held as BF16 in the round(z) operand tile
@@ -529,10 +535,10 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const int rs = 16 * split + hoff + c;
-          const long long sl = s_slot[rs];
-          if (sl >= 0 && i < n) {
-            const int sg = (s_fnz[rs] & 1) ? -1 : 1;
-            p.cand[sl * p.ldc + i] = (int8_t)(sg * __float2int_rn(__uint_as_float(v[c])));
+          const long long sv = s_slot[rs];
+          if (sv >= 0 && i < n) {
+            const int sg = (sv & 1) ? -1 : 1;
+            p.cand[(sv >> 1) * p.ldc + i] = (int8_t)(sg * __float2int_rn(__uint_as_float(v[c])));
           }
         }
       }
@@ -571,13 +577,6 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
         for (int off = n_pad; off < p.ldc; off += 16) *reinterpret_cast<uint4*>(row + off) = make_uint4(0, 0, 0, 0);
     }
   };
-  auto reset_collection = [&]() {
-    if (part == 0) {
-      s_fl[r] = 0;
-      if (!kId) s_fnz[r] = kNoNz;
-    }
-    if (tid == 0) *s_any = 0;
-  };
   uint32_t phaseG = 0, phaseF = 0, phase2 = 0;
   // gradient MMA wait; a time-out anywhere ends the launch for the whole CTA
   auto wait_grad = [&]() -> bool {
@@ -603,6 +602,9 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
         mma_commit(bar2);
       }
     }
+    // ||z||_inf and the group of its first maximiser, from the partials the
+    // last epilogue left (the forward chain is already on its way)
+    if (s > 0) combine_zinf(zinf, kmax);
     // every thread waits itself; the time-out vote joins the barrier after
     // the sign phase (warp-uniform: the TMEM loads are collective)
     bool late = __any_sync(0xffffffffu, !mbar_wait_bounded(barF, phaseF));
@@ -669,6 +671,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       tc_fence_after();
       if (!late) test_candidate();
     }
+    if (collect_prev && tid == 0) *s_any = 0;  // every thread read it in the last write_candidate
     tc_wait_ld();
     tc_fence_before();
     fence_async_smem();
@@ -696,8 +699,6 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       decide_slot();
       __syncthreads();
       write_candidate();
-      __syncthreads();
-      reset_collection();
     }
     if (kId && part == 0) {  // the Adam epilogue recomputes these for round(z) of this step
       s_fnz[r] = kNoNz;
@@ -897,7 +898,6 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       float inv = zinf > 0.f ? fmaxf(1.f / zinf - 1.f, 0.f) : INFINITY;
       p.dbg_phi[pg] = L1 + p.lambda1 * FR + p.lambda2 * inv;
     }
-    combine_zinf(zinf, kmax);
   }
 
   // the candidate of the last step
@@ -920,6 +920,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     } else if (!late) {
       test_candidate();
     }
+    if (tid == 0) *s_any = 0;
     tc_wait_ld();
     if (__syncthreads_or(late)) {
       if (tid == 0) atomicOr(p.flags, 16);
