@@ -347,9 +347,6 @@ __global__ void dominance_kernel(const int8_t* __restrict__ G, int n, int ldg, i
                                  const uint32_t* __restrict__ p_idx, const uint64_t* __restrict__ p_pk,
                                  const ulonglong2* __restrict__ p_sig, const int32_t* __restrict__ p_l1,
                                  uint8_t* __restrict__ dom) {
-  __shared__ uint64_t t_pk[kTile];
-  __shared__ ulonglong2 t_sig[kTile];
-  __shared__ int32_t t_l1[kTile];
   __shared__ int s_maxl1;
   const int4 gb = gblk[blockIdx.x];  // first position, rows, pattern list
   const int nsub = 1 << kb;
@@ -385,36 +382,21 @@ __global__ void dominance_kernel(const int8_t* __restrict__ G, int n, int ldg, i
   const ulonglong2 gs = mine ? p_sig[q] : make_ulonglong2(0, 0);
   const uint64_t gsp = ~gs.x, gsn = ~gs.y;
   const bool want_same = (mode & 1) != 0, want_flip = (mode & 2) != 0;
-  bool done = !mine || dom[k];
-  for (uint32_t base = lo; base < hi; base += kTile) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < kTile; t += blockDim.x) {
-      const uint32_t h = base + t;
-      if (h < hi) {
-        t_pk[t] = p_pk[h];
-        t_sig[t] = p_sig[h];
-        t_l1[t] = p_l1[h];
-      } else {
-        t_l1[t] = 0x7fffffff;
-      }
-    }
-    __syncthreads();
-    if (done) continue;
-#pragma unroll 4
-    for (int t = 0; t < kTile; ++t) {
-      if (t_l1[t] >= gl1) break;  // the rest of the list is not shorter
-      const uint64_t hk = t_pk[t];
-      const uint32_t hp = (uint32_t)hk, hn = (uint32_t)(hk >> 32);
-      const bool cand = (want_same && ((hp & np) | (hn & nn)) == 0) || (want_flip && ((hp & nn) | (hn & np)) == 0);
-      if (!cand) continue;
-      const ulonglong2 hs = t_sig[t];
-      const bool cand2 = (want_same && ((hs.x & gsp) | (hs.y & gsn)) == 0) ||
-                         (want_flip && ((hs.x & gsn) | (hs.y & gsp)) == 0);
-      if (cand2 && dominates(G, n, ldg, W, masks, p_idx[base + t], k)) {
-        done = true;
-        dom[k] = 1;
-        break;
-      }
+  if (!mine || dom[k]) return;
+  // every thread of the block reads the same source row at the same time: the
+  // loads are L1 broadcasts, and no block barrier is needed
+  for (uint32_t h = lo; h < hi; ++h) {
+    if (p_l1[h] >= gl1) break;  // the rest of the list is not shorter
+    const uint64_t hk = p_pk[h];
+    const uint32_t hp = (uint32_t)hk, hn = (uint32_t)(hk >> 32);
+    const bool cand = (want_same && ((hp & np) | (hn & nn)) == 0) || (want_flip && ((hp & nn) | (hn & np)) == 0);
+    if (!cand) continue;
+    const ulonglong2 hs = p_sig[h];
+    const bool cand2 = (want_same && ((hs.x & gsp) | (hs.y & gsn)) == 0) ||
+                       (want_flip && ((hs.x & gsn) | (hs.y & gsp)) == 0);
+    if (cand2 && dominates(G, n, ldg, W, masks, p_idx[h], k)) {
+      dom[k] = 1;
+      return;
     }
   }
 }
