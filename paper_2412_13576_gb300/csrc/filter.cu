@@ -383,20 +383,32 @@ __global__ void dominance_kernel(const int8_t* __restrict__ G, int n, int ldg, i
   const uint64_t gsp = ~gs.x, gsn = ~gs.y;
   const bool want_same = (mode & 1) != 0, want_flip = (mode & 2) != 0;
   if (!mine || dom[k]) return;
-  // every thread of the block reads the same source row at the same time: the
-  // loads are L1 broadcasts, and no block barrier is needed
-  for (uint32_t h = lo; h < hi; ++h) {
-    if (p_l1[h] >= gl1) break;  // the rest of the list is not shorter
-    const uint64_t hk = p_pk[h];
-    const uint32_t hp = (uint32_t)hk, hn = (uint32_t)(hk >> 32);
-    const bool cand = (want_same && ((hp & np) | (hn & nn)) == 0) || (want_flip && ((hp & nn) | (hn & np)) == 0);
-    if (!cand) continue;
-    const ulonglong2 hs = p_sig[h];
-    const bool cand2 = (want_same && ((hs.x & gsp) | (hs.y & gsn)) == 0) ||
-                       (want_flip && ((hs.x & gsn) | (hs.y & gsp)) == 0);
-    if (cand2 && dominates(G, n, ldg, W, masks, p_idx[h], k)) {
-      dom[k] = 1;
-      return;
+  // every thread of the block reads the same source rows at the same time:
+  // the loads are L1 broadcasts, and no block barrier is needed; four rows'
+  // words are loaded at once
+  for (uint32_t h0 = lo; h0 < hi; h0 += 4) {
+    int32_t l1v[4];
+    uint64_t pkv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool in = h0 + u < hi;
+      l1v[u] = in ? p_l1[h0 + u] : 0x7fffffff;
+      pkv[u] = in ? p_pk[h0 + u] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (l1v[u] >= gl1) return;  // the rest of the list is not shorter (or past its end)
+      const uint32_t hp = (uint32_t)pkv[u], hn = (uint32_t)(pkv[u] >> 32);
+      const bool cand = (want_same && ((hp & np) | (hn & nn)) == 0) || (want_flip && ((hp & nn) | (hn & np)) == 0);
+      if (!cand) continue;
+      const uint32_t h = h0 + u;
+      const ulonglong2 hs = p_sig[h];
+      const bool cand2 = (want_same && ((hs.x & gsp) | (hs.y & gsn)) == 0) ||
+                         (want_flip && ((hs.x & gsn) | (hs.y & gsp)) == 0);
+      if (cand2 && dominates(G, n, ldg, W, masks, p_idx[h], k)) {
+        dom[k] = 1;
+        return;
+      }
     }
   }
 }
