@@ -194,10 +194,16 @@ __global__ void bitonic_local_kernel(const int8_t* __restrict__ rows, int ldc, u
   }
 }
 
+constexpr int kRunWarpRows = 32;      // runs up to this length are sorted by one warp ...
+constexpr int kRunWarpBytes = 8192;   // ... when their rows fit in its share of shared memory
+constexpr int kRunWarps = 4;          // warps (runs) per block of the warp kernel (32 KB)
+
 // runs of equal keys among the first K sorted pairs: (start, length) of
-// every run of two or more, and the longest length
-__global__ void key_runs_kernel(const uint64_t* __restrict__ key, int64_t K, int2* __restrict__ runs,
-                                unsigned int* __restrict__ nruns, unsigned int* __restrict__ maxlen) {
+// every run of two or more (short ones, that one warp sorts, from the front
+// of `runs`, the others from the back), their counts and the longest length
+__global__ void key_runs_kernel(const uint64_t* __restrict__ key, int64_t K, int ldc, int2* __restrict__ runs,
+                                int64_t runs_cap, unsigned int* __restrict__ nshort, unsigned int* __restrict__ nlong,
+                                unsigned int* __restrict__ maxlen) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= K) return;
   if (i > 0 && key[i] == key[i - 1]) return;      // not the start of a run
@@ -206,21 +212,92 @@ __global__ void key_runs_kernel(const uint64_t* __restrict__ key, int64_t K, int
   while (j < K && key[j] == key[i]) ++j;
   const unsigned int len = (unsigned int)(j - i);
   atomicMax(maxlen, len);
-  const unsigned int at = atomicAdd(nruns, 1u);
-  runs[at] = make_int2((int)i, (int)len);
+  if (len <= (unsigned)kRunWarpRows && (int64_t)len * ldc <= kRunWarpBytes) {
+    const unsigned int at = atomicAdd(nshort, 1u);
+    runs[at] = make_int2((int)i, (int)len);
+  } else {
+    const unsigned int at = atomicAdd(nlong, 1u);
+    runs[runs_cap - 1 - at] = make_int2((int)i, (int)len);
+  }
+}
+
+constexpr int kRunStageBytes = 32 * 1024;  // rows of a run staged in shared memory up to this size
+constexpr int kRunStageRows = 256;
+
+// lexicographic order of two staged rows (positions a, b; kEmpty last), bytes 8 on
+__device__ __forceinline__ int cmp_staged(const int8_t* srow, int ldc, uint32_t a, uint32_t b) {
+  if (a == b) return 0;
+  if (a == kEmpty) return 1;
+  if (b == kEmpty) return -1;
+  const uint32_t* pa = reinterpret_cast<const uint32_t*>(srow + (size_t)a * ldc);
+  const uint32_t* pb = reinterpret_cast<const uint32_t*>(srow + (size_t)b * ldc);
+  for (int c = 2; c < ldc / 4; ++c) {
+    const uint32_t x = __byte_perm(pa[c], 0, 0x0123) ^ 0x80808080u;
+    const uint32_t y = __byte_perm(pb[c], 0, 0x0123) ^ 0x80808080u;
+    if (x != y) return x < y ? -1 : 1;
+  }
+  return 0;
+}
+
+// one warp per short run: the run's rows are copied into the warp's share of
+// shared memory, and a bitonic network over the lanes (one position each,
+// partners by shuffle) orders them from byte 8 on
+__global__ void run_sort_warp_kernel(const int8_t* __restrict__ rows, int ldc, const int2* __restrict__ runs,
+                                     unsigned int nruns, uint32_t* __restrict__ idx) {
+  extern __shared__ __align__(16) int8_t sm_runs[];  // kRunWarps x kRunWarpBytes
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned int run = blockIdx.x * kRunWarps + w;
+  if (run >= nruns) return;  // warp-uniform
+  const int2 rr = runs[run];
+  const int len = rr.y;
+  int8_t* srow = sm_runs + w * kRunWarpBytes;
+  const uint32_t orig = lane < len ? idx[rr.x + lane] : kEmpty;
+  const int q = ldc / 16, tot = len * q;
+  for (int base = 0; base < tot; base += 32) {  // the same trip count in every lane
+    const int e = base + lane;
+    const uint32_t src = __shfl_sync(0xffffffffu, orig, (e < tot ? e : tot - 1) / q);
+    if (e < tot) reinterpret_cast<uint4*>(srow)[e] = reinterpret_cast<const uint4*>(rows + (int64_t)src * ldc)[e % q];
+  }
+  __syncwarp();
+  int np = 2;
+  while (np < len) np <<= 1;
+  uint32_t pos = lane < len ? (uint32_t)lane : kEmpty;
+  for (int k = 2; k <= np; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const uint32_t other = __shfl_xor_sync(0xffffffffu, pos, j);
+      const bool lower = (lane & j) == 0, ascending = (lane & k) == 0;
+      const int c = cmp_staged(srow, ldc, lower ? pos : other, lower ? other : pos);  // lower vs upper element
+      const bool swap = ascending ? c > 0 : c < 0;
+      if (swap) pos = other;
+    }
+  }
+  const uint32_t out = __shfl_sync(0xffffffffu, orig, (int)(pos == kEmpty ? 0 : pos));
+  if (lane < len) idx[rr.x + lane] = out;
 }
 
 constexpr int kRunMax = 2048;  // longest run one block sorts
 
-// one block per run: bitonic on the run's row indices (padded with the
-// sentinel to a power of two) comparing the rows from byte 8 on
+// one block per (long) run: bitonic on the run (padded with the sentinel to a power
+// of two) comparing the rows from byte 8 on; a run whose rows fit is first
+// copied into shared memory, and the network then sorts positions in it
 __global__ void run_sort_kernel(const int8_t* __restrict__ rows, int ldc, const int2* __restrict__ runs,
                                 uint32_t* __restrict__ idx) {
   __shared__ uint32_t s[kRunMax];
+  __shared__ uint32_t s_orig[kRunStageRows];
+  extern __shared__ __align__(16) int8_t srow[];  // kRunStageBytes
   const int2 rr = runs[blockIdx.x];
   int np = 2;
   while (np < rr.y) np <<= 1;
-  for (int t = threadIdx.x; t < np; t += blockDim.x) s[t] = t < rr.y ? idx[rr.x + t] : kEmpty;
+  const bool staged = rr.y <= kRunStageRows && (int64_t)rr.y * ldc <= kRunStageBytes;
+  if (staged) {
+    for (int t = threadIdx.x; t < rr.y; t += blockDim.x) s_orig[t] = idx[rr.x + t];
+    __syncthreads();
+    const int w = ldc / 16;
+    for (int e = threadIdx.x; e < rr.y * w; e += blockDim.x)
+      reinterpret_cast<uint4*>(srow)[e] = reinterpret_cast<const uint4*>(rows + (int64_t)s_orig[e / w] * ldc)[e % w];
+  }
+  for (int t = threadIdx.x; t < np; t += blockDim.x)
+    s[t] = t < rr.y ? (staged ? (uint32_t)t : idx[rr.x + t]) : kEmpty;
   __syncthreads();
   for (int k = 2; k <= np; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
@@ -228,7 +305,7 @@ __global__ void run_sort_kernel(const int8_t* __restrict__ rows, int ldc, const 
         const int i = (t / j) * 2 * j + (t % j), l = i + j;
         const bool ascending = (i & k) == 0;
         const uint32_t a = s[i], b = s[l];
-        const int c = cmp_keyed(rows, ldc, 0, a, 0, b);  // equal keys: bytes 8 on
+        const int c = staged ? cmp_staged(srow, ldc, a, b) : cmp_keyed(rows, ldc, 0, a, 0, b);  // equal keys: bytes 8 on
         if ((ascending && c > 0) || (!ascending && c < 0)) {
           s[i] = b;
           s[l] = a;
@@ -237,7 +314,7 @@ __global__ void run_sort_kernel(const int8_t* __restrict__ rows, int ldc, const 
       __syncthreads();
     }
   }
-  for (int t = threadIdx.x; t < rr.y; t += blockDim.x) idx[rr.x + t] = s[t];
+  for (int t = threadIdx.x; t < rr.y; t += blockDim.x) idx[rr.x + t] = staged ? s_orig[s[t]] : s[t];
 }
 
 __global__ void gather_rows_kernel(const int8_t* __restrict__ rows, int ldc, const uint32_t* __restrict__ idx,
@@ -284,16 +361,22 @@ int sort_row_indices(const int8_t* rows, int ldc, uint32_t* idx, uint64_t* key, 
   if (npad < 2) return MAPE_OK;
   mape_detail::launch(key_rows_kernel, (unsigned)ceil_div(npad, 256), 256, 0, st, rows, ldc, idx, npad, key);
   bitonic_sort<false>(rows, ldc, idx, key, npad, st);
-  MAPE_CUDA_TRY(cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned int), st));
-  mape_detail::launch(key_runs_kernel, (unsigned)ceil_div(K, 256), 256, 0, st, key, K, runs, counters, counters + 1);
+  const int64_t runs_cap = K / 2 + 1;
+  MAPE_CUDA_TRY(cudaMemsetAsync(counters, 0, 3 * sizeof(unsigned int), st));
+  mape_detail::launch(key_runs_kernel, (unsigned)ceil_div(K, 256), 256, 0, st, key, K, ldc, runs, runs_cap, counters,
+                      counters + 1, counters + 2);
   MAPE_LAUNCH_CHECK();
-  unsigned int hc[2] = {0, 0};
+  unsigned int hc[3] = {0, 0, 0};  // short runs, long runs, longest
   MAPE_CUDA_TRY(cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, st));
   MAPE_CUDA_TRY(cudaStreamSynchronize(st));
-  if (hc[1] > (unsigned)kRunMax) {
+  if (hc[2] > (unsigned)kRunMax) {
     bitonic_sort<true>(rows, ldc, idx, key, npad, st);  // the rows decide every comparison
-  } else if (hc[0] > 0) {
-    mape_detail::launch(run_sort_kernel, hc[0], 256, 0, st, rows, ldc, runs, idx);
+  } else {
+    if (hc[0] > 0)
+      mape_detail::launch(run_sort_warp_kernel, (unsigned)ceil_div(hc[0], kRunWarps), 32 * kRunWarps,
+                          (size_t)kRunWarps * kRunWarpBytes, st, rows, ldc, runs, hc[0], idx);
+    if (hc[1] > 0)
+      mape_detail::launch(run_sort_kernel, hc[1], 128, kRunStageBytes, st, rows, ldc, runs + (runs_cap - hc[1]), idx);
   }
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
@@ -313,7 +396,7 @@ extern "C" size_t mape_dedup_workspace_bytes(int64_t count, int32_t ldc) {
   s.take<uint32_t>((size_t)next_pow2((uint64_t)(count > 0 ? count : 1)));  // sorted indices
   s.take<uint64_t>((size_t)next_pow2((uint64_t)(count > 0 ? count : 1)));  // their sort keys
   s.take<int2>((size_t)(count > 0 ? count : 1) / 2 + 1);          // runs of equal keys
-  s.take<unsigned int>(2);                                        // run count, longest run
+  s.take<unsigned int>(3);                                        // short and long run counts, longest run
   s.take<unsigned long long>(1);                                  // counter
   return s.bytes();
 }
@@ -336,7 +419,7 @@ extern "C" int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t 
   uint32_t* idx = cv.take<uint32_t>((size_t)npad_cap);
   uint64_t* keys = cv.take<uint64_t>((size_t)npad_cap);
   int2* runs = cv.take<int2>((size_t)count / 2 + 1);
-  unsigned int* run_counters = cv.take<unsigned int>(2);
+  unsigned int* run_counters = cv.take<unsigned int>(3);
   unsigned long long* dK = cv.take<unsigned long long>(1);
   if (!cv.ok) return MAPE_ERR_CAPACITY;
   cudaStream_t st = as_stream(stream);
