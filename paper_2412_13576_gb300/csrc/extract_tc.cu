@@ -1,36 +1,49 @@
 // Algorithm 2 (§3.2) on the 5th-generation tensor cores: one persistent
 // kernel runs all T Adam steps; each CTA owns 64 starts for the whole run.
 //
-// Start r of the tile is row r of every MMA (M = 64), held by TMEM lane
-// 32 * (r / 16) + r % 16 (lanes 0-15 of each 32-lane quarter).  Per step, with
-// B in shared memory as BF16 (exact: |B_ij| <= 256):
-//   D1 = hi(Z) . B^T + lo(Z) . B^T  (M=64, N=n_pad, K=d_pad) -> TMEM cols [0, n_pad)
-//        with hi = bf16(z), lo = bf16(z - hi): z carried to ~16 significant
-//        bits, so B z is as accurate as an FP32 dot product (one term, hi only,
-//        is the faster and coarser MAPE_PREC_BF16X1)
-//   D2 = bf16(round Z) . B^T     (same shape, previous step) -> TMEM cols [256, 256+n_pad)
-//        exact: |round z| <= 256 is exact in BF16, every partial sum is an
-//        integer below 2^24 and FP32 accumulation is exact; D2 holds g = B round(z)
-//   S  = sign(D1) as BF16 {-1,0,1} written to shared memory
-//   G  = S . B                   (M=64, N=d_pad, K=n_pad)   -> TMEM cols [0, d_pad)
-//        B is read through an MN-major descriptor of the same shared tile
-//        (a transposed K-major copy is kept instead when it fits)
-//   grad = G + lambda1 (ceil z + floor z - 2 z) + inverse-norm term; Adam on
-//   the FP32 master z, m, v, held for the whole run in TMEM lanes 16-31 of
-//   each quarter (the lanes an M=64 accumulator leaves free: z, m, v of the
-//   tile's starts in columns [0, d), [d, 2d), [2d, 3d)) when 3 d_pad <= 512,
-//   else blocked [tile][d/4][64][4] in global memory (L2 resident);
-//   the new bf16(z), bf16(round z) operands are written for the next step.
-// The candidate of step t (D2 of step t+1) is tested (C4, nonzero), signed
-// canonically and appended while the G MMA runs.
+// Per step, with B in shared memory as BF16 (exact: |B_ij| <= 256), and
+// hi = bf16(z), lo = bf16(z - hi) (z carried to ~16 significant bits, so that
+// B z is as accurate as an FP32 dot product; hi alone is the faster and
+// coarser MAPE_PREC_BF16X1):
+//   forward  B hi(z) + B lo(z), and g = B bf16(round z) of the previous step's
+//            iterate (exact: |round z| <= 256 is exact in BF16, every partial
+//            sum is an integer below 2^24 and FP32 accumulation is exact)
+//   S = sign(B z) as BF16 {-1, 0, 1} in shared memory
+//   G = S . B      (M = 64 starts, N = d_pad, K = n_pad rows of B), B read
+//            through an MN-major descriptor of the forward tile (or a
+//            transposed K-major copy when it fits)
+//   grad = G + lambda1 (ceil z + floor z - 2 z) + the inverse-norm term; Adam
+//   on the FP32 master z, m, v, held for the whole run in TMEM lanes 16-31
+//   of each 32-lane quarter (the lanes an M = 64 accumulator leaves free: z,
+//   m, v in columns [0, d), [d, 2d), [2d, 3d)) when 3 d_pad <= 512, else
+//   blocked [tile][d/4][64][4] in global memory (L2 resident); the new
+//   bf16(z) and bf16(round z) operands are written for the next step.
+// The forward product takes one of two forms.  For tiles of at most 64 rows
+// of B it is transposed: one MMA chain D^T = B_tile . [hi(Z); lo(Z); round(Z)]^T
+// (M = 64 rows of B, N = 64 starts per operand tile, K = d_pad), so that TMEM
+// lane i holds row i of B for every start and S is written MN-major; that is
+// 10 MMA instructions for d = 160 instead of 30 (an MMA instruction costs
+// about the same whatever its M and N).  Otherwise start r is row r of
+// D1 = hi(Z) . B^T + lo(Z) . B^T and D2 = bf16(round Z) . B^T (M = 64,
+// N = n_pad).  Row r of an M = 64 accumulator is TMEM lane 32 (r / 16) + r % 16
+// (lanes 0-15 of each quarter).  The candidate of step t (D2 of step t + 1)
+// is tested (C4, nonzero), signed canonically and appended while the
+// gradient MMA runs.
 //
 // 16 warps: warp w reads TMEM lane quarter w % 4 (the only lanes it may
-// access) with the 16x32bx2 shape, so its two half-warps take the two 8-column
-// halves of one 16-column chunk for the same 16 starts; warp w handles every
-// 4th chunk starting at chunk w / 4.  Each start is thus served by 8 threads
-// (4 chunk groups x 2 halves).  Operands are stored in the canonical
-// no-swizzle K-major layout: 8 rows x 16 bytes core matrices, K-adjacent core
-// matrices 128 bytes apart (LBO), 8-row groups (K/8) * 128 bytes apart (SBO).
+// access) with the 16x32bx2 shape, so its two half-warps take the two halves
+// of one column unit for the same 16 starts (or, transposed, rows of B);
+// split w / 4 takes every 4th unit.  Each start is thus served by 8 threads
+// (4 splits x 2 halves).  Operands are stored in the canonical no-swizzle
+// K-major layout: 8 rows x 16 bytes core matrices, K-adjacent core matrices
+// 128 bytes apart (LBO), 8-row groups (K/8) * 128 bytes apart (SBO).
+//
+// The Adam epilogue is limited by the integer/logic pipe more than by TMEM
+// latency: sign tests and rounding trackers are written as saturating
+// multiplies, sums and one maximum per unit, which the FMA pipe takes
+// (measured 5 % faster per launch than compares and selects), while issuing
+// the next unit's TMEM loads ahead of the current unit's arithmetic measured
+// slower.
 //
 // Every wait on the MMA barrier is bounded; on time-out the CTA records flag
 // 16, leaves the loop together (block-wide vote), frees its TMEM and returns.
@@ -87,11 +100,21 @@ using Width = std::integral_constant<int, W>;
 // sign as a float: +-1, and 0 for 0 (and NaN)
 __device__ __forceinline__ float sgn1(float x) { return fabsf(x) > 0.f ? copysignf(1.f, x) : 0.f; }
 
-// bf16 pair {sign(a), sign(b)} (low half a): 0x3f80 = 1, 0xbf80 = -1, 0 for 0 and NaN
+// the same sign from the FMA pipe instead of a compare and a select: |x|
+// 2^75 2^75 saturated to [0, 1] (two exact scalings, so that a subnormal x
+// also reaches 1; NaN gives 0) with the sign of x copied onto it, so that
+// zero and NaN give a signed zero
+__device__ __forceinline__ float sgn_sat(float x) {
+  const float t = fabsf(x) * 0x1p75f;
+  float a;
+  asm("mul.sat.f32 %0, %1, %2;" : "=f"(a) : "f"(t), "f"(0x1p75f));
+  return copysignf(a, x);
+}
+
+// bf16 pair {sign(a), sign(b)} (low half a): 0x3f80 = 1, 0xbf80 = -1, a signed
+// zero (0x0000 or 0x8000) for zero and NaN
 __device__ __forceinline__ uint32_t sign_bf16x2(float a, float b) {
-  const uint32_t sa = fabsf(a) > 0.f ? (((__float_as_uint(a) >> 16) & 0x8000u) | 0x3f80u) : 0u;
-  const uint32_t sb = fabsf(b) > 0.f ? ((__float_as_uint(b) & 0x80000000u) | 0x3f800000u) : 0u;
-  return sa | sb;
+  return pack_bf16x2(sgn_sat(a), sgn_sat(b));
 }
 
 // d/dz of the integrality term (ceil z - z)(z - floor z) of Eq. (3):
@@ -99,7 +122,7 @@ __device__ __forceinline__ uint32_t sign_bf16x2(float a, float b) {
 // the integers, +-1 - 2 e between them); every step is exact in FP32
 __device__ __forceinline__ float frac_grad(float z, float rz) {
   const float e = z - rz;
-  return fmaf(-2.f, e, sgn1(e));
+  return fmaf(-2.f, e, sgn_sat(e));
 }
 
 // square root and reciprocal of the Adam denominator (v >= 0, den >= eps > 0)
@@ -762,7 +785,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       }
       if (kId) {
 #pragma unroll
-        for (int c = 0; c < W; ++c) g[c] += sgn1(zc[c]);
+        for (int c = 0; c < W; ++c) g[c] += sgn_sat(zc[c]);
       }
     };
     // debug outputs of the first step: the integrality sum of Phi, the l1 norm
@@ -796,6 +819,9 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     float nzinf = 0.f;
     int nkmax = kNoNz, first_id = kNoNz;
     bool changed = false, unexact = false, out_id = false;
+    // rounding changes: the sum of |rint(z_new) - rint(z_old)| over the
+    // thread's coordinates (integers, exactly summed; 0 iff none changed)
+    float dsum = 0.f;
     auto epi_unit = [&](auto Wc, int ub) {
       constexpr int W = decltype(Wc)::value;
       const int c0 = ub + W * half;
@@ -821,8 +847,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
         // padding coordinates (z = 0 throughout) and inactive starts leave
         // every tracker unchanged: their roundings never change, are 0, are
         // within any box and never beat a real coordinate's |z| or index
-        changed |= rn[c] != rz[c];
-        unexact |= fabsf(rn[c]) > 256.f;
+        dsum += fabsf(rn[c] - rz[c]);
       }
       float cmax = fabsf(zn[0]);
 #pragma unroll
@@ -835,12 +860,9 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
           const float4 q4 = *reinterpret_cast<const float4*>(s_span + c0 + 4 * k);
           sp[4 * k] = q4.x; sp[4 * k + 1] = q4.y; sp[4 * k + 2] = q4.z; sp[4 * k + 3] = q4.w;
         }
-        bool nz = false;
+        const bool nz = cmax > 0.5f;  // some rint(z_j) != 0
 #pragma unroll
-        for (int c = 0; c < W; ++c) {
-          out_id |= fabsf(rn[c]) > sp[c];
-          nz |= rn[c] != 0.f;
-        }
+        for (int c = 0; c < W; ++c) out_id |= fabsf(rn[c]) > sp[c];
         if (first_id == kNoNz && nz) {
 #pragma unroll
           for (int c = 0; c < W; ++c)
@@ -884,6 +906,9 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
       s_pfr[part * kTileM + r] = frac;
       if (kId) s_pl1[part * kTileM + r] += l1_id;
     }
+    changed = dsum != 0.f;
+    // |rint(z_j)| > 256 for some j iff max |z_j| > 256.5 (256.5 rounds to 256)
+    unexact = nzinf > 256.5f;
     uint32_t fbits = (changed ? kChanged : 0u) | (unexact ? kUnexact : 0u) | (out_id ? kOutId : 0u);
     if (fbits) atomicOr(&s_fl[r], fbits);
     if (kId && first_id != kNoNz) atomicMin(&s_fnz[r], first_id);
