@@ -526,8 +526,11 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     s_fnz[r] = kNoNz;
   };
   // every lane of the warp executes the (warp-collective) TMEM loads; only
-  // lanes whose start has a slot store
-  auto write_candidate = [&]() {
+  // lanes whose start has a slot store.  In the transposed form the rows of
+  // the tile come from vd, the B round(z) words the sign phase loaded for the
+  // candidate test: a TMEM load here would run beside the gradient MMA, and
+  // the two slow each other down.
+  auto write_candidate = [&](const uint32_t (&vd)[8]) {
     if (*s_any == 0) return;  // CTA-uniform: no start of the tile has a slot
     const long long sv = s_slot[r];
     const long long slot = sv >= 0 ? sv >> 1 : -1;
@@ -549,11 +552,8 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     }
     if (tr) {
       // rows of the tile from D2^T: this thread holds row i of B for the 8
-      // starts 16 split + hoff + c (warp-collective loads)
+      // starts 16 split + hoff + c
       if (quarter < nch) {
-        uint32_t v[8];
-        tmem_ld8x2(tmem + lane_off + colD2 + 16 * split, v);
-        tc_wait_ld();
         const int i = r0 + quarter * 16 + (lane & 15);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -561,7 +561,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
           const long long sv = s_slot[rs];
           if (sv >= 0 && i < n) {
             const int sg = (sv & 1) ? -1 : 1;
-            p.cand[(sv >> 1) * p.ldc + i] = (int8_t)(sg * __float2int_rn(__uint_as_float(v[c])));
+            p.cand[(sv >> 1) * p.ldc + i] = (int8_t)(sg * __float2int_rn(__uint_as_float(vd[c])));
           }
         }
       }
@@ -635,13 +635,13 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     tc_fence_after();
     // (2) S = sign(D1) into shared memory; test the previous step's candidate
     float l1 = 0.f;
+    uint32_t vd[8];  // transposed form: B round(z) of the previous step's candidate
     if (tr) {
       // this thread: row i of the tile (lane), starts 16 split + hoff + c
       // (columns); B z = B hi(z) + B lo(z)
       float y[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) y[c] = 0.f;
-      uint32_t vd[8];  // B round(z) of the previous step's candidate
       if (quarter < nch) {  // warp-uniform: the quarter holds rows of the tile
         uint32_t vh[8], vl[8];
         tmem_ld8x2(tmem + lane_off + 16 * split, vh);
@@ -721,7 +721,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     if (collect_prev) {
       decide_slot();
       __syncthreads();
-      write_candidate();
+      write_candidate(vd);
     }
     if (kId && part == 0) {  // the Adam epilogue recomputes these for round(z) of this step
       s_fnz[r] = kNoNz;
@@ -935,8 +935,8 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     bool late = __any_sync(0xffffffffu, !mbar_wait_bounded(bar2, phase2));
     phase2 ^= 1;
     tc_fence_after();
+    uint32_t vd[8];
     if (tr) {
-      uint32_t vd[8];
       if (quarter < nch && !late) {
         tmem_ld8x2(tmem + lane_off + colD2 + 16 * split, vd);
         tc_wait_ld();
@@ -952,7 +952,7 @@ __device__ __forceinline__ void extract_tc_body(const TcParams& p, const int til
     } else {
       decide_slot();
       __syncthreads();
-      write_candidate();
+      write_candidate(vd);
     }
   }
   // arrives once every MMA of the CTA has completed (all were issued by this
