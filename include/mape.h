@@ -170,7 +170,9 @@ int mape_phi_grad(const int32_t* B, int32_t n, int32_t d, const float* Z,
 typedef struct {
   int32_t n, d, P;
   const int32_t* B;        /* [n x d] int32                                  */
-  const int32_t* span;     /* [n] int32, u - l (C4)                           */
+  const int32_t* span;     /* [n] int32, u - l (C4), each in [0, 127]: device  */
+                           /* memory, not checked by this call (a larger span  */
+                           /* lets values beyond int8 into the candidate rows) */
   float* Z;                /* [P x d] in/out                                  */
   float* M;                /* [P x d] in/out, Adam first moment               */
   float* V;                /* [P x d] in/out, Adam second moment              */

@@ -196,3 +196,4 @@ def test_bf16_shape_limits(M):
                   ldc=5008, workspace=torch.zeros(64, dtype=torch.uint8, device="cuda"))
     assert e.value.code == -2
     assert M.lib().mape_extract_workspace_bytes(300, 280, 128, M.PREC_BF16) > 0
+
