@@ -197,3 +197,49 @@ def test_bf16_shape_limits(M):
     assert e.value.code == -2
     assert M.lib().mape_extract_workspace_bytes(300, 280, 128, M.PREC_BF16) > 0
 
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_bf16_unexact_rounding_flagged(M, precision):
+    """round(z) enters the MMA as BF16, exact only while |round z_j| <= 256.
+    A candidate whose rounding reaches beyond (the kernel tests max |z_j| >
+    256.5, the same condition) is not appended and raises flag 2; every other
+    candidate of the run is the oracle's collection of the GPU's iterates.
+    The basis is B0 U with U = I + 200 e_0 e_1^T (unimodular, entries <= 201,
+    exact in BF16), so that round z = (-399, 2, ...) or (257, -1, ...) still
+    maps to a short g inside the box (spans 120); (256, -1, ...) is kept."""
+    import torch
+    inst = I.make_instance("unexact_n12_m3", 12, 3, c_k=1, c_density=0.3, lo=-60, hi=60, q_k=1, q_density=0.1,
+                           lin_k=3, seed=31)
+    U = np.eye(inst.d, dtype=np.int64)
+    U[0, 1] = 200
+    Bg = (inst.B.astype(np.int64) @ U).astype(np.int32)
+    assert O.kernel_basis_check(inst.A, Bg) and np.abs(Bg).max() <= 256
+    P, T = 192, 4
+    rng = np.random.default_rng(9)
+    Z0 = (rng.integers(-2, 3, size=(P, inst.d)) + 0.2 * rng.standard_normal((P, inst.d))).astype(np.float32)
+    Z0[:64, 0], Z0[:64, 1] = -399.3, 2.1        # dropped: U round z = (1, 2, ...)
+    Z0[64:96, 0], Z0[64:96, 1] = 256.4, -1.0    # kept: rounds to (256, -1, ...)
+    Z0[96:128, 0], Z0[96:128, 1] = 256.6, -1.1  # dropped: rounds to (257, -1, ...)
+    ldc = M.round16(inst.n)
+    cfg = M.default_config(precision=precision, T=1)
+    B, span = dev(Bg), dev((inst.u - inst.l).astype(np.int32))
+    Z = dev(Z0)
+    Mm = torch.zeros_like(Z)
+    V = torch.zeros_like(Z)
+    cand = torch.zeros((P * T + 8, ldc), dtype=torch.int8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    expect, kept = set(), set()
+    for t in range(T):
+        M.extract(B, span, Z, Mm, V, t0=t, T=1, cfg=cfg, cand=cand, cand_count=cnt, flags=flags, ldc=ldc)
+        torch.cuda.synchronize()
+        z1 = Z.cpu().numpy()
+        exact = np.all(np.abs(np.rint(z1.astype(np.float64))) <= 256, axis=1)
+        assert not exact[:64].any() and exact[64:96].all() and not exact[96:128].any()
+        expect |= O.collect(inst.A, Bg, inst.l, inst.u, z1[exact])
+        kept |= O.collect(inst.A, Bg, inst.l, inst.u, z1[64:96])
+    assert int(flags.item()) == 2
+    got = rows_set(cand[: int(cnt.item())].cpu().numpy(), inst.n)
+    assert got == expect
+    assert kept and kept <= got
