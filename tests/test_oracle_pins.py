@@ -491,3 +491,39 @@ def test_lll_hand_example_and_conditions():
     R = np.array(O.lll_reduce(Bh), dtype=np.int64)
     shortest = min(np.linalg.norm(g) for g in O.kernel_box(inst.A, 2))
     assert np.linalg.norm(R[:, 0]) <= 2 ** ((R.shape[1] - 1) / 2) * shortest + 1e-9
+
+
+# --- Algorithm 2: the collection step, by hand -------------------------------
+
+def test_collect_hand_example():
+    """A = [1 1], B = [1; -1] (Ker_Z(A) is spanned by (1, -1)), box [0, 2] so
+    that C4 admits |g_i| <= 2.  Worked by hand: z = 0.4 and 0.5 round to 0 (ties
+    to even) and give g = 0 (dropped); z = 1.6, 2.5 and -2.5 round to 2, 2 and
+    -2 and give (2, -2) up to sign; z = -0.7 gives (-1, 1), canonically (1, -1);
+    z = 3.2 gives (3, -3), outside the box.  With B = [1; 0], which is not in
+    the kernel, A g = 1 != 0 and C1 drops everything."""
+    A = np.array([[1, 1]])
+    l, u = np.array([0, 0]), np.array([2, 2])
+    Z = np.array([[0.4], [0.5], [1.6], [2.5], [-2.5], [-0.7], [3.2]])
+    assert O.collect(A, np.array([[1], [-1]]), l, u, Z) == {(2, -2), (1, -1)}
+    assert O.collect(A, np.array([[1], [0]]), l, u, Z) == set()
+    # the bound of C4 is inclusive: span 1 keeps (1, -1) and drops (2, -2)
+    assert O.collect(A, np.array([[1], [-1]]), l, np.array([1, 1]), Z) == {(1, -1)}
+
+
+def test_sort_directions_is_tuple_order():
+    rng = np.random.default_rng(4)
+    G = rng.integers(-3, 4, size=(200, 5))
+    expect = sorted(tuple(int(v) for v in r) for r in G)
+    assert [tuple(int(v) for v in r) for r in O.sort_directions(G)] == expect
+    assert O.sort_directions(np.zeros((0, 5), np.int64)).shape == (0, 5)
+
+
+def test_egcd_bezout_against_math_gcd():
+    import math
+    rng = np.random.default_rng(6)
+    pairs = [(0, 0), (0, 7), (7, 0), (-12, 18), (18, -12), (1, 1)]
+    pairs += [(int(a), int(b)) for a, b in rng.integers(-10 ** 6, 10 ** 6, size=(300, 2))]
+    for a, b in pairs:
+        g, x, y = O._egcd(a, b)
+        assert g == math.gcd(a, b) and x * a + y * b == g
