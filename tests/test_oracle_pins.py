@@ -527,3 +527,45 @@ def test_egcd_bezout_against_math_gcd():
     for a, b in pairs:
         g, x, y = O._egcd(a, b)
         assert g == math.gcd(a, b) and x * a + y * b == g
+
+
+def test_lll_conditions_reject_unreduced_bases():
+    """Appendix A's two conditions, each violated on its own, by hand.
+    Columns (1,0), (7,1): mu_21 = 7 > 1/2, not size-reduced; the
+    Gram-Schmidt norms are 1 and 1, so the exchange condition holds.
+    Columns (3,0), (0,1): mu_21 = 0, but ||b1*||^2 = 9 > 2 ||b2*||^2 = 2.
+    Columns (2,0), (1,2): mu_21 = 1/2 exactly (allowed) and norms 4 <= 2 * 4.
+    Columns (2,0), (1,1): mu_21 = 1/2, but 4 > 2 * 1.  Columns (1,0), (1,1):
+    mu_21 = 1 > 1/2, norms 1 and 1."""
+    def cols(*vs):
+        return np.array(vs, dtype=np.int64).T
+    assert O.lll_conditions(cols((1, 0), (7, 1))) == (False, True)
+    assert O.lll_conditions(cols((3, 0), (0, 1))) == (True, False)
+    assert O.lll_conditions(cols((2, 0), (1, 2))) == (True, True)
+    assert O.lll_conditions(cols((2, 0), (1, 1))) == (True, False)
+    assert O.lll_conditions(cols((1, 0), (1, 1))) == (False, True)
+    assert O.lll_conditions(cols((1, 0), (0, 1))) == (True, True)
+    # a three-column case where only a non-adjacent coefficient (mu_31) is
+    # too large: (1,0,0), (0,1,0), (5,0,1)
+    assert O.lll_conditions(cols((1, 0, 0), (0, 1, 0), (5, 0, 1))) == (False, True)
+    # and one where only the second pair fails the exchange test:
+    # (1,0,0), (0,3,0), (0,0,1): norms 1, 9, 1 and 9 > 2
+    assert O.lll_conditions(cols((1, 0, 0), (0, 3, 0), (0, 0, 1))) == (True, False)
+
+
+def test_in_feasible_region_rejects_each_violation():
+    """x in S needs A x = b and l <= x <= u; each part alone must fail.
+    A = [1 1 0; 0 1 1], b = (2, 3), box [0, 3]: (1, 1, 2) is feasible;
+    (1, 1, 1) is in the box with A x = (2, 2) != b; (-1, 3, 0) has
+    A x = (2, 3) = b but leaves the box below, (4, -2, 5) above and below."""
+    A = np.array([[1, 1, 0], [0, 1, 1]])
+    b = np.array([2, 3])
+    l, u = np.zeros(3, np.int64), np.full(3, 3)
+    assert O.in_feasible_region(A, b, l, u, [1, 1, 2])
+    assert not O.in_feasible_region(A, b, l, u, [1, 1, 1])
+    assert not O.in_feasible_region(A, b, l, u, [-1, 3, 0])
+    assert not O.in_feasible_region(A, b, l, u, [4, -2, 5])
+    assert O.in_feasible_region(A, b, l, u, [2, 0, 3])
+    # one row of A x = b wrong, the other right
+    assert not O.in_feasible_region(A, b, l, u, [0, 2, 2])   # A x = (2, 4)
+    assert not O.in_feasible_region(A, b, l, u, [0, 1, 2])   # A x = (1, 3)
