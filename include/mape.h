@@ -59,9 +59,12 @@ extern "C" {
 #define MAPE_ERR_CANCELLED       -14  /* mape_cancel was called */
 
 /* ---- precision of the extraction contractions ---------------------------- */
-#define MAPE_PREC_FP32 0  /* the plain FP32 baseline: per step, strict-FP32
+#define MAPE_PREC_FP32 0  /* comparator only, not a product path: the plain
+                             FP32 single-instance baseline that the tensor-core
+                             paths are measured against.  Per step, strict-FP32
                              cuBLAS GEMMs for B z, B^T sign(Bz), B round(z)
-                             and unfused elementwise kernels                  */
+                             and unfused elementwise kernels, as a direct
+                             PyTorch version of the method would run them    */
 #define MAPE_PREC_BF16 1  /* tcgen05 BF16 MMAs with FP32 accumulation in TMEM,
                              persistent fused kernel over all T steps; z enters
                              the forward product as hi + lo (two BF16 terms),
@@ -105,8 +108,9 @@ typedef struct {
   int32_t period;              /* collect every `period` steps (Algorithm 2)    */
   int32_t precision;           /* MAPE_PREC_*                                   */
   int32_t reserved;
-  int64_t cand_capacity;       /* candidate-buffer rows of a handle (0: P*(T+1),
-                                  at most 2^23 rows and 2 GiB per buffer)    */
+  int64_t cand_capacity;       /* candidate-buffer rows of a handle (0:
+                                  P * (T / period + 1), at most 2^23 rows and
+                                  2 GiB per buffer)                          */
   int64_t max_aug_iters;       /* cap on Algorithm 1 iterations per call        */
 } mape_config;
 
@@ -250,29 +254,38 @@ int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t ldc,
 
 /* mape_dedup without any device allocation (this entry point has no
  * counterpart in the paper; it is an interface for callers).  Some callers
- * cannot allocate device memory where they dedup: code running while a stream
- * is captured into a CUDA graph (cudaMalloc is not allowed there), hosts that
- * reserve all device memory up front and forbid later allocations, plugins
- * whose host owns the allocator.  This variant takes no workspace: its
- * scratch is a static device array of 10 MiB inside the library, which every
- * GPU that loads the library holds until the process exits.
- *   Limit: count <= mape_dedup_static_max_rows() (2^18 rows); larger counts
- *   return MAPE_ERR_CAPACITY before any device work.
+ * cannot allocate device memory where they dedup: hosts that reserve all
+ * device memory up front and forbid later allocations (a fixed memory budget
+ * for a long-running loop), or plugins whose host owns the device allocator
+ * and gives them none.  This variant takes no workspace: its scratch is a
+ * static device array of 10 MiB inside the library, which every GPU that
+ * loads the library holds until the process exits.
+ *   Limit: count <= mape_dedup_static_max_rows() (2^18 rows, any ldc up to
+ *   the stage's own limits); larger counts return MAPE_ERR_CAPACITY before
+ *   any device work.
+ *   The call is synchronous like mape_dedup: it reads the distinct count back
+ *   to the host and synchronises `stream`.  It therefore cannot be made while
+ *   a stream is being captured into a CUDA graph.
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ *   (cudaGetSymbolAddress) with that device current and caches it; a call
+ *   that fails with a CUDA error forgets the cached address, and so must the
+ *   caller's first call after a cudaDeviceReset (which invalidates it): such
+ *   a call looks it up again.  Devices numbered 64 and above are refused with
+ *   MAPE_ERR_INVALID_ARG.
  *   All calls share the array and it keeps the previous call's contents; the
  *   call clears what must start empty itself.  Calls that overlap on the GPU
  *   (different streams or threads at the same time) race on the array and
  *   must not be issued.
- * Arguments, output and errors otherwise as mape_dedup.  Synchronous. */
+ * Arguments, output and errors otherwise as mape_dedup. */
 int64_t mape_dedup_static_max_rows(void);
 int mape_dedup_static(const int8_t* cand, int64_t count, int32_t n, int32_t ldc,
                       int8_t* uniq, int64_t uniq_cap, int64_t* K_out,
                       void* stream);
 
-/* a9 -- condition C1 (§3): ok[k] = 1 iff A g_k = 0 exactly (int32
- * arithmetic, |A_ij| <= 2^23 and n <= 4096 keep every partial sum exact).
+/* a9 -- condition C1 (§3): ok[k] = 1 iff A g_k = 0 exactly.  The products
+ * are accumulated in int64 in general; when every A_ij fits in int8 (and the
+ * row pitch is at most 256 bytes) they are int8 dot products accumulated in
+ * int32, exact because |sum| <= 127 * 127 * n < 2^31.
  *   A [m x n] int32, G [K x ldg] int8.  *fail_count = rows with A g != 0.
  * Synchronous (returns the count). */
 size_t mape_kernel_test_workspace_bytes(void);
@@ -600,7 +613,8 @@ void mape_server_destroy(mape_server_h s);
 /* Version string of the library build. */
 const char* mape_version(void);
 
-/* Text of the last CUDA runtime error recorded by any call (or ""). */
+/* Text of the last CUDA runtime error recorded by any call, or of the last
+ * argument error that a call explained there (or ""). */
 const char* mape_last_cuda_error(void);
 
 /* Number of CUDA kernels this library has launched in this process (all

@@ -20,6 +20,8 @@
 namespace mape_detail {
 
 void record_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+// Records a plain message (an argument error worth explaining) in the same place.
+void record_message(const char* what);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -55,11 +57,12 @@ struct Sizer {
   size_t bytes() const { return align_up(used, 256) + 256; }
 };
 
-// Default candidate-buffer rows of a handle: one row per start and step,
-// at most 2^23 rows and at most 2 GiB per buffer (a handle holds three); the
-// extraction runs in chunks of steps that fit.
-inline int64_t default_cand_capacity(int64_t P, int64_t T, int64_t ldg) {
-  int64_t cap = P * (T > 0 ? T : 1) + P;
+// Default candidate-buffer rows of a handle: one row per start and
+// collection step (`collections` = T / period), at most 2^23 rows and at most
+// 2 GiB per buffer (a handle holds two); the extraction runs in chunks of
+// steps that fit.
+inline int64_t default_cand_capacity(int64_t P, int64_t collections, int64_t ldg) {
+  int64_t cap = P * (collections > 0 ? collections : 1) + P;
   cap = cap < ((int64_t)1 << 23) ? cap : ((int64_t)1 << 23);
   const int64_t by_bytes = ((int64_t)1 << 31) / (ldg > 0 ? ldg : 16);
   cap = cap < by_bytes ? cap : by_bytes;

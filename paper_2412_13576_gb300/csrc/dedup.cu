@@ -448,14 +448,16 @@ extern "C" int mape_dedup(const int8_t* cand, int64_t count, int32_t n, int32_t 
 // ---- the same stage without any device allocation ----------------------------
 //
 // For callers that cannot allocate device memory at the point where they
-// dedup: code running while a stream is being captured into a CUDA graph
-// (where cudaMalloc is not allowed), hosts that reserve all device memory up
-// front and forbid allocations later (fixed-memory real-time loops), or
-// plugins whose host owns the device allocator.  The scratch lives in a
-// file-scope device array that every GPU loading this library holds until the
-// process exits.  Host code cannot pass that array's name to a kernel (in host
-// code it is only a host-side stand-in), so its device address is looked up
-// once per device, with that device current, by cudaGetSymbolAddress.
+// dedup: hosts that reserve all device memory up front and forbid allocations
+// later (fixed-memory long-running loops), or plugins whose host owns the
+// device allocator.  The call stays synchronous (it reads the distinct count
+// back and synchronises the stream), so it cannot run inside a stream capture.
+// The scratch lives in a file-scope device array that every GPU loading this
+// library holds until the process exits.  Host code cannot pass that array's
+// name to a kernel (in host code it is only a host-side stand-in), so its
+// device address is looked up once per device, with that device current, by
+// cudaGetSymbolAddress, and cached; a CUDA error forgets the cached address
+// (a cudaDeviceReset invalidates it), so the next call looks it up again.
 
 namespace {
 
@@ -475,7 +477,10 @@ int static_dedup_scratch(void** out) {
     mape_detail::record_cuda_error(e, "cudaGetDevice", __FILE__, __LINE__);
     return MAPE_ERR_CUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) return MAPE_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) {
+    mape_detail::record_message("mape_dedup_static: device index beyond the 64 devices it supports");
+    return MAPE_ERR_INVALID_ARG;
+  }
   std::lock_guard<std::mutex> lk(g_scratch_mu);
   if (g_scratch_ptr[dev] == nullptr) {
     void* p = nullptr;
@@ -488,6 +493,15 @@ int static_dedup_scratch(void** out) {
   }
   *out = g_scratch_ptr[dev];
   return MAPE_OK;
+}
+
+// Drops the cached address of the current device (after a CUDA error, which
+// may come from a reset context): the next call looks it up again.
+void forget_static_dedup_scratch() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  g_scratch_ptr[dev] = nullptr;
 }
 
 }  // namespace
@@ -505,5 +519,7 @@ extern "C" int mape_dedup_static(const int8_t* cand, int64_t count, int32_t n, i
   int rc = static_dedup_scratch(&scratch);
   if (rc != MAPE_OK) return rc;
   // the table and the counter are cleared by the stage itself on every call
-  return mape_dedup(cand, count, n, ldc, uniq, uniq_cap, K_out, scratch, kStaticDedupBytes, stream);
+  rc = mape_dedup(cand, count, n, ldc, uniq, uniq_cap, K_out, scratch, kStaticDedupBytes, stream);
+  if (rc == MAPE_ERR_CUDA) forget_static_dedup_scratch();
+  return rc;
 }

@@ -26,6 +26,11 @@ void record_cuda_error(cudaError_t e, const char* what, const char* file, int li
                 file, line, what);
 }
 
+void record_message(const char* what) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  std::snprintf(g_last_err, sizeof(g_last_err), "%s", what);
+}
+
 }  // namespace mape_detail
 
 extern "C" const char* mape_last_cuda_error(void) { return mape_detail::g_last_err; }

@@ -1,12 +1,14 @@
 """mape_dedup_static, the dedup entry point that allocates no device memory,
-for callers that cannot allocate where they dedup (inside a CUDA graph
-capture, under a fixed up-front memory budget, or inside a host that owns
-the allocator).  It keeps its scratch in a static device array of the
+for callers that cannot allocate where they dedup (a host that reserves all
+device memory up front and forbids later allocations, or a plugin whose host
+owns the allocator).  It keeps its scratch in a static device array of the
 library, so this test checks, through the C ABI, that it returns exactly what
 mape_dedup returns with a caller workspace, on two calls in a row (the second
-call must not see the first one's leftovers), and that a count above its
-stated limit is refused before any device work.  This file is collected last
-so that a failure here comes after every other test has run."""
+call must not see the first one's leftovers), at the largest accepted count
+with a wide row pitch (where its scratch comes closest to the array's size),
+and that a count above its stated limit is refused before any device work.
+This file is collected last so that a failure here comes after every other
+test has run."""
 import ctypes
 
 import numpy as np
@@ -66,3 +68,27 @@ def test_static_dedup_refuses_counts_above_its_limit(M):
     K = ctypes.c_int64(-1)
     rc = M.lib().mape_dedup_static(None, limit + 1, 16, 16, None, 0, ctypes.byref(K), None)
     assert rc == -7
+
+
+def test_static_dedup_at_its_row_limit_with_wide_rows(M):
+    """count == mape_dedup_static_max_rows() with ldc = 4096: the hash table,
+    the padded sort keys and the run list all reach their largest sizes, and
+    must still fit the static array; the result equals mape_dedup's."""
+    import torch
+    limit = int(M.lib().mape_dedup_static_max_rows())
+    n, ldc, distinct = 4090, 4096, 3000
+    rng = np.random.default_rng(9)
+    base = np.zeros((distinct, ldc), np.int8)
+    base[:, :n] = rng.integers(-5, 6, size=(distinct, n))
+    # rows that differ only late in the row share their 8-byte sort prefix
+    base[distinct // 2:, :64] = base[0, :64]
+    pick = torch.from_numpy(rng.integers(0, distinct, size=limit)).cuda()
+    cand = dev(base)[pick].contiguous()
+    got = _static(M, cand, limit, n, ldc)
+    expect = M.dedup(cand, limit, n).cpu().numpy()
+    assert got.shape == expect.shape
+    assert np.array_equal(got, expect)
+    # and a second, small call right after it still starts from a clean table
+    buf, ldc2 = _rows(3, 3000, 50, 700)
+    cand2 = dev(buf)
+    assert np.array_equal(_static(M, cand2, 3000, 50, ldc2), M.dedup(cand2, 3000, 50).cpu().numpy())
