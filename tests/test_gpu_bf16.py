@@ -4,15 +4,16 @@ B is exact in BF16 and every partial sum of B round(z) is an integer below
 2^24, so the collected candidates are compared bit-exactly.  The forward
 product carries z as hi + lo (16 significant bits, MAPE_PREC_BF16) or hi
 alone (8 bits, MAPE_PREC_BF16X1); the gradient is compared within 1e-5 on
-the starts whose sign(Bz) that arithmetic determines, and Phi on all starts
-(1e-4 and 2e-2)."""
+each start within 2 |B_ij| per row of B z whose sign that arithmetic cannot
+fix and within 1e-5 elsewhere, Phi per start within the forward error bound
+(the rules are in tests/gpu_common.py)."""
 import numpy as np
 import pytest
 
 from oracle import mape_oracle as O
 from paper_2412_13576_gb300 import instances as I
 
-from .gpu_common import dev, rel_fro, rows_set
+from .gpu_common import check_steps, dev, report, rows_set
 from .test_gpu_stages import _extract_steps
 
 pytestmark = pytest.mark.gpu
@@ -31,19 +32,8 @@ def M():
     return mape
 
 
-def bf16_stable_rows(B, Z, bits):
-    """Starts whose sign(Bz) cannot change when z is rounded to `bits`
-    significant bits (relative error 2^-bits) and summed in FP32."""
-    Bf = np.asarray(B, np.float64)
-    Zf = np.asarray(Z, np.float64)
-    Y = Zf @ Bf.T
-    bound = (2.0 ** -bits + Bf.shape[1] * 2.0 ** -23) * (np.abs(Zf) @ np.abs(Bf).T) * 1.01 + 1e-6
-    return np.all(np.abs(Y) > bound, axis=1)
-
-
-# precision -> (significant bits of z in B z, tolerance on Phi over all starts,
-#               largest share of starts whose sign(Bz) the arithmetic cannot fix)
-PRECISIONS = {1: (16, 1e-4, 0.15), 2: (8, BF16_TOL, 1.0)}
+# precision -> significant bits of z in the forward product B z
+PRECISIONS = {1: 16, 2: 8}
 
 
 def _general_basis(make, seed=5):
@@ -84,39 +74,44 @@ def _starts(inst, P, seed):
     return O.project_to_coordinates(inst.B, I.uniform_samples(inst, P, seed=seed).G0).astype(np.float32)
 
 
+# Largest share of start-steps with an ambiguous row of B z (a row whose sign
+# the arithmetic cannot fix), per case and precision, as observed on GB300
+# (rounded up).  Those start-steps are still checked, against the per-row
+# allowance of 2 |B_ij| (tests/gpu_common.py); the cap only keeps a case from
+# drifting into one where that allowance covers most of the gradient.
+AMBIGUOUS_CAP = {
+    ("small_dense", 1): 0.005, ("small_dense", 2): 0.18,
+    ("medium_sparse", 1): 0.08, ("medium_sparse", 2): 0.95,
+    ("tiny_graver_case", 1): 0.005, ("tiny_graver_case", 2): 0.03,
+    ("small_dense_general_basis", 1): 0.005, ("small_dense_general_basis", 2): 0.2,
+    ("medium_sparse_general_basis", 1): 0.45, ("medium_sparse_general_basis", 2): 1.0,
+    ("tile64_last3", 1): 0.01, ("tile64_last3", 2): 0.6,
+    ("tile80_resident", 1): 0.03, ("tile80_resident", 2): 0.85,
+}
+
+
 @pytest.mark.parametrize("precision", [1, 2])
-@pytest.mark.parametrize("make,P,T,amb", [(I.small_dense, 256, 40, 1.0), (I.medium_sparse, 300, 8, 1.0),
-                                          (I.tiny_graver_case, 130, 40, 1.0),
-                                          (_general_basis(I.small_dense), 256, 30, 1.0),
-                                          (_general_basis(I.medium_sparse), 200, 6, 4.0),
-                                          (tile64_last3, 200, 10, 2.0), (tile80_resident, 200, 8, 2.0)])
-def test_bf16_per_step(M, make, P, T, amb, precision):
-    """The gradient of Eq. (3) jumps by 2 B_i where (Bz)_i changes sign, so it
-    is compared on the starts whose sign(Bz) the arithmetic fixes (every
-    |(Bz)_i| above the error bound of z carried to `bits` bits and summed in
-    FP32): there within 1e-5 for both precisions.  The share of other starts is
-    bounded (2% for hi + lo), Phi (continuous) is compared on all starts, and
-    the collected candidates are bit-exact."""
+@pytest.mark.parametrize("make,P,T", [(I.small_dense, 256, 40), (I.medium_sparse, 300, 8),
+                                      (I.tiny_graver_case, 130, 40),
+                                      (_general_basis(I.small_dense), 256, 30),
+                                      (_general_basis(I.medium_sparse), 200, 6),
+                                      (tile64_last3, 200, 10), (tile80_resident, 200, 8)])
+def test_bf16_per_step(M, make, P, T, precision):
+    """Per start and step: the gradient of Eq. (3) within 1e-5 (relative to the
+    start's gradient) on the coordinates that no ambiguous row of B z touches,
+    and within 2 |B_ij| per ambiguous row elsewhere (the jump of sign(Bz)_i);
+    Phi within the forward error bound of z carried to `bits` bits; the Adam
+    update within 1e-5 per start; the collected candidates bit-exact.  The
+    share of start-steps with an ambiguous row is reported and capped."""
     inst = make()
     Z0 = _starts(inst, P, 2001)
     ldc = M.round16(inst.n)
-    bits, tol_phi, max_ambiguous = PRECISIONS[precision]
+    bits = PRECISIONS[precision]
     states, grads, phis, cand = _extract_steps(M, inst, Z0, T, precision, ldc)
-    expect = set()
-    ambiguous = 0
-    for t, ((z, m, v), (z1, m1, v1)) in enumerate(states):
-        go = O.phi_grad(inst.B, z, 0.85, 1.0)
-        ok = bf16_stable_rows(inst.B, z, bits)
-        ambiguous += int((~ok).sum())
-        if ok.any():
-            assert rel_fro(grads[t][ok], go[ok]) < FP32_TOL
-        assert rel_fro(phis[t], O.phi(inst.B, z, 0.85, 1.0)) < tol_phi
-        zo, mo, vo = O.adam_update(z.astype(np.float64), m, v, grads[t].astype(np.float64), t + 1, 0.003)
-        assert rel_fro(z1, zo) < FP32_TOL
-        assert rel_fro(m1, mo) < FP32_TOL
-        assert rel_fro(v1, vo) < FP32_TOL
-        expect |= O.collect(inst.A, inst.B, inst.l, inst.u, z1)
-    assert ambiguous <= min(1.0, amb * max_ambiguous) * P * T
+    expect, share, rows, worst = check_steps(inst, states, grads, phis, bits, FP32_TOL)
+    report(f"bf16_per_step/{make.__name__}/{precision}", ambiguous_share=share, ambiguous_rows=rows,
+           max_rel_grad_determined=worst)
+    assert share <= AMBIGUOUS_CAP[(make.__name__, precision)]
     assert rows_set(cand, inst.n) == expect
 
 

@@ -1,7 +1,8 @@
 """The sparse path of Algorithm 2 (identity-topped B with sparse B', one
 block per start with its state in shared memory for all T steps) against
-the FP64 oracle: per step the gradient within 1e-5 on the starts whose
-sign(Bz) FP32 determines, Phi and the Adam update within 1e-5, the
+the FP64 oracle: per step and start the gradient, Phi and the Adam update
+within 1e-5 (with the allowance for rows of B z whose sign FP32 does not fix,
+tests/gpu_common.py), the
 collected rows exactly the oracle's collection of the GPU's own iterates; T
 steps in one launch bitwise equal to T launches of one step."""
 import numpy as np
@@ -10,7 +11,7 @@ import pytest
 from oracle import mape_oracle as O
 from paper_2412_13576_gb300 import instances as I
 
-from .gpu_common import dev, rel_fro, rows_set, sign_stable_rows
+from .gpu_common import check_steps, dev, report, rows_set
 from .test_gpu_bf16 import _general_basis
 from .test_gpu_stages import _extract_steps
 
@@ -44,16 +45,13 @@ def test_sparse_per_step(M, make, P, T, std):
     inst = make()
     Z0 = _z0(inst, P, 2005, std)
     states, grads, phis, cand = _extract_steps(M, inst, Z0, T, SPARSE, M.round16(inst.n), cap=P * (T + 1) + 16)
-    expect = set()
-    for t, ((z, m, v), (z1, m1, v1)) in enumerate(states):
-        go = O.phi_grad(inst.B, z, 0.85, 1.0)
-        ok = sign_stable_rows(inst.B, z)
-        assert ok.mean() > 0.5
-        assert rel_fro(grads[t][ok], go[ok]) < TOL
-        assert rel_fro(phis[t][ok], O.phi(inst.B, z, 0.85, 1.0)[ok]) < TOL
-        zo, mo, vo = O.adam_update(z.astype(np.float64), m, v, grads[t].astype(np.float64), t + 1, 0.003)
-        assert rel_fro(z1, zo) < TOL and rel_fro(m1, mo) < TOL and rel_fro(v1, vo) < TOL
-        expect |= O.collect(inst.A, inst.B, inst.l, inst.u, z1)
+    expect, share, rows, worst = check_steps(inst, states, grads, phis, 24, TOL)
+    report(f"sparse_per_step/{inst.name}/{std}", ambiguous_share=share, ambiguous_rows=rows,
+           max_rel_grad_determined=worst)
+    # observed on GB300, rounded up
+    cap = {"small_dense_n20_m5": 0.005, "medium_sparse_n200_m40": 0.05, "tiny_n6_m2": 0.005, "uneven_n500": 0.06,
+           "large_quartic_n2000_m400": 0.35}[inst.name]
+    assert share <= cap
     assert rows_set(cand, inst.n) == expect
 
 

@@ -2,17 +2,16 @@
 z, m, v streamed through shared memory) against the FP64 oracle, on the shapes
 only it takes (d or the MMA rows above 256: the uneven family up to n = 1000,
 the large n = 2000 instance) and, forced with MAPE_PREC_STREAMED, on the
-shapes the resident kernel also takes.  Same bar as the resident path: the
-gradient within 1e-5 on the starts whose sign(Bz) the arithmetic fixes, Phi
-on all starts, Adam within 1e-5, candidates bit-exact."""
+shapes the resident kernel also takes.  Same bar as the resident path, per
+start and step (tests/gpu_common.py), candidates bit-exact."""
 import numpy as np
 import pytest
 
 from oracle import mape_oracle as O
 from paper_2412_13576_gb300 import instances as I
 
-from .gpu_common import dev, rel_fro, rows_set
-from .test_gpu_bf16 import FP32_TOL, PRECISIONS, _general_basis, _starts, bf16_stable_rows
+from .gpu_common import check_steps, dev, report, rows_set
+from .test_gpu_bf16 import FP32_TOL, PRECISIONS, _general_basis, _starts
 from .test_gpu_stages import _extract_steps
 
 pytestmark = pytest.mark.gpu
@@ -46,51 +45,60 @@ def _z0(inst, P, seed, std):
     return I.normal_starts(inst, P, std=std, seed=seed).Z0
 
 
-# (instance, P, T, ambiguity factor, force the streamed path, start scale)
+# (instance, P, T, force the streamed path, start scale)
 CASES = [
-    (I.small_dense, 256, 20, 1.0, True, None),
-    (I.medium_sparse, 300, 5, 1.0, True, None),          # 3 tiles, the last one ragged
-    (I.tiny_graver_case, 130, 30, 1.0, True, None),
-    (_general_basis(I.small_dense), 256, 20, 1.0, True, None),
-    (uneven500, 200, 4, 4.0, False, None),               # d = 400: streamed by necessity
-    (uneven500, 200, 6, 4.0, False, 0.3),
-    (uneven1000, 130, 2, 6.0, False, None),              # d = 800, 160 rows of B'
-    (uneven1000, 130, 3, 6.0, False, 0.3),
-    (I.large_quartic, 256, 2, 6.0, False, None),         # n = 2000, d = 1600: 2 row blocks, 7 coordinate blocks
-    (I.large_quartic, 256, 3, 6.0, False, 0.3),
-    (_general_basis(uneven500), 130, 4, 6.0, False, 0.3),  # general B: all 500 rows through the MMA
+    (I.small_dense, 256, 20, True, None),
+    (I.medium_sparse, 300, 5, True, None),          # 3 tiles, the last one ragged
+    (I.tiny_graver_case, 130, 30, True, None),
+    (_general_basis(I.small_dense), 256, 20, True, None),
+    (uneven500, 200, 4, False, None),               # d = 400: streamed by necessity
+    (uneven500, 200, 6, False, 0.3),
+    (uneven1000, 130, 2, False, None),              # d = 800, 160 rows of B'
+    (uneven1000, 130, 3, False, 0.3),
+    (I.large_quartic, 256, 2, False, None),         # n = 2000, d = 1600: 2 row blocks, 7 coordinate blocks
+    (I.large_quartic, 256, 3, False, 0.3),
+    (_general_basis(uneven500), 130, 4, False, 0.3),  # general B: all 500 rows through the MMA
 ]
+
+# Largest share of start-steps with an ambiguous row of B z, per case (name,
+# start scale) and precision, as observed on GB300 (rounded up); those
+# start-steps are still checked against the per-row allowance.  Projected
+# uniform starts (scale None) on n >= 500 reach |z| ~ 10-20, where sum_j
+# |B_ij z_j| is large against |(Bz)_i|; with z as one BF16 term (8 bits) every
+# start then has ambiguous rows (a few of hundreds per start).
+AMBIGUOUS_CAP = {
+    ("small_dense", None, 1): 0.005, ("small_dense", None, 2): 0.12,
+    ("medium_sparse", None, 1): 0.05, ("medium_sparse", None, 2): 0.9,
+    ("tiny_graver_case", None, 1): 0.005, ("tiny_graver_case", None, 2): 0.02,
+    ("small_dense_general_basis", None, 1): 0.005, ("small_dense_general_basis", None, 2): 0.12,
+    ("uneven500", None, 1): 0.4, ("uneven500", None, 2): 1.0,
+    ("uneven500", 0.3, 1): 0.07, ("uneven500", 0.3, 2): 0.95,
+    ("uneven1000", None, 1): 0.75, ("uneven1000", None, 2): 1.0,
+    ("uneven1000", 0.3, 1): 0.16, ("uneven1000", 0.3, 2): 1.0,
+    ("large_quartic", None, 1): 0.9, ("large_quartic", None, 2): 1.0,
+    ("large_quartic", 0.3, 1): 0.35, ("large_quartic", 0.3, 2): 1.0,
+    ("uneven500_general_basis", 0.3, 1): 0.16, ("uneven500_general_basis", 0.3, 2): 1.0,
+}
 
 
 @pytest.mark.parametrize("precision", [1, 2])
-@pytest.mark.parametrize("make,P,T,amb,force,std", CASES)
-def test_streamed_per_step(M, make, P, T, amb, force, std, precision):
+@pytest.mark.parametrize("make,P,T,force,std", CASES)
+def test_streamed_per_step(M, make, P, T, force, std, precision):
+    """Per start and step, the rules of tests/gpu_common.py: gradient within
+    1e-5 off the ambiguous rows' reach and within 2 |B_ij| per ambiguous row,
+    Phi within the forward error bound, Adam within 1e-5; candidates
+    bit-exact."""
     inst = make()
     Z0 = _z0(inst, P, 2003, std)
     ldc = M.round16(inst.n)
-    bits, _, max_ambiguous = PRECISIONS[precision]
+    bits = PRECISIONS[precision]
     prec = precision | (STREAMED if force else 0)
     states, grads, phis, cand = _extract_steps(M, inst, Z0, T, prec, ldc, cap=P * (T + 1) + 16)
-    expect = set()
-    ambiguous = 0
-    for t, ((z, m, v), (z1, m1, v1)) in enumerate(states):
-        go = O.phi_grad(inst.B, z, 0.85, 1.0)
-        ok = bf16_stable_rows(inst.B, z, bits)
-        ambiguous += int((~ok).sum())
-        if ok.any():
-            assert rel_fro(grads[t][ok], go[ok]) < FP32_TOL
-        # Phi: within the spec BF16 tolerance overall, and per start within
-        # the error bound of z carried to `bits` bits and summed in FP32
-        po = O.phi(inst.B, z, 0.85, 1.0)
-        assert rel_fro(phis[t], po) < 2e-2
-        bound = (2.0 ** -bits + inst.d * 2.0 ** -23) * (np.abs(z) @ np.abs(inst.B.astype(np.float64)).T).sum(1)
-        assert np.all(np.abs(phis[t] - po) <= 1.01 * bound + 1e-5 * np.abs(po) + 1e-4)
-        zo, mo, vo = O.adam_update(z.astype(np.float64), m, v, grads[t].astype(np.float64), t + 1, 0.003)
-        assert rel_fro(z1, zo) < FP32_TOL
-        assert rel_fro(m1, mo) < FP32_TOL
-        assert rel_fro(v1, vo) < FP32_TOL
-        expect |= O.collect(inst.A, inst.B, inst.l, inst.u, z1)
-    assert ambiguous <= min(1.0, amb * max_ambiguous) * P * T
+    expect, share, rows, worst = check_steps(inst, states, grads, phis, bits, FP32_TOL)
+    key = (make.__name__, std, precision)
+    report(f"streamed_per_step/{make.__name__}/{std}/{precision}", ambiguous_share=share, ambiguous_rows=rows,
+           max_rel_grad_determined=worst)
+    assert share <= AMBIGUOUS_CAP[key]
     assert rows_set(cand, inst.n) == expect
 
 
