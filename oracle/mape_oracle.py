@@ -144,23 +144,26 @@ def conformal_leq(x, y):
     return bool(np.all(x * y >= 0) and np.all(np.abs(x) <= np.abs(y)))
 
 
-def minimal_elements(G):
+def minimal_elements(G, rows=None):
     """Rows g of G (a set stored once up to sign) with no other row h such that
     h ⊑ g or -h ⊑ g: the ⊑-minimal elements of the symmetric set (C3).
 
-    Returns a boolean mask.  Plain O(K^2 n) comparison of every pair.
+    Returns a boolean mask over G, or over the selected `rows` (indices into
+    G, each still compared with every row of G) when given.  Plain O(K^2 n)
+    comparison of every pair.
     """
     G = np.asarray(G, np.int64)
     K = G.shape[0]
-    keep = np.ones(K, dtype=bool)
+    sel = range(K) if rows is None else rows
+    keep = np.ones(len(sel), dtype=bool)
     absG = np.abs(G)
-    for i in range(K):
+    for q, i in enumerate(sel):
         g = G[i]
         dominated_pos = np.all((G * g >= 0) & (absG <= absG[i]), axis=1)
         dominated_neg = np.all((-G * g >= 0) & (absG <= absG[i]), axis=1)
         hit = dominated_pos | dominated_neg
         hit[i] = False
-        keep[i] = not hit.any()
+        keep[q] = not hit.any()
     return keep
 
 

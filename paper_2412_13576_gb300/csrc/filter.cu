@@ -78,6 +78,73 @@ __global__ void kernel_test_kernel(const int32_t* __restrict__ A, int m, int n, 
   }
 }
 
+// A in compressed rows (CSR), for the test of rows too long for the dp4a path:
+// row r's nonzeros are col[rowptr[r] .. rowptr[r+1]), val[...] in column order.
+// One warp per row of A.
+__global__ void csr_count_kernel(const int32_t* __restrict__ A, int m, int n, uint32_t* __restrict__ rowcnt) {
+  const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= m) return;
+  uint32_t c = 0;
+  for (int i = lane; i < n; i += 32) c += A[(int64_t)r * n + i] != 0;
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+  if (lane == 0) rowcnt[r] = c;
+}
+
+__global__ void csr_fill_kernel(const int32_t* __restrict__ A, int m, int n, const uint32_t* __restrict__ rowptr,
+                                uint16_t* __restrict__ col, int32_t* __restrict__ val) {
+  const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= m) return;
+  uint32_t pos = rowptr[r];
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    const int i = i0 + lane;
+    const int v = i < n ? A[(int64_t)r * n + i] : 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, v != 0);
+    if (v != 0) {
+      const uint32_t q = pos + __popc(bal & ((1u << lane) - 1));
+      col[q] = (uint16_t)i;
+      val[q] = v;
+    }
+    pos += __popc(bal);
+  }
+}
+
+// A g over a row staged in shared memory, one warp per candidate row: lane j
+// takes the rows j, j + 32, ... of A through their nonzeros (int64 sums, exact
+// for every int32 A and int8 g).  Each candidate row is read once, with
+// 16-byte loads.
+constexpr int kCsrWarps = 8;
+constexpr int kCsrMaxRow = 4096;
+
+__global__ void __launch_bounds__(32 * kCsrWarps)
+kernel_test_csr_kernel(const uint32_t* __restrict__ rowptr, const uint16_t* __restrict__ col,
+                       const int32_t* __restrict__ val, int m, const int8_t* __restrict__ G, int64_t K,
+                       int ldg, uint8_t* __restrict__ ok, unsigned long long* __restrict__ fails) {
+  __shared__ __align__(16) int8_t s_row[kCsrWarps][kCsrMaxRow];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int8_t* row = s_row[w];
+  const int nv = ldg / 16;
+  for (int64_t k = blockIdx.x * (int64_t)kCsrWarps + w; k < K; k += (int64_t)gridDim.x * kCsrWarps) {
+    const uint4* src = reinterpret_cast<const uint4*>(G + k * ldg);
+    for (int c = lane; c < nv; c += 32) reinterpret_cast<uint4*>(row)[c] = src[c];
+    __syncwarp();
+    bool good = true;
+    for (int r = lane; r < m; r += 32) {
+      long long acc = 0;
+      const uint32_t e1 = rowptr[r + 1];
+      for (uint32_t e = rowptr[r]; e < e1; ++e) acc += (long long)val[e] * row[col[e]];
+      good &= (acc == 0);
+    }
+    good = __all_sync(0xffffffffu, good);
+    if (lane == 0) {
+      ok[k] = good ? 1 : 0;
+      if (!good) atomicAdd(fails, 1ull);
+    }
+    __syncwarp();
+  }
+}
+
 // ---- a11 ----------------------------------------------------------------------
 
 // l1 norm and sign masks per row; rows with valid == 0 get l1 = kInvalidL1
@@ -463,9 +530,14 @@ int64_t l1_bins(int32_t n) { return (int64_t)127 * n + 1; }
 
 }  // namespace
 
-extern "C" size_t mape_kernel_test_workspace_bytes(void) {
+extern "C" size_t mape_kernel_test_workspace_bytes(int32_t m, int32_t n) {
+  if (m <= 0 || n <= 0) return 0;
   mape_detail::Sizer s;
-  s.take<unsigned long long>(1);
+  s.take<unsigned long long>(1);             // failure counter
+  s.take<uint32_t>((size_t)m + 1);           // nonzeros per row of A
+  s.take<uint32_t>((size_t)m + 1);           // row starts
+  s.take<uint16_t>((size_t)m * n);           // column indices
+  s.take<int32_t>((size_t)m * n);            // values
   return s.bytes();
 }
 
@@ -473,20 +545,35 @@ extern "C" int mape_kernel_test(const int32_t* A, int32_t m, int32_t n, const in
                                 uint8_t* ok, int64_t* fail_count, void* workspace, size_t workspace_bytes,
                                 void* stream) {
   using namespace mape_detail;
-  if (!A || m <= 0 || n <= 0 || ldg < n || K < 0 || !fail_count || (K > 0 && (!G || !ok)))
+  if (!A || m <= 0 || n <= 0 || ldg < n || ldg % 16 != 0 || K < 0 || !fail_count || (K > 0 && (!G || !ok)))
     return MAPE_ERR_INVALID_ARG;
-  if (n > 4096) return MAPE_ERR_SHAPE;
+  if (n > 4096 || ldg > kCsrMaxRow) return MAPE_ERR_SHAPE;
   *fail_count = 0;
   if (K == 0) return MAPE_OK;
   Carver cv(workspace, workspace_bytes);
   unsigned long long* d_fail = cv.take<unsigned long long>(1);
+  uint32_t* rowcnt = cv.take<uint32_t>((size_t)m + 1);
+  uint32_t* rowptr = cv.take<uint32_t>((size_t)m + 1);
+  uint16_t* col = cv.take<uint16_t>((size_t)m * n);
+  int32_t* val = cv.take<int32_t>((size_t)m * n);
   if (!cv.ok) return MAPE_ERR_CAPACITY;
   cudaStream_t st = as_stream(stream);
   const int stage8 = ((int64_t)m * ldg <= 48 * 1024 && ldg <= kMaxRegRow) ? 1 : 0;
   MAPE_CUDA_TRY(cudaMemsetAsync(d_fail, 0, sizeof(unsigned long long), st));
-  const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(K, 128), 152 * 4);
-  mape_detail::launch(kernel_test_kernel, grid, 128, stage8 ? (size_t)m * ldg : 0, st, A, m, n, G, K, ldg, stage8, ok,
-                      d_fail);
+  if (stage8) {
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(K, 128), 152 * 4);
+    mape_detail::launch(kernel_test_kernel, grid, 128, (size_t)m * ldg, st, A, m, n, G, K, ldg, stage8, ok, d_fail);
+  } else {
+    const unsigned gw = (unsigned)ceil_div((int64_t)m * 32, 256);
+    MAPE_CUDA_TRY(cudaMemsetAsync(rowcnt, 0, sizeof(uint32_t) * ((size_t)m + 1), st));
+    mape_detail::launch(csr_count_kernel, gw, 256, 0, st, A, m, n, rowcnt);
+    // exclusive prefix over m + 1 entries: entry m = nnz(A)
+    mape_detail::launch(bin_scan_kernel, 1, 1024, 0, st, rowcnt, m + 1, rowptr, rowptr);
+    mape_detail::launch(csr_fill_kernel, gw, 256, 0, st, A, m, n, rowptr, col, val);
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(K, kCsrWarps), 152 * 8);
+    mape_detail::launch(kernel_test_csr_kernel, grid, 32 * kCsrWarps, 0, st, rowptr, col, val, m, G, K, ldg, ok,
+                        d_fail);
+  }
   MAPE_LAUNCH_CHECK();
   unsigned long long f = 0;
   MAPE_CUDA_TRY(cudaMemcpyAsync(&f, d_fail, sizeof(f), cudaMemcpyDeviceToHost, st));

@@ -6,8 +6,9 @@
 //
 // Extraction memory is bounded: candidates go to a buffer of `cap` rows laid
 // out as [distinct rows so far | rows of the current chunk]; each chunk runs
-// at most (cap - distinct) / P Adam steps, which is at most one row per start
-// and step, so the buffer cannot overflow; after each chunk mape_dedup merges
+// at most (cap - distinct) / P collection steps (steps whose number is a
+// multiple of the period), which append at most one row per start each, so the
+// buffer cannot overflow; after each chunk mape_dedup merges
 // the buffer into the other buffer of the pair and the two swap.
 #include "common.cuh"
 
@@ -210,8 +211,13 @@ int mape_instance::run_extract() {
   int8_t* other = dBuf1;
   while (t_done < cfg.T) {
     if (cancel.load()) return MAPE_ERR_CANCELLED;
-    int64_t room = cap - U;
-    int64_t steps = room / P;
+    // a chunk may hold as many collections (steps whose number is a multiple
+    // of the period) as there is room for one row per start each: it ends
+    // just before the first collection that would not fit
+    const int64_t room = cap - U;
+    const int64_t fits = room / P;
+    const int64_t period = cfg.period;
+    const int64_t steps = (t_done / period + fits + 1) * period - 1 - t_done;
     if (steps < 1) return MAPE_ERR_CAPACITY;
     int chunk = (int)std::min<int64_t>(steps, cfg.T - t_done);
     MAPE_CUDA_TRY(cudaMemsetAsync(dCount, 0, sizeof(unsigned long long), s));
@@ -446,7 +452,8 @@ extern "C" int mape_extract_directions(mape_handle h, int32_t P, const float* Z0
   h->dirs = nullptr;
   const int n = h->n, d = h->d, ldg = h->ldg;
   const int64_t T = h->cfg.T;
-  int64_t cap = h->cfg.cand_capacity > 0 ? h->cfg.cand_capacity : default_cand_capacity(P, T, ldg);
+  int64_t cap = h->cfg.cand_capacity > 0 ? h->cfg.cand_capacity
+                                         : default_cand_capacity(P, T / h->cfg.period, ldg);
   cap = std::max<int64_t>(cap, (int64_t)P + 1);
   h->cap = cap;
   h->P = P;
@@ -465,7 +472,7 @@ extern "C" int mape_extract_directions(mape_handle h, int32_t P, const float* Z0
   size_t w = 0;
   w = std::max(w, mape_extract_workspace_bytes(n, d, P, h->cfg.precision));
   w = std::max(w, mape_dedup_workspace_bytes(cap, ldg));
-  w = std::max(w, mape_kernel_test_workspace_bytes());
+  w = std::max(w, mape_kernel_test_workspace_bytes(h->m, n));
   w = std::max(w, mape_minimal_workspace_bytes(cap, n));
   h->work_bytes = w;
   h->dWork = h->take<char>(h->job_bufs, w);

@@ -83,7 +83,9 @@ extern "C" size_t mape_request_bytes(int32_t n, int32_t m, int32_t P, int32_t S,
   using mape_detail::align_up;
   const size_t d = (size_t)(n - m), N = (size_t)n, ldg = align_up(N, 16);
   const int64_t T = cfg->T > 0 ? cfg->T : 1;
-  int64_t cap = cfg->cand_capacity > 0 ? cfg->cand_capacity : mape_detail::default_cand_capacity(P, T, (int64_t)ldg);
+  const int64_t period = cfg->period > 0 ? cfg->period : 1;
+  int64_t cap = cfg->cand_capacity > 0 ? cfg->cand_capacity
+                                       : mape_detail::default_cand_capacity(P, T / period, (int64_t)ldg);
   cap = std::max<int64_t>(cap, (int64_t)P + 1);
   size_t inst = (size_t)m * N * 4 + N * d * 4 + (size_t)m * 8 + 3 * N * 4 + 4;  // A, B, b, l, u, span
   inst += N * N * 12 / 8 + 2 * N * 4;                                            // Q as COO (bound), c, w
@@ -92,7 +94,7 @@ extern "C" size_t mape_request_bytes(int32_t n, int32_t m, int32_t P, int32_t S,
   job += 2 * (size_t)cap * ldg + 2 * (size_t)cap + 2 * (size_t)cap * 8 + 16;     // candidate buffers, flags, a, q4
   size_t w = mape_extract_workspace_bytes(n, (int32_t)d, P, cfg->precision);
   w = std::max(w, mape_dedup_workspace_bytes(cap, (int32_t)ldg));
-  w = std::max(w, mape_kernel_test_workspace_bytes());
+  w = std::max(w, mape_kernel_test_workspace_bytes(m, n));
   w = std::max(w, mape_minimal_workspace_bytes(cap, n));
   job += w;
   size_t aug = (size_t)S * N * 4 + (size_t)S * 8 + 4;

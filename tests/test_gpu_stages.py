@@ -1,14 +1,14 @@
 """Parity of every stage of the CUDA path against the CPU oracle, called
 through the C ABI (device buffers).  Integer stages are compared bit-exactly;
-the FP32 continuous stages within relative 1e-5 (Frobenius) on starts whose
-sign pattern sign(Bz) is unambiguous in FP32."""
+the FP32 continuous stages per start within relative 1e-5, with the allowance
+for rows of B z whose sign FP32 does not fix (tests/gpu_common.py)."""
 import numpy as np
 import pytest
 
 from oracle import mape_oracle as O
 from paper_2412_13576_gb300 import instances as I
 
-from .gpu_common import dev, rel_fro, rows_set, sign_stable_rows
+from .gpu_common import check_phi_grad, check_steps, dev, per_start_rel, report, rows_set
 
 pytestmark = pytest.mark.gpu
 
@@ -38,16 +38,20 @@ def test_project_starts(M, name, P):
     G0 = I.uniform_samples(inst, P, seed=7).G0
     Z = M.project_starts(dev(inst.B), dev(G0)).cpu().numpy()
     Zo = O.project_to_coordinates(inst.B, G0)
-    # FP32 Cholesky solve: relative error below d * cond(B^T B) * 2^-24 * 8
+    # FP32 Cholesky solve: relative error per start below d * cond(B^T B) * 2^-24 * 8
     H = inst.B.astype(np.float64).T @ inst.B
     bound = 8 * inst.d * np.linalg.cond(H) * 2.0 ** -24
-    assert rel_fro(Z, Zo) < bound, (rel_fro(Z, Zo), bound)
+    err = per_start_rel(Z, Zo)
+    assert err.max() < bound, (err.max(), bound)
 
 
 # --- a3-a5 -----------------------------------------------------------------------
 
 @pytest.mark.parametrize("name,P,scale", [("small", 512, 3.0), ("small", 512, 0.45), ("medium", 700, 4.0)])
 def test_phi_grad_fp32(M, name, P, scale):
+    """Eq. (3) and its gradient in FP32, per start (tests/gpu_common.py):
+    within 1e-5 where FP32 fixes every sign(Bz)_i, within 2 |B_ij| per row it
+    does not fix; z = 0 gives +inf and a zero gradient."""
     inst = _inst(name)
     rng = np.random.default_rng(11)
     Z = rng.uniform(-scale, scale, size=(P, inst.d)).astype(np.float32)
@@ -55,14 +59,10 @@ def test_phi_grad_fp32(M, name, P, scale):
     Z[1] = np.rint(Z[1]) + (Z[1] == 0)          # an integer point
     phi, grad = M.phi_grad(dev(inst.B), dev(Z))
     phi, grad = phi.cpu().numpy(), grad.cpu().numpy()
-    po = O.phi(inst.B, Z, 0.85, 1.0)
-    go = O.phi_grad(inst.B, Z, 0.85, 1.0)
     assert np.isinf(phi[0]) and np.all(grad[0] == 0)
-    ok = sign_stable_rows(inst.B, Z)
-    ok[0] = False
-    assert ok.sum() > 0.5 * (P - 2)
-    assert rel_fro(phi[ok], po[ok]) < FP32_TOL
-    assert rel_fro(grad[ok], go[ok]) < FP32_TOL
+    st = check_phi_grad(inst.B, Z, phi, grad, 24, FP32_TOL)
+    report(f"phi_grad_fp32/{name}/{scale}", **st)
+    assert st["ambiguous_share"] <= 0.02
 
 
 # --- a3-a8 (FP32 path), step by step against the oracle ------------------------
@@ -97,9 +97,10 @@ def _extract_steps(M, inst, Z0, T, precision, ldc, cap=1 << 16):
 
 @pytest.mark.parametrize("name,P,T", [("small", 256, 30), ("medium", 256, 6)])
 def test_extract_fp32_per_step(M, name, P, T):
-    """Each GPU step from the GPU's own state matches one oracle step (grad,
-    Adam update) within 1e-5, and the candidate rows collected over the run are
-    exactly the oracle's collection applied to the GPU's iterates."""
+    """Each GPU step from the GPU's own state matches one oracle step per start
+    (Phi, gradient, Adam update; tests/gpu_common.py) within 1e-5, and the
+    candidate rows collected over the run are exactly the oracle's collection
+    applied to the GPU's iterates."""
     inst = _inst(name)
     if name == "small":
         Z0 = I.normal_starts(inst, P, seed=2001).Z0
@@ -107,20 +108,10 @@ def test_extract_fp32_per_step(M, name, P, T):
         Z0 = O.project_to_coordinates(inst.B, I.uniform_samples(inst, P, seed=2002).G0).astype(np.float32)
     ldc = M.round16(inst.n)
     states, grads, phis, cand = _extract_steps(M, inst, Z0, T, M.PREC_FP32, ldc)
-    expect = set()
-    for t, ((z, m, v), (z1, m1, v1)) in enumerate(states):
-        go = O.phi_grad(inst.B, z, 0.85, 1.0)
-        ok = sign_stable_rows(inst.B, z)
-        assert ok.mean() > 0.5
-        assert rel_fro(grads[t][ok], go[ok]) < FP32_TOL
-        assert rel_fro(phis[t][ok], O.phi(inst.B, z, 0.85, 1.0)[ok]) < FP32_TOL
-        zo, mo, vo = O.adam_update(z.astype(np.float64), m, v, grads[t].astype(np.float64), t + 1, 0.003)
-        assert rel_fro(z1, zo) < FP32_TOL
-        assert rel_fro(m1, mo) < FP32_TOL
-        assert rel_fro(v1, vo) < FP32_TOL
-        expect |= O.collect(inst.A, inst.B, inst.l, inst.u, z1)
-    got = rows_set(cand, inst.n)
-    assert got == expect
+    expect, share, rows, worst = check_steps(inst, states, grads, phis, 24, FP32_TOL)
+    report(f"extract_fp32_per_step/{name}", ambiguous_share=share, ambiguous_rows=rows, max_rel_grad_determined=worst)
+    assert share <= {"small": 0.005, "medium": 0.03}[name]      # observed on GB300, rounded up
+    assert rows_set(cand, inst.n) == expect
 
 
 # --- a10 -----------------------------------------------------------------------
@@ -159,20 +150,62 @@ def test_dedup_shared_prefixes(M, count, n, groups):
 
 # --- a9 ------------------------------------------------------------------------
 
-def test_kernel_test_exact(M):
-    inst = I.medium_sparse()
+def _kernel_test_case(name):
+    """(A, B) pairs for C1: the medium instance (int8 A, 208-byte rows: the
+    dp4a path), the large one (n = 2000: compressed rows of A), a dense A with
+    entries beyond int8 on short rows, and a dense int8 A on 304-byte rows
+    (both compressed, the latter with every entry nonzero)."""
+    if name == "medium":
+        inst = I.medium_sparse()
+        return inst.A, inst.B
+    if name == "large":
+        inst = I.large_quartic()
+        return inst.A, inst.B
+    rng = np.random.default_rng(21)
+    if name == "wide_entries":
+        m, n, k = 6, 40, 1 << 20
+    else:
+        m, n, k = 30, 300, 3
+    C = rng.integers(-k, k + 1, size=(m, n - m))
+    C[C == 0] = 1
+    if name == "wide_entries":
+        # equal column pairs: e_2k - e_2k+1 (and sums of them) are short
+        # kernel elements although the entries of A are far beyond int8
+        C[:, 1::2] = C[:, 0::2]
+    A = np.concatenate([C, np.eye(m, dtype=np.int64)], axis=1)
+    B = np.concatenate([np.eye(n - m, dtype=np.int64), -C], axis=0)
+    return A.astype(np.int32), B
+
+
+@pytest.mark.parametrize("name,K", [("medium", 3000), ("large", 5000), ("wide_entries", 3000), ("dense300", 3000)])
+def test_kernel_test_exact(M, name, K):
+    A, B = _kernel_test_case(name)
+    m, n = A.shape
     rng = np.random.default_rng(3)
-    W = rng.integers(-2, 3, size=(3000, inst.d))
-    G = W @ inst.B.T.astype(np.int64)
-    G = np.clip(G, -127, 127)
+    # kernel elements B w with small w, rows outside the kernel planted among them
+    W = np.zeros((K, B.shape[1]), np.int64)
+    for r in range(K):
+        if name == "wide_entries":
+            for p in rng.choice(B.shape[1] // 2, size=2, replace=False):
+                s = rng.choice([-1, 1])
+                W[r, 2 * p], W[r, 2 * p + 1] = s, -s
+        else:
+            idx = rng.choice(B.shape[1], size=2, replace=False)
+            W[r, idx] = rng.integers(-1, 2, size=2)
+    G = W @ B.T.astype(np.int64)
+    keep = np.all(np.abs(G) <= 127, axis=1)
+    G = G[keep]
     G[::5, 7] += 1                      # planted rows outside the kernel
-    ldg = M.round16(inst.n)
+    G[1::7, n - 1] -= 1
+    ldg = M.round16(n)
     buf = np.zeros((G.shape[0], ldg), np.int8)
-    buf[:, : inst.n] = G
-    ok, fails = M.kernel_test(dev(inst.A), dev(buf), inst.n)
-    expect = O.kernel_condition(inst.A, G)
+    buf[:, :n] = G
+    buf[:, n:] = 5                      # the row padding must not take part
+    ok, fails = M.kernel_test(dev(A), dev(buf), n)
+    expect = O.kernel_condition(A, G)
     assert np.array_equal(ok.cpu().numpy().astype(bool), expect)
     assert fails == int((~expect).sum()) > 0
+    assert expect.sum() > 0.5 * len(G)
 
 
 # --- a11 -----------------------------------------------------------------------

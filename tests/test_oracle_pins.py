@@ -216,6 +216,10 @@ def test_minimal_elements_agrees_with_enumeration():
     canon = np.unique(np.array([O.canonical_sign(g) for g in kernel]), axis=0)
     mins = canon[O.minimal_elements(canon)]
     assert sorted(map(tuple, mins.tolist())) == sorted(map(tuple, O.graver_basis_box(inst.A, 3).tolist()))
+    # a selection of rows is judged against the whole set, as in the full mask
+    full = O.minimal_elements(canon)
+    for rows in ([0], [3, 1, 2], list(range(canon.shape[0] - 1, -1, -2))):
+        assert np.array_equal(O.minimal_elements(canon, rows=rows), full[rows])
 
 
 def test_extraction_on_tiny_instance_returns_graver_elements():
