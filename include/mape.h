@@ -282,13 +282,19 @@ int mape_dedup_static(const int8_t* cand, int64_t count, int32_t n, int32_t ldc,
                       int8_t* uniq, int64_t uniq_cap, int64_t* K_out,
                       void* stream);
 
-/* a9 -- condition C1 (§3): ok[k] = 1 iff A g_k = 0 exactly.  The products
- * are accumulated in int64 in general; when every A_ij fits in int8 (and the
- * row pitch is at most 256 bytes) they are int8 dot products accumulated in
- * int32, exact because |sum| <= 127 * 127 * n < 2^31.
- *   A [m x n] int32, G [K x ldg] int8.  *fail_count = rows with A g != 0.
+/* a9 -- condition C1 (§3): ok[k] = 1 iff A g_k = 0 exactly.
+ *   A [m x n] int32 (row-major, device), G [K x ldg] int8 (ldg a multiple of
+ *   16, at most 4096).  *fail_count = rows with A g != 0.
+ * Two exact implementations: when every A_ij fits in int8 and the rows are at
+ * most 256 bytes, int8 dot products (dp4a) accumulated in int32, exact because
+ * |sum| <= 127 * 127 * n < 2^31; otherwise A is compressed to its nonzeros
+ * (CSR, built on the device in the workspace) and each row of G, staged once
+ * in shared memory, is multiplied through them with int64 sums (the cost per
+ * row is nnz(A), not m n).  The workspace holds the CSR of a dense A
+ * (mape_kernel_test_workspace_bytes(m, n)).
+ * Errors: INVALID_ARG, SHAPE (n or ldg above 4096), CAPACITY (workspace), CUDA.
  * Synchronous (returns the count). */
-size_t mape_kernel_test_workspace_bytes(void);
+size_t mape_kernel_test_workspace_bytes(int32_t m, int32_t n);
 int mape_kernel_test(const int32_t* A, int32_t m, int32_t n, const int8_t* G,
                      int64_t K, int32_t ldg, uint8_t* ok, int64_t* fail_count,
                      void* workspace, size_t workspace_bytes, void* stream);
@@ -413,6 +419,20 @@ int mape_inequality_extension(int32_t n, int32_t m, int32_t m2, const int32_t* A
                               const int32_t* G, const int64_t* h, const int32_t* B,
                               int32_t* A2, int64_t* b2, int32_t* l2, int32_t* u2,
                               int32_t* B2);
+
+/* §3.4, Corollary 3.3 -- the objective and the points of the extended
+ * instance of mape_inequality_extension:
+ *   objective: Q2 [(n+m2) x (n+m2)] = [Q 0; 0 0], c2 = (c, 0), w2 = (w, 0)
+ *     (w may be NULL, then w2 is not written): f of the original variables;
+ *   points: for each of the S rows x of X [S x n], X2 [S x (n+m2)] = (x, s)
+ *     with the slacks s = G x - h, so that x feasible for A x = b, G x >= h
+ *     in the box maps to a point of the extended model (1).
+ * Errors: INVALID_ARG, BOUNDS (some x violates G x >= h), SHAPE (a slack
+ * beyond int32).  Host-only, host arrays owned by the caller. */
+int mape_inequality_extension_objective(int32_t n, int32_t m2, const int32_t* Q, const int32_t* c,
+                                        const int32_t* w, int32_t* Q2, int32_t* c2, int32_t* w2);
+int mape_inequality_extension_points(int32_t n, int32_t m2, const int32_t* G, const int64_t* h,
+                                     const int32_t* X, int32_t S, int32_t* X2);
 
 /* ========================================================================== *
  * Instance handle (host pointers)                                             *
@@ -609,6 +629,23 @@ int mape_server_get_stats(mape_server_h s, mape_server_stats* st);
 
 /* Waits (up to 10 minutes) for the running requests, then stops. */
 void mape_server_destroy(mape_server_h s);
+
+/* Launch timing, for measurement (no counterpart in the paper): while on,
+ * every launch of the extraction kernels below is bracketed by a pair of CUDA
+ * events on its stream; mape_launch_timing_read synchronises on them and
+ * returns, per kind, the summed milliseconds between each pair and the number
+ * of launches since timing was switched on (or last read: reading clears the
+ * pending pairs, not the sums).  mape_launch_timing(enable) switches it and
+ * clears everything.  The events add a little time around each launch, so
+ * time a region either with or without it. */
+#define MAPE_TIMED_STREAM_FWD     0   /* streamed forward + map kernel       */
+#define MAPE_TIMED_STREAM_COLLECT 1   /* streamed collection kernel          */
+#define MAPE_TIMED_STREAM_GRAD    2   /* streamed gradient + Adam kernel     */
+#define MAPE_TIMED_RESIDENT       3   /* resident fused kernel (T steps)     */
+#define MAPE_TIMED_KINDS          4
+int mape_launch_timing(int32_t enable);
+int mape_launch_timing_read(double* ms /* [MAPE_TIMED_KINDS] */,
+                            int64_t* launches /* [MAPE_TIMED_KINDS] */);
 
 /* Version string of the library build. */
 const char* mape_version(void);

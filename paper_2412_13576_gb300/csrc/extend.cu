@@ -48,3 +48,40 @@ extern "C" int mape_inequality_extension(int32_t n, int32_t m, int32_t m2, const
   std::memcpy(b2 + m, h, sizeof(int64_t) * m2);
   return MAPE_OK;
 }
+
+// The objective of the extended instance: f of the first n coordinates, the
+// slacks enter neither Q, c nor w.
+extern "C" int mape_inequality_extension_objective(int32_t n, int32_t m2, const int32_t* Q, const int32_t* c,
+                                                   const int32_t* w, int32_t* Q2, int32_t* c2, int32_t* w2) {
+  if (n <= 0 || m2 <= 0 || !Q || !c || !Q2 || !c2 || (w && !w2)) return MAPE_ERR_INVALID_ARG;
+  const int n2 = n + m2;
+  std::memset(Q2, 0, sizeof(int32_t) * (size_t)n2 * n2);
+  for (int i = 0; i < n; ++i) std::memcpy(Q2 + (int64_t)i * n2, Q + (int64_t)i * n, sizeof(int32_t) * n);
+  std::memcpy(c2, c, sizeof(int32_t) * n);
+  std::memset(c2 + n, 0, sizeof(int32_t) * m2);
+  if (w) {
+    std::memcpy(w2, w, sizeof(int32_t) * n);
+    std::memset(w2 + n, 0, sizeof(int32_t) * m2);
+  }
+  return MAPE_OK;
+}
+
+// Points of the extended instance: x followed by its slacks s = G x - h.
+extern "C" int mape_inequality_extension_points(int32_t n, int32_t m2, const int32_t* G, const int64_t* h,
+                                                const int32_t* X, int32_t S, int32_t* X2) {
+  if (n <= 0 || m2 <= 0 || S < 0 || !G || !h || (S > 0 && (!X || !X2))) return MAPE_ERR_INVALID_ARG;
+  const int n2 = n + m2;
+  for (int s = 0; s < S; ++s) {
+    const int32_t* x = X + (int64_t)s * n;
+    int32_t* y = X2 + (int64_t)s * n2;
+    std::memcpy(y, x, sizeof(int32_t) * n);
+    for (int k = 0; k < m2; ++k) {
+      long long v = -h[k];
+      for (int i = 0; i < n; ++i) v += (long long)G[(int64_t)k * n + i] * x[i];
+      if (v < 0) return MAPE_ERR_BOUNDS;  // x violates inequality k: no slack exists
+      if (v > INT32_MAX) return MAPE_ERR_SHAPE;
+      y[n + k] = (int32_t)v;
+    }
+  }
+  return MAPE_OK;
+}

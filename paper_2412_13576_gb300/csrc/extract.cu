@@ -31,7 +31,75 @@ void record_message(const char* what) {
   std::snprintf(g_last_err, sizeof(g_last_err), "%s", what);
 }
 
+// ---- launch timing (measurement only) ----------------------------------------
+
+namespace {
+std::mutex g_timing_mu;
+std::atomic<bool> g_timing_on{false};
+struct TimedPair {
+  int kind;
+  cudaEvent_t start, stop;
+};
+std::vector<TimedPair> g_timed;
+double g_timed_ms[MAPE_TIMED_KINDS] = {};
+int64_t g_timed_count[MAPE_TIMED_KINDS] = {};
+
+void drop_pending() {
+  for (auto& t : g_timed) {
+    cudaEventDestroy(t.start);
+    cudaEventDestroy(t.stop);
+  }
+  g_timed.clear();
+}
+}  // namespace
+
+bool launch_timing_on() { return g_timing_on.load(std::memory_order_relaxed); }
+
+void timed_record(int kind, cudaEvent_t start, cudaEvent_t stop) {
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  g_timed.push_back({kind, start, stop});
+}
+
 }  // namespace mape_detail
+
+extern "C" int mape_launch_timing(int32_t enable) {
+  using namespace mape_detail;
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  drop_pending();
+  for (int k = 0; k < MAPE_TIMED_KINDS; ++k) {
+    g_timed_ms[k] = 0.0;
+    g_timed_count[k] = 0;
+  }
+  g_timing_on.store(enable != 0);
+  return MAPE_OK;
+}
+
+extern "C" int mape_launch_timing_read(double* ms, int64_t* launches) {
+  using namespace mape_detail;
+  if (!ms || !launches) return MAPE_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  int rc = MAPE_OK;
+  for (auto& t : g_timed) {
+    cudaError_t e = cudaEventSynchronize(t.stop);
+    float v = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&v, t.start, t.stop);
+    if (e != cudaSuccess) {
+      record_cuda_error(e, "mape_launch_timing_read", __FILE__, __LINE__);
+      rc = MAPE_ERR_CUDA;
+      continue;
+    }
+    if (t.kind >= 0 && t.kind < MAPE_TIMED_KINDS) {
+      g_timed_ms[t.kind] += v;
+      g_timed_count[t.kind] += 1;
+    }
+  }
+  drop_pending();
+  for (int k = 0; k < MAPE_TIMED_KINDS; ++k) {
+    ms[k] = g_timed_ms[k];
+    launches[k] = g_timed_count[k];
+  }
+  return rc;
+}
 
 extern "C" const char* mape_last_cuda_error(void) { return mape_detail::g_last_err; }
 

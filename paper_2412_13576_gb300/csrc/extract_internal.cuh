@@ -46,4 +46,27 @@ void extract_stream_batch_free(StBatch* plan);
 // identity-topped test of every call's B (one launch each, one synchronisation)
 int identity_tops(const mape_extract_args* const* items, int count, int32_t* dflags, cudaStream_t st,
                   std::vector<bool>& ids);
+
+// Optional CUDA-event timing of the extraction kernels' launches
+// (mape_launch_timing): when on, timed_launch records an event pair around
+// the launch on its stream; the pairs are read at mape_launch_timing_read.
+bool launch_timing_on();
+void timed_record(int kind, cudaEvent_t start, cudaEvent_t stop);
+template <typename F>
+inline void timed_launch(int kind, cudaStream_t st, F&& f) {
+  if (!launch_timing_on()) {
+    f();
+    return;
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    f();
+    return;
+  }
+  cudaEventRecord(a, st);
+  f();
+  cudaEventRecord(b, st);
+  timed_record(kind, a, b);
+}
 }  // namespace mape_detail

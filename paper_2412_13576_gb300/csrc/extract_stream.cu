@@ -985,9 +985,12 @@ int extract_stream_widths(const mape_extract_args* a, cudaStream_t st, int wF, i
   auto collk = id ? stream_collect_kernel<true> : stream_collect_kernel<false>;
   const int fsm = fwd_smem(sh.wF), gsm = 2 * grad_stage(sh.wG);
   st_schedule(
-      a->t0, a->T, a->period, [&](int s, int f, int col) { launch(fwdk, gF, kThreadsF, fsm, st, p, s, f, col); },
-      [&](int s) { launch(collk, gC, 256, 0, st, p, s); },
-      [&](int s) { launch(gradk, gG, kThreads, gsm, st, p, s); });
+      a->t0, a->T, a->period,
+      [&](int s, int f, int col) {
+        timed_launch(MAPE_TIMED_STREAM_FWD, st, [&] { launch(fwdk, gF, kThreadsF, fsm, st, p, s, f, col); });
+      },
+      [&](int s) { timed_launch(MAPE_TIMED_STREAM_COLLECT, st, [&] { launch(collk, gC, 256, 0, st, p, s); }); },
+      [&](int s) { timed_launch(MAPE_TIMED_STREAM_GRAD, st, [&] { launch(gradk, gG, kThreads, gsm, st, p, s); }); });
   MAPE_LAUNCH_CHECK();
   return st_unpack(c, a, st);
 }

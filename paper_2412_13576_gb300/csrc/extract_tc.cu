@@ -1170,7 +1170,8 @@ int extract_tc(const mape_extract_args* a, cudaStream_t st) {
   auto kern = id ? (res ? extract_tc_kernel<true, true> : extract_tc_kernel<true, false>)
                  : (res ? extract_tc_kernel<false, true> : extract_tc_kernel<false, false>);
   MAPE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  mape_detail::launch(kern, (unsigned)ceil_div(a->P, kTileM), kThreads, smem, st, p);
+  mape_detail::timed_launch(MAPE_TIMED_RESIDENT, st,
+                            [&] { mape_detail::launch(kern, (unsigned)ceil_div(a->P, kTileM), kThreads, smem, st, p); });
   MAPE_LAUNCH_CHECK();
   return tc_unpack(p, a, st);
 }

@@ -155,7 +155,7 @@ _SIGS = {
     "mape_dedup": (C.c_int, [P_, I64, I32, I32, P_, I64, C.POINTER(I64), P_, C.c_size_t, P_]),
     "mape_dedup_static_max_rows": (I64, []),
     "mape_dedup_static": (C.c_int, [P_, I64, I32, I32, P_, I64, C.POINTER(I64), P_]),
-    "mape_kernel_test_workspace_bytes": (C.c_size_t, []),
+    "mape_kernel_test_workspace_bytes": (C.c_size_t, [I32, I32]),
     "mape_kernel_test": (C.c_int, [P_, I32, I32, P_, I64, I32, P_, C.POINTER(I64), P_, C.c_size_t, P_]),
     "mape_minimal_workspace_bytes": (C.c_size_t, [I64, I32]),
     "mape_minimal_filter": (C.c_int, [P_, I64, I32, I32, P_, P_, P_, C.POINTER(I64), P_, C.c_size_t, P_]),
@@ -178,6 +178,8 @@ _SIGS = {
     "mape_destroy": (None, [P_]),
     "mape_inequality_extension": (C.c_int, [I32, I32, I32, P_, P_, P_, P_, P_, P_, P_, P_, P_, P_, P_, P_]),
     "mape_kernel_basis": (C.c_int, [I32, I32, P_, I32, P_]),
+    "mape_inequality_extension_objective": (C.c_int, [I32, I32, P_, P_, P_, P_, P_, P_]),
+    "mape_inequality_extension_points": (C.c_int, [I32, I32, P_, P_, P_, I32, P_]),
     "mape_find_initial_solutions": (C.c_int, [P_, I32, P_, I32, I32, P_, I32, C.POINTER(I32)]),
     "mape_request_bytes": (C.c_size_t, [I32, I32, I32, I32, C.POINTER(Config)]),
     "mape_server_create": (C.c_int, [C.POINTER(ServerConfig), C.POINTER(P_)]),
@@ -190,6 +192,8 @@ _SIGS = {
     "mape_server_release": (C.c_int, [P_, C.c_uint64]),
     "mape_server_get_stats": (C.c_int, [P_, C.POINTER(ServerStats)]),
     "mape_server_destroy": (None, [P_]),
+    "mape_launch_timing": (C.c_int, [I32]),
+    "mape_launch_timing_read": (C.c_int, [C.POINTER(C.c_double), C.POINTER(I64)]),
 }
 
 
@@ -199,7 +203,9 @@ def library_path() -> str:
 
 
 def lib(build_if_missing: bool = False):
-    """The loaded libmape.  Raises if it is not built (or build_if_missing)."""
+    """The loaded libmape.  Raises if it is not built (or build_if_missing).
+    On a machine with a CUDA device, the handles' device memory is routed
+    through PyTorch's caching allocator (use_torch_allocator)."""
     global _LIB
     if _LIB is not None:
         return _LIB
@@ -214,7 +220,53 @@ def lib(build_if_missing: bool = False):
         fn.restype = res
         fn.argtypes = args
     _LIB = L
+    try:
+        import torch
+        if torch.cuda.is_available():
+            use_torch_allocator(True)
+    except ImportError:
+        pass
     return L
+
+
+# ---- device memory of the handles: PyTorch's caching allocator ---------------
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+def _torch_alloc(nbytes, stream, ctx):
+    # runs on the thread that creates or feeds a handle (a server's scheduler
+    # thread included), whose current device is the handle's; NULL = OOM
+    try:
+        import torch
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+    except Exception:
+        return None
+
+
+def _torch_free(ptr, nbytes, stream, ctx):
+    try:
+        import torch
+        torch.cuda.caching_allocator_delete(int(ptr))
+    except Exception:
+        pass
+
+
+_TORCH_HOOKS = (_ALLOC_FN(_torch_alloc), _FREE_FN(_torch_free))  # kept alive for the process
+
+
+def use_torch_allocator(enable: bool = True):
+    """Routes the device memory of every handle created afterwards through
+    PyTorch's caching allocator on the handle's stream (mape_set_allocator),
+    so that it is counted by torch.cuda.memory_allocated() and reused by
+    torch; enable=False restores the library's own memory pool."""
+    L = lib()
+    if enable:
+        _check(L.mape_set_allocator(C.cast(_TORCH_HOOKS[0], C.c_void_p), C.cast(_TORCH_HOOKS[1], C.c_void_p), None),
+               "mape_set_allocator")
+    else:
+        _check(L.mape_set_allocator(None, None, None), "mape_set_allocator")
 
 
 def _check(rc, where):
@@ -374,7 +426,7 @@ def kernel_test(A, G, n, stream=None):
     m = A.shape[0]
     K = G.shape[0]
     ok = torch.empty(max(K, 1), dtype=torch.uint8, device=G.device)
-    ws = _workspace(lib().mape_kernel_test_workspace_bytes(), G.device)
+    ws = _workspace(lib().mape_kernel_test_workspace_bytes(m, n), G.device)
     fails = I64(0)
     _check(lib().mape_kernel_test(_ptr(A), m, n, _ptr(G), K, G.shape[1], _ptr(ok), C.byref(fails), _ptr(ws),
                                   ws.numel(), _stream(stream)), "mape_kernel_test")
@@ -667,6 +719,24 @@ class Server:
         self.close()
 
 
+TIMED_KINDS = ("stream_fwd", "stream_collect", "stream_grad", "resident")
+
+
+def launch_timing(enable: bool):
+    """Switches the library's per-launch CUDA-event timing of the extraction
+    kernels on or off (mape_launch_timing) and clears its sums."""
+    _check(lib().mape_launch_timing(int(enable)), "mape_launch_timing")
+
+
+def launch_timing_read() -> dict:
+    """{kind: (summed ms, launches)} of the timed launches so far
+    (mape_launch_timing_read; synchronises on the recorded events)."""
+    ms = (C.c_double * len(TIMED_KINDS))()
+    cnt = (I64 * len(TIMED_KINDS))()
+    _check(lib().mape_launch_timing_read(ms, cnt), "mape_launch_timing_read")
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(TIMED_KINDS)}
+
+
 def trim_memory():
     """Hands back the memory that the library's pool on the current device
     keeps reserved beyond the live handles (mape_trim_memory)."""
@@ -680,8 +750,9 @@ def request_bytes(n, m, P, S, cfg: Config | None = None) -> int:
 
 def inequality_extension(inst, G, h):
     """The instance with G x >= h added, in equality form with slacks
-    (mape_inequality_extension): a copy of `inst` with n + m2 variables whose
-    objective ignores the slacks and whose xbar carries the slacks G xbar - h."""
+    (mape_inequality_extension, _objective and _points): a copy of `inst` with
+    n + m2 variables whose objective ignores the slacks and whose xbar carries
+    the slacks G xbar - h."""
     import dataclasses
     G = _np(np.atleast_2d(G), np.int32)
     h = _np(np.atleast_1d(h), np.int64)
@@ -696,13 +767,19 @@ def inequality_extension(inst, G, h):
     _check(lib().mape_inequality_extension(n, m, m2, _host(A), _host(b), _host(l), _host(u), _host(G), _host(h),
                                            _host(B), _host(A2), _host(b2), _host(l2), _host(u2), _host(B2)),
            "mape_inequality_extension")
-    Q2 = np.zeros((n + m2, n + m2), np.int32)
-    Q2[:n, :n] = inst.Q
-    c2 = np.concatenate([inst.c, np.zeros(m2, np.int32)]).astype(np.int32)
-    w2 = None if inst.w is None else np.concatenate([inst.w, np.zeros(m2, np.int32)]).astype(np.int32)
-    xbar2 = np.concatenate([inst.xbar, (G.astype(np.int64) @ inst.xbar - h)]).astype(np.int32)
+    Q, c = _np(inst.Q, np.int32), _np(inst.c, np.int32)
+    w = None if inst.w is None else _np(inst.w, np.int32)
+    Q2 = np.empty((n + m2, n + m2), np.int32)
+    c2 = np.empty(n + m2, np.int32)
+    w2 = None if w is None else np.empty(n + m2, np.int32)
+    _check(lib().mape_inequality_extension_objective(n, m2, _host(Q), _host(c), _host(w), _host(Q2), _host(c2),
+                                                     _host(w2)), "mape_inequality_extension_objective")
+    x = _np(inst.xbar[None, :], np.int32)
+    x2 = np.empty((1, n + m2), np.int32)
+    _check(lib().mape_inequality_extension_points(n, m2, _host(G), _host(h), _host(x), 1, _host(x2)),
+           "mape_inequality_extension_points")
     return dataclasses.replace(inst, name=inst.name + f"_ineq{m2}", n=n + m2, m=m + m2, A=A2, b=b2, l=l2, u=u2,
-                               B=B2, Q=Q2, c=c2, w=w2, xbar=xbar2)
+                               B=B2, Q=Q2, c=c2, w=w2, xbar=x2[0])
 
 
 def kernel_basis(A, reduce: bool = True) -> np.ndarray:

@@ -32,22 +32,62 @@ def check_direction_set(inst, D):
 
 
 def test_handles_reuse_pool_memory(M):
-    """Handles created one after another reuse the library pool's memory;
-    trimming hands it back and later handles still work."""
+    """With the library's own pool (the binding's PyTorch allocator switched
+    off): handles created one after another reuse the pool's memory; trimming
+    hands it back and later handles still work."""
     import torch
     inst = I.small_dense()
     st = I.normal_starts(inst, 128, seed=3)
     cfg = M.default_config(T=50)
     sets = []
-    for k in range(3):
-        with M.Instance.from_generated(inst, cfg) as h:
-            h.extract_directions(128, Z0=st.Z0)
-            h.wait(300)
-            sets.append(h.directions())
-        if k == 1:
-            M.trim_memory()
+    M.use_torch_allocator(False)
+    try:
+        for k in range(3):
+            with M.Instance.from_generated(inst, cfg) as h:
+                h.extract_directions(128, Z0=st.Z0)
+                h.wait(300)
+                sets.append(h.directions())
+            if k == 1:
+                M.trim_memory()
+    finally:
+        M.use_torch_allocator(True)
     torch.cuda.synchronize()
     assert all(np.array_equal(sets[0], D) for D in sets[1:]) and sets[0].shape[0] > 0
+
+
+def test_handle_memory_goes_through_torch(M):
+    """By default the binding registers PyTorch's caching allocator with the
+    library (mape_set_allocator): a handle's device buffers are counted by
+    torch.cuda.memory_allocated() while it lives (at least Z, M, V and the
+    two candidate buffers of the extraction) and given back when it closes;
+    the results equal those of the library's own pool."""
+    import torch
+    inst = I.medium_sparse()
+    P, T = 2048, 60
+    st = I.normal_starts(inst, P, std=0.3, seed=5)
+    cfg = M.default_config(T=T)
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    with M.Instance.from_generated(inst, cfg) as h:
+        h.extract_directions(P, Z0=st.Z0)
+        h.wait(300)
+        D_torch = h.directions()
+        torch.cuda.synchronize()
+        held = torch.cuda.memory_allocated() - base
+    ldg = M.round16(inst.n)
+    cap = P * (T + 1)
+    assert held >= 3 * P * inst.d * 4 + 2 * cap * ldg
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == base
+    M.use_torch_allocator(False)
+    try:
+        with M.Instance.from_generated(inst, cfg) as h:
+            h.extract_directions(P, Z0=st.Z0)
+            h.wait(300)
+            D_pool = h.directions()
+    finally:
+        M.use_torch_allocator(True)
+    assert np.array_equal(D_torch, D_pool) and D_torch.shape[0] > 0
 
 
 @pytest.mark.parametrize("precision", [0, 1])

@@ -163,10 +163,50 @@ def test_inequality_extension_matches_oracle(lib):
             assert np.array_equal(got, want)
         assert np.all(e.A.astype(np.int64) @ e.B == 0)
         assert np.array_equal(e.A.astype(np.int64) @ e.xbar, e.b)
+        # Corollary 3.3's objective and point: f ignores the slacks, and xbar
+        # carries them (G xbar - h), inside the slack bounds
+        n = inst.n
+        assert np.array_equal(e.xbar[:n], inst.xbar)
+        assert np.array_equal(e.xbar[n:], G @ inst.xbar.astype(np.int64) - h)
+        assert O.in_feasible_region(e.A, e.b, e.l, e.u, e.xbar)
+        assert np.all(e.Q[n:] == 0) and np.all(e.Q[:, n:] == 0) and np.array_equal(e.Q[:n, :n], inst.Q)
+        assert np.all(e.c[n:] == 0) and np.array_equal(e.c[:n], inst.c)
+        assert O.f_value(e.Q, e.c, e.w, e.xbar) == O.f_value(inst.Q, inst.c, inst.w, inst.xbar)
     inst = I.tiny_graver_case()
     with pytest.raises(mape.MapeError) as err:
         mape.inequality_extension(inst, np.ones((1, inst.n), np.int32), [10 ** 6])
     assert err.value.code == -4
+
+
+def test_inequality_extension_objective_and_points(lib):
+    """The objective (with the quartic weights) and several points of the
+    extended instance through the C ABI: w2 = (w, 0); a point that violates
+    G x >= h has no slack and is refused with MAPE_ERR_BOUNDS."""
+    import ctypes
+
+    import numpy as np
+    from oracle import mape_oracle as O
+    from paper_2412_13576_gb300 import instances as I
+    from paper_2412_13576_gb300 import mape
+    inst = I.make_instance("quartic_n12_m3", 12, 3, c_k=2, c_density=0.5, lo=-4, hi=4, q_k=3, q_density=0.3,
+                           lin_k=5, w_max=3, seed=41)
+    rng = np.random.default_rng(5)
+    n, m2 = inst.n, 2
+    G = rng.integers(-2, 3, size=(m2, n)).astype(np.int32)
+    h = (G @ inst.xbar.astype(np.int64) - 3).astype(np.int64)
+    e = mape.inequality_extension(inst, G, h)
+    assert np.array_equal(e.w[:n], inst.w) and np.all(e.w[n:] == 0)
+    X = np.stack([inst.xbar, inst.xbar]).astype(np.int32)
+    X2 = np.empty((2, n + m2), np.int32)
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    assert lib.mape_inequality_extension_points(n, m2, ptr(G), ptr(h), ptr(X), 2, ptr(X2)) == 0
+    for r in range(2):
+        assert np.array_equal(X2[r], e.xbar)
+        assert O.f_value(e.Q, e.c, e.w, X2[r]) == O.f_value(inst.Q, inst.c, inst.w, X[r])
+    # a point below one inequality: G x - h < 0
+    hb = h.copy()
+    hb[1] = G[1] @ inst.xbar.astype(np.int64) + 1
+    assert lib.mape_inequality_extension_points(n, m2, ptr(G), ptr(hb), ptr(X), 2, ptr(X2)) == -4
 
 
 def test_kernel_basis_matches_oracle(lib):
