@@ -1,21 +1,26 @@
 #!/usr/bin/env python
 """Benchmark of the MAPE hot path: verified Graver directions per second.
 
-One step = one pass of the whole path on the medium workload (n = 200, m = 40,
-A = [C | I] with C 40x160 in [-3,3] at density 0.1, box [0,10], nonconvex
-quadratic f; P = 8192 starts from projected uniform samples, T = 1000 Adam
-steps): starting points, Algorithm 2 with collection every step, dedup, the
-kernel test, the minimality filter, the direction coefficients and
-Algorithm 1 from xbar.  value = directions that pass C1, C4, nonzero and
-set-minimality, summed over the timed steps and ranks, over the max-over-ranks
-device time of those steps.  Inputs are resident in device memory; L2 is
-flushed (256 MiB write) before every timed step, outside the timed events.
+One step = one pass of the whole path on the large workload (n = 2000,
+m = 400, A = [C | I] with C 400x1600 in [-5,5] at density 0.01, box
+[-20,20], f = x'Qx + c'x + sum w_i x_i^4 with Q in [-5,5] at 0.005 and w in
+[0,3]; P = 65536 starts Z0 ~ N(0, 2), T = 1000 Adam steps, the rounded
+iterate collected every 50th step): Algorithm 2 on the streamed tensor-core
+kernels, dedup, the kernel test, the minimality filter, the direction
+coefficients and Algorithm 1 from xbar, all through the instance handle.
+value = directions that pass C1, C4, nonzero and set-minimality, summed over
+the timed steps and ranks, over the max-over-ranks device time of those
+steps.  Inputs are resident in device memory; they are larger than L2
+(the state alone is 1.26 GB), and L2 is flushed (256 MiB write) before every
+timed step as well, outside the timed events.  The medium workload (n = 200,
+P = 8192, the fused resident kernel) is measured beside it under "medium".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun every rank runs its own replica (its own start seed): the
 starts are independent problems, so there is no data-path collective and the
-scaling is weak.  --impl reference times the CPU oracle on a bounded sample.
+scaling is weak.  --impl reference times the CPU oracle, on all host cores,
+on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -33,11 +38,23 @@ sys.path.insert(0, ROOT)
 
 METRIC = "verified Graver directions/s"
 UNIT = "directions/s"
-N_FULL, M_FULL, P_FULL, T_FULL = 200, 40, 8192, 1000
-WORKLOAD = ("medium_sparse: n=200 m=40 d=160, A=[C|I_40], C 40x160 in [-3,3] at density 0.1, box [0,10], "
-            "Q sym in [-5,5] at 0.05, c in [-20,20]; P=8192 projected Uniform(l-u,u-l) starts, T=1000 Adam "
-            "steps (lr 0.003, lambda1 0.85, lambda2 1), collection every step; Algorithm 1 from xbar")
-CPU_SAMPLE_P = 48        # starts of the bounded CPU sample (T = 1000 as in the workload)
+
+# The timed workload: the large single instance.  Its starts are Z0 ~ N(0, 2)
+# (the projected uniform starts of Algorithm 2 never round into the box of
+# this instance within 1000 steps), and the rounded iterate is collected every
+# 50th step (one row per start and step would be 131 GB of candidates).
+LARGE = dict(name="large", n=2000, m=400, P=65536, T=1000, period=50, std=2.0, seed=2004)
+WORKLOAD = ("large_quartic: n=2000 m=400 d=1600, A=[C|I_400], C 400x1600 in [-5,5] at density 0.01, box [-20,20], "
+            "f = x'Qx + c'x + sum w_i x_i^4 with Q sym in [-5,5] at 0.005, c in [-20,20], w in [0,3]; P=65536 starts "
+            "Z0 ~ N(0,2), T=1000 Adam steps (lr 0.003, lambda1 0.85, lambda2 1), collection every 50th step; "
+            "streamed BF16 tensor-core kernels; Algorithm 1 from xbar")
+MEDIUM = dict(name="medium", n=200, m=40, P=8192, T=1000, period=1, std=None, seed=2002)
+MEDIUM_WORKLOAD = ("medium_sparse: n=200 m=40 d=160, A=[C|I_40], C 40x160 in [-3,3] at density 0.1, box [0,10], "
+                   "Q sym in [-5,5] at 0.05, c in [-20,20]; P=8192 projected Uniform(l-u,u-l) starts, T=1000 Adam "
+                   "steps, collection every step; fused resident BF16 kernel; Algorithm 1 from xbar")
+P_FULL, T_FULL = LARGE["P"], LARGE["T"]
+CPU_STARTS_PER_CORE = 4   # starts per host core in the bounded oracle sample (all T = 1000 steps)
+REF_STARTS_PER_CORE = 2   # the same for each step of the reference arm
 
 
 def parse_args(argv=None):
@@ -48,8 +65,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["bf16", "bf16x1", "fp32", "sparse"], default="bf16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
-    ap.add_argument("--cpu-sample", type=int, nargs=2, metavar=("P", "T"), help=argparse.SUPPRESS)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run (medium workload)")
+    ap.add_argument("--no-medium", action="store_true", help="skip the medium-workload measurement")
     ap.add_argument("--streamed-case", nargs=3, metavar=("NAME", "P", "T"),
                     help="time the streamed tensor-core extraction on a named instance (large: n=2000 m=400; "
                          "uneven1000: n=1000 m=200; medium: n=200 m=40) for P starts and T steps, and exit")
@@ -168,38 +185,74 @@ def measured_peaks():
 
 # ---------------------------------------------------------------- CPU oracle
 
-def cpu_sample(P, T):
-    """Oracle extraction + minimality filter on P starts of the workload, in
-    this (single-threaded) process; prints a JSON line."""
-    import numpy as np
-    from oracle import mape_oracle as O
+def _generated(wl):
     from paper_2412_13576_gb300 import instances as I
-    inst = I.medium_sparse()
-    G0 = I.uniform_samples(inst, P, seed=2002).G0
-    t0 = time.perf_counter()
-    Z0 = O.project_to_coordinates(inst.B, G0)
-    res = O.parallel_extraction(inst.A, inst.B, inst.l, inst.u, Z0, T=T)
-    dt = time.perf_counter() - t0
-    K = int(res["directions"].shape[0])
-    print(json.dumps({"directions": K, "unique": int(res["unique"].shape[0]), "seconds": dt,
-                      "value": K / dt, "P": P, "T": T, "threads": 1}))
+    return I.large_quartic() if wl["name"] == "large" else I.medium_sparse()
 
 
-def run_cpu_sample(P, T, timeout=600):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(P), str(T)],
-                         capture_output=True, text=True, env=env, timeout=timeout)
-    if out.returncode != 0:
-        raise RuntimeError("CPU sample failed: " + out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+def _starts(wl, inst, P, rank=0):
+    """Device-independent start arrays of a workload: (Z0, G0), one of them None."""
+    from paper_2412_13576_gb300 import instances as I
+    if wl["std"] is not None:
+        return I.normal_starts(inst, P, std=wl["std"], seed=wl["seed"] + rank).Z0, None
+    return None, I.uniform_samples(inst, P, seed=wl["seed"] + rank).G0
 
 
-def cpu_baseline_obj(r):
-    return {"value": r["value"], "unit": UNIT, "cores": r["threads"], "kind": "oracle",
-            "sample": (f"oracle (numpy fp64/int64, 1 thread) on {r['P']} of the {P_FULL} starts, all {r['T']} "
-                       f"steps of Algorithm 2 + dedup + minimality filter: {r['directions']} directions in "
-                       f"{r['seconds']:.1f} s (augmentation excluded: it adds no directions)")}
+def _oracle_part(args):
+    """One host core's share of the oracle sample: Algorithm 2 on a slice of
+    the starts (plain numpy, one thread); returns its distinct directions."""
+    name, lo, hi, T = args
+    from oracle import mape_oracle as O
+    wl = LARGE if name == "large" else MEDIUM
+    inst = _generated(wl)
+    Z0, G0 = _starts(wl, inst, hi)
+    Z0 = O.project_to_coordinates(inst.B, G0[lo:hi]) if Z0 is None else Z0[lo:hi]
+    res = O.parallel_extraction(inst.A, inst.B, inst.l, inst.u, Z0, T=T, period=wl["period"])
+    return res["unique"]
+
+
+class OraclePool:
+    """The CPU oracle on every host core: a pool of spawned one-thread worker
+    processes, each running Algorithm 2 on its slice of the sampled starts;
+    the parent takes the union of their sets and the minimality filter."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or os.cpu_count() or 1
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
+        os.environ["CUDA_VISIBLE_DEVICES"] = ""
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+
+    def run(self, wl, starts, T=None):
+        """Algorithm 2 + dedup + minimality on the first `starts` starts of the
+        workload for T steps (default: the workload's)."""
+        import numpy as np
+        from oracle import mape_oracle as O
+        T = wl["T"] if T is None else T
+        per = -(-starts // self.cores)
+        parts = [(wl["name"], lo, min(lo + per, starts), T) for lo in range(0, starts, per)]
+        t0 = time.perf_counter()
+        sets = self.pool.map(_oracle_part, parts)
+        found = {tuple(int(v) for v in r) for U in sets for r in U}
+        U = O.sort_directions(np.array(sorted(found), dtype=np.int64).reshape(-1, wl["n"]))
+        K = int(O.minimal_elements(U).sum()) if U.shape[0] else 0
+        dt = time.perf_counter() - t0
+        return {"directions": K, "unique": int(U.shape[0]), "seconds": dt, "value": K / dt, "P": starts,
+                "T": T, "cores": len(parts)}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline_obj(r, wl):
+    return {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+            "host_cores": os.cpu_count(),
+            "sample": (f"oracle (numpy fp64/int64, one thread per core, {r['cores']} cores) on {r['P']} of the "
+                       f"{wl['P']} starts, all {r['T']} steps of Algorithm 2 with collection every {wl['period']}"
+                       f"{'th' if wl['period'] > 1 else ''} step + dedup + minimality filter: {r['directions']} "
+                       f"directions in {r['seconds']:.1f} s (augmentation excluded: it adds no directions)")}
 
 
 # ---------------------------------------------------------------- our arm
@@ -207,11 +260,87 @@ def cpu_baseline_obj(r):
 PREC = {"bf16": 1, "bf16x1": 2, "fp32": 0, "sparse": 3}
 
 
-def run_ours(args):
+def handle_passes(mape, wl, inst, starts, stream, steps, warmup, prec, flush, clk=None):
+    """`warmup` untimed and `steps` timed passes of the whole path through one
+    instance handle (inputs resident on the device); returns the device time
+    of the timed passes (CUDA events on the handle's stream, L2 flushed before
+    each), their statuses and the library launches inside the timed region."""
+    import torch
+    Z0, G0 = starts
+    x0 = torch.from_numpy(inst.xbar[None, :].astype("int32")).to(flush.device)
+    cfg = mape.default_config(T=wl["T"], precision=prec, period=wl["period"])
+
+    def one(h):
+        h.extract_directions(wl["P"], Z0=Z0, G0=G0)
+        h.wait(900)
+        h.augment(x0)
+        h.wait(900)
+        return h.poll()
+
+    h = mape.Instance.from_generated(inst, cfg, stream=stream)
+    for _ in range(warmup):
+        one(h)
+    torch.cuda.synchronize()
+    total_ms, statuses = 0.0, []
+    L = mape.lib()
+    launches0 = L.mape_launch_count()
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = one(h)
+        e1.record(stream)
+        stream.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        statuses.append(st)
+    launches = L.mape_launch_count() - launches0
+    h.close()
+    return total_ms, statuses, launches
+
+
+def e2e_passes(mape, wl, inst, starts_host, stream, reps, directions_hint):
+    """The public handle API with host buffers, every copy inside the region:
+    the instance and the starts go up from pinned host memory, the direction
+    set (int8 rows) and the best point come back into pinned host memory
+    (buffers pinned once, before the region)."""
     import numpy as np
     import torch
+    Z0, G0 = starts_host
+    src = Z0 if Z0 is not None else G0
+    src_host = torch.from_numpy(np.ascontiguousarray(src)).pin_memory().numpy()
+    x0_host = inst.xbar[None, :].astype(np.int32)
+    D_host = torch.empty((max(int(1.2 * directions_hint), 1024), inst.n), dtype=torch.int8).pin_memory().numpy()
+    cfg = mape.default_config(T=wl["T"], precision=PREC["bf16"], period=wl["period"])
+    times, units = [], 0
+    h2d = (inst.A.nbytes + inst.b.nbytes + inst.l.nbytes + inst.u.nbytes + inst.B.nbytes + inst.Q.nbytes
+           + inst.c.nbytes + (0 if inst.w is None else inst.w.nbytes) + src_host.nbytes + x0_host.nbytes)
+    d2h = 0
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with mape.Instance.from_generated(inst, cfg, stream=stream) as he:
+            if Z0 is not None:
+                he.extract_directions(wl["P"], Z0=src_host)
+            else:
+                he.extract_directions(wl["P"], G0=src_host)
+            he.wait(900)
+            he.augment(x0_host)
+            he.wait(900)
+            D = he.directions_i8(out=D_host)
+            x, fx = he.solution()
+        times.append(time.perf_counter() - t0)
+        units += D.shape[0]
+        d2h = D.nbytes + x.nbytes + 8
+    return {"value": units / sum(times), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "steps": len(times)}
 
-    from paper_2412_13576_gb300 import instances as I
+
+def run_ours(args):
+    import torch
+
     from paper_2412_13576_gb300 import mape
 
     world, rank, local = dist_env()
@@ -221,79 +350,29 @@ def run_ours(args):
         dist.init_process_group("nccl")
     else:
         torch.cuda.set_device(0)
-    L = mape.lib(build_if_missing=True)
+    mape.lib(build_if_missing=True)
     dev = torch.device("cuda", torch.cuda.current_device())
-    inst = I.medium_sparse()
-    starts = I.uniform_samples(inst, P_FULL, seed=2002 + rank)
-    G0 = torch.from_numpy(starts.G0).to(dev)
-    x0 = torch.from_numpy(inst.xbar[None, :].astype(np.int32)).to(dev)
+    wl = LARGE
+    inst = _generated(wl)
+    starts_host = _starts(wl, inst, wl["P"], rank)
+    starts = tuple(None if a is None else torch.from_numpy(a).to(dev) for a in starts_host)
     stream = torch.cuda.Stream(device=dev)
-    cfg = mape.default_config(T=T_FULL, precision=PREC[args.precision])
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-
-    def one_step(h):
-        h.extract_directions(P_FULL, G0=G0)
-        h.wait(600)
-        h.augment(x0)
-        h.wait(600)
-        return h.poll()
-
-    h = mape.Instance.from_generated(inst, cfg, stream=stream)
-    for _ in range(args.warmup):
-        one_step(h)
+    prec = PREC[args.precision]
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
-    total_ms, directions, statuses = 0.0, 0, []
-    launches0 = L.mape_launch_count()
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            stream.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st = one_step(h)
-            e1.record(stream)
-            stream.synchronize()
-            total_ms += e0.elapsed_time(e1)
-            directions += st["directions"]
-            statuses.append(st)
-    launches = L.mape_launch_count() - launches0
+        total_ms, statuses, launches = handle_passes(mape, wl, inst, starts, stream, args.steps, args.warmup, prec,
+                                                     flush)
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
-    h.close()
+    directions = sum(st["directions"] for st in statuses)
     units_all, ms_max = reduce_over_ranks(directions, total_ms, world)
     value = units_all / (ms_max / 1e3)
-
-    # e2e: the public handle API with host buffers, every copy inside the
-    # region: the instance and the starts go up from pinned host memory, the
-    # direction set (int8 rows) and the best point come back into pinned
-    # host memory (buffers pinned once, before the region)
-    G0_host = torch.from_numpy(np.ascontiguousarray(starts.G0)).pin_memory().numpy()
-    x0_host = inst.xbar[None, :].astype(np.int32)
-    D_host = torch.empty((max(2 * int(directions / max(args.steps, 1)), 1024), inst.n),
-                         dtype=torch.int8).pin_memory().numpy()
-    e2e_times, e2e_units = [], 0
-    h2d = (inst.A.nbytes + inst.b.nbytes + inst.l.nbytes + inst.u.nbytes + inst.B.nbytes + inst.Q.nbytes
-           + inst.c.nbytes + G0_host.nbytes + x0_host.nbytes)
-    d2h = 0
-    for _ in range(max(1, min(args.steps, 3))):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        with mape.Instance.from_generated(inst, cfg, stream=stream) as he:
-            he.extract_directions(P_FULL, G0=G0_host)
-            he.wait(600)
-            he.augment(x0_host)
-            he.wait(600)
-            D = he.directions_i8(out=D_host)
-            x, fx = he.solution()
-        e2e_times.append(time.perf_counter() - t0)
-        e2e_units += D.shape[0]
-        d2h = D.nbytes + x.nbytes + 8
-    e2e_value = e2e_units / sum(e2e_times)
+    e2e = e2e_passes(mape, wl, inst, starts_host, stream, max(1, min(args.steps, 3)),
+                     directions / max(args.steps, 1))
 
     result = None
     if rank == 0:
@@ -303,58 +382,107 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"bf16": "bf16", "bf16x1": "bf16", "fp32": "f32", "sparse": "f32"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "P": P_FULL, "T": T_FULL, "n": N_FULL, "m": M_FULL,
-                       "precision": args.precision, "l2": "flushed (256 MiB write) before each timed step",
+            "config": {"workload": WORKLOAD, "P": wl["P"], "T": wl["T"], "n": wl["n"], "m": wl["m"],
+                       "period": wl["period"], "precision": args.precision,
+                       "l2": "inputs larger than L2, and L2 flushed (256 MiB write) before each timed step",
                        "replicas_per_rank": 1},
             "directions_per_step": directions / args.steps,
             "stages_ms": {k: statistics.median(s[k] for s in statuses)
                           for k in ("extract_ms", "filter_ms", "augment_ms", "first_improve_ms")},
+            "candidates_per_step": statistics.median(s["candidates"] for s in statuses),
             "best_f": statuses[-1]["best_f"],
+            "f_xbar": int(_f_value(inst, inst.xbar)),
             "gpu_launches": launches,
             "clocks": clk.summary(),
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                    "steps": len(e2e_times)},
+            "e2e": e2e,
         }
-        result["roofline"] = roofline(mape, inst, starts, stream, args)
-        if not args.no_plain and args.precision != "fp32":
-            result["vs_plain_fp32"] = plain_fp32(mape, inst, G0, x0, stream)
+        result["roofline"] = roofline_streamed(mape, wl, inst, starts, stream)
+        if world == 1 and not args.no_medium:
+            result["medium"] = medium_measure(mape, args, stream, flush)
         if args.batch > 0 and world == 1:
             result["batched"] = batch_measure(args.batch)
         if args.serve > 0 and world == 1:
             result["serving"] = serve_measure(args.serve, args.serve_T)
         if not args.no_cpu_baseline and world == 1:
-            result["cpu_baseline"] = cpu_baseline_obj(run_cpu_sample(CPU_SAMPLE_P, T_FULL))
+            pool = OraclePool()
+            try:
+                result["cpu_baseline"] = cpu_baseline_obj(pool.run(wl, CPU_STARTS_PER_CORE * pool.cores), wl)
+            finally:
+                pool.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return result
 
 
-def time_extract_kernel(mape, inst, G0, P, T, prec, stream, reps):
-    """CUDA-event times (ms, on `stream`) of `reps` + 1 launches of the fused
-    extraction on the first P rows of G0 for T steps from the same projected
-    starts; the first launch is a warm-up and is dropped."""
+def _f_value(inst, x):
+    """f(x) in exact integers (reporting only: the value the path starts from)."""
+    import numpy as np
+    x = np.asarray(x, dtype=object)
+    Q = np.asarray(inst.Q, dtype=object)
+    val = int(x @ Q @ x) + int(np.asarray(inst.c, dtype=object) @ x)
+    if inst.w is not None:
+        val += int(np.asarray(inst.w, dtype=object) @ (x ** 4))
+    return val
+
+
+def medium_measure(mape, args, stream, flush):
+    """The medium workload (fused resident kernel) through the same handle
+    passes, with its own roofline and the plain FP32 comparison."""
+    import torch
+    wl = MEDIUM
+    inst = _generated(wl)
+    starts_host = _starts(wl, inst, wl["P"])
+    starts = tuple(None if a is None else torch.from_numpy(a).to(flush.device) for a in starts_host)
+    total_ms, statuses, launches = handle_passes(mape, wl, inst, starts, stream, args.steps, min(args.warmup, 3),
+                                                 PREC["bf16"], flush)
+    directions = sum(st["directions"] for st in statuses)
+    out = {"workload": MEDIUM_WORKLOAD, "value": directions / (total_ms / 1e3), "unit": UNIT,
+           "ms_per_step": total_ms / args.steps, "directions_per_step": directions / args.steps,
+           "stages_ms": {k: statistics.median(s[k] for s in statuses)
+                         for k in ("extract_ms", "filter_ms", "augment_ms", "first_improve_ms")},
+           "best_f": statuses[-1]["best_f"], "gpu_launches": launches,
+           "e2e": e2e_passes(mape, wl, inst, starts_host, stream, max(1, min(args.steps, 3)),
+                             directions / max(args.steps, 1)),
+           "roofline": roofline_resident(mape, wl, inst, starts_host[1], stream)}
+    if not args.no_plain:
+        out["vs_plain_fp32"] = plain_fp32(mape, wl, inst, starts, stream)
+    return out
+
+
+def time_extract_kernel(mape, inst, starts, P, T, prec, stream, reps, period=1):
+    """CUDA-event times (ms, on `stream`) of `reps` + 1 calls of mape_extract
+    on the first P starts for T steps, all from the same starting state (the
+    first call is a warm-up and is dropped).  starts = (Z0, G0) host arrays,
+    one of them None (G0 rows are projected first)."""
     import numpy as np
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     B = torch.from_numpy(inst.B).to(dev)
     span = torch.from_numpy((inst.u - inst.l).astype(np.int32)).to(dev)
-    cfg = mape.default_config(T=T, precision=prec)
+    cfg = mape.default_config(T=T, precision=prec, period=period)
+    Zs, Gs = starts
     with torch.cuda.stream(stream):
-        Z0 = mape.project_starts(B, torch.from_numpy(G0[:P]).to(dev), stream=stream)
+        if Zs is not None:
+            Z0 = torch.from_numpy(np.ascontiguousarray(Zs[:P])).to(dev)
+        else:
+            Z0 = mape.project_starts(B, torch.from_numpy(Gs[:P]).to(dev), stream=stream)
     ldc = mape.round16(inst.n)
-    cand = torch.empty((P * T + 16, ldc), dtype=torch.int8, device=dev)  # every start-step fits
+    rows = P * (T // period + 1) + 16                      # every collection of every start fits
+    cand = torch.empty((rows, ldc), dtype=torch.int8, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
     flags = torch.zeros(1, dtype=torch.int32, device=dev)
     ws = torch.empty(mape.lib().mape_extract_workspace_bytes(inst.n, inst.d, P, prec), dtype=torch.uint8,
                      device=dev)
     times, counts = [], []
+    Z, Mm, V = torch.empty_like(Z0), torch.empty_like(Z0), torch.empty_like(Z0)
     for i in range(reps + 1):
-        Z = Z0.clone()
-        Mm = torch.zeros_like(Z)
-        V = torch.zeros_like(Z)
-        cnt.zero_()
-        flags.zero_()
+        with torch.cuda.stream(stream):
+            Z.copy_(Z0)
+            Mm.zero_()
+            V.zero_()
+            cnt.zero_()
+            flags.zero_()
         stream.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -372,31 +500,27 @@ def time_extract_kernel(mape, inst, G0, P, T, prec, stream, reps):
 
 
 def kernel_case(args):
-    """The fused extraction alone on a small case (P starts, T steps): the
-    command profilers run."""
+    """The fused extraction alone on a small case of the medium workload (P
+    starts, T steps): the command profilers run."""
     import torch
-    from paper_2412_13576_gb300 import instances as I
     from paper_2412_13576_gb300 import mape
     torch.cuda.set_device(0)
     mape.lib(build_if_missing=True)
-    inst = I.medium_sparse()
+    inst = _generated(MEDIUM)
     P, T = args.kernel_case
-    starts = I.uniform_samples(inst, P_FULL, seed=2002)
     stream = torch.cuda.Stream()
-    times, counts = time_extract_kernel(mape, inst, starts.G0, P, T, PREC[args.precision], stream, reps=1)
+    times, counts = time_extract_kernel(mape, inst, _starts(MEDIUM, inst, MEDIUM["P"]), P, T, PREC[args.precision],
+                                        stream, reps=1)
     return {"kernel_case": {"workload": "medium_sparse", "P": P, "T": T, "precision": args.precision,
                             "ms_per_launch": times, "candidates": counts}}
 
 
-STREAMED_CASES = {"large": "large_quartic", "uneven1000": "uneven1000", "medium": "medium_sparse"}
-
-
 def streamed_case(args):
-    """The streamed kernels (three per step) alone on a named instance: per
-    step, the forward pass reads z (4 d bytes per start) and writes sign(Bm z)
-    (2 R bytes), the gradient pass reads it back and reads and writes z, m, v
-    (24 d bytes): the algorithmic bytes are 28 d + 4 R per start-step."""
-    import numpy as np
+    """The streamed kernels (three per step) alone on a named instance, with
+    the large workload's starts and collection period: per step, the forward
+    pass reads z (4 d bytes per start) and writes sign(Bm z) (2 R bytes), the
+    gradient pass reads it back and reads and writes z, m, v (24 d bytes): the
+    algorithmic bytes are 28 d + 4 R per start-step."""
     import torch
     from paper_2412_13576_gb300 import instances as I
     from paper_2412_13576_gb300 import mape
@@ -407,9 +531,10 @@ def streamed_case(args):
             "uneven1000": lambda: I.uneven_single(1000, density=0.05)}[name]()
     bf = args.precision in ("bf16", "bf16x1")
     prec = PREC[args.precision] | (0 if not bf else (mape.PREC_AUTOTUNE if args.autotune else mape.PREC_STREAMED))
-    G0 = I.uniform_samples(inst, P, seed=2004).G0
+    Z0 = I.normal_starts(inst, P, std=LARGE["std"], seed=LARGE["seed"]).Z0
     stream = torch.cuda.Stream()
-    times, counts = time_extract_kernel(mape, inst, G0, P, T, prec, stream, reps=2)
+    times, counts = time_extract_kernel(mape, inst, (Z0, None), P, T, prec, stream, reps=2,
+                                        period=LARGE["period"])
     ms = statistics.median(times)
     R = inst.n - inst.d
     algo = (28.0 * inst.d + 4.0 * R) * P * T
@@ -572,16 +697,17 @@ def batch_measure(N, T=1000, seed=1003):
                          f"projected uniform starts; T = {T}; a3-a8 only")}
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "extract_tc_kernel_medium_sparse_P8192_T1000_traffic.md")
+RESIDENT_TRAFFIC = os.path.join(ROOT, "profiles", "extract_tc_kernel_medium_sparse_P8192_T1000_traffic.md")
+STREAM_TRAFFIC = os.path.join(ROOT, "profiles", "stream_grad_kernel_large_quartic_traffic.md")
 
 
-def measured_traffic(src_path):
-    """DRAM bytes per launch of the fused kernel from the committed ncu
-    record, if that record was taken on the current source (same SHA-256)."""
+def measured_traffic(record, src_path):
+    """DRAM bytes per launch from a committed ncu record, if that record was
+    taken on the current source of the kernel (same SHA-256)."""
     import hashlib
     import re
     try:
-        text = open(TRAFFIC_FILE).read()
+        text = open(record).read()
         sha = hashlib.sha256(open(src_path, "rb").read()).hexdigest()
     except OSError:
         return None
@@ -592,51 +718,100 @@ def measured_traffic(src_path):
     return int(m_b.group(1))
 
 
-def roofline(mape, inst, starts, stream, args, reps=3):
-    """The dominant kernel, the fused extraction launch (T = 1000 steps), timed
-    alone with CUDA events on its stream.  Its state (z, m, v) stays on chip
-    for the whole launch, so the bound is the tensor-core roofline and the
-    algorithmic work is the dense contraction count per start and step:
-    B.z (2nd), B^T.sign(Bz) (2nd) and B.round(z) (2nd)."""
+def roofline_streamed(mape, wl, inst, starts, stream, reps=2):
+    """The streamed kernels of the large workload, timed live: `reps` calls of
+    mape_extract (T steps, the workload's starts and period) with the
+    library's per-launch CUDA events on the call's stream.  The dominant
+    kernel is the gradient + Adam pass: per start-step it reads sign(Bm z)
+    (2 R bytes, BF16) and reads and writes z, m, v (24 d bytes, FP32), so its
+    algorithmic bytes per launch are (24 d + 2 R) P; the forward pass reads z
+    and writes sign(Bm z) ((4 d + 2 R) P).  The bound is HBM bandwidth: the
+    state (1.26 GB) is far larger than L2 and is streamed every step."""
+    import numpy as np
     peaks, src = measured_peaks()
-    prec = PREC[args.precision]
-    times, _ = time_extract_kernel(mape, inst, starts.G0, P_FULL, T_FULL, prec, stream, reps)
+    P, T, d = wl["P"], wl["T"], inst.d
+    R = inst.n - d
+    host = tuple(None if a is None else a.cpu().numpy() for a in starts)
+    mape.launch_timing(True)
+    try:
+        times, counts = time_extract_kernel(mape, inst, host, P, T, PREC["bf16"], stream, reps, period=wl["period"])
+        per = mape.launch_timing_read()
+    finally:
+        mape.launch_timing(False)
+    ms_grad = per["stream_grad"][0] / max(per["stream_grad"][1], 1)
+    ms_fwd = per["stream_fwd"][0] / max(per["stream_fwd"][1], 1)
+    ms_coll = per["stream_collect"][0] / max(per["stream_collect"][1], 1)
+    bytes_grad = (24.0 * d + 2.0 * R) * P
+    bytes_fwd = (4.0 * d + 2.0 * R) * P
+    gbs = bytes_grad / (ms_grad / 1e3) / 1e9
+    peak = peaks["hbm_gbs"]
+    call_ms = statistics.median(times)
+    step_bytes = (28.0 * d + 4.0 * R) * P
+    src_path = os.path.join(ROOT, "paper_2412_13576_gb300", "csrc", "extract_stream.cu")
+    return {"bound": "hbm", "kernel": "stream_grad_kernel", "achieved": gbs, "peak": peak, "unit": "GB/s",
+            "frac": gbs / peak, "traffic": measured_traffic(STREAM_TRAFFIC, src_path),
+            "ms_per_launch": ms_grad, "bytes_per_launch": bytes_grad,
+            "peak_source": f"{src} HBM copy rate (MEASURED_PEAKS.json hbm_gbs)",
+            "launches_timed": per["stream_grad"][1],
+            "forward": {"kernel": "stream_fwd_kernel", "ms_per_launch": ms_fwd, "bytes_per_launch": bytes_fwd,
+                        "achieved": bytes_fwd / (ms_fwd / 1e3) / 1e9,
+                        "frac": bytes_fwd / (ms_fwd / 1e3) / 1e9 / peak},
+            "collect_ms_per_launch": ms_coll, "collect_launches": per["stream_collect"][1],
+            "step": {"ms": call_ms / T, "bytes": step_bytes, "achieved": step_bytes * T / (call_ms / 1e3) / 1e9,
+                     "frac": step_bytes * T / (call_ms / 1e3) / 1e9 / peak,
+                     "note": "one step = forward + gradient (+ collection every period-th step), 28 d + 4 R bytes "
+                             "per start; the call also packs z, m, v into the blocked layout and back once"},
+            "candidates_per_call": int(np.median(counts)),
+            "note": "launch durations from CUDA events recorded by the library around each launch on the "
+                    "extraction stream, over T = 1000 steps for P = 65536 starts; traffic = ncu dram read+write "
+                    "bytes per launch, null unless taken on this source"}
+
+
+def roofline_resident(mape, wl, inst, G0, stream, reps=3):
+    """The fused resident extraction launch of the medium workload (T = 1000
+    steps), timed alone with CUDA events on its stream.  Its state (z, m, v)
+    stays on chip for the whole launch, so the bound is the tensor-core
+    roofline.  Two counts of the work: the dense contraction of the scope
+    table (B z, B^T sign(Bz), B round(z): 6 n d flops per start-step) and the
+    contraction the kernel performs (B = [I; -C], so only the m rows of -C go
+    through the tensor cores: 2 m d flops per product, with z as two BF16
+    terms: 8 m d)."""
+    peaks, src = measured_peaks()
+    P, T = wl["P"], wl["T"]
+    times, _ = time_extract_kernel(mape, inst, (None, G0), P, T, PREC["bf16"], stream, reps)
     ms = statistics.median(times)
     n, d, m = inst.n, inst.d, inst.n - inst.d
-    if prec == 0:
-        return {"kernel": "extract_fp32 (3 kernels per step)", "bound": "alu", "ms": ms}
-    nterms = 2 if prec == 1 else 1
-    flops = 6.0 * n * d * P_FULL * T_FULL
+    flops = 6.0 * n * d * P * T
+    performed = 2.0 * m * d * P * T * 4
     achieved = flops / (ms / 1e3) / 1e12
     peak = peaks["bf16_tflops"]
-    # what the tensor pipe actually issues: the basis is [I; -C], so only the
-    # m = n - d rows of -C are contracted (nterms forward terms, B round(z), gradient)
-    mma_flops = 2.0 * m * d * P_FULL * T_FULL * (nterms + 2)
     src_path = os.path.join(ROOT, "paper_2412_13576_gb300", "csrc", "extract_tc.cu")
     return {"bound": "tensor", "kernel": "extract_tc_kernel", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": measured_traffic(src_path), "ms_per_launch": ms,
+            "frac": achieved / peak, "traffic": measured_traffic(RESIDENT_TRAFFIC, src_path), "ms_per_launch": ms,
             "flops_per_launch": flops,
+            "performed": {"flops_per_launch": performed, "achieved": performed / (ms / 1e3) / 1e12,
+                          "frac": performed / (ms / 1e3) / 1e12 / peak},
             "peak_source": f"{src} cuBLAS BF16 dense burst (MEASURED_PEAKS.json bf16_tflops)",
-            "issued_mma_tflops": mma_flops / (ms / 1e3) / 1e12,
-            "state_bytes_per_s": 24.0 * d * P_FULL * T_FULL / (ms / 1e3),
-            "note": "one launch = T=1000 steps for P=8192 starts; algorithmic work = 6*n*d flops per start-step "
-                    "(B z, B^T sign(Bz), B round(z) as dense products); z, m, v stay in TMEM for the launch, so "
-                    "HBM carries only the state in and out and the candidates; traffic = ncu dram read+write "
-                    "bytes of one full launch, null unless taken on this source"}
+            "note": "one launch = T=1000 steps for P=8192 starts; frac on the dense 6 n d count; performed = "
+                    "the m rows of -C through the tensor cores (hi, lo, round(z), gradient: 8 m d flops per "
+                    "start-step); traffic = ncu dram read+write bytes of one full launch, null unless taken on "
+                    "this source"}
 
 
-def plain_fp32(mape, inst, G0, x0, stream):
+def plain_fp32(mape, wl, inst, starts, stream):
     """One pass of the plain FP32 single-instance path (per step: strict-FP32
     cuBLAS GEMMs and unfused elementwise kernels) for comparison, timed after
     one untimed warm-up pass."""
     import torch
-    cfg = mape.default_config(T=T_FULL, precision=0)
+    Z0, G0 = starts
+    x0 = torch.from_numpy(inst.xbar[None, :].astype("int32")).cuda()
+    cfg = mape.default_config(T=wl["T"], precision=0, period=wl["period"])
     with mape.Instance.from_generated(inst, cfg, stream=stream) as h:
         for rep in range(2):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            h.extract_directions(P_FULL, G0=G0)
+            h.extract_directions(wl["P"], Z0=Z0, G0=G0)
             h.wait(900)
             h.augment(x0)
             h.wait(900)
@@ -651,35 +826,40 @@ def plain_fp32(mape, inst, G0, x0, stream):
 # ---------------------------------------------------------------- reference arm
 
 def run_reference(args):
+    """The CPU oracle as it stands, on all host cores, on a bounded sample of
+    the large workload (REF_STARTS_PER_CORE starts per core, all T steps, per
+    step), under the same metric and unit."""
     world, rank, _ = dist_env()
     if rank != 0:
         return None
-    total_s, total_units = 0.0, 0
-    r = None
-    for _ in range(args.warmup):
-        run_cpu_sample(CPU_SAMPLE_P, T_FULL)
-    for _ in range(args.steps):
-        r = run_cpu_sample(CPU_SAMPLE_P, T_FULL)
-        total_s += r["seconds"]
-        total_units += r["directions"]
+    wl = LARGE
+    pool = OraclePool()
+    try:
+        starts = REF_STARTS_PER_CORE * pool.cores
+        for _ in range(args.warmup):      # warm-up: the workers import and build the instance
+            pool.run(wl, pool.cores, T=wl["period"])
+        total_s, total_units, r = 0.0, 0, None
+        for _ in range(args.steps):
+            r = pool.run(wl, starts)
+            total_s += r["seconds"]
+            total_units += r["directions"]
+    finally:
+        pool.close()
     value = total_units / total_s
-    cb = cpu_baseline_obj(r)
+    cb = cpu_baseline_obj(r, wl)
     cb["value"] = value
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+int64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "P": P_FULL, "T": T_FULL, "n": N_FULL, "m": M_FULL,
-                       "sample_starts": CPU_SAMPLE_P},
+            "config": {"workload": WORKLOAD, "P": wl["P"], "T": wl["T"], "n": wl["n"], "m": wl["m"],
+                       "period": wl["period"], "sample_starts": starts},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main(argv=None):
     args = parse_args(argv)
-    if args.cpu_sample:
-        cpu_sample(*args.cpu_sample)
-        return 0
     if args.kernel_case:
         print(json.dumps(kernel_case(args)), flush=True)
         return 0

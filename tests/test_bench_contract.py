@@ -1,6 +1,6 @@
 """The reference arm of bench.py prints the benchmark's one JSON line on the
-CPU: the oracle on its bounded sample, under the same metric, unit and
-workload as the GPU arm."""
+CPU: the oracle on all host cores on its bounded sample, under the same
+metric, unit and workload as the GPU arm."""
 import json
 import os
 import subprocess
@@ -24,9 +24,11 @@ def test_reference_arm_json_line():
     assert r["higher_is_better"] is True and r["scaling"] == "weak" and r["vs_baseline"] is None
     assert r["data"] == "synthetic"
     assert r["config"]["workload"] == bench.WORKLOAD
-    assert (r["config"]["P"], r["config"]["T"]) == (bench.P_FULL, bench.T_FULL)
+    assert (r["config"]["P"], r["config"]["T"], r["config"]["period"]) == (bench.LARGE["P"], bench.LARGE["T"],
+                                                                         bench.LARGE["period"])
     cb = r["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == r["value"]
+    assert cb["cores"] == min(os.cpu_count(), r["config"]["sample_starts"]) and cb["host_cores"] == os.cpu_count()
     e2e = r["e2e"]
     assert e2e["value"] == r["value"] and e2e["unit"] == r["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
