@@ -71,6 +71,16 @@ extern "C" {
                              accurate to about FP32                             */
 #define MAPE_PREC_BF16X1 2 /* as MAPE_PREC_BF16 with z as one BF16 term (hi):
                              half the forward MMAs, 8-bit z in B z            */
+#define MAPE_PREC_FP8 4    /* the streamed tensor-core kernels with the forward
+                             product B z in FP8: z as e4m3 scaled per start
+                             by a power of two (max |z| of each start lands in
+                             [128, 256)), B as e4m3 (entries must be exact
+                             in e4m3, e.g. |B_ij| <= 16; flag 8 otherwise),
+                             kind::f8f6f4 MMAs with FP32 accumulation, 2 per
+                             64 coordinates instead of 8 for MAPE_PREC_BF16;
+                             z carries 4 significant bits in B z (sign(Bz)
+                             is coarse), B round(z) stays exact in BF16 and
+                             the gradient runs as for MAPE_PREC_BF16       */
 #define MAPE_PREC_SPARSE 3 /* FP32 on CUDA cores for an identity-topped B =
                              [I ; B'] with sparse B' (compressed rows and
                              columns): one block per start with its z, m, v
@@ -95,6 +105,13 @@ extern "C" {
  * process; later calls reuse it.  Results are those of the chosen
  * implementation; mape_autotune_lookup reports the choice and the probes. */
 #define MAPE_PREC_AUTOTUNE 0x200
+/* OR-ing MAPE_PREC_SPARSE_FWD into MAPE_PREC_BF16 runs the forward product
+ * of the streamed path on the CUDA cores over the compressed rows of Bm, for
+ * an identity-topped B = [I; Bm] whose Bm has density at most 1/16
+ * (nnz(Bm) <= R d / 16; SHAPE otherwise): y = Bm z in FP32 from the full FP32
+ * z (at least as accurate as the two BF16 terms); the gradient stays on the
+ * tensor cores.  Implies MAPE_PREC_STREAMED. */
+#define MAPE_PREC_SPARSE_FWD 0x400
 #define MAPE_PREC_MASK 0xff
 
 /* ---- hyper-parameters (§3.2, §4: lambda1 = 0.85, lambda2 = 1, lr = 0.003) - */
@@ -229,7 +246,8 @@ int mape_extract_batch(const mape_extract_args* items, int32_t count,
                        void* workspace, size_t workspace_bytes, void* stream);
 
 typedef struct {
-  int32_t path;             /* chosen: 0 resident fused kernel, 1 streamed    */
+  int32_t path;             /* chosen: 0 resident fused kernel, 1 streamed,
+                               2 streamed with the sparse CUDA-core forward   */
   int32_t wF, wG;           /* streamed: forward / gradient N-block widths    */
   int32_t candidates;       /* candidates that ran                            */
   int32_t probe_steps;      /* Adam steps each candidate was timed on         */
@@ -646,6 +664,18 @@ void mape_server_destroy(mape_server_h s);
 int mape_launch_timing(int32_t enable);
 int mape_launch_timing_read(double* ms /* [MAPE_TIMED_KINDS] */,
                             int64_t* launches /* [MAPE_TIMED_KINDS] */);
+
+/* Tensor-core instruction cost on this GPU, for measurement (no counterpart
+ * in the paper): one thread issues `chain` tcgen05.mma instructions
+ * (cta_group::1; kind 0: kind::f16 with BF16 operands, K = 16; kind 1:
+ * kind::f8f6f4 with e4m3 operands, K = 32) of shape M x N (M 64 or 128,
+ * N 16..256 in steps of 16) into 1 or 2 TMEM accumulators; *issue_cycles and
+ * *total_cycles are SM cycles per instruction from the first issue to the last
+ * issue and to the completion of the chain.  Synchronous on the legacy
+ * default stream; allocates 24 bytes of device memory.  Errors: INVALID_ARG,
+ * CUDA, TIMEOUT (the completion wait gave up after 2 s). */
+int mape_mma_issue_probe(int32_t kind, int32_t M, int32_t N, int32_t accumulators, int32_t chain,
+                         double* issue_cycles, double* total_cycles);
 
 /* Version string of the library build. */
 const char* mape_version(void);

@@ -127,9 +127,11 @@ namespace {
 bool valid_precision(int32_t precision) {
   const int32_t base = precision & MAPE_PREC_MASK, extra = precision & ~MAPE_PREC_MASK;
   if (base == MAPE_PREC_FP32 || base == MAPE_PREC_SPARSE) return extra == 0;
+  if (base == MAPE_PREC_FP8) return (extra & ~MAPE_PREC_STREAMED) == 0;
   if ((extra & MAPE_PREC_STREAMED) && (extra & MAPE_PREC_AUTOTUNE)) return false;
+  if ((extra & MAPE_PREC_SPARSE_FWD) && ((extra & MAPE_PREC_AUTOTUNE) || base != MAPE_PREC_BF16)) return false;
   return (base == MAPE_PREC_BF16 || base == MAPE_PREC_BF16X1) &&
-         (extra & ~(MAPE_PREC_STREAMED | MAPE_PREC_AUTOTUNE)) == 0;
+         (extra & ~(MAPE_PREC_STREAMED | MAPE_PREC_AUTOTUNE | MAPE_PREC_SPARSE_FWD)) == 0;
 }
 
 // ---- autotuning of the BF16 implementation and the streamed tile widths ----
@@ -167,7 +169,8 @@ size_t tune_scratch_bytes(int32_t n, int32_t d, int32_t P) {
 
 int run_choice(const mape_extract_args* a, cudaStream_t st, const mape_tune_info& c) {
   if (c.path == 0) return mape_detail::extract_tc(a, st);
-  return mape_detail::extract_stream_widths(a, st, c.wF, c.wG);
+  return mape_detail::extract_stream_widths(a, st, c.wF, c.wG,
+                                            c.path == 2 ? mape_detail::kFwdSparse : mape_detail::kFwdDense);
 }
 
 }  // namespace
@@ -197,6 +200,11 @@ static int autotune(const mape_extract_args* a, cudaStream_t st, size_t impl_byt
       c.path = 1; c.wF = wf; c.wG = wg;
       cands.push_back(c);
     }
+  // the sparse forward (refused with SHAPE, and so skipped, when B does not qualify)
+  for (int wg : {64, 128, 256}) {
+    c.path = 2; c.wF = 256; c.wG = wg;
+    cands.push_back(c);
+  }
   cudaEvent_t e0, e1;
   MAPE_CUDA_TRY(cudaEventCreate(&e0));
   MAPE_CUDA_TRY(cudaEventCreate(&e1));
@@ -265,6 +273,7 @@ extern "C" size_t mape_extract_workspace_bytes(int32_t n, int32_t d, int32_t P, 
   const int32_t base = precision & MAPE_PREC_MASK;
   if (base == MAPE_PREC_FP32) return mape_detail::extract_fp32_workspace(n, d, P);
   if (base == MAPE_PREC_SPARSE) return mape_detail::extract_sparse_workspace(n, d, P);
+  if (base == MAPE_PREC_FP8) return mape_detail::extract_stream_workspace(n, d, P);
   // the streamed path also serves a general B of a shape whose resident tile
   // fits only when B is identity-topped, so its workspace is always included
   size_t w = mape_detail::extract_stream_workspace(n, d, P);
@@ -297,6 +306,7 @@ extern "C" int mape_extract(const mape_extract_args* a, void* stream) {
     if (a->workspace_bytes < mape_extract_workspace_bytes(a->n, a->d, a->P, a->precision)) return MAPE_ERR_CAPACITY;
     mape_extract_args b = *a;
     b.precision = base;
+    if (base == MAPE_PREC_FP8) return mape_detail::extract_stream(&b, st, mape_detail::kFwdDense);
     if (a->precision & MAPE_PREC_AUTOTUNE) {
       const size_t impl = mape_detail::align_up(mape_extract_workspace_bytes(a->n, a->d, a->P, base), 256);
       const TuneKey key{a->n, a->d, p_bucket(a->P), base};
@@ -316,11 +326,12 @@ extern "C" int mape_extract(const mape_extract_args* a, void* stream) {
       b.workspace_bytes = impl;
       return run_choice(&b, st, choice);
     }
+    if (a->precision & MAPE_PREC_SPARSE_FWD) return mape_detail::extract_stream(&b, st, mape_detail::kFwdSparse);
     if (!(a->precision & MAPE_PREC_STREAMED) && mape_detail::extract_tc_supported(a->n, a->d, base)) {
       const int rc = mape_detail::extract_tc(&b, st);
       if (rc != MAPE_ERR_SHAPE) return rc;  // SHAPE: a general B that only the streamed path takes
     }
-    return mape_detail::extract_stream(&b, st);
+    return mape_detail::extract_stream(&b, st, mape_detail::kFwdDense);
   }
   if (a->workspace_bytes < mape_detail::extract_fp32_workspace(a->n, a->d, a->P)) return MAPE_ERR_CAPACITY;
   return mape_detail::extract_fp32(a, st);

@@ -31,9 +31,13 @@ int extract_sparse(const mape_extract_args* a, cudaStream_t st);
 
 bool extract_stream_supported(int32_t n, int32_t d);
 size_t extract_stream_workspace(int32_t n, int32_t d, int32_t P);
-int extract_stream(const mape_extract_args* a, cudaStream_t st);
+// forward pass of the streamed path: the tensor-core forward, or the CUDA-core
+// sparse forward (SHAPE unless B is identity-topped, z is carried in full
+// and Bm has density at most 1/16)
+constexpr int kFwdDense = 1, kFwdSparse = 2;
+int extract_stream(const mape_extract_args* a, cudaStream_t st, int fwd_mode);
 // the same with the forward and gradient N-block widths chosen (64..256, multiples of 64)
-int extract_stream_widths(const mape_extract_args* a, cudaStream_t st, int wF, int wG);
+int extract_stream_widths(const mape_extract_args* a, cudaStream_t st, int wF, int wG, int fwd_mode);
 
 // Batches of calls on the streamed kernels: three launches per step for all
 // calls of one basis kind.

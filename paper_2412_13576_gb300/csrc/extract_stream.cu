@@ -30,6 +30,7 @@
 #include "extract_internal.cuh"
 #include "tc_ptx.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <memory>
 #include <vector>
@@ -61,6 +62,8 @@ struct StParams {
   int wF, wG;           // N block widths (multiples of 64, at most 256)
   int ldc, mapoff, lds; // candidate pitch; offset of the Bm rows in a staged row; staged pitch
   const uint8_t* BmF;   // forward B operand: [nbF][d64/64][N x 64] chunks (N = Bm rows)
+  const uint8_t* BmF8;  // the same in e4m3 (8-bit chunks, MAPE_PREC_FP8)
+  int f8;               // 1: the forward product in e4m3 (z scaled per start), D2 stays BF16
   const uint8_t* BmG;   // gradient B operand: [nbG][R64/64][N x 64] chunks (N = coordinates)
   const int32_t* span;
   float* Zt;
@@ -83,6 +86,9 @@ struct StParams {
   int32_t* flags;
   float* dbg_phi;
   float* dbg_grad;
+  const int32_t* sp_rp;   // sparse forward: CSR of Bm, row starts [R + 1]
+  const uint16_t* sp_ci;  //   column indices (coordinates)
+  const float* sp_rv;     //   values
 };
 
 __device__ __forceinline__ int ptot(const StParams& p) { return p.tiles * kTM; }
@@ -99,6 +105,20 @@ __device__ __forceinline__ bool conv_barrier_or(bool pred) {
       : "r"((uint32_t)pred), "r"(kThreads)
       : "memory");
   return r != 0;
+}
+
+// The e4m3 scale of start pg at step s: the power of two 2^(8 - e) with
+// ||z||_inf < 2^e (from the step's ||z||_inf word), so that the scaled z lies
+// within [-256, 256]; 1 for z = 0.  A power of two is exact, and the sign of
+// B (sc z) is that of B z.
+__device__ __forceinline__ float f8_scale(const StParams& p, int s, int64_t pg) {
+  const unsigned long long k = p.zkey[(int64_t)(s & 1) * ptot(p) + pg];
+  const float zinf = __uint_as_float((uint32_t)(k >> 32));
+  if (!(zinf > 0.f)) return 1.f;
+  int e;
+  frexpf(zinf, &e);
+  e = max(-100, min(100, 8 - e));
+  return ldexpf(1.f, e);
 }
 
 // blk: tile * nbF + row block of this CTA.  Warps 0-7 (the converters) turn
@@ -146,6 +166,7 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
   tc_fence_after();
   const uint32_t tmem = s_tmem;
   const uint32_t idesc = idesc_bf16(kTM, N);
+  const uint32_t idesc8 = idesc_e4m3(kTM, N);
   bool ok = s_abort == 0;
   int issued_copies = 0, issued_commits = 0;  // issuer thread
   int issued_z = 0;                           // converter thread 0
@@ -171,9 +192,20 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
   auto copy_bm = [&](int c) {
     const int stg = c & 1;
     uint8_t* Bc = smem + stg * fstage + 3 * kChunkA;
-    mbar_arrive_expect_tx(full0 + 8 * stg, (uint32_t)N * kKC * 2);
-    bulk_g2s(smem_u32(Bc), p.BmF + ((size_t)rb * p.wF * p.d64 + (size_t)c * N * kKC) * 2, (uint32_t)N * kKC * 2,
-             full0 + 8 * stg);
+    if (p.f8) {  // e4m3 chunk (N x 64 bytes) in the stage's unused lo slot; BF16 chunk only for D2
+      const bool b16 = collect != 0, b8 = fwd != 0;
+      mbar_arrive_expect_tx(full0 + 8 * stg, (uint32_t)N * kKC * ((b16 ? 2 : 0) + (b8 ? 1 : 0)));
+      if (b8)
+        bulk_g2s(smem_u32(Bc - 2 * kChunkA), p.BmF8 + (size_t)rb * p.wF * p.d64 + (size_t)c * N * kKC,
+                 (uint32_t)N * kKC, full0 + 8 * stg);
+      if (b16)
+        bulk_g2s(smem_u32(Bc), p.BmF + ((size_t)rb * p.wF * p.d64 + (size_t)c * N * kKC) * 2,
+                 (uint32_t)N * kKC * 2, full0 + 8 * stg);
+    } else {
+      mbar_arrive_expect_tx(full0 + 8 * stg, (uint32_t)N * kKC * 2);
+      bulk_g2s(smem_u32(Bc), p.BmF + ((size_t)rb * p.wF * p.d64 + (size_t)c * N * kKC) * 2, (uint32_t)N * kKC * 2,
+               full0 + 8 * stg);
+    }
     ++issued_copies;
   };
 
@@ -199,7 +231,15 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
         const float4 q0 = zs4[(2 * kc) * kTM + r], q1 = zs4[(2 * kc + 1) * kTM + r];
         const float z8[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
         const uint32_t o = chunk_off(r, kc * 8);
-        if (fwd) {
+        if (fwd && p.f8) {
+          // e4m3 of z scaled by the start's power of two (per-start scale:
+          // max |z| lands in [128, 256), inside the e4m3 range of 448)
+          const float sc = f8_scale(p, s, (int64_t)tile * kTM + r);
+          float v8[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) v8[k] = z8[k] * sc;
+          *reinterpret_cast<uint2*>(Ahi + chunk_off8(r, kc * 8)) = pack_e4m3x8(v8);
+        } else if (fwd) {
           uint32_t wh[4], wl[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
@@ -251,11 +291,18 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
         break;
       }
       tc_fence_after();
+      if (p.f8 && fwd) {  // D1 in e4m3: K = 32 per instruction, two per chunk
+        const uint32_t B8 = A0 + kChunkA;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk)
+          mma_e4m3(tmem, make_desc(A0 + kk * 256, kChunkLbo, kChunk8Sbo), make_desc(B8 + kk * 256, kChunkLbo, kChunk8Sbo),
+                   idesc8, (c | kk) ? 1u : 0u);
+      }
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         const uint64_t b = make_desc(Bc + kk * 256, kChunkLbo, kChunkSbo);
         const uint32_t a0 = (c | kk) ? 1u : 0u;
-        if (fwd) {
+        if (fwd && !p.f8) {
           mma_bf16(tmem, make_desc(A0 + kk * 256, kChunkLbo, kChunkSbo), b, idesc, a0);
           if (p.nterms > 1) mma_bf16(tmem, make_desc(A0 + kChunkA + kk * 256, kChunkLbo, kChunkSbo), b, idesc, 1u);
         }
@@ -292,6 +339,8 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
     float l1 = 0.f;
     bool out = false;
     int firstc = kNoNz;
+    // FP8: the accumulator holds B (sc z); its sign is that of B z
+    const float inv_sc = (fwd && p.f8) ? 1.f / f8_scale(p, s, pg) : 1.f;
     for (int ch = h; ch < N / 16; ch += 2) {
       uint32_t v[16];
       if (fwd) {
@@ -302,7 +351,7 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
         for (int k = 0; k < 8; ++k) {
           const float y0 = __uint_as_float(v[2 * k]), y1 = __uint_as_float(v[2 * k + 1]);
           w[k] = pack_bf16x2((float)mape_sign_f(y0), (float)mape_sign_f(y1));
-          l1 += fabsf(y0) + fabsf(y1);
+          l1 += (fabsf(y0) + fabsf(y1)) * inv_sc;
         }
         const int kg = row0 + ch * 16;  // column of S: row of Bm
         uint8_t* Sp = p.S + ((size_t)tile * (p.R64 / kKC) + kg / kKC) * kChunkA;
@@ -355,6 +404,165 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
     tc_fence_after();
     tmem_dealloc(tmem, fcols);
   }
+}
+
+// ---------------------------------------------------------------- sparse forward
+
+// The forward pass for an identity-topped B whose rows below the identity
+// (Bm) are sparse: y = Bm z over the compressed rows of Bm on the CUDA cores,
+// in FP32 from the exact FP32 z (no BF16 splitting), so a step costs about
+// nnz(Bm) fused multiply-adds per start instead of a dense R x d product and
+// is bound by reading z once.  Persistent CTAs of 512 threads hold the CSR of
+// Bm in shared memory (when it fits; else it is read through L1) and walk over
+// groups of 8 starts of a tile: the z of the next group is copied (cp.async,
+// 16-byte pieces of the blocked state) into the second of two buffers (rows of
+// d64 + 4 floats: the 8 starts of one column fall in 8 different banks) while
+// the current group is multiplied out.  Lane (r, q) of warp w forms rows
+// i = 4 w + q + 64 k of y for start r; sign(y) is staged as the 8-row group of
+// the tile in every 128 x 64 chunk of S (1 KB each) and copied out with
+// 16-byte stores.  On collection steps the same pass forms Bm round(z)
+// exactly in int32 (|round z| <= 256 and |B| <= 256 are guaranteed as on the
+// tensor-core path) and writes the staged candidate rows.  Outputs are those
+// of the tensor-core forward: S, the staged rows, the out-of-box word, the
+// debug Phi terms and the reset of the next step's per-start words.
+constexpr int kSpStarts = 8;
+constexpr int kSpThreads = 512;
+constexpr int kSpRowsPerRound = (kSpThreads / 32) * 4;
+
+__host__ __device__ constexpr int sp_ld(int d64) { return d64 + 4; }
+__host__ __device__ constexpr size_t sp_zbuf(int d64) { return (size_t)kSpStarts * sp_ld(d64) * 4; }
+__host__ __device__ constexpr size_t sp_csr_bytes(int R, int nnz) {
+  return ((size_t)(R + 1) * 4 + (size_t)nnz * 4 + (size_t)nnz * 2 + 15) / 16 * 16;
+}
+// shared memory: two z buffers, the S staging area, then the CSR (if staged)
+__host__ __device__ constexpr size_t sp_smem(int d64, int R64, size_t csr) {
+  return 2 * sp_zbuf(d64) + (size_t)(R64 / kKC) * 1024 + csr;
+}
+
+__global__ void __launch_bounds__(kSpThreads, 1) stream_fwd_sparse_kernel(StParams p, int s, int fwd, int collect,
+                                                                          int nnz, int csr_smem) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ float s_l1[kSpStarts];
+  __shared__ int s_out[kSpStarts];
+  const int tid = threadIdx.x;
+  constexpr int kGroups = kTM / kSpStarts;
+  const int ld = sp_ld(p.d64);
+  const int ng4 = p.d64 / 4;
+  const int nck = p.R64 / kKC;
+  float* zbuf0 = reinterpret_cast<float*>(smem);
+  uint8_t* ss = smem + 2 * sp_zbuf(p.d64);
+  // CSR of Bm: in shared memory when it fits, else read through L1
+  const int32_t* rp = p.sp_rp;
+  const float* rv = p.sp_rv;
+  const uint16_t* ci = p.sp_ci;
+  if (csr_smem) {  // values (16-byte aligned), column indices, row starts
+    float* s_rv = reinterpret_cast<float*>(ss + (size_t)nck * 1024);
+    uint16_t* s_ci = reinterpret_cast<uint16_t*>(s_rv + nnz);
+    int32_t* s_rp = reinterpret_cast<int32_t*>(s_ci + nnz);
+    for (int e = tid; e <= p.R; e += kSpThreads) s_rp[e] = p.sp_rp[e];
+    for (int e = tid; e < nnz; e += kSpThreads) {
+      s_rv[e] = p.sp_rv[e];
+      s_ci[e] = p.sp_ci[e];
+    }
+    rp = s_rp;
+    rv = s_rv;
+    ci = s_ci;
+  }
+  const int P2 = ptot(p);
+  const int groups = p.tiles * kGroups;
+  auto issue_z = [&](int grp, int buf) {  // the z of group grp into buffer buf (one commit group per thread)
+    if (grp < groups) {
+      const int tile = grp / kGroups, g8 = grp % kGroups;
+      const float4* zt = reinterpret_cast<const float4*>(p.Zt) + (size_t)tile * ng4 * kTM + g8 * kSpStarts;
+      const uint32_t base = smem_u32(zbuf0) + (uint32_t)(buf * sp_zbuf(p.d64));
+      for (int e = tid; e < ng4 * kSpStarts; e += kSpThreads) {
+        const int g = e / kSpStarts, r = e % kSpStarts;
+        cp_async16(base + (uint32_t)((r * ld + 4 * g) * 4), zt + (size_t)g * kTM + r);
+      }
+    }
+    cp_async_commit();
+  };
+  const int warp = tid >> 5, lane = tid & 31, r = lane & 7, q = lane >> 3;
+  int buf = 0;
+  issue_z(blockIdx.x, 0);
+  for (int grp = blockIdx.x; grp < groups; grp += gridDim.x, buf ^= 1) {
+    const int tile = grp / kGroups, g8 = grp % kGroups;
+    const int64_t pg0 = (int64_t)tile * kTM + g8 * kSpStarts;
+    if (tid < kSpStarts) {  // buffers of the next step's per-start reductions start empty
+      const int64_t nb = (int64_t)((s + 1) & 1) * P2 + pg0 + tid;
+      p.zkey[nb] = 0ull;
+      p.idw[nb] = 0u;
+      p.first[nb] = kNoNz;
+      s_l1[tid] = 0.f;
+      s_out[tid] = 0;
+    }
+    issue_z(grp + gridDim.x, buf ^ 1);  // the next group's z, while this one is multiplied out
+    cp_async_wait<1>();
+    __syncthreads();  // this group's z (every thread's copies) and the CSR are in place
+    const float* zs = zbuf0 + (size_t)buf * (sp_zbuf(p.d64) / 4);
+    const int64_t pg = pg0 + r;
+    const bool live = pg < p.P;
+    const float* zr = zs + r * ld;
+    int8_t* srow = p.stage + pg * p.lds + p.mapoff;
+    float l1 = 0.f;
+    bool out = false;
+    for (int i = warp * 4 + q; i < p.R64; i += kSpRowsPerRound) {
+      float acc0 = 0.f, acc1 = 0.f;
+      int g2 = 0;
+      if (i < p.R) {
+        // rows hold multiples of 4 entries (zero padded): 4 column indices
+        // and 4 values per pair of vector loads, 4 independent gathers of z
+        float acc2 = 0.f, acc3 = 0.f;
+        for (int e = rp[i], e1 = rp[i + 1]; e < e1; e += 4) {
+          const uint2 c4 = *reinterpret_cast<const uint2*>(ci + e);
+          const float4 v4 = *reinterpret_cast<const float4*>(rv + e);
+          const float z0 = zr[c4.x & 0xffff], z1 = zr[c4.x >> 16], z2 = zr[c4.y & 0xffff], z3 = zr[c4.y >> 16];
+          acc0 = fmaf(v4.x, z0, acc0);
+          acc1 = fmaf(v4.y, z1, acc1);
+          acc2 = fmaf(v4.z, z2, acc2);
+          acc3 = fmaf(v4.w, z3, acc3);
+          if (collect)
+            g2 += (int)v4.x * (int)rintf(z0) + (int)v4.y * (int)rintf(z1) + (int)v4.z * (int)rintf(z2) +
+                  (int)v4.w * (int)rintf(z3);
+        }
+        acc0 += acc2;
+        acc1 += acc3;
+      }
+      const float acc = acc0 + acc1;
+      if (fwd) {
+        const uint16_t sb = acc > 0.f ? (uint16_t)0x3F80 : (acc < 0.f ? (uint16_t)0xBF80 : (uint16_t)0);
+        *reinterpret_cast<uint16_t*>(ss + (i >> 6) * 1024 + ((i & 63) >> 3) * 128 + r * 16 + (i & 7) * 2) = sb;
+        l1 += fabsf(acc);
+      }
+      if (collect && i < p.R) {
+        const int sp = p.span[p.r0 + i];
+        if (g2 > sp || -g2 > sp) out = true;
+        if (live) srow[i] = (int8_t)(g2 & 0xff);
+      }
+    }
+    if (fwd && s == 0 && p.dbg_phi) atomicAdd(&s_l1[r], l1);
+    if (out) s_out[r] = 1;
+    if (collect) {  // identity rows of the staged candidates: round(z) itself
+      for (int e = tid; e < kSpStarts * p.d; e += kSpThreads) {
+        const int rr = e / p.d, j = e % p.d;
+        if (pg0 + rr < p.P) p.stage[(pg0 + rr) * p.lds + j] = (int8_t)((int)rintf(zs[rr * ld + j]) & 0xff);
+      }
+    }
+    __syncthreads();  // S staged; this z buffer is free for the group after next
+    if (fwd) {
+      for (int e = tid; e < nck * 64; e += kSpThreads) {
+        const int c = e >> 6, k = e & 63;
+        const uint4 v = reinterpret_cast<const uint4*>(ss + c * 1024)[k];
+        reinterpret_cast<uint4*>(p.S + ((size_t)tile * nck + c) * kChunkA + g8 * 1024)[k] = v;
+      }
+    }
+    if (tid < kSpStarts && pg0 + tid < p.P) {
+      if (collect && s_out[tid]) atomicOr(&p.oob[pg0 + tid], 1u);
+      if (fwd && s == 0 && p.dbg_phi) atomicAdd(&p.dbg_phi[pg0 + tid], s_l1[tid]);
+    }
+    __syncthreads();  // the S staging area and the per-start words are free for the next group
+  }
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------- collect
@@ -650,12 +858,21 @@ __global__ void __launch_bounds__(kThreads, 1) stream_grad_batch_kernel(const St
 // exact in BF16 (|B_ij| > 256)
 __global__ void pack_bm_kernel(const int32_t* __restrict__ B, int d, int R, int r0, int d64, int R64, int nbF,
                                int nbG, int wF, int wG, uint8_t* __restrict__ BmF, uint8_t* __restrict__ BmG,
-                               int32_t* bad, int32_t* flags) {
+                               uint8_t* __restrict__ BmF8, int f8, int32_t* bad, int32_t* flags) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= (int64_t)R64 * d64) return;
   const int i = (int)(e / d64), j = (int)(e % d64);
   const int v = (i < R && j < d) ? B[(int64_t)(r0 + i) * d + j] : 0;
-  if (v > 256 || v < -256) {
+  bool inexact = v > 256 || v < -256;
+  if (f8) {  // the e4m3 copy of the forward operand; its entries must be exact too
+    const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8((float)v, __NV_SATFINITE, __NV_E4M3);
+    const __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
+    if (__half2float(*reinterpret_cast<const __half*>(&hr)) != (float)v) inexact = true;
+    const int rb = i / wF, rl = i % wF;
+    const int Nr = rb < nbF - 1 ? wF : R64 - wF * (nbF - 1);
+    BmF8[(size_t)rb * wF * d64 + (size_t)(j / kKC) * Nr * kKC + chunk_off8(rl, j % kKC)] = (uint8_t)q;
+  }
+  if (inexact) {
     atomicOr(bad, 1);
     atomicOr(flags, 8);
   }
@@ -761,6 +978,66 @@ __global__ void stream_identity_top_kernel(const int32_t* __restrict__ B, int d,
   if (B[(int64_t)i * d + j] != (i == j ? 1 : 0)) atomicOr(flag, 1);
 }
 
+// compressed rows of Bm (rows r0 .. r0 + R - 1 of B): nonzeros per row (one
+// warp per row) rounded up to a multiple of 4, their exclusive prefix (one
+// block), the entries in column order followed by zero entries
+__global__ void bm_count_kernel(const int32_t* __restrict__ B, int d, int R, int r0, int32_t* __restrict__ cnt) {
+  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (i >= R) return;
+  int c = 0;
+  for (int j = lane; j < d; j += 32) c += B[(int64_t)(r0 + i) * d + j] != 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) cnt[i] = (c + 3) & ~3;  // rows padded to 4 entries: vector loads of the sparse forward
+}
+
+__global__ void bm_scan_kernel(const int32_t* __restrict__ cnt, int R, int32_t* __restrict__ rp) {
+  __shared__ int32_t s_part[1024];
+  const int t = threadIdx.x, per = (R + 1023) / 1024;
+  const int a = t * per, b = min(a + per, R);
+  int32_t sum = 0;
+  for (int i = a; i < b; ++i) sum += cnt[i];
+  s_part[t] = sum;
+  __syncthreads();
+  if (t == 0) {
+    int32_t run = 0;
+    for (int k = 0; k < 1024; ++k) {
+      const int32_t v = s_part[k];
+      s_part[k] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  int32_t run = s_part[t];
+  for (int i = a; i < b; ++i) {
+    rp[i] = run;
+    run += cnt[i];
+  }
+  if (b == R && a < b) rp[R] = run;
+  if (R == 0 && t == 0) rp[0] = 0;
+}
+
+__global__ void bm_fill_kernel(const int32_t* __restrict__ B, int d, int R, int r0, const int32_t* __restrict__ rp,
+                               uint16_t* __restrict__ ci, float* __restrict__ rv) {
+  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (i >= R) return;
+  int pos = rp[i];
+  for (int j0 = 0; j0 < d; j0 += 32) {
+    const int j = j0 + lane;
+    const int v = j < d ? B[(int64_t)(r0 + i) * d + j] : 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, v != 0);
+    if (v != 0) {
+      const int at = pos + __popc(bal & ((1u << lane) - 1));
+      ci[at] = (uint16_t)j;
+      rv[at] = (float)v;
+    }
+    pos += __popc(bal);
+  }
+  for (int e = pos + lane; e < rp[i + 1]; e += 32) {  // the row's padding: column 0, value 0
+    ci[e] = 0;
+    rv[e] = 0.f;
+  }
+}
+
 int r64(int x) { return (x + kKC - 1) / kKC * kKC; }
 int r16(int x) { return (x + 15) / 16 * 16; }
 
@@ -795,6 +1072,10 @@ StreamShape stream_bound(int n, int d, int P) {
 
 constexpr int32_t kBiasSteps = 1 << 20;  // bias-correction table: up to 2^20 steps per call
 
+// The sparse forward is used while nnz(Bm) <= R d / 16 (density at most 1/16).
+constexpr int kSparseDensityInv = 16;
+size_t sp_capacity(const StreamShape& sh) { return (size_t)sh.R64 * sh.d64 / kSparseDensityInv + 4 * (size_t)sh.R64 + 1; }
+
 template <typename Carve>
 void carve_stream(Carve& cv, const StreamShape& sh) {
   const size_t P2 = (size_t)sh.tiles * kTM;
@@ -804,6 +1085,7 @@ void carve_stream(Carve& cv, const StreamShape& sh) {
   cv.template take<int8_t>(P2 * sh.lds);                  // staged rows
   cv.template take<uint8_t>((size_t)sh.R64 * sh.d64 * 2); // BmF
   cv.template take<uint8_t>((size_t)sh.R64 * sh.d64 * 2); // BmG
+  cv.template take<uint8_t>((size_t)sh.R64 * sh.d64);     // BmF8
   cv.template take<unsigned long long>(2 * P2);           // zkey
   cv.template take<uint32_t>(P2);                         // acc
   cv.template take<uint32_t>(P2);                         // oob
@@ -812,6 +1094,10 @@ void carve_stream(Carve& cv, const StreamShape& sh) {
   cv.template take<int32_t>(P2);                          // first_map
   cv.template take<float2>((size_t)kBiasSteps);           // bias table
   cv.template take<int32_t>(2);                           // identity flag, inexact flag
+  cv.template take<int32_t>((size_t)sh.R64 + 1);          // sparse forward: nonzeros per row of Bm
+  cv.template take<int32_t>((size_t)sh.R64 + 1);          //   row starts
+  cv.template take<uint16_t>(sp_capacity(sh));            //   column indices
+  cv.template take<float>(sp_capacity(sh));               //   values
 }
 
 }  // namespace
@@ -833,12 +1119,15 @@ size_t extract_stream_workspace(int32_t n, int32_t d, int32_t P) {
 struct StCarved {
   StreamShape sh;
   float *Zt, *Mt, *Vt;
-  uint8_t *S, *BmF, *BmG;
+  uint8_t *S, *BmF, *BmG, *BmF8;
   int8_t* stage;
   unsigned long long* zkey;
   uint32_t *acc, *oob, *idw;
   int32_t *first, *first_map, *hflags;
   float2* bias;
+  int32_t *sp_cnt, *sp_rp;
+  uint16_t* sp_ci;
+  float* sp_rv;
 };
 
 static int st_carve(const mape_extract_args* a, bool id, StCarved& c) {
@@ -854,6 +1143,7 @@ static int st_carve(const mape_extract_args* a, bool id, StCarved& c) {
   c.stage = cv.take<int8_t>(P2 * gen.lds);
   c.BmF = cv.take<uint8_t>((size_t)gen.R64 * gen.d64 * 2);
   c.BmG = cv.take<uint8_t>((size_t)gen.R64 * gen.d64 * 2);
+  c.BmF8 = cv.take<uint8_t>((size_t)gen.R64 * gen.d64);
   c.zkey = cv.take<unsigned long long>(2 * P2);
   c.acc = cv.take<uint32_t>(P2);
   c.oob = cv.take<uint32_t>(P2);
@@ -862,6 +1152,10 @@ static int st_carve(const mape_extract_args* a, bool id, StCarved& c) {
   c.first_map = cv.take<int32_t>(P2);
   c.bias = cv.take<float2>((size_t)kBiasSteps);
   c.hflags = cv.take<int32_t>(2);
+  c.sp_cnt = cv.take<int32_t>((size_t)gen.R64 + 1);
+  c.sp_rp = cv.take<int32_t>((size_t)gen.R64 + 1);
+  c.sp_ci = cv.take<uint16_t>(sp_capacity(gen));
+  c.sp_rv = cv.take<float>(sp_capacity(gen));
   if (!cv.ok) return MAPE_ERR_CAPACITY;
   c.sh = stream_shape(n, d, P, id);
   return MAPE_OK;
@@ -871,8 +1165,9 @@ static int st_carve(const mape_extract_args* a, bool id, StCarved& c) {
 static int st_pack_b(const StCarved& c, const mape_extract_args* a, cudaStream_t st) {
   const StreamShape& sh = c.sh;
   MAPE_CUDA_TRY(cudaMemsetAsync(c.hflags + 1, 0, sizeof(int32_t), st));
+  const int f8 = (a->precision & MAPE_PREC_MASK) == MAPE_PREC_FP8 ? 1 : 0;
   launch(pack_bm_kernel, (unsigned)ceil_div((int64_t)sh.R64 * sh.d64, 256), 256, 0, st, a->B, a->d, sh.R, sh.r0,
-         sh.d64, sh.R64, sh.nbF, sh.nbG, sh.wF, sh.wG, c.BmF, c.BmG, c.hflags + 1, a->flags);
+         sh.d64, sh.R64, sh.nbF, sh.nbG, sh.wF, sh.wG, c.BmF, c.BmG, c.BmF8, f8, c.hflags + 1, a->flags);
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
 }
@@ -905,7 +1200,9 @@ static int st_setup(const StCarved& c, const mape_extract_args* a, cudaStream_t 
   p.lambda1 = a->lambda1; p.lambda2 = a->lambda2; p.eps = a->eps;
   p.beta1 = (float)a->beta1; p.beta2 = (float)a->beta2;
   p.omb1 = (float)(1.0 - a->beta1); p.omb2 = (float)(1.0 - a->beta2);
-  p.nterms = a->precision == MAPE_PREC_BF16X1 ? 1 : 2;
+  p.nterms = (a->precision & MAPE_PREC_MASK) == MAPE_PREC_BF16 ? 2 : 1;
+  p.f8 = (a->precision & MAPE_PREC_MASK) == MAPE_PREC_FP8 ? 1 : 0;
+  p.BmF8 = c.BmF8;
   p.cand = a->cand; p.cap = a->cand_cap; p.count = a->cand_count; p.flags = a->flags;
   p.dbg_phi = a->dbg_phi; p.dbg_grad = a->dbg_grad;
   launch(stream_init_kernel, (unsigned)ceil_div((int64_t)P2, 256), 256, 0, st, p);
@@ -955,7 +1252,7 @@ static void st_schedule(int t0, int T, int period, Fwd fwd, Coll coll, Grad grad
   }
 }
 
-int extract_stream_widths(const mape_extract_args* a, cudaStream_t st, int wF, int wG) {
+int extract_stream_widths(const mape_extract_args* a, cudaStream_t st, int wF, int wG, int fwd_mode) {
   const int d = a->d, P = a->P;
   if (wF < kKC || wF > kNB || wF % kKC || wG < kKC || wG > kNB || wG % kKC) return MAPE_ERR_INVALID_ARG;
   StCarved c;
@@ -970,10 +1267,26 @@ int extract_stream_widths(const mape_extract_args* a, cudaStream_t st, int wF, i
   const bool id = h_notid == 0;
   c.sh = stream_shape(a->n, d, P, id, wF, wG);
   if ((rc = st_pack_b(c, a, st)) != MAPE_OK) return rc;
-  int32_t h_bad = 0;
+  // the sparse forward: asked for, an identity-topped B, z carried in full
+  // (not the one-term BF16 precision), and Bm at density at most 1/16
+  if (fwd_mode == kFwdSparse && (!id || (a->precision & MAPE_PREC_MASK) != MAPE_PREC_BF16)) return MAPE_ERR_SHAPE;
+  const bool want_sparse = fwd_mode == kFwdSparse;
+  if (want_sparse) {
+    const unsigned gw = (unsigned)ceil_div((int64_t)c.sh.R * 32, 256);
+    launch(bm_count_kernel, gw, 256, 0, st, a->B, d, c.sh.R, c.sh.r0, c.sp_cnt);
+    launch(bm_scan_kernel, 1, 1024, 0, st, c.sp_cnt, c.sh.R, c.sp_rp);
+    MAPE_LAUNCH_CHECK();
+  }
+  int32_t h_bad = 0, h_nnz = 0;
   MAPE_CUDA_TRY(cudaMemcpyAsync(&h_bad, c.hflags + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (want_sparse) MAPE_CUDA_TRY(cudaMemcpyAsync(&h_nnz, c.sp_rp + c.sh.R, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   MAPE_CUDA_TRY(cudaStreamSynchronize(st));
   if (h_bad) return MAPE_OK;  // flag 8 is set; nothing runs, nothing is collected
+  // h_nnz counts the rows' padding to multiples of 4 (at most 3 per row)
+  const int64_t nnz_lo = std::max<int64_t>(0, (int64_t)h_nnz - 3 * (int64_t)c.sh.R);
+  const bool sparse = want_sparse && (size_t)h_nnz <= sp_capacity(c.sh) &&
+                      nnz_lo * kSparseDensityInv <= (int64_t)c.sh.R * d;
+  if (want_sparse && !sparse) return MAPE_ERR_SHAPE;
   StParams p;
   if ((rc = st_setup(c, a, st, p)) != MAPE_OK) return rc;
   if ((rc = st_attributes(false)) != MAPE_OK) return rc;
@@ -984,10 +1297,33 @@ int extract_stream_widths(const mape_extract_args* a, cudaStream_t st, int wF, i
   auto gradk = id ? stream_grad_kernel<true> : stream_grad_kernel<false>;
   auto collk = id ? stream_collect_kernel<true> : stream_collect_kernel<false>;
   const int fsm = fwd_smem(sh.wF), gsm = 2 * grad_stage(sh.wG);
+  // sparse forward: persistent CTAs, one per SM; the CSR joins their shared
+  // memory when the total stays within 200 KB
+  int dev = 0, nsm = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int groups = sh.tiles * (kTM / kSpStarts);
+  const unsigned gS = (unsigned)std::min(groups, nsm);
+  const size_t csr = sp_csr_bytes(sh.R, h_nnz);
+  const int csr_in_smem = sp_smem(sh.d64, sh.R64, csr) <= (size_t)200 * 1024 ? 1 : 0;
+  const size_t ssm = sp_smem(sh.d64, sh.R64, csr_in_smem ? csr : 0);
+  if (sparse) {
+    if (ssm > (size_t)227 * 1024) return MAPE_ERR_SHAPE;
+    const unsigned gw = (unsigned)ceil_div((int64_t)sh.R * 32, 256);
+    launch(bm_fill_kernel, gw, 256, 0, st, a->B, d, sh.R, sh.r0, c.sp_rp, c.sp_ci, c.sp_rv);
+    MAPE_CUDA_TRY(cudaFuncSetAttribute(stream_fwd_sparse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+    p.sp_rp = c.sp_rp;
+    p.sp_ci = c.sp_ci;
+    p.sp_rv = c.sp_rv;
+  }
   st_schedule(
       a->t0, a->T, a->period,
       [&](int s, int f, int col) {
-        timed_launch(MAPE_TIMED_STREAM_FWD, st, [&] { launch(fwdk, gF, kThreadsF, fsm, st, p, s, f, col); });
+        if (sparse)
+          timed_launch(MAPE_TIMED_STREAM_FWD, st, [&] {
+            launch(stream_fwd_sparse_kernel, gS, kSpThreads, ssm, st, p, s, f, col, h_nnz, csr_in_smem);
+          });
+        else
+          timed_launch(MAPE_TIMED_STREAM_FWD, st, [&] { launch(fwdk, gF, kThreadsF, fsm, st, p, s, f, col); });
       },
       [&](int s) { timed_launch(MAPE_TIMED_STREAM_COLLECT, st, [&] { launch(collk, gC, 256, 0, st, p, s); }); },
       [&](int s) { timed_launch(MAPE_TIMED_STREAM_GRAD, st, [&] { launch(gradk, gG, kThreads, gsm, st, p, s); }); });
@@ -995,7 +1331,9 @@ int extract_stream_widths(const mape_extract_args* a, cudaStream_t st, int wF, i
   return st_unpack(c, a, st);
 }
 
-int extract_stream(const mape_extract_args* a, cudaStream_t st) { return extract_stream_widths(a, st, kNB, kNB); }
+int extract_stream(const mape_extract_args* a, cudaStream_t st, int fwd_mode) {
+  return extract_stream_widths(a, st, kNB, kNB, fwd_mode);
+}
 
 struct StBatch {
   struct Class {  // the calls of one basis kind (identity-topped or general)

@@ -11,6 +11,7 @@
 
 #include <cstdint>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 namespace mape_tc {
 
@@ -40,6 +41,36 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
+
+// kind::f8f6f4 instruction descriptor: D f32, A and B e4m3, both K-major
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D (+)= A B^T with e4m3 operands, K = 32 per instruction
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// 8 floats to 8 e4m3 bytes (round to nearest even, saturating to +-448)
+__device__ __forceinline__ uint2 pack_e4m3x8(const float (&v)[8]) {
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    w[k] = (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(v[2 * k], v[2 * k + 1]), __NV_SATFINITE, __NV_E4M3);
+  return make_uint2(w[0] | (w[1] << 16), w[2] | (w[3] << 16));
+}
+
+// byte offset of 8-bit element (row r, column k) in a K = 64 chunk: core
+// matrices of 8 rows x 16 bytes, 4 of them along K (LBO 128), 8-row groups
+// 512 bytes apart (SBO)
+__host__ __device__ __forceinline__ uint32_t chunk_off8(int r, int k) {
+  return (uint32_t)((((r >> 3) * 4 + (k >> 4)) << 7) + ((r & 7) << 4) + (k & 15));
+}
+constexpr uint32_t kChunk8Sbo = 512;
 
 // arrives on the mbarrier once every tcgen05 operation issued so far by this
 // thread has completed
@@ -170,6 +201,15 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
+
+// per-thread asynchronous 16-byte copy global -> shared (L2 only), and its
+// commit / wait-for-all-but-N-groups
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // byte offset of BF16 element (row r, column k) in a K = 64 chunk
 __host__ __device__ __forceinline__ uint32_t chunk_off(int r, int k) {

@@ -24,8 +24,10 @@ PREC_FP32 = 0
 PREC_BF16 = 1
 PREC_BF16X1 = 2
 PREC_SPARSE = 3
+PREC_FP8 = 4
 PREC_STREAMED = 0x100   # OR into a BF16 precision: force the streamed tensor-core kernels
 PREC_AUTOTUNE = 0x200   # OR into a BF16 precision: choose the implementation and tile widths by timing
+PREC_SPARSE_FWD = 0x400  # OR into MAPE_PREC_BF16: the CUDA-core sparse forward product on the streamed path
 PHASES = ["IDLE", "EXTRACTING", "FILTERING", "AUGMENTING", "DONE", "ERROR"]
 
 
@@ -82,9 +84,10 @@ class TuneInfo(C.Structure):
 
     def as_dict(self):
         k = self.candidates
-        return {"path": ("resident", "streamed")[self.path], "wF": self.wF, "wG": self.wG,
+        names = ("resident", "streamed", "streamed_sparse_forward")
+        return {"path": names[self.path], "wF": self.wF, "wG": self.wG,
                 "probe_steps": self.probe_steps,
-                "candidates": [{"path": ("resident", "streamed")[self.cand_path[i]], "wF": self.cand_wF[i],
+                "candidates": [{"path": names[self.cand_path[i]], "wF": self.cand_wF[i],
                                 "wG": self.cand_wG[i], "ms": self.probe_ms[i]} for i in range(k)]}
 
 
@@ -193,6 +196,7 @@ _SIGS = {
     "mape_server_get_stats": (C.c_int, [P_, C.POINTER(ServerStats)]),
     "mape_server_destroy": (None, [P_]),
     "mape_launch_timing": (C.c_int, [I32]),
+    "mape_mma_issue_probe": (C.c_int, [I32, I32, I32, I32, I32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mape_launch_timing_read": (C.c_int, [C.POINTER(C.c_double), C.POINTER(I64)]),
 }
 
@@ -735,6 +739,16 @@ def launch_timing_read() -> dict:
     cnt = (I64 * len(TIMED_KINDS))()
     _check(lib().mape_launch_timing_read(ms, cnt), "mape_launch_timing_read")
     return {k: (ms[i], cnt[i]) for i, k in enumerate(TIMED_KINDS)}
+
+
+def mma_issue_probe(kind, M, N, accumulators=1, chain=512):
+    """SM cycles per tcgen05.mma instruction (issue, issue + completion) for a
+    chain of `chain` instructions (mape_mma_issue_probe; kind 0 BF16 K = 16,
+    kind 1 e4m3 K = 32)."""
+    a, b = C.c_double(0), C.c_double(0)
+    _check(lib().mape_mma_issue_probe(kind, M, N, accumulators, chain, C.byref(a), C.byref(b)),
+           "mape_mma_issue_probe")
+    return a.value, b.value
 
 
 def trim_memory():

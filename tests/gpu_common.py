@@ -41,16 +41,31 @@ def per_start_rel(a, b, floor=1e-30):
     return num / den
 
 
-def forward_error_bound(B, Z, bits):
+def forward_error_bound(B, Z, bits, abs_err=None):
     """[P x n] bound on |fl(B z)_i - (B z)_i| for z carried to `bits`
-    significant bits and d products summed in FP32, with 1% slack."""
+    significant bits and d products summed in FP32, with 1% slack.
+    abs_err [P], if given, is an absolute error per element of z on top of the
+    relative one (the subnormal range of a narrow format)."""
     Bf = np.abs(np.asarray(B, np.float64))
     Zf = np.abs(np.asarray(Z, np.float64))
     d = Bf.shape[1]
-    return (2.0 ** -bits + d * 2.0 ** -23) * (Zf @ Bf.T) * 1.01 + 1e-6
+    bound = (2.0 ** -bits + d * 2.0 ** -23) * (Zf @ Bf.T) * 1.01 + 1e-6
+    if abs_err is not None:
+        bound += np.asarray(abs_err, np.float64)[:, None] * Bf.sum(axis=1)[None, :] * 1.01
+    return bound
 
 
-def check_phi_grad(B, Z, phi, grad, bits, tol=1e-5, lam1=0.85, lam2=1.0):
+def e4m3_abs_err(Z):
+    """Per start, the absolute error of an element of z in the FP8 forward
+    product beyond the relative 2^-4: half the e4m3 subnormal step (2^-10) in
+    units of z, whose per-start scale is 2^(8 - e) with max |z| < 2^e."""
+    zinf = np.abs(np.asarray(Z, np.float64)).max(axis=1)
+    e = np.where(zinf > 0, np.frexp(np.where(zinf > 0, zinf, 1.0))[1], 0)
+    scale = np.where(zinf > 0, np.ldexp(1.0, np.clip(8 - e, -100, 100)), 1.0)
+    return 2.0 ** -10 / scale
+
+
+def check_phi_grad(B, Z, phi, grad, bits, tol=1e-5, lam1=0.85, lam2=1.0, abs_err=None):
     """Checks the kernel's Phi [P] and gradient [P x d] at the points Z against
     the FP64 oracle, start by start, under the rules in this module's
     docstring.  Returns statistics: the share of starts with an ambiguous row,
@@ -62,7 +77,7 @@ def check_phi_grad(B, Z, phi, grad, bits, tol=1e-5, lam1=0.85, lam2=1.0):
     grad = np.asarray(grad, np.float64)
     phi = np.asarray(phi, np.float64)
     Y = Zf @ Bf.T
-    eb = forward_error_bound(B, Z, bits)
+    eb = forward_error_bound(B, Z, bits, abs_err)
     amb = np.abs(Y) <= eb
     go = O.phi_grad(B, Zf, lam1, lam2)
     po = O.phi(B, Zf, lam1, lam2)
@@ -102,7 +117,7 @@ def rows_set(G, n):
     return {tuple(int(v) for v in r[:n]) for r in G}
 
 
-def check_steps(inst, states, grads, phis, bits, tol=1e-5):
+def check_steps(inst, states, grads, phis, bits, tol=1e-5, fp8=False):
     """Per-step parity of a run of single steps (states[t] = ((z, m, v) before,
     (z, m, v) after), grads/phis the kernel's debug outputs at the input
     point): Phi and gradient by check_phi_grad, Adam by check_adam, and the
@@ -113,7 +128,7 @@ def check_steps(inst, states, grads, phis, bits, tol=1e-5):
     expect = set()
     shares, rows, worst = [], [], 0.0
     for t, ((z, m, v), (z1, m1, v1)) in enumerate(states):
-        st = check_phi_grad(inst.B, z, phis[t], grads[t], bits, tol)
+        st = check_phi_grad(inst.B, z, phis[t], grads[t], bits, tol, abs_err=e4m3_abs_err(z) if fp8 else None)
         check_adam(z, m, v, grads[t], t + 1, z1, m1, v1, tol)
         shares.append(st["ambiguous_share"])
         rows.append(st["ambiguous_rows_per_start"])

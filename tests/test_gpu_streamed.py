@@ -102,18 +102,94 @@ def test_streamed_per_step(M, make, P, T, force, std, precision):
     assert rows_set(cand, inst.n) == expect
 
 
-@pytest.mark.parametrize("make,P,T,period,force,std", [(uneven500, 300, 12, 1, False, 0.3),
-                                                       (I.medium_sparse, 1000, 10, 3, True, None),
-                                                       (_general_basis(I.small_dense), 300, 15, 1, True, None)])
-def test_streamed_one_call_equals_single_steps(M, make, P, T, period, force, std):
+# the forward product of the streamed path: the tensor-core one (default) or
+# the CUDA-core sparse one (MAPE_PREC_SPARSE_FWD), which takes the
+# identity-topped bases of density <= 1/16 (large_quartic at 0.01, uneven1000
+# at 0.05)
+SPARSE_FWD = 0x400
+
+
+@pytest.mark.parametrize("fwd", [0, SPARSE_FWD])
+@pytest.mark.parametrize("make,P,T,std", [(I.large_quartic, 256, 3, 0.3), (uneven1000, 200, 4, 0.3),
+                                          (uneven1000, 130, 2, None)])
+def test_streamed_sparse_and_dense_forward_per_step(M, make, P, T, std, fwd):
+    """Both forward products on the bases the sparse one takes, per start and
+    step (tests/gpu_common.py); the sparse forward carries z in FP32 (24
+    bits), so its bound is the FP32 one."""
+    inst = make()
+    Z0 = _z0(inst, P, 2013, std)
+    ldc = M.round16(inst.n)
+    bits = 24 if fwd else 16
+    states, grads, phis, cand = _extract_steps(M, inst, Z0, T, M.PREC_BF16 | STREAMED | fwd, ldc,
+                                               cap=P * (T + 1) + 16)
+    expect, share, rows, worst = check_steps(inst, states, grads, phis, bits, FP32_TOL)
+    report(f"streamed_forward/{make.__name__}/{std}/{'sparse' if fwd else 'tensor'}", ambiguous_share=share,
+           ambiguous_rows=rows, max_rel_grad_determined=worst)
+    # observed on GB300, rounded up
+    assert share <= {(True, 0.3): 0.3, (False, 0.3): 0.3, (True, None): 0.65, (False, None): 0.7}[(bool(fwd), std)]
+    assert rows_set(cand, inst.n) == expect
+
+
+FP8 = 4
+
+
+@pytest.mark.parametrize("make,P,T,std", [(I.large_quartic, 256, 3, 0.3), (I.large_quartic, 256, 2, None),
+                                          (uneven1000, 200, 4, 0.3), (I.medium_sparse, 300, 5, None),
+                                          (I.small_dense, 256, 20, None)])
+def test_fp8_forward_per_step(M, make, P, T, std):
+    """MAPE_PREC_FP8: the forward product with z in e4m3 (per-start power-of-two
+    scale) against the FP64 oracle, per start and step: z carries 4
+    significant bits (relative 2^-4, plus half the e4m3 subnormal step in
+    units of the start's scale), so most starts have rows whose sign is not
+    fixed; those are held to the allowance of 2 |B_ij| per row; the gradient
+    product, Adam and the exact B round(z) map are those of the BF16 path
+    (candidates bit-exact)."""
+    inst = make()
+    Z0 = _z0(inst, P, 2017, std)
+    ldc = M.round16(inst.n)
+    states, grads, phis, cand = _extract_steps(M, inst, Z0, T, FP8, ldc, cap=P * (T + 1) + 16)
+    expect, share, rows, worst = check_steps(inst, states, grads, phis, 4, FP32_TOL, fp8=True)
+    report(f"fp8_per_step/{make.__name__}/{std}", ambiguous_share=share, ambiguous_rows=rows,
+           max_rel_grad_determined=worst)
+    assert rows_set(cand, inst.n) == expect
+
+
+def test_fp8_rejects_basis_not_exact_in_e4m3(M):
+    """An entry of B that e4m3 cannot hold (17) raises flag 8; nothing runs."""
+    import torch
+    inst = uneven1000()
+    Bb = inst.B.copy()
+    Bb[-1, 5] = 17
+    Z = dev(_z0(inst, 128, 1, 0.3))
+    cand = torch.zeros((1024, M.round16(inst.n)), dtype=torch.int8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    Z1 = Z.clone()
+    M.extract(dev(Bb), dev((inst.u - inst.l).astype(np.int32)), Z1, torch.zeros_like(Z), torch.zeros_like(Z),
+              t0=0, T=3, cfg=M.default_config(precision=FP8), cand=cand, cand_count=cnt, flags=flags,
+              ldc=M.round16(inst.n))
+    torch.cuda.synchronize()
+    assert int(flags.item()) & 8
+    assert int(cnt.item()) == 0 and torch.equal(Z1, Z)
+
+
+@pytest.mark.parametrize("make,P,T,period,force,std,fwd", [(uneven500, 300, 12, 1, False, 0.3, 0),
+                                                           (I.medium_sparse, 1000, 10, 3, True, None, 0),
+                                                           (_general_basis(I.small_dense), 300, 15, 1, True, None, 0),
+                                                           (uneven1000, 300, 12, 2, False, 0.3, 0),
+                                                           (uneven1000, 300, 12, 2, False, 0.3, SPARSE_FWD),
+                                                           (uneven1000, 300, 12, 2, False, 0.3, "fp8")])
+def test_streamed_one_call_equals_single_steps(M, make, P, T, period, force, std, fwd):
     """T steps in one call give bitwise the same Z, M, V as T calls of one
-    step, and the same set of collected directions."""
+    step, and the same set of collected directions (uneven1000: with the
+    tensor-core, the sparse and the FP8 forward)."""
     import torch
     inst = make()
     Z0 = _z0(inst, P, 7, std)
     ldc = M.round16(inst.n)
     B, span = dev(inst.B), dev((inst.u - inst.l).astype(np.int32))
-    prec = M.PREC_BF16 | (STREAMED if force else 0)
+    # fwd: 0 or SPARSE_FWD with MAPE_PREC_BF16, or "fp8" for MAPE_PREC_FP8
+    prec = (FP8 if fwd == "fp8" else M.PREC_BF16 | fwd) | (STREAMED if force else 0)
     results = []
     for single in (False, True):
         cfg = M.default_config(precision=prec, period=period)
