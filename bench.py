@@ -63,22 +63,29 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["bf16", "bf16x1", "fp32", "sparse"], default="bf16")
+    ap.add_argument("--precision", choices=["bf16", "bf16x1", "fp32", "sparse", "fp8"], default="bf16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run (medium workload)")
     ap.add_argument("--no-medium", action="store_true", help="skip the medium-workload measurement")
     ap.add_argument("--streamed-case", nargs=3, metavar=("NAME", "P", "T"),
                     help="time the streamed tensor-core extraction on a named instance (large: n=2000 m=400; "
                          "uneven1000: n=1000 m=200; medium: n=200 m=40) for P starts and T steps, and exit")
-    ap.add_argument("--serve", type=int, default=24, metavar="N",
+    ap.add_argument("--serve", type=int, default=2000, metavar="N",
                     help="requests in the serving measurement (Poisson stream at 200/s, n log-uniform in "
                          "[30, 3000], m = n/5, P = 4096); 0 skips it")
+    ap.add_argument("--serve-plain", type=int, default=24, metavar="N",
+                    help="the plain FP32 one-at-a-time comparison runs the first N requests of the stream")
     ap.add_argument("--serve-T", type=int, default=1000, help="Adam steps per request in the serving measurement")
     ap.add_argument("--batch", type=int, default=64, metavar="N",
                     help="instances in the batched-extraction measurement (n log-uniform in [50, 1000], m = n/5, "
                          "P in {1024, 4096, 16384}, T = 1000); 0 skips it")
+    ap.add_argument("--sparse-fwd", action="store_true",
+                    help="the large workload's forward product on the CUDA cores over the compressed rows of B "
+                         "(MAPE_PREC_SPARSE_FWD) instead of the tensor cores")
     ap.add_argument("--autotune", action="store_true",
                     help="with --streamed-case: let the library choose the implementation and tile widths")
+    ap.add_argument("--probe-mma", action="store_true",
+                    help="measure the issue cost of tcgen05.mma over M, N and operand kind, and exit")
     ap.add_argument("--kernel-case", type=int, nargs=2, metavar=("P", "T"),
                     help="time the fused extraction kernel alone on P starts of the workload for T steps "
                          "(two launches; a small case for profilers) and exit")
@@ -257,7 +264,7 @@ def cpu_baseline_obj(r, wl):
 
 # ---------------------------------------------------------------- our arm
 
-PREC = {"bf16": 1, "bf16x1": 2, "fp32": 0, "sparse": 3}
+PREC = {"bf16": 1, "bf16x1": 2, "fp32": 0, "sparse": 3, "fp8": 4}
 
 
 def handle_passes(mape, wl, inst, starts, stream, steps, warmup, prec, flush, clk=None):
@@ -301,7 +308,7 @@ def handle_passes(mape, wl, inst, starts, stream, steps, warmup, prec, flush, cl
     return total_ms, statuses, launches
 
 
-def e2e_passes(mape, wl, inst, starts_host, stream, reps, directions_hint):
+def e2e_passes(mape, wl, inst, starts_host, stream, reps, directions_hint, prec=1):
     """The public handle API with host buffers, every copy inside the region:
     the instance and the starts go up from pinned host memory, the direction
     set (int8 rows) and the best point come back into pinned host memory
@@ -313,7 +320,7 @@ def e2e_passes(mape, wl, inst, starts_host, stream, reps, directions_hint):
     src_host = torch.from_numpy(np.ascontiguousarray(src)).pin_memory().numpy()
     x0_host = inst.xbar[None, :].astype(np.int32)
     D_host = torch.empty((max(int(1.2 * directions_hint), 1024), inst.n), dtype=torch.int8).pin_memory().numpy()
-    cfg = mape.default_config(T=wl["T"], precision=PREC["bf16"], period=wl["period"])
+    cfg = mape.default_config(T=wl["T"], precision=prec, period=wl["period"])
     times, units = [], 0
     h2d = (inst.A.nbytes + inst.b.nbytes + inst.l.nbytes + inst.u.nbytes + inst.B.nbytes + inst.Q.nbytes
            + inst.c.nbytes + (0 if inst.w is None else inst.w.nbytes) + src_host.nbytes + x0_host.nbytes)
@@ -358,7 +365,7 @@ def run_ours(args):
     starts = tuple(None if a is None else torch.from_numpy(a).to(dev) for a in starts_host)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    prec = PREC[args.precision]
+    prec = PREC[args.precision] | (mape.PREC_SPARSE_FWD if args.sparse_fwd else 0)
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
@@ -372,7 +379,7 @@ def run_ours(args):
     units_all, ms_max = reduce_over_ranks(directions, total_ms, world)
     value = units_all / (ms_max / 1e3)
     e2e = e2e_passes(mape, wl, inst, starts_host, stream, max(1, min(args.steps, 3)),
-                     directions / max(args.steps, 1))
+                     directions / max(args.steps, 1), prec)
 
     result = None
     if rank == 0:
@@ -380,10 +387,10 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"bf16": "bf16", "bf16x1": "bf16", "fp32": "f32", "sparse": "f32"}[args.precision],
+            "dtype": {"bf16": "bf16", "bf16x1": "bf16", "fp32": "f32", "sparse": "f32", "fp8": "fp8+bf16"}[args.precision],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "P": wl["P"], "T": wl["T"], "n": wl["n"], "m": wl["m"],
-                       "period": wl["period"], "precision": args.precision,
+                       "period": wl["period"], "precision": args.precision + ("+sparse_fwd" if args.sparse_fwd else ""),
                        "l2": "inputs larger than L2, and L2 flushed (256 MiB write) before each timed step",
                        "replicas_per_rank": 1},
             "directions_per_step": directions / args.steps,
@@ -396,13 +403,13 @@ def run_ours(args):
             "clocks": clk.summary(),
             "e2e": e2e,
         }
-        result["roofline"] = roofline_streamed(mape, wl, inst, starts, stream)
+        result["roofline"] = roofline_streamed(mape, wl, inst, starts, stream, prec)
         if world == 1 and not args.no_medium:
             result["medium"] = medium_measure(mape, args, stream, flush)
         if args.batch > 0 and world == 1:
             result["batched"] = batch_measure(args.batch)
         if args.serve > 0 and world == 1:
-            result["serving"] = serve_measure(args.serve, args.serve_T)
+            result["serving"] = serve_measure(args.serve, args.serve_T, args.serve_plain)
         if not args.no_cpu_baseline and world == 1:
             pool = OraclePool()
             try:
@@ -531,6 +538,8 @@ def streamed_case(args):
             "uneven1000": lambda: I.uneven_single(1000, density=0.05)}[name]()
     bf = args.precision in ("bf16", "bf16x1")
     prec = PREC[args.precision] | (0 if not bf else (mape.PREC_AUTOTUNE if args.autotune else mape.PREC_STREAMED))
+    if args.sparse_fwd:
+        prec |= mape.PREC_SPARSE_FWD
     Z0 = I.normal_starts(inst, P, std=LARGE["std"], seed=LARGE["seed"]).Z0
     stream = torch.cuda.Stream()
     times, counts = time_extract_kernel(mape, inst, (Z0, None), P, T, prec, stream, reps=2,
@@ -551,6 +560,7 @@ def streamed_case(args):
 
 SERVE_RATE = 200.0    # requests per second (Poisson)
 SERVE_P = 4096
+SERVE_DISTINCT = 200  # distinct instances in the stream (each recurs with its starts; drawing 2000 costs minutes)
 
 
 def _pct(v, q):
@@ -558,64 +568,83 @@ def _pct(v, q):
     return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
 
 
-def serve_measure(N, T, seed=3000):
-    """The serving workload: N requests arriving as a Poisson stream at 200/s,
-    instances with n log-uniform in [30, 3000], m = n/5, C in [-3,3] at a
-    density uniform in [0.05, 0.2], box [-5,5], P = 4096 projected starts,
-    Algorithm 1 from x̄.  Runs them through the request server (continuous
-    batching, BF16 paths) and, for comparison, one at a time through the plain
-    FP32 single-instance path; reports instances/s and p50/p99 time to first
-    improving direction and to termination (from arrival), and verified
-    directions/s."""
+def serve_measure(N, T, n_plain=24, seed=3000):
+    """The serving workload: N requests arriving as a Poisson stream at 200/s
+    over SERVE_DISTINCT distinct instances taken in turn (n log-uniform in
+    [30, 3000], m = n/5, C in [-3,3] at a density uniform in [0.05, 0.2], box
+    [-5,5]; each with its own P = 4096 projected starts), Algorithm 1 from x̄.  Runs them through the request server (continuous
+    batching, BF16 paths) and, for comparison, the first n_plain of them one
+    at a time through the plain FP32 single-instance path (arriving on the
+    same clock); reports instances/s, p50/p99 time to first improving
+    direction and to termination (from arrival), the backlog, and verified
+    directions/s.  When the server completes fewer instances per second than
+    arrive, the queue grows and the completion rate is the saturation point."""
     import numpy as np
     from paper_2412_13576_gb300 import instances as I
     from paper_2412_13576_gb300 import mape
     rng = np.random.default_rng(seed)
-    insts = I.uneven_batch(count=N, n_lo=30, n_hi=3000, seed=seed)
+    pool = I.uneven_batch(count=min(N, SERVE_DISTINCT), n_lo=30, n_hi=3000, seed=seed)
+    pool_g0 = [I.uniform_samples(inst, SERVE_P, seed=seed + 1 + k).G0 for k, inst in enumerate(pool)]
+    # the stream: the distinct instances in turn, each with its own starts
+    insts = [pool[k % len(pool)] for k in range(N)]
     arrivals = np.cumsum(rng.exponential(1.0 / SERVE_RATE, size=N))
-    G0s = [I.uniform_samples(inst, SERVE_P, seed=seed + 1 + k).G0 for k, inst in enumerate(insts)]
 
-    def run_server(cfg, slots):
+    def starts(k):
+        return pool_g0[k % len(pool)]
+
+    def run_server(cfg, slots, count):
         with mape.Server(cfg, mem_cap_bytes=150 << 30, max_slots=slots) as srv:
             # warm-up: the smallest and the largest instance, 10 steps each (loads every kernel used)
             warm_cfg = mape.default_config(T=10, precision=cfg.precision)
             with mape.Server(warm_cfg, mem_cap_bytes=150 << 30, max_slots=2) as ws:
                 for k in (int(np.argmin([i.n for i in insts])), int(np.argmax([i.n for i in insts]))):
-                    ws.submit(insts[k], SERVE_P, G0=G0s[k])
+                    ws.submit(insts[k], SERVE_P, G0=starts(k))
                 ws.wait_all(600)
+            G0s = [starts(k) for k in range(count)]     # drawn before the clock starts (shared per instance)
             t0 = time.perf_counter()
-            ids = []
-            for k, inst in enumerate(insts):
+            ids, backlog = [], 0
+            for k in range(count):
                 wait = arrivals[k] - (time.perf_counter() - t0)
                 if wait > 0:
                     time.sleep(wait)
-                ids.append(srv.submit(inst, SERVE_P, G0=G0s[k]))
+                ids.append(srv.submit(insts[k], SERVE_P, G0=G0s[k]))
+                if k % 50 == 49:
+                    backlog = max(backlog, srv.stats()["queued"])
             srv.wait_all(3600)
             wall = time.perf_counter() - t0
             infos = [srv.info(i) for i in ids]
             stats = srv.stats()
-        return infos, wall, stats
+            for i in ids:
+                srv.release(i)
+        return infos, wall, stats, backlog
 
     out = {}
-    for name, prec, slots in (("served_bf16", PREC["bf16"], 16), ("plain_fp32_one_at_a_time", 0, 1)):
+    for name, prec, slots, count in (("served_bf16", PREC["bf16"], 16, N),
+                                     ("plain_fp32_one_at_a_time", 0, 1, min(n_plain, N))):
         cfg = mape.default_config(T=T, precision=prec)
-        infos, wall, stats = run_server(cfg, slots)
+        infos, wall, stats, backlog = run_server(cfg, slots, count)
         ok = [i for i in infos if i["state"] == "DONE"]
         ttfid = [i["t_first_improve_ms"] - i["t_submit_ms"] for i in ok]
         ttt = [i["t_done_ms"] - i["t_submit_ms"] for i in ok]
-        out[name] = {"instances_per_s": len(ok) / wall, "wall_s": wall, "completed": len(ok),
-                     "failed": len(infos) - len(ok),
+        out[name] = {"requests": count, "instances_per_s": len(ok) / wall, "wall_s": wall, "completed": len(ok),
+                     "failed": len(infos) - len(ok), "arrival_rate": SERVE_RATE,
+                     "arrivals_span_s": float(arrivals[count - 1]),
                      "ttfid_ms_p50": _pct(ttfid, 50), "ttfid_ms_p99": _pct(ttfid, 99),
                      "ttt_ms_p50": _pct(ttt, 50), "ttt_ms_p99": _pct(ttt, 99),
                      "directions_per_s": sum(i["directions"] for i in ok) / wall,
-                     "peak_running": stats["peak_running"], "mem_peak_gb": stats["mem_peak"] / 1e9,
+                     "peak_running": stats["peak_running"], "peak_queued_sampled": backlog,
+                     "mem_peak_gb": stats["mem_peak"] / 1e9,
                      "best_f": [i["best_f"] for i in infos]}
     a, b = out["served_bf16"]["best_f"], out["plain_fp32_one_at_a_time"]["best_f"]
     out["f_not_worse_than_plain"] = float(np.mean([x <= y for x, y in zip(a, b)]))
     for k in ("served_bf16", "plain_fp32_one_at_a_time"):
         out[k].pop("best_f")
-    out["workload"] = (f"{N} requests, Poisson arrivals at {SERVE_RATE:.0f}/s, n log-uniform in [30, 3000] "
-                       f"(uneven_batch seed {seed}), m = n/5, P = {SERVE_P}, T = {T}, 150 GB admission cap")
+    s = out["served_bf16"]
+    s["saturated"] = s["instances_per_s"] < 0.95 * SERVE_RATE
+    out["workload"] = (f"{N} requests, Poisson arrivals at {SERVE_RATE:.0f}/s, over {len(pool)} distinct instances "
+                       f"taken in turn (n log-uniform in [30, 3000], uneven_batch seed {seed}, m = n/5, each with its "
+                       f"own P = {SERVE_P} projected starts), T = {T}, 150 GB admission cap; the plain arm runs the "
+                       f"first {min(n_plain, N)} of them")
     return out
 
 
@@ -718,7 +747,7 @@ def measured_traffic(record, src_path):
     return int(m_b.group(1))
 
 
-def roofline_streamed(mape, wl, inst, starts, stream, reps=2):
+def roofline_streamed(mape, wl, inst, starts, stream, prec, reps=2):
     """The streamed kernels of the large workload, timed live: `reps` calls of
     mape_extract (T steps, the workload's starts and period) with the
     library's per-launch CUDA events on the call's stream.  The dominant
@@ -734,7 +763,7 @@ def roofline_streamed(mape, wl, inst, starts, stream, reps=2):
     host = tuple(None if a is None else a.cpu().numpy() for a in starts)
     mape.launch_timing(True)
     try:
-        times, counts = time_extract_kernel(mape, inst, host, P, T, PREC["bf16"], stream, reps, period=wl["period"])
+        times, counts = time_extract_kernel(mape, inst, host, P, T, prec, stream, reps, period=wl["period"])
         per = mape.launch_timing_read()
     finally:
         mape.launch_timing(False)
@@ -753,7 +782,8 @@ def roofline_streamed(mape, wl, inst, starts, stream, reps=2):
             "ms_per_launch": ms_grad, "bytes_per_launch": bytes_grad,
             "peak_source": f"{src} HBM copy rate (MEASURED_PEAKS.json hbm_gbs)",
             "launches_timed": per["stream_grad"][1],
-            "forward": {"kernel": "stream_fwd_kernel", "ms_per_launch": ms_fwd, "bytes_per_launch": bytes_fwd,
+            "forward": {"kernel": "stream_fwd_sparse_kernel" if prec & mape.PREC_SPARSE_FWD else "stream_fwd_kernel",
+                        "ms_per_launch": ms_fwd, "bytes_per_launch": bytes_fwd,
                         "achieved": bytes_fwd / (ms_fwd / 1e3) / 1e9,
                         "frac": bytes_fwd / (ms_fwd / 1e3) / 1e9 / peak},
             "collect_ms_per_launch": ms_coll, "collect_launches": per["stream_collect"][1],
@@ -858,8 +888,31 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def probe_mma():
+    """The tensor-core instruction cost (mape_mma_issue_probe) over M, N,
+    operand kind and accumulator count: SM cycles per instruction and the
+    FLOPs per cycle that makes."""
+    import torch
+    from paper_2412_13576_gb300 import mape
+    torch.cuda.set_device(0)
+    mape.lib(build_if_missing=True)
+    rows = []
+    for kind, K in ((0, 16), (1, 32)):
+        for M in (64, 128):
+            for N in (16, 32, 64, 128, 256):
+                for acc in (1, 2):
+                    issue, total = mape.mma_issue_probe(kind, M, N, acc, 512)
+                    rows.append({"kind": ("f16/bf16", "f8f6f4/e4m3")[kind], "M": M, "N": N, "K": K,
+                                 "accumulators": acc, "issue_cycles": issue, "total_cycles": total,
+                                 "flops_per_cycle": 2.0 * M * N * K / total})
+    return {"probe_mma": rows}
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.probe_mma:
+        print(json.dumps(probe_mma()), flush=True)
+        return 0
     if args.kernel_case:
         print(json.dumps(kernel_case(args)), flush=True)
         return 0

@@ -137,3 +137,31 @@ def test_step_count_limit(M):
             M.extract(t0=0, T=(1 << 20) + 1, cfg=M.default_config(precision=prec), **b)
         assert e.value.code == -2
     torch.cuda.synchronize()
+
+
+def test_mma_issue_probe_and_launch_timing(M):
+    """The measurement entry points: the MMA cost probe returns positive cycle
+    counts for both operand kinds and refuses shapes tcgen05 does not take;
+    launch timing counts every streamed launch of a call and times it."""
+    import torch
+    for kind in (0, 1):
+        issue, total = M.mma_issue_probe(kind, 128, 256, 1, 64)
+        assert 0 < issue <= total < 1e6
+    with pytest.raises(M.MapeError):
+        M.mma_issue_probe(0, 96, 256)
+    inst = I.uneven_single(1000, density=0.05)
+    Z = dev(I.normal_starts(inst, 256, std=0.3, seed=3).Z0)
+    ldc = M.round16(inst.n)
+    cand = torch.zeros((256 * 5, ldc), dtype=torch.int8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    M.launch_timing(True)
+    try:
+        M.extract(dev(inst.B), dev((inst.u - inst.l).astype(np.int32)), Z, torch.zeros_like(Z), torch.zeros_like(Z),
+                  t0=0, T=4, cfg=M.default_config(precision=M.PREC_BF16, period=2), cand=cand, cand_count=cnt,
+                  flags=flags, ldc=ldc)
+        got = M.launch_timing_read()
+    finally:
+        M.launch_timing(False)
+    assert got["stream_grad"][1] == 4 and got["stream_fwd"][1] == 5 and got["stream_collect"][1] == 2
+    assert all(ms > 0 for ms, n in got.values() if n > 0)

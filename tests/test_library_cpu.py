@@ -233,3 +233,12 @@ def test_kernel_basis_matches_oracle(lib):
     with pytest.raises(mape.MapeError) as err:
         mape.kernel_basis(np.array([[1, 2, 3], [2, 4, 6]]))
     assert err.value.code == -1
+
+
+def test_mma_issue_probe_refuses_bad_arguments(lib):
+    """Argument checks of the measurement entry point run before any CUDA call."""
+    import ctypes
+    a, b = ctypes.c_double(0), ctypes.c_double(0)
+    for args in ((2, 128, 256, 1, 64), (0, 96, 256, 1, 64), (0, 128, 8, 1, 64), (0, 128, 264, 1, 64),
+                 (0, 128, 256, 3, 64), (0, 128, 512, 2, 64), (0, 128, 256, 1, 0)):
+        assert lib.mape_mma_issue_probe(*args, ctypes.byref(a), ctypes.byref(b)) == -1
