@@ -404,18 +404,19 @@ def run_ours(args):
             "e2e": e2e,
         }
         result["roofline"] = roofline_streamed(mape, wl, inst, starts, stream, prec)
+        if not args.no_cpu_baseline and world == 1:
+            # before the serving measurement, whose host threads and arrays would share the cores
+            pool = OraclePool()
+            try:
+                result["cpu_baseline"] = cpu_baseline_obj(pool.run(wl, CPU_STARTS_PER_CORE * pool.cores), wl)
+            finally:
+                pool.close()
         if world == 1 and not args.no_medium:
             result["medium"] = medium_measure(mape, args, stream, flush)
         if args.batch > 0 and world == 1:
             result["batched"] = batch_measure(args.batch)
         if args.serve > 0 and world == 1:
             result["serving"] = serve_measure(args.serve, args.serve_T, args.serve_plain)
-        if not args.no_cpu_baseline and world == 1:
-            pool = OraclePool()
-            try:
-                result["cpu_baseline"] = cpu_baseline_obj(pool.run(wl, CPU_STARTS_PER_CORE * pool.cores), wl)
-            finally:
-                pool.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -69,6 +69,7 @@ struct mape_server {
   int64_t submitted = 0, completed = 0, failed = 0;
   bool stop = false;
   std::thread sched;
+  int starting = 0;  // admitted requests whose handle is being created (under mu)
 
   void loop();
   void start(Request* r, int slot);
@@ -169,8 +170,10 @@ extern "C" int mape_server_submit(mape_server_h s, const int32_t* A, const int64
 }
 
 // Creates the handle on the slot's stream and starts its extraction.  Runs on
-// the scheduler thread without the lock (uploads and the projection's
-// factorisation synchronise the slot's stream only).
+// a thread of its own per admission, without the lock (the uploads, the basis
+// check and the projection's factorisation synchronise the slot's stream
+// only), so that the scheduler keeps admitting and advancing requests while
+// the handles of several admissions are being set up.
 void mape_server::start(Request* r, int slot) {
   mape_problem f{r->n, r->m, r->Q.data(), r->c.data(), r->has_w ? r->w.data() : nullptr};
   mape_handle h = nullptr;
@@ -181,11 +184,13 @@ void mape_server::start(Request* r, int slot) {
                                  r->G0.empty() ? nullptr : r->G0.data());
   std::lock_guard<std::mutex> lk(mu);
   r->h = h;
+  --starting;
   if (rc != MAPE_OK) {
     finish(r, rc);
     return;
   }
   r->stage = 1;
+  cv.notify_all();
 }
 
 // Called with the lock held: releases the request's slot and memory.
@@ -267,9 +272,11 @@ void mape_server::loop() {
       mem_peak = std::max(mem_peak, mem_in_use);
       ++running;
       peak_running = std::max(peak_running, running);
-      lk.unlock();
-      start(r, slot);
-      lk.lock();
+      ++starting;
+      std::thread([this, r, slot] {
+        cudaSetDevice(dev);
+        start(r, slot);
+      }).detach();
     }
     cv.wait_for(lk, std::chrono::microseconds(200));
   }
@@ -376,6 +383,10 @@ extern "C" void mape_server_destroy(mape_server_h s) {
     s->cv.notify_all();
   }
   if (s->sched.joinable()) s->sched.join();
+  {  // the threads that set up admitted requests finish on their own (bounded)
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv.wait_for(lk, std::chrono::seconds(600), [s] { return s->starting == 0; });
+  }
   for (auto& kv : s->reqs)
     if (kv.second->h) {
       mape_cancel(kv.second->h);
