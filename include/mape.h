@@ -497,6 +497,22 @@ int mape_create_instance(const int32_t* A, const int64_t* b, const int32_t* l,
 int mape_extract_directions(mape_handle h, int32_t P, const float* Z0,
                             const float* G0);
 
+/* Starts Algorithm 2 for `count` handles together (the paper has no batched
+ * form; this is the interface a server uses to run uneven instances in one
+ * launch): for handle i, P[i] starts Z0[i] or G0[i] as in
+ * mape_extract_directions (Z0 or G0 may be NULL as a whole).  The extraction
+ * steps of all handles run as one mape_extract_batch call per chunk of steps
+ * (one CUDA graph of persistent launches, on the first handle's stream), each
+ * chunk's candidates are merged into each handle's set on its own stream, and
+ * the kernel test, minimality filter and coefficients of each handle then run
+ * on its own worker thread and stream.  Every handle must be idle, and all
+ * must share T, period and a BF16 precision (MAPE_PREC_BF16 or
+ * MAPE_PREC_BF16X1, without MAPE_PREC_SPARSE_FWD): INVALID_ARG otherwise.
+ * Returns at once; poll and wait on each handle as usual.  Each handle's
+ * direction set equals that of its own mape_extract_directions. */
+int mape_extract_directions_batch(mape_handle* hs, int32_t count, const int32_t* P,
+                                  const float* const* Z0, const float* const* G0);
+
 /* Starts Algorithm 1 from S starts X0 [S x n] (each must lie in S; host or
  * device pointer, copied before the call returns) with the current direction
  * set.  f_or_NULL replaces the objective (same n): the
@@ -583,6 +599,14 @@ typedef struct {
   int32_t max_slots;        /* requests on the device at once (1..256)       */
   int32_t keep_directions;  /* 1: keep each request's direction set on the
                                host for mape_server_result                  */
+  int32_t batch_extraction; /* 1: the extraction of the requests admitted
+                               together (whose handles are ready at the same
+                               time) runs as one mape_extract_directions_batch
+                               call, i.e. one graph of persistent launches per
+                               chunk of steps for all of them; needs a BF16
+                               precision.  0: each request's extraction runs
+                               on its own slot stream                        */
+  int32_t reserved;
 } mape_server_config;
 
 #define MAPE_REQ_QUEUED  0

@@ -375,7 +375,10 @@ extern "C" int mape_augment_run(const mape_augment_args* A, int64_t* iters_out, 
   }
   size_t smem = (size_t)n * (4 * sizeof(long long) + 2 * sizeof(int32_t));
   if (smem > 48 * 1024) {
-    MAPE_CUDA_TRY(cudaFuncSetAttribute(score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    size_t lim = 0;
+    const int rc = allow_max_dynamic_smem((const void*)score_kernel, &lim);
+    if (rc != MAPE_OK) return rc;
+    if (smem > lim) return MAPE_ERR_SHAPE;
   }
   int64_t done_iters = 0;
   const int64_t chunk = 8;

@@ -23,6 +23,13 @@ void record_cuda_error(cudaError_t e, const char* what, const char* file, int li
 // Records a plain message (an argument error worth explaining) in the same place.
 void record_message(const char* what);
 
+// Lets the kernel `func` take as much dynamic shared memory as the device
+// allows (its static shared memory deducted) and returns that amount in
+// *limit.  Every caller sets the same value, so that threads launching the
+// same kernel with different amounts (handles of a server) never lower the
+// limit under one another's launch.
+int allow_max_dynamic_smem(const void* func, size_t* limit);
+
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

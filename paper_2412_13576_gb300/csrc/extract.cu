@@ -26,6 +26,18 @@ void record_cuda_error(cudaError_t e, const char* what, const char* file, int li
                 file, line, what);
 }
 
+int allow_max_dynamic_smem(const void* func, size_t* limit) {
+  int dev = 0, optin = 0;
+  MAPE_CUDA_TRY(cudaGetDevice(&dev));
+  MAPE_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa{};
+  MAPE_CUDA_TRY(cudaFuncGetAttributes(&fa, func));
+  const int v = optin - (int)fa.sharedSizeBytes;
+  MAPE_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+  if (limit) *limit = (size_t)v;
+  return MAPE_OK;
+}
+
 void record_message(const char* what) {
   std::lock_guard<std::mutex> lk(g_err_mu);
   std::snprintf(g_last_err, sizeof(g_last_err), "%s", what);

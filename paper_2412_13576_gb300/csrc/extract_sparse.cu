@@ -371,7 +371,12 @@ int extract_sparse(const mape_extract_args* a, cudaStream_t st) {
   p.cand = a->cand; p.ldc = a->ldc; p.cap = a->cand_cap; p.count = a->cand_count; p.flags = a->flags;
   p.dbg_phi = a->dbg_phi; p.dbg_grad = a->dbg_grad;
   const size_t smem = sparse_smem(d, mr);
-  MAPE_CUDA_TRY(cudaFuncSetAttribute(sparse_extract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    size_t lim = 0;
+    const int rc = allow_max_dynamic_smem((const void*)sparse_extract_kernel, &lim);
+    if (rc != MAPE_OK) return rc;
+    if ((size_t)smem > lim) return MAPE_ERR_SHAPE;
+  }
   launch(sparse_extract_kernel, (unsigned)P, kThreads, smem, st, p);
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;

@@ -86,6 +86,7 @@ struct StParams {
   int32_t* flags;
   float* dbg_phi;
   float* dbg_grad;
+  int tile0;              // first tile of this launch (the tile range of a launch may be part of the call's)
   const int32_t* sp_rp;   // sparse forward: CSR of Bm, row starts [R + 1]
   const uint16_t* sp_ci;  //   column indices (coordinates)
   const float* sp_rv;     //   values
@@ -134,7 +135,7 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool conv = tid < kThreads;
-  const int tile = blk / p.nbF, rb = blk % p.nbF;
+  const int tile = p.tile0 + blk / p.nbF, rb = blk % p.nbF;
   const int N = rb < p.nbF - 1 ? p.wF : p.R64 - p.wF * (p.nbF - 1);
   const int row0 = rb * p.wF;
   const int fstage = fwd_stage(p.wF);
@@ -571,7 +572,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) stream_fwd_sparse_kernel(StPara
 template <bool kId>
 __device__ __forceinline__ void stream_collect_body(const StParams& p, const int blk, int s) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t pg = (int64_t)blk * (blockDim.x >> 5) + warp;
+  const int64_t pg = (int64_t)p.tile0 * kTM + (int64_t)blk * (blockDim.x >> 5) + warp;
   if (pg >= p.P) return;
   const int P2 = ptot(p);
   long long slot = -1;
@@ -617,7 +618,7 @@ __device__ __forceinline__ void stream_grad_body(const StParams& p, const int bl
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tile = blk / p.nbG, db = blk % p.nbG;
+  const int tile = p.tile0 + blk / p.nbG, db = blk % p.nbG;
   const int N = db < p.nbG - 1 ? p.wG : p.d64 - p.wG * (p.nbG - 1);
   const int col0 = db * p.wG;
   const int gstage = grad_stage(p.wG);
@@ -1071,6 +1072,7 @@ StreamShape stream_bound(int n, int d, int P) {
 }
 
 constexpr int32_t kBiasSteps = 1 << 20;  // bias-correction table: up to 2^20 steps per call
+constexpr int kSplitTiles = 64;          // calls of at least this many tiles run as two halves on two streams
 
 // The sparse forward is used while nnz(Bm) <= R d / 16 (density at most 1/16).
 constexpr int kSparseDensityInv = 16;
@@ -1310,24 +1312,89 @@ int extract_stream_widths(const mape_extract_args* a, cudaStream_t st, int wF, i
     if (ssm > (size_t)227 * 1024) return MAPE_ERR_SHAPE;
     const unsigned gw = (unsigned)ceil_div((int64_t)sh.R * 32, 256);
     launch(bm_fill_kernel, gw, 256, 0, st, a->B, d, sh.R, sh.r0, c.sp_rp, c.sp_ci, c.sp_rv);
-    MAPE_CUDA_TRY(cudaFuncSetAttribute(stream_fwd_sparse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+    size_t lim = 0;
+    if ((rc = allow_max_dynamic_smem((const void*)stream_fwd_sparse_kernel, &lim)) != MAPE_OK) return rc;
+    if (ssm > lim) return MAPE_ERR_SHAPE;
     p.sp_rp = c.sp_rp;
     p.sp_ci = c.sp_ci;
     p.sp_rv = c.sp_rv;
   }
-  st_schedule(
-      a->t0, a->T, a->period,
-      [&](int s, int f, int col) {
-        if (sparse)
+  if (sparse) {
+    st_schedule(
+        a->t0, a->T, a->period,
+        [&](int s, int f, int col) {
           timed_launch(MAPE_TIMED_STREAM_FWD, st, [&] {
             launch(stream_fwd_sparse_kernel, gS, kSpThreads, ssm, st, p, s, f, col, h_nnz, csr_in_smem);
           });
-        else
-          timed_launch(MAPE_TIMED_STREAM_FWD, st, [&] { launch(fwdk, gF, kThreadsF, fsm, st, p, s, f, col); });
-      },
-      [&](int s) { timed_launch(MAPE_TIMED_STREAM_COLLECT, st, [&] { launch(collk, gC, 256, 0, st, p, s); }); },
-      [&](int s) { timed_launch(MAPE_TIMED_STREAM_GRAD, st, [&] { launch(gradk, gG, kThreads, gsm, st, p, s); }); });
+        },
+        [&](int s) { timed_launch(MAPE_TIMED_STREAM_COLLECT, st, [&] { launch(collk, gC, 256, 0, st, p, s); }); },
+        [&](int s) { timed_launch(MAPE_TIMED_STREAM_GRAD, st, [&] { launch(gradk, gG, kThreads, gsm, st, p, s); }); });
+    MAPE_LAUNCH_CHECK();
+    return st_unpack(c, a, st);
+  }
+  // The tiles are independent problems, so with enough of them the call runs
+  // as two halves on two streams (the second joins the caller's stream at the
+  // end): the forward pass of one half, bound by moving z through shared
+  // memory, runs beside the gradient pass of the other, bound by HBM.
+  const int nhalf = sh.tiles >= kSplitTiles ? 2 : 1;
+  cudaStream_t st2 = st;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  if (nhalf == 2) {
+    MAPE_CUDA_TRY(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
+    MAPE_CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    MAPE_CUDA_TRY(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+    MAPE_CUDA_TRY(cudaEventRecord(ev_fork, st));
+    MAPE_CUDA_TRY(cudaStreamWaitEvent(st2, ev_fork, 0));
+  }
+  struct Half {
+    StParams p;
+    cudaStream_t st;
+    unsigned gF, gG, gC;
+  };
+  Half H[2];
+  const int tA = nhalf == 2 ? sh.tiles / 2 : sh.tiles;
+  for (int hh = 0; hh < nhalf; ++hh) {
+    const int t0 = hh == 0 ? 0 : tA, nt = hh == 0 ? tA : sh.tiles - tA;
+    H[hh].p = p;
+    H[hh].p.tile0 = t0;
+    H[hh].st = hh == 0 ? st : st2;
+    H[hh].gF = (unsigned)(nt * sh.nbF);
+    H[hh].gG = (unsigned)(nt * sh.nbG);
+    const int64_t starts = std::min<int64_t>(P, (int64_t)(t0 + nt) * kTM) - (int64_t)t0 * kTM;
+    H[hh].gC = (unsigned)ceil_div(std::max<int64_t>(starts, 1), 8);
+  }
+  auto fwd = [&](const Half& h, int s, int f, int col) {
+    timed_launch(MAPE_TIMED_STREAM_FWD, h.st, [&] { launch(fwdk, h.gF, kThreadsF, fsm, h.st, h.p, s, f, col); });
+  };
+  auto coll = [&](const Half& h, int s) {
+    timed_launch(MAPE_TIMED_STREAM_COLLECT, h.st, [&] { launch(collk, h.gC, 256, 0, h.st, h.p, s); });
+  };
+  auto grad = [&](const Half& h, int s) {
+    timed_launch(MAPE_TIMED_STREAM_GRAD, h.st, [&] { launch(gradk, h.gG, kThreads, gsm, h.st, h.p, s); });
+  };
+  // the halves' launches interleaved step by step, in st_schedule's order
+  for (int s = 0; s < a->T; ++s) {
+    const int t = a->t0 + s + 1;
+    const int collect = (s >= 1 && (t - 1) % a->period == 0) ? 1 : 0;
+    for (int hh = 0; hh < nhalf; ++hh) {
+      fwd(H[hh], s, 1, collect);
+      if (collect) coll(H[hh], s);
+      grad(H[hh], s);
+    }
+  }
+  if ((a->t0 + a->T) % a->period == 0)
+    for (int hh = 0; hh < nhalf; ++hh) {
+      fwd(H[hh], a->T, 0, 1);
+      coll(H[hh], a->T);
+    }
   MAPE_LAUNCH_CHECK();
+  if (nhalf == 2) {
+    MAPE_CUDA_TRY(cudaEventRecord(ev_join, st2));
+    MAPE_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
+    cudaEventDestroy(ev_fork);
+    cudaEventDestroy(ev_join);
+    cudaStreamDestroy(st2);  // released once its work has completed
+  }
   return st_unpack(c, a, st);
 }
 

@@ -1169,7 +1169,12 @@ int extract_tc(const mape_extract_args* a, cudaStream_t st) {
   const bool res = tc_resident_state(p);
   auto kern = id ? (res ? extract_tc_kernel<true, true> : extract_tc_kernel<true, false>)
                  : (res ? extract_tc_kernel<false, true> : extract_tc_kernel<false, false>);
-  MAPE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    size_t lim = 0;
+    const int rc = allow_max_dynamic_smem((const void*)kern, &lim);
+    if (rc != MAPE_OK) return rc;
+    if ((size_t)smem > lim) return MAPE_ERR_SHAPE;
+  }
   mape_detail::timed_launch(MAPE_TIMED_RESIDENT, st,
                             [&] { mape_detail::launch(kern, (unsigned)ceil_div(a->P, kTileM), kThreads, smem, st, p); });
   MAPE_LAUNCH_CHECK();
@@ -1259,7 +1264,10 @@ int extract_tc_batch_prepare(const mape_extract_args* const* items, const bool* 
   plan.params = std::move(params);
   for (auto& L : plan.launches) {
     auto kern = batch_kernel(L.variant);
-    MAPE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+    size_t lim = 0;
+    const int rc = allow_max_dynamic_smem((const void*)kern, &lim);
+    if (rc != MAPE_OK) return rc;
+    if ((size_t)L.smem > lim) return MAPE_ERR_SHAPE;
   }
   *out = hold.release();
   return MAPE_OK;

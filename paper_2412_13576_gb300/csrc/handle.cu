@@ -187,6 +187,17 @@ struct mape_instance {
     cv.notify_all();
   }
 
+  // extraction progress (the parts of run_extract, also driven by a batch)
+  double ex_start = 0;
+  int64_t ex_U = 0, ex_total = 0;
+  int ex_done = 0;
+  int8_t *ex_cur = nullptr, *ex_other = nullptr;
+  int extract_begin();
+  int extract_chunk_steps(int* chunk) const;
+  int extract_chunk_args(int chunk, mape_extract_args* a);
+  int extract_chunk_done(int chunk);
+  int extract_filter();
+
   int run_extract();
   int run_augment(int64_t max_iters);
 };
@@ -197,73 +208,107 @@ struct mape_instance {
     if (_rc != MAPE_OK) return _rc; \
   } while (0)
 
-int mape_instance::run_extract() {
-  using namespace mape_detail;
-  cudaStream_t s = stream;
-  double t_start = now_ms();
+// Algorithm 2 in three parts, so that a batch of handles can run the
+// extraction steps of all of them as one mape_extract_batch call per chunk:
+// begin (starts, Adam moments), chunks (each: the steps, then the merge of the
+// chunk's candidates into the distinct set), filter (kernel test, minimality,
+// coefficients).
+int mape_instance::extract_begin() {
+  ex_start = now_ms();
   set_phase(MAPE_PHASE_EXTRACTING);
-  if (dG0) H_TRY(mape_project_apply(dWproj, n, d, dG0, P, dZ, s));
-  MAPE_CUDA_TRY(cudaMemsetAsync(dM, 0, sizeof(float) * (size_t)P * d, s));
-  MAPE_CUDA_TRY(cudaMemsetAsync(dV, 0, sizeof(float) * (size_t)P * d, s));
-  int64_t U = 0, total_cand = 0;
-  int t_done = 0;
-  int8_t* cur = dBuf0;
-  int8_t* other = dBuf1;
-  while (t_done < cfg.T) {
-    if (cancel.load()) return MAPE_ERR_CANCELLED;
-    // a chunk may hold as many collections (steps whose number is a multiple
-    // of the period) as there is room for one row per start each: it ends
-    // just before the first collection that would not fit
-    const int64_t room = cap - U;
-    const int64_t fits = room / P;
-    const int64_t period = cfg.period;
-    const int64_t steps = (t_done / period + fits + 1) * period - 1 - t_done;
-    if (steps < 1) return MAPE_ERR_CAPACITY;
-    int chunk = (int)std::min<int64_t>(steps, cfg.T - t_done);
-    MAPE_CUDA_TRY(cudaMemsetAsync(dCount, 0, sizeof(unsigned long long), s));
-    MAPE_CUDA_TRY(cudaMemsetAsync(dFlags, 0, sizeof(int32_t), s));
-    mape_extract_args a{};
-    a.n = n; a.d = d; a.P = P; a.B = dB; a.span = dspan; a.Z = dZ; a.M = dM; a.V = dV;
-    a.t0 = t_done; a.T = chunk; a.period = cfg.period; a.precision = cfg.precision;
-    a.lambda1 = cfg.lambda1; a.lambda2 = cfg.lambda2; a.lr = cfg.lr; a.beta1 = cfg.beta1;
-    a.beta2 = cfg.beta2; a.eps = cfg.eps;
-    a.cand = cur + U * ldg; a.ldc = ldg; a.cand_cap = cap - U; a.cand_count = dCount; a.flags = dFlags;
-    a.workspace = dWork; a.workspace_bytes = work_bytes;
-    H_TRY(mape_extract(&a, s));
-    unsigned long long cnt = 0;
-    int32_t flags = 0;
-    MAPE_CUDA_TRY(cudaMemcpyAsync(&cnt, dCount, sizeof(cnt), cudaMemcpyDeviceToHost, s));
-    MAPE_CUDA_TRY(cudaMemcpyAsync(&flags, dFlags, sizeof(flags), cudaMemcpyDeviceToHost, s));
-    MAPE_CUDA_TRY(cudaStreamSynchronize(s));
-    if (flags & 1) return MAPE_ERR_CAPACITY;
-    total_cand += (int64_t)cnt;
-    int64_t K_new = 0;
-    H_TRY(mape_dedup(cur, U + (int64_t)cnt, n, ldg, other, cap, &K_new, dWork, work_bytes, s));
-    U = K_new;
-    std::swap(cur, other);
-    t_done += chunk;
-    std::lock_guard<std::mutex> lk(mu);
-    st.candidates = total_cand;
-    st.unique = U;
-  }
+  if (dG0) H_TRY(mape_project_apply(dWproj, n, d, dG0, P, dZ, stream));
+  MAPE_CUDA_TRY(cudaMemsetAsync(dM, 0, sizeof(float) * (size_t)P * d, stream));
+  MAPE_CUDA_TRY(cudaMemsetAsync(dV, 0, sizeof(float) * (size_t)P * d, stream));
+  ex_U = 0;
+  ex_total = 0;
+  ex_done = 0;
+  ex_cur = dBuf0;
+  ex_other = dBuf1;
+  return MAPE_OK;
+}
+
+// The longest chunk from ex_done: it may hold as many collections (steps
+// whose number is a multiple of the period) as there is room for one row per
+// start each, and ends just before the first collection that would not fit.
+int mape_instance::extract_chunk_steps(int* chunk) const {
+  const int64_t room = cap - ex_U;
+  const int64_t fits = room / P;
+  const int64_t period = cfg.period;
+  const int64_t steps = (ex_done / period + fits + 1) * period - 1 - ex_done;
+  if (steps < 1) return MAPE_ERR_CAPACITY;
+  *chunk = (int)std::min<int64_t>(steps, cfg.T - ex_done);
+  return MAPE_OK;
+}
+
+// The arguments of the next `chunk` steps (counter and flags cleared).
+int mape_instance::extract_chunk_args(int chunk, mape_extract_args* a) {
+  MAPE_CUDA_TRY(cudaMemsetAsync(dCount, 0, sizeof(unsigned long long), stream));
+  MAPE_CUDA_TRY(cudaMemsetAsync(dFlags, 0, sizeof(int32_t), stream));
+  *a = mape_extract_args{};
+  a->n = n; a->d = d; a->P = P; a->B = dB; a->span = dspan; a->Z = dZ; a->M = dM; a->V = dV;
+  a->t0 = ex_done; a->T = chunk; a->period = cfg.period; a->precision = cfg.precision;
+  a->lambda1 = cfg.lambda1; a->lambda2 = cfg.lambda2; a->lr = cfg.lr; a->beta1 = cfg.beta1;
+  a->beta2 = cfg.beta2; a->eps = cfg.eps;
+  a->cand = ex_cur + ex_U * ldg; a->ldc = ldg; a->cand_cap = cap - ex_U; a->cand_count = dCount; a->flags = dFlags;
+  a->workspace = dWork; a->workspace_bytes = work_bytes;
+  return MAPE_OK;
+}
+
+// After the steps of a chunk: its candidates are merged into the distinct set.
+int mape_instance::extract_chunk_done(int chunk) {
+  cudaStream_t s = stream;
+  unsigned long long cnt = 0;
+  int32_t flags = 0;
+  MAPE_CUDA_TRY(cudaMemcpyAsync(&cnt, dCount, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+  MAPE_CUDA_TRY(cudaMemcpyAsync(&flags, dFlags, sizeof(flags), cudaMemcpyDeviceToHost, s));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(s));
+  if (flags & 1) return MAPE_ERR_CAPACITY;
+  ex_total += (int64_t)cnt;
+  int64_t K_new = 0;
+  H_TRY(mape_dedup(ex_cur, ex_U + (int64_t)cnt, n, ldg, ex_other, cap, &K_new, dWork, work_bytes, s));
+  ex_U = K_new;
+  std::swap(ex_cur, ex_other);
+  ex_done += chunk;
+  std::lock_guard<std::mutex> lk(mu);
+  st.candidates = ex_total;
+  st.unique = ex_U;
+  return MAPE_OK;
+}
+
+int mape_instance::extract_filter() {
+  cudaStream_t s = stream;
   double t_ext = now_ms();
   set_phase(MAPE_PHASE_FILTERING);
   int64_t fails = 0;
-  H_TRY(mape_kernel_test(dA, m, n, cur, U, ldg, dOk, &fails, dWork, work_bytes, s));
+  H_TRY(mape_kernel_test(dA, m, n, ex_cur, ex_U, ldg, dOk, &fails, dWork, work_bytes, s));
   int64_t Kk = 0;
   // the kept rows go to the buffer of the pair that the last merge left free
-  H_TRY(mape_minimal_filter(cur, U, n, ldg, dOk, dKeep, other, &Kk, dWork, work_bytes, s));
-  H_TRY(mape_direction_coeffs(dqr, dqc, dqv, nnz, has_w ? dw : nullptr, n, other, Kk, ldg, da, dq4, s));
+  H_TRY(mape_minimal_filter(ex_cur, ex_U, n, ldg, dOk, dKeep, ex_other, &Kk, dWork, work_bytes, s));
+  H_TRY(mape_direction_coeffs(dqr, dqc, dqv, nnz, has_w ? dw : nullptr, n, ex_other, Kk, ldg, da, dq4, s));
   MAPE_CUDA_TRY(cudaStreamSynchronize(s));
   double t_fil = now_ms();
-  dirs = other;
+  dirs = ex_other;
   K = Kk;
   std::lock_guard<std::mutex> lk(mu);
   st.kernel_failures = fails;
   st.directions = Kk;
-  st.extract_ms = t_ext - t_start;
+  st.extract_ms = t_ext - ex_start;
   st.filter_ms = t_fil - t_ext;
   return fails ? MAPE_ERR_KERNEL_TEST : MAPE_OK;
+}
+
+int mape_instance::run_extract() {
+  H_TRY(extract_begin());
+  while (ex_done < cfg.T) {
+    if (cancel.load()) return MAPE_ERR_CANCELLED;
+    int chunk = 0;
+    H_TRY(extract_chunk_steps(&chunk));
+    mape_extract_args a;
+    H_TRY(extract_chunk_args(chunk, &a));
+    H_TRY(mape_extract(&a, stream));
+    H_TRY(extract_chunk_done(chunk));
+  }
+  return extract_filter();
 }
 
 int mape_instance::run_augment(int64_t max_iters) {
@@ -441,9 +486,13 @@ extern "C" int mape_create_instance(const int32_t* A, const int64_t* b, const in
   return MAPE_OK;
 }
 
-extern "C" int mape_extract_directions(mape_handle h, int32_t P, const float* Z0, const float* G0) {
+namespace {
+
+// The buffers of an extraction job of P starts and the upload of its starts;
+// the handle must be idle.
+int prepare_job(mape_handle h, int32_t P, const float* Z0, const float* G0) {
   using namespace mape_detail;
-  if (!h || P <= 0 || (Z0 == nullptr) == (G0 == nullptr)) return MAPE_ERR_INVALID_ARG;
+  if (P <= 0 || (Z0 == nullptr) == (G0 == nullptr)) return MAPE_ERR_INVALID_ARG;
   if (!idle(h)) return MAPE_ERR_STATE;
   h->join();
   if (mape_extract_workspace_bytes(h->n, h->d, P, h->cfg.precision) == 0) return MAPE_ERR_SHAPE;
@@ -482,18 +531,120 @@ extern "C" int mape_extract_directions(mape_handle h, int32_t P, const float* Z0
   int rc = G0 ? upload(h, h->dG0, G0, sizeof(float) * (size_t)P * n) : upload(h, h->dZ, Z0, sizeof(float) * (size_t)P * d);
   if (rc) return rc;
   MAPE_CUDA_TRY(cudaStreamSynchronize(h->stream));
-  {
-    std::lock_guard<std::mutex> lk(h->mu);
-    h->busy = true;
-    h->st = mape_status{};
-    h->st.phase = MAPE_PHASE_EXTRACTING;
-  }
+  return MAPE_OK;
+}
+
+void mark_busy(mape_handle h) {
+  std::lock_guard<std::mutex> lk(h->mu);
+  h->busy = true;
+  h->st = mape_status{};
+  h->st.phase = MAPE_PHASE_EXTRACTING;
   h->cancel.store(false);
+}
+
+// A batch of extraction jobs: the first handle's worker runs the steps of
+// every handle, chunk by chunk, as one mape_extract_batch call each; the
+// other workers wait for it and then filter their own sets in parallel.
+struct ExtractBatch {
+  std::vector<mape_handle> hs;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool done = false;
+  int rc = MAPE_OK;
+  std::vector<int> rcs;  // per handle
+};
+
+int run_batch_steps(ExtractBatch& b) {
+  const int count = (int)b.hs.size();
+  for (int i = 0; i < count; ++i) {
+    mape_handle h = b.hs[i];
+    if (h->dev != b.hs[0]->dev) return MAPE_ERR_INVALID_ARG;
+    H_TRY(h->extract_begin());
+  }
+  for (auto h : b.hs) MAPE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  mape_handle h0 = b.hs[0];
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  std::vector<mape_extract_args> items((size_t)count);
+  while (h0->ex_done < h0->cfg.T) {
+    int chunk = h0->cfg.T - h0->ex_done;
+    for (auto h : b.hs) {
+      if (h->cancel.load()) return MAPE_ERR_CANCELLED;
+      int c = 0;
+      H_TRY(h->extract_chunk_steps(&c));
+      chunk = std::min(chunk, c);
+    }
+    for (int i = 0; i < count; ++i) H_TRY(b.hs[i]->extract_chunk_args(chunk, &items[(size_t)i]));
+    for (auto h : b.hs) MAPE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const size_t need = mape_extract_batch_workspace_bytes(items.data(), count);
+    if (need > ws_bytes) {
+      ws = h0->take<char>(h0->job_bufs, need);
+      if (!ws) return MAPE_ERR_OOM;
+      ws_bytes = need;
+    }
+    H_TRY(mape_extract_batch(items.data(), count, ws, ws_bytes, h0->stream));
+    for (auto h : b.hs) H_TRY(h->extract_chunk_done(chunk));
+  }
+  return MAPE_OK;
+}
+
+}  // namespace
+
+extern "C" int mape_extract_directions(mape_handle h, int32_t P, const float* Z0, const float* G0) {
+  if (!h) return MAPE_ERR_INVALID_ARG;
+  int rc = prepare_job(h, P, Z0, G0);
+  if (rc) return rc;
+  mark_busy(h);
   h->worker = std::thread([h]() {
     cudaSetDevice(h->dev);
     int r = h->run_extract();
     h->finish(r);
   });
+  return MAPE_OK;
+}
+
+extern "C" int mape_extract_directions_batch(mape_handle* hs, int32_t count, const int32_t* P, const float* const* Z0,
+                                             const float* const* G0) {
+  if (!hs || count <= 0 || !P) return MAPE_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return MAPE_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return MAPE_ERR_INVALID_ARG;
+    const mape_config& c = hs[i]->cfg;
+    const int32_t base = c.precision & MAPE_PREC_MASK;
+    if ((base != MAPE_PREC_BF16 && base != MAPE_PREC_BF16X1) || (c.precision & MAPE_PREC_SPARSE_FWD) ||
+        c.T != hs[0]->cfg.T || c.period != hs[0]->cfg.period ||
+        (c.precision & MAPE_PREC_MASK) != (hs[0]->cfg.precision & MAPE_PREC_MASK))
+      return MAPE_ERR_INVALID_ARG;
+    if (!idle(hs[i])) return MAPE_ERR_STATE;
+  }
+  for (int i = 0; i < count; ++i) {
+    int rc = prepare_job(hs[i], P[i], Z0 ? Z0[i] : nullptr, G0 ? G0[i] : nullptr);
+    if (rc) return rc;
+  }
+  auto b = std::make_shared<ExtractBatch>();
+  b->hs.assign(hs, hs + count);
+  for (int i = 0; i < count; ++i) mark_busy(hs[i]);
+  for (int i = 0; i < count; ++i) {
+    mape_handle h = hs[i];
+    h->worker = std::thread([h, b, i]() {
+      cudaSetDevice(h->dev);
+      int r = MAPE_OK;
+      if (i == 0) {
+        r = run_batch_steps(*b);
+        std::lock_guard<std::mutex> lk(b->mu);
+        b->rc = r;
+        b->done = true;
+        b->cv.notify_all();
+      } else {
+        std::unique_lock<std::mutex> lk(b->mu);
+        b->cv.wait(lk, [&] { return b->done; });
+        r = b->rc;
+      }
+      if (r == MAPE_OK) r = h->extract_filter();
+      h->finish(r);
+    });
+  }
   return MAPE_OK;
 }
 

@@ -207,7 +207,12 @@ extern "C" int mape_initial_solutions(const mape_init_args* a, void* stream) {
   p.a_smem = with_a <= kSmemLimit ? 1 : 0;
   const size_t smem = p.a_smem ? with_a : per_warp;
   if (smem > kSmemLimit) return MAPE_ERR_SHAPE;
-  MAPE_CUDA_TRY(cudaFuncSetAttribute(init_sol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    size_t lim = 0;
+    const int rc = allow_max_dynamic_smem((const void*)init_sol_kernel, &lim);
+    if (rc != MAPE_OK) return rc;
+    if ((size_t)smem > lim) return MAPE_ERR_SHAPE;
+  }
   launch(init_sol_kernel, (unsigned)ceil_div(P, kWarps), 32 * kWarps, smem, st, p);
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;

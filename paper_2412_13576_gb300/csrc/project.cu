@@ -272,7 +272,12 @@ extern "C" int mape_project_prepare(const int32_t* B, int32_t n, int32_t d, floa
   const unsigned g32 = (unsigned)ceil_div(d, 32);
   mape_detail::launch(transpose_lower_kernel, dim3(g32, g32), dim3(32, 8), 0, st, H, d, Lt);
   const size_t smem = (size_t)kSolveWarps * d * sizeof(float);
-  MAPE_CUDA_TRY(cudaFuncSetAttribute(w_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    size_t lim = 0;
+    const int rc = allow_max_dynamic_smem((const void*)w_solve_kernel, &lim);
+    if (rc != MAPE_OK) return rc;
+    if ((size_t)smem > lim) return MAPE_ERR_SHAPE;
+  }
   mape_detail::launch(w_solve_kernel, (unsigned)ceil_div(n, kSolveWarps), 32 * kSolveWarps, smem, st, B, H, Lt, n,
                       d, W);
   MAPE_LAUNCH_CHECK();

@@ -45,6 +45,8 @@ struct Request {
   int stage = 0;  // 1: extracting, 2: augmenting
   mape_handle h = nullptr;
   int slot = -1;
+  bool ready = false;  // batch mode: handle created, extraction not started yet
+  double t_ready = 0;
   double t_submit = 0, t_admit = 0, t_extracted = 0, t_first = 0, t_done = 0;
   // results
   int64_t directions = 0, best_f = 0, aug_iters = 0;
@@ -73,6 +75,7 @@ struct mape_server {
 
   void loop();
   void start(Request* r, int slot);
+  void start_batch(std::vector<Request*>& rs);
   void advance(Request* r);
   void finish(Request* r, int err);
 };
@@ -108,6 +111,11 @@ extern "C" int mape_server_create(const mape_server_config* sc, mape_server_h* o
   if (!out || !sc) return MAPE_ERR_INVALID_ARG;
   *out = nullptr;
   if (sc->max_slots <= 0 || sc->max_slots > 256 || sc->mem_cap_bytes == 0) return MAPE_ERR_INVALID_ARG;
+  if (sc->batch_extraction) {
+    const int32_t base = sc->cfg.precision & MAPE_PREC_MASK;
+    if ((base != MAPE_PREC_BF16 && base != MAPE_PREC_BF16X1) || (sc->cfg.precision & MAPE_PREC_SPARSE_FWD))
+      return MAPE_ERR_INVALID_ARG;
+  }
   auto* s = new mape_server();
   s->cfg = *sc;
   if (cudaGetDevice(&s->dev) != cudaSuccess) {
@@ -179,7 +187,7 @@ void mape_server::start(Request* r, int slot) {
   mape_handle h = nullptr;
   int rc = mape_create_instance(r->A.data(), r->b.data(), r->l.data(), r->u.data(), &f, r->B.data(), &cfg.cfg,
                                 streams[slot], &h);
-  if (rc == MAPE_OK)
+  if (rc == MAPE_OK && !cfg.batch_extraction)
     rc = mape_extract_directions(h, r->P, r->Z0.empty() ? nullptr : r->Z0.data(),
                                  r->G0.empty() ? nullptr : r->G0.data());
   std::lock_guard<std::mutex> lk(mu);
@@ -189,7 +197,35 @@ void mape_server::start(Request* r, int slot) {
     finish(r, rc);
     return;
   }
-  r->stage = 1;
+  if (cfg.batch_extraction) {  // the scheduler starts its extraction with the next batch
+    r->ready = true;
+    r->t_ready = clock_ms();
+  } else {
+    r->stage = 1;
+  }
+  cv.notify_all();
+}
+
+// Batch mode: the extraction of every request whose handle is ready runs as
+// one mape_extract_directions_batch call (one graph of persistent launches
+// per chunk of steps for all of them).  Called without the lock.
+void mape_server::start_batch(std::vector<Request*>& rs) {
+  std::vector<mape_handle> hs;
+  std::vector<int32_t> P;
+  std::vector<const float*> Z0, G0;
+  for (auto r : rs) {
+    hs.push_back(r->h);
+    P.push_back(r->P);
+    Z0.push_back(r->Z0.empty() ? nullptr : r->Z0.data());
+    G0.push_back(r->G0.empty() ? nullptr : r->G0.data());
+  }
+  const int rc = mape_extract_directions_batch(hs.data(), (int32_t)hs.size(), P.data(), Z0.data(), G0.data());
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto r : rs) {
+    if (rc != MAPE_OK) finish(r, rc);
+    else r->stage = 1;
+  }
+  --starting;
   cv.notify_all();
 }
 
@@ -255,6 +291,28 @@ void mape_server::loop() {
     for (auto& kv : reqs) {
       Request* r = kv.second.get();
       if (r->state == MAPE_REQ_RUNNING && r->h && r->stage > 0) advance(r);
+    }
+    // batch mode: the requests whose handles are ready start their extraction
+    // together, once no admitted request is still being set up or the oldest
+    // ready one has waited 5 ms
+    if (cfg.batch_extraction) {
+      std::vector<Request*> ready;
+      double oldest = 1e300;
+      for (auto& kv : reqs) {
+        Request* r = kv.second.get();
+        if (r->state == MAPE_REQ_RUNNING && r->ready) {
+          ready.push_back(r);
+          oldest = std::min(oldest, r->t_ready);
+        }
+      }
+      if (!ready.empty() && (starting == 0 || clock_ms() - oldest > 5.0)) {
+        for (auto r : ready) r->ready = false;
+        ++starting;  // the batch's uploads run on a thread of their own, like a request's set-up
+        std::thread([this, ready]() mutable {
+          cudaSetDevice(dev);
+          start_batch(ready);
+        }).detach();
+      }
     }
     // admission, in arrival order, while a slot and the memory allow
     while (!queue.empty()) {

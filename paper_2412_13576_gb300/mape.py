@@ -109,7 +109,8 @@ class Status(C.Structure):
 
 
 class ServerConfig(C.Structure):
-    _fields_ = [("cfg", Config), ("mem_cap_bytes", C.c_size_t), ("max_slots", I32), ("keep_directions", I32)]
+    _fields_ = [("cfg", Config), ("mem_cap_bytes", C.c_size_t), ("max_slots", I32), ("keep_directions", I32),
+                ("batch_extraction", I32), ("reserved", I32)]
 
 
 class RequestInfo(C.Structure):
@@ -170,6 +171,7 @@ _SIGS = {
     "mape_create_instance": (C.c_int, [P_, P_, P_, P_, C.POINTER(Problem), P_, C.POINTER(Config), P_,
                                        C.POINTER(P_)]),
     "mape_extract_directions": (C.c_int, [P_, I32, P_, P_]),
+    "mape_extract_directions_batch": (C.c_int, [C.POINTER(P_), I32, C.POINTER(I32), C.POINTER(P_), C.POINTER(P_)]),
     "mape_augment": (C.c_int, [P_, P_, I32, C.POINTER(Problem)]),
     "mape_poll": (C.c_int, [P_, C.POINTER(Status)]),
     "mape_wait": (C.c_int, [P_, I64]),
@@ -502,6 +504,31 @@ def _host(a):
     return None if a is None else C.c_void_p(a.ctypes.data)
 
 
+def extract_directions_batch(handles, starts):
+    """mape_extract_directions_batch: Algorithm 2 for several Instance handles
+    at once.  starts: one (P, Z0, G0) per handle (host float32 arrays, one of
+    Z0 / G0 None)."""
+    k = len(handles)
+    hs = (P_ * k)(*[h.h for h in handles])
+    Ps = (I32 * k)(*[int(P) for P, _, _ in starts])
+    keep = []
+
+    def arr(x):
+        if x is None:
+            return None
+        x = _np(x, np.float32)
+        keep.append(x)
+        return x.ctypes.data
+
+    Z = (P_ * k)(*[arr(z) for _, z, _ in starts])
+    G = (P_ * k)(*[arr(g) for _, _, g in starts])
+    for h, x in zip(handles, keep):
+        h._keep["batch_start"] = x
+    for h in handles:
+        h._keep["batch_starts_all"] = keep
+    _check(lib().mape_extract_directions_batch(hs, k, Ps, Z, G), "mape_extract_directions_batch")
+
+
 class Instance:
     """mape_create_instance ... mape_destroy over host arrays."""
 
@@ -645,10 +672,11 @@ class Server:
     instances on one GPU, admitted by device memory."""
 
     def __init__(self, cfg: Config | None = None, mem_cap_bytes: int = 150 << 30, max_slots: int = 8,
-                 keep_directions: bool = False):
+                 keep_directions: bool = False, batch_extraction: bool = False):
         sc = ServerConfig()
         sc.cfg = cfg if cfg is not None else default_config()
         sc.mem_cap_bytes, sc.max_slots, sc.keep_directions = int(mem_cap_bytes), int(max_slots), int(keep_directions)
+        sc.batch_extraction = int(batch_extraction)
         self.cfg = sc.cfg
         h = C.c_void_p()
         _check(lib().mape_server_create(C.byref(sc), C.byref(h)), "mape_server_create")

@@ -95,3 +95,65 @@ def test_batch_matches_oracle_collection(M):
         assert int(b["flags"].item()) == 0
         got = rows_set(b["cand"][: int(b["cand_count"].item())].cpu().numpy(), inst.n)
         assert got == e, inst.name
+
+
+def _batched_vs_single(M, cases, cfg):
+    single = []
+    for inst, Z0 in cases:
+        with M.Instance.from_generated(inst, cfg) as h:
+            h.extract_directions(Z0.shape[0], Z0=Z0)
+            h.wait(300)
+            h.augment(inst.xbar[None, :])
+            h.wait(300)
+            single.append((h.directions(), h.solution()))
+    handles = [M.Instance.from_generated(inst, cfg) for inst, _ in cases]
+    try:
+        M.extract_directions_batch(handles, [(Z0.shape[0], Z0, None) for _, Z0 in cases])
+        for h in handles:
+            h.wait(300)
+        for (inst, _), h, (D, (x, f)) in zip(cases, handles, single):
+            st = h.poll()
+            assert st["phase"] == "DONE" and st["error"] == 0
+            assert np.array_equal(h.directions(), D)
+            h.augment(inst.xbar[None, :])
+            h.wait(300)
+            x2, f2 = h.solution()
+            assert f2 == f and np.array_equal(x2, x)
+        return [h.poll() for h in handles]
+    finally:
+        for h in handles:
+            h.close()
+
+
+def test_batched_handles_equal_single_handles(M):
+    """mape_extract_directions_batch on eight handles (resident and streamed
+    shapes, identity-topped and general bases): every handle's direction set
+    equals the set of its own mape_extract_directions, and Algorithm 1 then
+    reaches the same point."""
+    sts = _batched_vs_single(M, _cases(), M.default_config(T=60, period=2))
+    assert sum(st["directions"] for st in sts) > 0
+
+
+def test_batched_handles_in_chunks(M):
+    """A candidate buffer of 2000 rows makes the extraction run in chunks (the
+    batch takes the shortest chunk any handle allows, and merges each
+    handle's candidates after every chunk): the sets still equal the single
+    handles'."""
+    inst = I.tiny_graver_case()
+    cases = [(inst, I.normal_starts(inst, 256, seed=700 + k).Z0) for k in range(3)]
+    sts = _batched_vs_single(M, cases, M.default_config(T=200, cand_capacity=2000))
+    assert all(st["candidates"] > 2000 for st in sts)
+
+
+def test_batched_handles_refuse_mixed_configs(M):
+    inst = I.small_dense()
+    h1 = M.Instance.from_generated(inst, M.default_config(T=10))
+    h2 = M.Instance.from_generated(inst, M.default_config(T=20))
+    try:
+        Z0 = I.normal_starts(inst, 64, seed=1).Z0
+        with pytest.raises(M.MapeError) as e:
+            M.extract_directions_batch([h1, h2], [(64, Z0, None), (64, Z0, None)])
+        assert e.value.code == -1
+    finally:
+        h1.close()
+        h2.close()

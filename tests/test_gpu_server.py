@@ -33,9 +33,10 @@ def _requests():
     return out
 
 
-def _run(M, reqs, slots):
+def _run(M, reqs, slots, batch=False):
     cfg = M.default_config(T=100)
-    with M.Server(cfg, mem_cap_bytes=64 << 30, max_slots=slots, keep_directions=True) as srv:
+    with M.Server(cfg, mem_cap_bytes=64 << 30, max_slots=slots, keep_directions=True,
+                  batch_extraction=batch) as srv:
         ids = [srv.submit(inst, 512, Z0=Z0) for inst, Z0 in reqs]
         srv.wait_all(900)
         res = [srv.result(i, directions=True) for i in ids]
@@ -44,14 +45,18 @@ def _run(M, reqs, slots):
     return res, infos, stats
 
 
-def test_server_alone_equals_mix(M):
+@pytest.mark.parametrize("batch", [False, True])
+def test_server_alone_equals_mix(M, batch):
+    """Alone (one slot, its own extraction) and mixed (four slots; with
+    batch_extraction the requests admitted together extract in one batched
+    call): the same direction sets, points and values."""
     reqs = _requests()
     alone = []
     for r in reqs:
         res, infos, stats = _run(M, [r], 1)
         assert infos[0]["state"] == "DONE", infos[0]
         alone.append(res[0])
-    mixed, infos, stats = _run(M, reqs, 4)
+    mixed, infos, stats = _run(M, reqs, 4, batch)
     assert stats["completed"] == len(reqs) and stats["failed"] == 0
     assert stats["peak_running"] > 1          # the requests overlapped on the device
     for (inst, _), (xa, fa, Ga), (xm, fm, Gm), info in zip(reqs, alone, mixed, infos):
