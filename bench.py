@@ -116,6 +116,32 @@ def reduce_over_ranks(units, ms, world):
     return float(u.item()), float(t.item())
 
 
+def row_hashes(D):
+    """64-bit hashes of the rows of an int8 direction set (FNV-1a over the
+    bytes), for counting distinct directions across ranks."""
+    import numpy as np
+    D = np.ascontiguousarray(D, dtype=np.int8).view(np.uint8)
+    h = np.full(D.shape[0], 0xcbf29ce484222325, dtype=np.uint64)
+    prime = np.uint64(0x100000001b3)
+    with np.errstate(over="ignore"):
+        for j in range(D.shape[1]):
+            h = (h ^ D[:, j].astype(np.uint64)) * prime
+    return h
+
+
+def distinct_over_ranks(hashes, world):
+    """(distinct rows over all ranks, total rows): the replicas run disjoint
+    start seeds, so the job's directions are the union of the ranks' sets."""
+    import numpy as np
+    if world == 1:
+        return int(np.unique(hashes).size), int(hashes.size)
+    import torch.distributed as dist
+    parts = [None] * world
+    dist.all_gather_object(parts, hashes)
+    allh = np.concatenate(parts)
+    return int(np.unique(allh).size), int(allh.size)
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -342,7 +368,7 @@ def e2e_passes(mape, wl, inst, starts_host, stream, reps, directions_hint, prec=
         units += D.shape[0]
         d2h = D.nbytes + x.nbytes + 8
     return {"value": units / sum(times), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "steps": len(times)}
+            "steps": len(times), "_last_directions": D}
 
 
 def run_ours(args):
@@ -380,6 +406,8 @@ def run_ours(args):
     value = units_all / (ms_max / 1e3)
     e2e = e2e_passes(mape, wl, inst, starts_host, stream, max(1, min(args.steps, 3)),
                      directions / max(args.steps, 1), prec)
+    # the union of the replicas' sets: rows counted once across ranks
+    distinct, rows = distinct_over_ranks(row_hashes(e2e.pop("_last_directions")), world)
 
     result = None
     if rank == 0:
@@ -394,6 +422,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2, and L2 flushed (256 MiB write) before each timed step",
                        "replicas_per_rank": 1},
             "directions_per_step": directions / args.steps,
+            "distinct_over_ranks": {"rows": rows, "distinct": distinct},
             "stages_ms": {k: statistics.median(s[k] for s in statuses)
                           for k in ("extract_ms", "filter_ms", "augment_ms", "first_improve_ms")},
             "candidates_per_step": statistics.median(s["candidates"] for s in statuses),
@@ -415,6 +444,7 @@ def run_ours(args):
             result["medium"] = medium_measure(mape, args, stream, flush)
         if args.batch > 0 and world == 1:
             result["batched"] = batch_measure(args.batch)
+            result["batched"]["pipeline"] = batch_pipeline_measure(args.batch)
         if args.serve > 0 and world == 1:
             result["serving"] = serve_measure(args.serve, args.serve_T, args.serve_plain)
     if world > 1:
@@ -450,8 +480,8 @@ def medium_measure(mape, args, stream, flush):
            "stages_ms": {k: statistics.median(s[k] for s in statuses)
                          for k in ("extract_ms", "filter_ms", "augment_ms", "first_improve_ms")},
            "best_f": statuses[-1]["best_f"], "gpu_launches": launches,
-           "e2e": e2e_passes(mape, wl, inst, starts_host, stream, max(1, min(args.steps, 3)),
-                             directions / max(args.steps, 1)),
+           "e2e": {k: v for k, v in e2e_passes(mape, wl, inst, starts_host, stream, max(1, min(args.steps, 3)),
+                                                directions / max(args.steps, 1)).items() if not k.startswith("_")},
            "roofline": roofline_resident(mape, wl, inst, starts_host[1], stream)}
     if not args.no_plain:
         out["vs_plain_fp32"] = plain_fp32(mape, wl, inst, starts, stream)
@@ -593,8 +623,8 @@ def serve_measure(N, T, n_plain=24, seed=3000):
     def starts(k):
         return pool_g0[k % len(pool)]
 
-    def run_server(cfg, slots, count):
-        with mape.Server(cfg, mem_cap_bytes=150 << 30, max_slots=slots) as srv:
+    def run_server(cfg, slots, count, batch):
+        with mape.Server(cfg, mem_cap_bytes=150 << 30, max_slots=slots, batch_extraction=batch) as srv:
             # warm-up: the smallest and the largest instance, 10 steps each (loads every kernel used)
             warm_cfg = mape.default_config(T=10, precision=cfg.precision)
             with mape.Server(warm_cfg, mem_cap_bytes=150 << 30, max_slots=2) as ws:
@@ -620,15 +650,25 @@ def serve_measure(N, T, n_plain=24, seed=3000):
         return infos, wall, stats, backlog
 
     out = {}
-    for name, prec, slots, count in (("served_bf16", PREC["bf16"], 16, N),
-                                     ("plain_fp32_one_at_a_time", 0, 1, min(n_plain, N))):
+    for name, prec, slots, count, batch in (("served_bf16", PREC["bf16"], 16, N, True),
+                                            ("served_bf16_slot_streams", PREC["bf16"], 16, N, False),
+                                            ("plain_fp32_one_at_a_time", 0, 1, min(n_plain, N), False)):
         cfg = mape.default_config(T=T, precision=prec)
-        infos, wall, stats, backlog = run_server(cfg, slots, count)
+        infos, wall, stats, backlog = run_server(cfg, slots, count, batch)
         ok = [i for i in infos if i["state"] == "DONE"]
         ttfid = [i["t_first_improve_ms"] - i["t_submit_ms"] for i in ok]
         ttt = [i["t_done_ms"] - i["t_submit_ms"] for i in ok]
+        errors = {}
+        for i in infos:
+            if i["state"] != "DONE":
+                key = f"{mape.ERR.get(i['error'], i['error'])}"
+                errors[key] = errors.get(key, 0) + 1
+        if errors:
+            errors["last_cuda_error"] = mape.lib().mape_last_cuda_error().decode()
         out[name] = {"requests": count, "instances_per_s": len(ok) / wall, "wall_s": wall, "completed": len(ok),
-                     "failed": len(infos) - len(ok), "arrival_rate": SERVE_RATE,
+                     "failed": len(infos) - len(ok), "errors": errors,
+                     "failed_n": sorted(i["n"] for i in infos if i["state"] != "DONE")[:20],
+                     "arrival_rate": SERVE_RATE,
                      "arrivals_span_s": float(arrivals[count - 1]),
                      "ttfid_ms_p50": _pct(ttfid, 50), "ttfid_ms_p99": _pct(ttfid, 99),
                      "ttt_ms_p50": _pct(ttt, 50), "ttt_ms_p99": _pct(ttt, 99),
@@ -638,7 +678,8 @@ def serve_measure(N, T, n_plain=24, seed=3000):
                      "best_f": [i["best_f"] for i in infos]}
     a, b = out["served_bf16"]["best_f"], out["plain_fp32_one_at_a_time"]["best_f"]
     out["f_not_worse_than_plain"] = float(np.mean([x <= y for x, y in zip(a, b)]))
-    for k in ("served_bf16", "plain_fp32_one_at_a_time"):
+    out["batched_equals_slot_streams"] = bool(out["served_bf16"]["best_f"] == out["served_bf16_slot_streams"]["best_f"])
+    for k in ("served_bf16", "served_bf16_slot_streams", "plain_fp32_one_at_a_time"):
         out[k].pop("best_f")
     s = out["served_bf16"]
     s["saturated"] = s["instances_per_s"] < 0.95 * SERVE_RATE
@@ -727,8 +768,49 @@ def batch_measure(N, T=1000, seed=1003):
                          f"projected uniform starts; T = {T}; a3-a8 only")}
 
 
+def batch_pipeline_measure(N, T=1000, seed=1003):
+    """The batched configuration end to end: the same N uneven instances as
+    batch_measure, submitted at once to the request server (64 slots, 150 GB
+    cap), each through Algorithm 2, dedup, the kernel test, the minimality
+    filter, the coefficients and Algorithm 1 from xbar; once with the
+    extraction of the requests admitted together run as one batched call
+    (batch_extraction) and once with each request on its own slot stream.
+    Reports instances/s and p50/p99 time to first improving direction and to
+    termination."""
+    import numpy as np
+    from paper_2412_13576_gb300 import instances as I
+    from paper_2412_13576_gb300 import mape
+    rng = np.random.default_rng(seed + 1000)
+    insts = I.uneven_batch(count=N, n_lo=50, n_hi=1000, seed=seed)
+    Ps = rng.choice([1024, 4096, 16384], size=N)
+    G0s = [I.uniform_samples(inst, int(P), seed=seed + 2000 + k).G0 for k, (inst, P) in enumerate(zip(insts, Ps))]
+    out = {}
+    for name, batch in (("batched_extraction", True), ("slot_streams", False)):
+        cfg = mape.default_config(T=T, precision=PREC["bf16"])
+        with mape.Server(cfg, mem_cap_bytes=150 << 30, max_slots=64, batch_extraction=batch) as srv:
+            t0 = time.perf_counter()
+            ids = [srv.submit(inst, int(P), G0=G0) for inst, P, G0 in zip(insts, Ps, G0s)]
+            srv.wait_all(3600)
+            wall = time.perf_counter() - t0
+            infos = [srv.info(i) for i in ids]
+            stats = srv.stats()
+        ok = [i for i in infos if i["state"] == "DONE"]
+        ttfid = [i["t_first_improve_ms"] - i["t_submit_ms"] for i in ok]
+        ttt = [i["t_done_ms"] - i["t_submit_ms"] for i in ok]
+        out[name] = {"instances_per_s": len(ok) / wall, "wall_s": wall, "completed": len(ok),
+                     "failed": len(infos) - len(ok), "ttfid_ms_p50": _pct(ttfid, 50), "ttfid_ms_p99": _pct(ttfid, 99),
+                     "ttt_ms_p50": _pct(ttt, 50), "ttt_ms_p99": _pct(ttt, 99),
+                     "directions": sum(i["directions"] for i in ok), "peak_running": stats["peak_running"],
+                     "best_f": [i["best_f"] for i in infos]}
+    a, b = out["batched_extraction"].pop("best_f"), out["slot_streams"].pop("best_f")
+    out["same_f"] = bool(a == b)
+    out["workload"] = (f"uneven_batch(count={N}, n in [50,1000], seed {seed}); P from {{1024,4096,16384}}; projected "
+                       f"uniform starts; T = {T}; the whole path per instance, all submitted at once")
+    return out
+
+
 RESIDENT_TRAFFIC = os.path.join(ROOT, "profiles", "extract_tc_kernel_medium_sparse_P8192_T1000_traffic.md")
-STREAM_TRAFFIC = os.path.join(ROOT, "profiles", "stream_grad_kernel_large_quartic_traffic.md")
+STREAM_TRAFFIC = os.path.join(ROOT, "profiles", "stream_step_large_quartic_traffic.md")
 
 
 def measured_traffic(record, src_path):
@@ -749,14 +831,19 @@ def measured_traffic(record, src_path):
 
 
 def roofline_streamed(mape, wl, inst, starts, stream, prec, reps=2):
-    """The streamed kernels of the large workload, timed live: `reps` calls of
-    mape_extract (T steps, the workload's starts and period) with the
-    library's per-launch CUDA events on the call's stream.  The dominant
-    kernel is the gradient + Adam pass: per start-step it reads sign(Bm z)
-    (2 R bytes, BF16) and reads and writes z, m, v (24 d bytes, FP32), so its
-    algorithmic bytes per launch are (24 d + 2 R) P; the forward pass reads z
-    and writes sign(Bm z) ((4 d + 2 R) P).  The bound is HBM bandwidth: the
-    state (1.26 GB) is far larger than L2 and is streamed every step."""
+    """The streamed extraction of the large workload, timed live: `reps` calls
+    of mape_extract (T steps, the workload's starts and period) with the
+    library's per-launch CUDA events on the launches' streams.  A step is the
+    forward pass (reads z, writes sign(Bm z): (4 d + 2 R) bytes per start) and
+    the gradient + Adam pass (reads sign(Bm z) and reads and writes z, m, v:
+    (24 d + 2 R) bytes per start); the tiles run as two halves on two
+    streams, so that one half's forward pass overlaps the other's gradient
+    pass.  The unit of the roofline is therefore the step, both kernels
+    together: (28 d + 4 R) P bytes per step over the step's time (the call's
+    time over T, which includes packing z, m, v once per call).  The bound is
+    HBM bandwidth: the state (1.26 GB) is far larger than L2 and is streamed
+    every step.  The per-kernel launch durations are reported beside it; they
+    overlap in time."""
     import numpy as np
     peaks, src = measured_peaks()
     P, T, d = wl["P"], wl["T"], inst.d
@@ -768,34 +855,34 @@ def roofline_streamed(mape, wl, inst, starts, stream, prec, reps=2):
         per = mape.launch_timing_read()
     finally:
         mape.launch_timing(False)
-    ms_grad = per["stream_grad"][0] / max(per["stream_grad"][1], 1)
-    ms_fwd = per["stream_fwd"][0] / max(per["stream_fwd"][1], 1)
-    ms_coll = per["stream_collect"][0] / max(per["stream_collect"][1], 1)
-    bytes_grad = (24.0 * d + 2.0 * R) * P
-    bytes_fwd = (4.0 * d + 2.0 * R) * P
-    gbs = bytes_grad / (ms_grad / 1e3) / 1e9
     peak = peaks["hbm_gbs"]
     call_ms = statistics.median(times)
+    step_ms = call_ms / T
     step_bytes = (28.0 * d + 4.0 * R) * P
+    achieved = step_bytes / (step_ms / 1e3) / 1e9
+    kernels = {}
+    for kind, name, per_start in (("stream_grad", "stream_grad_kernel", 24.0 * d + 2.0 * R),
+                                  ("stream_fwd", "stream_fwd_sparse_kernel" if prec & mape.PREC_SPARSE_FWD
+                                   else "stream_fwd_kernel", 4.0 * d + 2.0 * R)):
+        ms, n = per[kind]
+        launches_per_step = max(1, round(n / ((reps + 1) * T)))  # two with the tile halves; reps + 1 calls ran
+        b = per_start * P / launches_per_step
+        kernels[name] = {"ms_per_launch": ms / max(n, 1), "launches_per_step": launches_per_step,
+                         "bytes_per_launch": b, "achieved": b / (ms / max(n, 1) / 1e3) / 1e9,
+                         "frac_while_overlapped": b / (ms / max(n, 1) / 1e3) / 1e9 / peak}
     src_path = os.path.join(ROOT, "paper_2412_13576_gb300", "csrc", "extract_stream.cu")
-    return {"bound": "hbm", "kernel": "stream_grad_kernel", "achieved": gbs, "peak": peak, "unit": "GB/s",
-            "frac": gbs / peak, "traffic": measured_traffic(STREAM_TRAFFIC, src_path),
-            "ms_per_launch": ms_grad, "bytes_per_launch": bytes_grad,
+    return {"bound": "hbm", "kernel": "streamed step: stream_fwd_kernel and stream_grad_kernel, tile halves on two streams",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": measured_traffic(STREAM_TRAFFIC, src_path), "ms_per_step": step_ms, "bytes_per_step": step_bytes,
             "peak_source": f"{src} HBM copy rate (MEASURED_PEAKS.json hbm_gbs)",
-            "launches_timed": per["stream_grad"][1],
-            "forward": {"kernel": "stream_fwd_sparse_kernel" if prec & mape.PREC_SPARSE_FWD else "stream_fwd_kernel",
-                        "ms_per_launch": ms_fwd, "bytes_per_launch": bytes_fwd,
-                        "achieved": bytes_fwd / (ms_fwd / 1e3) / 1e9,
-                        "frac": bytes_fwd / (ms_fwd / 1e3) / 1e9 / peak},
-            "collect_ms_per_launch": ms_coll, "collect_launches": per["stream_collect"][1],
-            "step": {"ms": call_ms / T, "bytes": step_bytes, "achieved": step_bytes * T / (call_ms / 1e3) / 1e9,
-                     "frac": step_bytes * T / (call_ms / 1e3) / 1e9 / peak,
-                     "note": "one step = forward + gradient (+ collection every period-th step), 28 d + 4 R bytes "
-                             "per start; the call also packs z, m, v into the blocked layout and back once"},
+            "kernels": kernels,
+            "collect_ms_per_launch": per["stream_collect"][0] / max(per["stream_collect"][1], 1),
             "candidates_per_call": int(np.median(counts)),
-            "note": "launch durations from CUDA events recorded by the library around each launch on the "
-                    "extraction stream, over T = 1000 steps for P = 65536 starts; traffic = ncu dram read+write "
-                    "bytes per launch, null unless taken on this source"}
+            "note": "one step = forward + gradient (+ collection every period-th step) for P = 65536 starts, 28 d + 4 R "
+                    "bytes per start; step time = CUDA-event time of a T = 1000 call / T (the call also packs z, m, v "
+                    "once); kernel launch durations from events the library records around each launch on its "
+                    "stream; traffic = ncu dram read+write bytes of one step (both kernels), null unless taken on "
+                    "this source"}
 
 
 def roofline_resident(mape, wl, inst, G0, stream, reps=3):
