@@ -6,8 +6,12 @@ m = 400, A = [C | I] with C 400x1600 in [-5,5] at density 0.01, box
 [-20,20], f = x'Qx + c'x + sum w_i x_i^4 with Q in [-5,5] at 0.005 and w in
 [0,3]; P = 65536 starts Z0 ~ N(0, 2), T = 1000 Adam steps, the rounded
 iterate collected every 50th step): Algorithm 2 on the streamed tensor-core
-kernels, dedup, the kernel test, the minimality filter, the direction
-coefficients and Algorithm 1 from xbar, all through the instance handle.
+kernels, the forward product B z in e4m3 with a power-of-two scale per start
+(the workload's stated precision; the gradient product and the exact map
+B round(z) in BF16, FP32 accumulation and state), dedup, the kernel test,
+the minimality filter, the direction coefficients and Algorithm 1 from xbar,
+all through the instance handle.  The same pass in BF16 (z as hi + lo
+terms) is reported beside it under "bf16".
 value = directions that pass C1, C4, nonzero and set-minimality, summed over
 the timed steps and ranks, over the max-over-ranks device time of those
 steps.  Inputs are resident in device memory; they are larger than L2
@@ -47,7 +51,8 @@ LARGE = dict(name="large", n=2000, m=400, P=65536, T=1000, period=50, std=2.0, s
 WORKLOAD = ("large_quartic: n=2000 m=400 d=1600, A=[C|I_400], C 400x1600 in [-5,5] at density 0.01, box [-20,20], "
             "f = x'Qx + c'x + sum w_i x_i^4 with Q sym in [-5,5] at 0.005, c in [-20,20], w in [0,3]; P=65536 starts "
             "Z0 ~ N(0,2), T=1000 Adam steps (lr 0.003, lambda1 0.85, lambda2 1), collection every 50th step; "
-            "streamed BF16 tensor-core kernels; Algorithm 1 from xbar")
+            "streamed tensor-core kernels, B z in e4m3 with per-start scales, B^T sign and B round(z) in BF16; "
+            "Algorithm 1 from xbar")
 MEDIUM = dict(name="medium", n=200, m=40, P=8192, T=1000, period=1, std=None, seed=2002)
 MEDIUM_WORKLOAD = ("medium_sparse: n=200 m=40 d=160, A=[C|I_40], C 40x160 in [-3,3] at density 0.1, box [0,10], "
                    "Q sym in [-5,5] at 0.05, c in [-20,20]; P=8192 projected Uniform(l-u,u-l) starts, T=1000 Adam "
@@ -63,7 +68,10 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["bf16", "bf16x1", "fp32", "sparse", "fp8"], default="bf16")
+    ap.add_argument("--precision", choices=["bf16", "bf16x1", "fp32", "sparse", "fp8"], default="fp8",
+                    help="precision of the large workload's extraction (default: e4m3 forward product)")
+    ap.add_argument("--no-bf16-pass", action="store_true",
+                    help="skip the BF16 comparison passes of the large workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run (medium workload)")
     ap.add_argument("--no-medium", action="store_true", help="skip the medium-workload measurement")
@@ -415,7 +423,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"bf16": "bf16", "bf16x1": "bf16", "fp32": "f32", "sparse": "f32", "fp8": "fp8+bf16"}[args.precision],
+            "dtype": {"bf16": "bf16", "bf16x1": "bf16", "fp32": "f32", "sparse": "f32",
+                      "fp8": "fp8_e4m3+bf16"}[args.precision],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "P": wl["P"], "T": wl["T"], "n": wl["n"], "m": wl["m"],
                        "period": wl["period"], "precision": args.precision + ("+sparse_fwd" if args.sparse_fwd else ""),
@@ -433,6 +442,8 @@ def run_ours(args):
             "e2e": e2e,
         }
         result["roofline"] = roofline_streamed(mape, wl, inst, starts, stream, prec)
+        if args.precision == "fp8" and not args.no_bf16_pass:
+            result["bf16"] = bf16_passes(mape, wl, inst, starts, stream, flush)
         if not args.no_cpu_baseline and world == 1:
             # before the serving measurement, whose host threads and arrays would share the cores
             pool = OraclePool()
@@ -451,6 +462,17 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return result
+
+
+def bf16_passes(mape, wl, inst, starts, stream, flush, steps=2, warmup=1):
+    """The same handle passes with the extraction in BF16 (z as hi + lo
+    terms, every product on BF16 operands): the comparison for the e4m3
+    forward product."""
+    total_ms, statuses, _ = handle_passes(mape, wl, inst, starts, stream, steps, warmup, PREC["bf16"], flush)
+    directions = sum(st["directions"] for st in statuses)
+    return {"value": directions / (total_ms / 1e3), "unit": UNIT, "ms_per_step": total_ms / steps,
+            "steps": steps, "directions_per_step": directions / steps,
+            "extract_ms": statistics.median(s["extract_ms"] for s in statuses), "best_f": statuses[-1]["best_f"]}
 
 
 def _f_value(inst, x):
@@ -650,8 +672,8 @@ def serve_measure(N, T, n_plain=24, seed=3000):
         return infos, wall, stats, backlog
 
     out = {}
-    for name, prec, slots, count, batch in (("served_bf16", PREC["bf16"], 16, N, True),
-                                            ("served_bf16_slot_streams", PREC["bf16"], 16, N, False),
+    for name, prec, slots, count, batch in (("served_bf16", PREC["bf16"], 16, N, False),
+                                            ("served_bf16_batched_extraction", PREC["bf16"], 16, N, True),
                                             ("plain_fp32_one_at_a_time", 0, 1, min(n_plain, N), False)):
         cfg = mape.default_config(T=T, precision=prec)
         infos, wall, stats, backlog = run_server(cfg, slots, count, batch)
@@ -678,8 +700,9 @@ def serve_measure(N, T, n_plain=24, seed=3000):
                      "best_f": [i["best_f"] for i in infos]}
     a, b = out["served_bf16"]["best_f"], out["plain_fp32_one_at_a_time"]["best_f"]
     out["f_not_worse_than_plain"] = float(np.mean([x <= y for x, y in zip(a, b)]))
-    out["batched_equals_slot_streams"] = bool(out["served_bf16"]["best_f"] == out["served_bf16_slot_streams"]["best_f"])
-    for k in ("served_bf16", "served_bf16_slot_streams", "plain_fp32_one_at_a_time"):
+    out["batched_equals_slot_streams"] = bool(out["served_bf16"]["best_f"] ==
+                                              out["served_bf16_batched_extraction"]["best_f"])
+    for k in ("served_bf16", "served_bf16_batched_extraction", "plain_fp32_one_at_a_time"):
         out[k].pop("best_f")
     s = out["served_bf16"]
     s["saturated"] = s["instances_per_s"] < 0.95 * SERVE_RATE

@@ -128,15 +128,22 @@ __device__ __forceinline__ float f8_scale(const StParams& p, int s, int64_t pg) 
 // handed over through the ready barrier (one arrival per converter warp), so
 // the conversion of chunk c + 1 runs while the MMAs of chunk c are issued.
 template <bool kId>
-__device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk, int s, int fwd, int collect) {
+// merged (FP8 forward steps without collection, at most two row blocks):
+// one CTA per tile multiplies every row block of Bm (N0 = wF rows into TMEM
+// columns [0, wF), the rest after them), so that z is read and converted
+// once per tile instead of once per row block.
+__device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk, int s, int fwd, int collect,
+                                                int merged = 0) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t bars[8];  // full[2] (Bm copy), done[2] (MMAs), zfull[2] (z copy), ready[2]
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool conv = tid < kThreads;
-  const int tile = p.tile0 + blk / p.nbF, rb = blk % p.nbF;
-  const int N = rb < p.nbF - 1 ? p.wF : p.R64 - p.wF * (p.nbF - 1);
+  const int nbl = merged ? 1 : p.nbF;  // CTAs per tile in this launch
+  const int tile = p.tile0 + blk / nbl, rb = merged ? 0 : blk % nbl;
+  const int N = merged ? p.R64 : (rb < p.nbF - 1 ? p.wF : p.R64 - p.wF * (p.nbF - 1));
+  const int N0 = merged ? p.wF : N, N1 = N - N0;  // merged: the two row blocks' widths
   const int row0 = rb * p.wF;
   const int fstage = fwd_stage(p.wF);
   const uint32_t fcols = (uint32_t)tmem_cols(2 * p.wF);  // D1 at 0, D2 at wF
@@ -193,7 +200,12 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
   auto copy_bm = [&](int c) {
     const int stg = c & 1;
     uint8_t* Bc = smem + stg * fstage + 3 * kChunkA;
-    if (p.f8) {  // e4m3 chunk (N x 64 bytes) in the stage's unused lo slot; BF16 chunk only for D2
+    if (merged) {  // both row blocks' e4m3 chunks, one after the other from the lo slot on
+      mbar_arrive_expect_tx(full0 + 8 * stg, (uint32_t)N * kKC);
+      bulk_g2s(smem_u32(Bc - 2 * kChunkA), p.BmF8 + (size_t)c * N0 * kKC, (uint32_t)N0 * kKC, full0 + 8 * stg);
+      bulk_g2s(smem_u32(Bc - 2 * kChunkA + N0 * kKC), p.BmF8 + (size_t)p.wF * p.d64 + (size_t)c * N1 * kKC,
+               (uint32_t)N1 * kKC, full0 + 8 * stg);
+    } else if (p.f8) {  // e4m3 chunk (N x 64 bytes) in the stage's unused lo slot; BF16 chunk only for D2
       const bool b16 = collect != 0, b8 = fwd != 0;
       mbar_arrive_expect_tx(full0 + 8 * stg, (uint32_t)N * kKC * ((b16 ? 2 : 0) + (b8 ? 1 : 0)));
       if (b8)
@@ -292,7 +304,16 @@ __device__ __forceinline__ void stream_fwd_body(const StParams& p, const int blk
         break;
       }
       tc_fence_after();
-      if (p.f8 && fwd) {  // D1 in e4m3: K = 32 per instruction, two per chunk
+      if (merged) {  // D1 of both row blocks in e4m3
+        const uint32_t B8 = A0 + kChunkA;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          const uint64_t a = make_desc(A0 + kk * 256, kChunkLbo, kChunk8Sbo);
+          mma_e4m3(tmem, a, make_desc(B8 + kk * 256, kChunkLbo, kChunk8Sbo), idesc_e4m3(kTM, N0), (c | kk) ? 1u : 0u);
+          mma_e4m3(tmem + (uint32_t)N0, a, make_desc(B8 + N0 * kKC + kk * 256, kChunkLbo, kChunk8Sbo),
+                   idesc_e4m3(kTM, N1), (c | kk) ? 1u : 0u);
+        }
+      } else if (p.f8 && fwd) {  // D1 in e4m3: K = 32 per instruction, two per chunk
         const uint32_t B8 = A0 + kChunkA;
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk)
@@ -811,8 +832,9 @@ __device__ __forceinline__ void stream_grad_body(const StParams& p, const int bl
 // ---------------------------------------------------------------- launch wrappers
 
 template <bool kId>
-__global__ void __launch_bounds__(kThreadsF, 1) stream_fwd_kernel(StParams p, int s, int fwd, int collect) {
-  stream_fwd_body<kId>(p, blockIdx.x, s, fwd, collect);
+__global__ void __launch_bounds__(kThreadsF, 1) stream_fwd_kernel(StParams p, int s, int fwd, int collect,
+                                                                   int merged) {
+  stream_fwd_body<kId>(p, blockIdx.x, s, fwd, collect, merged);
 }
 template <bool kId>
 __global__ void stream_collect_kernel(StParams p, int s) {
@@ -1363,8 +1385,12 @@ int extract_stream_widths(const mape_extract_args* a, cudaStream_t st, int wF, i
     const int64_t starts = std::min<int64_t>(P, (int64_t)(t0 + nt) * kTM) - (int64_t)t0 * kTM;
     H[hh].gC = (unsigned)ceil_div(std::max<int64_t>(starts, 1), 8);
   }
+  // FP8 steps without collection: one CTA per tile over both row blocks
+  const bool can_merge = p.f8 && sh.nbF == 2 && sh.wF == kNB && sh.R64 <= 2 * kNB;
   auto fwd = [&](const Half& h, int s, int f, int col) {
-    timed_launch(MAPE_TIMED_STREAM_FWD, h.st, [&] { launch(fwdk, h.gF, kThreadsF, fsm, h.st, h.p, s, f, col); });
+    const int merged = (can_merge && f && !col) ? 1 : 0;
+    const unsigned g = merged ? h.gF / (unsigned)sh.nbF : h.gF;
+    timed_launch(MAPE_TIMED_STREAM_FWD, h.st, [&] { launch(fwdk, g, kThreadsF, fsm, h.st, h.p, s, f, col, merged); });
   };
   auto coll = [&](const Half& h, int s) {
     timed_launch(MAPE_TIMED_STREAM_COLLECT, h.st, [&] { launch(collk, h.gC, 256, 0, h.st, h.p, s); });

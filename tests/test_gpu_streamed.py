@@ -178,11 +178,14 @@ def test_fp8_rejects_basis_not_exact_in_e4m3(M):
                                                            (_general_basis(I.small_dense), 300, 15, 1, True, None, 0),
                                                            (uneven1000, 300, 12, 2, False, 0.3, 0),
                                                            (uneven1000, 300, 12, 2, False, 0.3, SPARSE_FWD),
-                                                           (uneven1000, 300, 12, 2, False, 0.3, "fp8")])
+                                                           (uneven1000, 300, 12, 2, False, 0.3, "fp8"),
+                                                           (I.large_quartic, 300, 8, 3, False, 0.3, "fp8")])
 def test_streamed_one_call_equals_single_steps(M, make, P, T, period, force, std, fwd):
     """T steps in one call give bitwise the same Z, M, V as T calls of one
     step, and the same set of collected directions (uneven1000: with the
-    tensor-core, the sparse and the FP8 forward)."""
+    tensor-core, the sparse and the FP8 forward; large_quartic in FP8, where
+    the steps without collection multiply both row blocks of Bm in one CTA
+    per tile and the collecting steps one CTA per row block)."""
     import torch
     inst = make()
     Z0 = _z0(inst, P, 7, std)
