@@ -256,7 +256,8 @@ typedef struct {
 } mape_tune_info;
 /* The autotuned choice for a shape, or STATE if none was made yet. */
 int mape_autotune_lookup(int32_t n, int32_t d, int32_t P, int32_t precision, mape_tune_info* out);
-/* Forgets every autotuned choice of the process. */
+/* Forgets every autotuned choice of the process (extraction paths and the
+ * lane counts of the augmentation scoring pass). */
 void mape_autotune_clear(void);
 
 /* a10 -- set union of Algorithm 2: removes repeated rows of `cand` (count
@@ -300,6 +301,34 @@ int mape_dedup_static(const int8_t* cand, int64_t count, int32_t n, int32_t ldc,
                       int8_t* uniq, int64_t uniq_cap, int64_t* K_out,
                       void* stream);
 
+/* a10 for many candidate sets at once (the sets of a batch of instances):
+ * item i is one mape_dedup call -- its own rows, count, n, ldc, output and
+ * workspace of mape_dedup_workspace_bytes(count, ldc) -- and gets the same
+ * output and K.  Every kernel of the stage runs once over the rows of all
+ * sets (hash, insert, compaction, keys, the bitonic stages, the run sorts,
+ * the gather), each thread, warp or block finding its set by binary search
+ * over the launch's prefix table; `workspace` holds the batch's tables
+ * (mape_dedup_batch_workspace_bytes(count)).  Per item: K (distinct rows)
+ * and status (MAPE_OK, or CAPACITY when they exceed uniq_cap: nothing is
+ * then written for that item, as in mape_dedup).  Returns the first item's
+ * error, else INVALID_ARG / SHAPE for bad arguments (checked before any
+ * device work) or CUDA.  Synchronous. */
+typedef struct {
+  const int8_t* cand;       /* [count x ldc] device                          */
+  int64_t count;
+  int32_t n, ldc;
+  int8_t* uniq;             /* [uniq_cap x ldc] device                       */
+  int64_t uniq_cap;
+  int64_t K;                /* out: distinct rows                            */
+  int32_t status;           /* out                                           */
+  int32_t pad0;
+  void* workspace;
+  size_t workspace_bytes;
+} mape_dedup_item;
+size_t mape_dedup_batch_workspace_bytes(int32_t count);
+int mape_dedup_batch(mape_dedup_item* items, int32_t count, void* workspace,
+                     size_t workspace_bytes, void* stream);
+
 /* a9 -- condition C1 (§3): ok[k] = 1 iff A g_k = 0 exactly.
  *   A [m x n] int32 (row-major, device), G [K x ldg] int8 (ldg a multiple of
  *   16, at most 4096).  *fail_count = rows with A g != 0.
@@ -316,6 +345,32 @@ size_t mape_kernel_test_workspace_bytes(int32_t m, int32_t n);
 int mape_kernel_test(const int32_t* A, int32_t m, int32_t n, const int8_t* G,
                      int64_t K, int32_t ldg, uint8_t* ok, int64_t* fail_count,
                      void* workspace, size_t workspace_bytes, void* stream);
+
+/* a9 for many instances at once: item i is one mape_kernel_test call (its
+ * own A, G, flags and workspace of mape_kernel_test_workspace_bytes(m, n))
+ * and gets the same flags and fail_count.  Every A goes to compressed rows
+ * in its workspace (two launches over the rows of all the A's and one scan
+ * block per instance), then one launch tests the rows of all instances, a
+ * warp per row (the compressed-row product, exact for every int32 A).
+ * `workspace` holds the batch's tables
+ * (mape_kernel_test_batch_workspace_bytes(count)).  Errors: INVALID_ARG,
+ * SHAPE as mape_kernel_test for any item (before any device work),
+ * CAPACITY, CUDA.  Synchronous. */
+typedef struct {
+  const int32_t* A;         /* [m x n] int32 device                          */
+  int32_t m, n;
+  const int8_t* G;          /* [K x ldg] int8 device                         */
+  int64_t K;
+  int32_t ldg, pad0;
+  uint8_t* ok;              /* [K] out                                       */
+  int64_t fail_count;       /* out                                           */
+  void* workspace;
+  size_t workspace_bytes;
+} mape_kernel_test_item;
+size_t mape_kernel_test_batch_workspace_bytes(int32_t count);
+int mape_kernel_test_batch(mape_kernel_test_item* items, int32_t count,
+                           void* workspace, size_t workspace_bytes,
+                           void* stream);
 
 /* a11 -- condition C3 within the set: keep[k] = 1 iff no other row h (with
  * valid[h] != 0) satisfies h ⊑ g_k or -h ⊑ g_k, where x ⊑ y iff
@@ -340,6 +395,28 @@ int mape_direction_coeffs(const int32_t* q_row, const int32_t* q_col,
                           int32_t n, const int8_t* G, int64_t K, int32_t ldg,
                           int64_t* a, int64_t* q4, void* stream);
 
+/* a12 for many instances at once: item i is one mape_direction_coeffs call
+ * and gets the same a and q4; one launch, a warp per direction of any
+ * instance.  `workspace`: mape_direction_coeffs_batch_workspace_bytes(count).
+ * Errors: INVALID_ARG, SHAPE as mape_direction_coeffs for any item, CAPACITY,
+ * CUDA.  Asynchronous (the items are copied before the call returns). */
+typedef struct {
+  const int32_t* q_row;
+  const int32_t* q_col;
+  const int32_t* q_val;
+  int32_t nnz, n;
+  const int32_t* w;         /* NULL: no quartic term                         */
+  const int8_t* G;
+  int64_t K;
+  int32_t ldg, pad0;
+  int64_t* a;
+  int64_t* q4;
+} mape_coeffs_item;
+size_t mape_direction_coeffs_batch_workspace_bytes(int32_t count);
+int mape_direction_coeffs_batch(const mape_coeffs_item* items, int32_t count,
+                                void* workspace, size_t workspace_bytes,
+                                void* stream);
+
 /* a13-a14 -- Algorithm 1 (§2) for S starts at once, with the direction set
  * ±G as test set.  One iteration, for every start s still active:
  *   r_s = 2 Q x_s + c;  for every k, sign e in {+1,-1}, lambda in
@@ -359,7 +436,15 @@ int mape_direction_coeffs(const int32_t* q_row, const int32_t* q_col,
 typedef struct {
   int32_t n, S;
   int64_t K;
-  const int8_t* G; int32_t ldg; int32_t pad0;
+  const int8_t* G; int32_t ldg;
+  int32_t score_lanes;     /* lanes sharing a direction in the scoring pass:
+                              1, 2, 4, 8, 16 or 32; 0 = autotuned per shape
+                              (n, and K and S rounded up to powers of two,
+                              quartic or not) on the call's own data.  Rows
+                              are read as 16-byte pieces when ldg is a
+                              multiple of 16 and G 16-byte aligned, else byte
+                              by byte with one lane.  The results do not
+                              depend on it. */
   const int64_t* a; const int64_t* q4;
   const int32_t* q_row; const int32_t* q_col; const int32_t* q_val; int32_t nnz;
   int32_t pad1;
@@ -372,6 +457,40 @@ typedef struct {
 size_t mape_augment_workspace_bytes(int32_t n, int32_t S, int64_t K);
 int mape_augment_run(const mape_augment_args* args, int64_t* iters_out,
                      void* stream);
+
+/* a13-a14 for many instances at once (§3.3's multi-start augmentation over
+ * a batch of instances): every item as in mape_augment_run, each with its
+ * own directions, coefficients, objective, box, starts, outputs and
+ * workspace of mape_augment_workspace_bytes.  One launch per iteration scores
+ * the directions of every start of every instance and one applies the moves;
+ * a chunk of 8 iterations (with a device iteration counter, so that an
+ * instance stops at its own max_iters) is captured once as a CUDA graph and
+ * replayed until every start of every instance has stopped (on the legacy
+ * default stream, which cannot be captured, the chunk is launched directly).
+ * The lane count of the scoring pass is the items' own when they all give the
+ * same one, else the autotuned one of the item with the most row entries.
+ * iters_out [count] (host): each item's mape_augment_run *iters_out.  Every
+ * item's results (X, fval, moves, nmoves, iterations) are identical to its
+ * own mape_augment_run.  `workspace` holds the batch's tables
+ * (mape_augment_run_batch_workspace_bytes(count)).
+ * Errors: as mape_augment_run; BOUNDS if a start of any item lies outside its
+ * box (no item then iterates).  Synchronous. */
+size_t mape_augment_run_batch_workspace_bytes(int32_t count);
+int mape_augment_run_batch(const mape_augment_args* items, int32_t count,
+                           int64_t* iters_out, void* workspace,
+                           size_t workspace_bytes, void* stream);
+
+typedef struct {
+  int32_t lanes;           /* chosen lanes per direction                     */
+  int32_t candidates;      /* lane counts timed                              */
+  int32_t cand_lanes[8];
+  float probe_ms[8];       /* one scoring pass each, on the call's data      */
+} mape_augment_tune_info;
+/* The autotuned lane count of the scoring pass for a shape (n; K and S are
+ * rounded up to powers of two), or STATE if none was tuned yet.
+ * mape_autotune_clear forgets these choices too. */
+int mape_augment_tune_lookup(int32_t n, int64_t K, int32_t S, int32_t quartic,
+                             mape_augment_tune_info* out);
 
 /* Eq. (4) (§3.3) -- initial feasible solutions of model (1): projected Adam
  * on ||A x - b||_2^2 + lambda3 sum_i (x_i - floor x_i)(ceil x_i - x_i) over
@@ -520,6 +639,18 @@ int mape_extract_directions_batch(mape_handle* hs, int32_t count, const int32_t*
 int mape_augment(mape_handle h, const int32_t* X0, int32_t S,
                  const mape_problem* f_or_NULL);
 
+/* Starts Algorithm 1 for `count` handles together: handle i from S[i]
+ * starts X0[i] (as in mape_augment, with each handle's current objective and
+ * direction set).  The iterations of all handles run as
+ * mape_augment_run_batch calls on the first handle's stream (the first
+ * iteration alone, then the rest, as mape_augment does for one handle); each
+ * handle then reads back its own best start.  Every handle must be idle, on
+ * one device, with a direction set.  Returns at once; poll and wait on each
+ * handle as usual.  Each handle's results (points, values, iteration counts)
+ * equal those of its own mape_augment. */
+int mape_augment_batch(mape_handle* hs, int32_t count, const int32_t* const* X0,
+                       const int32_t* S);
+
 #define MAPE_PHASE_IDLE       0
 #define MAPE_PHASE_EXTRACTING 1
 #define MAPE_PHASE_FILTERING  2
@@ -604,8 +735,13 @@ typedef struct {
                                time) runs as one mape_extract_directions_batch
                                call, i.e. one graph of persistent launches per
                                chunk of steps for all of them; needs a BF16
-                               precision.  0: each request's extraction runs
-                               on its own slot stream                        */
+                               precision.  Likewise the requests whose
+                               direction sets are ready together start
+                               Algorithm 1 as one mape_augment_batch call
+                               (once no request is extracting, or the oldest
+                               waiting one has waited 5 ms).  0: each
+                               request's extraction and augmentation run on
+                               its own slot stream                           */
   int32_t reserved;
 } mape_server_config;
 

@@ -30,6 +30,9 @@ void record_message(const char* what);
 // limit under one another's launch.
 int allow_max_dynamic_smem(const void* func, size_t* limit);
 
+// Forgets the autotuned lane counts of Algorithm 1's scoring pass.
+void augment_tune_clear();
+
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -272,8 +272,11 @@ extern "C" int mape_autotune_lookup(int32_t n, int32_t d, int32_t P, int32_t pre
 }
 
 extern "C" void mape_autotune_clear(void) {
-  std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tuned.clear();
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
+  }
+  mape_detail::augment_tune_clear();
 }
 
 extern "C" size_t mape_extract_workspace_bytes(int32_t n, int32_t d, int32_t P, int32_t precision) {

@@ -117,32 +117,39 @@ __global__ void csr_fill_kernel(const int32_t* __restrict__ A, int m, int n, con
 constexpr int kCsrWarps = 8;
 constexpr int kCsrMaxRow = 4096;
 
+// candidate row k against A, by the calling warp (row: its shared-memory row)
+__device__ __forceinline__ void csr_test_row(const uint32_t* __restrict__ rowptr, const uint16_t* __restrict__ col,
+                                             const int32_t* __restrict__ val, int m, const int8_t* __restrict__ G,
+                                             int64_t k, int ldg, int8_t* row, uint8_t* __restrict__ ok,
+                                             unsigned long long* __restrict__ fails) {
+  const int lane = threadIdx.x & 31;
+  const int nv = ldg / 16;
+  const uint4* src = reinterpret_cast<const uint4*>(G + k * ldg);
+  for (int c = lane; c < nv; c += 32) reinterpret_cast<uint4*>(row)[c] = src[c];
+  __syncwarp();
+  bool good = true;
+  for (int r = lane; r < m; r += 32) {
+    long long acc = 0;
+    const uint32_t e1 = rowptr[r + 1];
+    for (uint32_t e = rowptr[r]; e < e1; ++e) acc += (long long)val[e] * row[col[e]];
+    good &= (acc == 0);
+  }
+  good = __all_sync(0xffffffffu, good);
+  if (lane == 0) {
+    ok[k] = good ? 1 : 0;
+    if (!good) atomicAdd(fails, 1ull);
+  }
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(32 * kCsrWarps)
 kernel_test_csr_kernel(const uint32_t* __restrict__ rowptr, const uint16_t* __restrict__ col,
                        const int32_t* __restrict__ val, int m, const int8_t* __restrict__ G, int64_t K,
                        int ldg, uint8_t* __restrict__ ok, unsigned long long* __restrict__ fails) {
   __shared__ __align__(16) int8_t s_row[kCsrWarps][kCsrMaxRow];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int8_t* row = s_row[w];
-  const int nv = ldg / 16;
-  for (int64_t k = blockIdx.x * (int64_t)kCsrWarps + w; k < K; k += (int64_t)gridDim.x * kCsrWarps) {
-    const uint4* src = reinterpret_cast<const uint4*>(G + k * ldg);
-    for (int c = lane; c < nv; c += 32) reinterpret_cast<uint4*>(row)[c] = src[c];
-    __syncwarp();
-    bool good = true;
-    for (int r = lane; r < m; r += 32) {
-      long long acc = 0;
-      const uint32_t e1 = rowptr[r + 1];
-      for (uint32_t e = rowptr[r]; e < e1; ++e) acc += (long long)val[e] * row[col[e]];
-      good &= (acc == 0);
-    }
-    good = __all_sync(0xffffffffu, good);
-    if (lane == 0) {
-      ok[k] = good ? 1 : 0;
-      if (!good) atomicAdd(fails, 1ull);
-    }
-    __syncwarp();
-  }
+  const int w = threadIdx.x >> 5;
+  for (int64_t k = blockIdx.x * (int64_t)kCsrWarps + w; k < K; k += (int64_t)gridDim.x * kCsrWarps)
+    csr_test_row(rowptr, col, val, m, G, k, ldg, s_row[w], ok, fails);
 }
 
 // ---- a11 ----------------------------------------------------------------------
@@ -579,6 +586,182 @@ extern "C" int mape_kernel_test(const int32_t* A, int32_t m, int32_t n, const in
   MAPE_CUDA_TRY(cudaMemcpyAsync(&f, d_fail, sizeof(f), cudaMemcpyDeviceToHost, st));
   MAPE_CUDA_TRY(cudaStreamSynchronize(st));
   *fail_count = (int64_t)f;
+  return MAPE_OK;
+}
+
+// ---- a9 for many instances at once ---------------------------------------------
+//
+// Every instance's A goes to compressed rows (one launch per kernel over the
+// rows of all the A's, one scan block per instance), then one launch tests
+// the candidate rows of all instances, a warp per row finding its instance by
+// binary search over the launch's prefix table.  The compressed-row test is
+// exact for every int32 A, so each instance's flags and count equal those of
+// its own mape_kernel_test (whichever path that takes).
+
+namespace {
+
+struct KtView {
+  const int32_t* A;
+  int m, n, ldg;
+  const int8_t* G;
+  int64_t K;
+  uint8_t* ok;
+  uint32_t *rowcnt, *rowptr;
+  uint16_t* col;
+  int32_t* val;
+};
+
+__device__ __forceinline__ int find_inst(const int64_t* __restrict__ prefix, int count, int64_t x) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// prefix: rows of the A's (a warp per row); phase 0 counts, 1 fills
+__global__ void csr_batch_kernel(const KtView* __restrict__ v, const int64_t* __restrict__ prefix, int count,
+                                 int phase) {
+  const int64_t wr = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (wr >= prefix[count]) return;  // warp-uniform
+  const int i = find_inst(prefix, count, wr);
+  const KtView& d = v[i];
+  const int r = (int)(wr - prefix[i]);
+  const int lane = threadIdx.x & 31;
+  const int32_t* a = d.A + (int64_t)r * d.n;
+  if (phase == 0) {
+    uint32_t c = 0;
+    for (int j = lane; j < d.n; j += 32) c += a[j] != 0;
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if (lane == 0) d.rowcnt[r] = c;
+    return;
+  }
+  uint32_t pos = d.rowptr[r];
+  for (int j0 = 0; j0 < d.n; j0 += 32) {
+    const int j = j0 + lane;
+    const int x = j < d.n ? a[j] : 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, x != 0);
+    if (x != 0) {
+      const uint32_t q = pos + __popc(bal & ((1u << lane) - 1));
+      d.col[q] = (uint16_t)j;
+      d.val[q] = x;
+    }
+    pos += __popc(bal);
+  }
+}
+
+// one block per instance: exclusive prefix of its row counts (entry m = nnz)
+__global__ void csr_scan_batch_kernel(const KtView* __restrict__ v) {
+  const KtView& d = v[blockIdx.x];
+  __shared__ uint32_t s_carry;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base <= d.m; base += blockDim.x) {
+    const int r = base + threadIdx.x;
+    uint32_t x = r < d.m ? d.rowcnt[r] : 0;
+    // block-wide inclusive scan of x by warp shuffles and a pass over the warp sums
+    __shared__ uint32_t s_w[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t y = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += t;
+    }
+    if (lane == 31) s_w[wid] = y;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t z = lane < (int)(blockDim.x >> 5) ? s_w[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, z, o);
+        if (lane >= o) z += t;
+      }
+      s_w[lane] = z;
+    }
+    __syncthreads();
+    const uint32_t incl = y + (wid > 0 ? s_w[wid - 1] : 0) + s_carry;
+    if (r <= d.m) d.rowptr[r] = incl - x;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_carry = incl;
+    __syncthreads();
+  }
+}
+
+// prefix: candidate rows of all instances (a warp per row)
+__global__ void __launch_bounds__(32 * kCsrWarps)
+kernel_test_batch_kernel(const KtView* __restrict__ v, const int64_t* __restrict__ prefix, int count,
+                         unsigned long long* __restrict__ fails) {
+  __shared__ __align__(16) int8_t s_row[kCsrWarps][kCsrMaxRow];
+  const int w = threadIdx.x >> 5;
+  const int64_t g = blockIdx.x * (int64_t)kCsrWarps + w;
+  if (g >= prefix[count]) return;  // warp-uniform
+  const int i = find_inst(prefix, count, g);
+  const KtView& d = v[i];
+  csr_test_row(d.rowptr, d.col, d.val, d.m, d.G, g - prefix[i], d.ldg, s_row[w], d.ok, fails + i);
+}
+
+}  // namespace
+
+extern "C" size_t mape_kernel_test_batch_workspace_bytes(int32_t count) {
+  if (count <= 0) return 0;
+  mape_detail::Sizer s;
+  s.take<KtView>((size_t)count);
+  s.take<int64_t>((size_t)2 * (count + 1));    // prefix tables: rows of A, candidate rows
+  s.take<unsigned long long>((size_t)count);   // failure counters
+  return s.bytes();
+}
+
+extern "C" int mape_kernel_test_batch(mape_kernel_test_item* items, int32_t count, void* workspace,
+                                      size_t workspace_bytes, void* stream) {
+  using namespace mape_detail;
+  if (!items || count <= 0) return MAPE_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    const mape_kernel_test_item& it = items[i];
+    if (!it.A || it.m <= 0 || it.n <= 0 || it.ldg < it.n || it.ldg % 16 != 0 || it.K < 0 ||
+        (it.K > 0 && (!it.G || !it.ok)))
+      return MAPE_ERR_INVALID_ARG;
+    if (it.n > 4096 || it.ldg > kCsrMaxRow) return MAPE_ERR_SHAPE;
+  }
+  Carver bc(workspace, workspace_bytes);
+  KtView* d_views = bc.take<KtView>((size_t)count);
+  int64_t* d_px = bc.take<int64_t>((size_t)2 * (count + 1));
+  unsigned long long* d_fail = bc.take<unsigned long long>((size_t)count);
+  if (!bc.ok) return MAPE_ERR_CAPACITY;
+  std::vector<KtView> v((size_t)count);
+  std::vector<int64_t> px((size_t)2 * (count + 1), 0);
+  for (int i = 0; i < count; ++i) {
+    mape_kernel_test_item& it = items[i];
+    it.fail_count = 0;
+    KtView& d = v[(size_t)i];
+    d = KtView{it.A, it.m, it.n, it.ldg, it.G, it.K, it.ok, nullptr, nullptr, nullptr, nullptr};
+    // the compressed rows in the instance's own workspace, carved as mape_kernel_test carves it
+    Carver cv(it.workspace, it.workspace_bytes);
+    cv.take<unsigned long long>(1);
+    d.rowcnt = cv.take<uint32_t>((size_t)it.m + 1);
+    d.rowptr = cv.take<uint32_t>((size_t)it.m + 1);
+    d.col = cv.take<uint16_t>((size_t)it.m * it.n);
+    d.val = cv.take<int32_t>((size_t)it.m * it.n);
+    if (!cv.ok) return MAPE_ERR_CAPACITY;
+    px[(size_t)i + 1] = px[(size_t)i] + it.m;
+    px[(size_t)(count + 1) + i + 1] = px[(size_t)(count + 1) + i] + it.K;
+  }
+  const int64_t arows = px[(size_t)count], crows = px[(size_t)2 * count + 1];
+  cudaStream_t st = as_stream(stream);
+  MAPE_CUDA_TRY(cudaMemcpyAsync(d_views, v.data(), sizeof(KtView) * count, cudaMemcpyHostToDevice, st));
+  MAPE_CUDA_TRY(cudaMemcpyAsync(d_px, px.data(), sizeof(int64_t) * px.size(), cudaMemcpyHostToDevice, st));
+  MAPE_CUDA_TRY(cudaMemsetAsync(d_fail, 0, sizeof(unsigned long long) * count, st));
+  const unsigned ga = (unsigned)ceil_div(arows * 32, 256);
+  launch(csr_batch_kernel, ga, 256, 0, st, (const KtView*)d_views, (const int64_t*)d_px, (int)count, 0);
+  launch(csr_scan_batch_kernel, (unsigned)count, 1024, 0, st, (const KtView*)d_views);
+  launch(csr_batch_kernel, ga, 256, 0, st, (const KtView*)d_views, (const int64_t*)d_px, (int)count, 1);
+  if (crows > 0)
+    launch(kernel_test_batch_kernel, (unsigned)ceil_div(crows, kCsrWarps), 32 * kCsrWarps, 0, st,
+           (const KtView*)d_views, (const int64_t*)(d_px + count + 1), (int)count, d_fail);
+  MAPE_LAUNCH_CHECK();
+  std::vector<unsigned long long> f((size_t)count, 0);
+  MAPE_CUDA_TRY(cudaMemcpyAsync(f.data(), d_fail, sizeof(unsigned long long) * count, cudaMemcpyDeviceToHost, st));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < count; ++i) items[i].fail_count = (int64_t)f[(size_t)i];
   return MAPE_OK;
 }
 

@@ -196,9 +196,14 @@ struct mape_instance {
   int extract_chunk_steps(int* chunk) const;
   int extract_chunk_args(int chunk, mape_extract_args* a);
   int extract_chunk_done(int chunk);
+  int chunk_candidates(cudaStream_t s, int64_t* cnt);
+  void chunk_merged(int chunk, int64_t cnt, int64_t K_new);
   int extract_filter();
 
   int run_extract();
+  // Algorithm 1 (the parts of run_augment, also driven by a batch)
+  void augment_args(mape_augment_args* a);
+  int augment_end(int64_t it1, int64_t it2, double t0, double t1);
   int run_augment(int64_t max_iters);
 };
 
@@ -256,23 +261,35 @@ int mape_instance::extract_chunk_args(int chunk, mape_extract_args* a) {
 
 // After the steps of a chunk: its candidates are merged into the distinct set.
 int mape_instance::extract_chunk_done(int chunk) {
-  cudaStream_t s = stream;
-  unsigned long long cnt = 0;
+  int64_t cnt = 0;
+  H_TRY(chunk_candidates(stream, &cnt));
+  int64_t K_new = 0;
+  H_TRY(mape_dedup(ex_cur, ex_U + cnt, n, ldg, ex_other, cap, &K_new, dWork, work_bytes, stream));
+  chunk_merged(chunk, cnt, K_new);
+  return MAPE_OK;
+}
+
+// The candidates the chunk appended (read on stream s).
+int mape_instance::chunk_candidates(cudaStream_t s, int64_t* cnt) {
+  unsigned long long c = 0;
   int32_t flags = 0;
-  MAPE_CUDA_TRY(cudaMemcpyAsync(&cnt, dCount, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+  MAPE_CUDA_TRY(cudaMemcpyAsync(&c, dCount, sizeof(c), cudaMemcpyDeviceToHost, s));
   MAPE_CUDA_TRY(cudaMemcpyAsync(&flags, dFlags, sizeof(flags), cudaMemcpyDeviceToHost, s));
   MAPE_CUDA_TRY(cudaStreamSynchronize(s));
   if (flags & 1) return MAPE_ERR_CAPACITY;
-  ex_total += (int64_t)cnt;
-  int64_t K_new = 0;
-  H_TRY(mape_dedup(ex_cur, ex_U + (int64_t)cnt, n, ldg, ex_other, cap, &K_new, dWork, work_bytes, s));
+  *cnt = (int64_t)c;
+  return MAPE_OK;
+}
+
+// The merge of the chunk's candidates left K_new distinct rows in ex_other.
+void mape_instance::chunk_merged(int chunk, int64_t cnt, int64_t K_new) {
+  ex_total += cnt;
   ex_U = K_new;
   std::swap(ex_cur, ex_other);
   ex_done += chunk;
   std::lock_guard<std::mutex> lk(mu);
   st.candidates = ex_total;
   st.unique = ex_U;
-  return MAPE_OK;
 }
 
 int mape_instance::extract_filter() {
@@ -311,24 +328,34 @@ int mape_instance::run_extract() {
   return extract_filter();
 }
 
+void mape_instance::augment_args(mape_augment_args* a) {
+  *a = mape_augment_args{};
+  a->n = n; a->S = S; a->K = K; a->G = dirs; a->ldg = ldg; a->a = da; a->q4 = dq4;
+  a->q_row = dqr; a->q_col = dqc; a->q_val = dqv; a->nnz = nnz; a->c = dc; a->w = has_w ? dw : nullptr;
+  a->l = dl; a->u = du; a->X = dX; a->fval = dF;
+  a->workspace = dAugWork; a->workspace_bytes = aug_work_bytes;
+}
+
 int mape_instance::run_augment(int64_t max_iters) {
-  cudaStream_t s = stream;
   set_phase(MAPE_PHASE_AUGMENTING);
   double t0 = now_ms();
-  mape_augment_args a{};
-  a.n = n; a.S = S; a.K = K; a.G = dirs; a.ldg = ldg; a.a = da; a.q4 = dq4;
-  a.q_row = dqr; a.q_col = dqc; a.q_val = dqv; a.nnz = nnz; a.c = dc; a.w = has_w ? dw : nullptr;
-  a.l = dl; a.u = du; a.X = dX; a.fval = dF;
-  a.workspace = dAugWork; a.workspace_bytes = aug_work_bytes;
+  mape_augment_args a;
+  augment_args(&a);
   // the first iteration alone: time to the first improving direction
   a.max_iters = std::min<int64_t>(1, max_iters);
   int64_t it1 = 0, it2 = 0;
-  H_TRY(mape_augment_run(&a, &it1, s));
+  H_TRY(mape_augment_run(&a, &it1, stream));
   double t1 = now_ms();
   if (max_iters > 1 && !cancel.load()) {
     a.max_iters = max_iters - 1;
-    H_TRY(mape_augment_run(&a, &it2, s));
+    H_TRY(mape_augment_run(&a, &it2, stream));
   }
+  return augment_end(it1, it2, t0, t1);
+}
+
+// The best start's point and value, and the status of the run.
+int mape_instance::augment_end(int64_t it1, int64_t it2, double t0, double t1) {
+  cudaStream_t s = stream;
   std::vector<int64_t> f(S);
   MAPE_CUDA_TRY(cudaMemcpyAsync(f.data(), dF, sizeof(int64_t) * S, cudaMemcpyDeviceToHost, s));
   MAPE_CUDA_TRY(cudaStreamSynchronize(s));
@@ -565,6 +592,8 @@ int run_batch_steps(ExtractBatch& b) {
   mape_handle h0 = b.hs[0];
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  void* dws = nullptr;  // the dedup batch's tables
+  size_t dws_bytes = 0;
   std::vector<mape_extract_args> items((size_t)count);
   while (h0->ex_done < h0->cfg.T) {
     int chunk = h0->cfg.T - h0->ex_done;
@@ -583,7 +612,24 @@ int run_batch_steps(ExtractBatch& b) {
       ws_bytes = need;
     }
     H_TRY(mape_extract_batch(items.data(), count, ws, ws_bytes, h0->stream));
-    for (auto h : b.hs) H_TRY(h->extract_chunk_done(chunk));
+    // every handle's candidates merged into its set by one mape_dedup_batch
+    std::vector<mape_dedup_item> dd((size_t)count);
+    std::vector<int64_t> cnt((size_t)count, 0);
+    for (int i = 0; i < count; ++i) {
+      mape_handle h = b.hs[i];
+      H_TRY(h->chunk_candidates(h0->stream, &cnt[(size_t)i]));
+      mape_dedup_item& it = dd[(size_t)i];
+      it = mape_dedup_item{};
+      it.cand = h->ex_cur; it.count = h->ex_U + cnt[(size_t)i]; it.n = h->n; it.ldc = h->ldg;
+      it.uniq = h->ex_other; it.uniq_cap = h->cap; it.workspace = h->dWork; it.workspace_bytes = h->work_bytes;
+    }
+    if (!dws) {
+      dws_bytes = mape_dedup_batch_workspace_bytes(count);
+      dws = h0->take<char>(h0->job_bufs, dws_bytes);
+      if (!dws) return MAPE_ERR_OOM;
+    }
+    H_TRY(mape_dedup_batch(dd.data(), count, dws, dws_bytes, h0->stream));
+    for (int i = 0; i < count; ++i) b.hs[i]->chunk_merged(chunk, cnt[(size_t)i], dd[(size_t)i].K);
   }
   return MAPE_OK;
 }
@@ -648,7 +694,10 @@ extern "C" int mape_extract_directions_batch(mape_handle* hs, int32_t count, con
   return MAPE_OK;
 }
 
-extern "C" int mape_augment(mape_handle h, const int32_t* X0, int32_t S, const mape_problem* f) {
+namespace {
+
+// The starts of an augmentation job are uploaded and checked (A x = b, box).
+int prepare_augment(mape_handle h, const int32_t* X0, int32_t S, const mape_problem* f) {
   using namespace mape_detail;
   if (!h || !X0 || S <= 0) return MAPE_ERR_INVALID_ARG;
   if (!idle(h)) return MAPE_ERR_STATE;
@@ -685,18 +734,119 @@ extern "C" int mape_augment(mape_handle h, const int32_t* X0, int32_t S, const m
   MAPE_CUDA_TRY(cudaMemcpyAsync(&bad, dbad, 4, cudaMemcpyDeviceToHost, h->stream));
   MAPE_CUDA_TRY(cudaStreamSynchronize(h->stream));
   if (bad) return MAPE_ERR_INFEASIBLE;
+  return MAPE_OK;
+}
+
+void mark_augmenting(mape_handle h) {
   {
     std::lock_guard<std::mutex> lk(h->mu);
     h->busy = true;
     h->st.phase = MAPE_PHASE_AUGMENTING;
   }
   h->cancel.store(false);
+}
+
+// A batch of augmentation jobs: the first handle's worker runs Algorithm 1
+// for every handle as mape_augment_run_batch calls (the first iteration
+// alone, then the rest, as run_augment does for one); every worker then reads
+// back its own best start.
+struct AugmentBatch {
+  std::vector<mape_handle> hs;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool done = false;
+  int rc = MAPE_OK;
+  std::vector<int64_t> it1, it2;
+  double t0 = 0, t1 = 0;
+};
+
+int run_augment_batch(AugmentBatch& b) {
+  const int count = (int)b.hs.size();
+  mape_handle h0 = b.hs[0];
+  for (auto h : b.hs) {
+    if (h->dev != h0->dev) return MAPE_ERR_INVALID_ARG;
+    h->set_phase(MAPE_PHASE_AUGMENTING);
+  }
+  std::vector<mape_augment_args> items((size_t)count);
+  std::vector<int64_t> max_iters((size_t)count);
+  for (int i = 0; i < count; ++i) {
+    b.hs[i]->augment_args(&items[(size_t)i]);
+    max_iters[(size_t)i] = b.hs[i]->cfg.max_aug_iters;
+  }
+  const size_t ws_bytes = mape_augment_run_batch_workspace_bytes(count);
+  void* ws = h0->take<char>(h0->aug_bufs, ws_bytes);
+  if (!ws) return MAPE_ERR_OOM;
+  b.it1.assign((size_t)count, 0);
+  b.it2.assign((size_t)count, 0);
+  b.t0 = now_ms();
+  for (int i = 0; i < count; ++i) items[(size_t)i].max_iters = std::min<int64_t>(1, max_iters[(size_t)i]);
+  H_TRY(mape_augment_run_batch(items.data(), count, b.it1.data(), ws, ws_bytes, h0->stream));
+  b.t1 = now_ms();
+  bool more = false;
+  for (int i = 0; i < count; ++i) {
+    mape_augment_args& a = items[(size_t)i];
+    if (max_iters[(size_t)i] > 1 && !b.hs[i]->cancel.load()) {
+      a.max_iters = max_iters[(size_t)i] - 1;
+      more = true;
+    } else {
+      a.S = 0;  // as run_augment: no second call for this handle
+    }
+  }
+  if (more) H_TRY(mape_augment_run_batch(items.data(), count, b.it2.data(), ws, ws_bytes, h0->stream));
+  return MAPE_OK;
+}
+
+}  // namespace
+
+extern "C" int mape_augment(mape_handle h, const int32_t* X0, int32_t S, const mape_problem* f) {
+  int rc = prepare_augment(h, X0, S, f);
+  if (rc) return rc;
+  mark_augmenting(h);
   int64_t iters = h->cfg.max_aug_iters;
   h->worker = std::thread([h, iters]() {
     cudaSetDevice(h->dev);
     int r = h->run_augment(iters);
     h->finish(r);
   });
+  return MAPE_OK;
+}
+
+extern "C" int mape_augment_batch(mape_handle* hs, int32_t count, const int32_t* const* X0, const int32_t* S) {
+  if (!hs || count <= 0 || !X0 || !S) return MAPE_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i]) return MAPE_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return MAPE_ERR_INVALID_ARG;
+    if (hs[i]->dev != hs[0]->dev) return MAPE_ERR_INVALID_ARG;
+    if (!idle(hs[i])) return MAPE_ERR_STATE;
+  }
+  for (int i = 0; i < count; ++i) {
+    int rc = prepare_augment(hs[i], X0[i], S[i], nullptr);
+    if (rc) return rc;
+  }
+  auto b = std::make_shared<AugmentBatch>();
+  b->hs.assign(hs, hs + count);
+  for (int i = 0; i < count; ++i) mark_augmenting(hs[i]);
+  for (int i = 0; i < count; ++i) {
+    mape_handle h = hs[i];
+    h->worker = std::thread([h, b, i]() {
+      cudaSetDevice(h->dev);
+      int r = MAPE_OK;
+      if (i == 0) {
+        r = run_augment_batch(*b);
+        std::lock_guard<std::mutex> lk(b->mu);
+        b->rc = r;
+        b->done = true;
+        b->cv.notify_all();
+      } else {
+        std::unique_lock<std::mutex> lk(b->mu);
+        b->cv.wait(lk, [&] { return b->done; });
+        r = b->rc;
+      }
+      if (r == MAPE_OK) r = h->augment_end(b->it1[(size_t)i], b->it2[(size_t)i], b->t0, b->t1);
+      h->finish(r);
+    });
+  }
   return MAPE_OK;
 }
 

@@ -42,11 +42,13 @@ struct Request {
   // progress
   int state = MAPE_REQ_QUEUED;
   int error = MAPE_OK;
-  int stage = 0;  // 1: extracting, 2: augmenting
+  int stage = 0;  // 1: extracting, 2: augmenting, 3: waiting for an augmentation batch
   mape_handle h = nullptr;
   int slot = -1;
   bool ready = false;  // batch mode: handle created, extraction not started yet
   double t_ready = 0;
+  bool aug_ready = false;  // batch mode: directions found, augmentation not started yet
+  double t_aug_ready = 0;
   double t_submit = 0, t_admit = 0, t_extracted = 0, t_first = 0, t_done = 0;
   // results
   int64_t directions = 0, best_f = 0, aug_iters = 0;
@@ -252,6 +254,7 @@ void mape_server::finish(Request* r, int err) {
 // Moves a running request on when its handle has finished a job.  Called with
 // the lock held; the calls it makes do not block on other requests.
 void mape_server::advance(Request* r) {
+  if (r->stage == 3) return;  // the scheduler starts its augmentation with the next batch
   mape_status st{};
   mape_poll(r->h, &st);
   if (st.phase == MAPE_PHASE_ERROR) {
@@ -269,6 +272,12 @@ void mape_server::advance(Request* r) {
       if (rc != MAPE_OK) { finish(r, rc); return; }
       r->G.resize(G.size());
       for (size_t i = 0; i < G.size(); ++i) r->G[i] = (int8_t)G[i];
+    }
+    if (cfg.batch_extraction) {
+      r->aug_ready = true;
+      r->t_aug_ready = clock_ms();
+      r->stage = 3;
+      return;
     }
     int rc = mape_augment(r->h, r->X0.data(), r->S, nullptr);
     if (rc != MAPE_OK) { finish(r, rc); return; }
@@ -312,6 +321,37 @@ void mape_server::loop() {
           cudaSetDevice(dev);
           start_batch(ready);
         }).detach();
+      }
+      // ... and the requests whose directions are found start Algorithm 1
+      // together (mape_augment_batch), once no request is still extracting or
+      // the oldest waiting one has waited 5 ms
+      std::vector<Request*> aug;
+      double aug_oldest = 1e300;
+      bool extracting = false;
+      for (auto& kv : reqs) {
+        Request* r = kv.second.get();
+        if (r->state != MAPE_REQ_RUNNING) continue;
+        if (r->stage == 1 || r->ready) extracting = true;
+        if (r->aug_ready) {
+          aug.push_back(r);
+          aug_oldest = std::min(aug_oldest, r->t_aug_ready);
+        }
+      }
+      if (!aug.empty() && (!extracting || clock_ms() - aug_oldest > 5.0)) {
+        std::vector<mape_handle> hs;
+        std::vector<const int32_t*> X0;
+        std::vector<int32_t> S;
+        for (auto r : aug) {
+          hs.push_back(r->h);
+          X0.push_back(r->X0.data());
+          S.push_back(r->S);
+        }
+        const int rc = mape_augment_batch(hs.data(), (int32_t)hs.size(), X0.data(), S.data());
+        for (auto r : aug) {
+          r->aug_ready = false;
+          if (rc != MAPE_OK) finish(r, rc);
+          else r->stage = 2;
+        }
       }
     }
     // admission, in arrival order, while a slot and the memory allow

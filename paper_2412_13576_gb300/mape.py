@@ -70,8 +70,17 @@ class InitArgs(C.Structure):
                 ("dbg_f", P_), ("dbg_grad", P_), ("workspace", P_), ("workspace_bytes", C.c_size_t)]
 
 
+class DedupItem(C.Structure):
+    _fields_ = [("cand", P_), ("count", I64), ("n", I32), ("ldc", I32), ("uniq", P_), ("uniq_cap", I64),
+                ("K", I64), ("status", I32), ("pad0", I32), ("workspace", P_), ("workspace_bytes", C.c_size_t)]
+
+
+class AugTuneInfo(C.Structure):
+    _fields_ = [("lanes", I32), ("candidates", I32), ("cand_lanes", I32 * 8), ("probe_ms", F32 * 8)]
+
+
 class AugmentArgs(C.Structure):
-    _fields_ = [("n", I32), ("S", I32), ("K", I64), ("G", P_), ("ldg", I32), ("pad0", I32),
+    _fields_ = [("n", I32), ("S", I32), ("K", I64), ("G", P_), ("ldg", I32), ("score_lanes", I32),
                 ("a", P_), ("q4", P_), ("q_row", P_), ("q_col", P_), ("q_val", P_), ("nnz", I32),
                 ("pad1", I32), ("c", P_), ("w", P_), ("l", P_), ("u", P_), ("X", P_), ("fval", P_),
                 ("moves", P_), ("nmoves", P_), ("moves_cap", I32), ("pad2", I32),
@@ -157,6 +166,8 @@ _SIGS = {
     "mape_autotune_clear": (None, []),
     "mape_dedup_workspace_bytes": (C.c_size_t, [I64, I32]),
     "mape_dedup": (C.c_int, [P_, I64, I32, I32, P_, I64, C.POINTER(I64), P_, C.c_size_t, P_]),
+    "mape_dedup_batch_workspace_bytes": (C.c_size_t, [I32]),
+    "mape_dedup_batch": (C.c_int, [C.POINTER(DedupItem), I32, P_, C.c_size_t, P_]),
     "mape_dedup_static_max_rows": (I64, []),
     "mape_dedup_static": (C.c_int, [P_, I64, I32, I32, P_, I64, C.POINTER(I64), P_]),
     "mape_kernel_test_workspace_bytes": (C.c_size_t, [I32, I32]),
@@ -166,6 +177,10 @@ _SIGS = {
     "mape_direction_coeffs": (C.c_int, [P_, P_, P_, I32, P_, I32, P_, I64, I32, P_, P_, P_]),
     "mape_augment_workspace_bytes": (C.c_size_t, [I32, I32, I64]),
     "mape_augment_run": (C.c_int, [C.POINTER(AugmentArgs), C.POINTER(I64), P_]),
+    "mape_augment_run_batch_workspace_bytes": (C.c_size_t, [I32]),
+    "mape_augment_run_batch": (C.c_int, [C.POINTER(AugmentArgs), I32, C.POINTER(I64), P_, C.c_size_t, P_]),
+    "mape_augment_tune_lookup": (C.c_int, [I32, I64, I32, I32, C.POINTER(AugTuneInfo)]),
+    "mape_augment_batch": (C.c_int, [C.POINTER(P_), I32, C.POINTER(P_), C.POINTER(I32)]),
     "mape_set_allocator": (C.c_int, [P_, P_, P_]),
     "mape_trim_memory": (C.c_int, []),
     "mape_create_instance": (C.c_int, [P_, P_, P_, P_, C.POINTER(Problem), P_, C.POINTER(Config), P_,
@@ -426,6 +441,34 @@ def dedup(cand, count, n, stream=None):
     return uniq[:K.value]
 
 
+def dedup_batch(sets, stream=None):
+    """mape_dedup_batch: a10 for several candidate sets in one sequence of
+    launches.  sets: (cand [rows x ldc] int8 CUDA tensor, count, n, uniq_cap
+    or None for count).  Returns one (distinct rows, K, status) per set (the
+    rows empty when the status is not OK)."""
+    import torch
+    k = len(sets)
+    items = (DedupItem * k)()
+    keep = []
+    for i, (cand, count, n, cap) in enumerate(sets):
+        ldc = cand.shape[1]
+        cap = count if cap is None else cap
+        uniq = torch.zeros((max(cap, 1), ldc), dtype=torch.int8, device=cand.device)
+        ws = _workspace(lib().mape_dedup_workspace_bytes(count, ldc), cand.device)
+        keep.append((uniq, ws))
+        it = items[i]
+        it.cand, it.count, it.n, it.ldc = _ptr(cand), count, n, ldc
+        it.uniq, it.uniq_cap = _ptr(uniq), cap
+        it.workspace, it.workspace_bytes = _ptr(ws), ws.numel()
+    dev = sets[0][0].device
+    bws = _workspace(lib().mape_dedup_batch_workspace_bytes(k), dev)
+    rc = lib().mape_dedup_batch(items, k, _ptr(bws), bws.numel(), _stream(stream))
+    if rc not in (OK, -7):  # CAPACITY is reported per set
+        _check(rc, "mape_dedup_batch")
+    return [(keep[i][0][: items[i].K] if items[i].status == OK else keep[i][0][:0], items[i].K, items[i].status)
+            for i in range(k)]
+
+
 def kernel_test(A, G, n, stream=None):
     """a9: (ok [K] uint8, failures)."""
     import torch
@@ -470,8 +513,9 @@ def direction_coeffs(qr, qc, qv, w, n, G, stream=None):
     return a[:K], q4[:K]
 
 
-def augment_run(G, n, a, q4, qr, qc, qv, c, w, l, u, X, *, max_iters=10 ** 6, moves_cap=0, stream=None):
-    """a13-a14: Algorithm 1 in place on X [S,n]; returns (fval, iters, moves, nmoves)."""
+def _augment_args(G, n, a, q4, qr, qc, qv, c, w, l, u, X, max_iters, moves_cap, lanes):
+    """The arguments of one Algorithm 1 run and the output tensors it fills
+    (fval, moves, nmoves) and its workspace."""
     import torch
     K, ldg = G.shape
     S = X.shape[0]
@@ -481,7 +525,7 @@ def augment_run(G, n, a, q4, qr, qc, qv, c, w, l, u, X, *, max_iters=10 ** 6, mo
     nmoves = torch.zeros(S, dtype=torch.int32, device=dev)
     ws = _workspace(lib().mape_augment_workspace_bytes(n, S, K), dev)
     A = AugmentArgs()
-    A.n, A.S, A.K, A.G, A.ldg = n, S, K, _ptr(G), ldg
+    A.n, A.S, A.K, A.G, A.ldg, A.score_lanes = n, S, K, _ptr(G), ldg, lanes
     A.a, A.q4 = _ptr(a), _ptr(q4)
     A.q_row, A.q_col, A.q_val, A.nnz = _ptr(qr), _ptr(qc), _ptr(qv), qv.numel()
     A.c, A.w, A.l, A.u = _ptr(c), _ptr(w), _ptr(l), _ptr(u)
@@ -489,9 +533,48 @@ def augment_run(G, n, a, q4, qr, qc, qv, c, w, l, u, X, *, max_iters=10 ** 6, mo
     A.moves, A.nmoves, A.moves_cap = _ptr(moves), _ptr(nmoves), moves_cap
     A.max_iters = max_iters
     A.workspace, A.workspace_bytes = _ptr(ws), ws.numel()
+    return A, (fval, moves, nmoves, ws)
+
+
+def augment_run(G, n, a, q4, qr, qc, qv, c, w, l, u, X, *, max_iters=10 ** 6, moves_cap=0, lanes=0, stream=None):
+    """a13-a14: Algorithm 1 in place on X [S,n]; returns (fval, iters, moves,
+    nmoves).  lanes: lanes per direction of the scoring pass (0: autotuned)."""
+    A, (fval, moves, nmoves, _ws) = _augment_args(G, n, a, q4, qr, qc, qv, c, w, l, u, X, max_iters, moves_cap,
+                                                  lanes)
     iters = I64(0)
     _check(lib().mape_augment_run(C.byref(A), C.byref(iters), _stream(stream)), "mape_augment_run")
     return fval, iters.value, moves, nmoves
+
+
+def augment_run_batch(runs, *, stream=None):
+    """mape_augment_run_batch: Algorithm 1 for several instances in one
+    sequence of launches.  runs: dicts of augment_run's arguments (G, n, a,
+    q4, qr, qc, qv, c, w, l, u, X, and optionally max_iters, moves_cap,
+    lanes).  Returns one (fval, iters, moves, nmoves) per run."""
+    k = len(runs)
+    args, outs = [], []
+    for r in runs:
+        A, o = _augment_args(r["G"], r["n"], r["a"], r["q4"], r["qr"], r["qc"], r["qv"], r["c"], r["w"], r["l"],
+                             r["u"], r["X"], r.get("max_iters", 10 ** 6), r.get("moves_cap", 0), r.get("lanes", 0))
+        args.append(A)
+        outs.append(o)
+    items = (AugmentArgs * k)(*args)
+    iters = (I64 * k)()
+    dev = runs[0]["X"].device
+    ws = _workspace(lib().mape_augment_run_batch_workspace_bytes(k), dev)
+    _check(lib().mape_augment_run_batch(items, k, iters, _ptr(ws), ws.numel(), _stream(stream)),
+           "mape_augment_run_batch")
+    return [(fval, int(iters[i]), moves, nmoves) for i, (fval, moves, nmoves, _w) in enumerate(outs)]
+
+
+def augment_tune_lookup(n, K, S, quartic):
+    """The autotuned lane count of the scoring pass for a shape, or None."""
+    info = AugTuneInfo()
+    rc = lib().mape_augment_tune_lookup(n, K, S, 1 if quartic else 0, C.byref(info))
+    if rc != OK:
+        return None
+    c = info.candidates
+    return {"lanes": info.lanes, "cand_lanes": list(info.cand_lanes[:c]), "probe_ms": list(info.probe_ms[:c])}
 
 
 # ---- instance handle (host numpy arrays) ------------------------------------
@@ -527,6 +610,19 @@ def extract_directions_batch(handles, starts):
     for h in handles:
         h._keep["batch_starts_all"] = keep
     _check(lib().mape_extract_directions_batch(hs, k, Ps, Z, G), "mape_extract_directions_batch")
+
+
+def augment_batch(handles, starts):
+    """mape_augment_batch: Algorithm 1 for several Instance handles at once.
+    starts: one X0 [S x n] int32 host array per handle."""
+    k = len(handles)
+    hs = (P_ * k)(*[h.h for h in handles])
+    keep = [_np(np.atleast_2d(x), np.int32) for x in starts]
+    X = (P_ * k)(*[x.ctypes.data for x in keep])
+    S = (I32 * k)(*[x.shape[0] for x in keep])
+    for h, x in zip(handles, keep):
+        h._keep["x0"] = x
+    _check(lib().mape_augment_batch(hs, k, X, S), "mape_augment_batch")
 
 
 class Instance:

@@ -125,6 +125,28 @@ def test_argument_checks_without_device(lib):
     assert lib.mape_dedup_workspace_bytes(1000, 32) > 1000 * 8
 
 
+def test_augment_batch_argument_checks(lib):
+    """Algorithm 1's batched and tuned entry points refuse bad arguments
+    before any device work: no items, a lane count that is not a power of two
+    up to 32, a null output."""
+    from paper_2412_13576_gb300 import mape
+    it = (ctypes.c_int64 * 2)()
+    assert lib.mape_augment_run_batch(None, 2, it, None, 0, None) == -1
+    A = (mape.AugmentArgs * 1)()
+    A[0].n, A[0].S, A[0].K, A[0].ldg, A[0].score_lanes = 4, 0, 0, 16, 3
+    assert lib.mape_augment_run_batch(A, 1, it, None, 0, None) == -1
+    assert lib.mape_augment_run(ctypes.byref(A[0]), it, None) == -1
+    A[0].score_lanes = 0
+    assert lib.mape_augment_run_batch(A, 0, it, None, 0, None) == -1
+    assert lib.mape_augment_run_batch_workspace_bytes(0) == 0
+    assert lib.mape_augment_run_batch_workspace_bytes(8) > 8 * 64
+    assert lib.mape_augment_tune_lookup(4, 1, 1, 0, None) == -1
+    assert mape.augment_tune_lookup(12345, 1, 1, False) is None
+    assert lib.mape_augment_batch(None, 1, None, None) == -1
+    # 1024 partial minima per start at most, whatever K
+    assert lib.mape_augment_workspace_bytes(200, 4, 1 << 30) == lib.mape_augment_workspace_bytes(200, 4, 1 << 20)
+
+
 def test_bounds_rejected_before_upload(lib):
     """u - l > 127 cannot be stored as int8 directions: BOUNDS, no device work."""
     import numpy as np
