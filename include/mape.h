@@ -384,6 +384,32 @@ int mape_minimal_filter(const int8_t* G, int64_t K, int32_t n, int32_t ldg,
                         int64_t* K_out, void* workspace,
                         size_t workspace_bytes, void* stream);
 
+/* a11 for many instances at once: item i is one mape_minimal_filter call
+ * (its own rows, valid flags, keep flags, output and workspace of
+ * mape_minimal_workspace_bytes(K, n)) and gets the same keep flags, output
+ * and K_out.  Every kernel of the filter runs once over the rows, positions
+ * or blocks of all instances; one dominance launch covers the pattern-list
+ * blocks of all of them.  `workspace`:
+ * mape_minimal_filter_batch_workspace_bytes(items, count).  Errors:
+ * INVALID_ARG, SHAPE as mape_minimal_filter for any item (before any device
+ * work), CAPACITY, CUDA.  Synchronous. */
+typedef struct {
+  const int8_t* G;          /* [K x ldg] distinct rows in canonical sign      */
+  int64_t K;
+  int32_t n, ldg;
+  const uint8_t* valid;     /* optional [K]                                   */
+  uint8_t* keep;            /* [K] out                                        */
+  int8_t* out;              /* [K x ldg] out: the kept rows in input order    */
+  int64_t K_out;            /* out                                            */
+  void* workspace;
+  size_t workspace_bytes;
+} mape_minimal_item;
+size_t mape_minimal_filter_batch_workspace_bytes(const mape_minimal_item* items,
+                                                 int32_t count);
+int mape_minimal_filter_batch(mape_minimal_item* items, int32_t count,
+                              void* workspace, size_t workspace_bytes,
+                              void* stream);
+
 /* a12 -- per-direction coefficients for Algorithm 1 with
  * f = x^T Q x + c^T x + sum w_i x_i^4:
  *   a[k]  = g^T Q g            (int64, exact)

@@ -155,11 +155,9 @@ kernel_test_csr_kernel(const uint32_t* __restrict__ rowptr, const uint16_t* __re
 // ---- a11 ----------------------------------------------------------------------
 
 // l1 norm and sign masks per row; rows with valid == 0 get l1 = kInvalidL1
-__global__ void prep_kernel(const int8_t* __restrict__ G, int64_t K, int n, int ldg, int W,
-                            const uint8_t* __restrict__ valid, int32_t* __restrict__ l1,
-                            uint64_t* __restrict__ masks, uint32_t* __restrict__ hist) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= K) return;
+__device__ __forceinline__ void prep_row(const int8_t* __restrict__ G, int64_t k, int n, int ldg, int W,
+                                         const uint8_t* __restrict__ valid, int32_t* __restrict__ l1,
+                                         uint64_t* __restrict__ masks, uint32_t* __restrict__ hist) {
   const int8_t* g = G + k * ldg;
   int s = 0;
   uint64_t* pm = masks + k * 2 * W;
@@ -181,13 +179,21 @@ __global__ void prep_kernel(const int8_t* __restrict__ G, int64_t K, int n, int 
   if (v_ok) atomicAdd(&hist[s], 1u);
 }
 
+__global__ void prep_kernel(const int8_t* __restrict__ G, int64_t K, int n, int ldg, int W,
+                            const uint8_t* __restrict__ valid, int32_t* __restrict__ l1,
+                            uint64_t* __restrict__ masks, uint32_t* __restrict__ hist) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  prep_row(G, k, n, ldg, W, valid, l1, masks, hist);
+}
+
 // exclusive prefix over bins (one block of 1024); cursor receives a copy of
 // the starts.  Warp w owns a contiguous segment; its lanes read it 32
 // consecutive words at a time (coalesced): a first sweep sums the segment, the
 // 32 segment sums are scanned by warp 0, and a second sweep scans the
 // segment with warp shuffles and writes it.
-__global__ void bin_scan_kernel(const uint32_t* __restrict__ hist, int nbins, uint32_t* __restrict__ start,
-                                uint32_t* __restrict__ cursor) {
+__device__ __forceinline__ void bin_scan_block(const uint32_t* __restrict__ hist, int nbins,
+                                               uint32_t* __restrict__ start, uint32_t* __restrict__ cursor) {
   __shared__ uint32_t s_warp[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
   const int per = (nbins + nw - 1) / nw;
@@ -223,13 +229,17 @@ __global__ void bin_scan_kernel(const uint32_t* __restrict__ hist, int nbins, ui
   }
 }
 
+__global__ void bin_scan_kernel(const uint32_t* __restrict__ hist, int nbins, uint32_t* __restrict__ start,
+                                uint32_t* __restrict__ cursor) {
+  bin_scan_block(hist, nbins, start, cursor);
+}
+
 // sorted arrays: row index, first mask words, folded signatures, l1
-__global__ void scatter_kernel(const int32_t* __restrict__ l1, const uint64_t* __restrict__ masks, int64_t K, int W,
-                               uint32_t* __restrict__ cursor, uint32_t* __restrict__ s_idx,
-                               uint64_t* __restrict__ s_pk, ulonglong2* __restrict__ s_sig,
-                               int32_t* __restrict__ s_l1) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= K || l1[k] == kInvalidL1) return;
+__device__ __forceinline__ void scatter_row(const int32_t* __restrict__ l1, const uint64_t* __restrict__ masks,
+                                            int64_t k, int W, uint32_t* __restrict__ cursor,
+                                            uint32_t* __restrict__ s_idx, uint64_t* __restrict__ s_pk,
+                                            ulonglong2* __restrict__ s_sig, int32_t* __restrict__ s_l1) {
+  if (l1[k] == kInvalidL1) return;
   uint32_t q = atomicAdd(&cursor[l1[k]], 1u);
   s_idx[q] = (uint32_t)k;
   // sign masks of coordinates 0..31: pos in the low half, neg in the high half
@@ -244,6 +254,15 @@ __global__ void scatter_kernel(const int32_t* __restrict__ l1, const uint64_t* _
   }
   s_sig[q] = make_ulonglong2(pos, neg);
   s_l1[q] = l1[k];
+}
+
+__global__ void scatter_kernel(const int32_t* __restrict__ l1, const uint64_t* __restrict__ masks, int64_t K, int W,
+                               uint32_t* __restrict__ cursor, uint32_t* __restrict__ s_idx,
+                               uint64_t* __restrict__ s_pk, ulonglong2* __restrict__ s_sig,
+                               int32_t* __restrict__ s_l1) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  scatter_row(l1, masks, k, W, cursor, s_idx, s_pk, s_sig, s_l1);
 }
 
 // ---- sign patterns -------------------------------------------------------------
@@ -268,12 +287,13 @@ constexpr int64_t kDensitySample = 16384;  // rows that choose the key coordinat
 // per-coordinate nonzero counts of the valid rows among the first rows (64
 // rows per block); any choice of key coordinates gives the same kept set, so
 // a sample is enough to find the densest
-__global__ void coord_count_kernel(const int8_t* __restrict__ G, int64_t K, int n, int ldg,
-                                   const int32_t* __restrict__ l1, uint32_t* __restrict__ cnt) {
+__device__ __forceinline__ void coord_count_block(const int8_t* __restrict__ G, int64_t K, int n, int ldg,
+                                                  const int32_t* __restrict__ l1, uint32_t* __restrict__ cnt,
+                                                  int64_t bx) {
   extern __shared__ uint32_t s_cnt[];  // n
   for (int i = threadIdx.x; i < n; i += blockDim.x) s_cnt[i] = 0;
   __syncthreads();
-  const int64_t r0 = (int64_t)blockIdx.x * 64;
+  const int64_t r0 = bx * 64;
   for (int64_t e = threadIdx.x; e < 64 * (int64_t)n; e += blockDim.x) {
     const int64_t k = r0 + e / n;
     const int i = (int)(e % n);
@@ -284,8 +304,14 @@ __global__ void coord_count_kernel(const int8_t* __restrict__ G, int64_t K, int 
     if (s_cnt[i]) atomicAdd(&cnt[i], s_cnt[i]);
 }
 
+__global__ void coord_count_kernel(const int8_t* __restrict__ G, int64_t K, int n, int ldg,
+                                   const int32_t* __restrict__ l1, uint32_t* __restrict__ cnt) {
+  coord_count_block(G, K, n, ldg, l1, cnt, blockIdx.x);
+}
+
 // the kb densest coordinates (ties to the lower index); one block of 1024
-__global__ void select_keys_kernel(const uint32_t* __restrict__ cnt, int n, int kb, int32_t* __restrict__ keys) {
+__device__ __forceinline__ void select_keys_block(const uint32_t* __restrict__ cnt, int n, int kb,
+                                                  int32_t* __restrict__ keys) {
   __shared__ unsigned long long s_best[32];
   __shared__ int s_taken[kKeyCoords];
   for (int b = 0; b < kb; ++b) {
@@ -316,11 +342,14 @@ __global__ void select_keys_kernel(const uint32_t* __restrict__ cnt, int n, int 
   }
 }
 
+__global__ void select_keys_kernel(const uint32_t* __restrict__ cnt, int n, int kb, int32_t* __restrict__ keys) {
+  select_keys_block(cnt, n, kb, keys);
+}
+
 // pattern list of the row at sorted position q
-__global__ void key_kernel(const int8_t* __restrict__ G, int ldg, const uint32_t* __restrict__ s_idx, int64_t nvalid,
-                           const int32_t* __restrict__ keys, int kb, uint16_t* __restrict__ s_list) {
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= nvalid) return;
+__device__ __forceinline__ void key_row(const int8_t* __restrict__ G, int ldg, const uint32_t* __restrict__ s_idx,
+                                        int64_t q, const int32_t* __restrict__ keys, int kb,
+                                        uint16_t* __restrict__ s_list) {
   const int8_t* g = G + (int64_t)s_idx[q] * ldg;
   int idx = 0, p3 = 1;
   for (int b = 0; b < kb; ++b) {
@@ -331,32 +360,45 @@ __global__ void key_kernel(const int8_t* __restrict__ G, int ldg, const uint32_t
   s_list[q] = (uint16_t)idx;
 }
 
+__global__ void key_kernel(const int8_t* __restrict__ G, int ldg, const uint32_t* __restrict__ s_idx, int64_t nvalid,
+                           const int32_t* __restrict__ keys, int kb, uint16_t* __restrict__ s_list) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nvalid) return;
+  key_row(G, ldg, s_idx, q, keys, kb, s_list);
+}
+
 // stable partition by list, step 1: counts per (list, block of positions)
-__global__ void part_count_kernel(const uint16_t* __restrict__ s_list, int64_t nvalid, int nlists, int nblk,
-                                  uint32_t* __restrict__ bc) {
+__device__ __forceinline__ void part_count_block(const uint16_t* __restrict__ s_list, int64_t nvalid, int nlists,
+                                                 int nblk, uint32_t* __restrict__ bc, int64_t bx) {
   __shared__ uint32_t s_c[kLists];
   for (int L = threadIdx.x; L < nlists; L += blockDim.x) s_c[L] = 0;
   __syncthreads();
-  const int64_t q = (int64_t)blockIdx.x * kPartBlock + threadIdx.x;
+  const int64_t q = bx * kPartBlock + threadIdx.x;
   if (q < nvalid) atomicAdd(&s_c[s_list[q]], 1u);
   __syncthreads();
-  for (int L = threadIdx.x; L < nlists; L += blockDim.x) bc[(int64_t)L * nblk + blockIdx.x] = s_c[L];
+  for (int L = threadIdx.x; L < nlists; L += blockDim.x) bc[(int64_t)L * nblk + bx] = s_c[L];
+}
+
+__global__ void part_count_kernel(const uint16_t* __restrict__ s_list, int64_t nvalid, int nlists, int nblk,
+                                  uint32_t* __restrict__ bc) {
+  part_count_block(s_list, nvalid, nlists, nblk, bc, blockIdx.x);
 }
 
 // step 2 (one warp per block of positions, in position order): rank among
 // the earlier rows of the same list, then move the row's sorted data
-__global__ void part_scatter_kernel(const uint16_t* __restrict__ s_list, int64_t nvalid, int nlists, int nblk,
-                                    const uint32_t* __restrict__ boff, const uint32_t* __restrict__ s_idx,
-                                    const uint64_t* __restrict__ s_pk, const ulonglong2* __restrict__ s_sig,
-                                    const int32_t* __restrict__ s_l1, uint32_t* __restrict__ p_idx,
-                                    uint64_t* __restrict__ p_pk, ulonglong2* __restrict__ p_sig,
-                                    int32_t* __restrict__ p_l1) {
+__device__ __forceinline__ void part_scatter_block(const uint16_t* __restrict__ s_list, int64_t nvalid, int nlists,
+                                                   int nblk, const uint32_t* __restrict__ boff,
+                                                   const uint32_t* __restrict__ s_idx, const uint64_t* __restrict__ s_pk,
+                                                   const ulonglong2* __restrict__ s_sig,
+                                                   const int32_t* __restrict__ s_l1, uint32_t* __restrict__ p_idx,
+                                                   uint64_t* __restrict__ p_pk, ulonglong2* __restrict__ p_sig,
+                                                   int32_t* __restrict__ p_l1, int64_t bx) {
   __shared__ uint32_t s_run[kLists];
   const int lane = threadIdx.x;
-  for (int L = lane; L < nlists; L += 32) s_run[L] = boff[(int64_t)L * nblk + blockIdx.x];
+  for (int L = lane; L < nlists; L += 32) s_run[L] = boff[(int64_t)L * nblk + bx];
   __syncwarp();
   for (int it = 0; it < kPartBlock / 32; ++it) {
-    const int64_t q = (int64_t)blockIdx.x * kPartBlock + it * 32 + lane;
+    const int64_t q = bx * kPartBlock + it * 32 + lane;
     const int L = q < nvalid ? (int)s_list[q] : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, L);
     const uint32_t rank = __popc(peers & ((1u << lane) - 1));
@@ -372,6 +414,16 @@ __global__ void part_scatter_kernel(const uint16_t* __restrict__ s_list, int64_t
       p_l1[dst] = s_l1[q];
     }
   }
+}
+
+__global__ void part_scatter_kernel(const uint16_t* __restrict__ s_list, int64_t nvalid, int nlists, int nblk,
+                                    const uint32_t* __restrict__ boff, const uint32_t* __restrict__ s_idx,
+                                    const uint64_t* __restrict__ s_pk, const ulonglong2* __restrict__ s_sig,
+                                    const int32_t* __restrict__ s_l1, uint32_t* __restrict__ p_idx,
+                                    uint64_t* __restrict__ p_pk, ulonglong2* __restrict__ p_sig,
+                                    int32_t* __restrict__ p_l1) {
+  part_scatter_block(s_list, nvalid, nlists, nblk, boff, s_idx, s_pk, s_sig, s_l1, p_idx, p_pk, p_sig, p_l1,
+                     blockIdx.x);
 }
 
 // list starts: lstart[L] = boff[L * nblk], lstart[nlists] = nvalid
@@ -416,15 +468,16 @@ constexpr int kChunk = 4096;  // rows of a source list scanned by one block
 // coordinates 0..31 packed in one word (pos | neg << 32), then the folded
 // 64-bit signatures of all coordinates, before the full test.  A dominated
 // row gets dom[k] = 1 (several units may write it).
-__global__ void dominance_kernel(const int8_t* __restrict__ G, int n, int ldg, int W, const uint64_t* __restrict__ masks,
-                                 const int4* __restrict__ gblk, const uint32_t* __restrict__ lstart, int kb,
-                                 const uint32_t* __restrict__ p_idx, const uint64_t* __restrict__ p_pk,
-                                 const ulonglong2* __restrict__ p_sig, const int32_t* __restrict__ p_l1,
-                                 uint8_t* __restrict__ dom) {
+__device__ __forceinline__ void dominance_block(const int8_t* __restrict__ G, int n, int ldg, int W,
+                                                const uint64_t* __restrict__ masks, const int4 gb,
+                                                const uint32_t* __restrict__ lstart, int kb,
+                                                const uint32_t* __restrict__ p_idx, const uint64_t* __restrict__ p_pk,
+                                                const ulonglong2* __restrict__ p_sig, const int32_t* __restrict__ p_l1,
+                                                uint8_t* __restrict__ dom, int by, int bz) {
   __shared__ int s_maxl1;
-  const int4 gb = gblk[blockIdx.x];  // first position, rows, pattern list
   const int nsub = 1 << kb;
-  const int o = (int)blockIdx.y / nsub, N = (int)blockIdx.y % nsub;
+  if (by >= 2 * nsub) return;  // batch: a unit beyond this instance's orientations and subsets
+  const int o = by / nsub, N = by % nsub;
   // g's pattern digits; the source pattern keeps digits in N (reversed for o = 1)
   int nzmask = 0, S = 0;
   {
@@ -439,7 +492,7 @@ __global__ void dominance_kernel(const int8_t* __restrict__ G, int n, int ldg, i
   }
   if ((N & ~nzmask) != 0 || (N == 0 && o == 1)) return;  // uniform over the block
   const int mode = N == 0 ? 3 : (o == 0 ? 1 : 2);  // bit 0: h ⊑ g, bit 1: -h ⊑ g
-  const uint32_t lo = lstart[S] + blockIdx.z * (uint32_t)kChunk, s_end = lstart[S + 1];
+  const uint32_t lo = lstart[S] + (uint32_t)bz * (uint32_t)kChunk, s_end = lstart[S + 1];
   if (lo >= s_end) return;
   const uint32_t hi = lo + kChunk < s_end ? lo + kChunk : s_end;
   const bool mine = (int)threadIdx.x < gb.y;
@@ -487,6 +540,15 @@ __global__ void dominance_kernel(const int8_t* __restrict__ G, int n, int ldg, i
   }
 }
 
+__global__ void dominance_kernel(const int8_t* __restrict__ G, int n, int ldg, int W, const uint64_t* __restrict__ masks,
+                                 const int4* __restrict__ gblk, const uint32_t* __restrict__ lstart, int kb,
+                                 const uint32_t* __restrict__ p_idx, const uint64_t* __restrict__ p_pk,
+                                 const ulonglong2* __restrict__ p_sig, const int32_t* __restrict__ p_l1,
+                                 uint8_t* __restrict__ dom) {
+  dominance_block(G, n, ldg, W, masks, gblk[blockIdx.x], lstart, kb, p_idx, p_pk, p_sig, p_l1, dom, blockIdx.y,
+                  blockIdx.z);
+}
+
 // keep = valid and not dominated
 __global__ void finalize_keep_kernel(const int32_t* __restrict__ l1, const uint8_t* __restrict__ dom, int64_t K,
                                      uint8_t* __restrict__ keep) {
@@ -501,21 +563,28 @@ __global__ void clear_keep_kernel(uint8_t* keep, int64_t K) {
 
 constexpr int kCompact = 1024;
 
-__global__ void count_kept_kernel(const uint8_t* __restrict__ keep, int64_t K, uint32_t* __restrict__ block_count) {
+__device__ __forceinline__ void count_kept_block(const uint8_t* __restrict__ keep, int64_t K,
+                                                 uint32_t* __restrict__ block_count, int64_t bx) {
   __shared__ uint32_t s_c;
   if (threadIdx.x == 0) s_c = 0;
   __syncthreads();
-  int64_t k = blockIdx.x * (int64_t)kCompact + threadIdx.x;
+  int64_t k = bx * (int64_t)kCompact + threadIdx.x;
   unsigned bal = __ballot_sync(0xffffffffu, k < K && keep[k]);
   if ((threadIdx.x & 31) == 0) atomicAdd(&s_c, (uint32_t)__popc(bal));
   __syncthreads();
-  if (threadIdx.x == 0) block_count[blockIdx.x] = s_c;
+  if (threadIdx.x == 0) block_count[bx] = s_c;
 }
 
-__global__ void write_kept_kernel(const int8_t* __restrict__ G, int64_t K, int ldg, const uint8_t* __restrict__ keep,
-                                  const uint32_t* __restrict__ block_start, int8_t* __restrict__ out) {
+__global__ void count_kept_kernel(const uint8_t* __restrict__ keep, int64_t K, uint32_t* __restrict__ block_count) {
+  count_kept_block(keep, K, block_count, blockIdx.x);
+}
+
+__device__ __forceinline__ void write_kept_block(const int8_t* __restrict__ G, int64_t K, int ldg,
+                                                 const uint8_t* __restrict__ keep,
+                                                 const uint32_t* __restrict__ block_start, int8_t* __restrict__ out,
+                                                 int64_t bx) {
   __shared__ uint32_t s_warp[kCompact / 32];
-  int64_t k = blockIdx.x * (int64_t)kCompact + threadIdx.x;
+  int64_t k = bx * (int64_t)kCompact + threadIdx.x;
   int f = (k < K && keep[k]) ? 1 : 0;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned bal = __ballot_sync(0xffffffffu, f);
@@ -527,10 +596,15 @@ __global__ void write_kept_kernel(const int8_t* __restrict__ G, int64_t K, int l
   }
   __syncthreads();
   if (!f) return;
-  int64_t dst = (int64_t)block_start[blockIdx.x] + s_warp[wid] + __popc(bal & ((1u << lane) - 1));
+  int64_t dst = (int64_t)block_start[bx] + s_warp[wid] + __popc(bal & ((1u << lane) - 1));
   const uint4* src = reinterpret_cast<const uint4*>(G + k * ldg);
   uint4* d4 = reinterpret_cast<uint4*>(out + dst * ldg);
   for (int c = 0; c < ldg / 16; ++c) d4[c] = src[c];
+}
+
+__global__ void write_kept_kernel(const int8_t* __restrict__ G, int64_t K, int ldg, const uint8_t* __restrict__ keep,
+                                  const uint32_t* __restrict__ block_start, int8_t* __restrict__ out) {
+  write_kept_block(G, K, ldg, keep, block_start, out, blockIdx.x);
 }
 
 int64_t l1_bins(int32_t n) { return (int64_t)127 * n + 1; }
@@ -899,5 +973,321 @@ extern "C" int mape_minimal_filter(const int8_t* G, int64_t K, int32_t n, int32_
   MAPE_CUDA_TRY(cudaMemcpyAsync(&total, bstart + nblk, 4, cudaMemcpyDeviceToHost, st));
   MAPE_CUDA_TRY(cudaStreamSynchronize(st));
   *K_out = (int64_t)total;
+  return MAPE_OK;
+}
+
+// ---- a11 for many instances at once --------------------------------------------
+//
+// Every kernel of the filter runs once over the rows (positions, blocks, g-
+// blocks) of all instances, each thread or block finding its instance by
+// binary search over the launch's prefix table; the dominance launch covers
+// the g-blocks of all instances (each g-block carries its instance).  Every
+// instance keeps its own arrays, carved from its own workspace as
+// mape_minimal_filter carves them, so its kept set and output equal those of
+// its own call.
+
+namespace {
+
+struct MinView {
+  const int8_t* G;
+  int64_t K;
+  int n, ldg, W, kb, nlists, nblk_part;
+  const uint8_t* valid;
+  uint8_t* keep;
+  int8_t* out;
+  int64_t nb, nblk, K_sample, nvalid;
+  int32_t* l1;
+  uint64_t* masks;
+  uint32_t *hist, *start, *cursor, *s_idx;
+  uint64_t* s_pk;
+  ulonglong2* s_sig;
+  int32_t* s_l1;
+  uint16_t* s_list;
+  uint32_t* p_idx;
+  uint64_t* p_pk;
+  ulonglong2* p_sig;
+  int32_t* p_l1;
+  uint32_t* cnt;
+  int32_t* keys;
+  uint32_t *bc, *boff, *lstart;
+  int4* gblk;
+  uint32_t *bcount, *bstart;
+};
+
+// phase 0: l1 and masks; 1: l1-sorted arrays; 2: keep cleared; 3: keep = valid and not dominated
+__global__ void min_rows_batch_kernel(const MinView* __restrict__ v, const int64_t* __restrict__ prefix, int count,
+                                      int phase) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= prefix[count]) return;
+  const int i = find_inst(prefix, count, t);
+  const MinView& d = v[i];
+  const int64_t k = t - prefix[i];
+  if (phase == 0) prep_row(d.G, k, d.n, d.ldg, d.W, d.valid, d.l1, d.masks, d.hist);
+  else if (phase == 1) scatter_row(d.l1, d.masks, k, d.W, d.cursor, d.s_idx, d.s_pk, d.s_sig, d.s_l1);
+  else if (phase == 2) d.keep[k] = 0;
+  else d.keep[k] = (d.l1[k] != kInvalidL1 && !d.keep[k]) ? 1 : 0;
+}
+
+// one block per instance: 0 the l1 bins, 1 the partition counts, 2 the kept-row counts
+__global__ void min_scan_batch_kernel(const MinView* __restrict__ v, int which) {
+  const MinView& d = v[blockIdx.x];
+  if (d.K == 0) return;
+  if (which == 0) bin_scan_block(d.hist, (int)d.nb, d.start, d.cursor);
+  else if (which == 1) {
+    if (d.nvalid > 0) bin_scan_block(d.bc, d.nlists * d.nblk_part, d.boff, d.boff);
+  } else {
+    bin_scan_block(d.bcount, (int)d.nblk + 1, d.bstart, d.bstart);
+  }
+}
+
+// per instance (one block each): the key coordinates; then the valid-row count
+__global__ void min_keys_batch_kernel(const MinView* __restrict__ v, int64_t* __restrict__ nvalid) {
+  const MinView& d = v[blockIdx.x];
+  if (d.K == 0) {
+    if (threadIdx.x == 0) nvalid[blockIdx.x] = 0;
+    return;
+  }
+  select_keys_block(d.cnt, d.n, d.kb, d.keys);
+  if (threadIdx.x == 0) nvalid[blockIdx.x] = (int64_t)d.start[d.nb - 1] + d.hist[d.nb - 1];
+}
+
+// prefix: blocks of 64 sampled rows
+__global__ void min_coord_batch_kernel(const MinView* __restrict__ v, const int64_t* __restrict__ prefix, int count) {
+  const int i = find_inst(prefix, count, blockIdx.x);
+  const MinView& d = v[i];
+  coord_count_block(d.G, d.K_sample, d.n, d.ldg, d.l1, d.cnt, blockIdx.x - prefix[i]);
+}
+
+// prefix: valid rows (pattern list of each)
+__global__ void min_key_rows_batch_kernel(const MinView* __restrict__ v, const int64_t* __restrict__ prefix,
+                                          int count) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= prefix[count]) return;
+  const int i = find_inst(prefix, count, t);
+  const MinView& d = v[i];
+  key_row(d.G, d.ldg, d.s_idx, t - prefix[i], d.keys, d.kb, d.s_list);
+}
+
+// prefix: partition blocks; phase 0 counts, 1 scatters
+__global__ void min_part_batch_kernel(const MinView* __restrict__ v, const int64_t* __restrict__ prefix, int count,
+                                      int phase) {
+  const int i = find_inst(prefix, count, blockIdx.x);
+  const MinView& d = v[i];
+  const int64_t b = blockIdx.x - prefix[i];
+  if (phase == 0) part_count_block(d.s_list, d.nvalid, d.nlists, d.nblk_part, d.bc, b);
+  else
+    part_scatter_block(d.s_list, d.nvalid, d.nlists, d.nblk_part, d.boff, d.s_idx, d.s_pk, d.s_sig, d.s_l1, d.p_idx,
+                       d.p_pk, d.p_sig, d.p_l1, b);
+}
+
+// prefix: list starts (nlists + 1 per instance)
+__global__ void min_list_start_batch_kernel(const MinView* __restrict__ v, const int64_t* __restrict__ prefix,
+                                            int count) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= prefix[count]) return;
+  const int i = find_inst(prefix, count, t);
+  const MinView& d = v[i];
+  const int L = (int)(t - prefix[i]);
+  d.lstart[L] = L < d.nlists ? d.boff[(int64_t)L * d.nblk_part] : (uint32_t)d.nvalid;
+}
+
+// the g-blocks of all instances (.w: instance)
+__global__ void min_dominance_batch_kernel(const MinView* __restrict__ v, const int4* __restrict__ gblk) {
+  const int4 gb = gblk[blockIdx.x];
+  const MinView& d = v[gb.w];
+  dominance_block(d.G, d.n, d.ldg, d.W, d.masks, gb, d.lstart, d.kb, d.p_idx, d.p_pk, d.p_sig, d.p_l1, d.keep,
+                  blockIdx.y, blockIdx.z);
+}
+
+// prefix: compaction blocks; phase 0 counts, 1 writes
+__global__ void min_compact_batch_kernel(const MinView* __restrict__ v, const int64_t* __restrict__ prefix, int count,
+                                         int phase) {
+  const int i = find_inst(prefix, count, blockIdx.x);
+  const MinView& d = v[i];
+  const int64_t b = blockIdx.x - prefix[i];
+  if (phase == 0) count_kept_block(d.keep, d.K, d.bcount, b);
+  else write_kept_block(d.G, d.K, d.ldg, d.keep, d.bstart, d.out, b);
+}
+
+int64_t min_gblocks_cap(int64_t K, int n) {
+  const int kb = n < kKeyCoords ? n : kKeyCoords;
+  int nlists = 1;
+  for (int b = 0; b < kb; ++b) nlists *= 3;
+  return mape_detail::ceil_div(K, kTile) + nlists;
+}
+
+}  // namespace
+
+extern "C" size_t mape_minimal_filter_batch_workspace_bytes(const mape_minimal_item* items, int32_t count) {
+  if (!items || count <= 0) return 0;
+  int64_t gb = 0;
+  for (int i = 0; i < count; ++i) gb += items[i].K > 0 && items[i].n > 0 ? min_gblocks_cap(items[i].K, items[i].n) : 0;
+  mape_detail::Sizer s;
+  s.take<MinView>((size_t)count);
+  s.take<int64_t>((size_t)6 * (count + 1));  // prefix tables
+  s.take<int64_t>((size_t)count);            // valid rows per instance
+  s.take<int4>((size_t)(gb > 0 ? gb : 1));   // g-blocks of all instances
+  return s.bytes();
+}
+
+extern "C" int mape_minimal_filter_batch(mape_minimal_item* items, int32_t count, void* workspace,
+                                         size_t workspace_bytes, void* stream) {
+  using namespace mape_detail;
+  if (!items || count <= 0) return MAPE_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    const mape_minimal_item& it = items[i];
+    if (it.K < 0 || it.n <= 0 || it.ldg < it.n || it.ldg % 16 != 0 || (it.K > 0 && (!it.G || !it.keep || !it.out)))
+      return MAPE_ERR_INVALID_ARG;
+    if (it.n > 4096 || it.K >= ((int64_t)1 << 31)) return MAPE_ERR_SHAPE;
+  }
+  int64_t gb_cap = 0;
+  for (int i = 0; i < count; ++i) gb_cap += items[i].K > 0 ? min_gblocks_cap(items[i].K, items[i].n) : 0;
+  Carver bc(workspace, workspace_bytes);
+  MinView* d_views = bc.take<MinView>((size_t)count);
+  int64_t* d_px = bc.take<int64_t>((size_t)6 * (count + 1));
+  int64_t* d_nvalid = bc.take<int64_t>((size_t)count);
+  int4* d_gblk = bc.take<int4>((size_t)(gb_cap > 0 ? gb_cap : 1));
+  if (!bc.ok) return MAPE_ERR_CAPACITY;
+  cudaStream_t st = as_stream(stream);
+  const int n1 = count + 1;
+  std::vector<int64_t> px((size_t)6 * n1, 0);
+  auto prefix = [&](int t, auto units) -> int64_t {
+    int64_t* p = px.data() + (size_t)t * n1;
+    p[0] = 0;
+    for (int i = 0; i < count; ++i) p[i + 1] = p[i] + units(i);
+    return p[count];
+  };
+  auto dpx = [&](int t) -> const int64_t* { return d_px + (size_t)t * n1; };
+  std::vector<MinView> v((size_t)count);
+  int max_n = 1;
+  for (int i = 0; i < count; ++i) {
+    mape_minimal_item& it = items[i];
+    it.K_out = 0;
+    MinView& d = v[(size_t)i];
+    d = MinView{};
+    d.G = it.G; d.K = it.K; d.n = it.n; d.ldg = it.ldg; d.valid = it.valid; d.keep = it.keep; d.out = it.out;
+    if (it.K == 0) continue;
+    const int64_t K = it.K;
+    const int n = it.n;
+    d.W = (n + 63) / 64;
+    d.nb = l1_bins(n);
+    d.nblk = ceil_div(K, kCompact);
+    const int64_t nblk_part_max = ceil_div(K, kPartBlock);
+    d.kb = n < kKeyCoords ? n : kKeyCoords;
+    d.nlists = 1;
+    for (int b = 0; b < d.kb; ++b) d.nlists *= 3;
+    d.K_sample = K < kDensitySample ? K : kDensitySample;
+    max_n = std::max(max_n, n);
+    // the same carve as mape_minimal_filter
+    Carver cv(it.workspace, it.workspace_bytes);
+    d.l1 = cv.take<int32_t>((size_t)K);
+    d.masks = cv.take<uint64_t>((size_t)K * 2 * d.W);
+    d.hist = cv.take<uint32_t>((size_t)d.nb);
+    d.start = cv.take<uint32_t>((size_t)d.nb);
+    d.cursor = cv.take<uint32_t>((size_t)d.nb);
+    d.s_idx = cv.take<uint32_t>((size_t)K);
+    d.s_pk = cv.take<uint64_t>((size_t)K);
+    d.s_sig = cv.take<ulonglong2>((size_t)K);
+    d.s_l1 = cv.take<int32_t>((size_t)K);
+    d.s_list = cv.take<uint16_t>((size_t)K);
+    d.p_idx = cv.take<uint32_t>((size_t)K);
+    d.p_pk = cv.take<uint64_t>((size_t)K);
+    d.p_sig = cv.take<ulonglong2>((size_t)K);
+    d.p_l1 = cv.take<int32_t>((size_t)K);
+    d.cnt = cv.take<uint32_t>((size_t)n);
+    d.keys = cv.take<int32_t>((size_t)kKeyCoords);
+    d.bc = cv.take<uint32_t>((size_t)kLists * nblk_part_max);
+    d.boff = cv.take<uint32_t>((size_t)kLists * nblk_part_max + 1);
+    d.lstart = cv.take<uint32_t>((size_t)kLists + 1);
+    d.gblk = cv.take<int4>((size_t)ceil_div(K, kTile) + kLists);
+    d.bcount = cv.take<uint32_t>((size_t)d.nblk + 1);
+    d.bstart = cv.take<uint32_t>((size_t)d.nblk + 1);
+    if (!cv.ok) return MAPE_ERR_CAPACITY;
+    MAPE_CUDA_TRY(cudaMemsetAsync(d.hist, 0, sizeof(uint32_t) * d.nb, st));
+    MAPE_CUDA_TRY(cudaMemsetAsync(d.bcount, 0, sizeof(uint32_t) * (d.nblk + 1), st));
+    MAPE_CUDA_TRY(cudaMemsetAsync(d.cnt, 0, sizeof(uint32_t) * n, st));
+  }
+  enum { kRows, kCoord, kValid, kPart, kLs, kCmp };
+  const int64_t rows = prefix(kRows, [&](int i) { return v[(size_t)i].K; });
+  if (rows == 0) return MAPE_OK;
+  const int64_t cblocks = prefix(kCoord, [&](int i) { return ceil_div(v[(size_t)i].K_sample, 64); });
+  const int64_t cmp = prefix(kCmp, [&](int i) { return v[(size_t)i].K > 0 ? v[(size_t)i].nblk : 0; });
+  MAPE_CUDA_TRY(cudaMemcpyAsync(d_views, v.data(), sizeof(MinView) * count, cudaMemcpyHostToDevice, st));
+  MAPE_CUDA_TRY(cudaMemcpyAsync(d_px, px.data(), sizeof(int64_t) * px.size(), cudaMemcpyHostToDevice, st));
+  const unsigned gr = (unsigned)ceil_div(rows, kTile);
+  const MinView* cv_ = d_views;
+  // l1 norms and masks, the l1 order, cleared flags, the key coordinates
+  launch(min_rows_batch_kernel, gr, kTile, 0, st, cv_, dpx(kRows), (int)count, 0);
+  launch(min_scan_batch_kernel, (unsigned)count, 1024, 0, st, cv_, 0);
+  launch(min_rows_batch_kernel, gr, kTile, 0, st, cv_, dpx(kRows), (int)count, 1);
+  launch(min_rows_batch_kernel, gr, kTile, 0, st, cv_, dpx(kRows), (int)count, 2);
+  launch(min_coord_batch_kernel, (unsigned)cblocks, 256, sizeof(uint32_t) * max_n, st, cv_, dpx(kCoord), (int)count);
+  launch(min_keys_batch_kernel, (unsigned)count, 1024, 0, st, cv_, d_nvalid);
+  MAPE_LAUNCH_CHECK();
+  std::vector<int64_t> nvalid((size_t)count, 0);
+  MAPE_CUDA_TRY(cudaMemcpyAsync(nvalid.data(), d_nvalid, sizeof(int64_t) * count, cudaMemcpyDeviceToHost, st));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < count; ++i) {
+    v[(size_t)i].nvalid = nvalid[(size_t)i];
+    v[(size_t)i].nblk_part = (int)ceil_div(nvalid[(size_t)i], kPartBlock);
+  }
+  const int64_t valid_rows = prefix(kValid, [&](int i) { return v[(size_t)i].nvalid; });
+  if (valid_rows > 0) {
+    // pattern lists, each in l1 order
+    const int64_t pblocks = prefix(kPart, [&](int i) { return (int64_t)v[(size_t)i].nblk_part; });
+    const int64_t ls = prefix(kLs, [&](int i) { return v[(size_t)i].nvalid > 0 ? v[(size_t)i].nlists + 1 : 0; });
+    MAPE_CUDA_TRY(cudaMemcpyAsync(d_views, v.data(), sizeof(MinView) * count, cudaMemcpyHostToDevice, st));
+    MAPE_CUDA_TRY(cudaMemcpyAsync(d_px + (size_t)kValid * n1, px.data() + (size_t)kValid * n1,
+                                  sizeof(int64_t) * 3 * n1, cudaMemcpyHostToDevice, st));
+    launch(min_key_rows_batch_kernel, (unsigned)ceil_div(valid_rows, kTile), kTile, 0, st, cv_, dpx(kValid),
+           (int)count);
+    launch(min_part_batch_kernel, (unsigned)pblocks, kPartBlock, 0, st, cv_, dpx(kPart), (int)count, 0);
+    launch(min_scan_batch_kernel, (unsigned)count, 1024, 0, st, cv_, 1);
+    launch(min_part_batch_kernel, (unsigned)pblocks, 32, 0, st, cv_, dpx(kPart), (int)count, 1);
+    launch(min_list_start_batch_kernel, (unsigned)ceil_div(ls, 256), 256, 0, st, cv_, dpx(kLs), (int)count);
+    MAPE_LAUNCH_CHECK();
+    std::vector<std::vector<uint32_t>> lst((size_t)count);
+    for (int i = 0; i < count; ++i) {
+      if (v[(size_t)i].nvalid == 0) continue;
+      lst[(size_t)i].resize((size_t)v[(size_t)i].nlists + 1);
+      MAPE_CUDA_TRY(cudaMemcpyAsync(lst[(size_t)i].data(), v[(size_t)i].lstart, sizeof(uint32_t) * lst[(size_t)i].size(),
+                                    cudaMemcpyDeviceToHost, st));
+    }
+    MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+    // g-blocks of every instance: runs of at most kTile rows of one list
+    std::vector<int4> gb;
+    uint32_t max_list = 0;
+    int max_kb = 0;
+    for (int i = 0; i < count; ++i) {
+      if (v[(size_t)i].nvalid == 0) continue;
+      max_kb = std::max(max_kb, v[(size_t)i].kb);
+      const std::vector<uint32_t>& l = lst[(size_t)i];
+      for (int L = 0; L < v[(size_t)i].nlists; ++L) {
+        const uint32_t a = l[(size_t)L], b = l[(size_t)L + 1];
+        max_list = std::max(max_list, b - a);
+        for (uint32_t o = a; o < b; o += kTile)
+          gb.push_back(make_int4((int)o, (int)std::min<uint32_t>(kTile, b - o), L, i));
+      }
+    }
+    if (!gb.empty()) {
+      if ((int64_t)gb.size() > gb_cap) return MAPE_ERR_CAPACITY;
+      MAPE_CUDA_TRY(cudaMemcpyAsync(d_gblk, gb.data(), sizeof(int4) * gb.size(), cudaMemcpyHostToDevice, st));
+      const dim3 grid((unsigned)gb.size(), 2u << max_kb, (unsigned)ceil_div(max_list, kChunk));
+      launch(min_dominance_batch_kernel, grid, kTile, 0, st, cv_, (const int4*)d_gblk);
+    }
+  }
+  // keep flags, then the kept rows in input order
+  launch(min_rows_batch_kernel, gr, kTile, 0, st, cv_, dpx(kRows), (int)count, 3);
+  launch(min_compact_batch_kernel, (unsigned)cmp, kCompact, 0, st, cv_, dpx(kCmp), (int)count, 0);
+  launch(min_scan_batch_kernel, (unsigned)count, 1024, 0, st, cv_, 2);
+  launch(min_compact_batch_kernel, (unsigned)cmp, kCompact, 0, st, cv_, dpx(kCmp), (int)count, 1);
+  MAPE_LAUNCH_CHECK();
+  std::vector<uint32_t> tot((size_t)count, 0);
+  for (int i = 0; i < count; ++i)
+    if (v[(size_t)i].K > 0)
+      MAPE_CUDA_TRY(cudaMemcpyAsync(&tot[(size_t)i], v[(size_t)i].bstart + v[(size_t)i].nblk, 4,
+                                    cudaMemcpyDeviceToHost, st));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < count; ++i) items[i].K_out = (int64_t)tot[(size_t)i];
   return MAPE_OK;
 }

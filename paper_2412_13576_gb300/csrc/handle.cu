@@ -199,6 +199,7 @@ struct mape_instance {
   int chunk_candidates(cudaStream_t s, int64_t* cnt);
   void chunk_merged(int chunk, int64_t cnt, int64_t K_new);
   int extract_filter();
+  int filter_done(int64_t fails, int64_t Kk, double t_ext, double t_fil);
 
   int run_extract();
   // Algorithm 1 (the parts of run_augment, also driven by a batch)
@@ -303,7 +304,11 @@ int mape_instance::extract_filter() {
   H_TRY(mape_minimal_filter(ex_cur, ex_U, n, ldg, dOk, dKeep, ex_other, &Kk, dWork, work_bytes, s));
   H_TRY(mape_direction_coeffs(dqr, dqc, dqv, nnz, has_w ? dw : nullptr, n, ex_other, Kk, ldg, da, dq4, s));
   MAPE_CUDA_TRY(cudaStreamSynchronize(s));
-  double t_fil = now_ms();
+  return filter_done(fails, Kk, t_ext, now_ms());
+}
+
+// The direction set after the filter stages (kept rows in ex_other).
+int mape_instance::filter_done(int64_t fails, int64_t Kk, double t_ext, double t_fil) {
   dirs = ex_other;
   K = Kk;
   std::lock_guard<std::mutex> lk(mu);
@@ -634,6 +639,45 @@ int run_batch_steps(ExtractBatch& b) {
   return MAPE_OK;
 }
 
+// The filter stages of every handle of the batch, each as one batched call:
+// the kernel test, the minimality filter and the coefficients.
+int run_batch_filter(ExtractBatch& b) {
+  const int count = (int)b.hs.size();
+  mape_handle h0 = b.hs[0];
+  const double t_ext = now_ms();
+  for (auto h : b.hs) h->set_phase(MAPE_PHASE_FILTERING);
+  std::vector<mape_kernel_test_item> kt((size_t)count);
+  std::vector<mape_minimal_item> mi((size_t)count);
+  std::vector<mape_coeffs_item> ci((size_t)count);
+  for (int i = 0; i < count; ++i) {
+    mape_handle h = b.hs[i];
+    kt[(size_t)i] = mape_kernel_test_item{h->dA, h->m, h->n, h->ex_cur, h->ex_U, h->ldg, 0, h->dOk, 0,
+                                          h->dWork, h->work_bytes};
+    // the kept rows go to the buffer of the pair that the last merge left free
+    mi[(size_t)i] = mape_minimal_item{h->ex_cur, h->ex_U, h->n, h->ldg, h->dOk, h->dKeep, h->ex_other, 0,
+                                      h->dWork, h->work_bytes};
+  }
+  const size_t b1 = mape_kernel_test_batch_workspace_bytes(count);
+  const size_t b2 = mape_minimal_filter_batch_workspace_bytes(mi.data(), count);
+  const size_t b3 = mape_direction_coeffs_batch_workspace_bytes(count);
+  const size_t wb = std::max(b1, std::max(b2, b3));
+  void* ws = h0->take<char>(h0->job_bufs, wb);
+  if (!ws) return MAPE_ERR_OOM;
+  H_TRY(mape_kernel_test_batch(kt.data(), count, ws, wb, h0->stream));
+  H_TRY(mape_minimal_filter_batch(mi.data(), count, ws, wb, h0->stream));
+  for (int i = 0; i < count; ++i) {
+    mape_handle h = b.hs[i];
+    ci[(size_t)i] = mape_coeffs_item{h->dqr, h->dqc, h->dqv, h->nnz, h->n, h->has_w ? h->dw : nullptr, h->ex_other,
+                                     mi[(size_t)i].K_out, h->ldg, 0, h->da, h->dq4};
+  }
+  H_TRY(mape_direction_coeffs_batch(ci.data(), count, ws, wb, h0->stream));
+  MAPE_CUDA_TRY(cudaStreamSynchronize(h0->stream));
+  const double t_fil = now_ms();
+  for (int i = 0; i < count; ++i) b.rcs[(size_t)i] = b.hs[i]->filter_done(kt[(size_t)i].fail_count, mi[(size_t)i].K_out,
+                                                                           t_ext, t_fil);
+  return MAPE_OK;
+}
+
 }  // namespace
 
 extern "C" int mape_extract_directions(mape_handle h, int32_t P, const float* Z0, const float* G0) {
@@ -677,7 +721,9 @@ extern "C" int mape_extract_directions_batch(mape_handle* hs, int32_t count, con
       cudaSetDevice(h->dev);
       int r = MAPE_OK;
       if (i == 0) {
+        b->rcs.assign(b->hs.size(), MAPE_OK);
         r = run_batch_steps(*b);
+        if (r == MAPE_OK) r = run_batch_filter(*b);
         std::lock_guard<std::mutex> lk(b->mu);
         b->rc = r;
         b->done = true;
@@ -687,7 +733,7 @@ extern "C" int mape_extract_directions_batch(mape_handle* hs, int32_t count, con
         b->cv.wait(lk, [&] { return b->done; });
         r = b->rc;
       }
-      if (r == MAPE_OK) r = h->extract_filter();
+      if (r == MAPE_OK) r = b->rcs[(size_t)i];
       h->finish(r);
     });
   }

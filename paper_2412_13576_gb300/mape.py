@@ -75,6 +75,21 @@ class DedupItem(C.Structure):
                 ("K", I64), ("status", I32), ("pad0", I32), ("workspace", P_), ("workspace_bytes", C.c_size_t)]
 
 
+class KernelTestItem(C.Structure):
+    _fields_ = [("A", P_), ("m", I32), ("n", I32), ("G", P_), ("K", I64), ("ldg", I32), ("pad0", I32), ("ok", P_),
+                ("fail_count", I64), ("workspace", P_), ("workspace_bytes", C.c_size_t)]
+
+
+class MinimalItem(C.Structure):
+    _fields_ = [("G", P_), ("K", I64), ("n", I32), ("ldg", I32), ("valid", P_), ("keep", P_), ("out", P_),
+                ("K_out", I64), ("workspace", P_), ("workspace_bytes", C.c_size_t)]
+
+
+class CoeffsItem(C.Structure):
+    _fields_ = [("q_row", P_), ("q_col", P_), ("q_val", P_), ("nnz", I32), ("n", I32), ("w", P_), ("G", P_),
+                ("K", I64), ("ldg", I32), ("pad0", I32), ("a", P_), ("q4", P_)]
+
+
 class AugTuneInfo(C.Structure):
     _fields_ = [("lanes", I32), ("candidates", I32), ("cand_lanes", I32 * 8), ("probe_ms", F32 * 8)]
 
@@ -166,6 +181,12 @@ _SIGS = {
     "mape_autotune_clear": (None, []),
     "mape_dedup_workspace_bytes": (C.c_size_t, [I64, I32]),
     "mape_dedup": (C.c_int, [P_, I64, I32, I32, P_, I64, C.POINTER(I64), P_, C.c_size_t, P_]),
+    "mape_kernel_test_batch_workspace_bytes": (C.c_size_t, [I32]),
+    "mape_kernel_test_batch": (C.c_int, [C.POINTER(KernelTestItem), I32, P_, C.c_size_t, P_]),
+    "mape_minimal_filter_batch_workspace_bytes": (C.c_size_t, [C.POINTER(MinimalItem), I32]),
+    "mape_minimal_filter_batch": (C.c_int, [C.POINTER(MinimalItem), I32, P_, C.c_size_t, P_]),
+    "mape_direction_coeffs_batch_workspace_bytes": (C.c_size_t, [I32]),
+    "mape_direction_coeffs_batch": (C.c_int, [C.POINTER(CoeffsItem), I32, P_, C.c_size_t, P_]),
     "mape_dedup_batch_workspace_bytes": (C.c_size_t, [I32]),
     "mape_dedup_batch": (C.c_int, [C.POINTER(DedupItem), I32, P_, C.c_size_t, P_]),
     "mape_dedup_static_max_rows": (I64, []),
@@ -467,6 +488,72 @@ def dedup_batch(sets, stream=None):
         _check(rc, "mape_dedup_batch")
     return [(keep[i][0][: items[i].K] if items[i].status == OK else keep[i][0][:0], items[i].K, items[i].status)
             for i in range(k)]
+
+
+def kernel_test_batch(cases, stream=None):
+    """mape_kernel_test_batch: a9 for several instances in one sequence of
+    launches.  cases: (A [m x n] int32, G [K x ldg] int8, n) CUDA tensors.
+    Returns one (ok [K] uint8, failures) per case."""
+    import torch
+    k = len(cases)
+    items = (KernelTestItem * k)()
+    keep = []
+    for i, (A, G, n) in enumerate(cases):
+        m, K = A.shape[0], G.shape[0]
+        ok = torch.empty(max(K, 1), dtype=torch.uint8, device=G.device)
+        ws = _workspace(lib().mape_kernel_test_workspace_bytes(m, n), G.device)
+        keep.append((ok, ws))
+        it = items[i]
+        it.A, it.m, it.n, it.G, it.K, it.ldg, it.ok = _ptr(A), m, n, _ptr(G), K, G.shape[1], _ptr(ok)
+        it.workspace, it.workspace_bytes = _ptr(ws), ws.numel()
+    bws = _workspace(lib().mape_kernel_test_batch_workspace_bytes(k), cases[0][1].device)
+    _check(lib().mape_kernel_test_batch(items, k, _ptr(bws), bws.numel(), _stream(stream)), "mape_kernel_test_batch")
+    return [(keep[i][0][: cases[i][1].shape[0]], items[i].fail_count) for i in range(k)]
+
+
+def minimal_filter_batch(cases, stream=None):
+    """mape_minimal_filter_batch: a11 for several instances.  cases: (G [K x
+    ldg] int8 CUDA tensor, n, valid [K] uint8 tensor or None).  Returns one
+    (keep [K] uint8, kept rows [K_out x ldg]) per case."""
+    import torch
+    k = len(cases)
+    items = (MinimalItem * k)()
+    keep = []
+    for i, (G, n, valid) in enumerate(cases):
+        K, ldg = G.shape
+        kp = torch.empty(max(K, 1), dtype=torch.uint8, device=G.device)
+        out = torch.empty((max(K, 1), ldg), dtype=torch.int8, device=G.device)
+        ws = _workspace(lib().mape_minimal_workspace_bytes(K, n), G.device)
+        keep.append((kp, out, ws))
+        it = items[i]
+        it.G, it.K, it.n, it.ldg, it.valid = _ptr(G), K, n, ldg, _ptr(valid)
+        it.keep, it.out, it.workspace, it.workspace_bytes = _ptr(kp), _ptr(out), _ptr(ws), ws.numel()
+    bws = _workspace(lib().mape_minimal_filter_batch_workspace_bytes(items, k), cases[0][0].device)
+    _check(lib().mape_minimal_filter_batch(items, k, _ptr(bws), bws.numel(), _stream(stream)),
+           "mape_minimal_filter_batch")
+    return [(keep[i][0][: cases[i][0].shape[0]], keep[i][1][: items[i].K_out]) for i in range(k)]
+
+
+def direction_coeffs_batch(cases, stream=None):
+    """mape_direction_coeffs_batch: a12 for several instances.  cases: (qr,
+    qc, qv, w or None, n, G) CUDA tensors.  Returns one (a, q4) per case."""
+    import torch
+    k = len(cases)
+    items = (CoeffsItem * k)()
+    keep = []
+    for i, (qr, qc, qv, w, n, G) in enumerate(cases):
+        K, ldg = G.shape
+        a = torch.empty(max(K, 1), dtype=torch.int64, device=G.device)
+        q4 = torch.empty(max(K, 1), dtype=torch.int64, device=G.device)
+        keep.append((a, q4))
+        it = items[i]
+        it.q_row, it.q_col, it.q_val, it.nnz, it.n, it.w = _ptr(qr), _ptr(qc), _ptr(qv), qv.numel(), n, _ptr(w)
+        it.G, it.K, it.ldg, it.a, it.q4 = _ptr(G), K, ldg, _ptr(a), _ptr(q4)
+    bws = _workspace(lib().mape_direction_coeffs_batch_workspace_bytes(k), cases[0][5].device)
+    _check(lib().mape_direction_coeffs_batch(items, k, _ptr(bws), bws.numel(), _stream(stream)),
+           "mape_direction_coeffs_batch")
+    torch.cuda.synchronize()
+    return [(keep[i][0][: cases[i][5].shape[0]], keep[i][1][: cases[i][5].shape[0]]) for i in range(k)]
 
 
 def kernel_test(A, G, n, stream=None):
