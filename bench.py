@@ -84,6 +84,7 @@ def parse_args(argv=None):
     ap.add_argument("--serve-plain", type=int, default=24, metavar="N",
                     help="the plain FP32 one-at-a-time comparison runs the first N requests of the stream")
     ap.add_argument("--serve-T", type=int, default=1000, help="Adam steps per request in the serving measurement")
+    ap.add_argument("--serve-slots", type=int, default=16, help="requests on the device at once in the serving measurement")
     ap.add_argument("--batch", type=int, default=64, metavar="N",
                     help="instances in the batched-extraction measurement (n log-uniform in [50, 1000], m = n/5, "
                          "P in {1024, 4096, 16384}, T = 1000); 0 skips it")
@@ -457,7 +458,7 @@ def run_ours(args):
             result["batched"] = batch_measure(args.batch)
             result["batched"]["pipeline"] = batch_pipeline_measure(args.batch)
         if args.serve > 0 and world == 1:
-            result["serving"] = serve_measure(args.serve, args.serve_T, args.serve_plain)
+            result["serving"] = serve_measure(args.serve, args.serve_T, args.serve_plain, slots=args.serve_slots)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -623,7 +624,7 @@ def _pct(v, q):
     return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
 
 
-def serve_measure(N, T, n_plain=24, seed=3000):
+def serve_measure(N, T, n_plain=24, seed=3000, slots=16):
     """The serving workload: N requests arriving as a Poisson stream at 200/s
     over SERVE_DISTINCT distinct instances taken in turn (n log-uniform in
     [30, 3000], m = n/5, C in [-3,3] at a density uniform in [0.05, 0.2], box
@@ -674,8 +675,8 @@ def serve_measure(N, T, n_plain=24, seed=3000):
         return infos, wall, stats, backlog
 
     out = {}
-    for name, prec, slots, count, batch in (("served_bf16", PREC["bf16"], 16, N, False),
-                                            ("served_bf16_batched_extraction", PREC["bf16"], 16, N, True),
+    for name, prec, slots, count, batch in (("served_bf16", PREC["bf16"], slots, N, False),
+                                            ("served_bf16_batched_extraction", PREC["bf16"], slots, N, True),
                                             ("plain_fp32_one_at_a_time", 0, 1, min(n_plain, N), False)):
         cfg = mape.default_config(T=T, precision=prec)
         infos, wall, stats, backlog = run_server(cfg, slots, count, batch)
