@@ -95,6 +95,8 @@ def parse_args(argv=None):
                     help="with --streamed-case: let the library choose the implementation and tile widths")
     ap.add_argument("--probe-mma", action="store_true",
                     help="measure the issue cost of tcgen05.mma over M, N and operand kind, and exit")
+    ap.add_argument("--medium-only", action="store_true",
+                    help="run only the medium workload's measurement (BF16 resident kernel) and exit")
     ap.add_argument("--kernel-case", type=int, nargs=2, metavar=("P", "T"),
                     help="time the fused extraction kernel alone on P starts of the workload for T steps "
                          "(two launches; a small case for profilers) and exit")
@@ -509,6 +511,19 @@ def medium_measure(mape, args, stream, flush):
     if not args.no_plain:
         out["vs_plain_fp32"] = plain_fp32(mape, wl, inst, starts, stream)
     return out
+
+
+def medium_only(args):
+    """The medium workload's measurement alone (the passes the "medium" key
+    reports): the command its launch list is taken on."""
+    import torch
+    from paper_2412_13576_gb300 import mape
+    torch.cuda.set_device(0)
+    mape.lib(build_if_missing=True)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    return {"medium": medium_measure(mape, args, stream, flush)}
 
 
 def time_extract_kernel(mape, inst, starts, P, T, prec, stream, reps, period=1):
@@ -1037,6 +1052,9 @@ def main(argv=None):
         return 0
     if args.streamed_case:
         print(json.dumps(streamed_case(args)), flush=True)
+        return 0
+    if args.medium_only:
+        print(json.dumps(medium_only(args)), flush=True)
         return 0
     res = run_reference(args) if args.impl == "reference" else run_ours(args)
     if res is not None:
