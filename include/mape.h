@@ -499,12 +499,20 @@ int mape_augment_run(const mape_augment_args* args, int64_t* iters_out,
  * item's results (X, fval, moves, nmoves, iterations) are identical to its
  * own mape_augment_run.  `workspace` holds the batch's tables
  * (mape_augment_run_batch_workspace_bytes(count)).
+ * done (optional) is called on the calling thread, once per item, as soon as
+ * a chunk shows that the item has finished (every start stopped, or its
+ * max_iters reached; items without starts or directions at once), with its
+ * iteration count; from then on the batch no longer writes that item's
+ * arrays (its X, fval, moves and nmoves may be read on another stream).
  * Errors: as mape_augment_run; BOUNDS if a start of any item lies outside its
- * box (no item then iterates).  Synchronous. */
+ * box (no item then iterates); after an error done is not called for the
+ * items not yet reported.  Synchronous. */
+typedef void (*mape_augment_done_fn)(int32_t item, int64_t iters, void* ctx);
 size_t mape_augment_run_batch_workspace_bytes(int32_t count);
 int mape_augment_run_batch(const mape_augment_args* items, int32_t count,
                            int64_t* iters_out, void* workspace,
-                           size_t workspace_bytes, void* stream);
+                           size_t workspace_bytes, void* stream,
+                           mape_augment_done_fn done, void* done_ctx);
 
 typedef struct {
   int32_t lanes;           /* chosen lanes per direction                     */

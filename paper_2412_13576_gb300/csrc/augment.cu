@@ -846,7 +846,8 @@ extern "C" size_t mape_augment_run_batch_workspace_bytes(int32_t count) {
 }
 
 extern "C" int mape_augment_run_batch(const mape_augment_args* items, int32_t count, int64_t* iters_out,
-                                      void* workspace, size_t workspace_bytes, void* stream) {
+                                      void* workspace, size_t workspace_bytes, void* stream,
+                                      mape_augment_done_fn done, void* done_ctx) {
   using namespace mape_detail;
   if (!items || count <= 0 || !iters_out) return MAPE_ERR_INVALID_ARG;
   int rc = MAPE_OK;
@@ -898,7 +899,11 @@ extern "C" int mape_augment_run_batch(const mape_augment_args* items, int32_t co
   }
   for (int i = 0; i < count; ++i) st_prefix[i + 1] = st_prefix[i] + items[i].S;
   const int64_t total_starts = st_prefix[count];
-  if (total_starts == 0) return MAPE_OK;
+  if (total_starts == 0) {
+    if (done)
+      for (int i = 0; i < count; ++i) done(i, 0, done_ctx);
+    return MAPE_OK;
+  }
   std::vector<unsigned int> h_active((size_t)count);
   for (int i = 0; i < count; ++i) h_active[i] = (unsigned)items[i].S;
   MAPE_CUDA_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int32_t) * count, st));
@@ -919,7 +924,11 @@ extern "C" int mape_augment_run_batch(const mape_augment_args* items, int32_t co
     if (items[i].K == 0) iters_out[i] = 1;  // as mape_augment_run: the initial pass only
     else max_iters = std::max(max_iters, items[i].max_iters);
   }
-  if (max_iters == 0) return MAPE_OK;  // no instance has an iteration to run
+  if (max_iters == 0) {  // no instance has an iteration to run
+    if (done)
+      for (int i = 0; i < count; ++i) done(i, iters_out[i], done_ctx);
+    return MAPE_OK;
+  }
   if ((rc = allow_score_smem(smem, true)) != MAPE_OK) return rc;
   if (!vec) {
     lanes = 1;
@@ -980,6 +989,33 @@ extern "C" int mape_augment_run_batch(const mape_augment_args* items, int32_t co
       return rc;
     }
   }
+  // items that have finished are reported (done) as soon as a chunk shows it:
+  // every start stopped, or its own iteration limit reached, or nothing to run
+  std::vector<char> told((size_t)count, 0);
+  std::vector<int64_t> it_now((size_t)count, 0);
+  auto running = [&](int i, int64_t iters_done) {
+    return items[i].S > 0 && items[i].K > 0 && h_active[(size_t)i] > 0 && iters_done < items[i].max_iters;
+  };
+  auto tell = [&](int64_t iters_done, bool all) -> int {
+    bool fresh = false;
+    for (int i = 0; i < count; ++i) fresh |= !told[(size_t)i] && (all || !running(i, iters_done));
+    if (!fresh || !done) return MAPE_OK;
+    launch(iters_max_kernel, (unsigned)count, 256, 0, st, (const AugView*)d_views, (int)count, d_iters);
+    MAPE_LAUNCH_CHECK();
+    MAPE_CUDA_TRY(cudaMemcpyAsync(it_now.data(), d_iters, sizeof(int64_t) * count, cudaMemcpyDeviceToHost, st));
+    MAPE_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < count; ++i) {
+      if (told[(size_t)i] || !(all || !running(i, iters_done))) continue;
+      told[(size_t)i] = 1;
+      const int64_t its = items[i].S == 0 ? 0 : (items[i].K == 0 ? 1 : it_now[(size_t)i]);
+      done(i, its, done_ctx);
+    }
+    return MAPE_OK;
+  };
+  if ((rc = tell(0, false)) != MAPE_OK) {
+    destroy_graph();
+    return rc;
+  }
   int64_t done_iters = 0;
   while (done_iters < max_iters) {
     if (exec) {
@@ -1002,9 +1038,12 @@ extern "C" int mape_augment_run_batch(const mape_augment_args* items, int32_t co
     }
     // an instance still running needs starts left and iterations left
     bool any = false;
-    for (int i = 0; i < count; ++i)
-      if (items[i].S > 0 && items[i].K > 0 && h_active[i] > 0 && done_iters < items[i].max_iters) any = true;
+    for (int i = 0; i < count; ++i) any |= running(i, done_iters);
     if (!any) break;
+    if ((rc = tell(done_iters, false)) != MAPE_OK) {
+      destroy_graph();
+      return rc;
+    }
   }
   destroy_graph();
   launch(iters_max_kernel, (unsigned)count, 256, 0, st, (const AugView*)d_views, (int)count, d_iters);
@@ -1014,5 +1053,8 @@ extern "C" int mape_augment_run_batch(const mape_augment_args* items, int32_t co
   MAPE_CUDA_TRY(cudaStreamSynchronize(st));
   for (int i = 0; i < count; ++i)
     if (items[i].S > 0 && items[i].K > 0) iters_out[i] = it[i];
+  if (done)
+    for (int i = 0; i < count; ++i)
+      if (!told[(size_t)i]) done(i, iters_out[i], done_ctx);
   return MAPE_OK;
 }

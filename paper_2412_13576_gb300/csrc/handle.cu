@@ -803,8 +803,19 @@ struct AugmentBatch {
   bool done = false;
   int rc = MAPE_OK;
   std::vector<int64_t> it1, it2;
+  std::vector<char> fin;  // per handle: its iterations are over (it2 set), before the whole batch ends
   double t0 = 0, t1 = 0;
 };
+
+// Called by mape_augment_run_batch as each handle's iterations end, so that
+// its worker reads back its result while the others still iterate.
+void augment_item_done(int32_t item, int64_t iters, void* ctx) {
+  AugmentBatch* b = static_cast<AugmentBatch*>(ctx);
+  std::lock_guard<std::mutex> lk(b->mu);
+  b->it2[(size_t)item] = iters;
+  b->fin[(size_t)item] = 1;
+  b->cv.notify_all();
+}
 
 int run_augment_batch(AugmentBatch& b) {
   const int count = (int)b.hs.size();
@@ -822,11 +833,9 @@ int run_augment_batch(AugmentBatch& b) {
   const size_t ws_bytes = mape_augment_run_batch_workspace_bytes(count);
   void* ws = h0->take<char>(h0->aug_bufs, ws_bytes);
   if (!ws) return MAPE_ERR_OOM;
-  b.it1.assign((size_t)count, 0);
-  b.it2.assign((size_t)count, 0);
   b.t0 = now_ms();
   for (int i = 0; i < count; ++i) items[(size_t)i].max_iters = std::min<int64_t>(1, max_iters[(size_t)i]);
-  H_TRY(mape_augment_run_batch(items.data(), count, b.it1.data(), ws, ws_bytes, h0->stream));
+  H_TRY(mape_augment_run_batch(items.data(), count, b.it1.data(), ws, ws_bytes, h0->stream, nullptr, nullptr));
   b.t1 = now_ms();
   bool more = false;
   for (int i = 0; i < count; ++i) {
@@ -838,7 +847,9 @@ int run_augment_batch(AugmentBatch& b) {
       a.S = 0;  // as run_augment: no second call for this handle
     }
   }
-  if (more) H_TRY(mape_augment_run_batch(items.data(), count, b.it2.data(), ws, ws_bytes, h0->stream));
+  std::vector<int64_t> it2((size_t)count, 0);
+  if (more) H_TRY(mape_augment_run_batch(items.data(), count, it2.data(), ws, ws_bytes, h0->stream,
+                                         augment_item_done, &b));
   return MAPE_OK;
 }
 
@@ -872,6 +883,9 @@ extern "C" int mape_augment_batch(mape_handle* hs, int32_t count, const int32_t*
   }
   auto b = std::make_shared<AugmentBatch>();
   b->hs.assign(hs, hs + count);
+  b->it1.assign((size_t)count, 0);
+  b->it2.assign((size_t)count, 0);
+  b->fin.assign((size_t)count, 0);
   for (int i = 0; i < count; ++i) mark_augmenting(hs[i]);
   for (int i = 0; i < count; ++i) {
     mape_handle h = hs[i];
@@ -885,9 +899,10 @@ extern "C" int mape_augment_batch(mape_handle* hs, int32_t count, const int32_t*
         b->done = true;
         b->cv.notify_all();
       } else {
+        // this handle's iterations end (reported by the batch), or the batch does
         std::unique_lock<std::mutex> lk(b->mu);
-        b->cv.wait(lk, [&] { return b->done; });
-        r = b->rc;
+        b->cv.wait(lk, [&] { return b->fin[(size_t)i] || b->done; });
+        r = b->fin[(size_t)i] ? MAPE_OK : b->rc;
       }
       if (r == MAPE_OK) r = h->augment_end(b->it1[(size_t)i], b->it2[(size_t)i], b->t0, b->t1);
       h->finish(r);

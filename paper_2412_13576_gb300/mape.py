@@ -199,7 +199,7 @@ _SIGS = {
     "mape_augment_workspace_bytes": (C.c_size_t, [I32, I32, I64]),
     "mape_augment_run": (C.c_int, [C.POINTER(AugmentArgs), C.POINTER(I64), P_]),
     "mape_augment_run_batch_workspace_bytes": (C.c_size_t, [I32]),
-    "mape_augment_run_batch": (C.c_int, [C.POINTER(AugmentArgs), I32, C.POINTER(I64), P_, C.c_size_t, P_]),
+    "mape_augment_run_batch": (C.c_int, [C.POINTER(AugmentArgs), I32, C.POINTER(I64), P_, C.c_size_t, P_, P_, P_]),
     "mape_augment_tune_lookup": (C.c_int, [I32, I64, I32, I32, C.POINTER(AugTuneInfo)]),
     "mape_augment_batch": (C.c_int, [C.POINTER(P_), I32, C.POINTER(P_), C.POINTER(I32)]),
     "mape_set_allocator": (C.c_int, [P_, P_, P_]),
@@ -633,11 +633,15 @@ def augment_run(G, n, a, q4, qr, qc, qv, c, w, l, u, X, *, max_iters=10 ** 6, mo
     return fval, iters.value, moves, nmoves
 
 
-def augment_run_batch(runs, *, stream=None):
+_DONE_FN = C.CFUNCTYPE(None, I32, I64, C.c_void_p)
+
+
+def augment_run_batch(runs, *, stream=None, on_done=None):
     """mape_augment_run_batch: Algorithm 1 for several instances in one
     sequence of launches.  runs: dicts of augment_run's arguments (G, n, a,
     q4, qr, qc, qv, c, w, l, u, X, and optionally max_iters, moves_cap,
-    lanes).  Returns one (fval, iters, moves, nmoves) per run."""
+    lanes).  on_done(item, iters) is called as each run's iterations end.
+    Returns one (fval, iters, moves, nmoves) per run."""
     k = len(runs)
     args, outs = [], []
     for r in runs:
@@ -649,7 +653,9 @@ def augment_run_batch(runs, *, stream=None):
     iters = (I64 * k)()
     dev = runs[0]["X"].device
     ws = _workspace(lib().mape_augment_run_batch_workspace_bytes(k), dev)
-    _check(lib().mape_augment_run_batch(items, k, iters, _ptr(ws), ws.numel(), _stream(stream)),
+    cb = _DONE_FN(lambda i, it, _ctx: on_done(int(i), int(it))) if on_done is not None else None
+    _check(lib().mape_augment_run_batch(items, k, iters, _ptr(ws), ws.numel(), _stream(stream),
+                                        C.cast(cb, C.c_void_p) if cb is not None else None, None),
            "mape_augment_run_batch")
     return [(fval, int(iters[i]), moves, nmoves) for i, (fval, moves, nmoves, _w) in enumerate(outs)]
 

@@ -173,7 +173,14 @@ def test_run_batch_equals_single_runs(M, lanes):
     cases = _batch_cases(M)
     single = [_run(M, _case(M, inst, D, w, X0, max_iters=mi, lanes=lanes)) for inst, D, w, X0, mi in cases]
     runs = [_case(M, inst, D, w, X0, max_iters=mi, lanes=lanes) for inst, D, w, X0, mi in cases]
-    batch = [_host(r["X"], *out) for r, out in zip(runs, M.augment_run_batch(runs))]
+    reported = []
+    batch = [_host(r["X"], *out) for r, out in zip(runs, M.augment_run_batch(
+        runs, on_done=lambda i, it: reported.append((i, it))))]
+    # every run is reported once, with its iteration count; the runs without
+    # starts or directions first, the one with 3 iterations before the longest
+    assert sorted(i for i, _ in reported) == list(range(len(runs)))
+    assert all(it == batch[i][2] for i, it in reported)
+    assert [i for i, _ in reported][:2] == sorted([len(runs) - 2, len(runs) - 1])
     for (inst, D, w, X0, mi), s, b in zip(cases, single, batch):
         assert np.array_equal(s[0], b[0]) and np.array_equal(s[1], b[1])
         assert s[2] == b[2]

@@ -131,13 +131,13 @@ def test_augment_batch_argument_checks(lib):
     up to 32, a null output."""
     from paper_2412_13576_gb300 import mape
     it = (ctypes.c_int64 * 2)()
-    assert lib.mape_augment_run_batch(None, 2, it, None, 0, None) == -1
+    assert lib.mape_augment_run_batch(None, 2, it, None, 0, None, None, None) == -1
     A = (mape.AugmentArgs * 1)()
     A[0].n, A[0].S, A[0].K, A[0].ldg, A[0].score_lanes = 4, 0, 0, 16, 3
-    assert lib.mape_augment_run_batch(A, 1, it, None, 0, None) == -1
+    assert lib.mape_augment_run_batch(A, 1, it, None, 0, None, None, None) == -1
     assert lib.mape_augment_run(ctypes.byref(A[0]), it, None) == -1
     A[0].score_lanes = 0
-    assert lib.mape_augment_run_batch(A, 0, it, None, 0, None) == -1
+    assert lib.mape_augment_run_batch(A, 0, it, None, 0, None, None, None) == -1
     assert lib.mape_augment_run_batch_workspace_bytes(0) == 0
     assert lib.mape_augment_run_batch_workspace_bytes(8) > 8 * 64
     assert lib.mape_augment_tune_lookup(4, 1, 1, 0, None) == -1
