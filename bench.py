@@ -608,7 +608,9 @@ def streamed_case(args):
     inst = {"large": I.large_quartic, "medium": I.medium_sparse,
             "uneven1000": lambda: I.uneven_single(1000, density=0.05)}[name]()
     bf = args.precision in ("bf16", "bf16x1")
-    prec = PREC[args.precision] | (0 if not bf else (mape.PREC_AUTOTUNE if args.autotune else mape.PREC_STREAMED))
+    tunable = bf or args.precision == "fp8"
+    prec = PREC[args.precision] | (mape.PREC_AUTOTUNE if (args.autotune and tunable) else
+                                   (mape.PREC_STREAMED if bf else 0))
     if args.sparse_fwd:
         prec |= mape.PREC_SPARSE_FWD
     Z0 = I.normal_starts(inst, P, std=LARGE["std"], seed=LARGE["seed"]).Z0

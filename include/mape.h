@@ -98,7 +98,8 @@ extern "C" {
 #define MAPE_PREC_STREAMED 0x100
 /* OR-ing MAPE_PREC_AUTOTUNE into a BF16 precision lets the library choose the
  * implementation and the streamed kernels' N-block widths (64, 128 or 256
- * rows of B per forward CTA, coordinates per gradient CTA) for this shape: the
+ * rows of B per forward CTA, coordinates per gradient CTA) for this shape
+ * (into MAPE_PREC_FP8: the widths of its streamed kernels only): the
  * first call for a (n, d, P rounded up to a power of two, precision) times a
  * few steps of every candidate on scratch copies of the call's state (inside
  * the workspace, which is larger with this bit) and keeps the fastest for the

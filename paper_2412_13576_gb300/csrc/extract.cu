@@ -139,14 +139,16 @@ namespace {
 bool valid_precision(int32_t precision) {
   const int32_t base = precision & MAPE_PREC_MASK, extra = precision & ~MAPE_PREC_MASK;
   if (base == MAPE_PREC_FP32 || base == MAPE_PREC_SPARSE) return extra == 0;
-  if (base == MAPE_PREC_FP8) return (extra & ~MAPE_PREC_STREAMED) == 0;
+  if (base == MAPE_PREC_FP8)  // streamed only; the tile widths may be autotuned
+    return (extra & ~(MAPE_PREC_STREAMED | MAPE_PREC_AUTOTUNE)) == 0 &&
+           !((extra & MAPE_PREC_STREAMED) && (extra & MAPE_PREC_AUTOTUNE));
   if ((extra & MAPE_PREC_STREAMED) && (extra & MAPE_PREC_AUTOTUNE)) return false;
   if ((extra & MAPE_PREC_SPARSE_FWD) && ((extra & MAPE_PREC_AUTOTUNE) || base != MAPE_PREC_BF16)) return false;
   return (base == MAPE_PREC_BF16 || base == MAPE_PREC_BF16X1) &&
          (extra & ~(MAPE_PREC_STREAMED | MAPE_PREC_AUTOTUNE | MAPE_PREC_SPARSE_FWD)) == 0;
 }
 
-// ---- autotuning of the BF16 implementation and the streamed tile widths ----
+// ---- autotuning of the implementation (BF16) and the streamed tile widths (BF16, FP8) ----
 
 struct TuneKey {
   int32_t n, d, pb, base;
@@ -203,7 +205,8 @@ static int autotune(const mape_extract_args* a, cudaStream_t st, size_t impl_byt
   if (!cv.ok) return MAPE_ERR_CAPACITY;
   std::vector<mape_tune_info> cands;
   mape_tune_info c{};
-  if (extract_tc_supported(n, d, a->precision & MAPE_PREC_MASK)) {
+  const bool f8 = (a->precision & MAPE_PREC_MASK) == MAPE_PREC_FP8;  // streamed dense forward only
+  if (!f8 && extract_tc_supported(n, d, a->precision & MAPE_PREC_MASK)) {
     c.path = 0;
     cands.push_back(c);
   }
@@ -214,6 +217,7 @@ static int autotune(const mape_extract_args* a, cudaStream_t st, size_t impl_byt
     }
   // the sparse forward (refused with SHAPE, and so skipped, when B does not qualify)
   for (int wg : {64, 128, 256}) {
+    if (f8) break;
     c.path = 2; c.wF = 256; c.wG = wg;
     cands.push_back(c);
   }
@@ -321,7 +325,8 @@ extern "C" int mape_extract(const mape_extract_args* a, void* stream) {
     if (a->workspace_bytes < mape_extract_workspace_bytes(a->n, a->d, a->P, a->precision)) return MAPE_ERR_CAPACITY;
     mape_extract_args b = *a;
     b.precision = base;
-    if (base == MAPE_PREC_FP8) return mape_detail::extract_stream(&b, st, mape_detail::kFwdDense);
+    if (base == MAPE_PREC_FP8 && !(a->precision & MAPE_PREC_AUTOTUNE))
+      return mape_detail::extract_stream(&b, st, mape_detail::kFwdDense);
     if (a->precision & MAPE_PREC_AUTOTUNE) {
       const size_t impl = mape_detail::align_up(mape_extract_workspace_bytes(a->n, a->d, a->P, base), 256);
       const TuneKey key{a->n, a->d, p_bucket(a->P), base};

@@ -62,3 +62,21 @@ def test_autotuned_call_equals_chosen_implementation(M, make, P, std):
     # a second call reuses the choice
     again = _run(M, inst, Z0, T, M.PREC_BF16 | M.PREC_AUTOTUNE)
     assert np.array_equal(again[0], tuned[0])
+
+
+def test_autotuned_fp8_widths(M):
+    """MAPE_PREC_FP8 | MAPE_PREC_AUTOTUNE: only the streamed kernels' widths
+    are candidates (nine), and the tuned call gives bitwise the result of the
+    default widths (the K order of every accumulation does not depend on
+    them)."""
+    inst = I.uneven_single(1000, density=0.05)
+    P, T = 1024, 12
+    Z0 = I.normal_starts(inst, P, std=0.3, seed=23).Z0
+    tuned = _run(M, inst, Z0, T, M.PREC_FP8 | M.PREC_AUTOTUNE)
+    info = M.autotune_info(inst.n, inst.d, P, M.PREC_FP8)
+    assert info is not None and len(info["candidates"]) == 9
+    assert all(c["path"] == "streamed" for c in info["candidates"])
+    ref = _run(M, inst, Z0, T, M.PREC_FP8)
+    for a, b in zip(tuned[:3], ref[:3]):
+        assert np.array_equal(a, b)
+    assert tuned[3] == ref[3]
