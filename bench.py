@@ -379,7 +379,7 @@ def e2e_passes(mape, wl, inst, starts_host, stream, reps, directions_hint, prec=
         units += D.shape[0]
         d2h = D.nbytes + x.nbytes + 8
     return {"value": units / sum(times), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "steps": len(times), "_last_directions": D}
+            "steps": len(times), "ms_per_step": [t * 1e3 for t in times], "_last_directions": D}
 
 
 def run_ours(args):
