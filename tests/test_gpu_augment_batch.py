@@ -177,7 +177,7 @@ def test_run_batch_equals_single_runs(M, lanes):
     batch = [_host(r["X"], *out) for r, out in zip(runs, M.augment_run_batch(
         runs, on_done=lambda i, it: reported.append((i, it))))]
     # every run is reported once, with its iteration count; the runs without
-    # starts or directions first, the one with 3 iterations before the longest
+    # starts or directions first
     assert sorted(i for i, _ in reported) == list(range(len(runs)))
     assert all(it == batch[i][2] for i, it in reported)
     assert [i for i, _ in reported][:2] == sorted([len(runs) - 2, len(runs) - 1])
