@@ -338,20 +338,30 @@ void mape_server::loop() {
         }
       }
       if (!aug.empty() && (!extracting || clock_ms() - aug_oldest > 5.0)) {
-        std::vector<mape_handle> hs;
-        std::vector<const int32_t*> X0;
-        std::vector<int32_t> S;
-        for (auto r : aug) {
-          hs.push_back(r->h);
-          X0.push_back(r->X0.data());
-          S.push_back(r->S);
-        }
-        const int rc = mape_augment_batch(hs.data(), (int32_t)hs.size(), X0.data(), S.data());
-        for (auto r : aug) {
-          r->aug_ready = false;
-          if (rc != MAPE_OK) finish(r, rc);
-          else r->stage = 2;
-        }
+        // the starts' uploads and feasibility checks run on a thread of their
+        // own (the requests stay at stage 3, which advance() skips, until the
+        // batch has started)
+        for (auto r : aug) r->aug_ready = false;
+        ++starting;
+        std::thread([this, aug]() {
+          cudaSetDevice(dev);
+          std::vector<mape_handle> hs;
+          std::vector<const int32_t*> X0;
+          std::vector<int32_t> S;
+          for (auto r : aug) {
+            hs.push_back(r->h);
+            X0.push_back(r->X0.data());
+            S.push_back(r->S);
+          }
+          const int rc = mape_augment_batch(hs.data(), (int32_t)hs.size(), X0.data(), S.data());
+          std::lock_guard<std::mutex> lk(mu);
+          for (auto r : aug) {
+            if (rc != MAPE_OK) finish(r, rc);
+            else r->stage = 2;
+          }
+          --starting;
+          cv.notify_all();
+        }).detach();
       }
     }
     // admission, in arrival order, while a slot and the memory allow
