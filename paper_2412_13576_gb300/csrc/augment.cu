@@ -64,9 +64,9 @@ __device__ __forceinline__ Best warp_min(Best v) {
   return v;
 }
 
-// One warp per direction: the lanes take the entries of Q (coalesced) and of
-// w, the direction's row is staged in shared memory, a warp reduction sums
-// (integer arithmetic, exact in any order).
+// One warp per group of directions: the lanes take the entries of Q
+// (coalesced) and of w, the directions' rows are staged in shared memory, a
+// warp reduction sums (integer arithmetic, exact in any order).
 constexpr int kCoefWarps = 8;
 constexpr int kCoefMaxRow = 4096;  // ldg <= 4096 bytes (n <= 4096)
 
@@ -75,56 +75,71 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// directions k0 .. k0 + cnt - 1 (cnt <= kCoefRows) by the calling warp (g:
+// its kCoefRows shared-memory rows, ldg bytes apart): each entry of Q and w
+// is loaded once for all of them, and their sums are independent chains
+constexpr int kCoefRows = 4;
 
-// direction k by the calling warp (g: its shared-memory row)
-__device__ __forceinline__ void coeffs_row(const int32_t* __restrict__ qr, const int32_t* __restrict__ qc,
-                                           const int32_t* __restrict__ qv, int nnz, const int32_t* __restrict__ w,
-                                           int n, const int8_t* __restrict__ G, int64_t k, int ldg, int vec,
-                                           int8_t* g, int64_t* __restrict__ a, int64_t* __restrict__ q4) {
+__device__ __forceinline__ void coeffs_rows(const int32_t* __restrict__ qr, const int32_t* __restrict__ qc,
+                                            const int32_t* __restrict__ qv, int nnz, const int32_t* __restrict__ w,
+                                            int n, const int8_t* __restrict__ G, int64_t k0, int cnt, int ldg,
+                                            int vec, int8_t* g, int64_t* __restrict__ a, int64_t* __restrict__ q4) {
   const int lane = threadIdx.x & 31;
-  if (vec) {  // rows 16-byte aligned (ldg a multiple of 16, G aligned)
-    const uint4* src = reinterpret_cast<const uint4*>(G + k * ldg);
-    for (int c = lane; c < ldg / 16; c += 32) reinterpret_cast<uint4*>(g)[c] = src[c];
-  } else {
-    for (int c = lane; c < n; c += 32) g[c] = G[k * ldg + c];
+  for (int q = 0; q < cnt; ++q) {
+    if (vec) {  // rows 16-byte aligned (ldg a multiple of 16, G aligned)
+      const uint4* src = reinterpret_cast<const uint4*>(G + (k0 + q) * ldg);
+      for (int c = lane; c < ldg / 16; c += 32) reinterpret_cast<uint4*>(g + q * ldg)[c] = src[c];
+    } else {
+      for (int c = lane; c < n; c += 32) g[q * ldg + c] = G[(k0 + q) * ldg + c];
+    }
   }
   __syncwarp();
-  long long acc = 0;
+  long long acc[kCoefRows] = {0, 0, 0, 0};
   for (int e = lane; e < nnz; e += 32) {
     const int i = qr[e], j = qc[e];
-    const long long t = (long long)qv[e] * g[i] * g[j];
-    acc += (i == j) ? t : 2 * t;
+    const long long v = (i == j) ? (long long)qv[e] : 2 * (long long)qv[e];
+#pragma unroll
+    for (int q = 0; q < kCoefRows; ++q) acc[q] += v * g[q * ldg + i] * g[q * ldg + j];  // rows past cnt: unused
   }
-  acc = warp_sum_ll(acc);
-  long long s4 = 0;
+  long long s4[kCoefRows] = {0, 0, 0, 0};
   if (w)
     for (int i = lane; i < n; i += 32) {
-      const long long gi = g[i];
-      s4 += (long long)w[i] * gi * gi * gi * gi;
+      const long long wi = w[i];
+#pragma unroll
+      for (int q = 0; q < kCoefRows; ++q) {
+        const long long gi = g[q * ldg + i];
+        s4[q] += wi * gi * gi * gi * gi;
+      }
     }
-  s4 = warp_sum_ll(s4);
-  if (lane == 0) {
-    a[k] = acc;
-    q4[k] = s4;
+#pragma unroll
+  for (int q = 0; q < kCoefRows; ++q) {
+    const long long sa = warp_sum_ll(acc[q]), sq = warp_sum_ll(s4[q]);
+    if (lane == 0 && q < cnt) {
+      a[k0 + q] = sa;
+      q4[k0 + q] = sq;
+    }
   }
 }
 
+// dynamic shared memory: kCoefWarps x kCoefRows rows of ldg bytes
 __global__ void coeffs_kernel(const int32_t* __restrict__ qr, const int32_t* __restrict__ qc,
                               const int32_t* __restrict__ qv, int nnz, const int32_t* __restrict__ w, int n,
                               const int8_t* __restrict__ G, int64_t K, int ldg, int vec, int64_t* __restrict__ a,
                               int64_t* __restrict__ q4) {
-  __shared__ __align__(16) int8_t s_row[kCoefWarps][kCoefMaxRow];
+  extern __shared__ __align__(16) int8_t s_rows[];
   const int wid = threadIdx.x >> 5;
-  const int64_t k = (int64_t)blockIdx.x * kCoefWarps + wid;
-  if (k >= K) return;  // warp-uniform
-  coeffs_row(qr, qc, qv, nnz, w, n, G, k, ldg, vec, s_row[wid], a, q4);
+  const int64_t k0 = ((int64_t)blockIdx.x * kCoefWarps + wid) * kCoefRows;
+  if (k0 >= K) return;  // warp-uniform
+  coeffs_rows(qr, qc, qv, nnz, w, n, G, k0, (int)(K - k0 < kCoefRows ? K - k0 : kCoefRows), ldg, vec,
+              s_rows + (size_t)wid * kCoefRows * ldg, a, q4);
 }
 
-// many instances: a warp per direction of any instance, the instance found by
-// binary search over the directions' prefix table
+// many instances: a warp per group of kCoefRows directions of any instance,
+// the instance found by binary search over the groups' prefix table; dynamic
+// shared memory kCoefWarps x kCoefRows rows of max_ldg bytes
 __global__ void coeffs_batch_kernel(const mape_coeffs_item* __restrict__ items, const int64_t* __restrict__ prefix,
-                                    const int32_t* __restrict__ vec, int count) {
-  __shared__ __align__(16) int8_t s_row[kCoefWarps][kCoefMaxRow];
+                                    const int32_t* __restrict__ vec, int count, int max_ldg) {
+  extern __shared__ __align__(16) int8_t s_rows[];
   const int wid = threadIdx.x >> 5;
   const int64_t g = (int64_t)blockIdx.x * kCoefWarps + wid;
   if (g >= prefix[count]) return;  // warp-uniform
@@ -134,8 +149,10 @@ __global__ void coeffs_batch_kernel(const mape_coeffs_item* __restrict__ items, 
     if (prefix[mid] <= g) lo = mid; else hi = mid - 1;
   }
   const mape_coeffs_item& it = items[lo];
-  coeffs_row(it.q_row, it.q_col, it.q_val, it.nnz, it.w, it.n, it.G, g - prefix[lo], it.ldg, vec[lo], s_row[wid],
-             it.a, it.q4);
+  const int64_t k0 = (g - prefix[lo]) * kCoefRows;
+  coeffs_rows(it.q_row, it.q_col, it.q_val, it.nnz, it.w, it.n, it.G, k0,
+              (int)(it.K - k0 < kCoefRows ? it.K - k0 : kCoefRows), it.ldg, vec[lo],
+              s_rows + (size_t)wid * kCoefRows * max_ldg, it.a, it.q4);
 }
 
 // One instance's arguments and its workspace, as the kernels see them.
@@ -709,8 +726,15 @@ extern "C" int mape_direction_coeffs(const int32_t* q_row, const int32_t* q_col,
   if (K == 0) return MAPE_OK;
   if (ldg > kCoefMaxRow) return MAPE_ERR_SHAPE;
   const int vec = (ldg % 16 == 0 && (reinterpret_cast<uintptr_t>(G) & 15) == 0) ? 1 : 0;
-  mape_detail::launch(coeffs_kernel, (unsigned)ceil_div(K, kCoefWarps), 32 * kCoefWarps, 0, as_stream(stream), q_row,
-                      q_col, q_val, nnz, w, n, G, K, ldg, vec, a, q4);
+  const size_t smem = (size_t)kCoefWarps * kCoefRows * ldg;
+  if (smem > 48 * 1024) {
+    size_t lim = 0;
+    const int rc = allow_max_dynamic_smem((const void*)coeffs_kernel, &lim);
+    if (rc != MAPE_OK) return rc;
+    if (smem > lim) return MAPE_ERR_SHAPE;
+  }
+  mape_detail::launch(coeffs_kernel, (unsigned)ceil_div(K, (int64_t)kCoefWarps * kCoefRows), 32 * kCoefWarps, smem,
+                      as_stream(stream), q_row, q_col, q_val, nnz, w, n, G, K, ldg, vec, a, q4);
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
 }
@@ -730,14 +754,16 @@ extern "C" int mape_direction_coeffs_batch(const mape_coeffs_item* items, int32_
   if (!items || count <= 0) return MAPE_ERR_INVALID_ARG;
   std::vector<int64_t> prefix((size_t)count + 1, 0);
   std::vector<int32_t> vec((size_t)count, 0);
+  int max_ldg = 16;
   for (int i = 0; i < count; ++i) {
     const mape_coeffs_item& it = items[i];
     if (it.nnz < 0 || it.n <= 0 || it.ldg < it.n || it.K < 0 || (it.nnz > 0 && (!it.q_row || !it.q_col || !it.q_val)) ||
         (it.K > 0 && (!it.G || !it.a || !it.q4)))
       return MAPE_ERR_INVALID_ARG;
     if (it.K > 0 && it.ldg > kCoefMaxRow) return MAPE_ERR_SHAPE;
-    prefix[(size_t)i + 1] = prefix[(size_t)i] + it.K;
+    prefix[(size_t)i + 1] = prefix[(size_t)i] + (it.K + kCoefRows - 1) / kCoefRows;  // groups of directions
     vec[(size_t)i] = (it.ldg % 16 == 0 && (reinterpret_cast<uintptr_t>(it.G) & 15) == 0) ? 1 : 0;
+    if (it.K > 0) max_ldg = std::max(max_ldg, (int)it.ldg);
   }
   const int64_t total = prefix[(size_t)count];
   if (total == 0) return MAPE_OK;
@@ -750,8 +776,15 @@ extern "C" int mape_direction_coeffs_batch(const mape_coeffs_item* items, int32_
   MAPE_CUDA_TRY(cudaMemcpyAsync(d_items, items, sizeof(mape_coeffs_item) * count, cudaMemcpyHostToDevice, st));
   MAPE_CUDA_TRY(cudaMemcpyAsync(d_prefix, prefix.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
   MAPE_CUDA_TRY(cudaMemcpyAsync(d_vec, vec.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, st));
-  launch(coeffs_batch_kernel, (unsigned)ceil_div(total, kCoefWarps), 32 * kCoefWarps, 0, st,
-         (const mape_coeffs_item*)d_items, (const int64_t*)d_prefix, (const int32_t*)d_vec, (int)count);
+  const size_t smem = (size_t)kCoefWarps * kCoefRows * max_ldg;
+  if (smem > 48 * 1024) {
+    size_t lim = 0;
+    const int rc = allow_max_dynamic_smem((const void*)coeffs_batch_kernel, &lim);
+    if (rc != MAPE_OK) return rc;
+    if (smem > lim) return MAPE_ERR_SHAPE;
+  }
+  launch(coeffs_batch_kernel, (unsigned)ceil_div(total, kCoefWarps), 32 * kCoefWarps, smem, st,
+         (const mape_coeffs_item*)d_items, (const int64_t*)d_prefix, (const int32_t*)d_vec, (int)count, max_ldg);
   MAPE_LAUNCH_CHECK();
   return MAPE_OK;
 }

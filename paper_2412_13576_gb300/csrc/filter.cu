@@ -110,46 +110,66 @@ __global__ void csr_fill_kernel(const int32_t* __restrict__ A, int m, int n, con
   }
 }
 
-// A g over a row staged in shared memory, one warp per candidate row: lane j
-// takes the rows j, j + 32, ... of A through their nonzeros (int64 sums, exact
-// for every int32 A and int8 g).  Each candidate row is read once, with
-// 16-byte loads.
+// A g over rows staged in shared memory, one warp per group of candidate
+// rows: lane j takes the rows j, j + 32, ... of A through their nonzeros
+// (int64 sums, exact for every int32 A and int8 g).  Each candidate row is
+// read once, with 16-byte loads.
 constexpr int kCsrWarps = 8;
 constexpr int kCsrMaxRow = 4096;
 
-// candidate row k against A, by the calling warp (row: its shared-memory row)
-__device__ __forceinline__ void csr_test_row(const uint32_t* __restrict__ rowptr, const uint16_t* __restrict__ col,
-                                             const int32_t* __restrict__ val, int m, const int8_t* __restrict__ G,
-                                             int64_t k, int ldg, int8_t* row, uint8_t* __restrict__ ok,
-                                             unsigned long long* __restrict__ fails) {
+// cnt <= kCsrRows candidate rows k0 .. k0 + cnt - 1 by the calling warp
+// (rows: its kCsrRows shared-memory rows, ldg bytes apart): every nonzero of A
+// is loaded once for all of them, and their sums are independent chains.
+constexpr int kCsrRows = 4;
+
+__device__ __forceinline__ void csr_test_rows(const uint32_t* __restrict__ rowptr, const uint16_t* __restrict__ col,
+                                              const int32_t* __restrict__ val, int m, const int8_t* __restrict__ G,
+                                              int64_t k0, int cnt, int ldg, int8_t* rows, uint8_t* __restrict__ ok,
+                                              unsigned long long* __restrict__ fails) {
   const int lane = threadIdx.x & 31;
   const int nv = ldg / 16;
-  const uint4* src = reinterpret_cast<const uint4*>(G + k * ldg);
-  for (int c = lane; c < nv; c += 32) reinterpret_cast<uint4*>(row)[c] = src[c];
-  __syncwarp();
-  bool good = true;
-  for (int r = lane; r < m; r += 32) {
-    long long acc = 0;
-    const uint32_t e1 = rowptr[r + 1];
-    for (uint32_t e = rowptr[r]; e < e1; ++e) acc += (long long)val[e] * row[col[e]];
-    good &= (acc == 0);
+  for (int q = 0; q < cnt; ++q) {
+    const uint4* src = reinterpret_cast<const uint4*>(G + (k0 + q) * ldg);
+    for (int c = lane; c < nv; c += 32) reinterpret_cast<uint4*>(rows + q * ldg)[c] = src[c];
   }
-  good = __all_sync(0xffffffffu, good);
-  if (lane == 0) {
-    ok[k] = good ? 1 : 0;
-    if (!good) atomicAdd(fails, 1ull);
+  __syncwarp();
+  bool good[kCsrRows];
+#pragma unroll
+  for (int q = 0; q < kCsrRows; ++q) good[q] = true;
+  for (int r = lane; r < m; r += 32) {
+    long long acc[kCsrRows] = {0, 0, 0, 0};
+    const uint32_t e1 = rowptr[r + 1];
+    for (uint32_t e = rowptr[r]; e < e1; ++e) {
+      const long long v = val[e];
+      const int c = col[e];
+#pragma unroll
+      for (int q = 0; q < kCsrRows; ++q) acc[q] += v * rows[q * ldg + c];  // rows past cnt: unused
+    }
+#pragma unroll
+    for (int q = 0; q < kCsrRows; ++q) good[q] &= (acc[q] == 0);
+  }
+#pragma unroll
+  for (int q = 0; q < kCsrRows; ++q) {
+    const bool g = __all_sync(0xffffffffu, good[q]);
+    if (lane == 0 && q < cnt) {
+      ok[k0 + q] = g ? 1 : 0;
+      if (!g) atomicAdd(fails, 1ull);
+    }
   }
   __syncwarp();
 }
 
+// dynamic shared memory: kCsrWarps x kCsrRows rows of ldg bytes
 __global__ void __launch_bounds__(32 * kCsrWarps)
 kernel_test_csr_kernel(const uint32_t* __restrict__ rowptr, const uint16_t* __restrict__ col,
                        const int32_t* __restrict__ val, int m, const int8_t* __restrict__ G, int64_t K,
                        int ldg, uint8_t* __restrict__ ok, unsigned long long* __restrict__ fails) {
-  __shared__ __align__(16) int8_t s_row[kCsrWarps][kCsrMaxRow];
+  extern __shared__ __align__(16) int8_t s_rows[];
   const int w = threadIdx.x >> 5;
-  for (int64_t k = blockIdx.x * (int64_t)kCsrWarps + w; k < K; k += (int64_t)gridDim.x * kCsrWarps)
-    csr_test_row(rowptr, col, val, m, G, k, ldg, s_row[w], ok, fails);
+  int8_t* rows = s_rows + (size_t)w * kCsrRows * ldg;
+  for (int64_t k0 = (blockIdx.x * (int64_t)kCsrWarps + w) * kCsrRows; k0 < K;
+       k0 += (int64_t)gridDim.x * kCsrWarps * kCsrRows)
+    csr_test_rows(rowptr, col, val, m, G, k0, (int)(K - k0 < kCsrRows ? K - k0 : kCsrRows), ldg, rows, ok, fails);
 }
 
 // ---- a11 ----------------------------------------------------------------------
@@ -651,8 +671,15 @@ extern "C" int mape_kernel_test(const int32_t* A, int32_t m, int32_t n, const in
     // exclusive prefix over m + 1 entries: entry m = nnz(A)
     mape_detail::launch(bin_scan_kernel, 1, 1024, 0, st, rowcnt, m + 1, rowptr, rowptr);
     mape_detail::launch(csr_fill_kernel, gw, 256, 0, st, A, m, n, rowptr, col, val);
-    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(K, kCsrWarps), 152 * 8);
-    mape_detail::launch(kernel_test_csr_kernel, grid, 32 * kCsrWarps, 0, st, rowptr, col, val, m, G, K, ldg, ok,
+    const size_t smem = (size_t)kCsrWarps * kCsrRows * ldg;
+    if (smem > 48 * 1024) {
+      size_t lim = 0;
+      const int rc = allow_max_dynamic_smem((const void*)kernel_test_csr_kernel, &lim);
+      if (rc != MAPE_OK) return rc;
+      if (smem > lim) return MAPE_ERR_SHAPE;
+    }
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(K, (int64_t)kCsrWarps * kCsrRows), 152 * 4);
+    mape_detail::launch(kernel_test_csr_kernel, grid, 32 * kCsrWarps, smem, st, rowptr, col, val, m, G, K, ldg, ok,
                         d_fail);
   }
   MAPE_LAUNCH_CHECK();
@@ -761,17 +788,21 @@ __global__ void csr_scan_batch_kernel(const KtView* __restrict__ v) {
   }
 }
 
-// prefix: candidate rows of all instances (a warp per row)
+// prefix: groups of kCsrRows candidate rows of every instance (a warp per
+// group); dynamic shared memory kCsrWarps x kCsrRows rows of max_ldg bytes
 __global__ void __launch_bounds__(32 * kCsrWarps)
 kernel_test_batch_kernel(const KtView* __restrict__ v, const int64_t* __restrict__ prefix, int count,
-                         unsigned long long* __restrict__ fails) {
-  __shared__ __align__(16) int8_t s_row[kCsrWarps][kCsrMaxRow];
+                         int max_ldg, unsigned long long* __restrict__ fails) {
+  extern __shared__ __align__(16) int8_t s_rows[];
   const int w = threadIdx.x >> 5;
   const int64_t g = blockIdx.x * (int64_t)kCsrWarps + w;
   if (g >= prefix[count]) return;  // warp-uniform
   const int i = find_inst(prefix, count, g);
   const KtView& d = v[i];
-  csr_test_row(d.rowptr, d.col, d.val, d.m, d.G, g - prefix[i], d.ldg, s_row[w], d.ok, fails + i);
+  const int64_t k0 = (g - prefix[i]) * kCsrRows;
+  const int cnt = (int)(d.K - k0 < kCsrRows ? d.K - k0 : kCsrRows);
+  csr_test_rows(d.rowptr, d.col, d.val, d.m, d.G, k0, cnt, d.ldg, s_rows + (size_t)w * kCsrRows * max_ldg, d.ok,
+                fails + i);
 }
 
 }  // namespace
@@ -803,6 +834,7 @@ extern "C" int mape_kernel_test_batch(mape_kernel_test_item* items, int32_t coun
   if (!bc.ok) return MAPE_ERR_CAPACITY;
   std::vector<KtView> v((size_t)count);
   std::vector<int64_t> px((size_t)2 * (count + 1), 0);
+  int max_ldg = 16;
   for (int i = 0; i < count; ++i) {
     mape_kernel_test_item& it = items[i];
     it.fail_count = 0;
@@ -817,7 +849,8 @@ extern "C" int mape_kernel_test_batch(mape_kernel_test_item* items, int32_t coun
     d.val = cv.take<int32_t>((size_t)it.m * it.n);
     if (!cv.ok) return MAPE_ERR_CAPACITY;
     px[(size_t)i + 1] = px[(size_t)i] + it.m;
-    px[(size_t)(count + 1) + i + 1] = px[(size_t)(count + 1) + i] + it.K;
+    px[(size_t)(count + 1) + i + 1] = px[(size_t)(count + 1) + i] + (it.K + kCsrRows - 1) / kCsrRows;
+    max_ldg = std::max(max_ldg, it.ldg);
   }
   const int64_t arows = px[(size_t)count], crows = px[(size_t)2 * count + 1];
   cudaStream_t st = as_stream(stream);
@@ -828,9 +861,17 @@ extern "C" int mape_kernel_test_batch(mape_kernel_test_item* items, int32_t coun
   launch(csr_batch_kernel, ga, 256, 0, st, (const KtView*)d_views, (const int64_t*)d_px, (int)count, 0);
   launch(csr_scan_batch_kernel, (unsigned)count, 1024, 0, st, (const KtView*)d_views);
   launch(csr_batch_kernel, ga, 256, 0, st, (const KtView*)d_views, (const int64_t*)d_px, (int)count, 1);
-  if (crows > 0)
-    launch(kernel_test_batch_kernel, (unsigned)ceil_div(crows, kCsrWarps), 32 * kCsrWarps, 0, st,
-           (const KtView*)d_views, (const int64_t*)(d_px + count + 1), (int)count, d_fail);
+  if (crows > 0) {  // crows: groups of kCsrRows candidate rows
+    const size_t smem = (size_t)kCsrWarps * kCsrRows * max_ldg;
+    if (smem > 48 * 1024) {
+      size_t lim = 0;
+      const int rc = allow_max_dynamic_smem((const void*)kernel_test_batch_kernel, &lim);
+      if (rc != MAPE_OK) return rc;
+      if (smem > lim) return MAPE_ERR_SHAPE;
+    }
+    launch(kernel_test_batch_kernel, (unsigned)ceil_div(crows, kCsrWarps), 32 * kCsrWarps, smem, st,
+           (const KtView*)d_views, (const int64_t*)(d_px + count + 1), (int)count, max_ldg, d_fail);
+  }
   MAPE_LAUNCH_CHECK();
   std::vector<unsigned long long> f((size_t)count, 0);
   MAPE_CUDA_TRY(cudaMemcpyAsync(f.data(), d_fail, sizeof(unsigned long long) * count, cudaMemcpyDeviceToHost, st));
