@@ -358,28 +358,35 @@ def e2e_passes(mape, wl, inst, starts_host, stream, reps, directions_hint, prec=
     x0_host = inst.xbar[None, :].astype(np.int32)
     D_host = torch.empty((max(int(1.2 * directions_hint), 1024), inst.n), dtype=torch.int8).pin_memory().numpy()
     cfg = mape.default_config(T=wl["T"], precision=prec, period=wl["period"])
-    times, units = [], 0
+    times, units, phases = [], 0, []
     h2d = (inst.A.nbytes + inst.b.nbytes + inst.l.nbytes + inst.u.nbytes + inst.B.nbytes + inst.Q.nbytes
            + inst.c.nbytes + (0 if inst.w is None else inst.w.nbytes) + src_host.nbytes + x0_host.nbytes)
     d2h = 0
     for _ in range(reps):
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        t = [time.perf_counter()]
         with mape.Instance.from_generated(inst, cfg, stream=stream) as he:
+            t.append(time.perf_counter())
             if Z0 is not None:
                 he.extract_directions(wl["P"], Z0=src_host)
             else:
                 he.extract_directions(wl["P"], G0=src_host)
             he.wait(900)
+            t.append(time.perf_counter())
             he.augment(x0_host)
             he.wait(900)
+            t.append(time.perf_counter())
             D = he.directions_i8(out=D_host)
             x, fx = he.solution()
-        times.append(time.perf_counter() - t0)
+            t.append(time.perf_counter())
+        t.append(time.perf_counter())
+        times.append(t[-1] - t[0])
+        phases.append({k: round((t[i + 1] - t[i]) * 1e3, 3)
+                       for i, k in enumerate(("create", "extract_filter", "augment", "download", "destroy"))})
         units += D.shape[0]
         d2h = D.nbytes + x.nbytes + 8
     return {"value": units / sum(times), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "steps": len(times), "ms_per_step": [t * 1e3 for t in times], "_last_directions": D}
+            "steps": len(times), "ms_per_step": [t * 1e3 for t in times], "phases_ms": phases, "_last_directions": D}
 
 
 def run_ours(args):

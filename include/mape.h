@@ -646,6 +646,9 @@ int mape_create_instance(const int32_t* A, const int64_t* b, const int32_t* l,
  * (Z0 [P x d], G0 == NULL) or as samples to project (G0 [P x n], Z0 == NULL).
  * Z0 / G0 may be host or device pointers (unified addressing); they are
  * copied before the call returns.
+ * The first call of a handle with G0 starts also forms the projection
+ * W = B (B^T B)^{-1} (as mape_project_prepare; NUMERIC if B^T B is not
+ * positive definite) and keeps it for later calls; calls with Z0 never need it.
  * Followed by dedup (a10), the kernel test (a9), the minimality filter (a11)
  * and the direction coefficients (a12).  Returns at once. */
 int mape_extract_directions(mape_handle h, int32_t P, const float* Z0,

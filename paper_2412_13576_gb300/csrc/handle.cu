@@ -103,6 +103,8 @@ struct mape_instance {
   int64_t* db = nullptr;
   int32_t *dc = nullptr, *dw = nullptr, *dqr = nullptr, *dqc = nullptr, *dqv = nullptr;
   float* dWproj = nullptr;  // B (B^T B)^{-1}, computed once per instance for the start projection
+  char* dWprojWork = nullptr;
+  bool proj_ready = false;  // dWproj holds W (formed at the first call with G0 starts)
 
   // extraction job buffers (replaced per extract call)
   std::vector<std::pair<void*, size_t>> job_bufs;
@@ -390,11 +392,18 @@ int upload(mape_instance* h, void* dst, const void* src, size_t bytes) {
 int set_objective(mape_instance* h, const mape_problem* f) {
   const int n = h->n;
   if (!f->Q || !f->c) return MAPE_ERR_INVALID_ARG;
-  std::vector<int32_t> qr, qc, qv;
+  // Q must be symmetric: compared in 64 x 64 blocks, so that the transposed
+  // reads stay within a few cache lines per row of a block
+  constexpr int kSymBlock = 64;
+  for (int i0 = 0; i0 < n; i0 += kSymBlock)
+    for (int j0 = i0; j0 < n; j0 += kSymBlock)
+      for (int i = i0; i < std::min(i0 + kSymBlock, n); ++i)
+        for (int j = std::max(j0, i + 1); j < std::min(j0 + kSymBlock, n); ++j)
+          if (f->Q[(int64_t)i * n + j] != f->Q[(int64_t)j * n + i]) return MAPE_ERR_INVALID_ARG;
+  std::vector<int32_t> qr, qc, qv;  // the upper triangle in COO form, row by row
   for (int i = 0; i < n; ++i)
     for (int j = i; j < n; ++j) {
-      int32_t v = f->Q[(int64_t)i * n + j];
-      if (v != f->Q[(int64_t)j * n + i]) return MAPE_ERR_INVALID_ARG;  // Q must be symmetric
+      const int32_t v = f->Q[(int64_t)i * n + j];
       if (v != 0) { qr.push_back(i); qc.push_back(j); qv.push_back(v); }
     }
   if (f->w)
@@ -506,19 +515,26 @@ extern "C" int mape_create_instance(const int32_t* A, const int64_t* b, const in
     return fail(MAPE_ERR_CUDA);
   if (bad) return fail(MAPE_ERR_NOT_KERNEL_BASIS);
   if ((rc = set_objective(h, f))) return fail(rc);
-  {
-    size_t pb = mape_project_prepare_workspace_bytes(n, d);
-    h->dWproj = h->take<float>(h->owned, (size_t)n * d);
-    char* pw = h->take<char>(h->owned, pb);
-    if (!h->dWproj || !pw) return fail(MAPE_ERR_OOM);
-    if ((rc = mape_project_prepare(h->dB, n, d, h->dWproj, pw, pb, h->stream))) return fail(rc);
-  }
   h->st.phase = MAPE_PHASE_IDLE;
   *out = h;
   return MAPE_OK;
 }
 
 namespace {
+
+// W = B (B^T B)^{-1} for the projection of G0 starts (a2), formed once per
+// instance, at its first job with G0 starts: a job given z0 directly never
+// needs it.  Synchronous on the handle's stream; the handle must be idle.
+int prepare_projection(mape_handle h) {
+  if (h->proj_ready) return MAPE_OK;
+  const size_t pb = mape_project_prepare_workspace_bytes(h->n, h->d);
+  if (!h->dWproj) h->dWproj = h->take<float>(h->owned, (size_t)h->n * h->d);
+  if (!h->dWprojWork) h->dWprojWork = h->take<char>(h->owned, pb);
+  if (!h->dWproj || !h->dWprojWork) return MAPE_ERR_OOM;
+  H_TRY(mape_project_prepare(h->dB, h->n, h->d, h->dWproj, h->dWprojWork, pb, h->stream));
+  h->proj_ready = true;
+  return MAPE_OK;
+}
 
 // The buffers of an extraction job of P starts and the upload of its starts;
 // the handle must be idle.
@@ -527,6 +543,7 @@ int prepare_job(mape_handle h, int32_t P, const float* Z0, const float* G0) {
   if (P <= 0 || (Z0 == nullptr) == (G0 == nullptr)) return MAPE_ERR_INVALID_ARG;
   if (!idle(h)) return MAPE_ERR_STATE;
   h->join();
+  if (G0) H_TRY(prepare_projection(h));
   if (mape_extract_workspace_bytes(h->n, h->d, P, h->cfg.precision) == 0) return MAPE_ERR_SHAPE;
   h->release_all(h->job_bufs);
   h->K = 0;

@@ -149,6 +149,33 @@ def test_handle_errors(M):
         assert e.value.code == -5
 
 
+def test_handle_projects_g0_starts(M):
+    """Starts given as samples g (a2: z0 = (B^T B)^{-1} B^T g inside the
+    handle, the projection formed at the first such call and kept): two calls
+    with G0 on one handle and one call with the stage entry point's z0 on
+    another return the same direction set (the projection's numerics are
+    checked against the oracle in the stage tests)."""
+    import torch
+    inst = I.small_dense()
+    P = 256
+    G0 = I.uniform_samples(inst, P, seed=11).G0
+    cfg = M.default_config(T=80)
+    Z = M.project_starts(torch.from_numpy(inst.B.astype(np.int32)).cuda(),
+                         torch.from_numpy(G0).cuda()).cpu().numpy()
+    sets = []
+    with M.Instance.from_generated(inst, cfg) as h:
+        for _ in range(2):
+            h.extract_directions(P, G0=G0)
+            h.wait(300)
+            sets.append(h.directions())
+    with M.Instance.from_generated(inst, cfg) as h:
+        h.extract_directions(P, Z0=Z)
+        h.wait(300)
+        sets.append(h.directions())
+    check_direction_set(inst, sets[0])
+    assert all(np.array_equal(sets[0], D) for D in sets[1:])
+
+
 def test_handle_initial_solutions_and_multistart_augmentation(M):
     """Eq. (4) on the handle gives distinct, exactly feasible starts S0; the
     multi-start augmentation from all of them (§3.3) gives, per start, the
