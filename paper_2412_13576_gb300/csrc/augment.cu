@@ -94,12 +94,16 @@ __device__ __forceinline__ void coeffs_rows(const int32_t* __restrict__ qr, cons
     }
   }
   __syncwarp();
+  // products of int8 entries in 32 bits (|g_i g_j| <= 2^14, twice that off
+  // the diagonal; g^4 <= 2^28), then one 32 x 32 -> 64-bit product each
   long long acc[kCoefRows] = {0, 0, 0, 0};
   for (int e = lane; e < nnz; e += 32) {
     const int i = qr[e], j = qc[e];
-    const long long v = (i == j) ? (long long)qv[e] : 2 * (long long)qv[e];
+    const int f = (i == j) ? 1 : 2;
+    const long long v = qv[e];
 #pragma unroll
-    for (int q = 0; q < kCoefRows; ++q) acc[q] += v * g[q * ldg + i] * g[q * ldg + j];  // rows past cnt: unused
+    for (int q = 0; q < kCoefRows; ++q)
+      acc[q] += v * (f * (int)g[q * ldg + i] * (int)g[q * ldg + j]);  // rows past cnt: unused
   }
   long long s4[kCoefRows] = {0, 0, 0, 0};
   if (w)
@@ -107,8 +111,9 @@ __device__ __forceinline__ void coeffs_rows(const int32_t* __restrict__ qr, cons
       const long long wi = w[i];
 #pragma unroll
       for (int q = 0; q < kCoefRows; ++q) {
-        const long long gi = g[q * ldg + i];
-        s4[q] += wi * gi * gi * gi * gi;
+        const int gi = g[q * ldg + i];
+        const int g2 = gi * gi;
+        s4[q] += wi * (g2 * g2);
       }
     }
 #pragma unroll
@@ -226,7 +231,20 @@ __device__ __forceinline__ long long floor_div(long long a, long long b) {  // b
 struct ScoreSmem {
   long long *r, *w3, *w2, *w1;  // 2 Q x + c; w x^3, w x^2, w x (quartic only)
   int32_t *up, *dn;             // u - x, x - l
+  const uint32_t* rcp;          // rcp[b] = ceil(2^20 / b), b = 1 .. 128
 };
+
+// floor(a / b) for 0 <= a < 2048 and 1 <= b <= 128 as (a ceil(2^20 / b)) >> 20:
+// with ceil(2^20 / b) = (2^20 + e) / b, 0 <= e < b, the product is
+// 2^20 (a / b) + a e / b and a e < 2^20, so the shift drops only the fraction
+// (division by an invariant integer by multiplication, Granlund and
+// Montgomery, PLDI 1994).  Other operands take the division instruction.
+// The steps' spans u - x, x - l lie in [0, 127] and |g_i| <= 128 (int8).
+constexpr int kRcpShift = 20;
+__device__ __forceinline__ int div_small(int a, int b, const uint32_t* rcp) {
+  if ((unsigned)a < 2048u && b <= 128) return (int)(((uint32_t)a * rcp[b]) >> kRcpShift);
+  return a / b;
+}
 
 __device__ __forceinline__ ScoreSmem stage_start(const AugView& v, int s) {
   extern __shared__ long long smem[];
@@ -238,6 +256,10 @@ __device__ __forceinline__ ScoreSmem stage_start(const AugView& v, int s) {
   t.w1 = t.w2 + n;
   t.up = reinterpret_cast<int32_t*>(t.w1 + n);
   t.dn = t.up + n;
+  __shared__ uint32_t s_rcp[129];
+  for (int b = threadIdx.x; b <= 128; b += blockDim.x)
+    s_rcp[b] = b ? ((1u << kRcpShift) + (uint32_t)b - 1u) / (uint32_t)b : 0u;
+  t.rcp = s_rcp;
   const int32_t* x = v.X + (int64_t)s * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     long long xi = x[i];
@@ -262,14 +284,14 @@ struct DirSums {
 
 __device__ __forceinline__ void add_entry(DirSums& d, const ScoreSmem& t, bool quartic, int i, int gi) {
   d.b += (long long)gi * t.r[i];
-  if (quartic) {
-    long long g1 = gi;
-    d.c1 += t.w3[i] * g1;
-    d.c2 += t.w2[i] * g1 * g1;
-    d.c3 += t.w1[i] * g1 * g1 * g1;
+  if (quartic) {  // g^2 <= 2^14 and |g^3| <= 2^21: one 64 x 32-bit product each
+    const int g2 = gi * gi;
+    d.c1 += t.w3[i] * gi;
+    d.c2 += t.w2[i] * g2;
+    d.c3 += t.w1[i] * (g2 * gi);
   }
   int ag = abs(gi);
-  int up = t.up[i] / ag, dn = t.dn[i] / ag;  // both nonnegative
+  int up = div_small(t.up[i], ag, t.rcp), dn = div_small(t.dn[i], ag, t.rcp);  // both nonnegative
   if (gi > 0) { d.lam_p = min(d.lam_p, up); d.lam_m = min(d.lam_m, dn); }
   else        { d.lam_p = min(d.lam_p, dn); d.lam_m = min(d.lam_m, up); }
 }
