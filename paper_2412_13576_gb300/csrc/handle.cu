@@ -981,8 +981,11 @@ extern "C" int mape_get_directions_i8(mape_handle h, int8_t* G, int64_t cap, int
   if (cap < h->K) return MAPE_ERR_CAPACITY;
   if (h->K == 0) return MAPE_OK;
   if (!G || ldg_out < h->n) return MAPE_ERR_INVALID_ARG;
-  cudaError_t e = cudaMemcpy2DAsync(G, (size_t)ldg_out, h->dirs, (size_t)h->ldg, (size_t)h->n, (size_t)h->K,
-                                    cudaMemcpyDeviceToHost, h->stream);
+  // one contiguous copy when both pitches equal the row length, else by rows
+  cudaError_t e = (ldg_out == h->n && h->ldg == h->n)
+                      ? cudaMemcpyAsync(G, h->dirs, (size_t)h->K * h->n, cudaMemcpyDeviceToHost, h->stream)
+                      : cudaMemcpy2DAsync(G, (size_t)ldg_out, h->dirs, (size_t)h->ldg, (size_t)h->n, (size_t)h->K,
+                                          cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     record_cuda_error(e, "get_directions_i8", __FILE__, __LINE__);
