@@ -127,6 +127,39 @@ def test_score_bytewise_rows(M):
     _oracle_moves(inst, None, D, X0, _run(M, _case(M, inst, D, None, X0, ldg=inst.n, lanes=8)))
 
 
+_WIDE = {}
+
+
+def _wide_case(quartic):
+    """Box spans of 127 (the largest the handle accepts) and direction entries
+    up to 120 in magnitude: the λ bounds floor((u - x) / |g_i|) take their
+    widest operands.  The directions are kernel vectors B z with sparse z of
+    entries up to 40, 12 and 3 in magnitude, kept while max |g| <= 120."""
+    if quartic not in _WIDE:
+        inst = I.make_instance("wide", 24, 4, c_k=1, c_density=None, lo=-63, hi=64, q_k=3, q_density=0.3,
+                               lin_k=200, w_max=2 if quartic else None, seed=1017)
+        rng = np.random.default_rng(23)
+        Z = np.concatenate([rng.integers(-k, k + 1, size=(200, inst.d)) * (rng.random((200, inst.d)) < 0.3)
+                            for k in (40, 12, 3)])
+        G = Z @ inst.B.T.astype(np.int64)
+        G = G[(np.abs(G).max(axis=1) <= 120) & np.any(G != 0, axis=1)]
+        G = np.unique(np.array([O.canonical_sign(g) for g in G]), axis=0)
+        G = G[rng.permutation(G.shape[0])[:200]]
+        X0 = _starts(inst, G, 2, seed=29)
+        _WIDE[quartic] = (inst, G, inst.w, X0)
+    return _WIDE[quartic]
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 0])
+@pytest.mark.parametrize("quartic", [False, True])
+def test_score_wide_spans_match_algorithm1(M, lanes, quartic):
+    inst, D, w, X0 = _wide_case(quartic)
+    assert D.shape[0] > 20 and int(np.abs(D).max()) > 90
+    got = _run(M, _case(M, inst, D, w, X0, lanes=lanes))
+    assert got[4].sum() > 0
+    _oracle_moves(inst, w, D, X0, got, key=("wide", quartic))
+
+
 def test_autotuned_lanes_recorded(M):
     inst, D, _, X0 = _medium_case(False)
     M.lib().mape_autotune_clear()
