@@ -352,7 +352,7 @@ int mape_kernel_test(const int32_t* A, int32_t m, int32_t n, const int8_t* G,
  * and gets the same flags and fail_count.  Every A goes to compressed rows
  * in its workspace (two launches over the rows of all the A's and one scan
  * block per instance), then one launch tests the rows of all instances, a
- * warp per row (the compressed-row product, exact for every int32 A).
+ * warp per four rows (the compressed-row product, exact for every int32 A).
  * `workspace` holds the batch's tables
  * (mape_kernel_test_batch_workspace_bytes(count)).  Errors: INVALID_ARG,
  * SHAPE as mape_kernel_test for any item (before any device work),
@@ -423,7 +423,7 @@ int mape_direction_coeffs(const int32_t* q_row, const int32_t* q_col,
                           int64_t* a, int64_t* q4, void* stream);
 
 /* a12 for many instances at once: item i is one mape_direction_coeffs call
- * and gets the same a and q4; one launch, a warp per direction of any
+ * and gets the same a and q4; one launch, a warp per four directions of any
  * instance.  `workspace`: mape_direction_coeffs_batch_workspace_bytes(count).
  * Errors: INVALID_ARG, SHAPE as mape_direction_coeffs for any item, CAPACITY,
  * CUDA.  Asynchronous (the items are copied before the call returns). */

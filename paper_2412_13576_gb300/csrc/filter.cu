@@ -694,8 +694,8 @@ extern "C" int mape_kernel_test(const int32_t* A, int32_t m, int32_t n, const in
 //
 // Every instance's A goes to compressed rows (one launch per kernel over the
 // rows of all the A's, one scan block per instance), then one launch tests
-// the candidate rows of all instances, a warp per row finding its instance by
-// binary search over the launch's prefix table.  The compressed-row test is
+// the candidate rows of all instances, a warp per four rows finding its
+// instance by binary search over the launch's prefix table.  The compressed-row test is
 // exact for every int32 A, so each instance's flags and count equal those of
 // its own mape_kernel_test (whichever path that takes).
 
