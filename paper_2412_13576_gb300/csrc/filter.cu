@@ -181,15 +181,34 @@ __device__ __forceinline__ void prep_row(const int8_t* __restrict__ G, int64_t k
   const int8_t* g = G + k * ldg;
   int s = 0;
   uint64_t* pm = masks + k * 2 * W;
+  // rows 16-byte aligned (ldg a multiple of 16, G aligned): 16-byte loads,
+  // four per mask word (a piece starting below n ends within the pitch)
+  const bool vec = (ldg & 15) == 0 && (reinterpret_cast<uintptr_t>(G) & 15) == 0;
   for (int w = 0; w < W; ++w) {
     uint64_t pos = 0, neg = 0;
-    for (int b = 0; b < 64; ++b) {
-      int i = w * 64 + b;
-      if (i >= n) break;
-      int v = g[i];
-      s += abs(v);
-      if (v > 0) pos |= 1ull << b;
-      if (v < 0) neg |= 1ull << b;
+    if (vec) {
+      for (int q = 0; q < 4; ++q) {
+        const int i0 = w * 64 + q * 16;
+        if (i0 >= n) break;
+        const int4 pc = *reinterpret_cast<const int4*>(g + i0);
+        const uint32_t wd[4] = {(uint32_t)pc.x, (uint32_t)pc.y, (uint32_t)pc.z, (uint32_t)pc.w};
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+          const int v = (i0 + b < n) ? (int)(int8_t)(wd[b >> 2] >> (8 * (b & 3))) : 0;
+          s += abs(v);
+          if (v > 0) pos |= 1ull << (q * 16 + b);
+          if (v < 0) neg |= 1ull << (q * 16 + b);
+        }
+      }
+    } else {
+      for (int b = 0; b < 64; ++b) {
+        int i = w * 64 + b;
+        if (i >= n) break;
+        int v = g[i];
+        s += abs(v);
+        if (v > 0) pos |= 1ull << b;
+        if (v < 0) neg |= 1ull << b;
+      }
     }
     pm[w] = pos;
     pm[W + w] = neg;
