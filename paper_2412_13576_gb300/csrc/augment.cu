@@ -75,6 +75,7 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
 // directions k0 .. k0 + cnt - 1 (cnt <= kCoefRows) by the calling warp (g:
 // its kCoefRows shared-memory rows, ldg bytes apart): each entry of Q and w
 // is loaded once for all of them, and their sums are independent chains
