@@ -228,11 +228,15 @@ __device__ __forceinline__ long long floor_div(long long a, long long b) {  // b
   return q;
 }
 
-// The per-start tables the score pass reads for every direction.
+// The per-start tables the score pass reads for every direction, by
+// coordinate i: rw[2 i] = (r_i, w x_i^3), rw[2 i + 1] = (w x_i^2, w x_i) with
+// r = 2 Q x + c (the w terms 0 without the quartic term), ud[i] = (u - x,
+// x - l), so that an entry takes one 16-byte load (two with the quartic term)
+// and one 8-byte load.
 struct ScoreSmem {
-  long long *r, *w3, *w2, *w1;  // 2 Q x + c; w x^3, w x^2, w x (quartic only)
-  int32_t *up, *dn;             // u - x, x - l
-  const uint32_t* rcp;          // rcp[b] = ceil(2^20 / b), b = 1 .. 128
+  longlong2* rw;
+  int2* ud;
+  const uint32_t* rcp;  // rcp[b] = ceil(2^20 / b), b = 1 .. 128
 };
 
 // floor(a / b) for 0 <= a < 2048 and 1 <= b <= 128 as (a ceil(2^20 / b)) >> 20:
@@ -248,31 +252,22 @@ __device__ __forceinline__ int div_small(int a, int b, const uint32_t* rcp) {
 }
 
 __device__ __forceinline__ ScoreSmem stage_start(const AugView& v, int s) {
-  extern __shared__ long long smem[];
+  extern __shared__ __align__(16) long long smem[];
   const int n = v.n;
   ScoreSmem t;
-  t.r = smem;
-  t.w3 = t.r + n;
-  t.w2 = t.w3 + n;
-  t.w1 = t.w2 + n;
-  t.up = reinterpret_cast<int32_t*>(t.w1 + n);
-  t.dn = t.up + n;
+  t.rw = reinterpret_cast<longlong2*>(smem);                 // 32 n bytes
+  t.ud = reinterpret_cast<int2*>(smem + 4 * (int64_t)n);    // 8 n bytes
   __shared__ uint32_t s_rcp[129];
   for (int b = threadIdx.x; b <= 128; b += blockDim.x)
     s_rcp[b] = b ? ((1u << kRcpShift) + (uint32_t)b - 1u) / (uint32_t)b : 0u;
   t.rcp = s_rcp;
   const int32_t* x = v.X + (int64_t)s * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    long long xi = x[i];
-    t.r[i] = v.R[(int64_t)s * n + i];
-    t.up[i] = v.u[i] - x[i];
-    t.dn[i] = x[i] - v.l[i];
-    if (v.w) {
-      long long wi = v.w[i];
-      t.w3[i] = wi * xi * xi * xi;
-      t.w2[i] = wi * xi * xi;
-      t.w1[i] = wi * xi;
-    }
+    const long long xi = x[i];
+    const long long wi = v.w ? v.w[i] : 0;
+    t.rw[2 * i] = make_longlong2(v.R[(int64_t)s * n + i], wi * xi * xi * xi);
+    t.rw[2 * i + 1] = make_longlong2(wi * xi * xi, wi * xi);
+    t.ud[i] = make_int2(v.u[i] - x[i], x[i] - v.l[i]);
   }
   return t;
 }
@@ -284,15 +279,18 @@ struct DirSums {
 };
 
 __device__ __forceinline__ void add_entry(DirSums& d, const ScoreSmem& t, bool quartic, int i, int gi) {
-  d.b += (long long)gi * t.r[i];
+  const longlong2 rw = t.rw[2 * i];
+  d.b += (long long)gi * rw.x;
   if (quartic) {  // g^2 <= 2^14 and |g^3| <= 2^21: one 64 x 32-bit product each
+    const longlong2 ww = t.rw[2 * i + 1];
     const int g2 = gi * gi;
-    d.c1 += t.w3[i] * gi;
-    d.c2 += t.w2[i] * g2;
-    d.c3 += t.w1[i] * (g2 * gi);
+    d.c1 += rw.y * gi;
+    d.c2 += ww.x * g2;
+    d.c3 += ww.y * (g2 * gi);
   }
-  int ag = abs(gi);
-  int up = div_small(t.up[i], ag, t.rcp), dn = div_small(t.dn[i], ag, t.rcp);  // both nonnegative
+  const int2 ud = t.ud[i];
+  const int ag = abs(gi);
+  const int up = div_small(ud.x, ag, t.rcp), dn = div_small(ud.y, ag, t.rcp);  // both nonnegative
   if (gi > 0) { d.lam_p = min(d.lam_p, up); d.lam_m = min(d.lam_m, dn); }
   else        { d.lam_p = min(d.lam_p, dn); d.lam_m = min(d.lam_m, up); }
 }
